@@ -1,0 +1,9 @@
+"""FP64 CPU oracle for the rasterizer and the anchor decoder.
+
+TEST INFRASTRUCTURE: imported only by the test-suite, the package smoke check
+and the benchmark's CPU-baseline and reference arms.  The CUDA product path
+never imports, links or runs anything in this package, and this package imports
+nothing from the product.
+"""
+from .raster import Options, Margins, render, render_scene, project, extent, quat_to_rotmat  # noqa: F401
+from .decode import decode, decode_scene, bf16_round, n_mlp_params, flatten_mlp, MLP_ORDER  # noqa: F401,E402
