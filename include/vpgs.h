@@ -1,0 +1,265 @@
+/*
+ * vpgs.h - C ABI of the GB300 (sm_103a) rasterizer and anchor decoder of
+ * VPGS-SLAM (voxel-based progressive Gaussian SLAM).
+ *
+ * The library renders 3D Gaussians into RGB, depth and accumulated alpha, and
+ * differentiates the render with respect to every Gaussian parameter and the
+ * 6-DoF camera pose.  The mapping loss (Sec. III-A, Eq. 7) and the coarse
+ * tracking stage (Sec. III-B) both use this render.  The library also decodes
+ * voxel anchors into neural Gaussians (Sec. III-A, Eq. 1-5) and
+ * differentiates that decode.
+ *
+ * Conventions for every entry point
+ *   - Pointers are DEVICE pointers unless a comment says "host".  Arrays are
+ *     dense, C-contiguous, little-endian and 16-byte aligned.  The caller
+ *     owns them all.
+ *   - The library allocates no memory.  Entry points that need scratch space
+ *     carve it from a caller-provided device workspace.  Size the workspace
+ *     with the matching *_workspace_bytes function.  The workspace must not
+ *     be shared by calls that may run concurrently.
+ *   - Every call is asynchronous on `stream` (NULL = the legacy default
+ *     stream).  No call synchronises with the host, so the calls can be
+ *     captured into a CUDA graph.
+ *   - Argument errors that the host can see (NULL pointers, negative sizes,
+ *     a workspace that is too small, unsupported options) return
+ *     VPGS_ERR_INVALID_ARG or VPGS_ERR_UNSUPPORTED and launch nothing.
+ *     Conditions found on the device (instance capacity exceeded, a
+ *     look-back wait that ran out) set a status word in the workspace.  The
+ *     outputs are then undefined.  Read the status with vpgs_workspace_status
+ *     after the stream has been synchronised.
+ *   - Kernel launch failures return VPGS_ERR_CUDA.
+ *
+ * Camera model (the paper gives only "known intrinsics K" and poses
+ * {R|t}, Sec. III).  T_cw is the world-to-camera rigid transform, stored as
+ * row-major double[4][4].  A camera-space point is p = R mu + t; the camera
+ * looks down +z, with +x right and +y down.  Pixel (i, j) has its centre at
+ * (i + 0.5, j + 0.5).
+ */
+#ifndef VPGS_H
+#define VPGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *vpgs_stream; /* a cudaStream_t */
+
+typedef enum {
+    VPGS_OK = 0,
+    VPGS_ERR_INVALID_ARG = 1,
+    VPGS_ERR_CAPACITY = 2,    /* device: more tile instances than the workspace holds */
+    VPGS_ERR_NONFINITE = 3,   /* device: a NaN/Inf input was seen */
+    VPGS_ERR_TIMEOUT = 4,     /* device: a bounded look-back wait ran out */
+    VPGS_ERR_CUDA = 5,        /* a CUDA runtime call failed */
+    VPGS_ERR_UNSUPPORTED = 6
+} vpgs_status;
+
+/* Pinhole intrinsics and image size, shared by every view of a call (host struct). */
+typedef struct {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+} vpgs_camera;
+
+/* Rasterizer options (host struct).  vpgs_render_opts_default() fills these defaults:
+ *   tile 16x16, alpha_min 1/255, alpha_max 0.99, t_min 1e-4, dilation 0.3 px^2,
+ *   near_z 0.2, background black.
+ * The paper cites 3D Gaussian Splatting for all of these (Sec. I, Sec. II) and
+ * states none of them. */
+typedef struct {
+    int32_t tile_w, tile_h;   /* tile_w * tile_h threads per tile; each in [4, 32], product <= 1024 */
+    float alpha_min;          /* skip a Gaussian at a pixel when alpha < alpha_min */
+    float alpha_max;          /* alpha = min(alpha_max, o exp(-d^T Sigma'^-1 d / 2)) */
+    float t_min;              /* stop before the first Gaussian that would take T below t_min */
+    float dilation;           /* added to the diagonal of the 2D covariance (px^2) */
+    float near_z;             /* Gaussians with camera z <= near_z are dropped */
+    float bg[3];              /* C = sum_i alpha_i T_i c_i + T_final bg */
+    int32_t persistent_ctas;  /* 0 = one CTA per tile; >0 = that many persistent CTAs per SM */
+} vpgs_render_opts;
+
+/* Gaussians, structure of arrays, float32 (device).
+ *   means [n,3], scales [n,3] (linear, > 0), quats [n,4] (w,x,y,z; normalised
+ *   inside), opacities [n] (in (0,1)), colors [n,3] (RGB).
+ * n is the capacity.  If n_dev is not NULL, the live count is the device scalar
+ * *n_dev (<= n), for example the output count of vpgs_decode_anchors.  Entries
+ * at and past *n_dev are ignored. */
+typedef struct {
+    const float *means, *scales, *quats, *opacities, *colors;
+    int64_t n;
+    const int32_t *n_dev;
+} vpgs_gaussians;
+
+/* Writable per-Gaussian arrays with the same layout as vpgs_gaussians.  Used
+ * for gradients (accumulated with +=; a NULL field is not computed) and for
+ * decoder outputs (written). */
+typedef struct {
+    float *means, *scales, *quats, *opacities, *colors;
+} vpgs_gaussian_buffers;
+
+/* Render outputs for V views (device, written by vpgs_render_fwd).
+ *   rgb [V,3,H,W], depth [V,H,W] (sum alpha_i T_i z_i, not normalised),
+ *   alpha [V,H,W] (1 - T_final), t_final [V,H,W],
+ *   n_contrib [V,H,W] (Gaussians blended into the pixel), n_iter [V,H,W] (how
+ *   many entries of the pixel's tile list the pixel walked; vpgs_render_bwd
+ *   reads it).  t_final and n_iter are required; the others may be NULL. */
+typedef struct {
+    float *rgb, *depth, *alpha, *t_final;
+    int32_t *n_contrib, *n_iter;
+} vpgs_images;
+
+/* Counters that a render leaves in its workspace (host struct, filled by
+ * vpgs_workspace_status). */
+typedef struct {
+    int32_t status;           /* a vpgs_status value */
+    int64_t n_visible;        /* (view, Gaussian) pairs touching at least one tile */
+    int64_t n_instances;      /* (view, tile, Gaussian) instances that were sorted */
+} vpgs_render_stats;
+
+void vpgs_render_opts_default(vpgs_render_opts *opts);            /* opts: host */
+
+/* Workspace size in bytes for renders of up to max_gaussians Gaussians into
+ * n_views views of the given camera, with room for max_instances tile
+ * instances.  Returns 0 if the arguments are invalid. */
+size_t vpgs_render_workspace_bytes(int64_t max_gaussians, int32_t n_views, const vpgs_camera *cam,
+                                   const vpgs_render_opts *opts, int64_t max_instances);
+
+/* Differentiable tile rasterization, forward pass (3D Gaussian Splatting as the
+ * paper uses it: Sec. I, Sec. II; RGB and depth renders in Sec. III-B and
+ * Eq. 14, accumulated alpha in Sec. III-A "Voxel-Based Submap Expansion").
+ *
+ * For each view v: project every Gaussian (EWA splatting), bin it into the
+ * tiles its alpha >= alpha_min ellipse can reach, sort each tile's list by
+ * camera depth (ties by Gaussian index), and blend front to back.
+ *   T_cw  [n_views,4,4] float64, device.
+ *   ws    workspace of ws_bytes bytes, from vpgs_render_workspace_bytes.
+ * Results are independent of the tile shape. */
+vpgs_status vpgs_render_fwd(void *ws, size_t ws_bytes, const vpgs_gaussians *g,
+                            const vpgs_camera *cam, const double *T_cw, int32_t n_views,
+                            const vpgs_render_opts *opts, const vpgs_images *out, vpgs_stream stream);
+
+/* Backward pass of vpgs_render_fwd.  It recomputes the projection, binning and
+ * per-tile sort from the inputs and stores none of them.  It reads
+ * fwd->t_final and fwd->n_iter from the forward call with identical inputs and
+ * options, then back-propagates
+ *   dL_drgb [V,3,H,W], dL_ddepth [V,H,W], dL_dalpha [V,H,W] (each may be NULL = 0)
+ * to the Gaussian parameters (grads: += into each non-NULL field; grads may be
+ * NULL) and to the camera poses.
+ *   dL_dpose [n_views,6] float64, device, += ; may be NULL.  Each pose gets a
+ *   left perturbation T_cw <- Exp(xi) T_cw at xi = 0, with
+ *   xi = (rho_x, rho_y, rho_z, phi_x, phi_y, phi_z).  The pose is optimised in
+ *   the coarse tracking stage (Sec. III-B).  Per-Gaussian pose terms are summed
+ *   in float64.
+ * Decisions (skips, clamp, stop) are held fixed, as in the forward pass. */
+vpgs_status vpgs_render_bwd(void *ws, size_t ws_bytes, const vpgs_gaussians *g,
+                            const vpgs_camera *cam, const double *T_cw, int32_t n_views,
+                            const vpgs_render_opts *opts, const vpgs_images *fwd,
+                            const float *dL_drgb, const float *dL_ddepth, const float *dL_dalpha,
+                            const vpgs_gaussian_buffers *grads, double *dL_dpose,
+                            vpgs_stream stream);
+
+/* Projection stage of vpgs_render_fwd alone: per (view, Gaussian) EWA
+ * projection and tile extent, written out for inspection (device outputs,
+ * each may be NULL):
+ *   tile_count [V,N] int32 (tiles the Gaussian is binned into; 0 = culled),
+ *   tile_rect [V,N,4] int32 (tx0, tx1, ty0, ty1, inclusive), mean2d [V,N,2]
+ *   float32 (u, v), depth [V,N] float32 (camera z), conic [V,N,3] float32
+ *   (a, b, c of Sigma'^-1 = [[a,b],[b,c]]).
+ * Entries of culled Gaussians other than tile_count are left unchanged. */
+vpgs_status vpgs_render_project(void *ws, size_t ws_bytes, const vpgs_gaussians *g,
+                                const vpgs_camera *cam, const double *T_cw, int32_t n_views,
+                                const vpgs_render_opts *opts, int32_t *tile_count,
+                                int32_t *tile_rect, float *mean2d, float *depth, float *conic,
+                                vpgs_stream stream);
+
+/* Reads the status word and counters of a render workspace (host `stats`).  It
+ * synchronises `stream` first, and is the one call here that blocks. */
+vpgs_status vpgs_workspace_status(const void *ws, vpgs_render_stats *stats, vpgs_stream stream);
+
+/* One step of the camera pose on the device (coarse tracking, Sec. III-B;
+ * the step rule is not given in the paper).  For each view v:
+ *   xi = -lr * m_hat / (sqrt(v_hat) + 1e-15)  (Adam, beta 0.9/0.999; adam_state
+ *        [n_views,13] float64 = m[6], v[6], step; zero it before the first step)
+ *   or xi = -lr * g  when adam_state is NULL;
+ *   T_cw[v] <- Exp(xi) T_cw[v]  (SE(3) exponential, float64)
+ * lr[0] applies to rho and lr[1] to phi (host values).  dL_dpose is read,
+ * then zeroed, so repeated steps can be replayed from a CUDA graph. */
+vpgs_status vpgs_pose_step(double *T_cw, double *dL_dpose, double *adam_state, int32_t n_views,
+                           const double lr[2], vpgs_stream stream);
+
+/* ---------------------------------------------------------------------- */
+/* Anchor decoder (Sec. III-A, Eq. 1-5)                                    */
+/* ---------------------------------------------------------------------- */
+
+/* Voxel anchors (device).
+ *   anchors [n,3] float32 (voxel centres x^a), scaling [n,3] float32 (l),
+ *   offsets [n,k,3] float32 (O), features [n,32] float32, or bfloat16 when
+ *   features_bf16 != 0 (f^a). */
+typedef struct {
+    const float *anchors, *scaling, *offsets;
+    const void *features;
+    int64_t n;
+    int32_t k;
+    int32_t features_bf16;
+} vpgs_anchors;
+
+/* Decoder MLPs (device), float32, flat.  For each MLP in the order opacity,
+ * colour, covariance, the layout is W1 [32,36], b1 [32], W2 [out,32],
+ * b2 [out], with out = k, 3k, 7k.  That is 3*(36*32+32) + 11k*32 + 11k
+ * floats (7,182 at k = 10).  bf16 != 0 selects the tensor-core decode: the
+ * network input, W1, W2 and the hidden activations are rounded to bfloat16,
+ * and the sums are accumulated in float32.  The FP32 form is used otherwise. */
+typedef struct {
+    const float *params;
+    int32_t bf16;
+} vpgs_mlp;
+
+/* Decoder options (host struct). */
+typedef struct {
+    float near_z;   /* anchors with camera z <= near_z are culled */
+    float guard;    /* keep anchors whose projected centre lies in the image widened by guard*W, guard*H */
+} vpgs_decode_opts;
+
+size_t vpgs_decode_workspace_bytes(int64_t n_anchors, int32_t k);
+
+/* Decode the anchors seen by one camera into neural Gaussians.
+ *   Cull each anchor by its camera depth and projected centre.
+ *   Eq. 3: view distance delta and direction d from the camera centre
+ *     -R^T t.
+ *   Eq. 2: [f^a, d, delta] goes through three LINEAR-ReLU-LINEAR MLPs.
+ *   Heads: tanh opacity (valid iff > 0), sigmoid colour (Eq. 4), normalised
+ *     quaternion, sigmoid(F_s) * l scale (Eq. 5).
+ *   Eq. 1: mu^m = x^a + O^m * l.
+ * The valid Gaussians are compacted in (anchor, m) order into `out`, which
+ * has capacity n*k.
+ *   T_cw [4,4] float64 device; n_out device int32 scalar (written);
+ *   src_index [n*k] int32 device (written; entry i = anchor*k + m of output i). */
+vpgs_status vpgs_decode_anchors(void *ws, size_t ws_bytes, const vpgs_anchors *a,
+                                const vpgs_mlp *mlp, const vpgs_camera *cam, const double *T_cw,
+                                const vpgs_decode_opts *opts, const vpgs_gaussian_buffers *out,
+                                int32_t *n_out, int32_t *src_index, vpgs_stream stream);
+
+/* Backward pass of vpgs_decode_anchors.  Inputs and options must be those of
+ * the forward call.  dL_dgauss holds the gradients with respect to the decoded
+ * Gaussians: n is the capacity and n_dev = n_out.  Outputs are float32 and
+ * accumulated (+=):
+ *   dL_dfeatures [n,32], dL_doffsets [n,k,3], dL_dscaling [n,3], and
+ *   dL_dparams, laid out as vpgs_mlp.params.
+ * Any output may be NULL.  The anchor centres and the camera receive no gradient. */
+vpgs_status vpgs_decode_anchors_bwd(void *ws, size_t ws_bytes, const vpgs_anchors *a,
+                                    const vpgs_mlp *mlp, const vpgs_camera *cam,
+                                    const double *T_cw, const vpgs_decode_opts *opts,
+                                    const vpgs_gaussians *dL_dgauss, const int32_t *src_index,
+                                    float *dL_dfeatures, float *dL_doffsets, float *dL_dscaling,
+                                    float *dL_dparams, vpgs_stream stream);
+
+const char *vpgs_status_string(vpgs_status s);
+/* Library version, "major.minor.patch" (host string). */
+const char *vpgs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VPGS_H */

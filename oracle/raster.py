@@ -29,8 +29,8 @@ rule below is the reading written out in the design notes, items C1-C12):
                  (rho_x, rho_y, rho_z, phi_x, phi_y, phi_z).
 
 The oracle composites every pixel against every Gaussian in depth order; the
-only shortcut is a candidate filter that drops Gaussians whose (slightly
-widened) extent rectangle misses the pixel block, which provably leaves every
+only shortcut is a candidate filter that drops Gaussians whose (widened)
+extent rectangle misses the pixel block, which provably leaves every
 alpha >= alpha_min pixel in (tests check `brute=True` gives the same result).
 
 Pins (tests/test_oracle_render.py): single-Gaussian closed forms, rotation
@@ -276,13 +276,14 @@ def render(means, scales, quats, opacities, colors, T_cw, fx, fy, cx, cy, width,
               "z": proj["z"].detach().clone().requires_grad_(want),
               "rgb": c3.detach().clone().requires_grad_(want)}
         order = _sorted_live(proj, ext)
-        # conservative candidate rectangles (a hair wider than the exact ones)
+        # candidate rectangles, widened so that every pixel at which an FP32
+        # evaluation could still reach alpha_min is evaluated (and flagged)
         rx, ry = ext["rx"], ext["ry"]
         un, vn = proj["u"].detach().numpy(), proj["v"].detach().numpy()
-        cx0 = un - rx * (1 + 1e-9) - 1e-9 - 0.5
-        cx1 = un + rx * (1 + 1e-9) + 1e-9 - 0.5
-        cy0 = vn - ry * (1 + 1e-9) - 1e-9 - 0.5
-        cy1 = vn + ry * (1 + 1e-9) + 1e-9 - 0.5
+        cx0 = un - rx * (1 + 1e-4) - 0.02 - 0.5
+        cx1 = un + rx * (1 + 1e-4) + 0.02 - 0.5
+        cy0 = vn - ry * (1 + 1e-4) - 0.02 - 0.5
+        cy1 = vn + ry * (1 + 1e-4) + 0.02 - 0.5
         order_np = order.numpy()
         for j in row_list:
             if brute:

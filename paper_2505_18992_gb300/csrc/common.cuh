@@ -1,0 +1,205 @@
+// Internal definitions shared by the CUDA translation units of libvpgs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "../../include/vpgs.h"
+
+#define VPGS_HD __host__ __device__ __forceinline__
+#define VPGS_D __device__ __forceinline__
+
+namespace vpgs {
+
+constexpr int kWarp = 32;
+
+// ---------------------------------------------------------------------------
+// status word: the first error wins (atomicCAS from OK)
+// ---------------------------------------------------------------------------
+VPGS_D void set_status(uint32_t *status, uint32_t code) {
+    atomicCAS(status, (uint32_t)VPGS_OK, code);
+}
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2.
+// Error-free transformations per Dekker / Knuth (TwoSum), with the product
+// error taken by one fused multiply-add.  Used where FP32 rounding of a pixel
+// position (~1e-4 px at u ~ 1000) would be visible in alpha.
+// ---------------------------------------------------------------------------
+struct df {
+    float hi, lo;
+};
+
+VPGS_D df two_sum(float a, float b) {
+    float s = a + b;
+    float bb = s - a;
+    float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+VPGS_D df quick_two_sum(float a, float b) {  // requires |a| >= |b|
+    float s = a + b;
+    return {s, b - (s - a)};
+}
+VPGS_D df two_prod(float a, float b) {
+    float p = a * b;
+    return {p, fmaf(a, b, -p)};
+}
+VPGS_D df df_add(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    float e = s.lo + (a.lo + b.lo);
+    return quick_two_sum(s.hi, e);
+}
+VPGS_D df df_mul_f(df a, float b) {
+    df p = two_prod(a.hi, b);
+    p.lo = fmaf(a.lo, b, p.lo);
+    return quick_two_sum(p.hi, p.lo);
+}
+VPGS_D df df_div(df a, df b) {
+    float q1 = a.hi / b.hi;
+    df qb = df_mul_f(b, q1);
+    df r = df_add(a, df{-qb.hi, -qb.lo});
+    float q2 = r.hi / b.hi;
+    return quick_two_sum(q1, q2);
+}
+VPGS_D df df_from_double(double x) {
+    float hi = (float)x;
+    return {hi, (float)(x - (double)hi)};
+}
+
+// ---------------------------------------------------------------------------
+// camera pose in the two precisions the kernels use
+// ---------------------------------------------------------------------------
+struct PoseDF {
+    df R[9];
+    df t[3];
+};
+
+VPGS_D void load_pose(const double *T, PoseDF &P) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) P.R[3 * r + c] = df_from_double(__ldg(T + 4 * r + c));
+        P.t[r] = df_from_double(__ldg(T + 4 * r + 3));
+    }
+}
+
+// p_c = R mu + t in double-float, mu exact float32
+VPGS_D void transform_df(const PoseDF &P, float mx, float my, float mz, df out[3]) {
+    const float m[3] = {mx, my, mz};
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        df acc = P.t[r];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            df p = two_prod(P.R[3 * r + c].hi, m[c]);
+            p.lo = fmaf(P.R[3 * r + c].lo, m[c], p.lo);
+            acc = df_add(acc, p);
+        }
+        out[r] = acc;
+    }
+}
+
+// rotation matrix of q / |q|, q = (w, x, y, z)
+VPGS_D void quat_to_rot(float w, float x, float y, float z, float R[9]) {
+    float inv = rsqrtf(w * w + x * x + y * y + z * z);
+    w *= inv; x *= inv; y *= inv; z *= inv;
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// ---------------------------------------------------------------------------
+// per-(view, Gaussian) screen-space record: 4 x float4 = 64 bytes
+//   r0 = (u_hi, v_hi, u_lo, v_lo)   image mean as a double-float pair
+//   r1 = (w1x, w1y, w2x, w2y)       whitening rows: d^T Sigma'^-1 d = (w1.d)^2 + (w2.d)^2
+//   r2 = (opacity, z, r, g)
+//   r3 = (b, -, -, -)
+// The whitening rows are the eigenvectors of Sigma' scaled by 1/sqrt(lambda),
+// which evaluates the quadratic form without the cancellation the
+// (a dx^2 + 2 b dx dy + c dy^2) form suffers on elongated Gaussians.
+// ---------------------------------------------------------------------------
+struct __align__(16) Rec {
+    float4 r0, r1, r2, r3;
+};
+
+// evaluated per pixel/Gaussian pair, bit-identically in forward and backward
+struct PairEval {
+    float t1, t2, G, alpha;
+};
+
+VPGS_D PairEval eval_pair(float dx, float dy, float w1x, float w1y, float w2x, float w2y,
+                          float opac, float alpha_max) {
+    PairEval e;
+    e.t1 = fmaf(w1x, dx, w1y * dy);
+    e.t2 = fmaf(w2x, dx, w2y * dy);
+    float power = -0.5f * fmaf(e.t1, e.t1, e.t2 * e.t2);
+    e.G = __expf(power);
+    e.alpha = fminf(alpha_max, opac * e.G);
+    return e;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace of a render call.  All pointers are carved from one caller buffer.
+// ---------------------------------------------------------------------------
+struct RenderLayout {
+    int64_t N;          // Gaussian capacity
+    int32_t V;          // views
+    int32_t tiles_x, tiles_y, T;  // tiles per view
+    int64_t VN;         // V * N
+    int64_t M_cap;      // instance capacity
+    int32_t tile_bits;  // bits of a global tile id
+    // offsets in bytes
+    size_t off_status, off_counters, off_rec, off_rect, off_tcount, off_scan_a, off_dkey0,
+        off_dval0, off_dkey1, off_dval1, off_ikey0, off_ival0, off_ikey1, off_ival1, off_ranges,
+        off_sort_hist, off_sort_look, off_scan_look, off_g2d, off_pose, total;
+    int64_t sort_blocks_max, scan_blocks_max;
+};
+
+// counters[] slots
+enum {
+    CNT_VISIBLE = 0,   // number of visible (view, Gaussian) pairs
+    CNT_INSTANCES = 1, // number of tile instances
+    CNT_TICKET_A = 2,  // decoupled look-back tickets (reset before each use)
+    CNT_TICKET_B = 3,  // 3..6: one ticket per sort pass
+    CNT_WORK = 7,      // persistent-kernel work queue
+    CNT_N = 8
+};
+
+struct RenderWs {
+    uint32_t *status;
+    uint32_t *counters;
+    Rec *rec;
+    uint2 *rect;          // (tx0 | tx1 << 16, ty0 | ty1 << 16)
+    uint32_t *tcount;
+    uint32_t *scan_a;     // scratch for scans
+    uint32_t *dkey[2], *dval[2];
+    uint32_t *ikey[2], *ival[2];
+    uint2 *ranges;
+    uint32_t *sort_hist;  // [passes][256] global digit histograms
+    uint32_t *sort_look;  // look-back status words
+    unsigned long long *scan_look;
+    float *g2d;           // [VN,10] 2D gradients
+    double *pose;         // [V,6]
+};
+
+// radix sort geometry
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;                     // per thread
+constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per block
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kMaxSortPasses = 8;
+
+// scan geometry
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// bounded spin for decoupled look-back: the predecessor always holds an
+// earlier ticket and is therefore resident, so this bound is never reached in
+// a healthy run; reaching it records VPGS_ERR_TIMEOUT and the kernel goes on.
+constexpr int kSpinLimit = 1 << 22;
+
+}  // namespace vpgs

@@ -1,0 +1,370 @@
+// Device-wide primitives: a single-pass exclusive scan and a stable LSD radix
+// sort, both with decoupled look-back (Merrill & Garland, "Single-pass Parallel
+// Prefix Scan with Decoupled Look-back", 2016; Adinets & Merrill, "Onesweep",
+// 2022).  Logical block ids come from an atomic ticket, so a block only ever
+// waits on blocks that started before it.  Every wait is bounded (kSpinLimit);
+// running out records VPGS_ERR_TIMEOUT and the kernel carries on.
+#pragma once
+
+#include "common.cuh"
+
+namespace vpgs {
+
+VPGS_D unsigned long long ld_volatile_u64(const unsigned long long *p) {
+    return *reinterpret_cast<const volatile unsigned long long *>(p);
+}
+VPGS_D void st_volatile_u64(unsigned long long *p, unsigned long long v) {
+    *reinterpret_cast<volatile unsigned long long *>(p) = v;
+}
+VPGS_D uint32_t ld_volatile_u32(const uint32_t *p) {
+    return *reinterpret_cast<const volatile uint32_t *>(p);
+}
+VPGS_D void st_volatile_u32(uint32_t *p, uint32_t v) {
+    *reinterpret_cast<volatile uint32_t *>(p) = v;
+}
+VPGS_D uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of n uint32 values: out prefix handed to a store functor
+//   Load:  __device__ uint32_t operator()(int64_t i) const         (i < n)
+//   Store: __device__ void operator()(int64_t i, uint32_t excl, uint32_t v) const
+// The scan total is written to *total (when total != nullptr).
+// n = min(n_cap, *n_dev) if n_dev else n_cap.
+// Status word layout (64 bit): [63:62] flag 1 = aggregate, 2 = inclusive prefix.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagPre = 2ull << 62;
+constexpr unsigned long long kValMask = (1ull << 62) - 1;
+
+template <class Load, class Store>
+__global__ void __launch_bounds__(kScanThreads)
+scan_kernel(Load load, Store store, int64_t n_cap, const uint32_t *n_dev, uint32_t *ticket,
+            unsigned long long *look, uint32_t *total, uint32_t *status) {
+    __shared__ uint32_t s_items[kScanTile + kScanTile / 32];
+    __shared__ uint32_t s_warp[kScanThreads / kWarp];
+    __shared__ uint32_t s_bid, s_excl;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_bid = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const int64_t bid = s_bid;
+    int64_t n = n_cap;
+    if (n_dev) n = min(n, (int64_t)*n_dev);
+    const int64_t base = bid * kScanTile;
+    if (base >= n) {
+        if (bid == 0 && tid == 0 && total) *total = 0;
+        return;
+    }
+    // striped, coalesced loads into a padded shared tile
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        int idx = j * kScanThreads + tid;
+        int64_t gi = base + idx;
+        s_items[idx + (idx >> 5)] = gi < n ? load(gi) : 0u;
+    }
+    __syncthreads();
+    // blocked: thread t owns items t*16 .. t*16+15
+    uint32_t v[kScanItems];
+    uint32_t tsum = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        int idx = tid * kScanItems + i;
+        v[i] = s_items[idx + (idx >> 5)];
+        tsum += v[i];
+    }
+    // block exclusive scan of the thread sums
+    uint32_t x = tsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < kScanThreads / kWarp ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < kScanThreads / kWarp) s_warp[lane] = w;  // inclusive warp totals
+    }
+    __syncthreads();
+    const uint32_t block_agg = s_warp[kScanThreads / kWarp - 1];
+    uint32_t texcl = x - tsum + (warp > 0 ? s_warp[warp - 1] : 0u);
+    // decoupled look-back (one thread)
+    if (tid == 0) {
+        uint32_t excl = 0;
+        if (bid == 0) {
+            st_volatile_u64(look, kFlagPre | block_agg);
+        } else {
+            st_volatile_u64(look + bid, kFlagAgg | block_agg);
+            int64_t j = bid - 1;
+            unsigned long long acc = 0;
+            while (j >= 0) {
+                unsigned long long w = ld_volatile_u64(look + j);
+                int spins = 0;
+                while ((w >> 62) == 0) {
+                    if (++spins > kSpinLimit) {
+                        set_status(status, VPGS_ERR_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(64);
+                    w = ld_volatile_u64(look + j);
+                }
+                acc += w & kValMask;
+                if ((w >> 62) == 2 || spins > kSpinLimit) break;
+                --j;
+            }
+            excl = (uint32_t)acc;
+            st_volatile_u64(look + bid, kFlagPre | (acc + block_agg));
+        }
+        s_excl = excl;
+        if (base + kScanTile >= n && total) *total = excl + block_agg;
+    }
+    __syncthreads();
+    uint32_t run = s_excl + texcl;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t gi = base + (int64_t)tid * kScanItems + i;
+        if (gi < n) store(gi, run, v[i]);
+        run += v[i];
+    }
+}
+
+inline int64_t scan_blocks(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
+
+// Launch a scan over at most n_cap items.  ticket / look must be zero on entry;
+// this launcher clears them on `stream` first.
+template <class Load, class Store>
+cudaError_t launch_scan(Load load, Store store, int64_t n_cap, const uint32_t *n_dev,
+                        uint32_t *ticket, unsigned long long *look, uint32_t *total,
+                        uint32_t *status, cudaStream_t stream) {
+    int64_t nb = scan_blocks(n_cap);
+    if (nb == 0) nb = 1;
+    cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(uint32_t), stream);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(look, 0, nb * sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return e;
+    scan_kernel<<<(unsigned)nb, kScanThreads, 0, stream>>>(load, store, n_cap, n_dev, ticket, look,
+                                                           total, status);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Stable LSD radix sort of (uint32 key, uint32 value) pairs.
+// One kernel computes the global histograms of every pass; then one kernel per
+// pass ranks and scatters ("one sweep") with per-digit decoupled look-back.
+// ---------------------------------------------------------------------------
+struct SortPass {
+    int shift, bits;
+};
+
+static __global__ void __launch_bounds__(256)
+radix_histogram_kernel(const uint32_t *keys, int64_t n_cap, const uint32_t *n_dev, int n_passes,
+                       SortPass p0, SortPass p1, SortPass p2, SortPass p3, uint32_t *hist) {
+    __shared__ uint32_t s_h[4][kRadix];
+    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0;
+    __syncthreads();
+    int64_t n = n_cap;
+    if (n_dev) n = min(n, (int64_t)*n_dev);
+    const SortPass ps[4] = {p0, p1, p2, p3};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t k = keys[i];
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+            if (p < n_passes) atomicAdd(&s_h[p][(k >> ps[p].shift) & ((1u << ps[p].bits) - 1u)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_passes * kRadix; i += blockDim.x) {
+        uint32_t c = (&s_h[0][0])[i];
+        if (c) atomicAdd(hist + i, c);
+    }
+}
+
+// look-back status word: [31:30] flag (1 aggregate, 2 inclusive), [29:0] count
+constexpr uint32_t kSFlagAgg = 1u << 30;
+constexpr uint32_t kSFlagPre = 2u << 30;
+constexpr uint32_t kSValMask = (1u << 30) - 1u;
+
+static __global__ void __launch_bounds__(kSortThreads)
+radix_onesweep_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__restrict__ val_in,
+                      uint32_t *__restrict__ key_out, uint32_t *__restrict__ val_out,
+                      int64_t n_cap, const uint32_t *n_dev, SortPass pass,
+                      const uint32_t *__restrict__ pass_hist, uint32_t *ticket, uint32_t *look,
+                      uint32_t *status) {
+    constexpr int kWarps = kSortThreads / kWarp;
+    constexpr int kSeg = kWarp * kSortItems;  // contiguous items per warp
+    __shared__ uint32_t s_cnt[kWarps][kRadix];
+    __shared__ uint32_t s_glob[kRadix];
+    __shared__ uint32_t s_bid;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_bid = atomicAdd(ticket, 1u);
+    for (int i = tid; i < kWarps * kRadix; i += kSortThreads) (&s_cnt[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t bid = s_bid;
+    int64_t n = n_cap;
+    if (n_dev) n = min(n, (int64_t)*n_dev);
+    const int64_t base = bid * kSortTile;
+    if (base >= n) return;
+    const uint32_t mask = (1u << pass.bits) - 1u;
+
+    // global exclusive digit offsets of this pass (every block recomputes them)
+    if (tid < kRadix) {
+        // 256 threads: inclusive scan via shared memory in two levels of warps
+        uint32_t h = pass_hist[tid];
+        uint32_t x = h;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        s_glob[tid] = x;  // inclusive within warp
+    }
+    __syncthreads();
+    uint32_t glob_excl = 0;
+    if (tid < kRadix) {
+        uint32_t add = 0;
+        for (int w = 0; w < warp; ++w) add += s_glob[w * 32 + 31];
+        glob_excl = s_glob[tid] - pass_hist[tid] + add;
+    }
+
+    // load this warp's contiguous segment, 32 consecutive keys per step
+    uint32_t k[kSortItems], v[kSortItems], d[kSortItems];
+    const int64_t seg = base + (int64_t)warp * kSeg;
+#pragma unroll
+    for (int s = 0; s < kSortItems; ++s) {
+        int64_t i = seg + s * kWarp + lane;
+        bool ok = i < n;
+        k[s] = ok ? key_in[i] : 0u;
+        v[s] = ok ? val_in[i] : 0u;
+        d[s] = ok ? ((k[s] >> pass.shift) & mask) : (kRadix + lane);  // sentinel never matches
+    }
+    // per-warp digit counts
+#pragma unroll
+    for (int s = 0; s < kSortItems; ++s) {
+        uint32_t m = __match_any_sync(0xffffffffu, d[s]);
+        if (d[s] < kRadix && (m & lanemask_lt()) == 0) s_cnt[warp][d[s]] += __popc(m);
+        __syncwarp();
+    }
+    __syncthreads();
+    // block count per digit, publish, look back
+    if (tid < kRadix) {
+        uint32_t c = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) c += s_cnt[w][tid];
+        uint32_t excl = 0;
+        uint32_t *my = look + bid * kRadix + tid;
+        if (bid == 0) {
+            st_volatile_u32(my, kSFlagPre | c);
+        } else {
+            st_volatile_u32(my, kSFlagAgg | c);
+            int64_t j = bid - 1;
+            uint32_t acc = 0;
+            while (j >= 0) {
+                const uint32_t *p = look + j * kRadix + tid;
+                uint32_t w = ld_volatile_u32(p);
+                int spins = 0;
+                while ((w >> 30) == 0) {
+                    if (++spins > kSpinLimit) {
+                        set_status(status, VPGS_ERR_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(32);
+                    w = ld_volatile_u32(p);
+                }
+                acc += w & kSValMask;
+                if ((w >> 30) == 2 || spins > kSpinLimit) break;
+                --j;
+            }
+            excl = acc;
+            st_volatile_u32(my, kSFlagPre | (acc + c));
+        }
+        // per-warp bases inside the block, offset by everything before it
+        uint32_t run = glob_excl + excl;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            uint32_t t = s_cnt[w][tid];
+            s_cnt[w][tid] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+    // stable scatter: order inside a step by lane, steps in order, warps in order
+#pragma unroll
+    for (int s = 0; s < kSortItems; ++s) {
+        uint32_t m = __match_any_sync(0xffffffffu, d[s]);
+        uint32_t rank = __popc(m & lanemask_lt());
+        if (d[s] < kRadix) {
+            const uint32_t pos = s_cnt[warp][d[s]] + rank;
+            if ((int64_t)pos < n) {  // always true unless a look-back wait timed out
+                key_out[pos] = k[s];
+                val_out[pos] = v[s];
+            }
+        }
+        __syncwarp();
+        if (d[s] < kRadix && rank == 0) s_cnt[warp][d[s]] += __popc(m);
+        __syncwarp();
+    }
+}
+
+// Split `bits` low key bits starting at `lo` into balanced passes of <= 8 bits.
+inline int plan_passes(int lo, int bits, SortPass *out) {
+    int np = (bits + kRadixBits - 1) / kRadixBits;
+    if (np == 0) return 0;
+    int base = bits / np, extra = bits % np, s = lo;
+    for (int p = 0; p < np; ++p) {
+        int b = base + (p < extra ? 1 : 0);
+        out[p] = {s, b};
+        s += b;
+    }
+    return np;
+}
+
+inline int64_t sort_blocks(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
+
+// Sort n (<= n_cap, or *n_dev) pairs from (k0, v0) using (k1, v1) as the other
+// buffer.  Returns in *result_in_1 whether the sorted data ended in buffer 1.
+// scratch: hist [kMaxSortPasses*256], ticket [1], look [sort_blocks(n_cap)*256*passes].
+inline cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
+                                    int64_t n_cap, const uint32_t *n_dev, int lo_bit, int bits,
+                                    uint32_t *hist, uint32_t *ticket, uint32_t *look,
+                                    uint32_t *status, int sms, cudaStream_t stream,
+                                    bool *result_in_1) {
+    SortPass ps[kMaxSortPasses];
+    int np = plan_passes(lo_bit, bits, ps);
+    *result_in_1 = (np & 1) != 0;
+    if (np == 0 || n_cap == 0) return cudaSuccess;
+    if (np > 4) return cudaErrorInvalidValue;
+    int64_t nb = sort_blocks(n_cap);
+    cudaError_t e = cudaMemsetAsync(hist, 0, np * kRadix * sizeof(uint32_t), stream);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(look, 0, (size_t)np * nb * kRadix * sizeof(uint32_t), stream);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(ticket, 0, np * sizeof(uint32_t), stream);
+    if (e != cudaSuccess) return e;
+    SortPass z{0, 1};
+    int hb = (int)std::min<int64_t>((int64_t)sms * 4, std::max<int64_t>(1, (n_cap + 4095) / 4096));
+    radix_histogram_kernel<<<hb, 256, 0, stream>>>(k0, n_cap, n_dev, np, ps[0], np > 1 ? ps[1] : z,
+                                                   np > 2 ? ps[2] : z, np > 3 ? ps[3] : z, hist);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
+    for (int p = 0; p < np; ++p) {
+        radix_onesweep_kernel<<<(unsigned)nb, kSortThreads, 0, stream>>>(
+            ki, vi, ko, vo, n_cap, n_dev, ps[p], hist + p * kRadix, ticket + p,
+            look + (size_t)p * nb * kRadix, status);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        uint32_t *tk = ki, *tv = vi;
+        ki = ko; vi = vo; ko = tk; vo = tv;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace vpgs

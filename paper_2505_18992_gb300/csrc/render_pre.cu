@@ -1,0 +1,375 @@
+// Per-Gaussian projection (EWA splatting) and its backward pass.
+//
+// Forward, one thread per (view, Gaussian):
+//   p_c = R mu + t (double-float), u = fx x/z + cx, v = fy y/z + cy (double-float)
+//   Sigma' = J R Sigma R^T J^T + dilation I = K K^T + dilation I,  K = J R R(q) S
+//   det(Sigma') via the Lagrange identity |K0 x K1|^2 + ... (no cancellation)
+//   whitening rows from the eigenvectors of Sigma'
+//   extent: half widths sqrt(2 ln(o/alpha_min) Sigma'_xx), sqrt(... Sigma'_yy),
+//           widened by 1e-5 r + 2e-3 px so the pixel set is a superset of the
+//           exact one; the alpha test at each pixel then decides membership
+// Backward, one thread per Gaussian, looping over views: chain rule from the
+// 2D gradients (u, v, conic, opacity, colour, depth) back to mean, scale,
+// quaternion, opacity and colour, plus the per-view pose terms summed in FP64.
+#include "internal.h"
+
+namespace vpgs {
+
+struct Proj {
+    df pc[3];
+    float px, py, pz;          // camera-space point (rounded)
+    float xz, yz, iz;          // x/z, y/z, 1/z
+    float j00, j02, j11, j12;  // projection Jacobian
+    float Wf[9];               // world->camera rotation (float)
+    float Rq[9];               // rotation of the quaternion
+    float WR[9];               // Wf * Rq
+    float K0[3], K1[3];        // J * WR * S rows
+    float A, B, C, det;        // Sigma' = [[A,B],[B,C]]
+    df u, v;
+};
+
+VPGS_D void project(const PoseDF &P, float mx, float my, float mz, float sx, float sy, float sz,
+                    float qw, float qx, float qy, float qz, const CamParams &cam, float dil,
+                    Proj &p) {
+    transform_df(P, mx, my, mz, p.pc);
+    p.px = p.pc[0].hi;
+    p.py = p.pc[1].hi;
+    p.pz = p.pc[2].hi;
+    df qxz = df_div(p.pc[0], p.pc[2]);
+    df qyz = df_div(p.pc[1], p.pc[2]);
+    p.u = df_add(df_mul_f(qxz, cam.fx), df{cam.cx, 0.f});
+    p.v = df_add(df_mul_f(qyz, cam.fy), df{cam.cy, 0.f});
+    p.xz = qxz.hi;
+    p.yz = qyz.hi;
+    p.iz = 1.0f / p.pz;
+    p.j00 = cam.fx * p.iz;
+    p.j02 = -cam.fx * p.xz * p.iz;
+    p.j11 = cam.fy * p.iz;
+    p.j12 = -cam.fy * p.yz * p.iz;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) p.Wf[k] = P.R[k].hi;
+    quat_to_rot(qw, qx, qy, qz, p.Rq);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            p.WR[3 * r + c] = fmaf(p.Wf[3 * r], p.Rq[c],
+                                   fmaf(p.Wf[3 * r + 1], p.Rq[3 + c], p.Wf[3 * r + 2] * p.Rq[6 + c]));
+    const float s[3] = {sx, sy, sz};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        p.K0[c] = (p.j00 * p.WR[c] + p.j02 * p.WR[6 + c]) * s[c];
+        p.K1[c] = (p.j11 * p.WR[3 + c] + p.j12 * p.WR[6 + c]) * s[c];
+    }
+    float n0 = p.K0[0] * p.K0[0] + p.K0[1] * p.K0[1] + p.K0[2] * p.K0[2];
+    float n1 = p.K1[0] * p.K1[0] + p.K1[1] * p.K1[1] + p.K1[2] * p.K1[2];
+    p.B = p.K0[0] * p.K1[0] + p.K0[1] * p.K1[1] + p.K0[2] * p.K1[2];
+    p.A = n0 + dil;
+    p.C = n1 + dil;
+    float c0 = p.K0[1] * p.K1[2] - p.K0[2] * p.K1[1];
+    float c1 = p.K0[2] * p.K1[0] - p.K0[0] * p.K1[2];
+    float c2 = p.K0[0] * p.K1[1] - p.K0[1] * p.K1[0];
+    p.det = (c0 * c0 + c1 * c1 + c2 * c2) + dil * (n0 + n1) + dil * dil;
+}
+
+__global__ void __launch_bounds__(256)
+preprocess_fwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamParams cam, OptParams o,
+                      RenderWs ws, bool zero_g2d) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t VN = (int64_t)V * g.N;
+    if (i >= VN) return;
+    const int v = (int)(i / g.N);
+    const int64_t gi = i - (int64_t)v * g.N;
+    int64_t nl = g.N;
+    if (g.n_dev) nl = min(nl, (int64_t)*g.n_dev);
+    uint32_t cnt = 0;
+    uint2 rc = make_uint2(0, 0);
+    Rec R;
+    if (gi < nl) {
+        const float mx = g.means[3 * gi], my = g.means[3 * gi + 1], mz = g.means[3 * gi + 2];
+        const float sx = g.scales[3 * gi], sy = g.scales[3 * gi + 1], sz = g.scales[3 * gi + 2];
+        const float4 q = reinterpret_cast<const float4 *>(g.quats)[gi];
+        const float op = g.opac[gi];
+        const float cr = g.colors[3 * gi], cg = g.colors[3 * gi + 1], cb = g.colors[3 * gi + 2];
+        const float chk = mx + my + mz + sx + sy + sz + q.x + q.y + q.z + q.w + op + cr + cg + cb;
+        if (!isfinite(chk)) {
+            set_status(ws.status, VPGS_ERR_NONFINITE);
+        } else if (op >= o.alpha_min) {
+            PoseDF P;
+            load_pose(T_cw + 16 * v, P);
+            Proj p;
+            // near test first (cheap): z from the double-float transform
+            project(P, mx, my, mz, sx, sy, sz, q.x, q.y, q.z, q.w, cam, o.dilation, p);
+            const bool in_front = p.pc[2].hi > o.near_z || (p.pc[2].hi == o.near_z && p.pc[2].lo > 0.f);
+            if (in_front) {
+                // eigen-decomposition of Sigma' (2x2 symmetric) for the whitening rows
+                const float h = 0.5f * (p.A - p.C);
+                const float r = hypotf(h, p.B);
+                const float lam1 = 0.5f * (p.A + p.C) + r;
+                const float lam2 = p.det / lam1;
+                float ex, ey;
+                if (r == 0.f) {
+                    ex = 1.f; ey = 0.f;
+                } else if (h >= 0.f) {
+                    ex = h + r; ey = p.B;
+                } else {
+                    ex = p.B; ey = r - h;
+                }
+                const float en = 1.0f / sqrtf(ex * ex + ey * ey);
+                ex *= en; ey *= en;
+                const float s1 = 1.0f / sqrtf(lam1), s2 = 1.0f / sqrtf(lam2);
+                // opacity-aware extent
+                const float kq = 2.0f * logf(op / o.alpha_min);
+                const float rx = sqrtf(fmaxf(kq, 0.f) * p.A), ry = sqrtf(fmaxf(kq, 0.f) * p.C);
+                const float rxe = rx * (1.0f + 1e-5f) + 2e-3f, rye = ry * (1.0f + 1e-5f) + 2e-3f;
+                const float uf = p.u.hi, vf = p.v.hi;
+                float lx = (uf - 0.5f - rxe) + p.u.lo, hx = (uf - 0.5f + rxe) + p.u.lo;
+                float ly = (vf - 0.5f - rye) + p.v.lo, hy = (vf - 0.5f + rye) + p.v.lo;
+                const bool fin = isfinite(lx + hx + ly + hy + s1 + s2 + ex + ey);
+                if (!fin) {
+                    set_status(ws.status, VPGS_ERR_NONFINITE);
+                } else {
+                    lx = fmaxf(lx, -1.f); hx = fminf(hx, (float)cam.W);
+                    ly = fmaxf(ly, -1.f); hy = fminf(hy, (float)cam.H);
+                    const int x0 = max(0, (int)ceilf(lx)), x1 = min(cam.W - 1, (int)floorf(hx));
+                    const int y0 = max(0, (int)ceilf(ly)), y1 = min(cam.H - 1, (int)floorf(hy));
+                    if (x0 <= x1 && y0 <= y1) {
+                        const int tx0 = x0 / cam.tile_w, tx1 = x1 / cam.tile_w;
+                        const int ty0 = y0 / cam.tile_h, ty1 = y1 / cam.tile_h;
+                        cnt = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+                        rc = make_uint2((uint32_t)tx0 | ((uint32_t)tx1 << 16),
+                                        (uint32_t)ty0 | ((uint32_t)ty1 << 16));
+                        R.r0 = make_float4(p.u.hi, p.v.hi, p.u.lo, p.v.lo);
+                        R.r1 = make_float4(ex * s1, ey * s1, -ey * s2, ex * s2);
+                        R.r2 = make_float4(op, p.pz, cr, cg);
+                        R.r3 = make_float4(cb, 0.f, 0.f, 0.f);
+                    }
+                }
+            }
+        }
+    }
+    ws.tcount[i] = cnt;
+    ws.rect[i] = rc;
+    if (cnt) {
+        ws.rec[i] = R;
+        if (zero_g2d) {
+            float2 *z2 = reinterpret_cast<float2 *>(ws.g2d + 10 * i);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) z2[k] = make_float2(0.f, 0.f);
+        }
+    }
+}
+
+VPGS_D float warp_sum(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__global__ void __launch_bounds__(256)
+preprocess_bwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamParams cam, OptParams o,
+                      RenderWs ws, GaussGrad gg, double *dpose) {
+    __shared__ double s_pose[8][6];
+    const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t nl = g.N;
+    if (g.n_dev) nl = min(nl, (int64_t)*g.n_dev);
+    const bool live = gi < nl;
+    float gm[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, go = 0.f, gc[3] = {0, 0, 0};
+    float mx = 0, my = 0, mz = 0, sx = 1, sy = 1, sz = 1;
+    float4 q = make_float4(1, 0, 0, 0);
+    if (live) {
+        mx = g.means[3 * gi]; my = g.means[3 * gi + 1]; mz = g.means[3 * gi + 2];
+        sx = g.scales[3 * gi]; sy = g.scales[3 * gi + 1]; sz = g.scales[3 * gi + 2];
+        q = reinterpret_cast<const float4 *>(g.quats)[gi];
+    }
+    for (int v = 0; v < V; ++v) {
+        float pv[6] = {0, 0, 0, 0, 0, 0};
+        const int64_t i = (int64_t)v * g.N + gi;
+        if (live && ws.tcount[i] > 0) {
+            const float *g2 = ws.g2d + 10 * i;
+            const float2 a01 = reinterpret_cast<const float2 *>(g2)[0];
+            const float2 a23 = reinterpret_cast<const float2 *>(g2)[1];
+            const float2 a45 = reinterpret_cast<const float2 *>(g2)[2];
+            const float2 a67 = reinterpret_cast<const float2 *>(g2)[3];
+            const float2 a89 = reinterpret_cast<const float2 *>(g2)[4];
+            const float gu = a01.x, gv = a01.y, ga = a23.x, gb = a23.y, gcn = a45.x;
+            go += a45.y;
+            gc[0] += a67.x; gc[1] += a67.y; gc[2] += a89.x;
+            const float gz = a89.y;
+            PoseDF P;
+            load_pose(T_cw + 16 * v, P);
+            Proj p;
+            project(P, mx, my, mz, sx, sy, sz, q.x, q.y, q.z, q.w, cam, o.dilation, p);
+            // conic M = Sigma'^-1 and G_Sigma' = -M G M, G = [[ga, gb/2], [gb/2, gc]]
+            const float id = 1.0f / p.det;
+            const float ma = p.C * id, mb = -p.B * id, mc = p.A * id;
+            const float hb = 0.5f * gb;
+            const float t00 = ma * ga + mb * hb, t01 = ma * hb + mb * gcn;
+            const float t10 = mb * ga + mc * hb, t11 = mb * hb + mc * gcn;
+            const float S00 = -(t00 * ma + t01 * mb);
+            const float S01 = -(t00 * mb + t01 * mc);
+            const float S11 = -(t10 * mb + t11 * mc);
+            // Sigma' = K K^T + eps I  ->  G_K = 2 G_S K
+            float GK0[3], GK1[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                GK0[c] = 2.f * (S00 * p.K0[c] + S01 * p.K1[c]);
+                GK1[c] = 2.f * (S01 * p.K0[c] + S11 * p.K1[c]);
+            }
+            // K0 = (j00 WR0 + j02 WR2) o s,  K1 = (j11 WR1 + j12 WR2) o s
+            const float sv[3] = {sx, sy, sz};
+            float Gj00 = 0, Gj02 = 0, Gj11 = 0, Gj12 = 0;
+            float GWR[9];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float a0 = GK0[c] * sv[c], a1 = GK1[c] * sv[c];
+                Gj00 += a0 * p.WR[c];
+                Gj02 += a0 * p.WR[6 + c];
+                Gj11 += a1 * p.WR[3 + c];
+                Gj12 += a1 * p.WR[6 + c];
+                GWR[c] = p.j00 * a0;
+                GWR[3 + c] = p.j11 * a1;
+                GWR[6 + c] = p.j02 * a0 + p.j12 * a1;
+                gs[c] += (GK0[c] * (p.j00 * p.WR[c] + p.j02 * p.WR[6 + c]) +
+                          GK1[c] * (p.j11 * p.WR[3 + c] + p.j12 * p.WR[6 + c]));
+            }
+            // camera-space point: projection Jacobian, image mean and depth
+            const float iz2 = p.iz * p.iz;
+            float gpx = Gj02 * (-cam.fx * iz2) + gu * cam.fx * p.iz;
+            float gpy = Gj12 * (-cam.fy * iz2) + gv * cam.fy * p.iz;
+            float gpz = Gj00 * (-cam.fx * iz2) + Gj02 * (2.f * cam.fx * p.xz * iz2) +
+                        Gj11 * (-cam.fy * iz2) + Gj12 * (2.f * cam.fy * p.yz * iz2) -
+                        gu * cam.fx * p.xz * p.iz - gv * cam.fy * p.yz * p.iz + gz;
+            // WR = Wf Rq: G_Rq = Wf^T G_WR; pose rotation term A = G_WR WR^T
+            float GRq[9];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    GRq[3 * r + c] = p.Wf[r] * GWR[c] + p.Wf[3 + r] * GWR[3 + c] + p.Wf[6 + r] * GWR[6 + c];
+            float A[9];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    A[3 * r + c] = GWR[3 * r] * p.WR[3 * c] + GWR[3 * r + 1] * p.WR[3 * c + 1] +
+                                   GWR[3 * r + 2] * p.WR[3 * c + 2];
+            // rotation matrix -> normalised quaternion -> raw quaternion
+            {
+                const float inv = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+                const float w = q.x * inv, x = q.y * inv, y = q.z * inv, z = q.w * inv;
+                const float *G = GRq;
+                float dw = 2.f * (-z * G[1] + y * G[2] + z * G[3] - x * G[5] - y * G[6] + x * G[7]);
+                float dx = 2.f * (y * G[1] + z * G[2] + y * G[3] - 2.f * x * G[4] - w * G[5] + z * G[6] +
+                                  w * G[7] - 2.f * x * G[8]);
+                float dy = 2.f * (-2.f * y * G[0] + x * G[1] + w * G[2] + x * G[3] + z * G[5] - w * G[6] +
+                                  z * G[7] - 2.f * y * G[8]);
+                float dz = 2.f * (-2.f * z * G[0] - w * G[1] + x * G[2] + w * G[3] - 2.f * z * G[4] +
+                                  y * G[5] + x * G[6] + y * G[7]);
+                const float dot = w * dw + x * dx + y * dy + z * dz;
+                gq[0] += (dw - w * dot) * inv;
+                gq[1] += (dx - x * dot) * inv;
+                gq[2] += (dy - y * dot) * inv;
+                gq[3] += (dz - z * dot) * inv;
+            }
+            // p_c = Wf mu + t
+            gm[0] += p.Wf[0] * gpx + p.Wf[3] * gpy + p.Wf[6] * gpz;
+            gm[1] += p.Wf[1] * gpx + p.Wf[4] * gpy + p.Wf[7] * gpz;
+            gm[2] += p.Wf[2] * gpx + p.Wf[5] * gpy + p.Wf[8] * gpz;
+            // left-perturbation pose terms
+            pv[0] = gpx; pv[1] = gpy; pv[2] = gpz;
+            pv[3] = p.py * gpz - p.pz * gpy + (A[7] - A[5]);
+            pv[4] = p.pz * gpx - p.px * gpz + (A[2] - A[6]);
+            pv[5] = p.px * gpy - p.py * gpx + (A[3] - A[1]);
+        }
+        if (dpose) {
+            // FP32 within a warp (32 terms), FP64 across warps and blocks
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                float s = warp_sum(pv[k]);
+                if (lane == 0) s_pose[warp][k] = (double)s;
+            }
+            __syncthreads();
+            if (threadIdx.x < 6) {
+                double t = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_pose[w][threadIdx.x];
+                if (t != 0.0) atomicAdd(dpose + 6 * v + threadIdx.x, t);
+            }
+            __syncthreads();
+        }
+    }
+    if (!live) return;
+    if (gg.means) {
+        gg.means[3 * gi] += gm[0]; gg.means[3 * gi + 1] += gm[1]; gg.means[3 * gi + 2] += gm[2];
+    }
+    if (gg.scales) {
+        gg.scales[3 * gi] += gs[0]; gg.scales[3 * gi + 1] += gs[1]; gg.scales[3 * gi + 2] += gs[2];
+    }
+    if (gg.quats) {
+        float4 *qq = reinterpret_cast<float4 *>(gg.quats) + gi;
+        float4 t = *qq;
+        t.x += gq[0]; t.y += gq[1]; t.z += gq[2]; t.w += gq[3];
+        *qq = t;
+    }
+    if (gg.opac) gg.opac[gi] += go;
+    if (gg.colors) {
+        gg.colors[3 * gi] += gc[0]; gg.colors[3 * gi + 1] += gc[1]; gg.colors[3 * gi + 2] += gc[2];
+    }
+}
+
+__global__ void export_projection_kernel(RenderWs ws, int64_t VN, int32_t *tile_count,
+                                         int32_t *tile_rect, float *mean2d, float *depth,
+                                         float *conic) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= VN) return;
+    const uint32_t cnt = ws.tcount[i];
+    if (tile_count) tile_count[i] = (int32_t)cnt;
+    if (!cnt) return;
+    const uint2 rc = ws.rect[i];
+    if (tile_rect) {
+        tile_rect[4 * i] = (int32_t)(rc.x & 0xffffu);
+        tile_rect[4 * i + 1] = (int32_t)(rc.x >> 16);
+        tile_rect[4 * i + 2] = (int32_t)(rc.y & 0xffffu);
+        tile_rect[4 * i + 3] = (int32_t)(rc.y >> 16);
+    }
+    const Rec r = ws.rec[i];
+    if (mean2d) {
+        mean2d[2 * i] = r.r0.x + r.r0.z;
+        mean2d[2 * i + 1] = r.r0.y + r.r0.w;
+    }
+    if (depth) depth[i] = r.r2.y;
+    if (conic) {  // Sigma'^-1 = w1 w1^T + w2 w2^T
+        conic[3 * i] = r.r1.x * r.r1.x + r.r1.z * r.r1.z;
+        conic[3 * i + 1] = r.r1.x * r.r1.y + r.r1.z * r.r1.w;
+        conic[3 * i + 2] = r.r1.y * r.r1.y + r.r1.w * r.r1.w;
+    }
+}
+
+cudaError_t launch_export_projection(const RenderWs &ws, int64_t VN, int32_t *tile_count,
+                                     int32_t *tile_rect, float *mean2d, float *depth, float *conic,
+                                     cudaStream_t s) {
+    if (VN == 0) return cudaSuccess;
+    export_projection_kernel<<<(unsigned)((VN + 255) / 256), 256, 0, s>>>(ws, VN, tile_count, tile_rect,
+                                                                          mean2d, depth, conic);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess_fwd(const GaussIn &g, const double *T_cw, int V, const CamParams &cam,
+                                  const OptParams &o, const RenderWs &ws, bool zero_g2d,
+                                  cudaStream_t s) {
+    const int64_t VN = (int64_t)V * g.N;
+    if (VN == 0) return cudaSuccess;
+    preprocess_fwd_kernel<<<(unsigned)((VN + 255) / 256), 256, 0, s>>>(g, T_cw, V, cam, o, ws, zero_g2d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess_bwd(const GaussIn &g, const double *T_cw, int V, const CamParams &cam,
+                                  const OptParams &o, const RenderWs &ws, const GaussGrad &gg,
+                                  double *dpose, cudaStream_t s) {
+    if (g.N == 0) return cudaSuccess;
+    preprocess_bwd_kernel<<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>(g, T_cw, V, cam, o, ws, gg, dpose);
+    return cudaGetLastError();
+}
+
+}  // namespace vpgs

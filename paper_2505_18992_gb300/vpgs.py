@@ -1,0 +1,162 @@
+"""ctypes binding of libvpgs (include/vpgs.h): struct mirrors and the C entry points.
+
+Argument marshalling only.  Every computation runs in the CUDA library; if
+the library is missing or no GPU is present, calling any entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_float, c_int32, c_int64, c_size_t, c_void_p
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libvpgs.so")
+
+VPGS_OK = 0
+STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "tile-instance capacity exceeded",
+                3: "non-finite input", 4: "bounded device wait ran out", 5: "CUDA error",
+                6: "unsupported"}
+
+
+class VpgsError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS_NAMES.get(code, code)} ({code})")
+        self.code = code
+
+
+class vpgs_camera(ctypes.Structure):
+    _fields_ = [("width", c_int32), ("height", c_int32), ("fx", c_float), ("fy", c_float),
+                ("cx", c_float), ("cy", c_float)]
+
+
+class vpgs_render_opts(ctypes.Structure):
+    _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("alpha_min", c_float),
+                ("alpha_max", c_float), ("t_min", c_float), ("dilation", c_float),
+                ("near_z", c_float), ("bg", c_float * 3), ("persistent_ctas", c_int32)]
+
+
+class vpgs_gaussians(ctypes.Structure):
+    _fields_ = [("means", c_void_p), ("scales", c_void_p), ("quats", c_void_p),
+                ("opacities", c_void_p), ("colors", c_void_p), ("n", c_int64), ("n_dev", c_void_p)]
+
+
+class vpgs_gaussian_buffers(ctypes.Structure):
+    _fields_ = [("means", c_void_p), ("scales", c_void_p), ("quats", c_void_p),
+                ("opacities", c_void_p), ("colors", c_void_p)]
+
+
+class vpgs_images(ctypes.Structure):
+    _fields_ = [("rgb", c_void_p), ("depth", c_void_p), ("alpha", c_void_p), ("t_final", c_void_p),
+                ("n_contrib", c_void_p), ("n_iter", c_void_p)]
+
+
+class vpgs_render_stats(ctypes.Structure):
+    _fields_ = [("status", c_int32), ("n_visible", c_int64), ("n_instances", c_int64)]
+
+
+class vpgs_anchors(ctypes.Structure):
+    _fields_ = [("anchors", c_void_p), ("scaling", c_void_p), ("offsets", c_void_p),
+                ("features", c_void_p), ("n", c_int64), ("k", c_int32), ("features_bf16", c_int32)]
+
+
+class vpgs_mlp(ctypes.Structure):
+    _fields_ = [("params", c_void_p), ("bf16", c_int32)]
+
+
+class vpgs_decode_opts(ctypes.Structure):
+    _fields_ = [("near_z", c_float), ("guard", c_float)]
+
+
+_SIGS = {
+    "vpgs_render_opts_default": (None, [POINTER(vpgs_render_opts)]),
+    "vpgs_render_workspace_bytes": (c_size_t, [c_int64, c_int32, POINTER(vpgs_camera),
+                                               POINTER(vpgs_render_opts), c_int64]),
+    "vpgs_render_fwd": (c_int32, [c_void_p, c_size_t, POINTER(vpgs_gaussians), POINTER(vpgs_camera),
+                                  c_void_p, c_int32, POINTER(vpgs_render_opts), POINTER(vpgs_images),
+                                  c_void_p]),
+    "vpgs_render_bwd": (c_int32, [c_void_p, c_size_t, POINTER(vpgs_gaussians), POINTER(vpgs_camera),
+                                  c_void_p, c_int32, POINTER(vpgs_render_opts), POINTER(vpgs_images),
+                                  c_void_p, c_void_p, c_void_p, POINTER(vpgs_gaussian_buffers),
+                                  c_void_p, c_void_p]),
+    "vpgs_render_project": (c_int32, [c_void_p, c_size_t, POINTER(vpgs_gaussians),
+                                      POINTER(vpgs_camera), c_void_p, c_int32,
+                                      POINTER(vpgs_render_opts), c_void_p, c_void_p, c_void_p,
+                                      c_void_p, c_void_p, c_void_p]),
+    "vpgs_workspace_status": (c_int32, [c_void_p, POINTER(vpgs_render_stats), c_void_p]),
+    "vpgs_pose_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, POINTER(c_double),
+                                 c_void_p]),
+    "vpgs_decode_workspace_bytes": (c_size_t, [c_int64, c_int32]),
+    "vpgs_decode_anchors": (c_int32, [c_void_p, c_size_t, POINTER(vpgs_anchors), POINTER(vpgs_mlp),
+                                      POINTER(vpgs_camera), c_void_p, POINTER(vpgs_decode_opts),
+                                      POINTER(vpgs_gaussian_buffers), c_void_p, c_void_p, c_void_p]),
+    "vpgs_decode_anchors_bwd": (c_int32, [c_void_p, c_size_t, POINTER(vpgs_anchors),
+                                          POINTER(vpgs_mlp), POINTER(vpgs_camera), c_void_p,
+                                          POINTER(vpgs_decode_opts), POINTER(vpgs_gaussians),
+                                          c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "vpgs_status_string": (c_char_p, [c_int32]),
+    "vpgs_version": (c_char_p, []),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libvpgs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "paper_2505_18992_gb300.build.build()")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def exported_names():
+    return list(_SIGS)
+
+
+def check(code: int, what: str):
+    if code != VPGS_OK:
+        raise VpgsError(code, what)
+
+
+def ptr(t) -> int | None:
+    """Device (or host) address of a tensor, None for None."""
+    return None if t is None else t.data_ptr()
+
+
+def _entry(name):
+    def call(*args):
+        return getattr(lib(), name)(*args)
+    call.__name__ = name
+    return call
+
+
+# same names as the C entry points
+vpgs_render_opts_default = _entry("vpgs_render_opts_default")
+vpgs_render_workspace_bytes = _entry("vpgs_render_workspace_bytes")
+vpgs_render_fwd = _entry("vpgs_render_fwd")
+vpgs_render_bwd = _entry("vpgs_render_bwd")
+vpgs_render_project = _entry("vpgs_render_project")
+vpgs_workspace_status = _entry("vpgs_workspace_status")
+vpgs_pose_step = _entry("vpgs_pose_step")
+vpgs_decode_workspace_bytes = _entry("vpgs_decode_workspace_bytes")
+vpgs_decode_anchors = _entry("vpgs_decode_anchors")
+vpgs_decode_anchors_bwd = _entry("vpgs_decode_anchors_bwd")
+vpgs_status_string = _entry("vpgs_status_string")
+vpgs_version = _entry("vpgs_version")
+
+
+def default_opts(**kw) -> vpgs_render_opts:
+    o = vpgs_render_opts()
+    vpgs_render_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "bg":
+            o.bg = (c_float * 3)(*v)
+        else:
+            setattr(o, k, v)
+    return o

@@ -1,0 +1,224 @@
+"""GPU rasterizer (through the C ABI) against the FP64 oracle."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle.raster import Options
+from paper_2505_18992_gb300 import scenes
+from paper_2505_18992_gb300 import vpgs as C
+from paper_2505_18992_gb300.render import Renderer, render
+from tests.helpers import (assert_grad_close, assert_images_close, assert_pose_close, dev,
+                           intrinsics, masked_upstream, scene_tensors, tile_count_mask)
+
+pytestmark = pytest.mark.gpu
+
+GRAD_KEYS = ("means", "scales", "quats", "opacities", "colors")
+
+
+def _np(out):
+    return {k: v.detach().cpu().numpy() for k, v in out.items()}
+
+
+def _gpu_forward(sc, **opts):
+    r = Renderer(intrinsics(sc), n_views=sc.camera.n_views, **opts)
+    g, T = scene_tensors(sc)
+    out = r.forward(*g, T)
+    torch.cuda.synchronize()
+    return r, g, T, _np(out)
+
+
+def _gpu_backward(r, g, T, out_np, grads_np):
+    fwd = {"t_final": dev(out_np["t_final"]), "n_iter": dev(out_np["n_iter"], torch.int32)}
+    gr = {k: torch.zeros_like(t) for k, t in zip(GRAD_KEYS, g)}
+    dpose = torch.zeros((r.V, 6), dtype=torch.float64, device="cuda")
+    r.backward(*g, T, fwd, dev(grads_np[0]), dev(grads_np[1]), dev(grads_np[2]), grads=gr, dpose=dpose,
+               check=True)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in gr.items()}, dpose.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def planes():
+    return scenes.tiny_planes()
+
+
+@pytest.fixture(scope="module")
+def planes_ref(planes):
+    g = scenes.upstream_grads(7, 1, planes.camera.height, planes.camera.width)
+    ref0 = oracle.render_scene(planes)
+    gm = masked_upstream(g, ref0["flags"])
+    ref = oracle.render_scene(planes, grads=gm)
+    return ref, gm
+
+
+def test_tile_counts_and_projection(planes, planes_ref):
+    ref, _ = planes_ref
+    r = Renderer(intrinsics(planes))
+    g, T = scene_tensors(planes)
+    p = {k: v.cpu().numpy() for k, v in r.project(*g, T).items()}
+    ext = ref["extent"][0]
+    mask = tile_count_mask(ext, planes.opacities)
+    cnt = p["tile_count"][0]
+    assert np.array_equal(cnt[~mask], ext["count"][~mask])
+    assert mask.mean() < 0.05
+    live = cnt > 0
+    assert np.array_equal(p["tile_rect"][0][live & ~mask], ext["tiles"][live & ~mask])
+    uv = np.stack([ref["proj"][0]["u"], ref["proj"][0]["v"]], 1)
+    assert np.abs(p["mean2d"][0][live] - uv[live]).max() < 1e-4
+    zz = ref["proj"][0]["z"]
+    assert np.abs(p["depth"][0][live] - zz[live]).max() <= 1e-6 * zz.max()
+    con = ref["proj"][0]["conic"]
+    rel = np.abs(p["conic"][0][live] - con[live]) / np.abs(con[live]).max(1, keepdims=True)
+    assert rel.max() < 1e-4
+
+
+def test_forward_parity(planes, planes_ref):
+    ref, _ = planes_ref
+    _, _, _, out = _gpu_forward(planes)
+    rep = assert_images_close(out, ref, ref["flags"], what="tiny planes")
+    assert rep["flagged_frac"] < 0.01
+    assert out["n_contrib"].max() > 10
+
+
+def test_backward_parity(planes, planes_ref):
+    ref, gm = planes_ref
+    r, g, T, out = _gpu_forward(planes)
+    grads, dpose = _gpu_backward(r, g, T, out, gm)
+    for k in GRAD_KEYS:
+        assert_grad_close(grads[k], ref["d_" + k], k)
+    assert_pose_close(dpose, ref["d_pose"])
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (32, 8), (8, 32), (16, 8)])
+def test_tile_shape_does_not_change_the_image(planes, planes_ref, tile):
+    ref, _ = planes_ref
+    _, _, _, out = _gpu_forward(planes, tile_w=tile[0], tile_h=tile[1])
+    assert_images_close(out, ref, ref["flags"], what=str(tile))
+
+
+def test_persistent_launch_is_bit_identical(planes):
+    _, _, _, a = _gpu_forward(planes)
+    _, _, _, b = _gpu_forward(planes, persistent_ctas=4)
+    for k in ("rgb", "depth", "alpha", "t_final", "n_contrib", "n_iter"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_multiview_pose_gradients_and_ragged_image():
+    sc = scenes.random_gaussians(300, 97, 61, 80.0, seed=21, scale_range=(0.02, 0.2), n_views=3)
+    g_up = scenes.upstream_grads(3, 3, 61, 97)
+    ref0 = oracle.render_scene(sc)
+    gm = masked_upstream(g_up, ref0["flags"])
+    ref = oracle.render_scene(sc, grads=gm)
+    r, g, T, out = _gpu_forward(sc)
+    assert_images_close(out, ref, ref["flags"], what="3 views")
+    grads, dpose = _gpu_backward(r, g, T, out, gm)
+    for k in GRAD_KEYS:
+        assert_grad_close(grads[k], ref["d_" + k], k)
+    assert_pose_close(dpose, ref["d_pose"])
+
+
+def test_background_and_depth_only_upstream():
+    sc = scenes.random_gaussians(200, 64, 48, 60.0, seed=5, scale_range=(0.02, 0.2))
+    bg = (0.2, 0.4, 0.6)
+    ref0 = oracle.render_scene(sc, opts=Options(bg=bg))
+    g_up = scenes.upstream_grads(8, 1, 48, 64)
+    g_up = (np.zeros_like(g_up[0]), g_up[1], np.zeros_like(g_up[2]))
+    gm = masked_upstream(g_up, ref0["flags"])
+    ref = oracle.render_scene(sc, opts=Options(bg=bg), grads=gm)
+    r, g, T, out = _gpu_forward(sc, bg=bg)
+    assert_images_close(out, ref, ref["flags"], what="bg")
+    grads, dpose = _gpu_backward(r, g, T, out, gm)
+    for k in ("means", "scales", "quats", "opacities"):
+        assert_grad_close(grads[k], ref["d_" + k], k)
+    assert np.all(grads["colors"] == 0.0)
+
+
+def test_empty_and_fully_culled_scenes():
+    sc = scenes.random_gaussians(50, 40, 30, 40.0, seed=1)
+    sc.means[:, 2] = -1.0  # behind the camera
+    _, _, _, out = _gpu_forward(sc)
+    assert out["alpha"].max() == 0.0 and out["n_contrib"].max() == 0
+    assert np.all(out["t_final"] == 1.0)
+    e = scenes.random_gaussians(1, 40, 30, 40.0, seed=1)
+    r = Renderer(intrinsics(e))
+    z = torch.zeros((0, 3), device="cuda")
+    out = r.forward(z, z.clone(), torch.zeros((0, 4), device="cuda"), torch.zeros(0, device="cuda"),
+                    z.clone(), dev(e.camera.T_cw, torch.float64))
+    assert float(out["alpha"].abs().max()) == 0.0
+
+
+def test_capacity_overflow_is_reported_then_grown(planes):
+    r = Renderer(intrinsics(planes), instances_per_gaussian=0.01)
+    g, T = scene_tensors(planes)
+    r.reserve(planes.n, max_instances=100)
+    out = r.forward(*g, T, check=False)
+    st = r.stats()
+    assert st.status == 2
+    out = r.forward(*g, T, check=True)  # grows the workspace and renders
+    assert r.stats().status == 0
+    assert r.cap_m >= r.last_stats.n_instances
+    del out
+
+
+def test_nonfinite_input_sets_status():
+    sc = scenes.random_gaussians(20, 32, 24, 30.0, seed=2)
+    sc.means[3, 0] = np.nan
+    r = Renderer(intrinsics(sc))
+    g, T = scene_tensors(sc)
+    r.forward(*g, T, check=False)
+    assert r.stats().status == 3
+
+
+def test_invalid_arguments_are_rejected_on_the_host(planes):
+    r = Renderer(intrinsics(planes))
+    g, T = scene_tensors(planes)
+    r.reserve(planes.n)
+    gs = r._gauss(*g)
+    bad = C.default_opts(tile_w=3)
+    out = r.alloc_images()
+    code = C.vpgs_render_fwd(r.ws.data_ptr(), r.ws_bytes, ctypes.byref(gs), ctypes.byref(r.cam),
+                             T.data_ptr(), 1, ctypes.byref(bad), ctypes.byref(r._images(out)), None)
+    assert code == 1
+    code = C.vpgs_render_fwd(r.ws.data_ptr(), 1024, ctypes.byref(gs), ctypes.byref(r.cam),
+                             T.data_ptr(), 1, ctypes.byref(r.opts), ctypes.byref(r._images(out)), None)
+    assert code == 1
+
+
+def test_autograd_function_matches_direct_calls(planes, planes_ref):
+    ref, gm = planes_ref
+    r = Renderer(intrinsics(planes))
+    g, T = scene_tensors(planes)
+    leaves = [t.clone().requires_grad_(True) for t in g]
+    xi = torch.zeros((1, 6), dtype=torch.float64, device="cuda", requires_grad=True)
+    rgb, depth, alpha = render(*leaves, T, r, xi=xi)
+    L = (rgb * dev(gm[0])).sum() + (depth * dev(gm[1])).sum() + (alpha * dev(gm[2])).sum()
+    L.backward()
+    for k, leaf in zip(GRAD_KEYS, leaves):
+        assert_grad_close(leaf.grad.cpu().numpy(), ref["d_" + k], k)
+    assert_pose_close(xi.grad.cpu().numpy(), ref["d_pose"])
+
+
+def test_full_size_room_sampled_rows():
+    # the 1M-Gaussian 1200x680 room in the benchmark's launch configuration,
+    # compared on sampled rows the oracle evaluates one by one
+    sc = scenes.indoor_room()
+    rows = [0, 171, 340, 521, 679]
+    g_up = scenes.upstream_grads(11, 1, 680, 1200)
+    ref0 = oracle.render_scene(sc, rows=rows)
+    sel = np.zeros_like(ref0["flags"])
+    sel[:, rows] = True
+    ignore = ref0["flags"] | ~sel
+    r, g, T, out = _gpu_forward(sc)
+    shown = {k: (np.where(sel[:, None], v, 0) if k == "rgb" else np.where(sel, v, 0))
+             for k, v in out.items()}
+    assert_images_close(shown, ref0, ignore, what="room rows")
+    # gradients from the sampled rows only
+    gm = masked_upstream(g_up, ignore)
+    ref = oracle.render_scene(sc, rows=rows, grads=gm)
+    grads, dpose = _gpu_backward(r, g, T, out, gm)
+    for k in GRAD_KEYS:
+        assert_grad_close(grads[k], ref["d_" + k], k)
+    assert_pose_close(dpose, ref["d_pose"])
