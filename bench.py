@@ -1,0 +1,438 @@
+#!/usr/bin/env python3
+"""Forward+backward RGB-D throughput of the Gaussian rasterizer on one GB300.
+
+Workload: the 1M-Gaussian room (6 walls of a 6x5x3 m room plus 20 boxes) seen
+by a 1200x680 camera (fx = fy = 600).  The room stands in for the paper's
+Replica/ScanNet rooms, whose data is not available.  One step is
+vpgs_render_fwd followed by vpgs_render_bwd: gradients to every Gaussian
+parameter and to the 6-DoF pose, with the tile lists recomputed in the
+backward.  The upstream gradient is a fixed seeded L1-type pattern
+(+-1/(3P) colour, +-1/P depth).  Inputs (56 MB) are smaller than L2, so a
+256 MiB buffer is written between timed steps to flush L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun, each rank renders its own copy of the workload (independent
+replicas, weak scaling).  There is no data-path collective; a barrier and a
+max-reduction of the timings are the only cross-rank steps.
+"""
+from __future__ import annotations
+
+import argparse
+import datetime as _dt
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd RGB-D Mpix/s at 1M Gaussians 1200×680; % HBM roofline; vs plain form"
+UNIT = "Mpix/s"
+WORKLOAD = "indoor room: 1,000,000 Gaussians, 1200x680 RGB-D-alpha, fwd+bwd (all Gaussian params + 6-DoF pose)"
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--cpu-rows", type=int, default=8, help="image rows in the CPU oracle sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true", help="skip tracking/e2e/profile passes")
+    p.add_argument("--persistent", type=int, default=0, help="persistent CTAs per SM (0 = per tile)")
+    return p.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline key)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(scene, n_rows: int):
+    """Times the FP64 oracle fwd+bwd on n_rows evenly spaced rows of the frame."""
+    import torch
+
+    import oracle
+    from paper_2505_18992_gb300 import scenes
+    H, W = scene.camera.height, scene.camera.width
+    rows = [int(r) for r in np.linspace(0, H - 1, n_rows)]
+    g = scenes.upstream_grads(11, 1, H, W)
+    t0 = time.perf_counter()
+    oracle.render_scene(scene, rows=rows, grads=g)
+    dt = time.perf_counter() - t0
+    px = n_rows * W
+    return {"value": px / dt / 1e6, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{n_rows} image rows x {W} px of the same 1M-Gaussian frame (projection of all "
+                      f"1M Gaussians + per-pixel compositing and backward), {dt:.2f} s"}
+
+
+def run_reference(a):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from paper_2505_18992_gb300 import scenes
+    scene = scenes.indoor_room()
+    vals = []
+    for _ in range(a.warmup):
+        oracle_sample(scene, 1)
+    last = None
+    for _ in range(a.steps):
+        last = oracle_sample(scene, max(1, a.cpu_rows // 4))
+        vals.append(last["value"])
+    v = statistics.median(vals)
+    px_step = max(1, a.cpu_rows // 4) * scene.camera.width
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": px_step / (v * 1e6) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_rows": max(1, a.cpu_rows // 4)},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50", "-i", gpu_id,
+                                          "-f", self.path], stdout=subprocess.DEVNULL,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                ts = _dt.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, f))
+        except Exception:
+            pass
+        inside = [f for ts, f in rows if t0 - 0.05 <= ts <= t1 + 0.05]
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(f[1]) for f in inside if f[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for f in inside:
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(inside[0][2]) if inside[0][2].replace(".", "").isdigit() else None,
+                "reasons": sorted(reasons), "samples": len(inside),
+                "power_w_max": max(float(f[3]) for f in inside if f[3].replace(".", "").isdigit())}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes of the hot kernels (per launch)
+# ---------------------------------------------------------------------------
+
+def algorithmic_bytes(kernel: str, N: int, Nv: int, M: int, P: int):
+    """Minimum DRAM bytes a launch must move, from the unit counts of the frame.
+
+    N Gaussians, Nv visible ones, M tile instances, P pixels."""
+    table = {
+        # read 56 B of parameters per Gaussian; write the 52 B screen record per visible one
+        "preprocess_fwd": 56 * N + 52 * Nv,
+        # gather id + 48 B record per instance; write RGB, depth, alpha, T, count (28 B/px)
+        "composite_fwd": 52 * M + 28 * P,
+        # same gather, read T, list length and 20 B of upstream gradient per pixel, write 40 B/visible
+        "composite_bwd": 52 * M + 28 * P + 40 * Nv,
+        # read 2D grads + 56 B parameters per visible, read-modify-write 56 B of gradients per Gaussian
+        "preprocess_bwd": 96 * Nv + 112 * N,
+        # per pass: read and write one 8-byte (key, value) pair per item
+        "radix_onesweep": None,
+    }
+    return table.get(kernel)
+
+
+def _sha(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+KERNEL_SOURCES = {
+    "composite_fwd": ["paper_2505_18992_gb300/csrc/render_comp.cu", "paper_2505_18992_gb300/csrc/common.cuh"],
+    "composite_bwd": ["paper_2505_18992_gb300/csrc/render_comp.cu", "paper_2505_18992_gb300/csrc/common.cuh"],
+    "preprocess_fwd": ["paper_2505_18992_gb300/csrc/render_pre.cu", "paper_2505_18992_gb300/csrc/common.cuh"],
+    "preprocess_bwd": ["paper_2505_18992_gb300/csrc/render_pre.cu", "paper_2505_18992_gb300/csrc/common.cuh"],
+    "radix_onesweep": ["paper_2505_18992_gb300/csrc/prims.cuh"],
+    "scan_lookback": ["paper_2505_18992_gb300/csrc/prims.cuh", "paper_2505_18992_gb300/csrc/render_bin.cu"],
+}
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as fh:
+            d = json.load(fh)
+        e = d[kernel]
+        if e.get("source_sha") != _sha(KERNEL_SOURCES[kernel]):
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2505_18992_gb300 import scenes
+    from paper_2505_18992_gb300 import vpgs as C
+    from paper_2505_18992_gb300.build import build
+    from paper_2505_18992_gb300.render import Intrinsics, Renderer
+
+    world, rank, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build()
+    if world > 1:
+        dist.barrier()
+    C.lib()
+    dev = torch.device("cuda", local)
+    sc = scenes.indoor_room()
+    cam = sc.camera
+    H, W, V = cam.height, cam.width, 1
+    P = V * H * W
+    g = [torch.tensor(x, device=dev).contiguous() for x in sc.arrays()]
+    T = torch.tensor(cam.T_cw, dtype=torch.float64, device=dev).contiguous()
+    r = Renderer(Intrinsics(W, H, cam.fx, cam.fy, cam.cx, cam.cy), device=dev,
+                 persistent_ctas=a.persistent)
+    rng = np.random.default_rng(5)
+    g_rgb = torch.tensor(np.sign(rng.normal(size=(1, 3, H, W))) / (3 * P), dtype=torch.float32, device=dev)
+    g_d = torch.tensor(np.sign(rng.normal(size=(1, H, W))) / P, dtype=torch.float32, device=dev)
+    names = ("means", "scales", "quats", "opacities", "colors")
+    grads = {k: torch.zeros_like(t) for k, t in zip(names, g)}
+    dpose = torch.zeros((1, 6), dtype=torch.float64, device=dev)
+    out = r.forward(*g, T, check=True)  # sizes the instance capacity (host sync, untimed)
+    st = r.stats()
+    Nv, M = int(st.n_visible), int(st.n_instances)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+
+    def step():
+        for t in grads.values():
+            t.zero_()
+        dpose.zero_()
+        r.forward(*g, T, out=out, check=False)
+        r.backward(*g, T, out, g_rgb, g_d, None, grads=grads, dpose=dpose)
+
+    for _ in range(max(3, a.warmup)):
+        step()
+    torch.cuda.synchronize()
+    C.check(r.stats().status, "warm-up render")
+
+    def timed(fn, k, flush_l2=True):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for e0, e1 in evs:
+            if flush_l2:
+                flush.fill_(1.0)
+            e0.record()
+            fn()
+            e1.record()
+        torch.cuda.synchronize()
+        return [e0.elapsed_time(e1) for e0, e1 in evs]
+
+    uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    sampler = ClockSampler(uuid) if rank == 0 else None
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = C.vpgs_launch_count()
+    t_wall0 = time.time()
+    ms = timed(step, a.steps)
+    t_wall1 = time.time()
+    launches = C.vpgs_launch_count() - l0
+    ms_step = sum(ms) / len(ms)
+    if world > 1:
+        tt = torch.tensor([ms_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_step = float(tt.item())
+        dist.barrier()
+    if sampler:
+        time.sleep(0.2)
+        sampler.stop()
+    C.check(r.stats().status, "timed renders")
+    value = P * world / (ms_step * 1e-3) / 1e6
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_gaussians": sc.n, "width": W, "height": H,
+                       "visible": Nv, "instances": M, "tile": "16x16",
+                       "l2": "256 MiB buffer written between timed steps (inputs 56 MB < L2)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "ms_p50": statistics.median(ms), "ms_min": min(ms)},
+            "gpu_launches": int(launches)}
+    if sampler:
+        line["clocks"] = sampler.summary(t_wall0, t_wall1)
+
+    if not a.no_extras:
+        # per-kernel live timing (CUDA events on the launching stream), same steps again
+        C.vpgs_profile_enable(1)
+        timed(step, min(a.steps, 50))
+        C.vpgs_profile_enable(0)
+        prof = C.profile_collect()
+        kern = {k: {"launches": n, "ms_total": t, "ms_avg": t / n} for k, (n, t) in prof.items()}
+        tot = sum(v["ms_total"] for v in kern.values())
+        for v in kern.values():
+            v["share"] = v["ms_total"] / tot if tot else 0.0
+        top = max(kern, key=lambda k: kern[k]["ms_total"])
+        peak, peak_src = _peaks()
+        ab = algorithmic_bytes(top, sc.n, Nv, M, P)
+        if ab is not None:
+            achieved = ab / (kern[top]["ms_avg"] * 1e-3) / 1e9
+            line["roofline"] = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peak,
+                                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
+                                "algorithmic_bytes": ab, "traffic": ncu_traffic(top)}
+        else:
+            line["roofline"] = {"kernel": top, "bound": "hbm", "achieved": None, "peak": peak,
+                                "unit": "GB/s", "frac": None, "traffic": None}
+        line["kernels"] = {k: {"launches": v["launches"] // min(a.steps, 50), "ms_avg": round(v["ms_avg"], 5),
+                               "share": round(v["share"], 4)} for k, v in sorted(kern.items(),
+                                                                                  key=lambda kv: -kv[1]["ms_total"])}
+        # end to end through the public API with host buffers
+        pin = lambda t: t.detach().cpu().pin_memory()  # noqa: E731
+        h_in = [pin(t) for t in g] + [pin(T), pin(g_rgb), pin(g_d)]
+        h_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items()
+                 if k in ("rgb", "depth", "alpha")}
+        h_gr = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in grads.items()}
+        h_pose = torch.empty((1, 6), dtype=torch.float64).pin_memory()
+        d_in = g + [T, g_rgb, g_d]
+
+        def e2e_step():
+            for d_t, h_t in zip(d_in, h_in):
+                d_t.copy_(h_t, non_blocking=True)
+            step()
+            for k in h_out:
+                h_out[k].copy_(out[k], non_blocking=True)
+            for k in h_gr:
+                h_gr[k].copy_(grads[k], non_blocking=True)
+            h_pose.copy_(dpose, non_blocking=True)
+
+        ms_e = timed(e2e_step, min(a.steps, 50))
+        e_ms = sum(ms_e) / len(ms_e)
+        h2d = sum(t.numel() * t.element_size() for t in h_in)
+        d2h = sum(t.numel() * t.element_size() for t in list(h_out.values()) + list(h_gr.values())) + 48
+        line["e2e"] = {"value": P * world / (e_ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": e_ms,
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        # coarse tracking: 50 pose-only iterations, eager vs one captured CUDA graph
+        try:
+            line["tracking"] = tracking_rows(sc, g, dev)
+        except Exception as exc:  # reported, not fatal
+            line["tracking"] = {"error": repr(exc)[:200]}
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(sc, a.cpu_rows)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def tracking_rows(sc, g, dev):
+    import torch
+
+    from paper_2505_18992_gb300.render import Intrinsics, Renderer
+    from paper_2505_18992_gb300.tracking import Tracker
+    cam = sc.camera
+    r = Renderer(Intrinsics(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy), device=dev)
+    T_true = torch.tensor(cam.T_cw, dtype=torch.float64, device=dev).contiguous()
+    ref = r.forward(*g, T_true, check=True)
+    tgt_rgb, tgt_d = ref["rgb"].clone(), ref["depth"].clone()
+    T0 = torch.tensor(sc.extra["T_track0"], dtype=torch.float64, device=dev).contiguous()
+    T = T0.clone()
+    tr = Tracker(r, g, T, tgt_rgb, tgt_d, lr=(2e-3, 2e-3))
+    tr.prepare()
+    iters = 50
+    tr.reset(T0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    tr.run_eager(iters)
+    e1.record()
+    torch.cuda.synchronize()
+    eager_ms = e0.elapsed_time(e1)
+    err0 = float(torch.linalg.norm(T0[0, :3, 3] - T_true[0, :3, 3]))
+    err_eager = float(torch.linalg.norm(T[0, :3, 3] - T_true[0, :3, 3]))
+    tr.reset(T0)
+    tr.capture(iters)
+    tr.reset(T0)
+    torch.cuda.synchronize()
+    e0.record()
+    tr.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    graph_ms = e0.elapsed_time(e1)
+    err_graph = float(torch.linalg.norm(T[0, :3, 3] - T_true[0, :3, 3]))
+    return {"iters": iters, "eager_ms": eager_ms, "graph_ms": graph_ms,
+            "ms_per_iter_graph": graph_ms / iters, "trans_err_m_start": err0,
+            "trans_err_m_eager": err_eager, "trans_err_m_graph": err_graph}
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

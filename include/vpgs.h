@@ -254,6 +254,25 @@ vpgs_status vpgs_decode_anchors_bwd(void *ws, size_t ws_bytes, const vpgs_anchor
                                     float *dL_dfeatures, float *dL_doffsets, float *dL_dscaling,
                                     float *dL_dparams, vpgs_stream stream);
 
+/* ---------------------------------------------------------------------- */
+/* Diagnostics (host)                                                      */
+/* ---------------------------------------------------------------------- */
+
+/* Number of CUDA kernels this process has launched through the library. */
+int64_t vpgs_launch_count(void);
+
+/* Per-kernel timing.  While enabled, every library kernel launch is bracketed
+ * by a CUDA event pair recorded on its own stream.  Off by default, because
+ * each event costs a few microseconds of host time. */
+void vpgs_profile_enable(int32_t on);
+
+/* Synchronises the recorded events, aggregates them per kernel name and clears
+ * them.  It writes up to max_entries entries: names as consecutive
+ * NUL-terminated strings in the host buffer names[name_bytes], launches[i],
+ * and total_ms[i].  Returns the number of entries written. */
+int32_t vpgs_profile_collect(char *names, size_t name_bytes, int64_t *launches, double *total_ms,
+                             int32_t max_entries);
+
 const char *vpgs_status_string(vpgs_status s);
 /* Library version, "major.minor.patch" (host string). */
 const char *vpgs_version(void);

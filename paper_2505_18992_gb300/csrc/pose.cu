@@ -4,6 +4,7 @@
 // The gradient is zeroed after use so a captured graph can replay
 // render -> backward -> step without host work.
 #include "internal.h"
+#include "profiler.h"
 
 namespace vpgs {
 
@@ -73,7 +74,8 @@ __global__ void pose_step_kernel(double *T_cw, double *dpose, double *adam, int 
 
 cudaError_t launch_pose_step(double *T_cw, double *dpose, double *adam, int V, double lr_rho,
                              double lr_phi, cudaStream_t s) {
-    pose_step_kernel<<<(V + 63) / 64, 64, 0, s>>>(T_cw, dpose, adam, V, lr_rho, lr_phi);
+    VPGS_LAUNCH("pose_step", s, pose_step_kernel<<<(V + 63) / 64, 64, 0, s>>>(T_cw, dpose, adam, V,
+                                                                              lr_rho, lr_phi));
     return cudaGetLastError();
 }
 

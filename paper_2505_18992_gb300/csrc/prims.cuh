@@ -7,6 +7,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "profiler.h"
 
 namespace vpgs {
 
@@ -150,8 +151,9 @@ cudaError_t launch_scan(Load load, Store store, int64_t n_cap, const uint32_t *n
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(look, 0, nb * sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return e;
-    scan_kernel<<<(unsigned)nb, kScanThreads, 0, stream>>>(load, store, n_cap, n_dev, ticket, look,
-                                                           total, status);
+    VPGS_LAUNCH("scan_lookback", stream,
+                scan_kernel<<<(unsigned)nb, kScanThreads, 0, stream>>>(load, store, n_cap, n_dev,
+                                                                       ticket, look, total, status));
     return cudaGetLastError();
 }
 
@@ -350,15 +352,18 @@ inline cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, ui
     if (e != cudaSuccess) return e;
     SortPass z{0, 1};
     int hb = (int)std::min<int64_t>((int64_t)sms * 4, std::max<int64_t>(1, (n_cap + 4095) / 4096));
-    radix_histogram_kernel<<<hb, 256, 0, stream>>>(k0, n_cap, n_dev, np, ps[0], np > 1 ? ps[1] : z,
-                                                   np > 2 ? ps[2] : z, np > 3 ? ps[3] : z, hist);
+    VPGS_LAUNCH("radix_histogram", stream,
+                radix_histogram_kernel<<<hb, 256, 0, stream>>>(k0, n_cap, n_dev, np, ps[0],
+                                                               np > 1 ? ps[1] : z, np > 2 ? ps[2] : z,
+                                                               np > 3 ? ps[3] : z, hist));
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
     for (int p = 0; p < np; ++p) {
-        radix_onesweep_kernel<<<(unsigned)nb, kSortThreads, 0, stream>>>(
-            ki, vi, ko, vo, n_cap, n_dev, ps[p], hist + p * kRadix, ticket + p,
-            look + (size_t)p * nb * kRadix, status);
+        VPGS_LAUNCH("radix_onesweep", stream,
+                    radix_onesweep_kernel<<<(unsigned)nb, kSortThreads, 0, stream>>>(
+                        ki, vi, ko, vo, n_cap, n_dev, ps[p], hist + p * kRadix, ticket + p,
+                        look + (size_t)p * nb * kRadix, status));
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         uint32_t *tk = ki, *tv = vi;

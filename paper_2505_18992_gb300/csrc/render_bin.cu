@@ -125,8 +125,9 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
     e = cudaMemsetAsync(ws.ranges, 0, sizeof(uint2) * (size_t)V * cam.T, s);
     if (e != cudaSuccess) return e;
     const int64_t rb = std::min<int64_t>((L.M_cap + 255) / 256, (int64_t)sms * 16);
-    tile_ranges_kernel<<<(unsigned)std::max<int64_t>(rb, 1), 256, 0, s>>>(
-        in1 ? ws.ikey[1] : ws.ikey[0], L.M_cap, n_inst, (uint32_t)(V * cam.T), ws.ranges);
+    VPGS_LAUNCH("tile_ranges", s,
+                tile_ranges_kernel<<<(unsigned)std::max<int64_t>(rb, 1), 256, 0, s>>>(
+                    in1 ? ws.ikey[1] : ws.ikey[0], L.M_cap, n_inst, (uint32_t)(V * cam.T), ws.ranges));
     return cudaGetLastError();
 }
 

@@ -18,6 +18,7 @@
 // summed by a transpose reduction (16 shuffles for 10 values) and added with
 // one atomic per value per warp.
 #include "internal.h"
+#include "profiler.h"
 
 namespace vpgs {
 
@@ -282,7 +283,9 @@ cudaError_t launch_composite_fwd(const RenderWs &ws, const uint32_t *ival, int V
     if (sm > 48 * 1024)
         cudaFuncSetAttribute((const void *)composite_fwd_kernel,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    composite_fwd_kernel<<<grid, B, sm, s>>>(ws.rec, ival, ws.ranges, n_tiles, cam, o, out, ws.status, work);
+    VPGS_LAUNCH("composite_fwd", s,
+                composite_fwd_kernel<<<grid, B, sm, s>>>(ws.rec, ival, ws.ranges, n_tiles, cam, o, out,
+                                                         ws.status, work));
     return cudaGetLastError();
 }
 
@@ -305,9 +308,10 @@ cudaError_t launch_composite_bwd(const RenderWs &ws, const uint32_t *ival, int V
     if (sm > 48 * 1024)
         cudaFuncSetAttribute((const void *)composite_bwd_kernel,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    composite_bwd_kernel<<<grid, B, sm, s>>>(ws.rec, ival, ws.ranges, n_tiles, cam, o, fwd.t_final,
-                                             fwd.n_iter, dL_drgb, dL_ddepth, dL_dalpha, ws.g2d,
-                                             ws.status, work);
+    VPGS_LAUNCH("composite_bwd", s,
+                composite_bwd_kernel<<<grid, B, sm, s>>>(ws.rec, ival, ws.ranges, n_tiles, cam, o,
+                                                         fwd.t_final, fwd.n_iter, dL_drgb, dL_ddepth,
+                                                         dL_dalpha, ws.g2d, ws.status, work));
     return cudaGetLastError();
 }
 

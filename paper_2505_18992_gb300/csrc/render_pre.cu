@@ -12,6 +12,7 @@
 // 2D gradients (u, v, conic, opacity, colour, depth) back to mean, scale,
 // quaternion, opacity and colour, plus the per-view pose terms summed in FP64.
 #include "internal.h"
+#include "profiler.h"
 
 namespace vpgs {
 
@@ -350,8 +351,9 @@ cudaError_t launch_export_projection(const RenderWs &ws, int64_t VN, int32_t *ti
                                      int32_t *tile_rect, float *mean2d, float *depth, float *conic,
                                      cudaStream_t s) {
     if (VN == 0) return cudaSuccess;
-    export_projection_kernel<<<(unsigned)((VN + 255) / 256), 256, 0, s>>>(ws, VN, tile_count, tile_rect,
-                                                                          mean2d, depth, conic);
+    VPGS_LAUNCH("export_projection", s,
+                export_projection_kernel<<<(unsigned)((VN + 255) / 256), 256, 0, s>>>(
+                    ws, VN, tile_count, tile_rect, mean2d, depth, conic));
     return cudaGetLastError();
 }
 
@@ -360,7 +362,9 @@ cudaError_t launch_preprocess_fwd(const GaussIn &g, const double *T_cw, int V, c
                                   cudaStream_t s) {
     const int64_t VN = (int64_t)V * g.N;
     if (VN == 0) return cudaSuccess;
-    preprocess_fwd_kernel<<<(unsigned)((VN + 255) / 256), 256, 0, s>>>(g, T_cw, V, cam, o, ws, zero_g2d);
+    VPGS_LAUNCH("preprocess_fwd", s,
+                preprocess_fwd_kernel<<<(unsigned)((VN + 255) / 256), 256, 0, s>>>(g, T_cw, V, cam, o,
+                                                                                    ws, zero_g2d));
     return cudaGetLastError();
 }
 
@@ -368,7 +372,9 @@ cudaError_t launch_preprocess_bwd(const GaussIn &g, const double *T_cw, int V, c
                                   const OptParams &o, const RenderWs &ws, const GaussGrad &gg,
                                   double *dpose, cudaStream_t s) {
     if (g.N == 0) return cudaSuccess;
-    preprocess_bwd_kernel<<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>(g, T_cw, V, cam, o, ws, gg, dpose);
+    VPGS_LAUNCH("preprocess_bwd", s,
+                preprocess_bwd_kernel<<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>(g, T_cw, V, cam, o,
+                                                                                    ws, gg, dpose));
     return cudaGetLastError();
 }
 

@@ -92,6 +92,10 @@ _SIGS = {
                                           POINTER(vpgs_mlp), POINTER(vpgs_camera), c_void_p,
                                           POINTER(vpgs_decode_opts), POINTER(vpgs_gaussians),
                                           c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "vpgs_launch_count": (c_int64, []),
+    "vpgs_profile_enable": (None, [c_int32]),
+    "vpgs_profile_collect": (c_int32, [c_char_p, c_size_t, POINTER(c_int64), POINTER(c_double),
+                                       c_int32]),
     "vpgs_status_string": (c_char_p, [c_int32]),
     "vpgs_version": (c_char_p, []),
 }
@@ -147,6 +151,9 @@ vpgs_pose_step = _entry("vpgs_pose_step")
 vpgs_decode_workspace_bytes = _entry("vpgs_decode_workspace_bytes")
 vpgs_decode_anchors = _entry("vpgs_decode_anchors")
 vpgs_decode_anchors_bwd = _entry("vpgs_decode_anchors_bwd")
+vpgs_launch_count = _entry("vpgs_launch_count")
+vpgs_profile_enable = _entry("vpgs_profile_enable")
+vpgs_profile_collect = _entry("vpgs_profile_collect")
 vpgs_status_string = _entry("vpgs_status_string")
 vpgs_version = _entry("vpgs_version")
 
@@ -160,3 +167,13 @@ def default_opts(**kw) -> vpgs_render_opts:
         else:
             setattr(o, k, v)
     return o
+
+
+def profile_collect(max_entries: int = 64):
+    """{kernel name: (launches, total ms)} of the events recorded while profiling was on."""
+    names = ctypes.create_string_buffer(64 * max_entries)
+    launches = (c_int64 * max_entries)()
+    total = (c_double * max_entries)()
+    n = vpgs_profile_collect(names, len(names), launches, total, max_entries)
+    raw = names.raw.split(b"\0")
+    return {raw[i].decode(): (int(launches[i]), float(total[i])) for i in range(n)}
