@@ -1,24 +1,682 @@
-// Anchor decoder entry points (filled in below the render path).
+// Anchor -> neural Gaussian decoder (Sec. III-A, Eq. 1-5) and its backward.
+//
+// Forward, one block per 128 anchors (block order from an atomic ticket):
+//   1. cull the anchor (camera depth, projected centre inside the widened image)
+//   2. Eq. 3: delta = |x^a - x^c|, d = (x^a - x^c) / delta
+//   3. Eq. 2: [f, d, delta] through three LINEAR-ReLU-LINEAR MLPs, either
+//      FP32 FMA (one thread per anchor, weights in shared memory) or BF16
+//      tensor cores (mma.sync m16n8k16, FP32 accumulation; each warp runs two
+//      16-anchor tiles: 36->96 hidden, then 32->{10,30,70} per MLP)
+//   4. heads: tanh opacity (valid iff > 0), sigmoid colour (Eq. 4), sigmoid
+//      scale times the anchor scaling (Eq. 5), normalised quaternion
+//   5. Eq. 1 positions, and compaction in (anchor, m) order: per-anchor valid
+//      counts are scanned inside the block and offset by a decoupled look-back
+//      over earlier blocks, so the decode writes compacted output directly.
+// Backward, one block per 128 anchors: recompute the activations, back-propagate
+// through heads and MLPs per anchor, then reduce the weight gradients over the
+// block's anchors in shared memory (one atomic per parameter per block).
+#include <cuda_bf16.h>
+
 #include "internal.h"
+#include "prims.cuh"
+#include "profiler.h"
+
+namespace vpgs {
+
+constexpr int kDecAnchors = 128;   // anchors (and threads) per block
+constexpr int kFeat = 32, kIn = 36, kHid = 32, kMaxK = 10;
+constexpr int kOutStride = 121;    // per-anchor row of layer-2 outputs in shared memory
+constexpr int kColOpa = 0, kColCol = 16, kColCov = 48;  // column bases (padded to n8 tiles)
+constexpr int kInPad = 56;         // bf16 row stride of the staged inputs / W1 rows
+constexpr int kW2Pad = 40;         // bf16 row stride of W2 rows
+
+struct DecParams {
+    const float *anchors, *scaling, *offsets;
+    const void *features;
+    int64_t A;
+    int K;
+    int feat_bf16;
+    const float *params;
+    int bf16;
+    float fx, fy, cx, cy;
+    int W, H;
+    float near_z, guard;
+};
+
+// flat parameter offsets of MLP j (opacity, colour, covariance)
+struct MlpOff {
+    int w1, b1, w2, b2, out;
+};
+
+VPGS_HD MlpOff mlp_off(int K, int j) {
+    const int outs[3] = {K, 3 * K, 7 * K};
+    int o = 0;
+    for (int q = 0; q < j; ++q) o += kIn * kHid + kHid + outs[q] * kHid + outs[q];
+    MlpOff m;
+    m.w1 = o;
+    m.b1 = o + kIn * kHid;
+    m.w2 = m.b1 + kHid;
+    m.b2 = m.w2 + outs[j] * kHid;
+    m.out = outs[j];
+    return m;
+}
+
+VPGS_HD int n_params(int K) {
+    MlpOff m = mlp_off(K, 2);
+    return m.b2 + m.out;
+}
+
+VPGS_D float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+VPGS_D float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+// camera data shared by the block
+struct DecCam {
+    float R[9], t[3], xc[3];
+};
+
+VPGS_D void load_dec_cam(const double *T, DecCam &c) {
+    double Rd[9], td[3];
+    for (int k = 0; k < 9; ++k) Rd[k] = T[4 * (k / 3) + (k % 3)];
+    for (int r = 0; r < 3; ++r) td[r] = T[4 * r + 3];
+    for (int k = 0; k < 9; ++k) c.R[k] = (float)Rd[k];
+    for (int r = 0; r < 3; ++r) {
+        c.t[r] = (float)td[r];
+        c.xc[r] = (float)(-(Rd[r] * td[0] + Rd[3 + r] * td[1] + Rd[6 + r] * td[2]));
+    }
+}
+
+// per-anchor inputs: cull decision and the 36 network inputs (f, d, delta)
+VPGS_D bool anchor_inputs(const DecParams &p, const DecCam &c, int64_t a, float in[kIn]) {
+    const float x = p.anchors[3 * a], y = p.anchors[3 * a + 1], z = p.anchors[3 * a + 2];
+    const float pz = c.R[6] * x + c.R[7] * y + c.R[8] * z + c.t[2];
+    const float px = c.R[0] * x + c.R[1] * y + c.R[2] * z + c.t[0];
+    const float py = c.R[3] * x + c.R[4] * y + c.R[5] * z + c.t[1];
+    bool keep = pz > p.near_z;
+    if (keep) {
+        const float u = p.fx * px / pz + p.cx, v = p.fy * py / pz + p.cy;
+        keep = u >= -p.guard * p.W && u <= (1.f + p.guard) * p.W && v >= -p.guard * p.H &&
+               v <= (1.f + p.guard) * p.H;
+    }
+    if (p.feat_bf16) {
+        const __nv_bfloat16 *f = reinterpret_cast<const __nv_bfloat16 *>(p.features) + kFeat * a;
+        for (int k = 0; k < kFeat; ++k) in[k] = __bfloat162float(f[k]);
+    } else {
+        const float4 *f = reinterpret_cast<const float4 *>(static_cast<const float *>(p.features) + kFeat * a);
+        for (int k = 0; k < kFeat / 4; ++k) {
+            const float4 q = f[k];
+            in[4 * k] = q.x; in[4 * k + 1] = q.y; in[4 * k + 2] = q.z; in[4 * k + 3] = q.w;
+        }
+    }
+    const float dx = x - c.xc[0], dy = y - c.xc[1], dz = z - c.xc[2];
+    const float dl = sqrtf(dx * dx + dy * dy + dz * dz);
+    in[32] = dx / dl;
+    in[33] = dy / dl;
+    in[34] = dz / dl;
+    in[35] = dl;
+    if (p.bf16)
+        for (int k = 0; k < kIn; ++k) in[k] = bf16r(in[k]);
+    return keep;
+}
+
+VPGS_D void mma_bf16_16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                           uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+VPGS_D uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+struct DecOut {
+    float *means, *scales, *quats, *opac, *colors;
+    int32_t *n_out, *src_index;
+};
+
+// dynamic shared memory of the forward kernel
+struct DecFwdSmem {
+    float out[kDecAnchors * kOutStride];
+    union {
+        float w[8192];  // FP32 weights (n_params(10) = 7182)
+        struct {
+            __nv_bfloat16 w1[96 * kInPad];
+            __nv_bfloat16 w2[120 * kW2Pad];
+            __nv_bfloat16 in[kDecAnchors * kInPad];
+            float b1[96];
+            float b2[120];
+        } h;
+    } u;
+};
+
+__global__ void __launch_bounds__(kDecAnchors)
+decode_fwd_kernel(DecParams p, const double *__restrict__ T, DecOut o, uint32_t *ticket,
+                  unsigned long long *look, uint32_t *status) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    DecFwdSmem &S = *reinterpret_cast<DecFwdSmem *>(dsm);
+    __shared__ uint32_t s_bid, s_base;
+    __shared__ uint32_t s_wsum[kDecAnchors / 32];
+    __shared__ DecCam s_cam;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        s_bid = atomicAdd(ticket, 1u);
+        load_dec_cam(T, s_cam);
+    }
+    const int K = p.K;
+    const int np = n_params(K);
+    // weights to shared memory
+    if (!p.bf16) {
+        for (int i = tid; i < np; i += kDecAnchors) S.u.w[i] = p.params[i];
+    } else {
+        for (int i = tid; i < 96 * kInPad; i += kDecAnchors) {
+            const int r = i / kInPad, c = i % kInPad;
+            const MlpOff m = mlp_off(K, r / 32);
+            S.u.h.w1[i] = __float2bfloat16_rn(c < kIn ? p.params[m.w1 + (r % 32) * kIn + c] : 0.f);
+        }
+        for (int i = tid; i < 120 * kW2Pad; i += kDecAnchors) {
+            const int r = i / kW2Pad, c = i % kW2Pad;
+            const int j = r < kColCol ? 0 : (r < kColCov ? 1 : 2);
+            const int base = j == 0 ? kColOpa : (j == 1 ? kColCol : kColCov);
+            const MlpOff m = mlp_off(K, j);
+            const int n = r - base;
+            S.u.h.w2[i] = __float2bfloat16_rn((c < kHid && n < m.out) ? p.params[m.w2 + n * kHid + c] : 0.f);
+        }
+        for (int i = tid; i < 96; i += kDecAnchors) S.u.h.b1[i] = p.params[mlp_off(K, i / 32).b1 + i % 32];
+        for (int i = tid; i < 120; i += kDecAnchors) {
+            const int j = i < kColCol ? 0 : (i < kColCov ? 1 : 2);
+            const int base = j == 0 ? kColOpa : (j == 1 ? kColCol : kColCov);
+            const MlpOff m = mlp_off(K, j);
+            S.u.h.b2[i] = (i - base < m.out) ? p.params[m.b2 + i - base] : 0.f;
+        }
+    }
+    __syncthreads();
+    const int64_t bid = s_bid;
+    const int64_t a = bid * kDecAnchors + tid;
+    const bool live = a < p.A;
+    float in[kIn];
+    bool keep = false;
+    if (live) keep = anchor_inputs(p, s_cam, a, in);
+    float *orow = S.out + tid * kOutStride;
+    if (!p.bf16) {
+        if (keep) {
+            for (int j = 0; j < 3; ++j) {
+                const MlpOff m = mlp_off(K, j);
+                float h[kHid];
+#pragma unroll
+                for (int q = 0; q < kHid; ++q) {
+                    const float *w = S.u.w + m.w1 + q * kIn;
+                    float acc = S.u.w[m.b1 + q];
+#pragma unroll
+                    for (int k = 0; k < kIn; ++k) acc = fmaf(w[k], in[k], acc);
+                    h[q] = fmaxf(acc, 0.f);
+                }
+                const int base = j == 0 ? kColOpa : (j == 1 ? kColCol : kColCov);
+                for (int n = 0; n < m.out; ++n) {
+                    const float *w = S.u.w + m.w2 + n * kHid;
+                    float acc = S.u.w[m.b2 + n];
+#pragma unroll
+                    for (int k = 0; k < kHid; ++k) acc = fmaf(w[k], h[k], acc);
+                    orow[base + n] = acc;
+                }
+            }
+        }
+    } else {
+        // stage the (already BF16-rounded) inputs, then tensor-core tiles
+        __nv_bfloat16 *irow = S.u.h.in + tid * kInPad;
+        for (int k = 0; k < kInPad; ++k) irow[k] = __float2bfloat16_rn(live && k < kIn ? in[k] : 0.f);
+        __syncwarp();
+        const int g = lane >> 2, t4 = lane & 3;
+        for (int mt = 0; mt < 2; ++mt) {
+            const int r0 = warp * 32 + mt * 16;
+            float acc[12][4];
+#pragma unroll
+            for (int nt = 0; nt < 12; ++nt) {
+                const float b0 = S.u.h.b1[8 * nt + 2 * t4], b1v = S.u.h.b1[8 * nt + 2 * t4 + 1];
+                acc[nt][0] = b0; acc[nt][1] = b1v; acc[nt][2] = b0; acc[nt][3] = b1v;
+            }
+            const __nv_bfloat16 *A0 = S.u.h.in + (r0 + g) * kInPad, *A1 = S.u.h.in + (r0 + g + 8) * kInPad;
+#pragma unroll
+            for (int ks = 0; ks < 3; ++ks) {
+                const int c0 = 16 * ks + 2 * t4;
+                const uint32_t a0 = *reinterpret_cast<const uint32_t *>(A0 + c0);
+                const uint32_t a1 = *reinterpret_cast<const uint32_t *>(A1 + c0);
+                const uint32_t a2 = *reinterpret_cast<const uint32_t *>(A0 + c0 + 8);
+                const uint32_t a3 = *reinterpret_cast<const uint32_t *>(A1 + c0 + 8);
+#pragma unroll
+                for (int nt = 0; nt < 12; ++nt) {
+                    const __nv_bfloat16 *Brow = S.u.h.w1 + (8 * nt + g) * kInPad;
+                    mma_bf16_16816(acc[nt], a0, a1, a2, a3, *reinterpret_cast<const uint32_t *>(Brow + c0),
+                                   *reinterpret_cast<const uint32_t *>(Brow + c0 + 8));
+                }
+            }
+            // layer 2 per MLP: hidden (ReLU, BF16) comes straight from the accumulators
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const int ntiles = j == 0 ? 2 : (j == 1 ? 4 : 9);
+                const int base = j == 0 ? kColOpa : (j == 1 ? kColCol : kColCov);
+                uint32_t ha[2][4];
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {
+                    const float *x0 = acc[4 * j + 2 * kk], *x1 = acc[4 * j + 2 * kk + 1];
+                    ha[kk][0] = pack_bf16(fmaxf(x0[0], 0.f), fmaxf(x0[1], 0.f));
+                    ha[kk][1] = pack_bf16(fmaxf(x0[2], 0.f), fmaxf(x0[3], 0.f));
+                    ha[kk][2] = pack_bf16(fmaxf(x1[0], 0.f), fmaxf(x1[1], 0.f));
+                    ha[kk][3] = pack_bf16(fmaxf(x1[2], 0.f), fmaxf(x1[3], 0.f));
+                }
+                for (int nt = 0; nt < ntiles; ++nt) {
+                    const int col = base + 8 * nt + 2 * t4;
+                    float d[4] = {S.u.h.b2[col], S.u.h.b2[col + 1], S.u.h.b2[col], S.u.h.b2[col + 1]};
+                    const __nv_bfloat16 *Brow = S.u.h.w2 + (base + 8 * nt + g) * kW2Pad;
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const int c0 = 16 * kk + 2 * t4;
+                        mma_bf16_16816(d, ha[kk][0], ha[kk][1], ha[kk][2], ha[kk][3],
+                                       *reinterpret_cast<const uint32_t *>(Brow + c0),
+                                       *reinterpret_cast<const uint32_t *>(Brow + c0 + 8));
+                    }
+                    float *o0 = S.out + (r0 + g) * kOutStride + col;
+                    float *o1 = S.out + (r0 + g + 8) * kOutStride + col;
+                    o0[0] = d[0]; o0[1] = d[1]; o1[0] = d[2]; o1[1] = d[3];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // valid Gaussians of this anchor and their count
+    uint32_t mask = 0;
+    if (keep)
+        for (int m = 0; m < K; ++m)
+            if (orow[kColOpa + m] > 0.f) mask |= 1u << m;
+    const uint32_t cnt = __popc(mask);
+    // block exclusive scan of the counts
+    uint32_t x = cnt;
+#pragma unroll
+    for (int q = 1; q < 32; q <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, q);
+        if (lane >= q) x += y;
+    }
+    if (lane == 31) s_wsum[warp] = x;
+    __syncthreads();
+    uint32_t wbase = 0, total = 0;
+    for (int w = 0; w < kDecAnchors / 32; ++w) {
+        if (w < warp) wbase += s_wsum[w];
+        total += s_wsum[w];
+    }
+    if (tid == 0) {
+        uint32_t excl = 0;
+        if (bid == 0) {
+            st_volatile_u64(look, kFlagPre | total);
+        } else {
+            st_volatile_u64(look + bid, kFlagAgg | total);
+            int64_t j = bid - 1;
+            unsigned long long acc = 0;
+            while (j >= 0) {
+                unsigned long long w = ld_volatile_u64(look + j);
+                int spins = 0;
+                while ((w >> 62) == 0) {
+                    if (++spins > kSpinLimit) {
+                        set_status(status, VPGS_ERR_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(64);
+                    w = ld_volatile_u64(look + j);
+                }
+                acc += w & kValMask;
+                if ((w >> 62) == 2 || spins > kSpinLimit) break;
+                --j;
+            }
+            excl = (uint32_t)acc;
+            st_volatile_u64(look + bid, kFlagPre | (acc + total));
+        }
+        s_base = excl;
+        if ((bid + 1) * kDecAnchors >= p.A) *o.n_out = (int32_t)(excl + total);
+    }
+    __syncthreads();
+    if (!mask) return;
+    const int64_t cap = p.A * K;
+    int64_t pos = (int64_t)s_base + wbase + (x - cnt);
+    const float l0 = p.scaling[3 * a], l1 = p.scaling[3 * a + 1], l2 = p.scaling[3 * a + 2];
+    const float xa = p.anchors[3 * a], ya = p.anchors[3 * a + 1], za = p.anchors[3 * a + 2];
+    for (int m = 0; m < K; ++m) {
+        if (!(mask >> m & 1u)) continue;
+        if (pos >= cap) break;  // only after a timed-out look-back
+        const float *O = p.offsets + (a * K + m) * 3;
+        o.means[3 * pos] = fmaf(O[0], l0, xa);
+        o.means[3 * pos + 1] = fmaf(O[1], l1, ya);
+        o.means[3 * pos + 2] = fmaf(O[2], l2, za);
+        o.opac[pos] = tanhf(orow[kColOpa + m]);
+        const float *cc = orow + kColCol + 3 * m;
+        o.colors[3 * pos] = sigmoidf_(cc[0]);
+        o.colors[3 * pos + 1] = sigmoidf_(cc[1]);
+        o.colors[3 * pos + 2] = sigmoidf_(cc[2]);
+        const float *cv = orow + kColCov + 7 * m;
+        o.scales[3 * pos] = sigmoidf_(cv[0]) * l0;
+        o.scales[3 * pos + 1] = sigmoidf_(cv[1]) * l1;
+        o.scales[3 * pos + 2] = sigmoidf_(cv[2]) * l2;
+        const float inv = 1.0f / sqrtf(cv[3] * cv[3] + cv[4] * cv[4] + cv[5] * cv[5] + cv[6] * cv[6]);
+        reinterpret_cast<float4 *>(o.quats)[pos] = make_float4(cv[3] * inv, cv[4] * inv, cv[5] * inv, cv[6] * inv);
+        o.src_index[pos] = (int32_t)(a * K + m);
+        ++pos;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// backward
+// ---------------------------------------------------------------------------
+
+__global__ void inverse_index_kernel(const int32_t *src_index, const int32_t *n_out, int64_t n_cap,
+                                     int64_t inv_size, int32_t *inv) {
+    const int64_t n = min(n_cap, (int64_t)*n_out);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = src_index[i];
+        if (s >= 0 && s < inv_size) inv[s] = (int32_t)i;
+    }
+}
+
+struct DecGradIn {
+    const float *means, *scales, *quats, *opac, *colors;
+};
+
+struct DecGradOut {
+    float *features, *offsets, *scaling, *params;
+};
+
+constexpr int kBwdAnchors = 64;
+constexpr int kRowIn = 37, kRowH = 33, kRowOut = 73;
+
+struct DecBwdSmem {
+    float w[8192];                                  // effective (FP32 or BF16-rounded) weights
+    float in[kBwdAnchors * kRowIn];
+    float h[kBwdAnchors * kRowH];
+    float dpre[kBwdAnchors * kRowH];
+    float dout[kBwdAnchors * kRowOut];
+    float din[kBwdAnchors * kRowIn];
+};
+
+__global__ void __launch_bounds__(kBwdAnchors)
+decode_bwd_kernel(DecParams p, const double *__restrict__ T, const int32_t *__restrict__ inv,
+                  DecGradIn gin, DecGradOut gout) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    DecBwdSmem &S = *reinterpret_cast<DecBwdSmem *>(dsm);
+    __shared__ DecCam s_cam;
+    const int tid = threadIdx.x;
+    const int K = p.K;
+    const int np = n_params(K);
+    if (tid == 0) load_dec_cam(T, s_cam);
+    for (int i = tid; i < np; i += kBwdAnchors) {
+        // BF16 form: the weight matrices were rounded in the forward pass, biases were not
+        float wv = p.params[i];
+        if (p.bf16) {
+            bool is_bias = false;
+            for (int j = 0; j < 3; ++j) {
+                const MlpOff m = mlp_off(K, j);
+                if ((i >= m.b1 && i < m.b1 + kHid) || (i >= m.b2 && i < m.b2 + m.out)) is_bias = true;
+            }
+            if (!is_bias) wv = bf16r(wv);
+        }
+        S.w[i] = wv;
+    }
+    __syncthreads();
+    const int64_t a = (int64_t)blockIdx.x * kBwdAnchors + tid;
+    const bool live = a < p.A;
+    float in[kIn];
+    bool keep = false;
+    if (live) keep = anchor_inputs(p, s_cam, a, in);
+    float *sin_ = S.in + tid * kRowIn;
+    float *sh = S.h + tid * kRowH;
+    float *sdp = S.dpre + tid * kRowH;
+    float *sdo = S.dout + tid * kRowOut;
+    float *sdi = S.din + tid * kRowIn;
+    for (int k = 0; k < kIn; ++k) {
+        sin_[k] = keep ? in[k] : 0.f;
+        sdi[k] = 0.f;
+    }
+    // which decoded Gaussians of this anchor survived, and where they are
+    int idx[kMaxK];
+    bool any = false;
+    for (int m = 0; m < K; ++m) {
+        idx[m] = keep ? inv[a * K + m] : -1;
+        any |= idx[m] >= 0;
+    }
+    float l[3] = {0, 0, 0}, dl[3] = {0, 0, 0};
+    if (live) {
+        l[0] = p.scaling[3 * a]; l[1] = p.scaling[3 * a + 1]; l[2] = p.scaling[3 * a + 2];
+    }
+    for (int j = 0; j < 3; ++j) {
+        const MlpOff m = mlp_off(K, j);
+        // recompute hidden activations
+        float h[kHid];
+        for (int q = 0; q < kHid; ++q) {
+            float acc = S.w[m.b1 + q];
+            for (int k = 0; k < kIn; ++k) acc = fmaf(S.w[m.w1 + q * kIn + k], in[k], acc);
+            const float hv = fmaxf(acc, 0.f);
+            h[q] = p.bf16 ? bf16r(hv) : hv;
+            sh[q] = any ? h[q] : 0.f;
+            sdp[q] = acc > 0.f ? 1.f : 0.f;  // ReLU mask, turned into dpre below
+        }
+        float dh[kHid];
+        for (int q = 0; q < kHid; ++q) dh[q] = 0.f;
+        for (int n = 0; n < m.out; ++n) sdo[n] = 0.f;
+        if (any) {
+            for (int g = 0; g < K; ++g) {
+                const int i = idx[g];
+                if (i < 0) continue;
+                // outputs of this Gaussian in MLP j
+                const int w = j == 0 ? 1 : (j == 1 ? 3 : 7);
+                float o[7];
+                for (int r = 0; r < w; ++r) {
+                    const int n = w * g + r;
+                    float acc = S.w[m.b2 + n];
+                    for (int k = 0; k < kHid; ++k) acc = fmaf(S.w[m.w2 + n * kHid + k], h[k], acc);
+                    o[r] = acc;
+                }
+                float d[7];
+                if (j == 0) {
+                    const float al = tanhf(o[0]);
+                    d[0] = gin.opac[i] * (1.f - al * al);
+                } else if (j == 1) {
+                    for (int r = 0; r < 3; ++r) {
+                        const float c = sigmoidf_(o[r]);
+                        d[r] = gin.colors[3 * i + r] * c * (1.f - c);
+                    }
+                } else {
+                    for (int r = 0; r < 3; ++r) {
+                        const float sg = sigmoidf_(o[r]);
+                        const float gs = gin.scales[3 * i + r];
+                        d[r] = gs * l[r] * sg * (1.f - sg);
+                        dl[r] += gs * sg;
+                    }
+                    const float nrm = sqrtf(o[3] * o[3] + o[4] * o[4] + o[5] * o[5] + o[6] * o[6]);
+                    const float inn = 1.0f / nrm;
+                    const float4 gq = reinterpret_cast<const float4 *>(gin.quats)[i];
+                    const float qn[4] = {o[3] * inn, o[4] * inn, o[5] * inn, o[6] * inn};
+                    const float gqv[4] = {gq.x, gq.y, gq.z, gq.w};
+                    const float dot = qn[0] * gqv[0] + qn[1] * gqv[1] + qn[2] * gqv[2] + qn[3] * gqv[3];
+                    for (int r = 0; r < 4; ++r) d[3 + r] = (gqv[r] - qn[r] * dot) * inn;
+                }
+                for (int r = 0; r < w; ++r) {
+                    const int n = w * g + r;
+                    sdo[n] = d[r];
+                    for (int k = 0; k < kHid; ++k) dh[k] = fmaf(S.w[m.w2 + n * kHid + k], d[r], dh[k]);
+                }
+            }
+        }
+        float dpre[kHid];
+        for (int q = 0; q < kHid; ++q) {
+            dpre[q] = any ? dh[q] * sdp[q] : 0.f;
+            sdp[q] = dpre[q];
+        }
+        for (int k = 0; k < kIn; ++k) {
+            float acc = 0.f;
+            for (int q = 0; q < kHid; ++q) acc = fmaf(S.w[m.w1 + q * kIn + k], dpre[q], acc);
+            sdi[k] += acc;
+        }
+        __syncthreads();
+        // block reduction of the weight gradients of MLP j
+        if (gout.params) {
+            for (int e = tid; e < kHid * kIn; e += kBwdAnchors) {  // dW1[q][k] = sum_a dpre[a][q] in[a][k]
+                const int q = e / kIn, k = e % kIn;
+                float acc = 0.f;
+                for (int r = 0; r < kBwdAnchors; ++r) acc = fmaf(S.dpre[r * kRowH + q], S.in[r * kRowIn + k], acc);
+                if (acc != 0.f) atomicAdd(gout.params + m.w1 + e, acc);
+            }
+            for (int q = tid; q < kHid; q += kBwdAnchors) {
+                float acc = 0.f;
+                for (int r = 0; r < kBwdAnchors; ++r) acc += S.dpre[r * kRowH + q];
+                if (acc != 0.f) atomicAdd(gout.params + m.b1 + q, acc);
+            }
+            for (int e = tid; e < m.out * kHid; e += kBwdAnchors) {  // dW2[n][k] = sum_a dout[a][n] h[a][k]
+                const int n = e / kHid, k = e % kHid;
+                float acc = 0.f;
+                for (int r = 0; r < kBwdAnchors; ++r) acc = fmaf(S.dout[r * kRowOut + n], S.h[r * kRowH + k], acc);
+                if (acc != 0.f) atomicAdd(gout.params + m.w2 + e, acc);
+            }
+            for (int n = tid; n < m.out; n += kBwdAnchors) {
+                float acc = 0.f;
+                for (int r = 0; r < kBwdAnchors; ++r) acc += S.dout[r * kRowOut + n];
+                if (acc != 0.f) atomicAdd(gout.params + m.b2 + n, acc);
+            }
+        }
+        __syncthreads();
+    }
+    if (!live || !any) return;
+    if (gout.features)
+        for (int k = 0; k < kFeat; ++k) gout.features[kFeat * a + k] += sdi[k];
+    for (int g = 0; g < K; ++g) {
+        const int i = idx[g];
+        if (i < 0) continue;
+        const float *O = p.offsets + (a * K + g) * 3;
+        const float gm[3] = {gin.means[3 * i], gin.means[3 * i + 1], gin.means[3 * i + 2]};
+        for (int r = 0; r < 3; ++r) {
+            if (gout.offsets) gout.offsets[(a * K + g) * 3 + r] += gm[r] * l[r];
+            dl[r] += gm[r] * O[r];
+        }
+    }
+    if (gout.scaling)
+        for (int r = 0; r < 3; ++r) gout.scaling[3 * a + r] += dl[r];
+}
+
+// ---------------------------------------------------------------------------
+// workspace: [0] status, [256] counters (ticket), [512] look-back words, inverse map
+// ---------------------------------------------------------------------------
+struct DecLayout {
+    size_t off_status, off_counters, off_look, off_inv, total;
+    int64_t nblocks;
+};
+
+static DecLayout dec_layout(int64_t A, int K) {
+    DecLayout L;
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    L.nblocks = (A + kDecAnchors - 1) / kDecAnchors;
+    L.off_status = 0;
+    L.off_counters = 256;
+    L.off_look = 512;
+    L.off_inv = up(L.off_look + 8 * (size_t)std::max<int64_t>(L.nblocks, 1));
+    L.total = up(L.off_inv + 4 * (size_t)std::max<int64_t>(A * K, 1));
+    return L;
+}
+
+static bool fill_params(const vpgs_anchors *a, const vpgs_mlp *mlp, const vpgs_camera *cam,
+                        const vpgs_decode_opts *opts, DecParams &p) {
+    if (!a || !mlp || !cam || !opts || !mlp->params || a->n < 0 || a->k < 1 || a->k > kMaxK) return false;
+    if (a->n > 0 && (!a->anchors || !a->scaling || !a->offsets || !a->features)) return false;
+    if (a->n * a->k >= (int64_t(1) << 31)) return false;
+    if (cam->width <= 0 || cam->height <= 0) return false;
+    if (!a->features_bf16 && (reinterpret_cast<uintptr_t>(a->features) & 15u)) return false;
+    p.anchors = a->anchors; p.scaling = a->scaling; p.offsets = a->offsets; p.features = a->features;
+    p.A = a->n; p.K = a->k; p.feat_bf16 = a->features_bf16 != 0;
+    p.params = mlp->params; p.bf16 = mlp->bf16 != 0;
+    p.fx = cam->fx; p.fy = cam->fy; p.cx = cam->cx; p.cy = cam->cy; p.W = cam->width; p.H = cam->height;
+    p.near_z = opts->near_z; p.guard = opts->guard;
+    return true;
+}
+
+}  // namespace vpgs
+
+using namespace vpgs;
 
 extern "C" {
 
 size_t vpgs_decode_workspace_bytes(int64_t n_anchors, int32_t k) {
-    (void)n_anchors; (void)k;
-    return 0;
+    if (n_anchors < 0 || k < 1 || k > kMaxK) return 0;
+    return dec_layout(n_anchors, k).total;
 }
 
-vpgs_status vpgs_decode_anchors(void *, size_t, const vpgs_anchors *, const vpgs_mlp *,
-                                const vpgs_camera *, const double *, const vpgs_decode_opts *,
-                                const vpgs_gaussian_buffers *, int32_t *, int32_t *, vpgs_stream) {
-    return VPGS_ERR_UNSUPPORTED;
+vpgs_status vpgs_decode_anchors(void *ws, size_t ws_bytes, const vpgs_anchors *a, const vpgs_mlp *mlp,
+                                const vpgs_camera *cam, const double *T_cw, const vpgs_decode_opts *opts,
+                                const vpgs_gaussian_buffers *out, int32_t *n_out, int32_t *src_index,
+                                vpgs_stream stream) {
+    DecParams p;
+    if (!ws || !T_cw || !out || !n_out || !src_index || !fill_params(a, mlp, cam, opts, p))
+        return VPGS_ERR_INVALID_ARG;
+    if (!out->means || !out->scales || !out->quats || !out->opacities || !out->colors)
+        return VPGS_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(out->quats) & 15u) return VPGS_ERR_INVALID_ARG;
+    const DecLayout L = dec_layout(p.A, p.K);
+    if (ws_bytes < L.total) return VPGS_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char *b = static_cast<char *>(ws);
+    cudaError_t e = cudaMemsetAsync(b, 0, L.off_look + 8 * (size_t)std::max<int64_t>(L.nblocks, 1), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n_out, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess || p.A == 0) return e == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
+    static bool attr_set = false;
+    const size_t smem = sizeof(DecFwdSmem);
+    if (!attr_set) {
+        cudaFuncSetAttribute((const void *)decode_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        attr_set = true;
+    }
+    DecOut o{out->means, out->scales, out->quats, out->opacities, out->colors, n_out, src_index};
+    uint32_t *status = reinterpret_cast<uint32_t *>(b + L.off_status);
+    uint32_t *ticket = reinterpret_cast<uint32_t *>(b + L.off_counters + 4 * CNT_TICKET_A);
+    unsigned long long *look = reinterpret_cast<unsigned long long *>(b + L.off_look);
+    VPGS_LAUNCH("decode_fwd", s,
+                decode_fwd_kernel<<<(unsigned)L.nblocks, kDecAnchors, smem, s>>>(p, T_cw, o, ticket,
+                                                                                 look, status));
+    return cudaGetLastError() == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
 }
 
-vpgs_status vpgs_decode_anchors_bwd(void *, size_t, const vpgs_anchors *, const vpgs_mlp *,
-                                    const vpgs_camera *, const double *, const vpgs_decode_opts *,
-                                    const vpgs_gaussians *, const int32_t *, float *, float *, float *,
-                                    float *, vpgs_stream) {
-    return VPGS_ERR_UNSUPPORTED;
+vpgs_status vpgs_decode_anchors_bwd(void *ws, size_t ws_bytes, const vpgs_anchors *a, const vpgs_mlp *mlp,
+                                    const vpgs_camera *cam, const double *T_cw,
+                                    const vpgs_decode_opts *opts, const vpgs_gaussians *dL,
+                                    const int32_t *src_index, float *dL_dfeatures, float *dL_doffsets,
+                                    float *dL_dscaling, float *dL_dparams, vpgs_stream stream) {
+    DecParams p;
+    if (!ws || !T_cw || !dL || !src_index || !dL->n_dev || !fill_params(a, mlp, cam, opts, p))
+        return VPGS_ERR_INVALID_ARG;
+    if (!dL->means || !dL->scales || !dL->quats || !dL->opacities || !dL->colors)
+        return VPGS_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(dL->quats) & 15u) return VPGS_ERR_INVALID_ARG;
+    const DecLayout L = dec_layout(p.A, p.K);
+    if (ws_bytes < L.total) return VPGS_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (p.A == 0) return VPGS_OK;
+    char *b = static_cast<char *>(ws);
+    int32_t *inv = reinterpret_cast<int32_t *>(b + L.off_inv);
+    const int64_t cap = p.A * p.K;
+    cudaError_t e = cudaMemsetAsync(inv, 0xff, 4 * (size_t)cap, s);
+    if (e != cudaSuccess) return VPGS_ERR_CUDA;
+    const int sms = device_sm_count();
+    const int ib = (int)std::min<int64_t>((cap + 255) / 256, (int64_t)sms * 8);
+    VPGS_LAUNCH("decode_inverse_index", s,
+                inverse_index_kernel<<<ib, 256, 0, s>>>(src_index, dL->n_dev, dL->n, cap, inv));
+    static bool attr_set = false;
+    const size_t smem = sizeof(DecBwdSmem);
+    if (!attr_set) {
+        cudaFuncSetAttribute((const void *)decode_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        attr_set = true;
+    }
+    DecGradIn gin{dL->means, dL->scales, dL->quats, dL->opacities, dL->colors};
+    DecGradOut gout{dL_dfeatures, dL_doffsets, dL_dscaling, dL_dparams};
+    const unsigned nb = (unsigned)((p.A + kBwdAnchors - 1) / kBwdAnchors);
+    VPGS_LAUNCH("decode_bwd", s, decode_bwd_kernel<<<nb, kBwdAnchors, smem, s>>>(p, T_cw, inv, gin, gout));
+    return cudaGetLastError() == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
 }
 
 }  // extern "C"
