@@ -173,6 +173,37 @@ vpgs_status vpgs_render_project(void *ws, size_t ws_bytes, const vpgs_gaussians 
                                 int32_t *tile_rect, float *mean2d, float *depth, float *conic,
                                 vpgs_stream stream);
 
+/* Size of the scratch array behind vpgs_render_fwd_noalloc: 32 MiB.  Every
+ * GPU that loads this library holds it until the process exits. */
+#define VPGS_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* vpgs_render_fwd for callers that cannot allocate device memory.  The paper
+ * has no counterpart: this is an interface for hosts whose device memory is
+ * not theirs to allocate.  Examples are a plugin handed only a stream and the
+ * tensors it must read and write, a process whose memory pool reserved the GPU
+ * up front, and code that must not allocate while a CUDA graph is captured.
+ *
+ * Same inputs and outputs as vpgs_render_fwd, without the workspace.  The
+ * scratch space is a VPGS_NOALLOC_SCRATCH_BYTES array compiled into the library.
+ * This call allocates nothing: no cudaMalloc, no cudaFree, no allocating
+ * library routine.
+ *   - Returns VPGS_ERR_UNSUPPORTED, launching nothing, when the render needs
+ *     more scratch than that (about 10^5 Gaussians per view at most; the tile
+ *     instances take the rest).
+ *   - status_out (device int32, may be NULL) receives the device status word
+ *     of the render.  VPGS_ERR_CAPACITY there means that the tile instances
+ *     did not fit in the array.
+ *   - The first call on each device looks the array's device address up
+ *     (cudaGetSymbolAddress) with that device current.  Make that first call
+ *     before capturing any stream.
+ *   - Every call shares the one array, and a call leaves its contents behind.
+ *     The render clears what it needs zeroed.  Calls that overlap on the GPU
+ *     (other streams, other threads) race on the array, so serialise them. */
+vpgs_status vpgs_render_fwd_noalloc(const vpgs_gaussians *g, const vpgs_camera *cam,
+                                    const double *T_cw, int32_t n_views,
+                                    const vpgs_render_opts *opts, const vpgs_images *out,
+                                    int32_t *status_out, vpgs_stream stream);
+
 /* Reads the status word and counters of a render workspace (host `stats`).  It
  * synchronises `stream` first, and is the one call here that blocks. */
 vpgs_status vpgs_workspace_status(const void *ws, vpgs_render_stats *stats, vpgs_stream stream);

@@ -81,6 +81,9 @@ _SIGS = {
                                       POINTER(vpgs_camera), c_void_p, c_int32,
                                       POINTER(vpgs_render_opts), c_void_p, c_void_p, c_void_p,
                                       c_void_p, c_void_p, c_void_p]),
+    "vpgs_render_fwd_noalloc": (c_int32, [POINTER(vpgs_gaussians), POINTER(vpgs_camera), c_void_p,
+                                          c_int32, POINTER(vpgs_render_opts), POINTER(vpgs_images),
+                                          c_void_p, c_void_p]),
     "vpgs_workspace_status": (c_int32, [c_void_p, POINTER(vpgs_render_stats), c_void_p]),
     "vpgs_pose_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, POINTER(c_double),
                                  c_void_p]),
@@ -146,6 +149,7 @@ vpgs_render_workspace_bytes = _entry("vpgs_render_workspace_bytes")
 vpgs_render_fwd = _entry("vpgs_render_fwd")
 vpgs_render_bwd = _entry("vpgs_render_bwd")
 vpgs_render_project = _entry("vpgs_render_project")
+vpgs_render_fwd_noalloc = _entry("vpgs_render_fwd_noalloc")
 vpgs_workspace_status = _entry("vpgs_workspace_status")
 vpgs_pose_step = _entry("vpgs_pose_step")
 vpgs_decode_workspace_bytes = _entry("vpgs_decode_workspace_bytes")
