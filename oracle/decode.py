@@ -57,26 +57,31 @@ def n_mlp_params(k: int, feat: int = 32, hidden: int = 32) -> int:
 
 
 def _bf16_midpoint_distance(x: np.ndarray) -> np.ndarray:
-    """Relative distance of x to the nearest BF16 rounding midpoint."""
+    """Absolute distance of x to the nearest BF16 rounding midpoint."""
     x = np.asarray(x, np.float64)
     ax = np.abs(x)
     with np.errstate(divide="ignore", invalid="ignore"):
         e = np.floor(np.log2(np.where(ax > 0, ax, 1.0)))
         ulp = np.exp2(e - 7)
         frac = ax / ulp - np.floor(ax / ulp)          # position inside the ulp
-        d = np.abs(frac - 0.5) * ulp / np.where(ax > 0, ax, 1.0)
+        d = np.abs(frac - 0.5) * ulp
     return np.where(ax > 0, d, np.inf)
 
 
+FP32_EPS = 2.0 ** -24
+
+
 def decode(anchors, features, scaling, offsets, mlp, T_cw, fx, fy, cx, cy, width, height,
-           near_z=0.2, guard=0.15, bf16=False, grads=None, margin=1e-5):
+           near_z=0.2, guard=0.15, bf16=False, grads=None, margin=1e-5, acc_ulps=8.0):
     """Decode anchors seen by one camera.
 
     Returns a dict with the compacted Gaussians (means, scales, quats,
     opacities, colors as float64 numpy arrays), src_index [N] (a*k + m), the
     kept-anchor mask [A], and a per-anchor `flags` mask marking anchors whose
     result depends on a decision taken within `margin` (relative) of its
-    threshold (cull, ReLU, validity, BF16 rounding).  With grads = dict of
+    threshold (cull, ReLU, validity), or, with bf16, a value that an FP32
+    evaluation within acc_ulps FP32 ulps of its sum of |terms| could round to
+    the other BF16 neighbour.  With grads = dict of
     dL/d{means,scales,quats,opacities,colors} for the compacted Gaussians it
     also returns d_features [A,32], d_offsets [A,k,3], d_scaling [A,3] and
     d_w (flat MLP parameter gradient).
@@ -132,13 +137,18 @@ def decode(anchors, features, scaling, offsets, mlp, T_cw, fx, fy, cx, cy, width
             oscale = h.abs() @ W2e.abs().T + b2.abs()
             if name == "opacity":
                 flags |= ((out.abs() <= margin * oscale).any(1))
-            pre_all.append(pre.detach().numpy())
+            pre_all.append((pre.detach().numpy(), scale.numpy()))
     if bf16:
         with torch.no_grad():
-            dist = np.stack([_bf16_midpoint_distance(pa) for pa in pre_all], 0)
-            flags |= torch.as_tensor((dist <= margin).any(axis=(0, 2)))
-            dd = _bf16_midpoint_distance(torch.cat([d, delta], 1).detach().numpy())
-            flags |= torch.as_tensor((dd <= margin).any(1))
+            # hidden units: FP32 accumulation error is bounded by a few ulps of the
+            # sum of |terms|; flag values that close to a BF16 rounding midpoint
+            for pa, sc in pre_all:
+                near = (pa > 0) & (_bf16_midpoint_distance(pa) <= acc_ulps * FP32_EPS * sc)
+                flags |= torch.as_tensor(near.any(1))
+            # view inputs computed in FP32 (a few roundings) before the BF16 rounding
+            vin = torch.cat([d, delta], 1).detach().numpy()
+            dd = _bf16_midpoint_distance(vin) <= acc_ulps * FP32_EPS * np.abs(vin)
+            flags |= torch.as_tensor(dd.any(1))
     # heads
     opac = torch.tanh(outs["opacity"])                    # [A,k]
     color = torch.sigmoid(outs["color"]).reshape(A, k, 3)

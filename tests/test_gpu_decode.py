@@ -63,7 +63,7 @@ def test_decode_forward_parity(bf16):
     ref = _oracle(sc, bf16)
     _, _, _, out = _gpu(sc, bf16)
     assert ref["n"] > 1000
-    assert ref["flags"].mean() < 0.2
+    assert ref["flags"].mean() < (0.15 if bf16 else 0.02)
     _compare_outputs(out, ref, ref["flags"], sc.k, 1e-5)
 
 

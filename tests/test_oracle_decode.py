@@ -95,8 +95,8 @@ def test_bf16_rounding_hand_values():
     assert r[0] == 1.0 and r[1] == 1.0 + 2 ** -6 and r[2] == 1.0 + 2 ** -7 and r[3] == -3.0
     # 1e-3 = 0x3A83126F in fp32 -> bf16 0x3A83 = 0.00099945068359375
     assert r[4] == 0.00099945068359375
-    d = _bf16_midpoint_distance(np.array([1.0 + 2 ** -8, 1.0 + 2 ** -7]))
-    assert d[0] == 0.0 and d[1] > 1e-3
+    d = _bf16_midpoint_distance(np.array([1.0 + 2 ** -8, 1.0 + 2 ** -7, 3.0 + 2 ** -8]))
+    assert d[0] == 0.0 and d[1] == 2 ** -8 and d[2] == 2 ** -8  # midpoints of [3, 3+2^-6] at 3+2^-7
 
 
 def test_bf16_decode_is_exact_on_bf16_representable_networks():
