@@ -49,6 +49,8 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip tracking/e2e/profile passes")
     p.add_argument("--persistent", type=int, default=0, help="persistent CTAs per SM (0 = per tile)")
+    p.add_argument("--scale", type=float, default=1.0,
+                   help="shrink the workload for profiling: N x scale^2 Gaussians, image x scale")
     return p.parse_args()
 
 
@@ -247,7 +249,11 @@ def run_ours(a):
         dist.barrier()
     C.lib()
     dev = torch.device("cuda", local)
-    sc = scenes.indoor_room()
+    if a.scale == 1.0:
+        sc = scenes.indoor_room()
+    else:
+        sc = scenes.indoor_room(n=int(1_000_000 * a.scale ** 2), width=int(1200 * a.scale),
+                                height=int(680 * a.scale) // 2 * 2, f=600.0 * a.scale)
     cam = sc.camera
     H, W, V = cam.height, cam.width, 1
     P = V * H * W
@@ -315,7 +321,8 @@ def run_ours(a):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_gaussians": sc.n, "width": W, "height": H,
+            "config": {"workload": WORKLOAD if a.scale == 1.0 else f"room scaled x{a.scale}",
+                       "n_gaussians": sc.n, "width": W, "height": H,
                        "visible": Nv, "instances": M, "tile": "16x16",
                        "l2": "256 MiB buffer written between timed steps (inputs 56 MB < L2)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",

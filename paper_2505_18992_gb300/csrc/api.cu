@@ -20,8 +20,9 @@ inline int bits_for(int64_t max_value) {
 bool valid_opts(const vpgs_render_opts *o) {
     if (!o) return false;
     if (o->tile_w < 4 || o->tile_w > 32 || o->tile_h < 1 || o->tile_h > 32) return false;
+    // two pixels per thread (rows y and y + tile_h/2): tile_h even, whole warps
     const int B = o->tile_w * o->tile_h;
-    if (B % 32 != 0 || B > 1024) return false;
+    if (o->tile_h % 2 != 0 || B % 64 != 0 || B > 1024) return false;
     if (!(o->alpha_min > 0.f && o->alpha_min < 1.f)) return false;
     if (!(o->alpha_max > o->alpha_min && o->alpha_max < 1.f)) return false;
     if (!(o->t_min > 0.f && o->t_min < 1.f)) return false;
@@ -76,6 +77,7 @@ bool make_layout(int64_t N, int V, const vpgs_camera *cam, const vpgs_render_opt
     L.scan_blocks_max = scan_blocks(VN1);
     L.off_scan_look = take(8 * (size_t)L.scan_blocks_max);
     L.off_g2d = take(4 * 10 * (size_t)VN1);
+    L.off_posedf = take(4 * 24 * (size_t)V);
     L.total = off;
     return true;
 }
@@ -102,7 +104,7 @@ RenderWs carve(void *base, const RenderLayout &L) {
     w.sort_look = reinterpret_cast<uint32_t *>(b + L.off_sort_look);
     w.scan_look = reinterpret_cast<unsigned long long *>(b + L.off_scan_look);
     w.g2d = reinterpret_cast<float *>(b + L.off_g2d);
-    w.pose = nullptr;
+    w.posedf = reinterpret_cast<float *>(b + L.off_posedf);
     return w;
 }
 

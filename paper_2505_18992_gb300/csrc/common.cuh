@@ -76,13 +76,26 @@ struct PoseDF {
     df t[3];
 };
 
-VPGS_D void load_pose(const double *T, PoseDF &P) {
-#pragma unroll
+// T (float64 [4,4]) -> 24 floats: R[9] and t[3] as (hi, lo) pairs.  Done once
+// per view and call; FP64 is far too slow on this part to convert per Gaussian.
+VPGS_D void pose_to_df(const double *T, float *out) {
     for (int r = 0; r < 3; ++r) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) P.R[3 * r + c] = df_from_double(__ldg(T + 4 * r + c));
-        P.t[r] = df_from_double(__ldg(T + 4 * r + 3));
+        for (int c = 0; c < 3; ++c) {
+            const df x = df_from_double(T[4 * r + c]);
+            out[2 * (3 * r + c)] = x.hi;
+            out[2 * (3 * r + c) + 1] = x.lo;
+        }
+        const df x = df_from_double(T[4 * r + 3]);
+        out[18 + 2 * r] = x.hi;
+        out[18 + 2 * r + 1] = x.lo;
     }
+}
+
+VPGS_D void load_pose(const float *pd, PoseDF &P) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) P.R[k] = df{__ldg(pd + 2 * k), __ldg(pd + 2 * k + 1)};
+#pragma unroll
+    for (int r = 0; r < 3; ++r) P.t[r] = df{__ldg(pd + 18 + 2 * r), __ldg(pd + 19 + 2 * r)};
 }
 
 // p_c = R mu + t in double-float, mu exact float32
@@ -153,7 +166,7 @@ struct RenderLayout {
     // offsets in bytes
     size_t off_status, off_counters, off_rec, off_rect, off_tcount, off_scan_a, off_dkey0,
         off_dval0, off_dkey1, off_dval1, off_ikey0, off_ival0, off_ikey1, off_ival1, off_ranges,
-        off_sort_hist, off_sort_look, off_scan_look, off_g2d, off_pose, total;
+        off_sort_hist, off_sort_look, off_scan_look, off_g2d, off_posedf, total;
     int64_t sort_blocks_max, scan_blocks_max;
 };
 
@@ -181,7 +194,7 @@ struct RenderWs {
     uint32_t *sort_look;  // look-back status words
     unsigned long long *scan_look;
     float *g2d;           // [VN,10] 2D gradients
-    double *pose;         // [V,6]
+    float *posedf;        // [V,24] poses as double-float pairs
 };
 
 // radix sort geometry

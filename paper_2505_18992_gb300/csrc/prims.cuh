@@ -97,35 +97,46 @@ scan_kernel(Load load, Store store, int64_t n_cap, const uint32_t *n_dev, uint32
     __syncthreads();
     const uint32_t block_agg = s_warp[kScanThreads / kWarp - 1];
     uint32_t texcl = x - tsum + (warp > 0 ? s_warp[warp - 1] : 0u);
-    // decoupled look-back (one thread)
-    if (tid == 0) {
-        uint32_t excl = 0;
+    // decoupled look-back, one warp: 32 predecessors per step
+    if (warp == 0) {
+        unsigned long long excl = 0;
         if (bid == 0) {
-            st_volatile_u64(look, kFlagPre | block_agg);
+            if (lane == 0) st_volatile_u64(look, kFlagPre | block_agg);
         } else {
-            st_volatile_u64(look + bid, kFlagAgg | block_agg);
-            int64_t j = bid - 1;
-            unsigned long long acc = 0;
-            while (j >= 0) {
-                unsigned long long w = ld_volatile_u64(look + j);
+            if (lane == 0) st_volatile_u64(look + bid, kFlagAgg | block_agg);
+            int64_t j0 = bid - 1;
+            for (;;) {
+                const int64_t j = j0 - lane;
+                unsigned long long w = j >= 0 ? ld_volatile_u64(look + j) : kFlagPre;
                 int spins = 0;
-                while ((w >> 62) == 0) {
+                bool timed_out = false;
+                while (!__all_sync(0xffffffffu, (w >> 62) != 0)) {
                     if (++spins > kSpinLimit) {
-                        set_status(status, VPGS_ERR_TIMEOUT);
+                        timed_out = true;
                         break;
                     }
                     __nanosleep(64);
-                    w = ld_volatile_u64(look + j);
+                    if ((w >> 62) == 0) w = ld_volatile_u64(look + j);
                 }
-                acc += w & kValMask;
-                if ((w >> 62) == 2 || spins > kSpinLimit) break;
-                --j;
+                if (timed_out) {
+                    if (lane == 0) set_status(status, VPGS_ERR_TIMEOUT);
+                    break;
+                }
+                const uint32_t pre = __ballot_sync(0xffffffffu, (w >> 62) == 2);
+                const int last = pre ? __ffs(pre) - 1 : 31;  // nearest inclusive prefix
+                unsigned long long v = lane <= last ? (w & kValMask) : 0ull;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                excl += v;
+                if (pre) break;
+                j0 -= 32;
             }
-            excl = (uint32_t)acc;
-            st_volatile_u64(look + bid, kFlagPre | (acc + block_agg));
+            if (lane == 0) st_volatile_u64(look + bid, kFlagPre | (excl + block_agg));
         }
-        s_excl = excl;
-        if (base + kScanTile >= n && total) *total = excl + block_agg;
+        if (lane == 0) {
+            s_excl = (uint32_t)excl;
+            if (base + kScanTile >= n && total) *total = (uint32_t)excl + block_agg;
+        }
     }
     __syncthreads();
     uint32_t run = s_excl + texcl;
@@ -142,7 +153,7 @@ inline int64_t scan_blocks(int64_t n) { return (n + kScanTile - 1) / kScanTile; 
 // Launch a scan over at most n_cap items.  ticket / look must be zero on entry;
 // this launcher clears them on `stream` first.
 template <class Load, class Store>
-cudaError_t launch_scan(Load load, Store store, int64_t n_cap, const uint32_t *n_dev,
+cudaError_t launch_scan(const char *name, Load load, Store store, int64_t n_cap, const uint32_t *n_dev,
                         uint32_t *ticket, unsigned long long *look, uint32_t *total,
                         uint32_t *status, cudaStream_t stream) {
     int64_t nb = scan_blocks(n_cap);
@@ -151,7 +162,7 @@ cudaError_t launch_scan(Load load, Store store, int64_t n_cap, const uint32_t *n
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(look, 0, nb * sizeof(unsigned long long), stream);
     if (e != cudaSuccess) return e;
-    VPGS_LAUNCH("scan_lookback", stream,
+    VPGS_LAUNCH(name, stream,
                 scan_kernel<<<(unsigned)nb, kScanThreads, 0, stream>>>(load, store, n_cap, n_dev,
                                                                        ticket, look, total, status));
     return cudaGetLastError();
@@ -266,26 +277,38 @@ radix_onesweep_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__res
             st_volatile_u32(my, kSFlagPre | c);
         } else {
             st_volatile_u32(my, kSFlagAgg | c);
-            int64_t j = bid - 1;
-            uint32_t acc = 0;
-            while (j >= 0) {
-                const uint32_t *p = look + j * kRadix + tid;
-                uint32_t w = ld_volatile_u32(p);
-                int spins = 0;
-                while ((w >> 30) == 0) {
-                    if (++spins > kSpinLimit) {
-                        set_status(status, VPGS_ERR_TIMEOUT);
-                        break;
-                    }
-                    __nanosleep(32);
-                    w = ld_volatile_u32(p);
+            // kLookDepth independent loads per step shorten the dependent chain
+            constexpr int kLookDepth = 16;
+            int64_t j0 = bid - 1;
+            bool done = false;
+            while (!done) {
+                uint32_t w[kLookDepth];
+#pragma unroll
+                for (int i = 0; i < kLookDepth; ++i) {
+                    const int64_t j = j0 - i;
+                    w[i] = j >= 0 ? ld_volatile_u32(look + j * kRadix + tid) : kSFlagPre;
                 }
-                acc += w & kSValMask;
-                if ((w >> 30) == 2 || spins > kSpinLimit) break;
-                --j;
+#pragma unroll
+                for (int i = 0; i < kLookDepth; ++i) {
+                    if (done) break;
+                    const int64_t j = j0 - i;
+                    uint32_t x = w[i];
+                    int spins = 0;
+                    while ((x >> 30) == 0) {
+                        if (++spins > kSpinLimit) {
+                            set_status(status, VPGS_ERR_TIMEOUT);
+                            x = kSFlagPre;
+                            break;
+                        }
+                        __nanosleep(32);
+                        x = ld_volatile_u32(look + j * kRadix + tid);
+                    }
+                    excl += x & kSValMask;
+                    if ((x >> 30) == 2) done = true;
+                }
+                j0 -= kLookDepth;
             }
-            excl = acc;
-            st_volatile_u32(my, kSFlagPre | (acc + c));
+            st_volatile_u32(my, kSFlagPre | (excl + c));
         }
         // per-warp bases inside the block, offset by everything before it
         uint32_t run = glob_excl + excl;
@@ -333,7 +356,7 @@ inline int64_t sort_blocks(int64_t n) { return (n + kSortTile - 1) / kSortTile; 
 // Sort n (<= n_cap, or *n_dev) pairs from (k0, v0) using (k1, v1) as the other
 // buffer.  Returns in *result_in_1 whether the sorted data ended in buffer 1.
 // scratch: hist [kMaxSortPasses*256], ticket [1], look [sort_blocks(n_cap)*256*passes].
-inline cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
+inline cudaError_t radix_sort_pairs(const char *name, uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
                                     int64_t n_cap, const uint32_t *n_dev, int lo_bit, int bits,
                                     uint32_t *hist, uint32_t *ticket, uint32_t *look,
                                     uint32_t *status, int sms, cudaStream_t stream,
@@ -360,7 +383,7 @@ inline cudaError_t radix_sort_pairs(uint32_t *k0, uint32_t *v0, uint32_t *k1, ui
     if (e != cudaSuccess) return e;
     uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
     for (int p = 0; p < np; ++p) {
-        VPGS_LAUNCH("radix_onesweep", stream,
+        VPGS_LAUNCH(name, stream,
                     radix_onesweep_kernel<<<(unsigned)nb, kSortThreads, 0, stream>>>(
                         ki, vi, ko, vo, n_cap, n_dev, ps[p], hist + p * kRadix, ticket + p,
                         look + (size_t)p * nb * kRadix, status));

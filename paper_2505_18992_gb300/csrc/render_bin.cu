@@ -4,8 +4,8 @@
 //   2. stable radix sort of the visible pairs by the FP32 bit pattern of the
 //      camera depth (positive floats order like their bits); ties keep index
 //      order, i.e. (view, Gaussian) order
-//   3. scan of the tile counts in depth order; the store step of that scan
-//      writes each Gaussian's (global tile id, id) instances at its offset
+//   3. scan of the tile counts in depth order, then a block-cooperative emit
+//      of each Gaussian's (global tile id, id) instances at its offset
 //   4. stable radix sort of the instances by global tile id (only the bits a
 //      tile id needs); instances stay in depth order inside each tile
 //   5. [start, end) of every tile from the sorted keys
@@ -15,6 +15,7 @@
 // over the instances, instead of a 44+ bit (tile, depth) key over all instances.
 #include "internal.h"
 #include "prims.cuh"
+#include "profiler.h"
 
 namespace vpgs {
 
@@ -40,35 +41,65 @@ struct CountLoad {
     __device__ uint32_t operator()(int64_t r) const { return tcount[dval[r]]; }
 };
 
-struct EmitStore {
-    const uint32_t *dval;
-    const uint2 *rect;
-    uint32_t *ikey, *ival;
-    int64_t N, M_cap;
-    int T, tiles_x;
-    uint32_t *status;
-    __device__ void operator()(int64_t r, uint32_t off, uint32_t cnt) const {
-        if (cnt == 0) return;
-        if ((int64_t)off + cnt > M_cap) {
-            set_status(status, VPGS_ERR_CAPACITY);
-            return;
-        }
-        const uint32_t i = dval[r];
-        const uint32_t v = (uint32_t)(i / N);
-        const uint2 rc = rect[i];
-        const uint32_t tx0 = rc.x & 0xffffu, tx1 = rc.x >> 16, ty0 = rc.y & 0xffffu, ty1 = rc.y >> 16;
-        uint32_t o = off;
-        const uint32_t base = v * (uint32_t)T;
-        for (uint32_t ty = ty0; ty <= ty1; ++ty) {
-            const uint32_t row = base + ty * (uint32_t)tiles_x;
-            for (uint32_t tx = tx0; tx <= tx1; ++tx) {
-                ikey[o] = row + tx;
-                ival[o] = i;
-                ++o;
-            }
-        }
-    }
+struct OffsetStore {
+    uint32_t *inst_off;
+    __device__ void operator()(int64_t r, uint32_t off, uint32_t) const { inst_off[r] = off; }
 };
+
+// Emits the (global tile id, record) instances of 256 consecutive depth-ranked
+// Gaussians per block.  The block's instances are spread evenly over its
+// threads; each finds its Gaussian by binary search over the block's local
+// offsets, so a Gaussian covering thousands of tiles does not serialise.
+constexpr int kEmitThreads = 256;
+
+__global__ void __launch_bounds__(kEmitThreads)
+emit_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__ tcount,
+            const uint32_t *__restrict__ inst_off, const uint2 *__restrict__ rect,
+            const uint32_t *n_vis, int64_t N, int64_t M_cap, int T, int tiles_x,
+            uint32_t *__restrict__ ikey, uint32_t *__restrict__ ival, uint32_t *status) {
+    __shared__ uint32_t s_start[kEmitThreads], s_id[kEmitThreads], s_w[kEmitThreads];
+    __shared__ uint32_t s_tx0[kEmitThreads], s_ty0[kEmitThreads], s_vb[kEmitThreads];
+    __shared__ uint32_t s_total;
+    const int64_t nv = *n_vis;
+    const int64_t r0 = (int64_t)blockIdx.x * kEmitThreads;
+    if (r0 >= nv) return;
+    const int tid = threadIdx.x;
+    const int nb = (int)min((int64_t)kEmitThreads, nv - r0);
+    const uint32_t base = inst_off[r0];
+    if (tid < nb) {
+        const int64_t r = r0 + tid;
+        const uint32_t id = dval[r];
+        const uint32_t cnt = tcount[id];
+        const uint32_t off = inst_off[r] - base;
+        const uint2 rc = rect[id];
+        s_start[tid] = off;
+        s_id[tid] = id;
+        s_tx0[tid] = rc.x & 0xffffu;
+        s_w[tid] = (rc.x >> 16) - (rc.x & 0xffffu) + 1u;
+        s_ty0[tid] = rc.y & 0xffffu;
+        s_vb[tid] = (uint32_t)(id / N) * (uint32_t)T;
+        if (tid == nb - 1) s_total = off + cnt;
+    }
+    __syncthreads();
+    const uint32_t total = s_total;
+    if ((int64_t)base + total > M_cap) {
+        if (tid == 0) set_status(status, VPGS_ERR_CAPACITY);
+        return;
+    }
+    for (uint32_t e = tid; e < total; e += kEmitThreads) {
+        int lo = 0, hi = nb - 1;  // last Gaussian whose local start is <= e
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_start[mid] <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        const uint32_t local = e - s_start[lo];
+        const uint32_t w = s_w[lo];
+        const uint32_t ty = s_ty0[lo] + local / w, tx = s_tx0[lo] + local % w;
+        ikey[base + e] = s_vb[lo] + ty * (uint32_t)tiles_x + tx;
+        ival[base + e] = s_id[lo];
+    }
+}
 
 __global__ void tile_ranges_kernel(const uint32_t *__restrict__ keys, int64_t cap, const uint32_t *n_dev,
                                    uint32_t n_tiles, uint2 *ranges) {
@@ -100,23 +131,29 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
     uint32_t *n_vis = ws.counters + CNT_VISIBLE;
     uint32_t *n_inst = ws.counters + CNT_INSTANCES;
     // 1. compaction of visible (view, Gaussian) pairs
-    e = launch_scan(VisLoad{ws.tcount}, VisStore{ws.rec, ws.dkey[0], ws.dval[0], L.VN}, L.VN, nullptr,
-                    ws.counters + CNT_TICKET_A, ws.scan_look, n_vis, ws.status, s);
+    e = launch_scan("scan_visible", VisLoad{ws.tcount}, VisStore{ws.rec, ws.dkey[0], ws.dval[0], L.VN},
+                    L.VN, nullptr, ws.counters + CNT_TICKET_A, ws.scan_look, n_vis, ws.status, s);
     if (e != cudaSuccess) return e;
     // 2. depth sort
     bool in1 = false;
-    e = radix_sort_pairs(ws.dkey[0], ws.dval[0], ws.dkey[1], ws.dval[1], L.VN, n_vis, 0, 32,
-                         ws.sort_hist, ws.counters + CNT_TICKET_B, ws.sort_look, ws.status, sms, s,
+    e = radix_sort_pairs("sort_depth_pass", ws.dkey[0], ws.dval[0], ws.dkey[1], ws.dval[1], L.VN, n_vis,
+                         0, 32, ws.sort_hist, ws.counters + CNT_TICKET_B, ws.sort_look, ws.status, sms, s,
                          &in1);
     if (e != cudaSuccess) return e;
     const uint32_t *dval = in1 ? ws.dval[1] : ws.dval[0];
-    // 3. instance offsets and emission
-    EmitStore em{dval, ws.rect, ws.ikey[0], ws.ival[0], L.N, L.M_cap, cam.T, cam.tiles_x, ws.status};
-    e = launch_scan(CountLoad{ws.tcount, dval}, em, L.VN, n_vis, ws.counters + CNT_TICKET_A,
-                    ws.scan_look, n_inst, ws.status, s);
+    uint32_t *inst_off = in1 ? ws.dkey[0] : ws.dkey[1];  // the depth-sort buffer not holding the result
+    // 3. instance offsets, then emission
+    e = launch_scan("scan_offsets", CountLoad{ws.tcount, dval}, OffsetStore{inst_off}, L.VN, n_vis,
+                    ws.counters + CNT_TICKET_A, ws.scan_look, n_inst, ws.status, s);
+    if (e != cudaSuccess) return e;
+    VPGS_LAUNCH("emit_instances", s,
+                emit_kernel<<<(unsigned)std::max<int64_t>((L.VN + kEmitThreads - 1) / kEmitThreads, 1),
+                              kEmitThreads, 0, s>>>(dval, ws.tcount, inst_off, ws.rect, n_vis, L.N, L.M_cap,
+                                                    cam.T, cam.tiles_x, ws.ikey[0], ws.ival[0], ws.status));
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // 4. stable sort by tile id
-    e = radix_sort_pairs(ws.ikey[0], ws.ival[0], ws.ikey[1], ws.ival[1], L.M_cap, n_inst, 0,
+    e = radix_sort_pairs("sort_tile_pass", ws.ikey[0], ws.ival[0], ws.ikey[1], ws.ival[1], L.M_cap, n_inst, 0,
                          L.tile_bits, ws.sort_hist, ws.counters + CNT_TICKET_B, ws.sort_look,
                          ws.status, sms, s, &in1);
     if (e != cudaSuccess) return e;

@@ -35,18 +35,26 @@ VPGS_D TileCoord tile_coord(int t, const CamParams &cam) {
     return c;
 }
 
-__global__ void __launch_bounds__(1024)
+// Each thread owns kPix pixels of its tile column: rows ly and ly + tile_h/kPix.
+constexpr int kPix = 2;
+constexpr int kMaxThreads = 512;
+
+__global__ void __launch_bounds__(kMaxThreads)
 composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ ival,
                      const uint2 *__restrict__ ranges, int n_tiles, CamParams cam, OptParams o,
                      vpgs_images out, const uint32_t *status, uint32_t *work) {
     extern __shared__ float4 smem[];
-    const int B = blockDim.x;
-    float4 *s0 = smem, *s1 = smem + B, *s2 = smem + 2 * B;
+    const int NT = blockDim.x;
+    float4 *s0 = smem, *s1 = smem + NT, *s2 = smem + 2 * NT;
     __shared__ int s_tile;
     if (*status != 0u) return;
     const int tid = threadIdx.x;
+    const int half = cam.tile_h / kPix;
     const int lx = tid % cam.tile_w, ly = tid / cam.tile_w;
-    const float pxl = (float)lx + 0.5f, pyl = (float)ly + 0.5f;
+    const float pxl = (float)lx + 0.5f;
+    float pyl[kPix];
+#pragma unroll
+    for (int q = 0; q < kPix; ++q) pyl[q] = (float)(ly + q * half) + 0.5f;
     int t = blockIdx.x;
     for (;;) {
         if (work) {
@@ -57,16 +65,22 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
         }
         if (t >= n_tiles) return;
         const TileCoord tc = tile_coord(t, cam);
-        const int px = tc.tx * cam.tile_w + lx, py = tc.ty * cam.tile_h + ly;
-        const bool inside = px < cam.W && py < cam.H;
+        const int px = tc.tx * cam.tile_w + lx;
         const float ox = (float)(tc.tx * cam.tile_w), oy = (float)(tc.ty * cam.tile_h);
         const uint2 rg = ranges[t];
         const int start = (int)rg.x, end = (int)rg.y;
-        float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
-        int cnt = 0, last = 0;
-        bool done = !inside;
-        for (int b0 = start; b0 < end; b0 += B) {
-            if (__syncthreads_count(done) == B) break;
+        float T[kPix], C0[kPix], C1[kPix], C2[kPix], D[kPix];
+        int cnt[kPix], last[kPix];
+        bool done[kPix];
+#pragma unroll
+        for (int q = 0; q < kPix; ++q) {
+            T[q] = 1.f; C0[q] = C1[q] = C2[q] = D[q] = 0.f; cnt[q] = 0; last[q] = 0;
+            const int py = tc.ty * cam.tile_h + ly + q * half;
+            done[q] = !(px < cam.W && py < cam.H);
+        }
+        bool all_done = done[0] && done[1];
+        for (int b0 = start; b0 < end; b0 += NT) {
+            if (__syncthreads_count(all_done) == NT) break;
             const int j = b0 + tid;
             if (j < end) {
                 const Rec r = rec[ival[j]];
@@ -75,43 +89,54 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                 s2[tid] = make_float4(r.r2.z, r.r2.w, r.r3.x, 0.f);
             }
             __syncthreads();
-            if (!done) {
-                const int nb = min(B, end - b0);
+            if (!all_done) {
+                const int nb = min(NT, end - b0);
                 for (int k = 0; k < nb; ++k) {
                     const float4 a = s0[k], b = s1[k];
-                    const PairEval e = eval_pair(pxl - a.x, pyl - a.y, a.z, a.w, b.x, b.y, b.z, o.alpha_max);
-                    if (e.alpha < o.alpha_min) continue;
-                    const float nt = T * (1.f - e.alpha);
-                    if (nt < o.t_min) {
-                        done = true;
+#pragma unroll
+                    for (int q = 0; q < kPix; ++q) {
+                        if (done[q]) continue;
+                        const PairEval e = eval_pair(pxl - a.x, pyl[q] - a.y, a.z, a.w, b.x, b.y, b.z, o.alpha_max);
+                        if (e.alpha < o.alpha_min) continue;
+                        const float nt = T[q] * (1.f - e.alpha);
+                        if (nt < o.t_min) {
+                            done[q] = true;
+                            continue;
+                        }
+                        const float w = e.alpha * T[q];
+                        const float4 c = s2[k];
+                        C0[q] = fmaf(w, c.x, C0[q]);
+                        C1[q] = fmaf(w, c.y, C1[q]);
+                        C2[q] = fmaf(w, c.z, C2[q]);
+                        D[q] = fmaf(w, b.w, D[q]);
+                        T[q] = nt;
+                        ++cnt[q];
+                        last[q] = b0 + k - start + 1;
+                    }
+                    if (done[0] && done[1]) {
+                        all_done = true;
                         break;
                     }
-                    const float w = e.alpha * T;
-                    const float4 c = s2[k];
-                    C0 = fmaf(w, c.x, C0);
-                    C1 = fmaf(w, c.y, C1);
-                    C2 = fmaf(w, c.z, C2);
-                    D = fmaf(w, b.w, D);
-                    T = nt;
-                    ++cnt;
-                    last = b0 + k - start + 1;
                 }
             }
         }
-        if (inside) {
-            const int64_t HW = (int64_t)cam.H * cam.W;
+        const int64_t HW = (int64_t)cam.H * cam.W;
+#pragma unroll
+        for (int q = 0; q < kPix; ++q) {
+            const int py = tc.ty * cam.tile_h + ly + q * half;
+            if (!(px < cam.W && py < cam.H)) continue;
             const int64_t pix = (int64_t)tc.v * HW + (int64_t)py * cam.W + px;
             if (out.rgb) {
                 float *rgb = out.rgb + (int64_t)tc.v * 3 * HW + (int64_t)py * cam.W + px;
-                rgb[0] = fmaf(T, o.bg0, C0);
-                rgb[HW] = fmaf(T, o.bg1, C1);
-                rgb[2 * HW] = fmaf(T, o.bg2, C2);
+                rgb[0] = fmaf(T[q], o.bg0, C0[q]);
+                rgb[HW] = fmaf(T[q], o.bg1, C1[q]);
+                rgb[2 * HW] = fmaf(T[q], o.bg2, C2[q]);
             }
-            if (out.depth) out.depth[pix] = D;
-            if (out.alpha) out.alpha[pix] = 1.f - T;
-            out.t_final[pix] = T;
-            if (out.n_contrib) out.n_contrib[pix] = cnt;
-            out.n_iter[pix] = last;
+            if (out.depth) out.depth[pix] = D[q];
+            if (out.alpha) out.alpha[pix] = 1.f - T[q];
+            out.t_final[pix] = T[q];
+            if (out.n_contrib) out.n_contrib[pix] = cnt[q];
+            out.n_iter[pix] = last[q];
         }
         if (!work) return;
         __syncthreads();
@@ -130,18 +155,20 @@ VPGS_D void tr_step(float (&v)[16], int lane) {
     }
 }
 
-// sum v[0..9] over the warp and add the 10 totals to dst[0..9]
-VPGS_D void warp_reduce_add10(float (&v)[16], float *dst, int lane) {
+// sum v[0..9] over the warp; lanes 0,2,..,18 end up holding the totals of slots 0..9
+VPGS_D int warp_reduce10(float (&v)[16], int lane) {
     tr_step<16, 16>(v, lane);
     tr_step<8, 8>(v, lane);
     tr_step<4, 4>(v, lane);
     tr_step<2, 2>(v, lane);
     v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
     const int slot = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-    if (!(lane & 1) && slot < 10 && v[0] != 0.f) atomicAdd(dst + slot, v[0]);
+    return (lane & 1) ? 16 : slot;
 }
 
-__global__ void __launch_bounds__(1024)
+constexpr int kPartStride = 11;  // floats per (warp, Gaussian) partial, padded against bank conflicts
+
+__global__ void __launch_bounds__(kMaxThreads)
 composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ ival,
                      const uint2 *__restrict__ ranges, int n_tiles, CamParams cam, OptParams o,
                      const float *__restrict__ t_final, const int32_t *__restrict__ n_iter,
@@ -149,15 +176,22 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                      const float *__restrict__ dL_dalpha, float *__restrict__ g2d,
                      const uint32_t *status, uint32_t *work) {
     extern __shared__ float4 smem[];
-    const int B = blockDim.x;
-    float4 *s0 = smem, *s1 = smem + B, *s2 = smem + 2 * B;
-    uint32_t *s_id = reinterpret_cast<uint32_t *>(smem + 3 * B);
+    const int NT = blockDim.x;
+    const int NW = NT >> 5;
+    float4 *s0 = smem, *s1 = smem + NT, *s2 = smem + 2 * NT;
+    uint32_t *s_id = reinterpret_cast<uint32_t *>(smem + 3 * NT);
+    float *s_part = reinterpret_cast<float *>(s_id + NT);  // [NW][NT][kPartStride]
     __shared__ int s_tile;
     __shared__ int s_max;
     if (*status != 0u) return;
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int half = cam.tile_h / kPix;
     const int lx = tid % cam.tile_w, ly = tid / cam.tile_w;
-    const float pxl = (float)lx + 0.5f, pyl = (float)ly + 0.5f;
+    const float pxl = (float)lx + 0.5f;
+    float pyl[kPix];
+#pragma unroll
+    for (int q = 0; q < kPix; ++q) pyl[q] = (float)(ly + q * half) + 0.5f;
+    float *my_part = s_part + (size_t)warp * NT * kPartStride;
     int t = blockIdx.x;
     for (;;) {
         if (work) {
@@ -169,35 +203,43 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
         __syncthreads();
         if (t >= n_tiles) return;
         const TileCoord tc = tile_coord(t, cam);
-        const int px = tc.tx * cam.tile_w + lx, py = tc.ty * cam.tile_h + ly;
-        const bool inside = px < cam.W && py < cam.H;
+        const int px = tc.tx * cam.tile_w + lx;
         const float ox = (float)(tc.tx * cam.tile_w), oy = (float)(tc.ty * cam.tile_h);
         const uint2 rg = ranges[t];
         const int start = (int)rg.x;
         const int64_t HW = (int64_t)cam.H * cam.W;
-        const int64_t pix = (int64_t)tc.v * HW + (int64_t)py * cam.W + px;
-        float T = 1.f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gA = 0.f;
-        int last = 0;
-        if (inside) {
-            T = t_final[pix];
-            last = n_iter[pix];
-            if (dL_drgb) {
-                const float *gp = dL_drgb + (int64_t)tc.v * 3 * HW + (int64_t)py * cam.W + px;
-                gC0 = gp[0]; gC1 = gp[HW]; gC2 = gp[2 * HW];
+        float T[kPix], T_fin[kPix], gC0[kPix], gC1[kPix], gC2[kPix], gD[kPix], gA[kPix];
+        float B0[kPix], B1[kPix], B2[kPix], BD[kPix];
+        int last[kPix];
+        int my_max = 0;
+#pragma unroll
+        for (int q = 0; q < kPix; ++q) {
+            T[q] = 1.f; gC0[q] = gC1[q] = gC2[q] = gD[q] = gA[q] = 0.f; last[q] = 0;
+            B0[q] = o.bg0; B1[q] = o.bg1; B2[q] = o.bg2; BD[q] = 0.f;
+            const int py = tc.ty * cam.tile_h + ly + q * half;
+            if (px < cam.W && py < cam.H) {
+                const int64_t pix = (int64_t)tc.v * HW + (int64_t)py * cam.W + px;
+                T[q] = t_final[pix];
+                last[q] = n_iter[pix];
+                if (dL_drgb) {
+                    const float *gp = dL_drgb + (int64_t)tc.v * 3 * HW + (int64_t)py * cam.W + px;
+                    gC0[q] = gp[0]; gC1[q] = gp[HW]; gC2[q] = gp[2 * HW];
+                }
+                if (dL_ddepth) gD[q] = dL_ddepth[pix];
+                if (dL_dalpha) gA[q] = dL_dalpha[pix];
             }
-            if (dL_ddepth) gD = dL_ddepth[pix];
-            if (dL_dalpha) gA = dL_dalpha[pix];
+            T_fin[q] = T[q];
+            my_max = max(my_max, last[q]);
         }
-        const float T_fin = T;
-        float B0 = o.bg0, B1 = o.bg1, B2 = o.bg2, BD = 0.f;
         {
-            int m = __reduce_max_sync(0xffffffffu, (unsigned)last);
+            const int m = (int)__reduce_max_sync(0xffffffffu, (unsigned)my_max);
             if (lane == 0 && m > 0) atomicMax(&s_max, m);
         }
         __syncthreads();
         const int list_end = start + min(s_max, (int)rg.y - start);  // n_iter never exceeds the list
-        for (int b1 = list_end; b1 > start; b1 -= B) {
-            const int b0 = max(start, b1 - B);
+        for (int b1 = list_end; b1 > start; b1 -= NT) {
+            const int b0 = max(start, b1 - NT);
+            const int nb = b1 - b0;
             __syncthreads();
             const int j = b0 + tid;
             if (j < b1) {
@@ -208,46 +250,61 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                 s2[tid] = make_float4(r.r2.z, r.r2.w, r.r3.x, 0.f);
                 s_id[tid] = id;
             }
+            for (int e = lane; e < nb * kPartStride; e += 32) my_part[e] = 0.f;
             __syncthreads();
-            for (int k = b1 - b0 - 1; k >= 0; --k) {
+            for (int k = nb - 1; k >= 0; --k) {
                 const int jj = b0 + k - start;
                 float v[16];
 #pragma unroll
                 for (int q = 0; q < 16; ++q) v[q] = 0.f;
-                bool act = jj < last;
-                if (act) {
-                    const float4 a = s0[k], b = s1[k];
-                    const float dx = pxl - a.x, dy = pyl - a.y;
+                bool act_any = false;
+                const float4 a = s0[k], b = s1[k];
+#pragma unroll
+                for (int q = 0; q < kPix; ++q) {
+                    if (jj >= last[q]) continue;
+                    const float dx = pxl - a.x, dy = pyl[q] - a.y;
                     const PairEval e = eval_pair(dx, dy, a.z, a.w, b.x, b.y, b.z, o.alpha_max);
-                    if (e.alpha < o.alpha_min) {
-                        act = false;
-                    } else {
-                        const float4 c = s2[k];
-                        const float om = 1.f - e.alpha;
-                        T = T / om;
-                        const float w = e.alpha * T;
-                        v[6] = w * gC0;
-                        v[7] = w * gC1;
-                        v[8] = w * gC2;
-                        v[9] = w * gD;
-                        const float dA = (gC0 * (c.x - B0) + gC1 * (c.y - B1) + gC2 * (c.z - B2) +
-                                          gD * (b.w - BD)) * T + gA * T_fin / om;
-                        B0 = fmaf(e.alpha, c.x, om * B0);
-                        B1 = fmaf(e.alpha, c.y, om * B1);
-                        B2 = fmaf(e.alpha, c.z, om * B2);
-                        BD = fmaf(e.alpha, b.w, om * BD);
-                        if (b.z * e.G <= o.alpha_max) {
-                            const float dpow = dA * e.alpha;
-                            v[5] = dA * e.G;
-                            v[0] = dpow * (a.z * e.t1 + b.x * e.t2);
-                            v[1] = dpow * (a.w * e.t1 + b.y * e.t2);
-                            v[2] = -0.5f * dpow * dx * dx;
-                            v[3] = -dpow * dx * dy;
-                            v[4] = -0.5f * dpow * dy * dy;
-                        }
+                    if (e.alpha < o.alpha_min) continue;
+                    act_any = true;
+                    const float4 c = s2[k];
+                    const float om = 1.f - e.alpha;
+                    T[q] = T[q] / om;
+                    const float w = e.alpha * T[q];
+                    v[6] = fmaf(w, gC0[q], v[6]);
+                    v[7] = fmaf(w, gC1[q], v[7]);
+                    v[8] = fmaf(w, gC2[q], v[8]);
+                    v[9] = fmaf(w, gD[q], v[9]);
+                    const float dA = (gC0[q] * (c.x - B0[q]) + gC1[q] * (c.y - B1[q]) + gC2[q] * (c.z - B2[q]) +
+                                      gD[q] * (b.w - BD[q])) * T[q] + gA[q] * T_fin[q] / om;
+                    B0[q] = fmaf(e.alpha, c.x, om * B0[q]);
+                    B1[q] = fmaf(e.alpha, c.y, om * B1[q]);
+                    B2[q] = fmaf(e.alpha, c.z, om * B2[q]);
+                    BD[q] = fmaf(e.alpha, b.w, om * BD[q]);
+                    if (b.z * e.G <= o.alpha_max) {
+                        const float dpow = dA * e.alpha;
+                        v[5] = fmaf(dA, e.G, v[5]);
+                        v[0] = fmaf(dpow, a.z * e.t1 + b.x * e.t2, v[0]);
+                        v[1] = fmaf(dpow, a.w * e.t1 + b.y * e.t2, v[1]);
+                        v[2] = fmaf(-0.5f * dpow, dx * dx, v[2]);
+                        v[3] = fmaf(-dpow, dx * dy, v[3]);
+                        v[4] = fmaf(-0.5f * dpow, dy * dy, v[4]);
                     }
                 }
-                if (__any_sync(0xffffffffu, act)) warp_reduce_add10(v, g2d + 10 * (int64_t)s_id[k], lane);
+                if (__any_sync(0xffffffffu, act_any)) {
+                    const int slot = warp_reduce10(v, lane);
+                    if (slot < 10) my_part[k * kPartStride + slot] = v[0];
+                }
+            }
+            __syncthreads();
+            // one thread per Gaussian of the batch: sum the warps, one atomic per value
+            for (int k = tid; k < nb; k += NT) {
+                float *dst = g2d + 10 * (int64_t)s_id[k];
+#pragma unroll
+                for (int slot = 0; slot < 10; ++slot) {
+                    float acc = 0.f;
+                    for (int w = 0; w < NW; ++w) acc += s_part[((size_t)w * NT + k) * kPartStride + slot];
+                    if (acc != 0.f) atomicAdd(dst + slot, acc);
+                }
             }
         }
         if (!work) return;
@@ -255,7 +312,10 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
     }
 }
 
-static size_t comp_smem(int B, bool bwd) { return sizeof(float4) * 3 * B + (bwd ? sizeof(uint32_t) * B : 0); }
+static size_t comp_smem(int NT, bool bwd) {
+    return sizeof(float4) * 3 * NT +
+           (bwd ? sizeof(uint32_t) * NT + sizeof(float) * (size_t)(NT / 32) * NT * kPartStride : 0);
+}
 
 static int persistent_grid(const void *kernel, int B, size_t smem, int per_sm, int n_tiles) {
     int occ = 0;
@@ -268,7 +328,7 @@ static int persistent_grid(const void *kernel, int B, size_t smem, int per_sm, i
 cudaError_t launch_composite_fwd(const RenderWs &ws, const uint32_t *ival, int V,
                                  const CamParams &cam, const OptParams &o, const vpgs_images &out,
                                  int persistent_ctas, cudaStream_t s) {
-    const int B = cam.tile_w * cam.tile_h;
+    const int B = cam.tile_w * cam.tile_h / kPix;
     const int n_tiles = V * cam.T;
     const size_t sm = comp_smem(B, false);
     uint32_t *work = nullptr;
@@ -293,7 +353,7 @@ cudaError_t launch_composite_bwd(const RenderWs &ws, const uint32_t *ival, int V
                                  const CamParams &cam, const OptParams &o, const vpgs_images &fwd,
                                  const float *dL_drgb, const float *dL_ddepth,
                                  const float *dL_dalpha, int persistent_ctas, cudaStream_t s) {
-    const int B = cam.tile_w * cam.tile_h;
+    const int B = cam.tile_w * cam.tile_h / kPix;
     const int n_tiles = V * cam.T;
     const size_t sm = comp_smem(B, true);
     uint32_t *work = nullptr;

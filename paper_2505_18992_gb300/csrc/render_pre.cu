@@ -73,6 +73,11 @@ VPGS_D void project(const PoseDF &P, float mx, float my, float mz, float sx, flo
     p.det = (c0 * c0 + c1 * c1 + c2 * c2) + dil * (n0 + n1) + dil * dil;
 }
 
+__global__ void pose_prepare_kernel(const double *__restrict__ T_cw, int V, float *posedf) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < V) pose_to_df(T_cw + 16 * v, posedf + 24 * v);
+}
+
 __global__ void __launch_bounds__(256)
 preprocess_fwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamParams cam, OptParams o,
                       RenderWs ws, bool zero_g2d) {
@@ -97,9 +102,8 @@ preprocess_fwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamPara
             set_status(ws.status, VPGS_ERR_NONFINITE);
         } else if (op >= o.alpha_min) {
             PoseDF P;
-            load_pose(T_cw + 16 * v, P);
+            load_pose(ws.posedf + 24 * v, P);
             Proj p;
-            // near test first (cheap): z from the double-float transform
             project(P, mx, my, mz, sx, sy, sz, q.x, q.y, q.z, q.w, cam, o.dilation, p);
             const bool in_front = p.pc[2].hi > o.near_z || (p.pc[2].hi == o.near_z && p.pc[2].lo > 0.f);
             if (in_front) {
@@ -199,7 +203,7 @@ preprocess_bwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamPara
             gc[0] += a67.x; gc[1] += a67.y; gc[2] += a89.x;
             const float gz = a89.y;
             PoseDF P;
-            load_pose(T_cw + 16 * v, P);
+            load_pose(ws.posedf + 24 * v, P);
             Proj p;
             project(P, mx, my, mz, sx, sy, sz, q.x, q.y, q.z, q.w, cam, o.dilation, p);
             // conic M = Sigma'^-1 and G_Sigma' = -M G M, G = [[ga, gb/2], [gb/2, gc]]
@@ -361,7 +365,8 @@ cudaError_t launch_preprocess_fwd(const GaussIn &g, const double *T_cw, int V, c
                                   const OptParams &o, const RenderWs &ws, bool zero_g2d,
                                   cudaStream_t s) {
     const int64_t VN = (int64_t)V * g.N;
-    if (VN == 0) return cudaSuccess;
+    VPGS_LAUNCH("pose_prepare", s, pose_prepare_kernel<<<(V + 63) / 64, 64, 0, s>>>(T_cw, V, ws.posedf));
+    if (VN == 0) return cudaGetLastError();
     VPGS_LAUNCH("preprocess_fwd", s,
                 preprocess_fwd_kernel<<<(unsigned)((VN + 255) / 256), 256, 0, s>>>(g, T_cw, V, cam, o,
                                                                                     ws, zero_g2d));
