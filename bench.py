@@ -49,6 +49,7 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip tracking/e2e/profile passes")
     p.add_argument("--persistent", type=int, default=0, help="persistent CTAs per SM (0 = per tile)")
+    p.add_argument("--tile", default="16x16", help="tile shape WxH")
     p.add_argument("--scale", type=float, default=1.0,
                    help="shrink the workload for profiling: N x scale^2 Gaussians, image x scale")
     return p.parse_args()
@@ -195,6 +196,20 @@ def algorithmic_bytes(kernel: str, N: int, Nv: int, M: int, P: int):
     return table.get(kernel)
 
 
+# FP32 flops (FMA = 2) of one pixel-Gaussian pair, counted from the method's
+# arithmetic: evaluating alpha (offset 2, whitened form 6, power 4, exp 2,
+# opacity 1, clamp 1 = 17) and, for blended pairs, the blend (forward: 1 - alpha,
+# T update, weight, 4 accumulations = 11) or the gradient (backward: T recovery 4,
+# weight 1, colour/depth grads 8, dalpha 18, behind-colour update 12, opacity
+# and power 3, mean 8, conic 9 = 63).
+PAIR_FLOPS = {"eval": 17, "blend_fwd": 11, "blend_bwd": 63}
+
+
+def alu_peak_tflops(sm_mhz):
+    """FP32 FMA peak: 152 SMs x 128 lanes x 2 flops x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
 def _sha(paths):
     h = hashlib.sha256()
     for p in paths:
@@ -259,8 +274,9 @@ def run_ours(a):
     P = V * H * W
     g = [torch.tensor(x, device=dev).contiguous() for x in sc.arrays()]
     T = torch.tensor(cam.T_cw, dtype=torch.float64, device=dev).contiguous()
+    tw, th = (int(x) for x in a.tile.lower().split("x"))
     r = Renderer(Intrinsics(W, H, cam.fx, cam.fy, cam.cx, cam.cy), device=dev,
-                 persistent_ctas=a.persistent)
+                 persistent_ctas=a.persistent, tile_w=tw, tile_h=th)
     rng = np.random.default_rng(5)
     g_rgb = torch.tensor(np.sign(rng.normal(size=(1, 3, H, W))) / (3 * P), dtype=torch.float32, device=dev)
     g_d = torch.tensor(np.sign(rng.normal(size=(1, H, W))) / P, dtype=torch.float32, device=dev)
@@ -323,7 +339,8 @@ def run_ours(a):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD if a.scale == 1.0 else f"room scaled x{a.scale}",
                        "n_gaussians": sc.n, "width": W, "height": H,
-                       "visible": Nv, "instances": M, "tile": "16x16",
+                       "visible": Nv, "instances": M, "tile": a.tile,
+                       "persistent_ctas_per_sm": a.persistent,
                        "l2": "256 MiB buffer written between timed steps (inputs 56 MB < L2)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "ms_p50": statistics.median(ms), "ms_min": min(ms)},
@@ -344,7 +361,30 @@ def run_ours(a):
         top = max(kern, key=lambda k: kern[k]["ms_total"])
         peak, peak_src = _peaks()
         ab = algorithmic_bytes(top, sc.n, Nv, M, P)
-        if ab is not None:
+        pairs_eval = int(out["n_iter"].to(torch.int64).sum())
+        pairs_blend = int(out["n_contrib"].to(torch.int64).sum())
+        # tile-level SIMD waste: a tile walks its list as far as its slowest pixel
+        ni = out["n_iter"][0].to(torch.float32)
+        ph, pw = (-H) % th, (-W) % tw
+        nip = torch.nn.functional.pad(ni, (0, pw, 0, ph))
+        tmax = torch.nn.functional.max_pool2d(nip[None, None], (th, tw))[0, 0]
+        line["config"]["pairs_useful"] = pairs_eval
+        line["config"]["pairs_tile_walk"] = int(tmax.sum().item()) * tw * th
+        if top in ("composite_fwd", "composite_bwd"):
+            blend = PAIR_FLOPS["blend_fwd" if top == "composite_fwd" else "blend_bwd"]
+            flops = pairs_eval * PAIR_FLOPS["eval"] + pairs_blend * blend
+            mhz = (line.get("clocks") or {}).get("sm_mhz") or 2070.0
+            pk = alu_peak_tflops(mhz)
+            ach = flops / (kern[top]["ms_avg"] * 1e-3) / 1e12
+            line["roofline"] = {"kernel": top, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                                "frac": ach / pk, "traffic": ncu_traffic(top),
+                                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz",
+                                "algorithmic_flops": flops, "pairs_evaluated": pairs_eval,
+                                "pairs_blended": pairs_blend,
+                                "hbm": {"algorithmic_bytes": ab,
+                                        "achieved_gbs": ab / (kern[top]["ms_avg"] * 1e-3) / 1e9 if ab else None,
+                                        "peak_gbs": peak, "peak_source": peak_src}}
+        elif ab is not None:
             achieved = ab / (kern[top]["ms_avg"] * 1e-3) / 1e9
             line["roofline"] = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peak,
                                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
@@ -381,16 +421,97 @@ def run_ours(a):
         line["e2e"] = {"value": P * world / (e_ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": e_ms,
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
         # coarse tracking: 50 pose-only iterations, eager vs one captured CUDA graph
-        try:
-            line["tracking"] = tracking_rows(sc, g, dev)
-        except Exception as exc:  # reported, not fatal
-            line["tracking"] = {"error": repr(exc)[:200]}
+        for key, fn in (("tracking", lambda: tracking_rows(sc, g, dev)), ("decode", lambda: decode_rows(dev)),
+                        ("batched_keyframes", lambda: batched_rows(dev))):
+            try:
+                line[key] = fn()
+            except Exception as exc:  # reported, not fatal
+                line[key] = {"error": repr(exc)[:300]}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(sc, a.cpu_rows)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def _time_ms(fn, reps=20):
+    import torch
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def decode_rows(dev):
+    """Anchor decode of 100,000 street anchors: FP32 FMA vs BF16 tensor cores, fwd and bwd."""
+    import torch
+
+    from paper_2505_18992_gb300 import scenes
+    from paper_2505_18992_gb300.decode import Decoder
+    sc = scenes.street_anchors()
+    t = lambda a, dt=torch.float32: torch.tensor(a, dtype=dt, device=dev).contiguous()  # noqa: E731
+    anchors, feats, scal, offs = t(sc.anchors), t(sc.features), t(sc.scaling), t(sc.offsets)
+    params = t(np.concatenate([np.asarray(p, np.float32).reshape(-1)
+                               for name in ("opacity", "color", "cov") for p in sc.mlp[name]]))
+    T = t(sc.camera.T_cw[0], torch.float64)
+    res = {"anchors": sc.n, "k": sc.k}
+    for name, bf in (("fp32", False), ("bf16", True)):
+        d = Decoder(sc.k, bf16=bf, device=dev)
+        out = d.forward(anchors, feats, scal, offs, params, sc.camera, T)
+        grads = {k: torch.ones_like(out[k]) for k in ("means", "scales", "quats", "opacities", "colors")}
+        fwd_ms = _time_ms(lambda: d.forward(anchors, feats, scal, offs, params, sc.camera, T))
+        bwd_ms = _time_ms(lambda: d.backward(anchors, feats, scal, offs, params, sc.camera, T, out, grads))
+        res[name] = {"fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "gaussians_out": out["n"],
+                     "anchors_per_s_fwd": sc.n / (fwd_ms * 1e-3)}
+    return res
+
+
+def batched_rows(dev, steps=10):
+    """8 keyframes of a 2M-Gaussian submap: one 8-view call vs 8 one-view calls (fwd+bwd)."""
+    import torch
+
+    from paper_2505_18992_gb300 import scenes
+    from paper_2505_18992_gb300.render import Intrinsics, Renderer
+    sc = scenes.batched_keyframes()
+    cam = sc.camera
+    g = [torch.tensor(x, device=dev).contiguous() for x in sc.arrays()]
+    T = torch.tensor(cam.T_cw, dtype=torch.float64, device=dev).contiguous()
+    V, H, W = cam.n_views, cam.height, cam.width
+    intr = Intrinsics(W, H, cam.fx, cam.fy, cam.cx, cam.cy)
+    grads = {k: torch.zeros_like(x) for k, x in zip(("means", "scales", "quats", "opacities", "colors"), g)}
+    rb = Renderer(intr, n_views=V, device=dev)
+    outb = rb.forward(*g, T, check=True)
+    gb = torch.full((V, 3, H, W), 1.0 / (3 * H * W), device=dev)
+    dpb = torch.zeros((V, 6), dtype=torch.float64, device=dev)
+
+    def batched():
+        rb.forward(*g, T, out=outb, check=False)
+        rb.backward(*g, T, outb, gb, None, None, grads=grads, dpose=dpb)
+
+    r1 = Renderer(intr, n_views=1, device=dev)
+    Ts = [T[v:v + 1].contiguous() for v in range(V)]
+    outs = [r1.forward(*g, Tv, check=True) for Tv in Ts]
+    g1 = gb[:1].contiguous()
+    dp1 = torch.zeros((1, 6), dtype=torch.float64, device=dev)
+
+    def separate():
+        for Tv, o in zip(Ts, outs):
+            r1.forward(*g, Tv, out=o, check=False)
+            r1.backward(*g, Tv, o, g1, None, None, grads=grads, dpose=dp1)
+
+    mb = _time_ms(batched, steps)
+    ms = _time_ms(separate, steps)
+    px = V * H * W
+    return {"views": V, "gaussians": sc.n, "width": W, "height": H,
+            "batched_ms": mb, "separate_ms": ms, "batched_mpix_s": px / (mb * 1e-3) / 1e6,
+            "separate_mpix_s": px / (ms * 1e-3) / 1e6}
 
 
 def tracking_rows(sc, g, dev):

@@ -69,7 +69,7 @@ typedef struct {
  * The paper cites 3D Gaussian Splatting for all of these (Sec. I, Sec. II) and
  * states none of them. */
 typedef struct {
-    int32_t tile_w, tile_h;   /* tile_w * tile_h threads per tile; each in [4, 32], product <= 1024 */
+    int32_t tile_w, tile_h;   /* tile_w in {4,8,16,32}; tile_h even; tile_w*tile_h a multiple of 64, <= 1024 */
     float alpha_min;          /* skip a Gaussian at a pixel when alpha < alpha_min */
     float alpha_max;          /* alpha = min(alpha_max, o exp(-d^T Sigma'^-1 d / 2)) */
     float t_min;              /* stop before the first Gaussian that would take T below t_min */

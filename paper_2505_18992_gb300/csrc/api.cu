@@ -19,7 +19,9 @@ inline int bits_for(int64_t max_value) {
 
 bool valid_opts(const vpgs_render_opts *o) {
     if (!o) return false;
-    if (o->tile_w < 4 || o->tile_w > 32 || o->tile_h < 1 || o->tile_h > 32) return false;
+    // a warp covers whole rows of a tile: tile_w divides 32
+    if (o->tile_w != 4 && o->tile_w != 8 && o->tile_w != 16 && o->tile_w != 32) return false;
+    if (o->tile_h < 2 || o->tile_h > 64) return false;
     // two pixels per thread (rows y and y + tile_h/2): tile_h even, whole warps
     const int B = o->tile_w * o->tile_h;
     if (o->tile_h % 2 != 0 || B % 64 != 0 || B > 1024) return false;
@@ -71,7 +73,8 @@ bool make_layout(int64_t N, int V, const vpgs_camera *cam, const vpgs_render_opt
     L.off_ival1 = take(4 * L.M_cap);
     L.off_ranges = take(sizeof(uint2) * (size_t)V * L.T);
     L.off_sort_hist = take(4 * kRadix * 4);
-    const int64_t look_a = 4 * sort_blocks(VN1), look_b = (int64_t)np_tile * sort_blocks(L.M_cap);
+    const int64_t look_a = 4 * sort_blocks(VN1, kDepthSortItems);
+    const int64_t look_b = (int64_t)np_tile * sort_blocks(L.M_cap, kTileSortItems);
     L.sort_blocks_max = look_a > look_b ? look_a : look_b;
     L.off_sort_look = take(4 * kRadix * (size_t)L.sort_blocks_max);
     L.scan_blocks_max = scan_blocks(VN1);

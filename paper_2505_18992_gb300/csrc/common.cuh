@@ -128,7 +128,8 @@ VPGS_D void quat_to_rot(float w, float x, float y, float z, float R[9]) {
 //   r0 = (u_hi, v_hi, u_lo, v_lo)   image mean as a double-float pair
 //   r1 = (w1x, w1y, w2x, w2y)       whitening rows: d^T Sigma'^-1 d = (w1.d)^2 + (w2.d)^2
 //   r2 = (opacity, z, r, g)
-//   r3 = (b, -, -, -)
+//   r3 = (b, rx, ry, -)             conservative pixel half-extents (alpha >= alpha_min
+//                                   is impossible farther than this from the mean)
 // The whitening rows are the eigenvectors of Sigma' scaled by 1/sqrt(lambda),
 // which evaluates the quadratic form without the cancellation the
 // (a dx^2 + 2 b dx dy + c dy^2) form suffers on elongated Gaussians.
@@ -199,8 +200,8 @@ struct RenderWs {
 
 // radix sort geometry
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;                     // per thread
-constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per block
+constexpr int kDepthSortItems = 4;  // keys per thread in the depth sort (1024 per block)
+constexpr int kTileSortItems = 16;  // keys per thread in the tile-id sort (4096 per block)
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kMaxSortPasses = 8;

@@ -205,6 +205,7 @@ constexpr uint32_t kSFlagAgg = 1u << 30;
 constexpr uint32_t kSFlagPre = 2u << 30;
 constexpr uint32_t kSValMask = (1u << 30) - 1u;
 
+template <int ITEMS>
 static __global__ void __launch_bounds__(kSortThreads)
 radix_onesweep_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__restrict__ val_in,
                       uint32_t *__restrict__ key_out, uint32_t *__restrict__ val_out,
@@ -212,7 +213,7 @@ radix_onesweep_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__res
                       const uint32_t *__restrict__ pass_hist, uint32_t *ticket, uint32_t *look,
                       uint32_t *status) {
     constexpr int kWarps = kSortThreads / kWarp;
-    constexpr int kSeg = kWarp * kSortItems;  // contiguous items per warp
+    constexpr int kSeg = kWarp * ITEMS;  // contiguous items per warp
     __shared__ uint32_t s_cnt[kWarps][kRadix];
     __shared__ uint32_t s_glob[kRadix];
     __shared__ uint32_t s_bid;
@@ -223,7 +224,7 @@ radix_onesweep_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__res
     const int64_t bid = s_bid;
     int64_t n = n_cap;
     if (n_dev) n = min(n, (int64_t)*n_dev);
-    const int64_t base = bid * kSortTile;
+    const int64_t base = bid * (int64_t)(kSortThreads * ITEMS);
     if (base >= n) return;
     const uint32_t mask = (1u << pass.bits) - 1u;
 
@@ -248,10 +249,10 @@ radix_onesweep_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__res
     }
 
     // load this warp's contiguous segment, 32 consecutive keys per step
-    uint32_t k[kSortItems], v[kSortItems], d[kSortItems];
+    uint32_t k[ITEMS], v[ITEMS], d[ITEMS];
     const int64_t seg = base + (int64_t)warp * kSeg;
 #pragma unroll
-    for (int s = 0; s < kSortItems; ++s) {
+    for (int s = 0; s < ITEMS; ++s) {
         int64_t i = seg + s * kWarp + lane;
         bool ok = i < n;
         k[s] = ok ? key_in[i] : 0u;
@@ -260,7 +261,7 @@ radix_onesweep_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__res
     }
     // per-warp digit counts
 #pragma unroll
-    for (int s = 0; s < kSortItems; ++s) {
+    for (int s = 0; s < ITEMS; ++s) {
         uint32_t m = __match_any_sync(0xffffffffu, d[s]);
         if (d[s] < kRadix && (m & lanemask_lt()) == 0) s_cnt[warp][d[s]] += __popc(m);
         __syncwarp();
@@ -322,7 +323,7 @@ radix_onesweep_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__res
     __syncthreads();
     // stable scatter: order inside a step by lane, steps in order, warps in order
 #pragma unroll
-    for (int s = 0; s < kSortItems; ++s) {
+    for (int s = 0; s < ITEMS; ++s) {
         uint32_t m = __match_any_sync(0xffffffffu, d[s]);
         uint32_t rank = __popc(m & lanemask_lt());
         if (d[s] < kRadix) {
@@ -351,7 +352,10 @@ inline int plan_passes(int lo, int bits, SortPass *out) {
     return np;
 }
 
-inline int64_t sort_blocks(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
+inline int64_t sort_blocks(int64_t n, int items) {
+    const int64_t tile = (int64_t)kSortThreads * items;
+    return (n + tile - 1) / tile;
+}
 
 // Sort n (<= n_cap, or *n_dev) pairs from (k0, v0) using (k1, v1) as the other
 // buffer.  Returns in *result_in_1 whether the sorted data ended in buffer 1.
@@ -360,13 +364,14 @@ inline cudaError_t radix_sort_pairs(const char *name, uint32_t *k0, uint32_t *v0
                                     int64_t n_cap, const uint32_t *n_dev, int lo_bit, int bits,
                                     uint32_t *hist, uint32_t *ticket, uint32_t *look,
                                     uint32_t *status, int sms, cudaStream_t stream,
-                                    bool *result_in_1) {
+                                    bool *result_in_1, int items = 16) {
     SortPass ps[kMaxSortPasses];
     int np = plan_passes(lo_bit, bits, ps);
     *result_in_1 = (np & 1) != 0;
     if (np == 0 || n_cap == 0) return cudaSuccess;
     if (np > 4) return cudaErrorInvalidValue;
-    int64_t nb = sort_blocks(n_cap);
+    if (items != 4 && items != 8 && items != 16) return cudaErrorInvalidValue;
+    int64_t nb = sort_blocks(n_cap, items);
     cudaError_t e = cudaMemsetAsync(hist, 0, np * kRadix * sizeof(uint32_t), stream);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(look, 0, (size_t)np * nb * kRadix * sizeof(uint32_t), stream);
@@ -383,10 +388,16 @@ inline cudaError_t radix_sort_pairs(const char *name, uint32_t *k0, uint32_t *v0
     if (e != cudaSuccess) return e;
     uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
     for (int p = 0; p < np; ++p) {
-        VPGS_LAUNCH(name, stream,
-                    radix_onesweep_kernel<<<(unsigned)nb, kSortThreads, 0, stream>>>(
-                        ki, vi, ko, vo, n_cap, n_dev, ps[p], hist + p * kRadix, ticket + p,
-                        look + (size_t)p * nb * kRadix, status));
+        uint32_t *lk = look + (size_t)p * nb * kRadix;
+        if (items == 4)
+            VPGS_LAUNCH(name, stream, radix_onesweep_kernel<4><<<(unsigned)nb, kSortThreads, 0, stream>>>(
+                                          ki, vi, ko, vo, n_cap, n_dev, ps[p], hist + p * kRadix, ticket + p, lk, status));
+        else if (items == 8)
+            VPGS_LAUNCH(name, stream, radix_onesweep_kernel<8><<<(unsigned)nb, kSortThreads, 0, stream>>>(
+                                          ki, vi, ko, vo, n_cap, n_dev, ps[p], hist + p * kRadix, ticket + p, lk, status));
+        else
+            VPGS_LAUNCH(name, stream, radix_onesweep_kernel<16><<<(unsigned)nb, kSortThreads, 0, stream>>>(
+                                          ki, vi, ko, vo, n_cap, n_dev, ps[p], hist + p * kRadix, ticket + p, lk, status));
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         uint32_t *tk = ki, *tv = vi;

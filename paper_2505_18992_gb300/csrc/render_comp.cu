@@ -231,10 +231,9 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
             T_fin[q] = T[q];
             my_max = max(my_max, last[q]);
         }
-        {
-            const int m = (int)__reduce_max_sync(0xffffffffu, (unsigned)my_max);
-            if (lane == 0 && m > 0) atomicMax(&s_max, m);
-        }
+        // the warp's own list length: warps whose pixels stop early skip the tail
+        const int warp_max = (int)__reduce_max_sync(0xffffffffu, (unsigned)my_max);
+        if (lane == 0 && warp_max > 0) atomicMax(&s_max, warp_max);
         __syncthreads();
         const int list_end = start + min(s_max, (int)rg.y - start);  // n_iter never exceeds the list
         for (int b1 = list_end; b1 > start; b1 -= NT) {
@@ -252,7 +251,8 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
             }
             for (int e = lane; e < nb * kPartStride; e += 32) my_part[e] = 0.f;
             __syncthreads();
-            for (int k = nb - 1; k >= 0; --k) {
+            const int k_end = min(nb, warp_max - (b0 - start));  // warp-uniform
+            for (int k = k_end - 1; k >= 0; --k) {
                 const int jj = b0 + k - start;
                 float v[16];
 #pragma unroll
