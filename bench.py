@@ -48,6 +48,7 @@ def _args():
     p.add_argument("--cpu-rows", type=int, default=8, help="image rows in the CPU oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip tracking/e2e/profile passes")
+    p.add_argument("--no-rows", action="store_true", help="keep the kernel profile, skip the other rows")
     p.add_argument("--persistent", type=int, default=0, help="persistent CTAs per SM (0 = per tile)")
     p.add_argument("--tile", default="16x16", help="tile shape WxH")
     p.add_argument("--scale", type=float, default=1.0,
@@ -395,6 +396,7 @@ def run_ours(a):
         line["kernels"] = {k: {"launches": v["launches"] // min(a.steps, 50), "ms_avg": round(v["ms_avg"], 5),
                                "share": round(v["share"], 4)} for k, v in sorted(kern.items(),
                                                                                   key=lambda kv: -kv[1]["ms_total"])}
+    if not a.no_extras and not a.no_rows:
         # end to end through the public API with host buffers
         pin = lambda t: t.detach().cpu().pin_memory()  # noqa: E731
         h_in = [pin(t) for t in g] + [pin(T), pin(g_rgb), pin(g_d)]

@@ -35,12 +35,17 @@ def _headers():
         glob.glob(os.path.join(ROOT, "include", "*.h"))
 
 
+def _env_flags():
+    """Extra nvcc flags from VPGS_NVCC_FLAGS (e.g. -DVPGS_PIX=2 to retune the compositing geometry)."""
+    return os.environ.get("VPGS_NVCC_FLAGS", "").split()
+
+
 def _compile(src: str, extra) -> str:
     obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
     newest = max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in _headers()])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest and not extra:
         return obj
-    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
+    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *_env_flags(), *extra, "-c", src, "-o", obj]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{res.stderr}")

@@ -11,6 +11,20 @@
 #define VPGS_HD __host__ __device__ __forceinline__
 #define VPGS_D __device__ __forceinline__
 
+// Compositing launch geometry (compile-time tuning knobs):
+//   VPGS_PIX    pixels per thread (rows y and y + tile_h/VPGS_PIX)
+//   VPGS_CHUNK  Gaussians evaluated together before the forward's sequential blend
+//   VPGS_GSTEP  Gaussians per step of the backward loop (1 or 2)
+#ifndef VPGS_PIX
+#define VPGS_PIX 1
+#endif
+#ifndef VPGS_CHUNK
+#define VPGS_CHUNK 1
+#endif
+#ifndef VPGS_GSTEP
+#define VPGS_GSTEP 1
+#endif
+
 namespace vpgs {
 
 constexpr int kWarp = 32;
@@ -128,8 +142,10 @@ VPGS_D void quat_to_rot(float w, float x, float y, float z, float R[9]) {
 //   r0 = (u_hi, v_hi, u_lo, v_lo)   image mean as a double-float pair
 //   r1 = (w1x, w1y, w2x, w2y)       whitening rows: d^T Sigma'^-1 d = (w1.d)^2 + (w2.d)^2
 //   r2 = (opacity, z, r, g)
-//   r3 = (b, rx, ry, -)             conservative pixel half-extents (alpha >= alpha_min
-//                                   is impossible farther than this from the mean)
+//   r3 = (b, rx, ry, kq)            conservative pixel half-extents (alpha >= alpha_min
+//                                   is impossible farther than this from the mean) and
+//                                   kq = 2 ln(o / alpha_min), the largest quadratic form
+//                                   at which alpha >= alpha_min is possible
 // The whitening rows are the eigenvectors of Sigma' scaled by 1/sqrt(lambda),
 // which evaluates the quadratic form without the cancellation the
 // (a dx^2 + 2 b dx dy + c dy^2) form suffers on elongated Gaussians.
@@ -138,19 +154,27 @@ struct __align__(16) Rec {
     float4 r0, r1, r2, r3;
 };
 
-// evaluated per pixel/Gaussian pair, bit-identically in forward and backward
+// evaluated per pixel/Gaussian pair, bit-identically in forward and backward.
+// Pairs whose quadratic form exceeds kq (plus 1e-4, far above the FP32 error
+// of q) have alpha < alpha_min and get alpha = 0 without the exp: the alpha
+// test would reject every one of them, so results are unchanged.
 struct PairEval {
     float t1, t2, G, alpha;
 };
 
 VPGS_D PairEval eval_pair(float dx, float dy, float w1x, float w1y, float w2x, float w2y,
-                          float opac, float alpha_max) {
+                          float opac, float kq, float alpha_max) {
     PairEval e;
     e.t1 = fmaf(w1x, dx, w1y * dy);
     e.t2 = fmaf(w2x, dx, w2y * dy);
-    float power = -0.5f * fmaf(e.t1, e.t1, e.t2 * e.t2);
-    e.G = __expf(power);
-    e.alpha = fminf(alpha_max, opac * e.G);
+    const float q = fmaf(e.t1, e.t1, e.t2 * e.t2);
+    if (q > kq + 1e-4f) {
+        e.G = 0.f;
+        e.alpha = 0.f;
+    } else {
+        e.G = __expf(-0.5f * q);
+        e.alpha = fminf(alpha_max, opac * e.G);
+    }
     return e;
 }
 

@@ -214,8 +214,12 @@ radix_onesweep_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__res
                       uint32_t *status) {
     constexpr int kWarps = kSortThreads / kWarp;
     constexpr int kSeg = kWarp * ITEMS;  // contiguous items per warp
+    constexpr int kTile = kSortThreads * ITEMS;
+    static_assert(kSortThreads == kRadix, "one thread per digit");
     __shared__ uint32_t s_cnt[kWarps][kRadix];
     __shared__ uint32_t s_glob[kRadix];
+    __shared__ uint32_t s_dstart[kRadix], s_gbase[kRadix], s_wsum[kWarps];
+    __shared__ uint32_t s_key[kTile], s_val[kTile];
     __shared__ uint32_t s_bid;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_bid = atomicAdd(ticket, 1u);
@@ -267,11 +271,25 @@ radix_onesweep_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__res
         __syncwarp();
     }
     __syncthreads();
-    // block count per digit, publish, look back
-    if (tid < kRadix) {
-        uint32_t c = 0;
+    // block count per digit and its block-local exclusive start (kRadix == threads)
+    uint32_t c = 0;
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) c += s_cnt[w][tid];
+    for (int w = 0; w < kWarps; ++w) c += s_cnt[w][tid];
+    {
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_wsum[warp] = x;
+        __syncthreads();
+        uint32_t add = 0;
+        for (int w = 0; w < warp; ++w) add += s_wsum[w];
+        s_dstart[tid] = x - c + add;
+    }
+    // publish, look back over earlier blocks
+    {
         uint32_t excl = 0;
         uint32_t *my = look + bid * kRadix + tid;
         if (bid == 0) {
@@ -311,31 +329,43 @@ radix_onesweep_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__res
             }
             st_volatile_u32(my, kSFlagPre | (excl + c));
         }
-        // per-warp bases inside the block, offset by everything before it
-        uint32_t run = glob_excl + excl;
+        s_gbase[tid] = glob_excl + excl;  // global slot of this block's first key with digit tid
+        // per-warp bases inside the block (block-local digit order)
+        uint32_t run = s_dstart[tid];
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) {
-            uint32_t t = s_cnt[w][tid];
+            const uint32_t t = s_cnt[w][tid];
             s_cnt[w][tid] = run;
             run += t;
         }
     }
     __syncthreads();
-    // stable scatter: order inside a step by lane, steps in order, warps in order
+    // stable ranking into shared memory: order inside a step by lane, steps in
+    // order, warps in order
 #pragma unroll
     for (int s = 0; s < ITEMS; ++s) {
-        uint32_t m = __match_any_sync(0xffffffffu, d[s]);
-        uint32_t rank = __popc(m & lanemask_lt());
+        const uint32_t m = __match_any_sync(0xffffffffu, d[s]);
+        const uint32_t rank = __popc(m & lanemask_lt());
         if (d[s] < kRadix) {
-            const uint32_t pos = s_cnt[warp][d[s]] + rank;
-            if ((int64_t)pos < n) {  // always true unless a look-back wait timed out
-                key_out[pos] = k[s];
-                val_out[pos] = v[s];
-            }
+            const uint32_t lp = s_cnt[warp][d[s]] + rank;
+            s_key[lp] = k[s];
+            s_val[lp] = v[s];
         }
         __syncwarp();
         if (d[s] < kRadix && rank == 0) s_cnt[warp][d[s]] += __popc(m);
         __syncwarp();
+    }
+    __syncthreads();
+    // coalesced write-out: consecutive threads write consecutive slots of each digit run
+    const int nb = (int)min((int64_t)kTile, n - base);
+    for (int i = tid; i < nb; i += kSortThreads) {
+        const uint32_t key = s_key[i];
+        const uint32_t dg = (key >> pass.shift) & mask;
+        const uint32_t pos = s_gbase[dg] + ((uint32_t)i - s_dstart[dg]);
+        if ((int64_t)pos < n) {  // always true unless a look-back wait timed out
+            key_out[pos] = key;
+            val_out[pos] = s_val[i];
+        }
     }
 }
 

@@ -36,7 +36,9 @@ VPGS_D TileCoord tile_coord(int t, const CamParams &cam) {
 }
 
 // Each thread owns kPix pixels of its tile column: rows ly and ly + tile_h/kPix.
-constexpr int kPix = 2;
+constexpr int kPix = VPGS_PIX;
+constexpr int kChunk = VPGS_CHUNK;  // Gaussians evaluated together before the sequential blend
+constexpr int kGStep = VPGS_GSTEP;  // Gaussians per step of the backward loop
 constexpr int kMaxThreads = 512;
 
 __global__ void __launch_bounds__(kMaxThreads)
@@ -78,7 +80,9 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
             const int py = tc.ty * cam.tile_h + ly + q * half;
             done[q] = !(px < cam.W && py < cam.H);
         }
-        bool all_done = done[0] && done[1];
+        bool all_done = true;
+#pragma unroll
+        for (int q = 0; q < kPix; ++q) all_done = all_done && done[q];
         for (int b0 = start; b0 < end; b0 += NT) {
             if (__syncthreads_count(all_done) == NT) break;
             const int j = b0 + tid;
@@ -86,34 +90,54 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                 const Rec r = rec[ival[j]];
                 s0[tid] = make_float4((r.r0.x - ox) + r.r0.z, (r.r0.y - oy) + r.r0.w, r.r1.x, r.r1.y);
                 s1[tid] = make_float4(r.r1.z, r.r1.w, r.r2.x, r.r2.y);
-                s2[tid] = make_float4(r.r2.z, r.r2.w, r.r3.x, 0.f);
+                s2[tid] = make_float4(r.r2.z, r.r2.w, r.r3.x, r.r3.w);
             }
             __syncthreads();
             if (!all_done) {
                 const int nb = min(NT, end - b0);
-                for (int k = 0; k < nb; ++k) {
-                    const float4 a = s0[k], b = s1[k];
+                for (int k0 = 0; k0 < nb; k0 += kChunk) {
+                    // independent evaluations of kChunk Gaussians x kPix pixels ...
+                    float al[kChunk][kPix];
 #pragma unroll
-                    for (int q = 0; q < kPix; ++q) {
-                        if (done[q]) continue;
-                        const PairEval e = eval_pair(pxl - a.x, pyl[q] - a.y, a.z, a.w, b.x, b.y, b.z, o.alpha_max);
-                        if (e.alpha < o.alpha_min) continue;
-                        const float nt = T[q] * (1.f - e.alpha);
-                        if (nt < o.t_min) {
-                            done[q] = true;
-                            continue;
+                    for (int c = 0; c < kChunk; ++c) {
+                        const int k = min(k0 + c, nb - 1);
+                        const float4 a = s0[k], b = s1[k];
+                        const float kq = s2[k].w;
+#pragma unroll
+                        for (int q = 0; q < kPix; ++q) {
+                            const PairEval e = eval_pair(pxl - a.x, pyl[q] - a.y, a.z, a.w, b.x, b.y, b.z, kq,
+                                                         o.alpha_max);
+                            al[c][q] = (k0 + c < nb) ? e.alpha : 0.f;
                         }
-                        const float w = e.alpha * T[q];
-                        const float4 c = s2[k];
-                        C0[q] = fmaf(w, c.x, C0[q]);
-                        C1[q] = fmaf(w, c.y, C1[q]);
-                        C2[q] = fmaf(w, c.z, C2[q]);
-                        D[q] = fmaf(w, b.w, D[q]);
-                        T[q] = nt;
-                        ++cnt[q];
-                        last[q] = b0 + k - start + 1;
                     }
-                    if (done[0] && done[1]) {
+                    // ... then the sequential blend in depth order
+#pragma unroll
+                    for (int c = 0; c < kChunk; ++c) {
+#pragma unroll
+                        for (int q = 0; q < kPix; ++q) {
+                            const float alpha = al[c][q];
+                            if (done[q] || alpha < o.alpha_min) continue;
+                            const float nt = T[q] * (1.f - alpha);
+                            if (nt < o.t_min) {
+                                done[q] = true;
+                                continue;
+                            }
+                            const int k = k0 + c;
+                            const float w = alpha * T[q];
+                            const float4 col = s2[k];
+                            C0[q] = fmaf(w, col.x, C0[q]);
+                            C1[q] = fmaf(w, col.y, C1[q]);
+                            C2[q] = fmaf(w, col.z, C2[q]);
+                            D[q] = fmaf(w, s1[k].w, D[q]);
+                            T[q] = nt;
+                            ++cnt[q];
+                            last[q] = b0 + k - start + 1;
+                        }
+                    }
+                    bool fin = true;
+#pragma unroll
+                    for (int q = 0; q < kPix; ++q) fin = fin && done[q];
+                    if (fin) {
                         all_done = true;
                         break;
                     }
@@ -143,27 +167,90 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
     }
 }
 
-// one reduction step of the transpose reduction: C live values -> C/2
-template <int C, int O>
-VPGS_D void tr_step(float (&v)[16], int lane) {
+// Transpose reduction of 10 values over a warp.  Each halving step keeps
+// ceil(R/2) live values per lane: one half of the lanes keeps the low slots,
+// its partners the high slots, and each adds what the partner sent (5+3+2+1
+// shuffles, then one more to sum lane pairs).  Afterwards lane l holds the warp
+// total of slot red_slot(l) in v[0] (or nothing, red_slot = -1).
+template <int R, int O>
+VPGS_D void half_step(float (&v)[10], int lane) {
+    constexpr int S = (R + 1) / 2;
     const bool up = (lane & O) != 0;
 #pragma unroll
-    for (int i = 0; i < C / 2; ++i) {
-        const float send = up ? v[i] : v[i + C / 2];
-        const float keep = up ? v[i + C / 2] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+    for (int i = 0; i < S; ++i) {
+        const float lo = v[i];
+        const float hi = (i + S < R) ? v[i + S] : 0.f;
+        v[i] = (up ? hi : lo) + __shfl_xor_sync(0xffffffffu, up ? lo : hi, O);
     }
 }
 
-// sum v[0..9] over the warp; lanes 0,2,..,18 end up holding the totals of slots 0..9
-VPGS_D int warp_reduce10(float (&v)[16], int lane) {
-    tr_step<16, 16>(v, lane);
-    tr_step<8, 8>(v, lane);
-    tr_step<4, 4>(v, lane);
-    tr_step<2, 2>(v, lane);
-    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-    const int slot = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-    return (lane & 1) ? 16 : slot;
+VPGS_D int red_slot(int lane) {
+    int n = 10, off = 0;
+    const int S[4] = {5, 3, 2, 1}, bit[4] = {16, 8, 4, 2};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (lane & bit[i]) {
+            off += S[i];
+            n = max(n - S[i], 0);
+        } else {
+            n = min(n, S[i]);
+        }
+    }
+    return (n >= 1 && !(lane & 1)) ? off : -1;
+}
+
+VPGS_D void warp_reduce10(float (&a)[10], int lane) {
+    half_step<10, 16>(a, lane);
+    half_step<5, 8>(a, lane);
+    half_step<3, 4>(a, lane);
+    half_step<2, 2>(a, lane);
+    a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
+}
+
+// two reductions interleaved, for instruction-level parallelism
+VPGS_D void warp_reduce10x2(float (&a)[10], float (&b)[10], int lane) {
+    half_step<10, 16>(a, lane); half_step<10, 16>(b, lane);
+    half_step<5, 8>(a, lane);   half_step<5, 8>(b, lane);
+    half_step<3, 4>(a, lane);   half_step<3, 4>(b, lane);
+    half_step<2, 2>(a, lane);   half_step<2, 2>(b, lane);
+    a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
+    b[0] += __shfl_xor_sync(0xffffffffu, b[0], 1);
+}
+
+// per-pixel backward state
+struct PixState {
+    float T, T_fin, gC0, gC1, gC2, gD, gA, B0, B1, B2, BD;
+    int last;
+};
+
+// gradient of one pixel-Gaussian pair (Gaussian at list position jj), added to v;
+// updates the pixel's transmittance and behind-colour; returns whether it blended
+VPGS_D bool pair_grad(PixState &p, int jj, const PairEval &e, float dx, float dy, const float4 &a,
+                      const float4 &b, const float4 &c, const OptParams &o, float (&v)[10]) {
+    if (jj >= p.last || e.alpha < o.alpha_min) return false;
+    const float om = 1.f - e.alpha;
+    p.T = p.T / om;
+    const float w = e.alpha * p.T;
+    v[6] = fmaf(w, p.gC0, v[6]);
+    v[7] = fmaf(w, p.gC1, v[7]);
+    v[8] = fmaf(w, p.gC2, v[8]);
+    v[9] = fmaf(w, p.gD, v[9]);
+    const float dA = (p.gC0 * (c.x - p.B0) + p.gC1 * (c.y - p.B1) + p.gC2 * (c.z - p.B2) +
+                      p.gD * (b.w - p.BD)) * p.T + p.gA * p.T_fin / om;
+    p.B0 = fmaf(e.alpha, c.x, om * p.B0);
+    p.B1 = fmaf(e.alpha, c.y, om * p.B1);
+    p.B2 = fmaf(e.alpha, c.z, om * p.B2);
+    p.BD = fmaf(e.alpha, b.w, om * p.BD);
+    if (b.z * e.G <= o.alpha_max) {
+        const float dpow = dA * e.alpha;
+        v[5] = fmaf(dA, e.G, v[5]);
+        v[0] = fmaf(dpow, a.z * e.t1 + b.x * e.t2, v[0]);
+        v[1] = fmaf(dpow, a.w * e.t1 + b.y * e.t2, v[1]);
+        v[2] = fmaf(-0.5f * dpow, dx * dx, v[2]);
+        v[3] = fmaf(-dpow, dx * dy, v[3]);
+        v[4] = fmaf(-0.5f * dpow, dy * dy, v[4]);
+    }
+    return true;
 }
 
 constexpr int kPartStride = 11;  // floats per (warp, Gaussian) partial, padded against bank conflicts
@@ -192,6 +279,7 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
 #pragma unroll
     for (int q = 0; q < kPix; ++q) pyl[q] = (float)(ly + q * half) + 0.5f;
     float *my_part = s_part + (size_t)warp * NT * kPartStride;
+    const int slot = red_slot(lane);
     int t = blockIdx.x;
     for (;;) {
         if (work) {
@@ -208,28 +296,27 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
         const uint2 rg = ranges[t];
         const int start = (int)rg.x;
         const int64_t HW = (int64_t)cam.H * cam.W;
-        float T[kPix], T_fin[kPix], gC0[kPix], gC1[kPix], gC2[kPix], gD[kPix], gA[kPix];
-        float B0[kPix], B1[kPix], B2[kPix], BD[kPix];
-        int last[kPix];
+        PixState ps[kPix];
         int my_max = 0;
 #pragma unroll
         for (int q = 0; q < kPix; ++q) {
-            T[q] = 1.f; gC0[q] = gC1[q] = gC2[q] = gD[q] = gA[q] = 0.f; last[q] = 0;
-            B0[q] = o.bg0; B1[q] = o.bg1; B2[q] = o.bg2; BD[q] = 0.f;
+            PixState &p = ps[q];
+            p.T = 1.f; p.gC0 = p.gC1 = p.gC2 = p.gD = p.gA = 0.f; p.last = 0;
+            p.B0 = o.bg0; p.B1 = o.bg1; p.B2 = o.bg2; p.BD = 0.f;
             const int py = tc.ty * cam.tile_h + ly + q * half;
             if (px < cam.W && py < cam.H) {
                 const int64_t pix = (int64_t)tc.v * HW + (int64_t)py * cam.W + px;
-                T[q] = t_final[pix];
-                last[q] = n_iter[pix];
+                p.T = t_final[pix];
+                p.last = n_iter[pix];
                 if (dL_drgb) {
                     const float *gp = dL_drgb + (int64_t)tc.v * 3 * HW + (int64_t)py * cam.W + px;
-                    gC0[q] = gp[0]; gC1[q] = gp[HW]; gC2[q] = gp[2 * HW];
+                    p.gC0 = gp[0]; p.gC1 = gp[HW]; p.gC2 = gp[2 * HW];
                 }
-                if (dL_ddepth) gD[q] = dL_ddepth[pix];
-                if (dL_dalpha) gA[q] = dL_dalpha[pix];
+                if (dL_ddepth) p.gD = dL_ddepth[pix];
+                if (dL_dalpha) p.gA = dL_dalpha[pix];
             }
-            T_fin[q] = T[q];
-            my_max = max(my_max, last[q]);
+            p.T_fin = p.T;
+            my_max = max(my_max, p.last);
         }
         // the warp's own list length: warps whose pixels stop early skip the tail
         const int warp_max = (int)__reduce_max_sync(0xffffffffu, (unsigned)my_max);
@@ -246,53 +333,63 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                 const Rec r = rec[id];
                 s0[tid] = make_float4((r.r0.x - ox) + r.r0.z, (r.r0.y - oy) + r.r0.w, r.r1.x, r.r1.y);
                 s1[tid] = make_float4(r.r1.z, r.r1.w, r.r2.x, r.r2.y);
-                s2[tid] = make_float4(r.r2.z, r.r2.w, r.r3.x, 0.f);
+                s2[tid] = make_float4(r.r2.z, r.r2.w, r.r3.x, r.r3.w);
                 s_id[tid] = id;
             }
             for (int e = lane; e < nb * kPartStride; e += 32) my_part[e] = 0.f;
             __syncthreads();
             const int k_end = min(nb, warp_max - (b0 - start));  // warp-uniform
-            for (int k = k_end - 1; k >= 0; --k) {
-                const int jj = b0 + k - start;
-                float v[16];
+            // kGStep Gaussians per step, back to front: kk (behind) then kk - 1
+            for (int kk = k_end - 1; kk >= 0; kk -= kGStep) {
+                if (kGStep == 1) {
+                    const float4 a = s0[kk], b = s1[kk], c = s2[kk];
+                    float v[10];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) v[q] = 0.f;
-                bool act_any = false;
-                const float4 a = s0[k], b = s1[k];
+                    for (int q = 0; q < 10; ++q) v[q] = 0.f;
+                    const int jj = b0 + kk - start;
+                    bool act = false;
+#pragma unroll
+                    for (int q = 0; q < kPix; ++q) {
+                        const float dx = pxl - a.x, dy = pyl[q] - a.y;
+                        const PairEval e = eval_pair(dx, dy, a.z, a.w, b.x, b.y, b.z, c.w, o.alpha_max);
+                        act |= pair_grad(ps[q], jj, e, dx, dy, a, b, c, o, v);
+                    }
+                    if (__any_sync(0xffffffffu, act)) {
+                        warp_reduce10(v, lane);
+                        if (slot >= 0) my_part[kk * kPartStride + slot] = v[0];
+                    }
+                    continue;
+                }
+                const bool has_b = kk >= 1;
+                const int ka = kk, kb = has_b ? kk - 1 : kk;
+                const float4 aA = s0[ka], bA = s1[ka], cA = s2[ka];
+                const float4 aB = s0[kb], bB = s1[kb], cB = s2[kb];
+                PairEval eA[kPix], eB[kPix];
+                float dxA[kPix], dyA[kPix], dxB[kPix], dyB[kPix];
 #pragma unroll
                 for (int q = 0; q < kPix; ++q) {
-                    if (jj >= last[q]) continue;
-                    const float dx = pxl - a.x, dy = pyl[q] - a.y;
-                    const PairEval e = eval_pair(dx, dy, a.z, a.w, b.x, b.y, b.z, o.alpha_max);
-                    if (e.alpha < o.alpha_min) continue;
-                    act_any = true;
-                    const float4 c = s2[k];
-                    const float om = 1.f - e.alpha;
-                    T[q] = T[q] / om;
-                    const float w = e.alpha * T[q];
-                    v[6] = fmaf(w, gC0[q], v[6]);
-                    v[7] = fmaf(w, gC1[q], v[7]);
-                    v[8] = fmaf(w, gC2[q], v[8]);
-                    v[9] = fmaf(w, gD[q], v[9]);
-                    const float dA = (gC0[q] * (c.x - B0[q]) + gC1[q] * (c.y - B1[q]) + gC2[q] * (c.z - B2[q]) +
-                                      gD[q] * (b.w - BD[q])) * T[q] + gA[q] * T_fin[q] / om;
-                    B0[q] = fmaf(e.alpha, c.x, om * B0[q]);
-                    B1[q] = fmaf(e.alpha, c.y, om * B1[q]);
-                    B2[q] = fmaf(e.alpha, c.z, om * B2[q]);
-                    BD[q] = fmaf(e.alpha, b.w, om * BD[q]);
-                    if (b.z * e.G <= o.alpha_max) {
-                        const float dpow = dA * e.alpha;
-                        v[5] = fmaf(dA, e.G, v[5]);
-                        v[0] = fmaf(dpow, a.z * e.t1 + b.x * e.t2, v[0]);
-                        v[1] = fmaf(dpow, a.w * e.t1 + b.y * e.t2, v[1]);
-                        v[2] = fmaf(-0.5f * dpow, dx * dx, v[2]);
-                        v[3] = fmaf(-dpow, dx * dy, v[3]);
-                        v[4] = fmaf(-0.5f * dpow, dy * dy, v[4]);
-                    }
+                    dxA[q] = pxl - aA.x; dyA[q] = pyl[q] - aA.y;
+                    dxB[q] = pxl - aB.x; dyB[q] = pyl[q] - aB.y;
+                    eA[q] = eval_pair(dxA[q], dyA[q], aA.z, aA.w, bA.x, bA.y, bA.z, cA.w, o.alpha_max);
+                    eB[q] = eval_pair(dxB[q], dyB[q], aB.z, aB.w, bB.x, bB.y, bB.z, cB.w, o.alpha_max);
                 }
-                if (__any_sync(0xffffffffu, act_any)) {
-                    const int slot = warp_reduce10(v, lane);
-                    if (slot < 10) my_part[k * kPartStride + slot] = v[0];
+                float vA[10], vB[10];
+#pragma unroll
+                for (int q = 0; q < 10; ++q) vA[q] = vB[q] = 0.f;
+                const int jjA = b0 + ka - start, jjB = b0 + kb - start;
+                bool act = false;
+#pragma unroll
+                for (int q = 0; q < kPix; ++q) act |= pair_grad(ps[q], jjA, eA[q], dxA[q], dyA[q], aA, bA, cA, o, vA);
+                if (has_b) {
+#pragma unroll
+                    for (int q = 0; q < kPix; ++q) act |= pair_grad(ps[q], jjB, eB[q], dxB[q], dyB[q], aB, bB, cB, o, vB);
+                }
+                if (__any_sync(0xffffffffu, act)) {
+                    warp_reduce10x2(vA, vB, lane);
+                    if (slot >= 0) {
+                        my_part[ka * kPartStride + slot] = vA[0];
+                        if (has_b) my_part[kb * kPartStride + slot] = vB[0];
+                    }
                 }
             }
             __syncthreads();

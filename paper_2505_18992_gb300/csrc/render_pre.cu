@@ -147,7 +147,7 @@ preprocess_fwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamPara
                         R.r0 = make_float4(p.u.hi, p.v.hi, p.u.lo, p.v.lo);
                         R.r1 = make_float4(ex * s1, ey * s1, -ey * s2, ex * s2);
                         R.r2 = make_float4(op, p.pz, cr, cg);
-                        R.r3 = make_float4(cb, rxe, rye, 0.f);
+                        R.r3 = make_float4(cb, rxe, rye, kq);
                     }
                 }
             }
