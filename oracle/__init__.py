@@ -7,3 +7,4 @@ nothing from the product.
 """
 from .raster import Options, Margins, render, render_scene, project, extent, quat_to_rotmat  # noqa: F401
 from .decode import decode, decode_scene, bf16_round, n_mlp_params, flatten_mlp, MLP_ORDER  # noqa: F401,E402
+from .pose import pose_step, se3_exp  # noqa: F401,E402

@@ -24,6 +24,12 @@
 #ifndef VPGS_GSTEP
 #define VPGS_GSTEP 1
 #endif
+//   VPGS_BWD_ACC how the backward combines per-warp sums of a Gaussian's 2D
+//                gradient: 0 = one global atomic per warp, 1 = per-warp shared
+//                slots summed per batch, 2 = shared-memory atomics per batch
+#ifndef VPGS_BWD_ACC
+#define VPGS_BWD_ACC 1
+#endif
 
 namespace vpgs {
 

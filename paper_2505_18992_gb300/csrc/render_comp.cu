@@ -39,6 +39,7 @@ VPGS_D TileCoord tile_coord(int t, const CamParams &cam) {
 constexpr int kPix = VPGS_PIX;
 constexpr int kChunk = VPGS_CHUNK;  // Gaussians evaluated together before the sequential blend
 constexpr int kGStep = VPGS_GSTEP;  // Gaussians per step of the backward loop
+constexpr int kAcc = VPGS_BWD_ACC;  // combination of per-warp gradient sums (see common.cuh)
 constexpr int kMaxThreads = 512;
 
 __global__ void __launch_bounds__(kMaxThreads)
@@ -280,6 +281,16 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
     for (int q = 0; q < kPix; ++q) pyl[q] = (float)(ly + q * half) + 0.5f;
     float *my_part = s_part + (size_t)warp * NT * kPartStride;
     const int slot = red_slot(lane);
+    // hands one warp total (this lane's slot) of Gaussian k to the combination scheme
+    auto put = [&](int k, float val) {
+        if (kAcc == 0) {
+            if (val != 0.f) atomicAdd(g2d + 10 * (int64_t)s_id[k] + slot, val);
+        } else if (kAcc == 1) {
+            my_part[k * kPartStride + slot] = val;
+        } else {
+            if (val != 0.f) atomicAdd(s_part + k * kPartStride + slot, val);
+        }
+    };
     int t = blockIdx.x;
     for (;;) {
         if (work) {
@@ -336,7 +347,10 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                 s2[tid] = make_float4(r.r2.z, r.r2.w, r.r3.x, r.r3.w);
                 s_id[tid] = id;
             }
-            for (int e = lane; e < nb * kPartStride; e += 32) my_part[e] = 0.f;
+            if (kAcc == 1)
+                for (int e = lane; e < nb * kPartStride; e += 32) my_part[e] = 0.f;
+            if (kAcc == 2)
+                for (int e = tid; e < nb * kPartStride; e += NT) s_part[e] = 0.f;
             __syncthreads();
             const int k_end = min(nb, warp_max - (b0 - start));  // warp-uniform
             // kGStep Gaussians per step, back to front: kk (behind) then kk - 1
@@ -356,7 +370,7 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                     }
                     if (__any_sync(0xffffffffu, act)) {
                         warp_reduce10(v, lane);
-                        if (slot >= 0) my_part[kk * kPartStride + slot] = v[0];
+                        if (slot >= 0) put(kk, v[0]);
                     }
                     continue;
                 }
@@ -387,20 +401,26 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                 if (__any_sync(0xffffffffu, act)) {
                     warp_reduce10x2(vA, vB, lane);
                     if (slot >= 0) {
-                        my_part[ka * kPartStride + slot] = vA[0];
-                        if (has_b) my_part[kb * kPartStride + slot] = vB[0];
+                        put(ka, vA[0]);
+                        if (has_b) put(kb, vB[0]);
                     }
                 }
             }
-            __syncthreads();
-            // one thread per Gaussian of the batch: sum the warps, one atomic per value
-            for (int k = tid; k < nb; k += NT) {
-                float *dst = g2d + 10 * (int64_t)s_id[k];
+            if (kAcc != 0) {
+                __syncthreads();
+                // one thread per Gaussian of the batch: one global atomic per value
+                for (int k = tid; k < nb; k += NT) {
+                    float *dst = g2d + 10 * (int64_t)s_id[k];
 #pragma unroll
-                for (int slot = 0; slot < 10; ++slot) {
-                    float acc = 0.f;
-                    for (int w = 0; w < NW; ++w) acc += s_part[((size_t)w * NT + k) * kPartStride + slot];
-                    if (acc != 0.f) atomicAdd(dst + slot, acc);
+                    for (int sl = 0; sl < 10; ++sl) {
+                        float acc = 0.f;
+                        if (kAcc == 1) {
+                            for (int w = 0; w < NW; ++w) acc += s_part[((size_t)w * NT + k) * kPartStride + sl];
+                        } else {
+                            acc = s_part[k * kPartStride + sl];
+                        }
+                        if (acc != 0.f) atomicAdd(dst + sl, acc);
+                    }
                 }
             }
         }
@@ -410,8 +430,8 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
 }
 
 static size_t comp_smem(int NT, bool bwd) {
-    return sizeof(float4) * 3 * NT +
-           (bwd ? sizeof(uint32_t) * NT + sizeof(float) * (size_t)(NT / 32) * NT * kPartStride : 0);
+    const size_t parts = kAcc == 1 ? (size_t)(NT / 32) * NT * kPartStride : (kAcc == 2 ? (size_t)NT * kPartStride : 0);
+    return sizeof(float4) * 3 * NT + (bwd ? sizeof(uint32_t) * NT + sizeof(float) * parts : 0);
 }
 
 static int persistent_grid(const void *kernel, int B, size_t smem, int per_sm, int n_tiles) {
