@@ -77,7 +77,9 @@ bool make_layout(int64_t N, int V, const vpgs_camera *cam, const vpgs_render_opt
     const int64_t look_b = (int64_t)np_tile * sort_blocks(L.M_cap, kTileSortItems);
     L.sort_blocks_max = look_a > look_b ? look_a : look_b;
     L.off_sort_look = take(4 * kRadix * (size_t)L.sort_blocks_max);
-    L.scan_blocks_max = scan_blocks(VN1);
+    // scans: visibility and offsets over V*N items, radix count matrices of 256 x blocks
+    const int64_t cm = kRadix * std::max(sort_blocks(VN1, kDepthSortItems), sort_blocks(L.M_cap, kTileSortItems));
+    L.scan_blocks_max = std::max(scan_blocks(VN1), scan_blocks(cm));
     L.off_scan_look = take(8 * (size_t)L.scan_blocks_max);
     L.off_g2d = take(4 * 10 * (size_t)VN1);
     L.off_posedf = take(4 * 24 * (size_t)V);

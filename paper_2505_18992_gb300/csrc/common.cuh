@@ -28,7 +28,7 @@
 //                gradient: 0 = one global atomic per warp, 1 = per-warp shared
 //                slots summed per batch, 2 = shared-memory atomics per batch
 #ifndef VPGS_BWD_ACC
-#define VPGS_BWD_ACC 1
+#define VPGS_BWD_ACC 0
 #endif
 
 namespace vpgs {
@@ -160,27 +160,18 @@ struct __align__(16) Rec {
     float4 r0, r1, r2, r3;
 };
 
-// evaluated per pixel/Gaussian pair, bit-identically in forward and backward.
-// Pairs whose quadratic form exceeds kq (plus 1e-4, far above the FP32 error
-// of q) have alpha < alpha_min and get alpha = 0 without the exp: the alpha
-// test would reject every one of them, so results are unchanged.
+// evaluated per pixel/Gaussian pair, bit-identically in forward and backward
 struct PairEval {
     float t1, t2, G, alpha;
 };
 
 VPGS_D PairEval eval_pair(float dx, float dy, float w1x, float w1y, float w2x, float w2y,
-                          float opac, float kq, float alpha_max) {
+                          float opac, float alpha_max) {
     PairEval e;
     e.t1 = fmaf(w1x, dx, w1y * dy);
     e.t2 = fmaf(w2x, dx, w2y * dy);
-    const float q = fmaf(e.t1, e.t1, e.t2 * e.t2);
-    if (q > kq + 1e-4f) {
-        e.G = 0.f;
-        e.alpha = 0.f;
-    } else {
-        e.G = __expf(-0.5f * q);
-        e.alpha = fminf(alpha_max, opac * e.G);
-    }
+    e.G = __expf(-0.5f * fmaf(e.t1, e.t1, e.t2 * e.t2));
+    e.alpha = fminf(alpha_max, opac * e.G);
     return e;
 }
 
@@ -232,6 +223,13 @@ struct RenderWs {
 constexpr int kSortThreads = 256;
 constexpr int kDepthSortItems = 4;  // keys per thread in the depth sort (1024 per block)
 constexpr int kTileSortItems = 16;  // keys per thread in the tile-id sort (4096 per block)
+// radix pass kind per sort: one-sweep (decoupled look-back) or count/scan/scatter
+#ifndef VPGS_DEPTH_LOOKBACK
+#define VPGS_DEPTH_LOOKBACK 1
+#endif
+#ifndef VPGS_TILE_LOOKBACK
+#define VPGS_TILE_LOOKBACK 0
+#endif
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kMaxSortPasses = 8;

@@ -369,6 +369,131 @@ radix_onesweep_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__res
     }
 }
 
+// ---------------------------------------------------------------------------
+// Radix pass without look-back: count -> scan -> scatter.
+// The per-block digit counts are stored digit-major (counts[d * nb + b]), so an
+// exclusive scan of that matrix gives every (digit, block) its global output
+// position directly, and no block ever waits on another.
+// ---------------------------------------------------------------------------
+template <int ITEMS>
+static __global__ void __launch_bounds__(kSortThreads)
+radix_count_kernel(const uint32_t *__restrict__ key_in, int64_t n_cap, const uint32_t *n_dev, SortPass pass,
+                   uint32_t *__restrict__ counts, int64_t nb) {
+    constexpr int kTile = kSortThreads * ITEMS;
+    __shared__ uint32_t s_h[kRadix];
+    const int tid = threadIdx.x;
+    s_h[tid] = 0;
+    __syncthreads();
+    int64_t n = n_cap;
+    if (n_dev) n = min(n, (int64_t)*n_dev);
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    const uint32_t mask = (1u << pass.bits) - 1u;
+#pragma unroll
+    for (int s = 0; s < ITEMS; ++s) {
+        const int64_t i = base + s * kSortThreads + tid;
+        if (i < n) atomicAdd(&s_h[(key_in[i] >> pass.shift) & mask], 1u);
+    }
+    __syncthreads();
+    counts[(int64_t)tid * nb + blockIdx.x] = s_h[tid];
+}
+
+struct CountsLoad {
+    const uint32_t *c;
+    __device__ uint32_t operator()(int64_t i) const { return c[i]; }
+};
+struct CountsStore {
+    uint32_t *c;
+    __device__ void operator()(int64_t i, uint32_t excl, uint32_t) const { c[i] = excl; }
+};
+
+template <int ITEMS>
+static __global__ void __launch_bounds__(kSortThreads)
+radix_scatter_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__restrict__ val_in,
+                     uint32_t *__restrict__ key_out, uint32_t *__restrict__ val_out, int64_t n_cap,
+                     const uint32_t *n_dev, SortPass pass, const uint32_t *__restrict__ offsets, int64_t nb) {
+    constexpr int kWarps = kSortThreads / kWarp;
+    constexpr int kSeg = kWarp * ITEMS;
+    constexpr int kTile = kSortThreads * ITEMS;
+    __shared__ uint32_t s_cnt[kWarps][kRadix];
+    __shared__ uint32_t s_dstart[kRadix], s_gbase[kRadix], s_wsum[kWarps];
+    __shared__ uint32_t s_key[kTile], s_val[kTile];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < kWarps * kRadix; i += kSortThreads) (&s_cnt[0][0])[i] = 0;
+    int64_t n = n_cap;
+    if (n_dev) n = min(n, (int64_t)*n_dev);
+    const int64_t b = blockIdx.x;
+    const int64_t base = b * kTile;
+    if (base >= n) return;
+    const uint32_t mask = (1u << pass.bits) - 1u;
+    s_gbase[tid] = offsets[(int64_t)tid * nb + b];  // global slot of this block's first key with digit tid
+    __syncthreads();
+    uint32_t k[ITEMS], v[ITEMS], d[ITEMS];
+    const int64_t seg = base + (int64_t)warp * kSeg;
+#pragma unroll
+    for (int s = 0; s < ITEMS; ++s) {
+        const int64_t i = seg + s * kWarp + lane;
+        const bool ok = i < n;
+        k[s] = ok ? key_in[i] : 0u;
+        v[s] = ok ? val_in[i] : 0u;
+        d[s] = ok ? ((k[s] >> pass.shift) & mask) : (kRadix + lane);
+    }
+#pragma unroll
+    for (int s = 0; s < ITEMS; ++s) {
+        const uint32_t m = __match_any_sync(0xffffffffu, d[s]);
+        if (d[s] < kRadix && (m & lanemask_lt()) == 0) s_cnt[warp][d[s]] += __popc(m);
+        __syncwarp();
+    }
+    __syncthreads();
+    uint32_t c = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) c += s_cnt[w][tid];
+    {
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_wsum[warp] = x;
+        __syncthreads();
+        uint32_t add = 0;
+        for (int w = 0; w < warp; ++w) add += s_wsum[w];
+        s_dstart[tid] = x - c + add;
+        uint32_t run = s_dstart[tid];
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t t = s_cnt[w][tid];
+            s_cnt[w][tid] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < ITEMS; ++s) {
+        const uint32_t m = __match_any_sync(0xffffffffu, d[s]);
+        const uint32_t rank = __popc(m & lanemask_lt());
+        if (d[s] < kRadix) {
+            const uint32_t lp = s_cnt[warp][d[s]] + rank;
+            s_key[lp] = k[s];
+            s_val[lp] = v[s];
+        }
+        __syncwarp();
+        if (d[s] < kRadix && rank == 0) s_cnt[warp][d[s]] += __popc(m);
+        __syncwarp();
+    }
+    __syncthreads();
+    const int nbk = (int)min((int64_t)kTile, n - base);
+    for (int i = tid; i < nbk; i += kSortThreads) {
+        const uint32_t key = s_key[i];
+        const uint32_t dg = (key >> pass.shift) & mask;
+        const uint32_t pos = s_gbase[dg] + ((uint32_t)i - s_dstart[dg]);
+        if ((int64_t)pos < n) {
+            key_out[pos] = key;
+            val_out[pos] = s_val[i];
+        }
+    }
+}
+
 // Split `bits` low key bits starting at `lo` into balanced passes of <= 8 bits.
 inline int plan_passes(int lo, int bits, SortPass *out) {
     int np = (bits + kRadixBits - 1) / kRadixBits;
@@ -389,20 +514,52 @@ inline int64_t sort_blocks(int64_t n, int items) {
 
 // Sort n (<= n_cap, or *n_dev) pairs from (k0, v0) using (k1, v1) as the other
 // buffer.  Returns in *result_in_1 whether the sorted data ended in buffer 1.
-// scratch: hist [kMaxSortPasses*256], ticket [1], look [sort_blocks(n_cap)*256*passes].
+// lookback = true: one-sweep passes (scratch: hist [4*256], ticket [4],
+//   look [passes * sort_blocks * 256]);
+// lookback = false: count / scan / scatter passes (scratch: look holds the
+//   [256 * sort_blocks] count matrix; scan_ticket/scan_look as for launch_scan).
 inline cudaError_t radix_sort_pairs(const char *name, uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
                                     int64_t n_cap, const uint32_t *n_dev, int lo_bit, int bits,
                                     uint32_t *hist, uint32_t *ticket, uint32_t *look,
                                     uint32_t *status, int sms, cudaStream_t stream,
-                                    bool *result_in_1, int items = 16) {
+                                    bool *result_in_1, int items, bool lookback,
+                                    uint32_t *scan_ticket, unsigned long long *scan_look) {
     SortPass ps[kMaxSortPasses];
     int np = plan_passes(lo_bit, bits, ps);
     *result_in_1 = (np & 1) != 0;
     if (np == 0 || n_cap == 0) return cudaSuccess;
     if (np > 4) return cudaErrorInvalidValue;
     if (items != 4 && items != 8 && items != 16) return cudaErrorInvalidValue;
-    int64_t nb = sort_blocks(n_cap, items);
-    cudaError_t e = cudaMemsetAsync(hist, 0, np * kRadix * sizeof(uint32_t), stream);
+    const int64_t nb = sort_blocks(n_cap, items);
+    cudaError_t e;
+    uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
+    if (!lookback) {
+        for (int p = 0; p < np; ++p) {
+            if (items == 4)
+                VPGS_LAUNCH("radix_count", stream, radix_count_kernel<4><<<(unsigned)nb, kSortThreads, 0, stream>>>(ki, n_cap, n_dev, ps[p], look, nb));
+            else if (items == 8)
+                VPGS_LAUNCH("radix_count", stream, radix_count_kernel<8><<<(unsigned)nb, kSortThreads, 0, stream>>>(ki, n_cap, n_dev, ps[p], look, nb));
+            else
+                VPGS_LAUNCH("radix_count", stream, radix_count_kernel<16><<<(unsigned)nb, kSortThreads, 0, stream>>>(ki, n_cap, n_dev, ps[p], look, nb));
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            e = launch_scan("radix_offsets", CountsLoad{look}, CountsStore{look}, (int64_t)kRadix * nb, nullptr,
+                            scan_ticket, scan_look, nullptr, status, stream);
+            if (e != cudaSuccess) return e;
+            if (items == 4)
+                VPGS_LAUNCH(name, stream, radix_scatter_kernel<4><<<(unsigned)nb, kSortThreads, 0, stream>>>(ki, vi, ko, vo, n_cap, n_dev, ps[p], look, nb));
+            else if (items == 8)
+                VPGS_LAUNCH(name, stream, radix_scatter_kernel<8><<<(unsigned)nb, kSortThreads, 0, stream>>>(ki, vi, ko, vo, n_cap, n_dev, ps[p], look, nb));
+            else
+                VPGS_LAUNCH(name, stream, radix_scatter_kernel<16><<<(unsigned)nb, kSortThreads, 0, stream>>>(ki, vi, ko, vo, n_cap, n_dev, ps[p], look, nb));
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            uint32_t *tk = ki, *tv = vi;
+            ki = ko; vi = vo; ko = tk; vo = tv;
+        }
+        return cudaSuccess;
+    }
+    e = cudaMemsetAsync(hist, 0, np * kRadix * sizeof(uint32_t), stream);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(look, 0, (size_t)np * nb * kRadix * sizeof(uint32_t), stream);
     if (e != cudaSuccess) return e;
@@ -416,7 +573,6 @@ inline cudaError_t radix_sort_pairs(const char *name, uint32_t *k0, uint32_t *v0
                                                                np > 3 ? ps[3] : z, hist));
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
     for (int p = 0; p < np; ++p) {
         uint32_t *lk = look + (size_t)p * nb * kRadix;
         if (items == 4)

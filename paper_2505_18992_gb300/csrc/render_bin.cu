@@ -138,7 +138,8 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
     bool in1 = false;
     e = radix_sort_pairs("sort_depth_pass", ws.dkey[0], ws.dval[0], ws.dkey[1], ws.dval[1], L.VN, n_vis,
                          0, 32, ws.sort_hist, ws.counters + CNT_TICKET_B, ws.sort_look, ws.status, sms, s,
-                         &in1, kDepthSortItems);
+                         &in1, kDepthSortItems, VPGS_DEPTH_LOOKBACK != 0, ws.counters + CNT_TICKET_A,
+                         ws.scan_look);
     if (e != cudaSuccess) return e;
     const uint32_t *dval = in1 ? ws.dval[1] : ws.dval[0];
     uint32_t *inst_off = in1 ? ws.dkey[0] : ws.dkey[1];  // the depth-sort buffer not holding the result
@@ -155,7 +156,8 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
     // 4. stable sort by tile id
     e = radix_sort_pairs("sort_tile_pass", ws.ikey[0], ws.ival[0], ws.ikey[1], ws.ival[1], L.M_cap, n_inst, 0,
                          L.tile_bits, ws.sort_hist, ws.counters + CNT_TICKET_B, ws.sort_look,
-                         ws.status, sms, s, &in1, kTileSortItems);
+                         ws.status, sms, s, &in1, kTileSortItems, VPGS_TILE_LOOKBACK != 0,
+                         ws.counters + CNT_TICKET_A, ws.scan_look);
     if (e != cudaSuccess) return e;
     *sorted_buf = in1 ? 1 : 0;
     // 5. tile ranges

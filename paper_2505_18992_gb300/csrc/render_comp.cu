@@ -103,10 +103,9 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                     for (int c = 0; c < kChunk; ++c) {
                         const int k = min(k0 + c, nb - 1);
                         const float4 a = s0[k], b = s1[k];
-                        const float kq = s2[k].w;
 #pragma unroll
                         for (int q = 0; q < kPix; ++q) {
-                            const PairEval e = eval_pair(pxl - a.x, pyl[q] - a.y, a.z, a.w, b.x, b.y, b.z, kq,
+                            const PairEval e = eval_pair(pxl - a.x, pyl[q] - a.y, a.z, a.w, b.x, b.y, b.z,
                                                          o.alpha_max);
                             al[c][q] = (k0 + c < nb) ? e.alpha : 0.f;
                         }
@@ -365,7 +364,7 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
 #pragma unroll
                     for (int q = 0; q < kPix; ++q) {
                         const float dx = pxl - a.x, dy = pyl[q] - a.y;
-                        const PairEval e = eval_pair(dx, dy, a.z, a.w, b.x, b.y, b.z, c.w, o.alpha_max);
+                        const PairEval e = eval_pair(dx, dy, a.z, a.w, b.x, b.y, b.z, o.alpha_max);
                         act |= pair_grad(ps[q], jj, e, dx, dy, a, b, c, o, v);
                     }
                     if (__any_sync(0xffffffffu, act)) {
@@ -384,8 +383,8 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                 for (int q = 0; q < kPix; ++q) {
                     dxA[q] = pxl - aA.x; dyA[q] = pyl[q] - aA.y;
                     dxB[q] = pxl - aB.x; dyB[q] = pyl[q] - aB.y;
-                    eA[q] = eval_pair(dxA[q], dyA[q], aA.z, aA.w, bA.x, bA.y, bA.z, cA.w, o.alpha_max);
-                    eB[q] = eval_pair(dxB[q], dyB[q], aB.z, aB.w, bB.x, bB.y, bB.z, cB.w, o.alpha_max);
+                    eA[q] = eval_pair(dxA[q], dyA[q], aA.z, aA.w, bA.x, bA.y, bA.z, o.alpha_max);
+                    eB[q] = eval_pair(dxB[q], dyB[q], aB.z, aB.w, bB.x, bB.y, bB.z, o.alpha_max);
                 }
                 float vA[10], vB[10];
 #pragma unroll
