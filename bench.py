@@ -50,7 +50,7 @@ def _args():
     p.add_argument("--no-extras", action="store_true", help="skip tracking/e2e/profile passes")
     p.add_argument("--no-rows", action="store_true", help="keep the kernel profile, skip the other rows")
     p.add_argument("--persistent", type=int, default=0, help="persistent CTAs per SM (0 = per tile)")
-    p.add_argument("--tile", default="16x16", help="tile shape WxH")
+    p.add_argument("--tile", default="8x16", help="tile shape WxH")
     p.add_argument("--scale", type=float, default=1.0,
                    help="shrink the workload for profiling: N x scale^2 Gaussians, image x scale")
     return p.parse_args()
@@ -329,14 +329,50 @@ def run_ours(a):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms_step = float(tt.item())
         dist.barrier()
+    C.check(r.stats().status, "timed renders")
+    value_eager = P * world / (ms_step * 1e-3) / 1e6
+    eager = {"value": value_eager, "ms_per_step": ms_step, "ms_p50": statistics.median(ms)}
+    # the same step captured once into a CUDA graph and replayed (the library
+    # is capturable: no host sync, device-side counts); L2 flushed between replays
+    graph_ms = None
+    try:
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            step()
+        torch.cuda.current_stream(dev).wait_stream(side)
+        torch.cuda.synchronize()
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(cg):
+            step()
+        for _ in range(3):
+            cg.replay()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t_wall0g = time.time()
+        g_ms = timed(cg.replay, a.steps)
+        t_wall1 = time.time()
+        graph_ms = sum(g_ms) / len(g_ms)
+        if world > 1:
+            tt = torch.tensor([graph_ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            graph_ms = float(tt.item())
+        C.check(r.stats().status, "graph replays")
+    except Exception as exc:  # reported; the eager number stands
+        eager["graph_error"] = repr(exc)[:200]
     if sampler:
         time.sleep(0.2)
         sampler.stop()
-    C.check(r.stats().status, "timed renders")
-    value = P * world / (ms_step * 1e-3) / 1e6
+    if graph_ms is not None and graph_ms < ms_step:
+        ms_step_head, launch = graph_ms, "cuda_graph"
+        t_wall0 = t_wall0g  # clocks of the region that gives the headline number
+    else:
+        ms_step_head, launch = ms_step, "eager"
+    value = P * world / (ms_step_head * 1e-3) / 1e6
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": a.warmup, "ms_per_step": ms_step_head, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD if a.scale == 1.0 else f"room scaled x{a.scale}",
                        "n_gaussians": sc.n, "width": W, "height": H,
@@ -344,7 +380,9 @@ def run_ours(a):
                        "persistent_ctas_per_sm": a.persistent,
                        "l2": "256 MiB buffer written between timed steps (inputs 56 MB < L2)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "ms_p50": statistics.median(ms), "ms_min": min(ms)},
+                       "launch": launch},
+            "eager": eager, "cuda_graph": {"ms_per_step": graph_ms,
+                                           "value": P * world / (graph_ms * 1e-3) / 1e6 if graph_ms else None},
             "gpu_launches": int(launches)}
     if sampler:
         line["clocks"] = sampler.summary(t_wall0, t_wall1)
@@ -424,7 +462,7 @@ def run_ours(a):
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
         # coarse tracking: 50 pose-only iterations, eager vs one captured CUDA graph
         for key, fn in (("tracking", lambda: tracking_rows(sc, g, dev)), ("decode", lambda: decode_rows(dev)),
-                        ("batched_keyframes", lambda: batched_rows(dev))):
+                        ("batched_keyframes", lambda: batched_rows(dev)), ("fusion", lambda: fusion_rows(dev))):
             try:
                 line[key] = fn()
             except Exception as exc:  # reported, not fatal
@@ -514,6 +552,59 @@ def batched_rows(dev, steps=10):
     return {"views": V, "gaussians": sc.n, "width": W, "height": H,
             "batched_ms": mb, "separate_ms": ms, "batched_mpix_s": px / (mb * 1e-3) / 1e6,
             "separate_mpix_s": px / (ms * 1e-3) / 1e6}
+
+
+def fusion_rows(dev):
+    """Submap fusion (Eq. 14 shape): two overlapping 500k-Gaussian submaps of a
+    street (50,000 anchors x k = 10 each) decoded with BF16 MLPs, each rendered
+    at 1920x1080 from a camera in the overlap, L1 distillation between the two
+    renders, backward through both renders and both decoders."""
+    import torch
+
+    from paper_2505_18992_gb300 import scenes
+    from paper_2505_18992_gb300.decode import Decoder
+    from paper_2505_18992_gb300.render import Intrinsics, Renderer
+    torch.cuda.reset_peak_memory_stats(dev)
+    subs = [scenes.street_anchors(n_anchors=50_000, length=62.5, x0=x0, seed=20 + i, width=1920, height=1080,
+                                  f=1000.0, cam_x=495.0, mlp_seed=7)
+            for i, x0 in enumerate((437.5, 490.0))]
+    t = lambda a, dt=torch.float32: torch.tensor(a, dtype=dt, device=dev).contiguous()  # noqa: E731
+    cam = subs[0].camera
+    T = t(cam.T_cw[0], torch.float64)
+    r = Renderer(Intrinsics(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy), device=dev)
+    state = []
+    for sc in subs:
+        params = t(np.concatenate([np.asarray(p, np.float32).reshape(-1)
+                                   for name in ("opacity", "color", "cov") for p in sc.mlp[name]]))
+        inp = (t(sc.anchors), t(sc.features), t(sc.scaling), t(sc.offsets), params)
+        state.append((Decoder(sc.k, bf16=True, device=dev), inp, sc))
+    P = cam.width * cam.height
+
+    def step():
+        outs, imgs = [], []
+        for d, inp, sc in state:
+            o = d.forward(*inp, sc.camera, T)
+            img = r.forward(o["means"], o["scales"], o["quats"], o["opacities"], o["colors"], T[None].contiguous(),
+                            n_dev=o["n_dev"], check=False)
+            outs.append(o)
+            imgs.append({k: v.clone() for k, v in img.items()})
+        # L1 distillation between the two submaps' colour and depth (caller-side)
+        g_rgb = torch.sign(imgs[0]["rgb"] - imgs[1]["rgb"]) / (3 * P)
+        g_d = torch.sign(imgs[0]["depth"] - imgs[1]["depth"]) / P
+        for i, ((d, inp, sc), o, img) in enumerate(zip(state, outs, imgs)):
+            sgn = 1.0 if i == 0 else -1.0
+            grads = {k: torch.zeros_like(o[k]) for k in ("means", "scales", "quats", "opacities", "colors")}
+            r.backward(o["means"], o["scales"], o["quats"], o["opacities"], o["colors"], T[None].contiguous(), img,
+                       sgn * g_rgb, sgn * g_d, None, grads=grads, n_dev=o["n_dev"])
+            d.backward(*inp, sc.camera, T, o, grads)
+
+    step()
+    torch.cuda.synchronize()
+    ms = _time_ms(step, 5)
+    return {"submaps": 2, "gaussians_decoded": [int(s[0].forward(*s[1], s[2].camera, T)["n"]) for s in state],
+            "width": cam.width, "height": cam.height, "ms_per_step": ms,
+            "mpix_s": 2 * P / (ms * 1e-3) / 1e6,
+            "peak_hbm_gb": torch.cuda.max_memory_allocated(dev) / 1e9}
 
 
 def tracking_rows(sc, g, dev):

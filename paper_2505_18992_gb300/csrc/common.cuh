@@ -228,7 +228,7 @@ constexpr int kTileSortItems = 16;  // keys per thread in the tile-id sort (4096
 #define VPGS_DEPTH_LOOKBACK 1
 #endif
 #ifndef VPGS_TILE_LOOKBACK
-#define VPGS_TILE_LOOKBACK 0
+#define VPGS_TILE_LOOKBACK 1
 #endif
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;

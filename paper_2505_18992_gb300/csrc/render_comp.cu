@@ -367,7 +367,16 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                         const PairEval e = eval_pair(dx, dy, a.z, a.w, b.x, b.y, b.z, o.alpha_max);
                         act |= pair_grad(ps[q], jj, e, dx, dy, a, b, c, o, v);
                     }
-                    if (__any_sync(0xffffffffu, act)) {
+                    const uint32_t am = __ballot_sync(0xffffffffu, act);
+                    if (kAcc == 0 && am != 0u && __popc(am) <= 2) {
+                        // one or two active lanes: their own atomics beat a reduction
+                        if (act) {
+                            float *dst = g2d + 10 * (int64_t)s_id[kk];
+#pragma unroll
+                            for (int q = 0; q < 10; ++q)
+                                if (v[q] != 0.f) atomicAdd(dst + q, v[q]);
+                        }
+                    } else if (am != 0u) {
                         warp_reduce10(v, lane);
                         if (slot >= 0) put(kk, v[0]);
                     }

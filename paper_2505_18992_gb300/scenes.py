@@ -277,8 +277,8 @@ def decoder_mlps(rng, k: int = K_PER_ANCHOR) -> dict:
 def street_anchors(n_anchors: int = 100_000, width: int = 1241, height: int = 376,
                    f: float = 718.0, length: float = 200.0, seed: int = 2,
                    voxel: float = 0.2, k: int = K_PER_ANCHOR,
-                   cam_x: float = 2.0) -> AnchorScene:
-    """Voxel anchors over a street corridor [0,length]x[-10,10]x[0,8] m.
+                   cam_x: float = 2.0, x0: float = 0.0, mlp_seed=None) -> AnchorScene:
+    """Voxel anchors over a street corridor [x0,x0+length]x[-10,10]x[0,8] m.
 
     Anchors sit at centres of 0.2 m voxels on the ground and on the two facades,
     sampled without replacement; 32-dim N(0,1) features, per-anchor scaling
@@ -296,20 +296,20 @@ def street_anchors(n_anchors: int = 100_000, width: int = 1241, height: int = 37
     pts = np.empty((n_anchors, 3), np.float64)
     g = pick < n_ground
     ig = pick[g]
-    pts[g] = np.stack([(ig // ny + 0.5) * voxel, -10.0 + (ig % ny + 0.5) * voxel,
+    pts[g] = np.stack([x0 + (ig // ny + 0.5) * voxel, -10.0 + (ig % ny + 0.5) * voxel,
                        np.full(ig.shape, 0.5 * voxel)], 1)
     fa = pick[~g] - n_ground
     side = fa // n_facade
     r = fa % n_facade
     ysgn = np.where(side == 0, -1.0, 1.0)
-    pts[~g] = np.stack([(r // nz + 0.5) * voxel, ysgn * (10.0 - 0.5 * voxel),
+    pts[~g] = np.stack([x0 + (r // nz + 0.5) * voxel, ysgn * (10.0 - 0.5 * voxel),
                         (r % nz + 0.5) * voxel], 1)
     perm = rng.permutation(n_anchors)
     anchors = pts[perm].astype(np.float32)
     features = rng.normal(size=(n_anchors, FEAT_DIM)).astype(np.float32)
     scaling = (0.2 * np.exp(rng.uniform(-0.2, 0.2, size=(n_anchors, 3)))).astype(np.float32)
     offsets = rng.uniform(-1, 1, size=(n_anchors, k, 3)).astype(np.float32)
-    mlp = decoder_mlps(rng, k)
+    mlp = decoder_mlps(rng if mlp_seed is None else np.random.default_rng(mlp_seed), k)
     T = look_at([cam_x, 0.0, 1.7], [cam_x + 1.0, 0.0, 1.7], [0, 0, 1])
     cam = Camera(width, height, f, f, width / 2.0, height / 2.0, T[None])
     return AnchorScene("street_anchors", anchors, features, scaling, offsets, mlp, cam, k)

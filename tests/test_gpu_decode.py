@@ -134,3 +134,14 @@ def test_decode_rejects_bad_arguments():
     code = C.vpgs_decode_anchors(None, 0, ctypes.byref(a), ctypes.byref(mlp), ctypes.byref(cam), None,
                                  ctypes.byref(opts), ctypes.byref(out), None, None, None)
     assert code == 1
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_full_size_street_decode(bf16):
+    # 100,000 anchors, 1241x376 camera: the decode the benchmark times
+    sc = scenes.street_anchors()
+    ref = _oracle(sc, bf16)
+    _, _, _, out = _gpu(sc, bf16)
+    assert int(out["n"]) > 400_000
+    assert ref["flags"].mean() < (0.15 if bf16 else 0.02)
+    _compare_outputs(out, ref, ref["flags"], sc.k, 1e-5)

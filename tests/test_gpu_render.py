@@ -222,3 +222,30 @@ def test_full_size_room_sampled_rows():
     for k in GRAD_KEYS:
         assert_grad_close(grads[k], ref["d_" + k], k)
     assert_pose_close(dpose, ref["d_pose"])
+
+
+def test_batched_views_equal_separate_views():
+    sc = scenes.random_gaussians(3000, 160, 120, 140.0, seed=31, scale_range=(0.01, 0.1), n_views=4)
+    r, g, T, out = _gpu_forward(sc)
+    for v in range(4):
+        r1 = Renderer(intrinsics(sc), n_views=1)
+        o1 = _np(r1.forward(*g, T[v:v + 1].contiguous()))
+        for k in ("rgb", "depth", "alpha", "t_final", "n_contrib", "n_iter"):
+            assert np.array_equal(out[k][v:v + 1], o1[k]), (v, k)
+
+
+def test_full_size_batched_keyframes_sampled_rows():
+    # 2M Gaussians, 8 keyframes at 640x480 in one call, as timed by the benchmark
+    sc = scenes.batched_keyframes()
+    rows = [0, 239, 479]
+    views = [0, 7]
+    sub = scenes.GaussianScene("kf", sc.means, sc.scales, sc.quats, sc.opacities, sc.colors,
+                               scenes.Camera(640, 480, sc.camera.fx, sc.camera.fy, sc.camera.cx, sc.camera.cy,
+                                             sc.camera.T_cw[views]))
+    ref = oracle.render_scene(sub, rows=rows)
+    sel = np.zeros_like(ref["flags"])
+    sel[:, rows] = True
+    _, _, _, out = _gpu_forward(sc)
+    shown = {k: (np.where(sel[:, None], v[views], 0) if k == "rgb" else np.where(sel, v[views], 0))
+             for k, v in out.items()}
+    assert_images_close(shown, ref, ref["flags"] | ~sel, what="keyframes")
