@@ -336,6 +336,8 @@ def run_ours(a):
     # is capturable: no host sync, device-side counts); L2 flushed between replays
     graph_ms = None
     try:
+        if a.no_extras:
+            raise RuntimeError("skipped (--no-extras)")
         side = torch.cuda.Stream(device=dev)
         side.wait_stream(torch.cuda.current_stream(dev))
         with torch.cuda.stream(side):

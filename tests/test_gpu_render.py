@@ -56,7 +56,7 @@ def planes_ref(planes):
 
 def test_tile_counts_and_projection(planes, planes_ref):
     ref, _ = planes_ref
-    r = Renderer(intrinsics(planes))
+    r = Renderer(intrinsics(planes), tile_w=16, tile_h=16)  # the oracle's extents use 16x16 tiles
     g, T = scene_tensors(planes)
     p = {k: v.cpu().numpy() for k, v in r.project(*g, T).items()}
     ext = ref["extent"][0]
@@ -92,7 +92,7 @@ def test_backward_parity(planes, planes_ref):
     assert_pose_close(dpose, ref["d_pose"])
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (32, 8), (8, 32), (16, 8)])
+@pytest.mark.parametrize("tile", [(16, 16), (8, 16), (32, 8), (8, 32), (16, 8), (8, 8)])
 def test_tile_shape_does_not_change_the_image(planes, planes_ref, tile):
     ref, _ = planes_ref
     _, _, _, out = _gpu_forward(planes, tile_w=tile[0], tile_h=tile[1])
@@ -249,3 +249,18 @@ def test_full_size_batched_keyframes_sampled_rows():
     shown = {k: (np.where(sel[:, None], v[views], 0) if k == "rgb" else np.where(sel, v[views], 0))
              for k, v in out.items()}
     assert_images_close(shown, ref, ref["flags"] | ~sel, what="keyframes")
+
+
+@pytest.mark.parametrize("tile", [(8, 16), (16, 8)])
+def test_tile_counts_other_shapes(planes, tile):
+    from oracle.raster import Options, _t
+    opts = Options(tile_w=tile[0], tile_h=tile[1])
+    cam = planes.camera
+    pr = oracle.project(_t(planes.means), _t(planes.scales), _t(planes.quats), _t(cam.T_cw[0]),
+                        cam.fx, cam.fy, cam.cx, cam.cy, opts)
+    ext = oracle.extent(pr, planes.opacities, cam.width, cam.height, opts)
+    r = Renderer(intrinsics(planes), tile_w=tile[0], tile_h=tile[1])
+    g, T = scene_tensors(planes)
+    cnt = r.project(*g, T)["tile_count"][0].cpu().numpy()
+    mask = tile_count_mask(ext, planes.opacities)
+    assert np.array_equal(cnt[~mask], ext["count"][~mask])
