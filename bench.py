@@ -571,6 +571,10 @@ def fusion_rows(dev):
                                   f=1000.0, cam_x=495.0, mlp_seed=7)
             for i, x0 in enumerate((437.5, 490.0))]
     t = lambda a, dt=torch.float32: torch.tensor(a, dtype=dt, device=dev).contiguous()  # noqa: E731
+    # camera in the 10 m overlap, facing the facade, so both submaps are in view
+    T_np = scenes.look_at([495.0, 0.0, 1.7], [495.0, 10.0, 1.7], [0, 0, 1])
+    for sc in subs:
+        sc.camera.T_cw = T_np[None]
     cam = subs[0].camera
     T = t(cam.T_cw[0], torch.float64)
     r = Renderer(Intrinsics(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy), device=dev)
