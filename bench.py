@@ -63,6 +63,18 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """The largest value over all ranks (one MAX all-reduce; identity when not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    dev = device if (device is not None and dist.get_backend() == "nccl") else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -323,11 +335,8 @@ def run_ours(a):
     ms = timed(step, a.steps)
     t_wall1 = time.time()
     launches = C.vpgs_launch_count() - l0
-    ms_step = sum(ms) / len(ms)
+    ms_step = max_over_ranks(sum(ms) / len(ms), dev)
     if world > 1:
-        tt = torch.tensor([ms_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_step = float(tt.item())
         dist.barrier()
     C.check(r.stats().status, "timed renders")
     value_eager = P * world / (ms_step * 1e-3) / 1e6
@@ -355,11 +364,7 @@ def run_ours(a):
         t_wall0g = time.time()
         g_ms = timed(cg.replay, a.steps)
         t_wall1 = time.time()
-        graph_ms = sum(g_ms) / len(g_ms)
-        if world > 1:
-            tt = torch.tensor([graph_ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            graph_ms = float(tt.item())
+        graph_ms = max_over_ranks(sum(g_ms) / len(g_ms), dev)
         C.check(r.stats().status, "graph replays")
     except Exception as exc:  # reported; the eager number stands
         eager["graph_error"] = repr(exc)[:200]

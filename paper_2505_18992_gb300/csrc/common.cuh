@@ -221,8 +221,14 @@ struct RenderWs {
 
 // radix sort geometry
 constexpr int kSortThreads = 256;
-constexpr int kDepthSortItems = 4;  // keys per thread in the depth sort (1024 per block)
-constexpr int kTileSortItems = 16;  // keys per thread in the tile-id sort (4096 per block)
+#ifndef VPGS_DEPTH_SORT_ITEMS
+#define VPGS_DEPTH_SORT_ITEMS 4
+#endif
+#ifndef VPGS_TILE_SORT_ITEMS
+#define VPGS_TILE_SORT_ITEMS 16
+#endif
+constexpr int kDepthSortItems = VPGS_DEPTH_SORT_ITEMS;  // keys per thread in the depth sort
+constexpr int kTileSortItems = VPGS_TILE_SORT_ITEMS;    // keys per thread in the tile-id sort
 // radix pass kind per sort: one-sweep (decoupled look-back) or count/scan/scatter
 #ifndef VPGS_DEPTH_LOOKBACK
 #define VPGS_DEPTH_LOOKBACK 1

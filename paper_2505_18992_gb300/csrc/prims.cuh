@@ -529,7 +529,8 @@ inline cudaError_t radix_sort_pairs(const char *name, uint32_t *k0, uint32_t *v0
     *result_in_1 = (np & 1) != 0;
     if (np == 0 || n_cap == 0) return cudaSuccess;
     if (np > 4) return cudaErrorInvalidValue;
-    if (items != 4 && items != 8 && items != 16) return cudaErrorInvalidValue;
+    if (items != 4 && items != 8 && items != 16 && items != 32) return cudaErrorInvalidValue;
+    if (!lookback && items == 32) return cudaErrorInvalidValue;  // count/scatter kernels exist for 4..16
     const int64_t nb = sort_blocks(n_cap, items);
     cudaError_t e;
     uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
@@ -580,6 +581,9 @@ inline cudaError_t radix_sort_pairs(const char *name, uint32_t *k0, uint32_t *v0
                                           ki, vi, ko, vo, n_cap, n_dev, ps[p], hist + p * kRadix, ticket + p, lk, status));
         else if (items == 8)
             VPGS_LAUNCH(name, stream, radix_onesweep_kernel<8><<<(unsigned)nb, kSortThreads, 0, stream>>>(
+                                          ki, vi, ko, vo, n_cap, n_dev, ps[p], hist + p * kRadix, ticket + p, lk, status));
+        else if (items == 32)
+            VPGS_LAUNCH(name, stream, radix_onesweep_kernel<32><<<(unsigned)nb, kSortThreads, 0, stream>>>(
                                           ki, vi, ko, vo, n_cap, n_dev, ps[p], hist + p * kRadix, ticket + p, lk, status));
         else
             VPGS_LAUNCH(name, stream, radix_onesweep_kernel<16><<<(unsigned)nb, kSortThreads, 0, stream>>>(
