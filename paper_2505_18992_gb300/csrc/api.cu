@@ -77,12 +77,19 @@ bool make_layout(int64_t N, int V, const vpgs_camera *cam, const vpgs_render_opt
     const int64_t look_b = (int64_t)np_tile * sort_blocks(L.M_cap, kTileSortItems);
     L.sort_blocks_max = look_a > look_b ? look_a : look_b;
     L.off_sort_look = take(4 * kRadix * (size_t)L.sort_blocks_max);
-    // scans: visibility and offsets over V*N items, radix count matrices of 256 x blocks
+    // direct binning when the tile counters fit shared memory and the matrix fits its budget
+    const int64_t n_tiles_all = (int64_t)V * L.T;
+    L.bin_blocks = (VN1 + kBinRanks - 1) / kBinRanks;
+    const int64_t bin_entries = n_tiles_all * L.bin_blocks;
+    L.direct_bins = n_tiles_all <= kBinMaxTiles && (size_t)bin_entries * 4 <= kBinMaxBytes;
+    // scans: visibility and offsets over V*N items, radix count matrices, the bin matrix
     const int64_t cm = kRadix * std::max(sort_blocks(VN1, kDepthSortItems), sort_blocks(L.M_cap, kTileSortItems));
     L.scan_blocks_max = std::max(scan_blocks(VN1), scan_blocks(cm));
+    if (L.direct_bins) L.scan_blocks_max = std::max(L.scan_blocks_max, scan_blocks(bin_entries));
     L.off_scan_look = take(8 * (size_t)L.scan_blocks_max);
     L.off_g2d = take(4 * 10 * (size_t)VN1);
     L.off_posedf = take(4 * 24 * (size_t)V);
+    L.off_bins = L.direct_bins ? take(4 * (size_t)bin_entries) : 0;
     L.total = off;
     return true;
 }
@@ -110,6 +117,7 @@ RenderWs carve(void *base, const RenderLayout &L) {
     w.scan_look = reinterpret_cast<unsigned long long *>(b + L.off_scan_look);
     w.g2d = reinterpret_cast<float *>(b + L.off_g2d);
     w.posedf = reinterpret_cast<float *>(b + L.off_posedf);
+    w.bins = L.direct_bins ? reinterpret_cast<uint32_t *>(b + L.off_bins) : nullptr;
     return w;
 }
 

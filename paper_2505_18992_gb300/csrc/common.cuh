@@ -188,8 +188,10 @@ struct RenderLayout {
     // offsets in bytes
     size_t off_status, off_counters, off_rec, off_rect, off_tcount, off_scan_a, off_dkey0,
         off_dval0, off_dkey1, off_dval1, off_ikey0, off_ival0, off_ikey1, off_ival1, off_ranges,
-        off_sort_hist, off_sort_look, off_scan_look, off_g2d, off_posedf, total;
+        off_sort_hist, off_sort_look, off_scan_look, off_g2d, off_posedf, off_bins, total;
     int64_t sort_blocks_max, scan_blocks_max;
+    bool direct_bins;     // direct binning (else: stable radix sort of the instances by tile id)
+    int64_t bin_blocks;   // ceil(VN / kBinRanks)
 };
 
 // counters[] slots
@@ -199,7 +201,8 @@ enum {
     CNT_TICKET_A = 2,  // decoupled look-back tickets (reset before each use)
     CNT_TICKET_B = 3,  // 3..6: one ticket per sort pass
     CNT_WORK = 7,      // persistent-kernel work queue
-    CNT_N = 8
+    CNT_BIN_N = 8,     // length of the tile-count matrix of the direct binning
+    CNT_N = 12
 };
 
 struct RenderWs {
@@ -217,7 +220,13 @@ struct RenderWs {
     unsigned long long *scan_look;
     float *g2d;           // [VN,10] 2D gradients
     float *posedf;        // [V,24] poses as double-float pairs
+    uint32_t *bins;       // [V*T, ceil(VN/256)] tile-count matrix (direct binning), or null
 };
+
+// direct binning: depth-ranked Gaussians per bin block, and its limits
+constexpr int kBinRanks = 256;
+constexpr int kBinMaxTiles = 24 * 1024;                 // tile counters held in shared memory
+constexpr size_t kBinMaxBytes = size_t(512) << 20;      // tile-count matrix budget
 
 // radix sort geometry
 constexpr int kSortThreads = 256;

@@ -101,6 +101,133 @@ emit_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__ tcou
     }
 }
 
+// ---------------------------------------------------------------------------
+// Direct binning: the visible Gaussians are already in depth order, so tile
+// lists in depth order are a stable counting sort by tile id over that order.
+//   bin_count: per block of kBinRanks ranks, instances per tile (shared-memory
+//              counters), written tile-major: bins[t * nbk + b]
+//   scan:      exclusive scan of bins -> global slot of (tile t, block b)
+//   bin_place: one warp per block walks its instances in (rank, tile) order and
+//              places each at its tile's slot + its stable rank (match-any on
+//              the tile id); blocks also write the [start, end) of a slice of tiles
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBinRanks)
+bin_count_kernel(const uint32_t *__restrict__ dval, const uint2 *__restrict__ rect, const uint32_t *n_vis,
+                 int64_t N, int T, int tiles_x, int n_tiles, uint32_t *__restrict__ bins, uint32_t *bin_n) {
+    extern __shared__ uint32_t s_h[];
+    const int64_t nv = *n_vis;
+    const int64_t nbk = (nv + kBinRanks - 1) / kBinRanks;
+    const int64_t b = blockIdx.x;
+    const int tid = threadIdx.x;
+    if (b == 0 && tid == 0) *bin_n = (uint32_t)(nbk * n_tiles);
+    if (b >= nbk) return;
+    for (int t = tid; t < n_tiles; t += kBinRanks) s_h[t] = 0u;
+    __syncthreads();
+    const int64_t r = b * kBinRanks + tid;
+    if (r < nv) {
+        const uint32_t i = dval[r];
+        const uint32_t vb = (uint32_t)(i / N) * (uint32_t)T;
+        const uint2 rc = rect[i];
+        for (uint32_t ty = rc.y & 0xffffu; ty <= (rc.y >> 16); ++ty)
+            for (uint32_t tx = rc.x & 0xffffu; tx <= (rc.x >> 16); ++tx)
+                atomicAdd(&s_h[vb + ty * (uint32_t)tiles_x + tx], 1u);
+    }
+    __syncthreads();
+    for (int t = tid; t < n_tiles; t += kBinRanks) bins[(int64_t)t * nbk + b] = s_h[t];
+}
+
+__global__ void __launch_bounds__(32)
+bin_place_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__ tcount,
+                 const uint2 *__restrict__ rect, const uint32_t *n_vis, const uint32_t *n_inst, int64_t N,
+                 int T, int tiles_x, int n_tiles, const uint32_t *__restrict__ bins, int64_t M_cap,
+                 uint32_t *__restrict__ ival, uint2 *__restrict__ ranges, uint32_t *status) {
+    extern __shared__ uint32_t s_pos[];
+    __shared__ uint32_t s_off[kBinRanks + 1], s_id[kBinRanks], s_tx0[kBinRanks], s_w[kBinRanks],
+        s_ty0[kBinRanks], s_vb[kBinRanks];
+    const int64_t nv = *n_vis;
+    const int64_t nbk = (nv + kBinRanks - 1) / kBinRanks;
+    const int64_t b = blockIdx.x;
+    const int lane = threadIdx.x;
+    if (b >= nbk) return;
+    const uint32_t total = *n_inst;
+    if ((int64_t)total > M_cap) {
+        if (b == 0 && lane == 0) set_status(status, VPGS_ERR_CAPACITY);
+        return;
+    }
+    // [start, end) of this block's slice of tiles
+    const int64_t chunk = (n_tiles + nbk - 1) / nbk;
+    for (int64_t t = b * chunk + lane; t < min((int64_t)n_tiles, (b + 1) * chunk); t += 32) {
+        const uint32_t st = bins[t * nbk];
+        const uint32_t en = t + 1 < n_tiles ? bins[(t + 1) * nbk] : total;
+        ranges[t] = make_uint2(st, en);
+    }
+    for (int t = lane; t < n_tiles; t += 32) s_pos[t] = bins[(int64_t)t * nbk + b];
+    const int nb = (int)min((int64_t)kBinRanks, nv - b * kBinRanks);
+    // the block's ranks and their local instance offsets (warp scan, 8 per lane)
+    uint32_t run = 0;
+    uint32_t cnt8[kBinRanks / 32];
+#pragma unroll
+    for (int q = 0; q < kBinRanks / 32; ++q) {
+        const int i = lane * (kBinRanks / 32) + q;
+        uint32_t c = 0;
+        if (i < nb) {
+            const uint32_t id = dval[b * kBinRanks + i];
+            const uint2 rc = rect[id];
+            c = tcount[id];
+            s_id[i] = id;
+            s_tx0[i] = rc.x & 0xffffu;
+            s_w[i] = (rc.x >> 16) - (rc.x & 0xffffu) + 1u;
+            s_ty0[i] = rc.y & 0xffffu;
+            s_vb[i] = (uint32_t)(id / N) * (uint32_t)T;
+        }
+        cnt8[q] = c;
+        run += c;
+    }
+    uint32_t x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    uint32_t acc = x - run;
+#pragma unroll
+    for (int q = 0; q < kBinRanks / 32; ++q) {
+        s_off[lane * (kBinRanks / 32) + q] = acc;
+        acc += cnt8[q];
+    }
+    const uint32_t blk_total = __shfl_sync(0xffffffffu, x, 31);
+    __syncwarp();
+    // stable placement in (rank, tile) order
+    for (uint32_t e0 = 0; e0 < blk_total; e0 += 32) {
+        const uint32_t e = e0 + lane;
+        const bool valid = e < blk_total;
+        uint32_t t = 0xffffffe0u + lane;  // unique, never a tile id
+        uint32_t id = 0;
+        if (valid) {
+            int lo = 0, hi = nb - 1;  // last rank whose local start is <= e
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_off[mid] <= e) lo = mid;
+                else hi = mid - 1;
+            }
+            const uint32_t local = e - s_off[lo];
+            const uint32_t w = s_w[lo];
+            t = s_vb[lo] + (s_ty0[lo] + local / w) * (uint32_t)tiles_x + s_tx0[lo] + local % w;
+            id = s_id[lo];
+        }
+        const uint32_t m = __match_any_sync(0xffffffffu, t);
+        const uint32_t rk = __popc(m & lanemask_lt());
+        uint32_t pos = 0;
+        if (valid) pos = s_pos[t] + rk;
+        __syncwarp();
+        if (valid) {
+            if ((int64_t)pos < M_cap) ival[pos] = id;
+            if (rk == 0) s_pos[t] += __popc(m);
+        }
+        __syncwarp();
+    }
+}
+
 __global__ void tile_ranges_kernel(const uint32_t *__restrict__ keys, int64_t cap, const uint32_t *n_dev,
                                    uint32_t n_tiles, uint2 *ranges) {
     int64_t n = min(cap, (int64_t)*n_dev);
@@ -142,6 +269,32 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
                          ws.scan_look);
     if (e != cudaSuccess) return e;
     const uint32_t *dval = in1 ? ws.dval[1] : ws.dval[0];
+    const int n_tiles = V * cam.T;
+    if (L.direct_bins) {
+        // 3. + 4. + 5. direct binning (count, scan, stable placement + tile ranges)
+        e = cudaMemsetAsync(ws.ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);
+        if (e != cudaSuccess) return e;
+        const size_t hsm = sizeof(uint32_t) * (size_t)n_tiles;
+        if (hsm > 48 * 1024) {  // per device and call: cheap, and right on every GPU of the process
+            cudaFuncSetAttribute((const void *)bin_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
+            cudaFuncSetAttribute((const void *)bin_place_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
+        }
+        uint32_t *bin_n = ws.counters + CNT_BIN_N;
+        VPGS_LAUNCH("bin_count", s,
+                    bin_count_kernel<<<(unsigned)L.bin_blocks, kBinRanks, hsm, s>>>(
+                        dval, ws.rect, n_vis, L.N, cam.T, cam.tiles_x, n_tiles, ws.bins, bin_n));
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = launch_scan("scan_bins", CountsLoad{ws.bins}, CountsStore{ws.bins}, (int64_t)n_tiles * L.bin_blocks,
+                        bin_n, ws.counters + CNT_TICKET_A, ws.scan_look, n_inst, ws.status, s);
+        if (e != cudaSuccess) return e;
+        VPGS_LAUNCH("bin_place", s,
+                    bin_place_kernel<<<(unsigned)L.bin_blocks, 32, hsm, s>>>(
+                        dval, ws.tcount, ws.rect, n_vis, n_inst, L.N, cam.T, cam.tiles_x, n_tiles, ws.bins,
+                        L.M_cap, ws.ival[0], ws.ranges, ws.status));
+        *sorted_buf = 0;
+        return cudaGetLastError();
+    }
     uint32_t *inst_off = in1 ? ws.dkey[0] : ws.dkey[1];  // the depth-sort buffer not holding the result
     // 3. instance offsets, then emission
     e = launch_scan("scan_offsets", CountLoad{ws.tcount, dval}, OffsetStore{inst_off}, L.VN, n_vis,
