@@ -81,7 +81,7 @@ bool make_layout(int64_t N, int V, const vpgs_camera *cam, const vpgs_render_opt
     const int64_t n_tiles_all = (int64_t)V * L.T;
     L.bin_blocks = (VN1 + kBinRanks - 1) / kBinRanks;
     const int64_t bin_entries = n_tiles_all * L.bin_blocks;
-    L.direct_bins = n_tiles_all <= kBinMaxTiles && (size_t)bin_entries * 4 <= kBinMaxBytes;
+    L.direct_bins = VPGS_DIRECT_BINS && n_tiles_all <= kBinMaxTiles && (size_t)bin_entries * 4 <= kBinMaxBytes;
     // scans: visibility and offsets over V*N items, radix count matrices, the bin matrix
     const int64_t cm = kRadix * std::max(sort_blocks(VN1, kDepthSortItems), sort_blocks(L.M_cap, kTileSortItems));
     L.scan_blocks_max = std::max(scan_blocks(VN1), scan_blocks(cm));

@@ -224,7 +224,10 @@ struct RenderWs {
 };
 
 // direct binning: depth-ranked Gaussians per bin block, and its limits
-constexpr int kBinRanks = 256;
+#ifndef VPGS_DIRECT_BINS
+#define VPGS_DIRECT_BINS 1
+#endif
+constexpr int kBinRanks = 512;
 constexpr int kBinMaxTiles = 24 * 1024;                 // tile counters held in shared memory
 constexpr size_t kBinMaxBytes = size_t(512) << 20;      // tile-count matrix budget
 

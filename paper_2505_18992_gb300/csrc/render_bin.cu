@@ -161,11 +161,13 @@ bin_place_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__
         const uint32_t en = t + 1 < n_tiles ? bins[(t + 1) * nbk] : total;
         ranges[t] = make_uint2(st, en);
     }
-    for (int t = lane; t < n_tiles; t += 32) s_pos[t] = bins[(int64_t)t * nbk + b];
+    // a tile's global slot is read on first touch (most tiles are never touched by a block)
+    constexpr uint32_t kUnread = 0xffffffffu;
+    for (int t = lane; t < n_tiles; t += 32) s_pos[t] = kUnread;
     const int nb = (int)min((int64_t)kBinRanks, nv - b * kBinRanks);
     // the block's ranks and their local instance offsets (warp scan, 8 per lane)
     uint32_t run = 0;
-    uint32_t cnt8[kBinRanks / 32];
+    uint32_t cnt8[kBinRanks / 32];  // ranks per lane: kBinRanks / 32
 #pragma unroll
     for (int q = 0; q < kBinRanks / 32; ++q) {
         const int i = lane * (kBinRanks / 32) + q;
@@ -217,12 +219,18 @@ bin_place_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__
         }
         const uint32_t m = __match_any_sync(0xffffffffu, t);
         const uint32_t rk = __popc(m & lanemask_lt());
-        uint32_t pos = 0;
-        if (valid) pos = s_pos[t] + rk;
+        const int leader = __ffs(m) - 1;
+        uint32_t base = 0;
+        if (valid && rk == 0) {
+            base = s_pos[t];
+            if (base == kUnread) base = bins[(int64_t)t * nbk + b];
+        }
+        base = __shfl_sync(0xffffffffu, base, leader);
         __syncwarp();
         if (valid) {
+            const uint32_t pos = base + rk;
             if ((int64_t)pos < M_cap) ival[pos] = id;
-            if (rk == 0) s_pos[t] += __popc(m);
+            if (rk == 0) s_pos[t] = base + __popc(m);
         }
         __syncwarp();
     }
