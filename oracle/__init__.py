@@ -5,6 +5,7 @@ and the benchmark's CPU-baseline and reference arms.  The CUDA product path
 never imports, links or runs anything in this package, and this package imports
 nothing from the product.
 """
-from .raster import Options, Margins, render, render_scene, project, extent, quat_to_rotmat  # noqa: F401
+from .raster import (Options, Margins, render, render_scene, project, extent, tile_cover,  # noqa: F401
+                     rect_min_quadratic, quat_to_rotmat)
 from .decode import decode, decode_scene, bf16_round, n_mlp_params, flatten_mlp, MLP_ORDER  # noqa: F401,E402
 from .pose import pose_step, se3_exp  # noqa: F401,E402

@@ -6,7 +6,7 @@ path never does.  It shares no code with the CUDA path.
 
 What it computes (the paper renders with 3D Gaussian Splatting, Sec. I and
 Sec. II, and states neither the projection nor the compositing rules, so every
-rule below is the reading written out in the design notes, items C1-C12):
+rule below is a reading of it, stated here in full):
 
   * covariance   Sigma = R(q) diag(s)^2 R(q)^T, q=(w,x,y,z) normalised (Sec. III-A,
                  "follow 3D-GS" for the rotation head)
@@ -27,6 +27,11 @@ rule below is the reading written out in the design notes, items C1-C12):
                  of this very code; the camera-pose gradient is with respect to a
                  left perturbation T_cw <- Exp(xi) T_cw at xi = 0, ordered
                  (rho_x, rho_y, rho_z, phi_x, phi_y, phi_z).
+
+  * tile cover   (binning, not part of the image) a Gaussian is listed in a
+                 tile when its alpha_min ellipse d^T Sigma'^-1 d <= 2 ln(o/alpha_min)
+                 meets the rectangle spanned by the tile's pixel centres, widened
+                 by the extent margin 1e-5 r + 2e-3 px on each side.
 
 The oracle composites every pixel against every Gaussian in depth order; the
 only shortcut is a candidate filter that drops Gaussians whose (widened)
@@ -163,6 +168,85 @@ def extent(proj, opac: np.ndarray, width: int, height: int, opts: Options):
             "edges": np.stack([ex0, ex1, ey0, ey1], 1),
             "pix": np.stack([x0, x1, y0, y1], 1),
             "tiles": np.stack([tx0, tx1, ty0, ty1], 1), "count": count}
+
+
+def rect_min_quadratic(a, b, c, x0, x1, y0, y1):
+    """Minimum of q(x, y) = a x^2 + 2 b x y + c y^2 over [x0, x1] x [y0, y1].
+
+    q is convex (a > 0, ac > b^2) with its unconstrained minimum 0 at the
+    origin.  When the origin lies outside the box, the minimum is on the box
+    boundary; along each edge q is a one-dimensional convex quadratic whose
+    minimiser (stationary point clamped to the edge) is taken in closed form.
+    """
+    a, b, c, x0, x1, y0, y1 = np.broadcast_arrays(*(np.asarray(t, np.float64)
+                                                     for t in (a, b, c, x0, x1, y0, y1)))
+    best = np.full(a.shape, np.inf)
+    for xe in (x0, x1):                       # vertical edges: y free
+        ys = np.clip(-b * xe / c, y0, y1)
+        best = np.minimum(best, a * xe * xe + 2.0 * b * xe * ys + c * ys * ys)
+    for ye in (y0, y1):                       # horizontal edges: x free
+        xs = np.clip(-b * ye / a, x0, x1)
+        best = np.minimum(best, a * xs * xs + 2.0 * b * xs * ye + c * ye * ye)
+    inside = (x0 <= 0.0) & (x1 >= 0.0) & (y0 <= 0.0) & (y1 >= 0.0)
+    return np.where(inside, 0.0, best)
+
+
+def tile_cover(proj, opac: np.ndarray, width: int, height: int, opts: Options,
+               tol_px: float = 1e-3, tol_rel: float = 1e-5):
+    """Tiles each Gaussian is listed in (the tile-cover rule of the header).
+
+    Every tile of the widened pixel rectangle is tested: the Mahalanobis
+    distance s of the (widened) pixel-centre rectangle is sqrt(min q) with
+    q = d^T Sigma'^-1 d; the tile counts when s <= sqrt(k), k = 2 ln(o/alpha_min).
+    Returns per Gaussian the count and a flag set when some tile lies within
+    tol_px pixels (Mahalanobis tol_px / sqrt(lambda_min(Sigma'))) or tol_rel
+    relative of the threshold, where an FP32 evaluation may decide otherwise.
+    """
+    u = proj["u"].detach().numpy()
+    v = proj["v"].detach().numpy()
+    z = proj["z"].detach().numpy()
+    cov = proj["cov"].detach().numpy()
+    con = proj["conic"].detach().numpy()
+    o = np.asarray(opac, np.float64)
+    n = len(u)
+    count = np.zeros(n, np.int64)
+    flag = np.zeros(n, bool)
+    live = (z > opts.near_z) & (o >= opts.alpha_min)
+    idx = np.nonzero(live)[0]
+    if idx.size == 0:
+        return {"count": count, "flags": flag}
+    k = 2.0 * np.log(o[idx] / opts.alpha_min)
+    A, B, C = cov[idx, 0], cov[idx, 1], cov[idx, 2]
+    rx, ry = np.sqrt(k * A), np.sqrt(k * C)
+    mx, my = 1e-5 * rx + 2e-3, 1e-5 * ry + 2e-3
+    x0 = np.maximum(np.ceil(u[idx] - rx - mx - 0.5), 0).astype(np.int64)
+    x1 = np.minimum(np.floor(u[idx] + rx + mx - 0.5), width - 1).astype(np.int64)
+    y0 = np.maximum(np.ceil(v[idx] - ry - my - 0.5), 0).astype(np.int64)
+    y1 = np.minimum(np.floor(v[idx] + ry + my - 0.5), height - 1).astype(np.int64)
+    ok = (x0 <= x1) & (y0 <= y1)
+    tw, th = opts.tile_w, opts.tile_h
+    ntx = np.where(ok, x1 // tw - x0 // tw + 1, 0)
+    nty = np.where(ok, y1 // th - y0 // th + 1, 0)
+    per = ntx * nty
+    g = np.repeat(np.arange(idx.size), per)              # one entry per (Gaussian, tile)
+    local = np.arange(per.sum()) - np.repeat(np.cumsum(per) - per, per)
+    tx = x0[g] // tw + local % ntx[g]
+    ty = y0[g] // th + local // ntx[g]
+    # the tile's pixel-centre rectangle (clipped to the image), relative to (u, v), widened
+    rx0 = tx * tw + 0.5 - u[idx][g] - mx[g]
+    rx1 = np.minimum(tx * tw + tw, width) - 0.5 - u[idx][g] + mx[g]
+    ry0 = ty * th + 0.5 - v[idx][g] - my[g]
+    ry1 = np.minimum(ty * th + th, height) - 0.5 - v[idx][g] + my[g]
+    q = rect_min_quadratic(con[idx, 0][g], con[idx, 1][g], con[idx, 2][g], rx0, rx1, ry0, ry1)
+    s, sk = np.sqrt(q), np.sqrt(k)[g]
+    hit = s <= sk
+    lam_min = 0.5 * (A + C) - np.sqrt(0.25 * (A - C) ** 2 + B * B)
+    tol = tol_rel * sk + tol_px / np.sqrt(lam_min[g])
+    near = np.abs(s - sk) <= tol
+    count[idx] = np.bincount(g, weights=hit, minlength=idx.size).astype(np.int64)
+    flag[idx] = np.bincount(g, weights=near, minlength=idx.size) > 0
+    flag |= live & (np.abs(o - opts.alpha_min) <= 1e-4 * opts.alpha_min)
+    return {"count": count, "flags": flag}
 
 
 def _composite_block(px, py, cand, g2, opts: Options, margins: Margins, want_flags=True):

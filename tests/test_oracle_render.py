@@ -121,6 +121,91 @@ def test_tile_counts_by_enumerating_pixels():
         assert ext["count"][i] == len(tiles)
 
 
+def test_rect_min_quadratic_separable_closed_form_and_sampling():
+    rng = np.random.default_rng(11)
+    for _ in range(100):
+        # b = 0: the minimum is a dx^2 + c dy^2, dx and dy the distances of 0 to the intervals
+        a, c = rng.uniform(0.1, 3.0, 2)
+        x0, x1 = np.sort(rng.uniform(-3, 3, 2))
+        y0, y1 = np.sort(rng.uniform(-3, 3, 2))
+        dx, dy = max(x0, -x1, 0.0), max(y0, -y1, 0.0)
+        assert oracle.rect_min_quadratic(a, 0.0, c, x0, x1, y0, y1) == pytest.approx(
+            a * dx * dx + c * dy * dy, rel=1e-14, abs=1e-15)
+        # general positive-definite form: dense sampling bounds the minimum from above,
+        # and from below within the largest change of q over one grid step
+        L = rng.normal(size=(2, 2))
+        M = L @ L.T + 0.05 * np.eye(2)
+        got = oracle.rect_min_quadratic(M[0, 0], M[0, 1], M[1, 1], x0, x1, y0, y1)
+        X, Y = np.meshgrid(np.linspace(x0, x1, 401), np.linspace(y0, y1, 401))
+        qs = (M[0, 0] * X * X + 2 * M[0, 1] * X * Y + M[1, 1] * Y * Y).min()
+        step = max(x1 - x0, y1 - y0) / 400.0
+        grad = 2.0 * np.abs(M).sum() * 3.0
+        assert got <= qs + 1e-12
+        assert qs - got <= grad * step
+
+
+def _proj_dict(u, v, cov, z=1.0):
+    A, B, C = (np.asarray(t, np.float64) for t in cov)
+    det = A * C - B * B
+    return {"u": _t(u), "v": _t(v), "z": _t(np.full(np.shape(u), z)),
+            "cov": _t(np.stack([A, B, C], -1)), "conic": _t(np.stack([C / det, -B / det, A / det], -1))}
+
+
+def test_tile_cover_hand_worked_circle():
+    # sigma = 2 px, o = 0.5: r = 2 sqrt(2 ln(127.5)) = 6.228 px around (21.5, 11.5) on
+    # 16x8 tiles.  The bounding box spans tile columns 0-1 and rows 0-2 (6 tiles); the
+    # corner tiles (0, 0) and (0, 2) are 7.2 and 7.8 px from the centre, the other
+    # four 0, 4, 5 and 6 px away.
+    pr = _proj_dict([21.5], [11.5], ([4.0], [0.0], [4.0]))
+    opts = Options(tile_w=16, tile_h=8)
+    cov = oracle.tile_cover(pr, np.array([0.5]), 64, 32, opts)
+    assert cov["count"][0] == 4 and not cov["flags"][0]
+    ext = oracle.extent(pr, np.array([0.5]), 64, 32, opts)
+    assert ext["count"][0] == 6
+
+
+def test_tile_cover_against_pixels_and_dense_sampling():
+    sc = scenes.random_gaussians(80, 150, 90, 120.0, seed=9, scale_range=(0.01, 0.4))
+    opts = Options(tile_w=16, tile_h=8)
+    pr = oracle.project(_t(sc.means), _t(sc.scales), _t(sc.quats), _t(sc.camera.T_cw[0]),
+                        120.0, 120.0, 75.0, 45.0, opts)
+    ext = oracle.extent(pr, sc.opacities, 150, 90, opts)
+    cov = oracle.tile_cover(pr, sc.opacities, 150, 90, opts)
+    u, v = pr["u"].numpy(), pr["v"].numpy()
+    con = pr["conic"].numpy()
+    tighter = 0
+    for i in range(80):
+        if not ext["live"][i]:
+            assert cov["count"][i] == 0
+            continue
+        a, b, c = con[i]
+        k = 2 * math.log(sc.opacities[i] / opts.alpha_min)
+        qf = lambda X, Y: a * X * X + 2 * b * X * Y + c * Y * Y  # noqa: E731
+        # tiles holding a pixel centre with alpha >= alpha_min are all listed
+        X, Y = np.meshgrid(np.arange(150) + 0.5 - u[i], np.arange(90) + 0.5 - v[i])
+        ys, xs = np.nonzero(qf(X, Y) <= k)
+        lattice = {(x // 16, y // 8) for x, y in zip(xs, ys)}
+        assert cov["count"][i] >= len(lattice)
+        # dense samples of each (widened) tile rectangle: a sampled hit is a hit, and a
+        # tile without one is a hit only when its sampled minimum is within one step of k
+        r = max(ext["rx"][i], ext["ry"][i])
+        m = 1e-5 * r + 2e-3
+        sampled, near = 0, 0
+        for ty in range(12):
+            for tx in range(10):
+                xa, xb = tx * 16 + 0.5 - u[i] - m, min(tx * 16 + 16, 150) - 0.5 - u[i] + m
+                ya, yb = ty * 8 + 0.5 - v[i] - m, min(ty * 8 + 8, 90) - 0.5 - v[i] + m
+                Xs, Ys = np.meshgrid(np.linspace(xa, xb, 121), np.linspace(ya, yb, 61))
+                qmin = qf(Xs, Ys).min()
+                step = max((xb - xa) / 120, (yb - ya) / 60)
+                bound = 2 * (abs(a) + 2 * abs(b) + abs(c)) * (abs(xa) + abs(xb) + abs(ya) + abs(yb)) * step
+                sampled += qmin <= k
+                near += k < qmin <= k + bound
+        assert sampled <= cov["count"][i] <= sampled + near
+        tighter += cov["count"][i] < ext["count"][i]
+    assert tighter > 0  # the ellipse test drops bounding-box tiles
+
+
 def test_two_gaussians_hand_worked_and_depth_order():
     # Two isotropic Gaussians centred on the same pixel centre.  At that pixel
     # alpha_i = o_i, so C = o1 c1 + (1 - o1) o2 c2 with the nearer one first.
