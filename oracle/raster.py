@@ -30,8 +30,10 @@ rule below is a reading of it, stated here in full):
 
   * tile cover   (binning, not part of the image) a Gaussian is listed in a
                  tile when its alpha_min ellipse d^T Sigma'^-1 d <= 2 ln(o/alpha_min)
-                 meets the rectangle spanned by the tile's pixel centres, widened
-                 by the extent margin 1e-5 r + 2e-3 px on each side.
+                 meets one of the tile's pixel-centre columns: the segment from
+                 the first to the last pixel-centre row of the tile at the
+                 column's centre x, widened by the extent margins 1e-5 r + 2e-3 px
+                 (1e-5 rx + 2e-3 across, 1e-5 ry + 2e-3 along).
 
 The oracle composites every pixel against every Gaussian in depth order; the
 only shortcut is a candidate filter that drops Gaussians whose (widened)
@@ -195,18 +197,18 @@ def tile_cover(proj, opac: np.ndarray, width: int, height: int, opts: Options,
                tol_px: float = 1e-3, tol_rel: float = 1e-5):
     """Tiles each Gaussian is listed in (the tile-cover rule of the header).
 
-    Every tile of the widened pixel rectangle is tested: the Mahalanobis
-    distance s of the (widened) pixel-centre rectangle is sqrt(min q) with
-    q = d^T Sigma'^-1 d; the tile counts when s <= sqrt(k), k = 2 ln(o/alpha_min).
-    Returns per Gaussian the count and a flag set when some tile lies within
-    tol_px pixels (Mahalanobis tol_px / sqrt(lambda_min(Sigma'))) or tol_rel
-    relative of the threshold, where an FP32 evaluation may decide otherwise.
+    Every tile of the widened pixel rectangle is tested column by column: the
+    Mahalanobis distance of a (widened) column segment is s = sqrt(min q),
+    q = d^T Sigma'^-1 d, and the tile counts when some column has
+    s <= sqrt(k), k = 2 ln(o/alpha_min).  Returns per Gaussian the count and a
+    flag set when some column lies within tol_px pixels (Mahalanobis
+    tol_px / sqrt(lambda_min(Sigma'))) or tol_rel relative of the threshold,
+    where an FP32 evaluation may decide otherwise.
     """
-    u = proj["u"].detach().numpy()
-    v = proj["v"].detach().numpy()
-    z = proj["z"].detach().numpy()
-    cov = proj["cov"].detach().numpy()
-    con = proj["conic"].detach().numpy()
+    def arr(t):
+        return t.detach().numpy() if torch.is_tensor(t) else np.asarray(t, np.float64)
+
+    u, v, z, cov, con = (arr(proj[key]) for key in ("u", "v", "z", "cov", "conic"))
     o = np.asarray(opac, np.float64)
     n = len(u)
     count = np.zeros(n, np.int64)
@@ -232,19 +234,23 @@ def tile_cover(proj, opac: np.ndarray, width: int, height: int, opts: Options,
     local = np.arange(per.sum()) - np.repeat(np.cumsum(per) - per, per)
     tx = x0[g] // tw + local % ntx[g]
     ty = y0[g] // th + local // ntx[g]
-    # the tile's pixel-centre rectangle (clipped to the image), relative to (u, v), widened
-    rx0 = tx * tw + 0.5 - u[idx][g] - mx[g]
-    rx1 = np.minimum(tx * tw + tw, width) - 0.5 - u[idx][g] + mx[g]
-    ry0 = ty * th + 0.5 - v[idx][g] - my[g]
-    ry1 = np.minimum(ty * th + th, height) - 0.5 - v[idx][g] + my[g]
-    q = rect_min_quadratic(con[idx, 0][g], con[idx, 1][g], con[idx, 2][g], rx0, rx1, ry0, ry1)
-    s, sk = np.sqrt(q), np.sqrt(k)[g]
-    hit = s <= sk
+    ncol = np.minimum(tx * tw + tw, width) - tx * tw      # pixel columns of the tile
+    t = np.repeat(np.arange(g.size), ncol)                 # one entry per (Gaussian, tile, column)
+    col = tx[t] * tw + np.arange(t.size) - np.repeat(np.cumsum(ncol) - ncol, ncol)
+    gt = g[t]
+    # the column's pixel-centre segment (rows clipped to the image), relative to (u, v), widened
+    cx0 = col + 0.5 - u[idx][gt] - mx[gt]
+    cx1 = col + 0.5 - u[idx][gt] + mx[gt]
+    cy0 = ty[t] * th + 0.5 - v[idx][gt] - my[gt]
+    cy1 = np.minimum(ty[t] * th + th, height) - 0.5 - v[idx][gt] + my[gt]
+    q = rect_min_quadratic(con[idx, 0][gt], con[idx, 1][gt], con[idx, 2][gt], cx0, cx1, cy0, cy1)
+    s, sk = np.sqrt(q), np.sqrt(k)[gt]
     lam_min = 0.5 * (A + C) - np.sqrt(0.25 * (A - C) ** 2 + B * B)
-    tol = tol_rel * sk + tol_px / np.sqrt(lam_min[g])
-    near = np.abs(s - sk) <= tol
-    count[idx] = np.bincount(g, weights=hit, minlength=idx.size).astype(np.int64)
-    flag[idx] = np.bincount(g, weights=near, minlength=idx.size) > 0
+    tol = tol_rel * sk + tol_px / np.sqrt(lam_min[gt])
+    tile_hit = np.bincount(t, weights=s <= sk, minlength=g.size) > 0
+    tile_near = np.bincount(t, weights=np.abs(s - sk) <= tol, minlength=g.size) > 0
+    count[idx] = np.bincount(g, weights=tile_hit, minlength=idx.size).astype(np.int64)
+    flag[idx] = np.bincount(g, weights=tile_near, minlength=idx.size) > 0
     flag |= live & (np.abs(o - opts.alpha_min) <= 1e-4 * opts.alpha_min)
     return {"count": count, "flags": flag}
 

@@ -154,8 +154,8 @@ def _proj_dict(u, v, cov, z=1.0):
 def test_tile_cover_hand_worked_circle():
     # sigma = 2 px, o = 0.5: r = 2 sqrt(2 ln(127.5)) = 6.228 px around (21.5, 11.5) on
     # 16x8 tiles.  The bounding box spans tile columns 0-1 and rows 0-2 (6 tiles); the
-    # corner tiles (0, 0) and (0, 2) are 7.2 and 7.8 px from the centre, the other
-    # four 0, 4, 5 and 6 px away.
+    # nearest pixel-centre column segments of the corner tiles (0, 0) and (0, 2) are
+    # 7.2 and 7.8 px from the centre, those of the other four 0, 4, 5 and 6 px away.
     pr = _proj_dict([21.5], [11.5], ([4.0], [0.0], [4.0]))
     opts = Options(tile_w=16, tile_h=8)
     cov = oracle.tile_cover(pr, np.array([0.5]), 64, 32, opts)
@@ -186,19 +186,22 @@ def test_tile_cover_against_pixels_and_dense_sampling():
         ys, xs = np.nonzero(qf(X, Y) <= k)
         lattice = {(x // 16, y // 8) for x, y in zip(xs, ys)}
         assert cov["count"][i] >= len(lattice)
-        # dense samples of each (widened) tile rectangle: a sampled hit is a hit, and a
-        # tile without one is a hit only when its sampled minimum is within one step of k
-        r = max(ext["rx"][i], ext["ry"][i])
-        m = 1e-5 * r + 2e-3
+        # dense samples of each tile's (widened) pixel-centre columns: a sampled hit is
+        # a hit, and a tile without one is a hit only when its sampled minimum is
+        # within one sampling step of k
+        mx = 1e-5 * ext["rx"][i] + 2e-3
+        my = 1e-5 * ext["ry"][i] + 2e-3
         sampled, near = 0, 0
         for ty in range(12):
+            ya, yb = ty * 8 + 0.5 - v[i] - my, min(ty * 8 + 8, 90) - 0.5 - v[i] + my
             for tx in range(10):
-                xa, xb = tx * 16 + 0.5 - u[i] - m, min(tx * 16 + 16, 150) - 0.5 - u[i] + m
-                ya, yb = ty * 8 + 0.5 - v[i] - m, min(ty * 8 + 8, 90) - 0.5 - v[i] + m
-                Xs, Ys = np.meshgrid(np.linspace(xa, xb, 121), np.linspace(ya, yb, 61))
+                cols = np.arange(tx * 16, min(tx * 16 + 16, 150)) + 0.5 - u[i]
+                Xs = (cols[:, None, None] + np.linspace(-mx, mx, 5)[None, :, None]).reshape(-1, 1)
+                Ys = np.linspace(ya, yb, 401)[None, :]
                 qmin = qf(Xs, Ys).min()
-                step = max((xb - xa) / 120, (yb - ya) / 60)
-                bound = 2 * (abs(a) + 2 * abs(b) + abs(c)) * (abs(xa) + abs(xb) + abs(ya) + abs(yb)) * step
+                step = max(mx / 2, (yb - ya) / 400)
+                reach = np.abs(Xs).max() + max(abs(ya), abs(yb))
+                bound = 2 * (abs(a) + 2 * abs(b) + abs(c)) * reach * step
                 sampled += qmin <= k
                 near += k < qmin <= k + bound
         assert sampled <= cov["count"][i] <= sampled + near
