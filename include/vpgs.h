@@ -54,7 +54,8 @@ typedef enum {
     VPGS_ERR_NONFINITE = 3,   /* device: a NaN/Inf input was seen */
     VPGS_ERR_TIMEOUT = 4,     /* device: a bounded look-back wait ran out */
     VPGS_ERR_CUDA = 5,        /* a CUDA runtime call failed */
-    VPGS_ERR_UNSUPPORTED = 6
+    VPGS_ERR_UNSUPPORTED = 6,
+    VPGS_ERR_INTERNAL = 7     /* device: an internal consistency check failed (a bug) */
 } vpgs_status;
 
 /* Pinhole intrinsics and image size, shared by every view of a call (host struct). */
@@ -69,7 +70,7 @@ typedef struct {
  * The paper cites 3D Gaussian Splatting for all of these (Sec. I, Sec. II) and
  * states none of them. */
 typedef struct {
-    int32_t tile_w, tile_h;   /* tile_w in {4,8,16,32}; tile_h even; tile_w*tile_h a multiple of 64, <= 1024 */
+    int32_t tile_w, tile_h;   /* tile_w in {4,8,16,32}; tile_h even; tile_w*tile_h a multiple of 64, <= 512 */
     float alpha_min;          /* skip a Gaussian at a pixel when alpha < alpha_min */
     float alpha_max;          /* alpha = min(alpha_max, o exp(-d^T Sigma'^-1 d / 2)) */
     float t_min;              /* stop before the first Gaussian that would take T below t_min */
@@ -77,7 +78,18 @@ typedef struct {
     float near_z;             /* Gaussians with camera z <= near_z are dropped */
     float bg[3];              /* C = sum_i alpha_i T_i c_i + T_final bg */
     int32_t persistent_ctas;  /* 0 = one CTA per tile; >0 = that many persistent CTAs per SM */
+    int32_t flags;            /* VPGS_RENDER_* bits below; 0 by default */
 } vpgs_render_opts;
+
+/* vpgs_render_bwd: take the projection and tile lists from the workspace
+ * instead of recomputing them.  Valid when the last render call on this
+ * workspace was vpgs_render_fwd with the same inputs (same workspace, arrays,
+ * camera, poses and options other than flags and persistent_ctas), with their
+ * contents unchanged since; backward calls in between are allowed.  The
+ * library records the arguments of each forward call per workspace and
+ * recomputes everything when they do not match; it cannot see a change made in
+ * place to the contents of the arrays, so the caller must not make one. */
+#define VPGS_RENDER_REUSE_BINNING 1
 
 /* Gaussians, structure of arrays, float32 (device).
  *   means [n,3], scales [n,3] (linear, > 0), quats [n,4] (w,x,y,z; normalised
@@ -140,7 +152,8 @@ vpgs_status vpgs_render_fwd(void *ws, size_t ws_bytes, const vpgs_gaussians *g,
                             const vpgs_render_opts *opts, const vpgs_images *out, vpgs_stream stream);
 
 /* Backward pass of vpgs_render_fwd.  It recomputes the projection, binning and
- * per-tile sort from the inputs and stores none of them.  It reads
+ * per-tile sort from the inputs, or, with VPGS_RENDER_REUSE_BINNING in
+ * opts->flags, takes them from the forward call's workspace.  It reads
  * fwd->t_final and fwd->n_iter from the forward call with identical inputs and
  * options, then back-propagates
  *   dL_drgb [V,3,H,W], dL_ddepth [V,H,W], dL_dalpha [V,H,W] (each may be NULL = 0)
@@ -162,8 +175,11 @@ vpgs_status vpgs_render_bwd(void *ws, size_t ws_bytes, const vpgs_gaussians *g,
 /* Projection stage of vpgs_render_fwd alone: per (view, Gaussian) EWA
  * projection and tile extent, written out for inspection (device outputs,
  * each may be NULL):
- *   tile_count [V,N] int32 (tiles the Gaussian is binned into; 0 = culled),
- *   tile_rect [V,N,4] int32 (tx0, tx1, ty0, ty1, inclusive), mean2d [V,N,2]
+ *   tile_count [V,N] int32 (tiles the Gaussian is binned into; 0 = culled):
+ *     the tiles whose pixel-centre rectangle, widened by 1e-5 r + 2e-3 px,
+ *     meets the ellipse d^T Sigma'^-1 d <= 2 ln(o / alpha_min),
+ *   tile_rect [V,N,4] int32 (tx0, tx1, ty0, ty1, inclusive: the bounding box
+ *     of that ellipse, widened the same way, in tiles), mean2d [V,N,2]
  *   float32 (u, v), depth [V,N] float32 (camera z), conic [V,N,3] float32
  *   (a, b, c of Sigma'^-1 = [[a,b],[b,c]]).
  * Entries of culled Gaussians other than tile_count are left unchanged. */

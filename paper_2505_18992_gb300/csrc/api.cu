@@ -2,6 +2,9 @@
 // the launch sequence.  Decoder entry points live in decode.cu.
 #include <string.h>
 
+#include <mutex>
+#include <vector>
+
 #include "internal.h"
 #include "prims.cuh"
 
@@ -24,12 +27,14 @@ bool valid_opts(const vpgs_render_opts *o) {
     if (o->tile_h < 2 || o->tile_h > 64) return false;
     // VPGS_PIX pixels per thread (rows y and y + tile_h/VPGS_PIX): whole warps
     const int B = o->tile_w * o->tile_h;
-    if (o->tile_h % 2 != 0 || B % 64 != 0 || B > 1024 || o->tile_h % VPGS_PIX != 0) return false;
+    // one compositing thread per VPGS_PIX pixels, at most 512 threads per tile
+    if (o->tile_h % 2 != 0 || B % 64 != 0 || B / VPGS_PIX > 512 || o->tile_h % VPGS_PIX != 0) return false;
     if (!(o->alpha_min > 0.f && o->alpha_min < 1.f)) return false;
     if (!(o->alpha_max > o->alpha_min && o->alpha_max < 1.f)) return false;
     if (!(o->t_min > 0.f && o->t_min < 1.f)) return false;
     if (!(o->dilation >= 0.f) || !(o->near_z >= 0.f)) return false;
     if (o->persistent_ctas < 0 || o->persistent_ctas > 32) return false;
+    if ((o->flags & ~VPGS_RENDER_REUSE_BINNING) != 0) return false;
     return true;
 }
 
@@ -77,19 +82,13 @@ bool make_layout(int64_t N, int V, const vpgs_camera *cam, const vpgs_render_opt
     const int64_t look_b = (int64_t)np_tile * sort_blocks(L.M_cap, kTileSortItems);
     L.sort_blocks_max = look_a > look_b ? look_a : look_b;
     L.off_sort_look = take(4 * kRadix * (size_t)L.sort_blocks_max);
-    // direct binning when the tile counters fit shared memory and the matrix fits its budget
-    const int64_t n_tiles_all = (int64_t)V * L.T;
-    L.bin_blocks = (VN1 + kBinRanks - 1) / kBinRanks;
-    const int64_t bin_entries = n_tiles_all * L.bin_blocks;
-    L.direct_bins = VPGS_DIRECT_BINS && n_tiles_all <= kBinMaxTiles && (size_t)bin_entries * 4 <= kBinMaxBytes;
-    // scans: visibility and offsets over V*N items, radix count matrices, the bin matrix
+    // scans: visibility and offsets over V*N items, radix count matrices
     const int64_t cm = kRadix * std::max(sort_blocks(VN1, kDepthSortItems), sort_blocks(L.M_cap, kTileSortItems));
     L.scan_blocks_max = std::max(scan_blocks(VN1), scan_blocks(cm));
-    if (L.direct_bins) L.scan_blocks_max = std::max(L.scan_blocks_max, scan_blocks(bin_entries));
     L.off_scan_look = take(8 * (size_t)L.scan_blocks_max);
     L.off_g2d = take(4 * 10 * (size_t)VN1);
     L.off_posedf = take(4 * 24 * (size_t)V);
-    L.off_bins = L.direct_bins ? take(4 * (size_t)bin_entries) : 0;
+    L.off_cover = take(sizeof(Cover) * (size_t)VN1);
     L.total = off;
     return true;
 }
@@ -117,7 +116,7 @@ RenderWs carve(void *base, const RenderLayout &L) {
     w.scan_look = reinterpret_cast<unsigned long long *>(b + L.off_scan_look);
     w.g2d = reinterpret_cast<float *>(b + L.off_g2d);
     w.posedf = reinterpret_cast<float *>(b + L.off_posedf);
-    w.bins = L.direct_bins ? reinterpret_cast<uint32_t *>(b + L.off_bins) : nullptr;
+    w.cover = reinterpret_cast<Cover *>(b + L.off_cover);
     return w;
 }
 
@@ -163,7 +162,8 @@ vpgs_status setup(void *ws, size_t ws_bytes, const vpgs_gaussians *g, const vpgs
     if (cap < 1 || !make_layout(g->n, V, cam, opts, cap, S.L)) return VPGS_ERR_INVALID_ARG;
     S.ws = carve(ws, S.L);
     S.cam = CamParams{cam->width, cam->height, cam->fx, cam->fy, cam->cx, cam->cy,
-                      opts->tile_w, opts->tile_h, S.L.tiles_x, S.L.tiles_y, S.L.T};
+                      opts->tile_w, opts->tile_h, S.L.tiles_x, S.L.tiles_y, S.L.T,
+                      __builtin_ctz((unsigned)opts->tile_w)};
     S.o = OptParams{opts->alpha_min, opts->alpha_max, opts->t_min, opts->dilation, opts->near_z,
                     opts->bg[0], opts->bg[1], opts->bg[2]};
     S.g = GaussIn{g->means, g->scales, g->quats, g->opacities, g->colors, g->n, g->n_dev};
@@ -171,6 +171,79 @@ vpgs_status setup(void *ws, size_t ws_bytes, const vpgs_gaussians *g, const vpgs
 }
 
 vpgs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA; }
+
+// Arguments of the last call that left a complete projection + tile lists in a
+// workspace.  A backward with VPGS_RENDER_REUSE_BINNING reuses them only when
+// its own arguments match.
+struct BinTag {
+    const void *ws;
+    size_t ws_bytes;
+    vpgs_gaussians g;
+    vpgs_camera cam;
+    const double *T_cw;
+    int32_t V;
+    vpgs_render_opts o;  // flags and persistent_ctas cleared
+};
+
+std::mutex g_tag_mu;
+std::vector<BinTag> g_tags;
+constexpr size_t kMaxTags = 256;
+
+BinTag make_tag(const void *ws, size_t ws_bytes, const vpgs_gaussians *g, const vpgs_camera *cam,
+                const double *T_cw, int32_t V, const vpgs_render_opts *o) {
+    BinTag t;
+    memset(&t, 0, sizeof(t));
+    t.ws = ws;
+    t.ws_bytes = ws_bytes;
+    t.g = *g;
+    t.cam = *cam;
+    t.T_cw = T_cw;
+    t.V = V;
+    t.o = *o;
+    t.o.flags = 0;
+    t.o.persistent_ctas = 0;
+    return t;
+}
+
+bool same_tag(const BinTag &a, const BinTag &b) {
+    const bool g = a.g.means == b.g.means && a.g.scales == b.g.scales && a.g.quats == b.g.quats &&
+                   a.g.opacities == b.g.opacities && a.g.colors == b.g.colors && a.g.n == b.g.n &&
+                   a.g.n_dev == b.g.n_dev;
+    const bool c = a.cam.width == b.cam.width && a.cam.height == b.cam.height && a.cam.fx == b.cam.fx &&
+                   a.cam.fy == b.cam.fy && a.cam.cx == b.cam.cx && a.cam.cy == b.cam.cy;
+    const bool o = a.o.tile_w == b.o.tile_w && a.o.tile_h == b.o.tile_h && a.o.alpha_min == b.o.alpha_min &&
+                   a.o.alpha_max == b.o.alpha_max && a.o.t_min == b.o.t_min &&
+                   a.o.dilation == b.o.dilation && a.o.near_z == b.o.near_z && a.o.bg[0] == b.o.bg[0] &&
+                   a.o.bg[1] == b.o.bg[1] && a.o.bg[2] == b.o.bg[2];
+    return a.ws == b.ws && a.ws_bytes == b.ws_bytes && g && c && o && a.T_cw == b.T_cw && a.V == b.V;
+}
+
+void tag_set(const BinTag &t) {
+    std::lock_guard<std::mutex> lk(g_tag_mu);
+    for (auto &x : g_tags)
+        if (x.ws == t.ws) {
+            x = t;
+            return;
+        }
+    if (g_tags.size() >= kMaxTags) g_tags.erase(g_tags.begin());
+    g_tags.push_back(t);
+}
+
+void tag_clear(const void *ws) {
+    std::lock_guard<std::mutex> lk(g_tag_mu);
+    for (size_t i = 0; i < g_tags.size(); ++i)
+        if (g_tags[i].ws == ws) {
+            g_tags.erase(g_tags.begin() + (long)i);
+            return;
+        }
+}
+
+bool tag_matches(const BinTag &t) {
+    std::lock_guard<std::mutex> lk(g_tag_mu);
+    for (const auto &x : g_tags)
+        if (x.ws == t.ws) return same_tag(x, t);
+    return false;
+}
 
 }  // namespace
 
@@ -187,6 +260,7 @@ void vpgs_render_opts_default(vpgs_render_opts *o) {
     o->near_z = 0.2f;
     o->bg[0] = o->bg[1] = o->bg[2] = 0.f;
     o->persistent_ctas = 0;
+    o->flags = 0;
 }
 
 size_t vpgs_render_workspace_bytes(int64_t max_gaussians, int32_t n_views, const vpgs_camera *cam,
@@ -204,12 +278,15 @@ vpgs_status vpgs_render_fwd(void *ws, size_t ws_bytes, const vpgs_gaussians *g,
     vpgs_status st = setup(ws, ws_bytes, g, cam, T_cw, n_views, opts, S);
     if (st != VPGS_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    tag_clear(ws);
     cudaError_t e = cudaMemsetAsync(ws, 0, S.L.off_counters + 4 * CNT_N, s);
-    if (e == cudaSuccess) e = launch_preprocess_fwd(S.g, T_cw, n_views, S.cam, S.o, S.ws, false, s);
+    // the 2D gradient slots of visible Gaussians start at zero for a backward that reuses this call
+    if (e == cudaSuccess) e = launch_preprocess_fwd(S.g, T_cw, n_views, S.cam, S.o, S.ws, true, s);
     int buf = 0;
-    if (e == cudaSuccess) e = build_tile_lists(S.g, n_views, S.cam, S.ws, S.L, &buf, s);
+    if (e == cudaSuccess) e = build_tile_lists(S.g, n_views, S.cam, S.ws, S.L, &buf, nullptr, s);
     if (e == cudaSuccess)
         e = launch_composite_fwd(S.ws, S.ws.ival[buf], n_views, S.cam, S.o, *out, opts->persistent_ctas, s);
+    if (e == cudaSuccess) tag_set(make_tag(ws, ws_bytes, g, cam, T_cw, n_views, opts));
     return cuda_status(e);
 }
 
@@ -227,16 +304,29 @@ vpgs_status vpgs_render_bwd(void *ws, size_t ws_bytes, const vpgs_gaussians *g,
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     GaussGrad gg{nullptr, nullptr, nullptr, nullptr, nullptr};
     if (grads) gg = GaussGrad{grads->means, grads->scales, grads->quats, grads->opacities, grads->colors};
-    cudaError_t e = cudaMemsetAsync(ws, 0, S.L.off_counters + 4 * CNT_N, s);
-    // recompute projection, binning and per-tile sort (nothing is kept from the forward call)
-    if (e == cudaSuccess) e = launch_preprocess_fwd(S.g, T_cw, n_views, S.cam, S.o, S.ws, true, s);
+    if (!grads && !dL_dpose) return VPGS_OK;  // nothing to compute
+    const BinTag tag = make_tag(ws, ws_bytes, g, cam, T_cw, n_views, opts);
     int buf = 0;
-    if (e == cudaSuccess) e = build_tile_lists(S.g, n_views, S.cam, S.ws, S.L, &buf, s);
+    const uint32_t *vis = nullptr;
+    cudaError_t e;
+    if ((opts->flags & VPGS_RENDER_REUSE_BINNING) && tag_matches(tag)) {
+        // the forward's projection and lists stand; its status word is kept, so an
+        // error it recorded stops this pass too
+        e = cudaSuccess;
+        tile_list_buffers(S.ws, S.L, &buf, &vis);
+    } else {
+        // recompute projection, binning and per-tile sort
+        e = cudaMemsetAsync(ws, 0, S.L.off_counters + 4 * CNT_N, s);
+        if (e == cudaSuccess) e = launch_preprocess_fwd(S.g, T_cw, n_views, S.cam, S.o, S.ws, true, s);
+        if (e == cudaSuccess) e = build_tile_lists(S.g, n_views, S.cam, S.ws, S.L, &buf, &vis, s);
+        if (e == cudaSuccess) tag_set(tag);
+        else tag_clear(ws);
+    }
     if (e == cudaSuccess)
         e = launch_composite_bwd(S.ws, S.ws.ival[buf], n_views, S.cam, S.o, *fwd, dL_drgb, dL_ddepth,
                                  dL_dalpha, opts->persistent_ctas, s);
     if (e == cudaSuccess && (grads || dL_dpose))
-        e = launch_preprocess_bwd(S.g, T_cw, n_views, S.cam, S.o, S.ws, gg, dL_dpose, s);
+        e = launch_preprocess_bwd(S.g, T_cw, n_views, S.cam, S.o, S.ws, gg, dL_dpose, vis, s);
     return cuda_status(e);
 }
 
@@ -249,6 +339,7 @@ vpgs_status vpgs_render_project(void *ws, size_t ws_bytes, const vpgs_gaussians 
     vpgs_status st = setup(ws, ws_bytes, g, cam, T_cw, n_views, opts, S);
     if (st != VPGS_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    tag_clear(ws);
     cudaError_t e = cudaMemsetAsync(ws, 0, S.L.off_counters + 4 * CNT_N, s);
     if (e == cudaSuccess) e = launch_preprocess_fwd(S.g, T_cw, n_views, S.cam, S.o, S.ws, false, s);
     if (e == cudaSuccess)
@@ -290,6 +381,7 @@ const char *vpgs_status_string(vpgs_status s) {
         case VPGS_ERR_TIMEOUT: return "bounded device wait ran out";
         case VPGS_ERR_CUDA: return "CUDA error";
         case VPGS_ERR_UNSUPPORTED: return "unsupported";
+        case VPGS_ERR_INTERNAL: return "internal consistency check failed";
     }
     return "unknown status";
 }

@@ -13,22 +13,19 @@
 
 // Compositing launch geometry (compile-time tuning knobs):
 //   VPGS_PIX    pixels per thread (rows y and y + tile_h/VPGS_PIX)
-//   VPGS_CHUNK  Gaussians evaluated together before the forward's sequential blend
-//   VPGS_GSTEP  Gaussians per step of the backward loop (1 or 2)
 #ifndef VPGS_PIX
 #define VPGS_PIX 1
-#endif
-#ifndef VPGS_CHUNK
-#define VPGS_CHUNK 1
-#endif
-#ifndef VPGS_GSTEP
-#define VPGS_GSTEP 1
 #endif
 //   VPGS_BWD_ACC how the backward combines per-warp sums of a Gaussian's 2D
 //                gradient: 0 = one global atomic per warp, 1 = per-warp shared
 //                slots summed per batch, 2 = shared-memory atomics per batch
 #ifndef VPGS_BWD_ACC
 #define VPGS_BWD_ACC 0
+#endif
+//   VPGS_BWD_RCP 1: the backward takes one approximate reciprocal of 1 - alpha
+//                per blended pair (relative error ~1e-7 per step), 0: IEEE divisions
+#ifndef VPGS_BWD_RCP
+#define VPGS_BWD_RCP 1
 #endif
 
 namespace vpgs {
@@ -146,13 +143,15 @@ VPGS_D void quat_to_rot(float w, float x, float y, float z, float R[9]) {
 // ---------------------------------------------------------------------------
 // per-(view, Gaussian) screen-space record: 4 x float4 = 64 bytes
 //   r0 = (u_hi, v_hi, u_lo, v_lo)   image mean as a double-float pair
-//   r1 = (w1x, w1y, w2x, w2y)       whitening rows: d^T Sigma'^-1 d = (w1.d)^2 + (w2.d)^2
+//   r1 = (w1x, w1y, w2x, w2y)       whitening rows times sqrt(log2(e)/2):
+//                                   (w1.d)^2 + (w2.d)^2 = log2(e)/2 d^T Sigma'^-1 d
 //   r2 = (opacity, z, r, g)
 //   r3 = (b, rx, ry, kq)            conservative pixel half-extents (alpha >= alpha_min
 //                                   is impossible farther than this from the mean) and
 //                                   kq = 2 ln(o / alpha_min), the largest quadratic form
 //                                   at which alpha >= alpha_min is possible
-// The whitening rows are the eigenvectors of Sigma' scaled by 1/sqrt(lambda),
+// The whitening rows are the eigenvectors of Sigma' scaled by 1/sqrt(lambda) (and
+// by sqrt(log2(e)/2), so that alpha needs a single ex2),
 // which evaluates the quadratic form without the cancellation the
 // (a dx^2 + 2 b dx dy + c dy^2) form suffers on elongated Gaussians.
 // ---------------------------------------------------------------------------
@@ -165,14 +164,70 @@ struct PairEval {
     float t1, t2, G, alpha;
 };
 
+// exp(-q/2) = 2^(-q log2(e)/2): the factor rides in the whitening rows
+constexpr float kRowScale = 0.84932180028801907f;     // sqrt(log2(e) / 2)
+constexpr float kInvExp2Half = 1.38629436111989061f;  // 2 ln 2
+
+VPGS_D float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 VPGS_D PairEval eval_pair(float dx, float dy, float w1x, float w1y, float w2x, float w2y,
                           float opac, float alpha_max) {
     PairEval e;
     e.t1 = fmaf(w1x, dx, w1y * dy);
     e.t2 = fmaf(w2x, dx, w2y * dy);
-    e.G = __expf(-0.5f * fmaf(e.t1, e.t1, e.t2 * e.t2));
+    e.G = ex2_approx(-fmaf(e.t1, e.t1, e.t2 * e.t2));
     e.alpha = fminf(alpha_max, opac * e.G);
     return e;
+}
+
+// ---------------------------------------------------------------------------
+// Tile cover.  A Gaussian is listed in a tile when its alpha_min ellipse
+// d^T Sigma'^-1 d <= kq (kq = 2 ln(o / alpha_min)) meets the rectangle of the
+// tile's pixel centres widened by the extent margins (mx, my).  With
+// Sigma' = [[A, B], [B, C]] the ellipse at row offset y spans
+//   x = beta y -/+ sqrt(g1 - g2 y^2),  beta = B/C, g1 = kq det/C, g2 = det/C^2,
+// for |y| <= ry = sqrt(kq C); its leftmost point sits at y = yL = -B sqrt(kq/A)
+// and its rightmost at -yL.  x_min(y) is convex and x_max(y) concave, so over a
+// band of rows the x extent is reached at yL (resp. -yL) clamped into the band.
+// The counting pass (preprocess) stores the spans themselves when the box has
+// at most kCoverRows tile rows, else these parameters; the emitting pass then
+// walks the rows with the same function in round-to-nearest intrinsics, so
+// both see identical spans.
+// ---------------------------------------------------------------------------
+constexpr int kCoverRows = 8;
+struct Cover {
+    float4 a;  // ry, my, yL, beta          | packed spans of rows 0-3
+    float4 b;  // g1, g2, mx, 0             | packed spans of rows 4-7
+};
+// packed span of one tile row: first tile column | last << 16 (first > last: empty)
+constexpr uint32_t kEmptySpan = 0xffffu;
+
+// Tile columns [x, y] of tile row ty (x > y: none) within [tx_lo, tx_hi].
+VPGS_D int2 cover_row(const Cover &cv, float u_hi, float u_lo, float v_hi, float v_lo, int ty, int tx_lo,
+                      int tx_hi, int tw_shift, int tile_h, int W, int H) {
+    const int y_first = ty * tile_h;
+    const int y_last = min(y_first + tile_h, H) - 1;
+    float ya = __fsub_rn(__fsub_rn(__fsub_rn((float)y_first + 0.5f, v_hi), v_lo), cv.a.y);
+    float yb = __fadd_rn(__fsub_rn(__fsub_rn((float)y_last + 0.5f, v_hi), v_lo), cv.a.y);
+    ya = fmaxf(ya, -cv.a.x);
+    yb = fminf(yb, cv.a.x);
+    if (!(ya <= yb)) return make_int2(1, 0);
+    const float yl = fminf(fmaxf(cv.a.z, ya), yb);
+    const float yr = fminf(fmaxf(-cv.a.z, ya), yb);
+    const float wl = __fsqrt_rn(fmaxf(__fsub_rn(cv.b.x, __fmul_rn(cv.b.y, __fmul_rn(yl, yl))), 0.f));
+    const float wr = __fsqrt_rn(fmaxf(__fsub_rn(cv.b.x, __fmul_rn(cv.b.y, __fmul_rn(yr, yr))), 0.f));
+    const float xmin = __fsub_rn(__fsub_rn(__fmul_rn(cv.a.w, yl), wl), cv.b.z);
+    const float xmax = __fadd_rn(__fadd_rn(__fmul_rn(cv.a.w, yr), wr), cv.b.z);
+    const float u0 = __fsub_rn(u_hi, 0.5f);
+    const float lx = fmaxf(__fadd_rn(__fadd_rn(u0, xmin), u_lo), -1.f);
+    const float hx = fminf(__fadd_rn(__fadd_rn(u0, xmax), u_lo), (float)W);
+    const int x0 = max(0, (int)ceilf(lx)), x1 = min(W - 1, (int)floorf(hx));
+    if (x0 > x1) return make_int2(1, 0);
+    return make_int2(max(x0 >> tw_shift, tx_lo), min(x1 >> tw_shift, tx_hi));
 }
 
 // ---------------------------------------------------------------------------
@@ -188,10 +243,8 @@ struct RenderLayout {
     // offsets in bytes
     size_t off_status, off_counters, off_rec, off_rect, off_tcount, off_scan_a, off_dkey0,
         off_dval0, off_dkey1, off_dval1, off_ikey0, off_ival0, off_ikey1, off_ival1, off_ranges,
-        off_sort_hist, off_sort_look, off_scan_look, off_g2d, off_posedf, off_bins, total;
+        off_sort_hist, off_sort_look, off_scan_look, off_g2d, off_posedf, off_cover, total;
     int64_t sort_blocks_max, scan_blocks_max;
-    bool direct_bins;     // direct binning (else: stable radix sort of the instances by tile id)
-    int64_t bin_blocks;   // ceil(VN / kBinRanks)
 };
 
 // counters[] slots
@@ -201,7 +254,6 @@ enum {
     CNT_TICKET_A = 2,  // decoupled look-back tickets (reset before each use)
     CNT_TICKET_B = 3,  // 3..6: one ticket per sort pass
     CNT_WORK = 7,      // persistent-kernel work queue
-    CNT_BIN_N = 8,     // length of the tile-count matrix of the direct binning
     CNT_N = 12
 };
 
@@ -220,16 +272,8 @@ struct RenderWs {
     unsigned long long *scan_look;
     float *g2d;           // [VN,10] 2D gradients
     float *posedf;        // [V,24] poses as double-float pairs
-    uint32_t *bins;       // [V*T, ceil(VN/256)] tile-count matrix (direct binning), or null
+    Cover *cover;         // [VN] row-wise tile-cover parameters of visible Gaussians
 };
-
-// direct binning: depth-ranked Gaussians per bin block, and its limits
-#ifndef VPGS_DIRECT_BINS
-#define VPGS_DIRECT_BINS 1
-#endif
-constexpr int kBinRanks = 512;
-constexpr int kBinMaxTiles = 24 * 1024;                 // tile counters held in shared memory
-constexpr size_t kBinMaxBytes = size_t(512) << 20;      // tile-count matrix budget
 
 // radix sort geometry
 constexpr int kSortThreads = 256;

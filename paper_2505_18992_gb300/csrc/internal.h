@@ -12,6 +12,7 @@ struct CamParams {
     int W, H;
     float fx, fy, cx, cy;
     int tile_w, tile_h, tiles_x, tiles_y, T;  // T = tiles per view
+    int tw_shift;                             // log2(tile_w)
 };
 
 struct OptParams {
@@ -40,12 +41,15 @@ cudaError_t launch_export_projection(const RenderWs &ws, int64_t VN, int32_t *ti
                                      cudaStream_t s);
 cudaError_t launch_preprocess_bwd(const GaussIn &g, const double *T_cw, int V, const CamParams &cam,
                                   const OptParams &o, const RenderWs &ws, const GaussGrad &gg,
-                                  double *dpose, cudaStream_t s);
+                                  double *dpose, const uint32_t *vis, cudaStream_t s);
 
 // render_bin.cu: visibility compaction, depth sort, instance emission, tile
 // sort and tile ranges.  On return ws.ival[*sorted_buf] holds the tile lists.
 cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, const RenderWs &ws,
-                             const RenderLayout &L, int *sorted_buf, cudaStream_t s);
+                             const RenderLayout &L, int *sorted_buf, const uint32_t **vis_list,
+                             cudaStream_t s);
+// Where build_tile_lists leaves its results for a layout (host only, no launch).
+void tile_list_buffers(const RenderWs &ws, const RenderLayout &L, int *sorted_buf, const uint32_t **vis_list);
 
 // render_comp.cu
 cudaError_t launch_composite_fwd(const RenderWs &ws, const uint32_t *ival, int V,

@@ -5,7 +5,8 @@
 //      camera depth (positive floats order like their bits); ties keep index
 //      order, i.e. (view, Gaussian) order
 //   3. scan of the tile counts in depth order, then a block-cooperative emit
-//      of each Gaussian's (global tile id, id) instances at its offset
+//      of each Gaussian's (global tile id, id) instances at its offset; the
+//      tiles are those of the row-wise tile cover counted by the projection
 //   4. stable radix sort of the instances by global tile id (only the bits a
 //      tile id needs); instances stay in depth order inside each tile
 //   5. [start, end) of every tile from the sorted keys
@@ -49,16 +50,21 @@ struct OffsetStore {
 // Emits the (global tile id, record) instances of 256 consecutive depth-ranked
 // Gaussians per block.  The block's instances are spread evenly over its
 // threads; each finds its Gaussian by binary search over the block's local
-// offsets, so a Gaussian covering thousands of tiles does not serialise.
+// offsets, so a Gaussian covering thousands of tiles does not serialise, and
+// then its tile by walking the Gaussian's tile rows with the same row-span
+// function that counted them.
 constexpr int kEmitThreads = 256;
 
 __global__ void __launch_bounds__(kEmitThreads)
 emit_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__ tcount,
             const uint32_t *__restrict__ inst_off, const uint2 *__restrict__ rect,
-            const uint32_t *n_vis, int64_t N, int64_t M_cap, int T, int tiles_x,
-            uint32_t *__restrict__ ikey, uint32_t *__restrict__ ival, uint32_t *status) {
-    __shared__ uint32_t s_start[kEmitThreads], s_id[kEmitThreads], s_w[kEmitThreads];
-    __shared__ uint32_t s_tx0[kEmitThreads], s_ty0[kEmitThreads], s_vb[kEmitThreads];
+            const Rec *__restrict__ rec, const Cover *__restrict__ cover, const uint32_t *n_vis,
+            int64_t N, int64_t M_cap, CamParams cam, uint32_t *__restrict__ ikey,
+            uint32_t *__restrict__ ival, uint32_t *status) {
+    __shared__ uint32_t s_start[kEmitThreads], s_id[kEmitThreads], s_vb[kEmitThreads];
+    __shared__ uint2 s_rect[kEmitThreads];
+    __shared__ float4 s_uv[kEmitThreads];
+    __shared__ Cover s_cv[kEmitThreads];
     __shared__ uint32_t s_total;
     const int64_t nv = *n_vis;
     const int64_t r0 = (int64_t)blockIdx.x * kEmitThreads;
@@ -71,13 +77,12 @@ emit_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__ tcou
         const uint32_t id = dval[r];
         const uint32_t cnt = tcount[id];
         const uint32_t off = inst_off[r] - base;
-        const uint2 rc = rect[id];
         s_start[tid] = off;
         s_id[tid] = id;
-        s_tx0[tid] = rc.x & 0xffffu;
-        s_w[tid] = (rc.x >> 16) - (rc.x & 0xffffu) + 1u;
-        s_ty0[tid] = rc.y & 0xffffu;
-        s_vb[tid] = (uint32_t)(id / N) * (uint32_t)T;
+        s_rect[tid] = rect[id];
+        s_uv[tid] = rec[id].r0;
+        s_cv[tid] = cover[id];
+        s_vb[tid] = (uint32_t)(id / N) * (uint32_t)cam.T;
         if (tid == nb - 1) s_total = off + cnt;
     }
     __syncthreads();
@@ -93,146 +98,48 @@ emit_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__ tcou
             if (s_start[mid] <= e) lo = mid;
             else hi = mid - 1;
         }
-        const uint32_t local = e - s_start[lo];
-        const uint32_t w = s_w[lo];
-        const uint32_t ty = s_ty0[lo] + local / w, tx = s_tx0[lo] + local % w;
-        ikey[base + e] = s_vb[lo] + ty * (uint32_t)tiles_x + tx;
-        ival[base + e] = s_id[lo];
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Direct binning: the visible Gaussians are already in depth order, so tile
-// lists in depth order are a stable counting sort by tile id over that order.
-//   bin_count: per block of kBinRanks ranks, instances per tile (shared-memory
-//              counters), written tile-major: bins[t * nbk + b]
-//   scan:      exclusive scan of bins -> global slot of (tile t, block b)
-//   bin_place: one warp per block walks its instances in (rank, tile) order and
-//              places each at its tile's slot + its stable rank (match-any on
-//              the tile id); blocks also write the [start, end) of a slice of tiles
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBinRanks)
-bin_count_kernel(const uint32_t *__restrict__ dval, const uint2 *__restrict__ rect, const uint32_t *n_vis,
-                 int64_t N, int T, int tiles_x, int n_tiles, uint32_t *__restrict__ bins, uint32_t *bin_n) {
-    extern __shared__ uint32_t s_h[];
-    const int64_t nv = *n_vis;
-    const int64_t nbk = (nv + kBinRanks - 1) / kBinRanks;
-    const int64_t b = blockIdx.x;
-    const int tid = threadIdx.x;
-    if (b == 0 && tid == 0) *bin_n = (uint32_t)(nbk * n_tiles);
-    if (b >= nbk) return;
-    for (int t = tid; t < n_tiles; t += kBinRanks) s_h[t] = 0u;
-    __syncthreads();
-    const int64_t r = b * kBinRanks + tid;
-    if (r < nv) {
-        const uint32_t i = dval[r];
-        const uint32_t vb = (uint32_t)(i / N) * (uint32_t)T;
-        const uint2 rc = rect[i];
-        for (uint32_t ty = rc.y & 0xffffu; ty <= (rc.y >> 16); ++ty)
-            for (uint32_t tx = rc.x & 0xffffu; tx <= (rc.x >> 16); ++tx)
-                atomicAdd(&s_h[vb + ty * (uint32_t)tiles_x + tx], 1u);
-    }
-    __syncthreads();
-    for (int t = tid; t < n_tiles; t += kBinRanks) bins[(int64_t)t * nbk + b] = s_h[t];
-}
-
-__global__ void __launch_bounds__(32)
-bin_place_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__ tcount,
-                 const uint2 *__restrict__ rect, const uint32_t *n_vis, const uint32_t *n_inst, int64_t N,
-                 int T, int tiles_x, int n_tiles, const uint32_t *__restrict__ bins, int64_t M_cap,
-                 uint32_t *__restrict__ ival, uint2 *__restrict__ ranges, uint32_t *status) {
-    extern __shared__ uint32_t s_pos[];
-    __shared__ uint32_t s_off[kBinRanks + 1], s_id[kBinRanks], s_tx0[kBinRanks], s_w[kBinRanks],
-        s_ty0[kBinRanks], s_vb[kBinRanks];
-    const int64_t nv = *n_vis;
-    const int64_t nbk = (nv + kBinRanks - 1) / kBinRanks;
-    const int64_t b = blockIdx.x;
-    const int lane = threadIdx.x;
-    if (b >= nbk) return;
-    const uint32_t total = *n_inst;
-    if ((int64_t)total > M_cap) {
-        if (b == 0 && lane == 0) set_status(status, VPGS_ERR_CAPACITY);
-        return;
-    }
-    // [start, end) of this block's slice of tiles
-    const int64_t chunk = (n_tiles + nbk - 1) / nbk;
-    for (int64_t t = b * chunk + lane; t < min((int64_t)n_tiles, (b + 1) * chunk); t += 32) {
-        const uint32_t st = bins[t * nbk];
-        const uint32_t en = t + 1 < n_tiles ? bins[(t + 1) * nbk] : total;
-        ranges[t] = make_uint2(st, en);
-    }
-    // a tile's global slot is read on first touch (most tiles are never touched by a block)
-    constexpr uint32_t kUnread = 0xffffffffu;
-    for (int t = lane; t < n_tiles; t += 32) s_pos[t] = kUnread;
-    const int nb = (int)min((int64_t)kBinRanks, nv - b * kBinRanks);
-    // the block's ranks and their local instance offsets (warp scan, 8 per lane)
-    uint32_t run = 0;
-    uint32_t cnt8[kBinRanks / 32];  // ranks per lane: kBinRanks / 32
+        uint32_t local = e - s_start[lo];
+        const uint2 rc = s_rect[lo];
+        const float4 uv = s_uv[lo];
+        const Cover cv = s_cv[lo];
+        const int tx_lo = (int)(rc.x & 0xffffu), tx_hi = (int)(rc.x >> 16);
+        const int ty_lo = (int)(rc.y & 0xffffu), ty_hi = (int)(rc.y >> 16);
+        uint32_t key = 0xffffffffu;
+        if (ty_hi - ty_lo + 1 <= kCoverRows) {
+            // spans stored by the counting pass
+            const uint32_t pk[kCoverRows] = {__float_as_uint(cv.a.x), __float_as_uint(cv.a.y),
+                                             __float_as_uint(cv.a.z), __float_as_uint(cv.a.w),
+                                             __float_as_uint(cv.b.x), __float_as_uint(cv.b.y),
+                                             __float_as_uint(cv.b.z), __float_as_uint(cv.b.w)};
 #pragma unroll
-    for (int q = 0; q < kBinRanks / 32; ++q) {
-        const int i = lane * (kBinRanks / 32) + q;
-        uint32_t c = 0;
-        if (i < nb) {
-            const uint32_t id = dval[b * kBinRanks + i];
-            const uint2 rc = rect[id];
-            c = tcount[id];
-            s_id[i] = id;
-            s_tx0[i] = rc.x & 0xffffu;
-            s_w[i] = (rc.x >> 16) - (rc.x & 0xffffu) + 1u;
-            s_ty0[i] = rc.y & 0xffffu;
-            s_vb[i] = (uint32_t)(id / N) * (uint32_t)T;
-        }
-        cnt8[q] = c;
-        run += c;
-    }
-    uint32_t x = run;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    uint32_t acc = x - run;
-#pragma unroll
-    for (int q = 0; q < kBinRanks / 32; ++q) {
-        s_off[lane * (kBinRanks / 32) + q] = acc;
-        acc += cnt8[q];
-    }
-    const uint32_t blk_total = __shfl_sync(0xffffffffu, x, 31);
-    __syncwarp();
-    // stable placement in (rank, tile) order
-    for (uint32_t e0 = 0; e0 < blk_total; e0 += 32) {
-        const uint32_t e = e0 + lane;
-        const bool valid = e < blk_total;
-        uint32_t t = 0xffffffe0u + lane;  // unique, never a tile id
-        uint32_t id = 0;
-        if (valid) {
-            int lo = 0, hi = nb - 1;  // last rank whose local start is <= e
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_off[mid] <= e) lo = mid;
-                else hi = mid - 1;
+            for (int r = 0; r < kCoverRows; ++r) {
+                const uint32_t t0 = pk[r] & 0xffffu, t1 = pk[r] >> 16;
+                const uint32_t n = t0 <= t1 ? t1 - t0 + 1u : 0u;
+                if (key == 0xffffffffu && r <= ty_hi - ty_lo) {
+                    if (local < n)
+                        key = s_vb[lo] + (uint32_t)(ty_lo + r) * (uint32_t)cam.tiles_x + t0 + local;
+                    else
+                        local -= n;
+                }
             }
-            const uint32_t local = e - s_off[lo];
-            const uint32_t w = s_w[lo];
-            t = s_vb[lo] + (s_ty0[lo] + local / w) * (uint32_t)tiles_x + s_tx0[lo] + local % w;
-            id = s_id[lo];
+        } else {
+            for (int ty = ty_lo; ty <= ty_hi; ++ty) {
+                const int2 sp = cover_row(cv, uv.x, uv.z, uv.y, uv.w, ty, tx_lo, tx_hi, cam.tw_shift,
+                                          cam.tile_h, cam.W, cam.H);
+                const uint32_t n = sp.x <= sp.y ? (uint32_t)(sp.y - sp.x + 1) : 0u;
+                if (local < n) {
+                    key = s_vb[lo] + (uint32_t)ty * (uint32_t)cam.tiles_x + (uint32_t)sp.x + local;
+                    break;
+                }
+                local -= n;
+            }
         }
-        const uint32_t m = __match_any_sync(0xffffffffu, t);
-        const uint32_t rk = __popc(m & lanemask_lt());
-        const int leader = __ffs(m) - 1;
-        uint32_t base = 0;
-        if (valid && rk == 0) {
-            base = s_pos[t];
-            if (base == kUnread) base = bins[(int64_t)t * nbk + b];
+        if (key == 0xffffffffu) {  // the rows hold fewer tiles than were counted: never in a sound build
+            set_status(status, VPGS_ERR_INTERNAL);
+            key = 0u;
         }
-        base = __shfl_sync(0xffffffffu, base, leader);
-        __syncwarp();
-        if (valid) {
-            const uint32_t pos = base + rk;
-            if ((int64_t)pos < M_cap) ival[pos] = id;
-            if (rk == 0) s_pos[t] = base + __popc(m);
-        }
-        __syncwarp();
+        ikey[base + e] = key;
+        ival[base + e] = s_id[lo];
     }
 }
 
@@ -248,6 +155,14 @@ __global__ void tile_ranges_kernel(const uint32_t *__restrict__ keys, int64_t ca
     }
 }
 
+void tile_list_buffers(const RenderWs &ws, const RenderLayout &L, int *sorted_buf, const uint32_t **vis_list) {
+    SortPass ps[kMaxSortPasses];
+    const bool depth_in1 = (plan_passes(0, 32, ps) & 1) != 0;
+    const bool tile_in1 = (plan_passes(0, L.tile_bits, ps) & 1) != 0;
+    *vis_list = depth_in1 ? ws.dval[1] : ws.dval[0];
+    *sorted_buf = tile_in1 ? 1 : 0;
+}
+
 int device_sm_count() {
     static int sms = 0;
     if (sms == 0) {
@@ -260,7 +175,8 @@ int device_sm_count() {
 }
 
 cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, const RenderWs &ws,
-                             const RenderLayout &L, int *sorted_buf, cudaStream_t s) {
+                             const RenderLayout &L, int *sorted_buf, const uint32_t **vis_list,
+                             cudaStream_t s) {
     cudaError_t e;
     const int sms = device_sm_count();
     uint32_t *n_vis = ws.counters + CNT_VISIBLE;
@@ -277,32 +193,10 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
                          ws.scan_look);
     if (e != cudaSuccess) return e;
     const uint32_t *dval = in1 ? ws.dval[1] : ws.dval[0];
-    const int n_tiles = V * cam.T;
-    if (L.direct_bins) {
-        // 3. + 4. + 5. direct binning (count, scan, stable placement + tile ranges)
-        e = cudaMemsetAsync(ws.ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);
-        if (e != cudaSuccess) return e;
-        const size_t hsm = sizeof(uint32_t) * (size_t)n_tiles;
-        if (hsm > 48 * 1024) {  // per device and call: cheap, and right on every GPU of the process
-            cudaFuncSetAttribute((const void *)bin_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
-            cudaFuncSetAttribute((const void *)bin_place_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
-        }
-        uint32_t *bin_n = ws.counters + CNT_BIN_N;
-        VPGS_LAUNCH("bin_count", s,
-                    bin_count_kernel<<<(unsigned)L.bin_blocks, kBinRanks, hsm, s>>>(
-                        dval, ws.rect, n_vis, L.N, cam.T, cam.tiles_x, n_tiles, ws.bins, bin_n));
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        e = launch_scan("scan_bins", CountsLoad{ws.bins}, CountsStore{ws.bins}, (int64_t)n_tiles * L.bin_blocks,
-                        bin_n, ws.counters + CNT_TICKET_A, ws.scan_look, n_inst, ws.status, s);
-        if (e != cudaSuccess) return e;
-        VPGS_LAUNCH("bin_place", s,
-                    bin_place_kernel<<<(unsigned)L.bin_blocks, 32, hsm, s>>>(
-                        dval, ws.tcount, ws.rect, n_vis, n_inst, L.N, cam.T, cam.tiles_x, n_tiles, ws.bins,
-                        L.M_cap, ws.ival[0], ws.ranges, ws.status));
-        *sorted_buf = 0;
-        return cudaGetLastError();
-    }
+    if (vis_list) *vis_list = dval;  // visible (view, Gaussian) records in depth order
+    int expect_buf = 0;
+    const uint32_t *expect_vis = nullptr;
+    tile_list_buffers(ws, L, &expect_buf, &expect_vis);
     uint32_t *inst_off = in1 ? ws.dkey[0] : ws.dkey[1];  // the depth-sort buffer not holding the result
     // 3. instance offsets, then emission
     e = launch_scan("scan_offsets", CountLoad{ws.tcount, dval}, OffsetStore{inst_off}, L.VN, n_vis,
@@ -310,8 +204,9 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
     if (e != cudaSuccess) return e;
     VPGS_LAUNCH("emit_instances", s,
                 emit_kernel<<<(unsigned)std::max<int64_t>((L.VN + kEmitThreads - 1) / kEmitThreads, 1),
-                              kEmitThreads, 0, s>>>(dval, ws.tcount, inst_off, ws.rect, n_vis, L.N, L.M_cap,
-                                                    cam.T, cam.tiles_x, ws.ikey[0], ws.ival[0], ws.status));
+                              kEmitThreads, 0, s>>>(dval, ws.tcount, inst_off, ws.rect, ws.rec, ws.cover,
+                                                    n_vis, L.N, L.M_cap, cam, ws.ikey[0], ws.ival[0],
+                                                    ws.status));
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // 4. stable sort by tile id
@@ -321,13 +216,15 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
                          ws.counters + CNT_TICKET_A, ws.scan_look);
     if (e != cudaSuccess) return e;
     *sorted_buf = in1 ? 1 : 0;
+    if (dval != expect_vis || *sorted_buf != expect_buf) return cudaErrorUnknown;  // never: same pass plans
     // 5. tile ranges
-    e = cudaMemsetAsync(ws.ranges, 0, sizeof(uint2) * (size_t)V * cam.T, s);
+    const int n_tiles = V * cam.T;
+    e = cudaMemsetAsync(ws.ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);
     if (e != cudaSuccess) return e;
     const int64_t rb = std::min<int64_t>((L.M_cap + 255) / 256, (int64_t)sms * 16);
     VPGS_LAUNCH("tile_ranges", s,
                 tile_ranges_kernel<<<(unsigned)std::max<int64_t>(rb, 1), 256, 0, s>>>(
-                    in1 ? ws.ikey[1] : ws.ikey[0], L.M_cap, n_inst, (uint32_t)(V * cam.T), ws.ranges));
+                    in1 ? ws.ikey[1] : ws.ikey[0], L.M_cap, n_inst, (uint32_t)n_tiles, ws.ranges));
     return cudaGetLastError();
 }
 

@@ -4,8 +4,11 @@
 // persistent mode, a fixed number of CTAs per SM pull tiles from a work queue.
 // The tile's depth-ordered Gaussian list is staged through shared memory in
 // batches of one record per thread; each pixel walks the batch in order:
-//   alpha = min(alpha_max, o exp(-((w1.d)^2 + (w2.d)^2)/2)), d = pixel - mean
+//   alpha = min(alpha_max, o 2^-((w1.d)^2 + (w2.d)^2)), d = pixel - mean, with
+//           the whitening rows w scaled by sqrt(log2(e)/2) when the record is made
 //   skip alpha < alpha_min; stop before T (1 - alpha) < t_min
+// A warp skips a Gaussian outright when its widened y extent misses all of the
+// warp's pixel rows (alpha < alpha_min at every one of them).
 //   C += alpha T c, D += alpha T z, T *= 1 - alpha
 // Means are made tile-local when staged ((u_hi - x0) + u_lo), so d keeps
 // ~1e-7 px accuracy anywhere in the image.
@@ -37,10 +40,28 @@ VPGS_D TileCoord tile_coord(int t, const CamParams &cam) {
 
 // Each thread owns kPix pixels of its tile column: rows ly and ly + tile_h/kPix.
 constexpr int kPix = VPGS_PIX;
-constexpr int kChunk = VPGS_CHUNK;  // Gaussians evaluated together before the sequential blend
-constexpr int kGStep = VPGS_GSTEP;  // Gaussians per step of the backward loop
 constexpr int kAcc = VPGS_BWD_ACC;  // combination of per-warp gradient sums (see common.cuh)
 constexpr int kMaxThreads = 512;
+
+// Centre and half height of the band of tile-local pixel-centre rows held by
+// this thread's warp.
+VPGS_D float2 warp_rows(const float (&pyl)[kPix]) {
+    float lo = pyl[0], hi = pyl[kPix - 1];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    return make_float2(0.5f * (lo + hi), 0.5f * (hi - lo));
+}
+
+// record -> shared staging: s0 = (u, v) tile-local, w1; s1 = w2, opacity, widened
+// y half extent; s2 = colour, camera z
+VPGS_D void stage(const Rec &r, float ox, float oy, float4 &a, float4 &b, float4 &c) {
+    a = make_float4((r.r0.x - ox) + r.r0.z, (r.r0.y - oy) + r.r0.w, r.r1.x, r.r1.y);
+    b = make_float4(r.r1.z, r.r1.w, r.r2.x, r.r3.z);
+    c = make_float4(r.r2.z, r.r2.w, r.r3.x, r.r2.y);
+}
 
 __global__ void __launch_bounds__(kMaxThreads)
 composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ ival,
@@ -58,6 +79,7 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
     float pyl[kPix];
 #pragma unroll
     for (int q = 0; q < kPix; ++q) pyl[q] = (float)(ly + q * half) + 0.5f;
+    const float2 band = warp_rows(pyl);
     int t = blockIdx.x;
     for (;;) {
         if (work) {
@@ -87,56 +109,38 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
         for (int b0 = start; b0 < end; b0 += NT) {
             if (__syncthreads_count(all_done) == NT) break;
             const int j = b0 + tid;
-            if (j < end) {
-                const Rec r = rec[ival[j]];
-                s0[tid] = make_float4((r.r0.x - ox) + r.r0.z, (r.r0.y - oy) + r.r0.w, r.r1.x, r.r1.y);
-                s1[tid] = make_float4(r.r1.z, r.r1.w, r.r2.x, r.r2.y);
-                s2[tid] = make_float4(r.r2.z, r.r2.w, r.r3.x, r.r3.w);
-            }
+            if (j < end) stage(rec[ival[j]], ox, oy, s0[tid], s1[tid], s2[tid]);
             __syncthreads();
             if (!all_done) {
                 const int nb = min(NT, end - b0);
-                for (int k0 = 0; k0 < nb; k0 += kChunk) {
-                    // independent evaluations of kChunk Gaussians x kPix pixels ...
-                    float al[kChunk][kPix];
-#pragma unroll
-                    for (int c = 0; c < kChunk; ++c) {
-                        const int k = min(k0 + c, nb - 1);
-                        const float4 a = s0[k], b = s1[k];
-#pragma unroll
-                        for (int q = 0; q < kPix; ++q) {
-                            const PairEval e = eval_pair(pxl - a.x, pyl[q] - a.y, a.z, a.w, b.x, b.y, b.z,
-                                                         o.alpha_max);
-                            al[c][q] = (k0 + c < nb) ? e.alpha : 0.f;
-                        }
-                    }
-                    // ... then the sequential blend in depth order
-#pragma unroll
-                    for (int c = 0; c < kChunk; ++c) {
-#pragma unroll
-                        for (int q = 0; q < kPix; ++q) {
-                            const float alpha = al[c][q];
-                            if (done[q] || alpha < o.alpha_min) continue;
-                            const float nt = T[q] * (1.f - alpha);
-                            if (nt < o.t_min) {
-                                done[q] = true;
-                                continue;
-                            }
-                            const int k = k0 + c;
-                            const float w = alpha * T[q];
-                            const float4 col = s2[k];
-                            C0[q] = fmaf(w, col.x, C0[q]);
-                            C1[q] = fmaf(w, col.y, C1[q]);
-                            C2[q] = fmaf(w, col.z, C2[q]);
-                            D[q] = fmaf(w, s1[k].w, D[q]);
-                            T[q] = nt;
-                            ++cnt[q];
-                            last[q] = b0 + k - start + 1;
-                        }
-                    }
+                for (int k = 0; k < nb; ++k) {
+                    const float4 a = s0[k], b = s1[k];
+                    if (fabsf(a.y - band.x) > b.w + band.y) continue;  // warp-uniform
                     bool fin = true;
 #pragma unroll
-                    for (int q = 0; q < kPix; ++q) fin = fin && done[q];
+                    for (int q = 0; q < kPix; ++q) {
+                        if (!done[q]) {
+                            const PairEval e = eval_pair(pxl - a.x, pyl[q] - a.y, a.z, a.w, b.x, b.y, b.z,
+                                                         o.alpha_max);
+                            if (e.alpha >= o.alpha_min) {
+                                const float nt = T[q] * (1.f - e.alpha);
+                                if (nt < o.t_min) {
+                                    done[q] = true;
+                                } else {
+                                    const float w = e.alpha * T[q];
+                                    const float4 col = s2[k];
+                                    C0[q] = fmaf(w, col.x, C0[q]);
+                                    C1[q] = fmaf(w, col.y, C1[q]);
+                                    C2[q] = fmaf(w, col.z, C2[q]);
+                                    D[q] = fmaf(w, col.w, D[q]);
+                                    T[q] = nt;
+                                    ++cnt[q];
+                                    last[q] = b0 + k - start + 1;
+                                }
+                            }
+                        }
+                        fin = fin && done[q];
+                    }
                     if (fin) {
                         all_done = true;
                         break;
@@ -207,16 +211,6 @@ VPGS_D void warp_reduce10(float (&a)[10], int lane) {
     a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
 }
 
-// two reductions interleaved, for instruction-level parallelism
-VPGS_D void warp_reduce10x2(float (&a)[10], float (&b)[10], int lane) {
-    half_step<10, 16>(a, lane); half_step<10, 16>(b, lane);
-    half_step<5, 8>(a, lane);   half_step<5, 8>(b, lane);
-    half_step<3, 4>(a, lane);   half_step<3, 4>(b, lane);
-    half_step<2, 2>(a, lane);   half_step<2, 2>(b, lane);
-    a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
-    b[0] += __shfl_xor_sync(0xffffffffu, b[0], 1);
-}
-
 // per-pixel backward state
 struct PixState {
     float T, T_fin, gC0, gC1, gC2, gD, gA, B0, B1, B2, BD;
@@ -229,23 +223,31 @@ VPGS_D bool pair_grad(PixState &p, int jj, const PairEval &e, float dx, float dy
                       const float4 &b, const float4 &c, const OptParams &o, float (&v)[10]) {
     if (jj >= p.last || e.alpha < o.alpha_min) return false;
     const float om = 1.f - e.alpha;
+#if VPGS_BWD_RCP
+    const float iom = __fdividef(1.f, om);  // om >= 1 - alpha_max > 0
+    p.T *= iom;
+    const float tfo = p.T_fin * iom;
+#else
     p.T = p.T / om;
+    const float tfo = p.T_fin / om;
+#endif
     const float w = e.alpha * p.T;
     v[6] = fmaf(w, p.gC0, v[6]);
     v[7] = fmaf(w, p.gC1, v[7]);
     v[8] = fmaf(w, p.gC2, v[8]);
     v[9] = fmaf(w, p.gD, v[9]);
     const float dA = (p.gC0 * (c.x - p.B0) + p.gC1 * (c.y - p.B1) + p.gC2 * (c.z - p.B2) +
-                      p.gD * (b.w - p.BD)) * p.T + p.gA * p.T_fin / om;
+                      p.gD * (c.w - p.BD)) * p.T + p.gA * tfo;
     p.B0 = fmaf(e.alpha, c.x, om * p.B0);
     p.B1 = fmaf(e.alpha, c.y, om * p.B1);
     p.B2 = fmaf(e.alpha, c.z, om * p.B2);
-    p.BD = fmaf(e.alpha, b.w, om * p.BD);
+    p.BD = fmaf(e.alpha, c.w, om * p.BD);
     if (b.z * e.G <= o.alpha_max) {
         const float dpow = dA * e.alpha;
+        const float dmu = dpow * kInvExp2Half;  // the rows carry sqrt(log2(e)/2)
         v[5] = fmaf(dA, e.G, v[5]);
-        v[0] = fmaf(dpow, a.z * e.t1 + b.x * e.t2, v[0]);
-        v[1] = fmaf(dpow, a.w * e.t1 + b.y * e.t2, v[1]);
+        v[0] = fmaf(dmu, a.z * e.t1 + b.x * e.t2, v[0]);
+        v[1] = fmaf(dmu, a.w * e.t1 + b.y * e.t2, v[1]);
         v[2] = fmaf(-0.5f * dpow, dx * dx, v[2]);
         v[3] = fmaf(-dpow, dx * dy, v[3]);
         v[4] = fmaf(-0.5f * dpow, dy * dy, v[4]);
@@ -278,6 +280,7 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
     float pyl[kPix];
 #pragma unroll
     for (int q = 0; q < kPix; ++q) pyl[q] = (float)(ly + q * half) + 0.5f;
+    const float2 band = warp_rows(pyl);
     float *my_part = s_part + (size_t)warp * NT * kPartStride;
     const int slot = red_slot(lane);
     // hands one warp total (this lane's slot) of Gaussian k to the combination scheme
@@ -340,10 +343,7 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
             const int j = b0 + tid;
             if (j < b1) {
                 const uint32_t id = ival[j];
-                const Rec r = rec[id];
-                s0[tid] = make_float4((r.r0.x - ox) + r.r0.z, (r.r0.y - oy) + r.r0.w, r.r1.x, r.r1.y);
-                s1[tid] = make_float4(r.r1.z, r.r1.w, r.r2.x, r.r2.y);
-                s2[tid] = make_float4(r.r2.z, r.r2.w, r.r3.x, r.r3.w);
+                stage(rec[id], ox, oy, s0[tid], s1[tid], s2[tid]);
                 s_id[tid] = id;
             }
             if (kAcc == 1)
@@ -352,66 +352,34 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                 for (int e = tid; e < nb * kPartStride; e += NT) s_part[e] = 0.f;
             __syncthreads();
             const int k_end = min(nb, warp_max - (b0 - start));  // warp-uniform
-            // kGStep Gaussians per step, back to front: kk (behind) then kk - 1
-            for (int kk = k_end - 1; kk >= 0; kk -= kGStep) {
-                if (kGStep == 1) {
-                    const float4 a = s0[kk], b = s1[kk], c = s2[kk];
-                    float v[10];
+            // back to front
+            for (int kk = k_end - 1; kk >= 0; --kk) {
+                const float4 a = s0[kk], b = s1[kk];
+                if (fabsf(a.y - band.x) > b.w + band.y) continue;  // warp-uniform
+                const float4 c = s2[kk];
+                float v[10];
 #pragma unroll
-                    for (int q = 0; q < 10; ++q) v[q] = 0.f;
-                    const int jj = b0 + kk - start;
-                    bool act = false;
-#pragma unroll
-                    for (int q = 0; q < kPix; ++q) {
-                        const float dx = pxl - a.x, dy = pyl[q] - a.y;
-                        const PairEval e = eval_pair(dx, dy, a.z, a.w, b.x, b.y, b.z, o.alpha_max);
-                        act |= pair_grad(ps[q], jj, e, dx, dy, a, b, c, o, v);
-                    }
-                    const uint32_t am = __ballot_sync(0xffffffffu, act);
-                    if (kAcc == 0 && am != 0u && __popc(am) <= 2) {
-                        // one or two active lanes: their own atomics beat a reduction
-                        if (act) {
-                            float *dst = g2d + 10 * (int64_t)s_id[kk];
-#pragma unroll
-                            for (int q = 0; q < 10; ++q)
-                                if (v[q] != 0.f) atomicAdd(dst + q, v[q]);
-                        }
-                    } else if (am != 0u) {
-                        warp_reduce10(v, lane);
-                        if (slot >= 0) put(kk, v[0]);
-                    }
-                    continue;
-                }
-                const bool has_b = kk >= 1;
-                const int ka = kk, kb = has_b ? kk - 1 : kk;
-                const float4 aA = s0[ka], bA = s1[ka], cA = s2[ka];
-                const float4 aB = s0[kb], bB = s1[kb], cB = s2[kb];
-                PairEval eA[kPix], eB[kPix];
-                float dxA[kPix], dyA[kPix], dxB[kPix], dyB[kPix];
-#pragma unroll
-                for (int q = 0; q < kPix; ++q) {
-                    dxA[q] = pxl - aA.x; dyA[q] = pyl[q] - aA.y;
-                    dxB[q] = pxl - aB.x; dyB[q] = pyl[q] - aB.y;
-                    eA[q] = eval_pair(dxA[q], dyA[q], aA.z, aA.w, bA.x, bA.y, bA.z, o.alpha_max);
-                    eB[q] = eval_pair(dxB[q], dyB[q], aB.z, aB.w, bB.x, bB.y, bB.z, o.alpha_max);
-                }
-                float vA[10], vB[10];
-#pragma unroll
-                for (int q = 0; q < 10; ++q) vA[q] = vB[q] = 0.f;
-                const int jjA = b0 + ka - start, jjB = b0 + kb - start;
+                for (int q = 0; q < 10; ++q) v[q] = 0.f;
+                const int jj = b0 + kk - start;
                 bool act = false;
 #pragma unroll
-                for (int q = 0; q < kPix; ++q) act |= pair_grad(ps[q], jjA, eA[q], dxA[q], dyA[q], aA, bA, cA, o, vA);
-                if (has_b) {
-#pragma unroll
-                    for (int q = 0; q < kPix; ++q) act |= pair_grad(ps[q], jjB, eB[q], dxB[q], dyB[q], aB, bB, cB, o, vB);
+                for (int q = 0; q < kPix; ++q) {
+                    const float dx = pxl - a.x, dy = pyl[q] - a.y;
+                    const PairEval e = eval_pair(dx, dy, a.z, a.w, b.x, b.y, b.z, o.alpha_max);
+                    act |= pair_grad(ps[q], jj, e, dx, dy, a, b, c, o, v);
                 }
-                if (__any_sync(0xffffffffu, act)) {
-                    warp_reduce10x2(vA, vB, lane);
-                    if (slot >= 0) {
-                        put(ka, vA[0]);
-                        if (has_b) put(kb, vB[0]);
+                const uint32_t am = __ballot_sync(0xffffffffu, act);
+                if (kAcc == 0 && am != 0u && __popc(am) <= 2) {
+                    // one or two active lanes: their own atomics beat a reduction
+                    if (act) {
+                        float *dst = g2d + 10 * (int64_t)s_id[kk];
+#pragma unroll
+                        for (int q = 0; q < 10; ++q)
+                            if (v[q] != 0.f) atomicAdd(dst + q, v[q]);
                     }
+                } else if (am != 0u) {
+                    warp_reduce10(v, lane);
+                    if (slot >= 0) put(kk, v[0]);
                 }
             }
             if (kAcc != 0) {

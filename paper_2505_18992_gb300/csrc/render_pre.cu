@@ -8,6 +8,8 @@
 //   extent: half widths sqrt(2 ln(o/alpha_min) Sigma'_xx), sqrt(... Sigma'_yy),
 //           widened by 1e-5 r + 2e-3 px so the pixel set is a superset of the
 //           exact one; the alpha test at each pixel then decides membership
+//   tile count: the tiles of that box whose pixel-centre rectangle (widened
+//           by the same margins) meets the alpha_min ellipse, row by row
 // Backward, one thread per Gaussian, looping over views: chain rule from the
 // 2D gradients (u, v, conic, opacity, colour, depth) back to mean, scale,
 // quaternion, opacity and colour, plus the per-view pose terms summed in FP64.
@@ -91,6 +93,7 @@ preprocess_fwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamPara
     uint32_t cnt = 0;
     uint2 rc = make_uint2(0, 0);
     Rec R;
+    Cover cv;
     if (gi < nl) {
         const float mx = g.means[3 * gi], my = g.means[3 * gi + 1], mz = g.means[3 * gi + 2];
         const float sx = g.scales[3 * gi], sy = g.scales[3 * gi + 1], sz = g.scales[3 * gi + 2];
@@ -122,7 +125,7 @@ preprocess_fwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamPara
                 }
                 const float en = 1.0f / sqrtf(ex * ex + ey * ey);
                 ex *= en; ey *= en;
-                const float s1 = 1.0f / sqrtf(lam1), s2 = 1.0f / sqrtf(lam2);
+                const float s1 = kRowScale / sqrtf(lam1), s2 = kRowScale / sqrtf(lam2);
                 // opacity-aware extent
                 const float kq = 2.0f * logf(op / o.alpha_min);
                 const float rx = sqrtf(fmaxf(kq, 0.f) * p.A), ry = sqrtf(fmaxf(kq, 0.f) * p.C);
@@ -139,9 +142,38 @@ preprocess_fwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamPara
                     const int x0 = max(0, (int)ceilf(lx)), x1 = min(cam.W - 1, (int)floorf(hx));
                     const int y0 = max(0, (int)ceilf(ly)), y1 = min(cam.H - 1, (int)floorf(hy));
                     if (x0 <= x1 && y0 <= y1) {
-                        const int tx0 = x0 / cam.tile_w, tx1 = x1 / cam.tile_w;
+                        const int tx0 = x0 >> cam.tw_shift, tx1 = x1 >> cam.tw_shift;
                         const int ty0 = y0 / cam.tile_h, ty1 = y1 / cam.tile_h;
-                        cnt = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+                        const float kc = fmaxf(kq, 0.f), iC = 1.0f / p.C, dC = p.det * iC;
+                        cv.a = make_float4(ry, fmaf(ry, 1e-5f, 2e-3f), -p.B * sqrtf(kc / p.A), p.B * iC);
+                        cv.b = make_float4(kc * dC, dC * iC, fmaf(rx, 1e-5f, 2e-3f), 0.f);
+                        const int rows = ty1 - ty0 + 1;
+                        if (rows <= kCoverRows) {
+                            // few rows: keep the spans themselves for the emitting pass
+                            uint32_t pk[kCoverRows];
+#pragma unroll
+                            for (int r = 0; r < kCoverRows; ++r) {
+                                pk[r] = kEmptySpan;
+                                if (r < rows) {
+                                    const int2 sp = cover_row(cv, p.u.hi, p.u.lo, p.v.hi, p.v.lo, ty0 + r, tx0,
+                                                              tx1, cam.tw_shift, cam.tile_h, cam.W, cam.H);
+                                    if (sp.x <= sp.y) {
+                                        cnt += (uint32_t)(sp.y - sp.x + 1);
+                                        pk[r] = (uint32_t)sp.x | ((uint32_t)sp.y << 16);
+                                    }
+                                }
+                            }
+                            cv.a = make_float4(__uint_as_float(pk[0]), __uint_as_float(pk[1]),
+                                               __uint_as_float(pk[2]), __uint_as_float(pk[3]));
+                            cv.b = make_float4(__uint_as_float(pk[4]), __uint_as_float(pk[5]),
+                                               __uint_as_float(pk[6]), __uint_as_float(pk[7]));
+                        } else {
+                            for (int ty = ty0; ty <= ty1; ++ty) {
+                                const int2 sp = cover_row(cv, p.u.hi, p.u.lo, p.v.hi, p.v.lo, ty, tx0, tx1,
+                                                          cam.tw_shift, cam.tile_h, cam.W, cam.H);
+                                if (sp.x <= sp.y) cnt += (uint32_t)(sp.y - sp.x + 1);
+                            }
+                        }
                         rc = make_uint2((uint32_t)tx0 | ((uint32_t)tx1 << 16),
                                         (uint32_t)ty0 | ((uint32_t)ty1 << 16));
                         R.r0 = make_float4(p.u.hi, p.v.hi, p.u.lo, p.v.lo);
@@ -157,6 +189,7 @@ preprocess_fwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamPara
     ws.rect[i] = rc;
     if (cnt) {
         ws.rec[i] = R;
+        ws.cover[i] = cv;
         if (zero_g2d) {
             float2 *z2 = reinterpret_cast<float2 *>(ws.g2d + 10 * i);
 #pragma unroll
@@ -173,13 +206,24 @@ VPGS_D float warp_sum(float x) {
 
 __global__ void __launch_bounds__(256)
 preprocess_bwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamParams cam, OptParams o,
-                      RenderWs ws, GaussGrad gg, double *dpose) {
+                      RenderWs ws, GaussGrad gg, double *dpose, const uint32_t *__restrict__ vis,
+                      const uint32_t *n_vis) {
     __shared__ double s_pose[8][6];
-    const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int64_t nl = g.N;
-    if (g.n_dev) nl = min(nl, (int64_t)*g.n_dev);
-    const bool live = gi < nl;
+    const int64_t tix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t gi = tix;
+    bool live;
+    if (vis) {
+        // one view: walk the visible list, so every lane of a warp has work
+        const int64_t nv = *n_vis;
+        if ((int64_t)blockIdx.x * blockDim.x >= nv) return;  // whole block past the list
+        live = tix < nv;
+        gi = live ? (int64_t)vis[tix] : 0;
+    } else {
+        int64_t nl = g.N;
+        if (g.n_dev) nl = min(nl, (int64_t)*g.n_dev);
+        live = gi < nl;
+    }
     float gm[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, go = 0.f, gc[3] = {0, 0, 0};
     float mx = 0, my = 0, mz = 0, sx = 1, sy = 1, sz = 1;
     float4 q = make_float4(1, 0, 0, 0);
@@ -192,12 +236,16 @@ preprocess_bwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamPara
         float pv[6] = {0, 0, 0, 0, 0, 0};
         const int64_t i = (int64_t)v * g.N + gi;
         if (live && ws.tcount[i] > 0) {
-            const float *g2 = ws.g2d + 10 * i;
+            const float *g2 = ws.g2d + 10 * i;  // [u, v, a, b, c, o, r, g, b, z]
             const float2 a01 = reinterpret_cast<const float2 *>(g2)[0];
             const float2 a23 = reinterpret_cast<const float2 *>(g2)[1];
             const float2 a45 = reinterpret_cast<const float2 *>(g2)[2];
             const float2 a67 = reinterpret_cast<const float2 *>(g2)[3];
             const float2 a89 = reinterpret_cast<const float2 *>(g2)[4];
+            // consumed: the slots start at zero again for the next backward
+            float2 *z2 = reinterpret_cast<float2 *>(ws.g2d + 10 * i);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) z2[k] = make_float2(0.f, 0.f);
             const float gu = a01.x, gv = a01.y, ga = a23.x, gb = a23.y, gcn = a45.x;
             go += a45.y;
             gc[0] += a67.x; gc[1] += a67.y; gc[2] += a89.x;
@@ -344,10 +392,10 @@ __global__ void export_projection_kernel(RenderWs ws, int64_t VN, int32_t *tile_
         mean2d[2 * i + 1] = r.r0.y + r.r0.w;
     }
     if (depth) depth[i] = r.r2.y;
-    if (conic) {  // Sigma'^-1 = w1 w1^T + w2 w2^T
-        conic[3 * i] = r.r1.x * r.r1.x + r.r1.z * r.r1.z;
-        conic[3 * i + 1] = r.r1.x * r.r1.y + r.r1.z * r.r1.w;
-        conic[3 * i + 2] = r.r1.y * r.r1.y + r.r1.w * r.r1.w;
+    if (conic) {  // Sigma'^-1 = (w1 w1^T + w2 w2^T) 2 / log2(e)
+        conic[3 * i] = (r.r1.x * r.r1.x + r.r1.z * r.r1.z) * kInvExp2Half;
+        conic[3 * i + 1] = (r.r1.x * r.r1.y + r.r1.z * r.r1.w) * kInvExp2Half;
+        conic[3 * i + 2] = (r.r1.y * r.r1.y + r.r1.w * r.r1.w) * kInvExp2Half;
     }
 }
 
@@ -375,11 +423,12 @@ cudaError_t launch_preprocess_fwd(const GaussIn &g, const double *T_cw, int V, c
 
 cudaError_t launch_preprocess_bwd(const GaussIn &g, const double *T_cw, int V, const CamParams &cam,
                                   const OptParams &o, const RenderWs &ws, const GaussGrad &gg,
-                                  double *dpose, cudaStream_t s) {
+                                  double *dpose, const uint32_t *vis, cudaStream_t s) {
     if (g.N == 0) return cudaSuccess;
+    const uint32_t *list = V == 1 ? vis : nullptr;
     VPGS_LAUNCH("preprocess_bwd", s,
-                preprocess_bwd_kernel<<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>(g, T_cw, V, cam, o,
-                                                                                    ws, gg, dpose));
+                preprocess_bwd_kernel<<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>(
+                    g, T_cw, V, cam, o, ws, gg, dpose, list, ws.counters + CNT_VISIBLE));
     return cudaGetLastError();
 }
 

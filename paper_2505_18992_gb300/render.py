@@ -2,8 +2,10 @@
 
 `Renderer` owns the device workspace of a camera and passes tensors to the C
 entry points; `RenderFn` puts the forward/backward pair behind
-torch.autograd.  The backward recomputes the tile lists inside the library
-(only the final transmittance and the per-pixel list length are kept).
+torch.autograd.  Only the final transmittance and the per-pixel list length
+are kept from the forward; the backward takes the projection and tile lists
+from the workspace when no other render call used it in between, and
+recomputes them otherwise.
 """
 from __future__ import annotations
 
@@ -60,6 +62,7 @@ class Renderer:
         self.cap_m = 0
         self.inst_per_g = instances_per_gaussian
         self.last_stats = None
+        self.generation = 0  # counts the calls that replace the workspace's tile lists
 
     # -- workspace -----------------------------------------------------------
     def reserve(self, n: int, max_instances: int | None = None):
@@ -72,6 +75,7 @@ class Renderer:
         if self.ws is None or need > self.ws_bytes or n > self.cap_n:
             self.ws = torch.empty(need, dtype=torch.uint8, device=self.device)
             self.ws_bytes = need
+            self.generation += 1
         self.cap_n = max(self.cap_n, int(n))
         self.cap_m = max(self.cap_m, int(max_instances))
 
@@ -116,6 +120,7 @@ class Renderer:
             self.reserve(n)
         g = self._gauss(means, scales, quats, opacities, colors, n_dev)
         out = self.alloc_images() if out is None else out
+        self.generation += 1
         for _ in range(4):
             code = C.vpgs_render_fwd(self.ws.data_ptr(), self.ws_bytes, ctypes.byref(g),
                                      ctypes.byref(self.cam), T_cw.data_ptr(), self.V,
@@ -139,6 +144,7 @@ class Renderer:
         if self.ws is None or n > self.cap_n:
             self.reserve(n)
         g = self._gauss(means, scales, quats, opacities, colors, n_dev)
+        self.generation += 1
         V, dev = self.V, self.device
         out = {"tile_count": torch.zeros((V, n), dtype=torch.int32, device=dev),
                "tile_rect": torch.zeros((V, n, 4), dtype=torch.int32, device=dev),
@@ -154,17 +160,24 @@ class Renderer:
         return out
 
     def backward(self, means, scales, quats, opacities, colors, T_cw, fwd, g_rgb=None, g_depth=None,
-                 g_alpha=None, grads=None, dpose=None, n_dev=None, check=False):
+                 g_alpha=None, grads=None, dpose=None, n_dev=None, check=False, reuse=False):
         """Accumulates gradients into `grads` (dict of float32 tensors shaped like
-        the inputs; missing keys are not computed) and `dpose` [V,6] float64."""
+        the inputs; missing keys are not computed) and `dpose` [V,6] float64.
+
+        reuse=True takes the projection and tile lists from the workspace (the
+        preceding forward on this renderer had these very inputs, unchanged)."""
         g = self._gauss(means, scales, quats, opacities, colors, n_dev)
+        opts = self.opts
+        if reuse:
+            opts = C.vpgs_render_opts.from_buffer_copy(self.opts)
+            opts.flags |= C.RENDER_REUSE_BINNING
         grads = grads or {}
         gb = C.vpgs_gaussian_buffers(C.ptr(grads.get("means")), C.ptr(grads.get("scales")),
                                      C.ptr(grads.get("quats")), C.ptr(grads.get("opacities")),
                                      C.ptr(grads.get("colors")))
         code = C.vpgs_render_bwd(self.ws.data_ptr(), self.ws_bytes, ctypes.byref(g),
                                  ctypes.byref(self.cam), T_cw.data_ptr(), self.V,
-                                 ctypes.byref(self.opts), ctypes.byref(self._images(fwd)),
+                                 ctypes.byref(opts), ctypes.byref(self._images(fwd)),
                                  C.ptr(g_rgb), C.ptr(g_depth), C.ptr(g_alpha), ctypes.byref(gb),
                                  C.ptr(dpose), current_stream_handle())
         C.check(code, "vpgs_render_bwd")
@@ -183,6 +196,7 @@ class RenderFn(torch.autograd.Function):
     def forward(ctx, means, scales, quats, opacities, colors, xi, T_cw, renderer):
         out = renderer.forward(means, scales, quats, opacities, colors, T_cw)
         ctx.renderer = renderer
+        ctx.generation = renderer.generation
         ctx.save_for_backward(means, scales, quats, opacities, colors, T_cw, out["t_final"],
                               out["n_iter"])
         ctx.mark_non_differentiable(out["t_final"])
@@ -199,8 +213,10 @@ class RenderFn(torch.autograd.Function):
         dpose = torch.zeros((r.V, 6), dtype=torch.float64, device=means.device) if need[5] else None
         fwd = {"t_final": t_final, "n_iter": n_iter}
         cont = lambda t: None if t is None else t.contiguous()  # noqa: E731
+        # saved tensors cannot have been changed in place (autograd checks their
+        # versions), so the lists are reusable unless another call replaced them
         r.backward(means, scales, quats, opacities, colors, T_cw, fwd, cont(g_rgb), cont(g_depth),
-                   cont(g_alpha), grads=grads, dpose=dpose)
+                   cont(g_alpha), grads=grads, dpose=dpose, reuse=r.generation == ctx.generation)
         return (grads.get("means"), grads.get("scales"), grads.get("quats"),
                 grads.get("opacities"), grads.get("colors"), dpose, None, None)
 

@@ -56,7 +56,7 @@ class Tracker:
         torch.sub(self.out["depth"], self.target_depth, out=self.g_depth)
         self.g_depth.sign_().mul_(self.s_d)
         r.backward(*self.g, self.T, self.out, self.g_rgb, self.g_depth, None, grads=None,
-                   dpose=self.dpose)
+                   dpose=self.dpose, reuse=True)
         C.check(C.vpgs_pose_step(self.T.data_ptr(), self.dpose.data_ptr(), self.adam.data_ptr(),
                                  r.V, self.lr, current_stream_handle()), "vpgs_pose_step")
 

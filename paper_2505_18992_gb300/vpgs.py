@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libvpgs.so"
 VPGS_OK = 0
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "tile-instance capacity exceeded",
                 3: "non-finite input", 4: "bounded device wait ran out", 5: "CUDA error",
-                6: "unsupported"}
+                6: "unsupported", 7: "internal consistency check failed"}
 
 
 class VpgsError(RuntimeError):
@@ -31,7 +31,11 @@ class vpgs_camera(ctypes.Structure):
 class vpgs_render_opts(ctypes.Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("alpha_min", c_float),
                 ("alpha_max", c_float), ("t_min", c_float), ("dilation", c_float),
-                ("near_z", c_float), ("bg", c_float * 3), ("persistent_ctas", c_int32)]
+                ("near_z", c_float), ("bg", c_float * 3), ("persistent_ctas", c_int32),
+                ("flags", c_int32)]
+
+
+RENDER_REUSE_BINNING = 1
 
 
 class vpgs_gaussians(ctypes.Structure):

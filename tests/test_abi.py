@@ -77,8 +77,10 @@ def test_host_side_validation_without_a_gpu(lib):
     n1 = C.vpgs_render_workspace_bytes(1000, 1, ctypes.byref(cam), ctypes.byref(o), 10000)
     n2 = C.vpgs_render_workspace_bytes(1000, 1, ctypes.byref(cam), ctypes.byref(o), 20000)
     assert n1 > 0 and n2 > n1
-    bad = C.default_opts(tile_w=3)
-    assert C.vpgs_render_workspace_bytes(1000, 1, ctypes.byref(cam), ctypes.byref(bad), 10) == 0
+    for bad in (C.default_opts(tile_w=3), C.default_opts(tile_w=32, tile_h=32), C.default_opts(tile_h=7)):
+        assert C.vpgs_render_workspace_bytes(1000, 1, ctypes.byref(cam), ctypes.byref(bad), 10) == 0
+    assert C.vpgs_render_workspace_bytes(1000, 1, ctypes.byref(cam), ctypes.byref(C.default_opts(tile_w=32, tile_h=16)), 10) > 0
+    assert C.vpgs_status_string(7) == b"internal consistency check failed"
     # NULL arguments are rejected before anything touches the device
     assert C.vpgs_render_fwd(None, 0, None, None, None, 1, None, None, None) == 1
     assert C.vpgs_render_bwd(None, 0, None, None, None, 1, None, None, None, None, None, None, None,
