@@ -301,12 +301,13 @@ def run_ours(a):
     Nv, M = int(st.n_visible), int(st.n_instances)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
 
-    def step():
+    def step(reuse=False):
+        # the metric's form: the backward recomputes projection and tile lists
         for t in grads.values():
             t.zero_()
         dpose.zero_()
         r.forward(*g, T, out=out, check=False)
-        r.backward(*g, T, out, g_rgb, g_d, None, grads=grads, dpose=dpose, reuse=True)
+        r.backward(*g, T, out, g_rgb, g_d, None, grads=grads, dpose=dpose, reuse=reuse)
 
     for _ in range(max(3, a.warmup)):
         step()
@@ -368,6 +369,11 @@ def run_ours(a):
         C.check(r.stats().status, "graph replays")
     except Exception as exc:  # reported; the eager number stands
         eager["graph_error"] = repr(exc)[:200]
+    reuse_ms = None
+    if not a.no_extras:
+        # opt-in variant (not the metric's form): the backward reuses the forward's lists
+        reuse_ms = max_over_ranks(statistics.fmean(timed(lambda: step(reuse=True), min(a.steps, 100))), dev)
+        C.check(r.stats().status, "reuse renders")
     if sampler:
         time.sleep(0.2)
         sampler.stop()
@@ -385,14 +391,18 @@ def run_ours(a):
                        "n_gaussians": sc.n, "width": W, "height": H,
                        "visible": Nv, "instances": M, "tile": a.tile,
                        "persistent_ctas_per_sm": a.persistent,
-                       "step": "projection + binning once; forward compositing; backward reusing the "
-                               "forward's tile lists; all Gaussian and pose gradients",
+                       "step": "forward (projection, binning, compositing) + backward recomputing "
+                               "projection and tile lists; all Gaussian and pose gradients",
                        "l2": "256 MiB buffer written between timed steps (inputs 56 MB < L2)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "launch": launch},
             "eager": eager, "cuda_graph": {"ms_per_step": graph_ms,
                                            "value": P * world / (graph_ms * 1e-3) / 1e6 if graph_ms else None},
             "gpu_launches": int(launches)}
+    if reuse_ms is not None:
+        line["reuse_binning"] = {"ms_per_step": reuse_ms, "value": P * world / (reuse_ms * 1e-3) / 1e6,
+                                 "note": "opt-in VPGS_RENDER_REUSE_BINNING: backward takes the forward's tile "
+                                         "lists (eager; not the metric's recompute form)"}
     if sampler:
         line["clocks"] = sampler.summary(t_wall0, t_wall1)
 
@@ -542,7 +552,7 @@ def batched_rows(dev, steps=10):
 
     def batched():
         rb.forward(*g, T, out=outb, check=False)
-        rb.backward(*g, T, outb, gb, None, None, grads=grads, dpose=dpb, reuse=True)
+        rb.backward(*g, T, outb, gb, None, None, grads=grads, dpose=dpb)
 
     r1 = Renderer(intr, n_views=1, device=dev)
     Ts = [T[v:v + 1].contiguous() for v in range(V)]
@@ -553,14 +563,27 @@ def batched_rows(dev, steps=10):
     def separate():
         for Tv, o in zip(Ts, outs):
             r1.forward(*g, Tv, out=o, check=False)
-            r1.backward(*g, Tv, o, g1, None, None, grads=grads, dpose=dp1, reuse=True)
+            r1.backward(*g, Tv, o, g1, None, None, grads=grads, dpose=dp1)
 
     mb = _time_ms(batched, steps)
     ms = _time_ms(separate, steps)
     px = V * H * W
-    return {"views": V, "gaussians": sc.n, "width": W, "height": H,
-            "batched_ms": mb, "separate_ms": ms, "batched_mpix_s": px / (mb * 1e-3) / 1e6,
-            "separate_mpix_s": px / (ms * 1e-3) / 1e6}
+    row = {"views": V, "gaussians": sc.n, "width": W, "height": H,
+           "batched_ms": mb, "separate_ms": ms, "batched_mpix_s": px / (mb * 1e-3) / 1e6,
+           "separate_mpix_s": px / (ms * 1e-3) / 1e6}
+    # launch shape picked by the autotuner (tile shape x persistent CTAs x views per call)
+    from paper_2505_18992_gb300 import autotune
+    del outb, outs
+    torch.cuda.empty_cache()
+    shapes = autotune.candidates(V, tiles=((8, 16), (16, 16), (16, 8), (8, 8)), persistent=(0, 4),
+                                 views_per_call=(8, 4, 1))
+    best, timings = autotune.tune(g, T, intr, gb, shapes=shapes, steps=3)
+    row["autotuned"] = {"shape": {"tile": f"{best.tile_w}x{best.tile_h}", "persistent_ctas": best.persistent_ctas,
+                                  "views_per_call": best.views_per_call},
+                        "ms": timings[best], "mpix_s": px / (timings[best] * 1e-3) / 1e6,
+                        "candidates": len(timings),
+                        "default_ms": timings.get(autotune.LaunchShape(8, 16, 0, V))}
+    return row
 
 
 def fusion_rows(dev):

@@ -66,7 +66,6 @@ bool make_layout(int64_t N, int V, const vpgs_camera *cam, const vpgs_render_opt
     L.off_status = take(4);
     L.off_counters = take(4 * CNT_N);
     L.off_rec = take(sizeof(Rec) * VN1);
-    L.off_rect = take(sizeof(uint2) * VN1);
     L.off_tcount = take(4 * VN1);
     L.off_dkey0 = take(4 * VN1);
     L.off_dval0 = take(4 * VN1);
@@ -88,7 +87,8 @@ bool make_layout(int64_t N, int V, const vpgs_camera *cam, const vpgs_render_opt
     L.off_scan_look = take(8 * (size_t)L.scan_blocks_max);
     L.off_g2d = take(4 * 10 * (size_t)VN1);
     L.off_posedf = take(4 * 24 * (size_t)V);
-    L.off_cover = take(sizeof(Cover) * (size_t)VN1);
+    L.off_bin = take(sizeof(BinRec) * (size_t)VN1);
+    L.off_vis_idx = take(4 * (size_t)VN1);
     L.total = off;
     return true;
 }
@@ -99,9 +99,7 @@ RenderWs carve(void *base, const RenderLayout &L) {
     w.status = reinterpret_cast<uint32_t *>(b + L.off_status);
     w.counters = reinterpret_cast<uint32_t *>(b + L.off_counters);
     w.rec = reinterpret_cast<Rec *>(b + L.off_rec);
-    w.rect = reinterpret_cast<uint2 *>(b + L.off_rect);
     w.tcount = reinterpret_cast<uint32_t *>(b + L.off_tcount);
-    w.scan_a = nullptr;
     w.dkey[0] = reinterpret_cast<uint32_t *>(b + L.off_dkey0);
     w.dval[0] = reinterpret_cast<uint32_t *>(b + L.off_dval0);
     w.dkey[1] = reinterpret_cast<uint32_t *>(b + L.off_dkey1);
@@ -116,7 +114,8 @@ RenderWs carve(void *base, const RenderLayout &L) {
     w.scan_look = reinterpret_cast<unsigned long long *>(b + L.off_scan_look);
     w.g2d = reinterpret_cast<float *>(b + L.off_g2d);
     w.posedf = reinterpret_cast<float *>(b + L.off_posedf);
-    w.cover = reinterpret_cast<Cover *>(b + L.off_cover);
+    w.bin = reinterpret_cast<BinRec *>(b + L.off_bin);
+    w.vis_idx = reinterpret_cast<uint32_t *>(b + L.off_vis_idx);
     return w;
 }
 
@@ -283,7 +282,7 @@ vpgs_status vpgs_render_fwd(void *ws, size_t ws_bytes, const vpgs_gaussians *g,
     // the 2D gradient slots of visible Gaussians start at zero for a backward that reuses this call
     if (e == cudaSuccess) e = launch_preprocess_fwd(S.g, T_cw, n_views, S.cam, S.o, S.ws, true, s);
     int buf = 0;
-    if (e == cudaSuccess) e = build_tile_lists(S.g, n_views, S.cam, S.ws, S.L, &buf, nullptr, s);
+    if (e == cudaSuccess) e = build_tile_lists(S.g, n_views, S.cam, S.ws, S.L, &buf, s);
     if (e == cudaSuccess)
         e = launch_composite_fwd(S.ws, S.ws.ival[buf], n_views, S.cam, S.o, *out, opts->persistent_ctas, s);
     if (e == cudaSuccess) tag_set(make_tag(ws, ws_bytes, g, cam, T_cw, n_views, opts));
@@ -307,18 +306,17 @@ vpgs_status vpgs_render_bwd(void *ws, size_t ws_bytes, const vpgs_gaussians *g,
     if (!grads && !dL_dpose) return VPGS_OK;  // nothing to compute
     const BinTag tag = make_tag(ws, ws_bytes, g, cam, T_cw, n_views, opts);
     int buf = 0;
-    const uint32_t *vis = nullptr;
     cudaError_t e;
     if ((opts->flags & VPGS_RENDER_REUSE_BINNING) && tag_matches(tag)) {
         // the forward's projection and lists stand; its status word is kept, so an
         // error it recorded stops this pass too
         e = cudaSuccess;
-        tile_list_buffers(S.ws, S.L, &buf, &vis);
+        buf = tile_list_buffer(S.L);
     } else {
         // recompute projection, binning and per-tile sort
         e = cudaMemsetAsync(ws, 0, S.L.off_counters + 4 * CNT_N, s);
         if (e == cudaSuccess) e = launch_preprocess_fwd(S.g, T_cw, n_views, S.cam, S.o, S.ws, true, s);
-        if (e == cudaSuccess) e = build_tile_lists(S.g, n_views, S.cam, S.ws, S.L, &buf, &vis, s);
+        if (e == cudaSuccess) e = build_tile_lists(S.g, n_views, S.cam, S.ws, S.L, &buf, s);
         if (e == cudaSuccess) tag_set(tag);
         else tag_clear(ws);
     }
@@ -326,7 +324,7 @@ vpgs_status vpgs_render_bwd(void *ws, size_t ws_bytes, const vpgs_gaussians *g,
         e = launch_composite_bwd(S.ws, S.ws.ival[buf], n_views, S.cam, S.o, *fwd, dL_drgb, dL_ddepth,
                                  dL_dalpha, opts->persistent_ctas, s);
     if (e == cudaSuccess && (grads || dL_dpose))
-        e = launch_preprocess_bwd(S.g, T_cw, n_views, S.cam, S.o, S.ws, gg, dL_dpose, vis, s);
+        e = launch_preprocess_bwd(S.g, T_cw, n_views, S.cam, S.o, S.ws, gg, dL_dpose, s);
     return cuda_status(e);
 }
 

@@ -206,6 +206,16 @@ struct Cover {
 // packed span of one tile row: first tile column | last << 16 (first > last: empty)
 constexpr uint32_t kEmptySpan = 0xffffu;
 
+// What the emitting pass needs of one visible (view, Gaussian), in one 64-byte
+// record: a single aligned gather per Gaussian.
+struct __align__(16) BinRec {
+    float4 uv;     // (u_hi, v_hi, u_lo, v_lo)
+    uint2 rect;    // (tx0 | tx1 << 16, ty0 | ty1 << 16): bounding box in tiles
+    uint32_t cnt;  // tiles of the cover
+    uint32_t pad;
+    Cover cv;
+};
+
 // Tile columns [x, y] of tile row ty (x > y: none) within [tx_lo, tx_hi].
 VPGS_D int2 cover_row(const Cover &cv, float u_hi, float u_lo, float v_hi, float v_lo, int ty, int tx_lo,
                       int tx_hi, int tw_shift, int tile_h, int W, int H) {
@@ -241,9 +251,9 @@ struct RenderLayout {
     int64_t M_cap;      // instance capacity
     int32_t tile_bits;  // bits of a global tile id
     // offsets in bytes
-    size_t off_status, off_counters, off_rec, off_rect, off_tcount, off_scan_a, off_dkey0,
+    size_t off_status, off_counters, off_rec, off_tcount, off_dkey0,
         off_dval0, off_dkey1, off_dval1, off_ikey0, off_ival0, off_ikey1, off_ival1, off_ranges,
-        off_sort_hist, off_sort_look, off_scan_look, off_g2d, off_posedf, off_cover, total;
+        off_sort_hist, off_sort_look, off_scan_look, off_g2d, off_posedf, off_bin, off_vis_idx, total;
     int64_t sort_blocks_max, scan_blocks_max;
 };
 
@@ -261,9 +271,7 @@ struct RenderWs {
     uint32_t *status;
     uint32_t *counters;
     Rec *rec;
-    uint2 *rect;          // (tx0 | tx1 << 16, ty0 | ty1 << 16)
     uint32_t *tcount;
-    uint32_t *scan_a;     // scratch for scans
     uint32_t *dkey[2], *dval[2];
     uint32_t *ikey[2], *ival[2];
     uint2 *ranges;
@@ -272,7 +280,8 @@ struct RenderWs {
     unsigned long long *scan_look;
     float *g2d;           // [VN,10] 2D gradients
     float *posedf;        // [V,24] poses as double-float pairs
-    Cover *cover;         // [VN] row-wise tile-cover parameters of visible Gaussians
+    BinRec *bin;          // [VN] binning records of visible Gaussians
+    uint32_t *vis_idx;    // [VN] visible (view, Gaussian) indices in index order
 };
 
 // radix sort geometry

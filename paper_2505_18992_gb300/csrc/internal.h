@@ -41,15 +41,14 @@ cudaError_t launch_export_projection(const RenderWs &ws, int64_t VN, int32_t *ti
                                      cudaStream_t s);
 cudaError_t launch_preprocess_bwd(const GaussIn &g, const double *T_cw, int V, const CamParams &cam,
                                   const OptParams &o, const RenderWs &ws, const GaussGrad &gg,
-                                  double *dpose, const uint32_t *vis, cudaStream_t s);
+                                  double *dpose, cudaStream_t s);
 
 // render_bin.cu: visibility compaction, depth sort, instance emission, tile
 // sort and tile ranges.  On return ws.ival[*sorted_buf] holds the tile lists.
 cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, const RenderWs &ws,
-                             const RenderLayout &L, int *sorted_buf, const uint32_t **vis_list,
-                             cudaStream_t s);
-// Where build_tile_lists leaves its results for a layout (host only, no launch).
-void tile_list_buffers(const RenderWs &ws, const RenderLayout &L, int *sorted_buf, const uint32_t **vis_list);
+                             const RenderLayout &L, int *sorted_buf, cudaStream_t s);
+// Which ival buffer build_tile_lists leaves the tile lists in (host only, no launch).
+int tile_list_buffer(const RenderLayout &L);
 
 // render_comp.cu
 cudaError_t launch_composite_fwd(const RenderWs &ws, const uint32_t *ival, int V,

@@ -27,12 +27,13 @@ struct VisLoad {
 
 struct VisStore {
     const Rec *rec;
-    uint32_t *dkey, *dval;
+    uint32_t *dkey, *dval, *vis_idx;
     int64_t cap;
     __device__ void operator()(int64_t i, uint32_t pos, uint32_t v) const {
         if (v && (int64_t)pos < cap) {
             dkey[pos] = __float_as_uint(rec[i].r2.y);  // camera z > near_z > 0
             dval[pos] = (uint32_t)i;
+            vis_idx[pos] = (uint32_t)i;  // kept in index order (the sort reuses dval)
         }
     }
 };
@@ -56,11 +57,10 @@ struct OffsetStore {
 constexpr int kEmitThreads = 256;
 
 __global__ void __launch_bounds__(kEmitThreads)
-emit_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__ tcount,
-            const uint32_t *__restrict__ inst_off, const uint2 *__restrict__ rect,
-            const Rec *__restrict__ rec, const Cover *__restrict__ cover, const uint32_t *n_vis,
-            int64_t N, int64_t M_cap, CamParams cam, uint32_t *__restrict__ ikey,
-            uint32_t *__restrict__ ival, uint32_t *status) {
+emit_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__ inst_off,
+            const BinRec *__restrict__ bin, const uint32_t *n_vis, const uint32_t *n_inst, int64_t N,
+            int64_t M_cap, CamParams cam, uint32_t *__restrict__ ikey, uint32_t *__restrict__ ival,
+            uint32_t *status) {
     __shared__ uint32_t s_start[kEmitThreads], s_id[kEmitThreads], s_vb[kEmitThreads];
     __shared__ uint2 s_rect[kEmitThreads];
     __shared__ float4 s_uv[kEmitThreads];
@@ -75,15 +75,15 @@ emit_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__ tcou
     if (tid < nb) {
         const int64_t r = r0 + tid;
         const uint32_t id = dval[r];
-        const uint32_t cnt = tcount[id];
-        const uint32_t off = inst_off[r] - base;
-        s_start[tid] = off;
+        const BinRec br = bin[id];
+        s_start[tid] = inst_off[r] - base;
         s_id[tid] = id;
-        s_rect[tid] = rect[id];
-        s_uv[tid] = rec[id].r0;
-        s_cv[tid] = cover[id];
+        s_rect[tid] = br.rect;
+        s_uv[tid] = br.uv;
+        s_cv[tid] = br.cv;
         s_vb[tid] = (uint32_t)(id / N) * (uint32_t)cam.T;
-        if (tid == nb - 1) s_total = off + cnt;
+        // the block's end offset: the next block's start, or the total
+        if (tid == nb - 1) s_total = (r0 + nb < nv ? inst_off[r0 + nb] : *n_inst) - base;
     }
     __syncthreads();
     const uint32_t total = s_total;
@@ -100,7 +100,6 @@ emit_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__ tcou
         }
         uint32_t local = e - s_start[lo];
         const uint2 rc = s_rect[lo];
-        const float4 uv = s_uv[lo];
         const Cover cv = s_cv[lo];
         const int tx_lo = (int)(rc.x & 0xffffu), tx_hi = (int)(rc.x >> 16);
         const int ty_lo = (int)(rc.y & 0xffffu), ty_hi = (int)(rc.y >> 16);
@@ -123,6 +122,7 @@ emit_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__ tcou
                 }
             }
         } else {
+            const float4 uv = s_uv[lo];
             for (int ty = ty_lo; ty <= ty_hi; ++ty) {
                 const int2 sp = cover_row(cv, uv.x, uv.z, uv.y, uv.w, ty, tx_lo, tx_hi, cam.tw_shift,
                                           cam.tile_h, cam.W, cam.H);
@@ -155,12 +155,9 @@ __global__ void tile_ranges_kernel(const uint32_t *__restrict__ keys, int64_t ca
     }
 }
 
-void tile_list_buffers(const RenderWs &ws, const RenderLayout &L, int *sorted_buf, const uint32_t **vis_list) {
+int tile_list_buffer(const RenderLayout &L) {
     SortPass ps[kMaxSortPasses];
-    const bool depth_in1 = (plan_passes(0, 32, ps) & 1) != 0;
-    const bool tile_in1 = (plan_passes(0, L.tile_bits, ps) & 1) != 0;
-    *vis_list = depth_in1 ? ws.dval[1] : ws.dval[0];
-    *sorted_buf = tile_in1 ? 1 : 0;
+    return (plan_passes(0, L.tile_bits, ps) & 1) != 0 ? 1 : 0;
 }
 
 int device_sm_count() {
@@ -175,14 +172,13 @@ int device_sm_count() {
 }
 
 cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, const RenderWs &ws,
-                             const RenderLayout &L, int *sorted_buf, const uint32_t **vis_list,
-                             cudaStream_t s) {
+                             const RenderLayout &L, int *sorted_buf, cudaStream_t s) {
     cudaError_t e;
     const int sms = device_sm_count();
     uint32_t *n_vis = ws.counters + CNT_VISIBLE;
     uint32_t *n_inst = ws.counters + CNT_INSTANCES;
     // 1. compaction of visible (view, Gaussian) pairs
-    e = launch_scan("scan_visible", VisLoad{ws.tcount}, VisStore{ws.rec, ws.dkey[0], ws.dval[0], L.VN},
+    e = launch_scan("scan_visible", VisLoad{ws.tcount}, VisStore{ws.rec, ws.dkey[0], ws.dval[0], ws.vis_idx, L.VN},
                     L.VN, nullptr, ws.counters + CNT_TICKET_A, ws.scan_look, n_vis, ws.status, s);
     if (e != cudaSuccess) return e;
     // 2. depth sort
@@ -192,11 +188,7 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
                          &in1, kDepthSortItems, VPGS_DEPTH_LOOKBACK != 0, ws.counters + CNT_TICKET_A,
                          ws.scan_look);
     if (e != cudaSuccess) return e;
-    const uint32_t *dval = in1 ? ws.dval[1] : ws.dval[0];
-    if (vis_list) *vis_list = dval;  // visible (view, Gaussian) records in depth order
-    int expect_buf = 0;
-    const uint32_t *expect_vis = nullptr;
-    tile_list_buffers(ws, L, &expect_buf, &expect_vis);
+    const uint32_t *dval = in1 ? ws.dval[1] : ws.dval[0];  // visible records in depth order
     uint32_t *inst_off = in1 ? ws.dkey[0] : ws.dkey[1];  // the depth-sort buffer not holding the result
     // 3. instance offsets, then emission
     e = launch_scan("scan_offsets", CountLoad{ws.tcount, dval}, OffsetStore{inst_off}, L.VN, n_vis,
@@ -204,9 +196,8 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
     if (e != cudaSuccess) return e;
     VPGS_LAUNCH("emit_instances", s,
                 emit_kernel<<<(unsigned)std::max<int64_t>((L.VN + kEmitThreads - 1) / kEmitThreads, 1),
-                              kEmitThreads, 0, s>>>(dval, ws.tcount, inst_off, ws.rect, ws.rec, ws.cover,
-                                                    n_vis, L.N, L.M_cap, cam, ws.ikey[0], ws.ival[0],
-                                                    ws.status));
+                              kEmitThreads, 0, s>>>(dval, inst_off, ws.bin, n_vis, n_inst, L.N, L.M_cap,
+                                                    cam, ws.ikey[0], ws.ival[0], ws.status));
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // 4. stable sort by tile id
@@ -216,7 +207,7 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
                          ws.counters + CNT_TICKET_A, ws.scan_look);
     if (e != cudaSuccess) return e;
     *sorted_buf = in1 ? 1 : 0;
-    if (dval != expect_vis || *sorted_buf != expect_buf) return cudaErrorUnknown;  // never: same pass plans
+    if (*sorted_buf != tile_list_buffer(L)) return cudaErrorUnknown;  // never: same pass plan
     // 5. tile ranges
     const int n_tiles = V * cam.T;
     e = cudaMemsetAsync(ws.ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);

@@ -7,8 +7,9 @@
 //   alpha = min(alpha_max, o 2^-((w1.d)^2 + (w2.d)^2)), d = pixel - mean, with
 //           the whitening rows w scaled by sqrt(log2(e)/2) when the record is made
 //   skip alpha < alpha_min; stop before T (1 - alpha) < t_min
-// A warp skips a Gaussian outright when its widened y extent misses all of the
-// warp's pixel rows (alpha < alpha_min at every one of them).
+// Each warp first compacts the staged batch into its own list of the Gaussians
+// whose widened y extent reaches one of the warp's pixel rows (at the others
+// alpha < alpha_min at every pixel of the warp), then walks only that list.
 //   C += alpha T c, D += alpha T z, T *= 1 - alpha
 // Means are made tile-local when staged ((u_hi - x0) + u_lo), so d keeps
 // ~1e-7 px accuracy anywhere in the image.
@@ -55,6 +56,24 @@ VPGS_D float2 warp_rows(const float (&pyl)[kPix]) {
     return make_float2(0.5f * (lo + hi), 0.5f * (hi - lo));
 }
 
+// Compacts the batch positions [0, n) whose Gaussian's widened y extent reaches
+// the warp's pixel rows into list, in ascending order; returns how many
+// (warp-uniform).  All 32 lanes take part.
+VPGS_D int warp_list(const float4 *s0, const float4 *s1, int n, float2 band, uint16_t *list, int lane) {
+    const uint32_t below = (1u << lane) - 1u;
+    int cnt = 0;
+    for (int c0 = 0; c0 < n; c0 += 32) {
+        const int k = c0 + lane;
+        bool touch = false;
+        if (k < n) touch = fabsf(s0[k].y - band.x) <= s1[k].w + band.y;
+        const uint32_t m = __ballot_sync(0xffffffffu, touch);
+        if (touch) list[cnt + __popc(m & below)] = (uint16_t)k;
+        cnt += __popc(m);
+    }
+    __syncwarp();
+    return cnt;
+}
+
 // record -> shared staging: s0 = (u, v) tile-local, w1; s1 = w2, opacity, widened
 // y half extent; s2 = colour, camera z
 VPGS_D void stage(const Rec &r, float ox, float oy, float4 &a, float4 &b, float4 &c) {
@@ -70,9 +89,11 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
     extern __shared__ float4 smem[];
     const int NT = blockDim.x;
     float4 *s0 = smem, *s1 = smem + NT, *s2 = smem + 2 * NT;
+    uint16_t *s_wl = reinterpret_cast<uint16_t *>(smem + 3 * NT);  // [NW][NT] per-warp lists
     __shared__ int s_tile;
     if (*status != 0u) return;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
+    uint16_t *wl = s_wl + (size_t)(tid >> 5) * NT;
     const int half = cam.tile_h / kPix;
     const int lx = tid % cam.tile_w, ly = tid / cam.tile_w;
     const float pxl = (float)lx + 0.5f;
@@ -111,11 +132,11 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
             const int j = b0 + tid;
             if (j < end) stage(rec[ival[j]], ox, oy, s0[tid], s1[tid], s2[tid]);
             __syncthreads();
+            const int nl = warp_list(s0, s1, min(NT, end - b0), band, wl, lane);
             if (!all_done) {
-                const int nb = min(NT, end - b0);
-                for (int k = 0; k < nb; ++k) {
+                for (int i = 0; i < nl; ++i) {
+                    const int k = wl[i];
                     const float4 a = s0[k], b = s1[k];
-                    if (fabsf(a.y - band.x) > b.w + band.y) continue;  // warp-uniform
                     bool fin = true;
 #pragma unroll
                     for (int q = 0; q < kPix; ++q) {
@@ -269,7 +290,8 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
     const int NW = NT >> 5;
     float4 *s0 = smem, *s1 = smem + NT, *s2 = smem + 2 * NT;
     uint32_t *s_id = reinterpret_cast<uint32_t *>(smem + 3 * NT);
-    float *s_part = reinterpret_cast<float *>(s_id + NT);  // [NW][NT][kPartStride]
+    uint16_t *s_wl = reinterpret_cast<uint16_t *>(s_id + NT);             // [NW][NT] per-warp lists
+    float *s_part = reinterpret_cast<float *>(s_wl + (size_t)NW * NT);  // [NW][NT][kPartStride]
     __shared__ int s_tile;
     __shared__ int s_max;
     if (*status != 0u) return;
@@ -281,6 +303,7 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
 #pragma unroll
     for (int q = 0; q < kPix; ++q) pyl[q] = (float)(ly + q * half) + 0.5f;
     const float2 band = warp_rows(pyl);
+    uint16_t *wl = s_wl + (size_t)warp * NT;
     float *my_part = s_part + (size_t)warp * NT * kPartStride;
     const int slot = red_slot(lane);
     // hands one warp total (this lane's slot) of Gaussian k to the combination scheme
@@ -352,11 +375,11 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                 for (int e = tid; e < nb * kPartStride; e += NT) s_part[e] = 0.f;
             __syncthreads();
             const int k_end = min(nb, warp_max - (b0 - start));  // warp-uniform
+            const int nl = warp_list(s0, s1, k_end, band, wl, lane);
             // back to front
-            for (int kk = k_end - 1; kk >= 0; --kk) {
-                const float4 a = s0[kk], b = s1[kk];
-                if (fabsf(a.y - band.x) > b.w + band.y) continue;  // warp-uniform
-                const float4 c = s2[kk];
+            for (int i = nl - 1; i >= 0; --i) {
+                const int kk = wl[i];
+                const float4 a = s0[kk], b = s1[kk], c = s2[kk];
                 float v[10];
 #pragma unroll
                 for (int q = 0; q < 10; ++q) v[q] = 0.f;
@@ -407,7 +430,8 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
 
 static size_t comp_smem(int NT, bool bwd) {
     const size_t parts = kAcc == 1 ? (size_t)(NT / 32) * NT * kPartStride : (kAcc == 2 ? (size_t)NT * kPartStride : 0);
-    return sizeof(float4) * 3 * NT + (bwd ? sizeof(uint32_t) * NT + sizeof(float) * parts : 0);
+    const size_t lists = sizeof(uint16_t) * (size_t)(NT / 32) * NT;
+    return sizeof(float4) * 3 * NT + lists + (bwd ? sizeof(uint32_t) * NT + sizeof(float) * parts : 0);
 }
 
 static int persistent_grid(const void *kernel, int B, size_t smem, int per_sm, int n_tiles) {

@@ -75,123 +75,200 @@ VPGS_D void project(const PoseDF &P, float mx, float my, float mz, float sx, flo
     p.det = (c0 * c0 + c1 * c1 + c2 * c2) + dil * (n0 + n1) + dil * dil;
 }
 
+// Conservative FP32 pre-cull.  False only when the Gaussian certainly lies
+// behind the near plane or its whole alpha_min extent certainly misses the
+// image: p_c carries a 1e-5 relative error bound (about 40 times the FP32
+// rounding of the transform), and the screen half width is bounded through
+// Sigma'_xx <= (fx/z)^2 (1 + (x/z)^2) s_max^2 + dilation (and likewise in y),
+// plus a pixel of slack.  The exact double-float path decides everything else.
+VPGS_D bool maybe_in_view(const PoseDF &P, float mx, float my, float mz, float smax, float kq,
+                          const CamParams &cam, const OptParams &o) {
+    float pc[3], tol[3];
+    const float am = fabsf(mx) + fabsf(my) + fabsf(mz);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        pc[r] = fmaf(P.R[3 * r].hi, mx, fmaf(P.R[3 * r + 1].hi, my, fmaf(P.R[3 * r + 2].hi, mz, P.t[r].hi)));
+        tol[r] = 1e-5f * (am + fabsf(P.t[r].hi)) + 1e-6f;
+    }
+    if (pc[2] + tol[2] <= o.near_z) return false;
+    const float zl = pc[2] - tol[2];
+    if (!(zl > 1e-3f)) return true;  // too close to z = 0 for a bound: the exact path decides
+    const float iz = 1.0f / zl;
+    const float kqc = fmaxf(kq, 0.f);
+    const float xr = (fabsf(pc[0]) + tol[0]) * iz, yr = (fabsf(pc[1]) + tol[1]) * iz;
+    const float rx = sqrtf(kqc * (cam.fx * cam.fx * iz * iz * (1.f + xr * xr) * smax * smax + o.dilation));
+    const float ry = sqrtf(kqc * (cam.fy * cam.fy * iz * iz * (1.f + yr * yr) * smax * smax + o.dilation));
+    // image mean and its error bound
+    const float u = fmaf(cam.fx, pc[0] / pc[2], cam.cx), v = fmaf(cam.fy, pc[1] / pc[2], cam.cy);
+    const float eu = 2.f * cam.fx * (tol[0] + xr * tol[2]) * iz + 1e-4f * fabsf(u);
+    const float ev = 2.f * cam.fy * (tol[1] + yr * tol[2]) * iz + 1e-4f * fabsf(v);
+    const float sx = rx + eu + 1.f, sy = ry + ev + 1.f;
+    return !(u + sx < 0.f || u - sx > (float)cam.W || v + sy < 0.f || v - sy > (float)cam.H);
+}
+
 __global__ void pose_prepare_kernel(const double *__restrict__ T_cw, int V, float *posedf) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v < V) pose_to_df(T_cw + 16 * v, posedf + 24 * v);
 }
 
-__global__ void __launch_bounds__(256)
-preprocess_fwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamParams cam, OptParams o,
-                      RenderWs ws, bool zero_g2d) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t VN = (int64_t)V * g.N;
-    if (i >= VN) return;
-    const int v = (int)(i / g.N);
-    const int64_t gi = i - (int64_t)v * g.N;
-    int64_t nl = g.N;
-    if (g.n_dev) nl = min(nl, (int64_t)*g.n_dev);
-    uint32_t cnt = 0;
-    uint2 rc = make_uint2(0, 0);
-    Rec R;
+// Exact projection, extent and tile cover of one (view, Gaussian) that passed
+// the pre-cull.  Returns its tile count (0: culled) and fills R and B when > 0.
+VPGS_D uint32_t project_one(const PoseDF &P, float mx, float my, float mz, float sx, float sy, float sz,
+                            float4 q, float op, float cr, float cg, float cb, const CamParams &cam,
+                            const OptParams &o, uint32_t *status, Rec &R, BinRec &B) {
+    Proj p;
+    project(P, mx, my, mz, sx, sy, sz, q.x, q.y, q.z, q.w, cam, o.dilation, p);
+    const bool in_front = p.pc[2].hi > o.near_z || (p.pc[2].hi == o.near_z && p.pc[2].lo > 0.f);
+    if (!in_front) return 0u;
+    // eigen-decomposition of Sigma' (2x2 symmetric) for the whitening rows
+    const float h = 0.5f * (p.A - p.C);
+    const float r = hypotf(h, p.B);
+    const float lam1 = 0.5f * (p.A + p.C) + r;
+    const float lam2 = p.det / lam1;
+    float ex, ey;
+    if (r == 0.f) {
+        ex = 1.f; ey = 0.f;
+    } else if (h >= 0.f) {
+        ex = h + r; ey = p.B;
+    } else {
+        ex = p.B; ey = r - h;
+    }
+    const float en = 1.0f / sqrtf(ex * ex + ey * ey);
+    ex *= en; ey *= en;
+    const float s1 = kRowScale / sqrtf(lam1), s2 = kRowScale / sqrtf(lam2);
+    // opacity-aware extent
+    const float kq = 2.0f * logf(op / o.alpha_min);
+    const float rx = sqrtf(fmaxf(kq, 0.f) * p.A), ry = sqrtf(fmaxf(kq, 0.f) * p.C);
+    const float rxe = rx * (1.0f + 1e-5f) + 2e-3f, rye = ry * (1.0f + 1e-5f) + 2e-3f;
+    const float uf = p.u.hi, vf = p.v.hi;
+    float lx = (uf - 0.5f - rxe) + p.u.lo, hx = (uf - 0.5f + rxe) + p.u.lo;
+    float ly = (vf - 0.5f - rye) + p.v.lo, hy = (vf - 0.5f + rye) + p.v.lo;
+    if (!isfinite(lx + hx + ly + hy + s1 + s2 + ex + ey)) {
+        set_status(status, VPGS_ERR_NONFINITE);
+        return 0u;
+    }
+    lx = fmaxf(lx, -1.f); hx = fminf(hx, (float)cam.W);
+    ly = fmaxf(ly, -1.f); hy = fminf(hy, (float)cam.H);
+    const int x0 = max(0, (int)ceilf(lx)), x1 = min(cam.W - 1, (int)floorf(hx));
+    const int y0 = max(0, (int)ceilf(ly)), y1 = min(cam.H - 1, (int)floorf(hy));
+    if (!(x0 <= x1 && y0 <= y1)) return 0u;
+    const int tx0 = x0 >> cam.tw_shift, tx1 = x1 >> cam.tw_shift;
+    const int ty0 = y0 / cam.tile_h, ty1 = y1 / cam.tile_h;
     Cover cv;
-    if (gi < nl) {
-        const float mx = g.means[3 * gi], my = g.means[3 * gi + 1], mz = g.means[3 * gi + 2];
-        const float sx = g.scales[3 * gi], sy = g.scales[3 * gi + 1], sz = g.scales[3 * gi + 2];
-        const float4 q = reinterpret_cast<const float4 *>(g.quats)[gi];
-        const float op = g.opac[gi];
-        const float cr = g.colors[3 * gi], cg = g.colors[3 * gi + 1], cb = g.colors[3 * gi + 2];
-        const float chk = mx + my + mz + sx + sy + sz + q.x + q.y + q.z + q.w + op + cr + cg + cb;
-        if (!isfinite(chk)) {
-            set_status(ws.status, VPGS_ERR_NONFINITE);
-        } else if (op >= o.alpha_min) {
-            PoseDF P;
-            load_pose(ws.posedf + 24 * v, P);
-            Proj p;
-            project(P, mx, my, mz, sx, sy, sz, q.x, q.y, q.z, q.w, cam, o.dilation, p);
-            const bool in_front = p.pc[2].hi > o.near_z || (p.pc[2].hi == o.near_z && p.pc[2].lo > 0.f);
-            if (in_front) {
-                // eigen-decomposition of Sigma' (2x2 symmetric) for the whitening rows
-                const float h = 0.5f * (p.A - p.C);
-                const float r = hypotf(h, p.B);
-                const float lam1 = 0.5f * (p.A + p.C) + r;
-                const float lam2 = p.det / lam1;
-                float ex, ey;
-                if (r == 0.f) {
-                    ex = 1.f; ey = 0.f;
-                } else if (h >= 0.f) {
-                    ex = h + r; ey = p.B;
-                } else {
-                    ex = p.B; ey = r - h;
-                }
-                const float en = 1.0f / sqrtf(ex * ex + ey * ey);
-                ex *= en; ey *= en;
-                const float s1 = kRowScale / sqrtf(lam1), s2 = kRowScale / sqrtf(lam2);
-                // opacity-aware extent
-                const float kq = 2.0f * logf(op / o.alpha_min);
-                const float rx = sqrtf(fmaxf(kq, 0.f) * p.A), ry = sqrtf(fmaxf(kq, 0.f) * p.C);
-                const float rxe = rx * (1.0f + 1e-5f) + 2e-3f, rye = ry * (1.0f + 1e-5f) + 2e-3f;
-                const float uf = p.u.hi, vf = p.v.hi;
-                float lx = (uf - 0.5f - rxe) + p.u.lo, hx = (uf - 0.5f + rxe) + p.u.lo;
-                float ly = (vf - 0.5f - rye) + p.v.lo, hy = (vf - 0.5f + rye) + p.v.lo;
-                const bool fin = isfinite(lx + hx + ly + hy + s1 + s2 + ex + ey);
-                if (!fin) {
-                    set_status(ws.status, VPGS_ERR_NONFINITE);
-                } else {
-                    lx = fmaxf(lx, -1.f); hx = fminf(hx, (float)cam.W);
-                    ly = fmaxf(ly, -1.f); hy = fminf(hy, (float)cam.H);
-                    const int x0 = max(0, (int)ceilf(lx)), x1 = min(cam.W - 1, (int)floorf(hx));
-                    const int y0 = max(0, (int)ceilf(ly)), y1 = min(cam.H - 1, (int)floorf(hy));
-                    if (x0 <= x1 && y0 <= y1) {
-                        const int tx0 = x0 >> cam.tw_shift, tx1 = x1 >> cam.tw_shift;
-                        const int ty0 = y0 / cam.tile_h, ty1 = y1 / cam.tile_h;
-                        const float kc = fmaxf(kq, 0.f), iC = 1.0f / p.C, dC = p.det * iC;
-                        cv.a = make_float4(ry, fmaf(ry, 1e-5f, 2e-3f), -p.B * sqrtf(kc / p.A), p.B * iC);
-                        cv.b = make_float4(kc * dC, dC * iC, fmaf(rx, 1e-5f, 2e-3f), 0.f);
-                        const int rows = ty1 - ty0 + 1;
-                        if (rows <= kCoverRows) {
-                            // few rows: keep the spans themselves for the emitting pass
-                            uint32_t pk[kCoverRows];
+    const float kc = fmaxf(kq, 0.f), iC = 1.0f / p.C, dC = p.det * iC;
+    cv.a = make_float4(ry, fmaf(ry, 1e-5f, 2e-3f), -p.B * sqrtf(kc / p.A), p.B * iC);
+    cv.b = make_float4(kc * dC, dC * iC, fmaf(rx, 1e-5f, 2e-3f), 0.f);
+    uint32_t cnt = 0;
+    const int rows = ty1 - ty0 + 1;
+    if (rows <= kCoverRows) {
+        // few rows: keep the spans themselves for the emitting pass
+        uint32_t pk[kCoverRows];
 #pragma unroll
-                            for (int r = 0; r < kCoverRows; ++r) {
-                                pk[r] = kEmptySpan;
-                                if (r < rows) {
-                                    const int2 sp = cover_row(cv, p.u.hi, p.u.lo, p.v.hi, p.v.lo, ty0 + r, tx0,
-                                                              tx1, cam.tw_shift, cam.tile_h, cam.W, cam.H);
-                                    if (sp.x <= sp.y) {
-                                        cnt += (uint32_t)(sp.y - sp.x + 1);
-                                        pk[r] = (uint32_t)sp.x | ((uint32_t)sp.y << 16);
-                                    }
-                                }
-                            }
-                            cv.a = make_float4(__uint_as_float(pk[0]), __uint_as_float(pk[1]),
-                                               __uint_as_float(pk[2]), __uint_as_float(pk[3]));
-                            cv.b = make_float4(__uint_as_float(pk[4]), __uint_as_float(pk[5]),
-                                               __uint_as_float(pk[6]), __uint_as_float(pk[7]));
-                        } else {
-                            for (int ty = ty0; ty <= ty1; ++ty) {
-                                const int2 sp = cover_row(cv, p.u.hi, p.u.lo, p.v.hi, p.v.lo, ty, tx0, tx1,
-                                                          cam.tw_shift, cam.tile_h, cam.W, cam.H);
-                                if (sp.x <= sp.y) cnt += (uint32_t)(sp.y - sp.x + 1);
-                            }
-                        }
-                        rc = make_uint2((uint32_t)tx0 | ((uint32_t)tx1 << 16),
-                                        (uint32_t)ty0 | ((uint32_t)ty1 << 16));
-                        R.r0 = make_float4(p.u.hi, p.v.hi, p.u.lo, p.v.lo);
-                        R.r1 = make_float4(ex * s1, ey * s1, -ey * s2, ex * s2);
-                        R.r2 = make_float4(op, p.pz, cr, cg);
-                        R.r3 = make_float4(cb, rxe, rye, kq);
-                    }
+        for (int k = 0; k < kCoverRows; ++k) {
+            pk[k] = kEmptySpan;
+            if (k < rows) {
+                const int2 sp = cover_row(cv, p.u.hi, p.u.lo, p.v.hi, p.v.lo, ty0 + k, tx0, tx1, cam.tw_shift,
+                                          cam.tile_h, cam.W, cam.H);
+                if (sp.x <= sp.y) {
+                    cnt += (uint32_t)(sp.y - sp.x + 1);
+                    pk[k] = (uint32_t)sp.x | ((uint32_t)sp.y << 16);
                 }
             }
         }
+        cv.a = make_float4(__uint_as_float(pk[0]), __uint_as_float(pk[1]), __uint_as_float(pk[2]),
+                           __uint_as_float(pk[3]));
+        cv.b = make_float4(__uint_as_float(pk[4]), __uint_as_float(pk[5]), __uint_as_float(pk[6]),
+                           __uint_as_float(pk[7]));
+    } else {
+        for (int ty = ty0; ty <= ty1; ++ty) {
+            const int2 sp = cover_row(cv, p.u.hi, p.u.lo, p.v.hi, p.v.lo, ty, tx0, tx1, cam.tw_shift, cam.tile_h,
+                                      cam.W, cam.H);
+            if (sp.x <= sp.y) cnt += (uint32_t)(sp.y - sp.x + 1);
+        }
     }
-    ws.tcount[i] = cnt;
-    ws.rect[i] = rc;
+    if (cnt == 0u) return 0u;
+    R.r0 = make_float4(p.u.hi, p.v.hi, p.u.lo, p.v.lo);
+    R.r1 = make_float4(ex * s1, ey * s1, -ey * s2, ex * s2);
+    R.r2 = make_float4(op, p.pz, cr, cg);
+    R.r3 = make_float4(cb, rxe, rye, kq);
+    B.uv = R.r0;
+    B.rect = make_uint2((uint32_t)tx0 | ((uint32_t)tx1 << 16), (uint32_t)ty0 | ((uint32_t)ty1 << 16));
+    B.cnt = cnt;
+    B.pad = 0u;
+    B.cv = cv;
+    return cnt;
+}
+
+// One thread per (view, Gaussian) for the finiteness check and the FP32
+// pre-cull; the block then compacts its candidates so that the exact
+// projection runs on consecutive threads (full warps) instead of on the
+// scattered lanes that passed.
+constexpr int kPreThreads = 256;
+
+__global__ void __launch_bounds__(kPreThreads)
+preprocess_fwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamParams cam, OptParams o,
+                      RenderWs ws, bool zero_g2d) {
+    __shared__ uint16_t s_cand[kPreThreads];
+    __shared__ int s_wcnt[kPreThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t i0 = (int64_t)blockIdx.x * kPreThreads;
+    const int64_t i = i0 + tid;
+    const int64_t VN = (int64_t)V * g.N;
+    int64_t nl = g.N;
+    if (g.n_dev) nl = min(nl, (int64_t)*g.n_dev);
+    bool cand = false;
+    if (i < VN) {
+        const int v = (int)(i / g.N);
+        const int64_t gi = i - (int64_t)v * g.N;
+        if (gi < nl) {
+            const float mx = g.means[3 * gi], my = g.means[3 * gi + 1], mz = g.means[3 * gi + 2];
+            const float sx = g.scales[3 * gi], sy = g.scales[3 * gi + 1], sz = g.scales[3 * gi + 2];
+            const float4 q = reinterpret_cast<const float4 *>(g.quats)[gi];
+            const float op = g.opac[gi];
+            const float cr = g.colors[3 * gi], cg = g.colors[3 * gi + 1], cb = g.colors[3 * gi + 2];
+            const float chk = mx + my + mz + sx + sy + sz + q.x + q.y + q.z + q.w + op + cr + cg + cb;
+            if (!isfinite(chk)) {
+                set_status(ws.status, VPGS_ERR_NONFINITE);
+            } else if (op >= o.alpha_min) {
+                PoseDF P;
+                load_pose(ws.posedf + 24 * v, P);
+                cand = maybe_in_view(P, mx, my, mz, fmaxf(fabsf(sx), fmaxf(fabsf(sy), fabsf(sz))),
+                                     2.0f * logf(op / o.alpha_min), cam, o);
+            }
+        }
+        if (!cand) ws.tcount[i] = 0u;
+    }
+    // block compaction of the candidates
+    const uint32_t m = __ballot_sync(0xffffffffu, cand);
+    if (lane == 0) s_wcnt[warp] = __popc(m);
+    __syncthreads();
+    int base = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < kPreThreads / 32; ++w) {
+        const int c = s_wcnt[w];
+        base += w < warp ? c : 0;
+        total += c;
+    }
+    if (cand) s_cand[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)tid;
+    __syncthreads();
+    if (tid >= total) return;
+    const int64_t ic = i0 + s_cand[tid];
+    const int v = (int)(ic / g.N);
+    const int64_t gi = ic - (int64_t)v * g.N;
+    const float4 q = reinterpret_cast<const float4 *>(g.quats)[gi];
+    PoseDF P;
+    load_pose(ws.posedf + 24 * v, P);
+    Rec R;
+    BinRec B;
+    const uint32_t cnt = project_one(P, g.means[3 * gi], g.means[3 * gi + 1], g.means[3 * gi + 2], g.scales[3 * gi],
+                                     g.scales[3 * gi + 1], g.scales[3 * gi + 2], q, g.opac[gi], g.colors[3 * gi],
+                                     g.colors[3 * gi + 1], g.colors[3 * gi + 2], cam, o, ws.status, R, B);
+    ws.tcount[ic] = cnt;
     if (cnt) {
-        ws.rec[i] = R;
-        ws.cover[i] = cv;
+        ws.rec[ic] = R;
+        ws.bin[ic] = B;
         if (zero_g2d) {
-            float2 *z2 = reinterpret_cast<float2 *>(ws.g2d + 10 * i);
+            float2 *z2 = reinterpret_cast<float2 *>(ws.g2d + 10 * ic);
 #pragma unroll
             for (int k = 0; k < 5; ++k) z2[k] = make_float2(0.f, 0.f);
         }
@@ -204,7 +281,11 @@ VPGS_D float warp_sum(float x) {
     return x;
 }
 
-__global__ void __launch_bounds__(256)
+// blocks per SM the register budget must allow (3: 24 warps to hide gather latency)
+#ifndef VPGS_PRE_BWD_MINB
+#define VPGS_PRE_BWD_MINB 3
+#endif
+__global__ void __launch_bounds__(256, VPGS_PRE_BWD_MINB)
 preprocess_bwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamParams cam, OptParams o,
                       RenderWs ws, GaussGrad gg, double *dpose, const uint32_t *__restrict__ vis,
                       const uint32_t *n_vis) {
@@ -214,7 +295,7 @@ preprocess_bwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamPara
     int64_t gi = tix;
     bool live;
     if (vis) {
-        // one view: walk the visible list, so every lane of a warp has work
+        // one view: walk the visible list (index order), so every lane of a warp has work
         const int64_t nv = *n_vis;
         if ((int64_t)blockIdx.x * blockDim.x >= nv) return;  // whole block past the list
         live = tix < nv;
@@ -232,10 +313,12 @@ preprocess_bwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamPara
         sx = g.scales[3 * gi]; sy = g.scales[3 * gi + 1]; sz = g.scales[3 * gi + 2];
         q = reinterpret_cast<const float4 *>(g.quats)[gi];
     }
+    bool any = false;  // visible in some view
     for (int v = 0; v < V; ++v) {
         float pv[6] = {0, 0, 0, 0, 0, 0};
         const int64_t i = (int64_t)v * g.N + gi;
         if (live && ws.tcount[i] > 0) {
+            any = true;
             const float *g2 = ws.g2d + 10 * i;  // [u, v, a, b, c, o, r, g, b, z]
             const float2 a01 = reinterpret_cast<const float2 *>(g2)[0];
             const float2 a23 = reinterpret_cast<const float2 *>(g2)[1];
@@ -352,22 +435,25 @@ preprocess_bwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamPara
             __syncthreads();
         }
     }
-    if (!live) return;
+    if (!live || !any) return;
+    // += as fire-and-forget reductions: no load round trip (one thread per Gaussian,
+    // so nothing contends)
+    auto add = [](float *p, float x) {
+        if (x != 0.f) atomicAdd(p, x);
+    };
     if (gg.means) {
-        gg.means[3 * gi] += gm[0]; gg.means[3 * gi + 1] += gm[1]; gg.means[3 * gi + 2] += gm[2];
+        add(gg.means + 3 * gi, gm[0]); add(gg.means + 3 * gi + 1, gm[1]); add(gg.means + 3 * gi + 2, gm[2]);
     }
     if (gg.scales) {
-        gg.scales[3 * gi] += gs[0]; gg.scales[3 * gi + 1] += gs[1]; gg.scales[3 * gi + 2] += gs[2];
+        add(gg.scales + 3 * gi, gs[0]); add(gg.scales + 3 * gi + 1, gs[1]); add(gg.scales + 3 * gi + 2, gs[2]);
     }
     if (gg.quats) {
-        float4 *qq = reinterpret_cast<float4 *>(gg.quats) + gi;
-        float4 t = *qq;
-        t.x += gq[0]; t.y += gq[1]; t.z += gq[2]; t.w += gq[3];
-        *qq = t;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) add(gg.quats + 4 * gi + k, gq[k]);
     }
-    if (gg.opac) gg.opac[gi] += go;
+    if (gg.opac) add(gg.opac + gi, go);
     if (gg.colors) {
-        gg.colors[3 * gi] += gc[0]; gg.colors[3 * gi + 1] += gc[1]; gg.colors[3 * gi + 2] += gc[2];
+        add(gg.colors + 3 * gi, gc[0]); add(gg.colors + 3 * gi + 1, gc[1]); add(gg.colors + 3 * gi + 2, gc[2]);
     }
 }
 
@@ -379,7 +465,7 @@ __global__ void export_projection_kernel(RenderWs ws, int64_t VN, int32_t *tile_
     const uint32_t cnt = ws.tcount[i];
     if (tile_count) tile_count[i] = (int32_t)cnt;
     if (!cnt) return;
-    const uint2 rc = ws.rect[i];
+    const uint2 rc = ws.bin[i].rect;
     if (tile_rect) {
         tile_rect[4 * i] = (int32_t)(rc.x & 0xffffu);
         tile_rect[4 * i + 1] = (int32_t)(rc.x >> 16);
@@ -416,16 +502,16 @@ cudaError_t launch_preprocess_fwd(const GaussIn &g, const double *T_cw, int V, c
     VPGS_LAUNCH("pose_prepare", s, pose_prepare_kernel<<<(V + 63) / 64, 64, 0, s>>>(T_cw, V, ws.posedf));
     if (VN == 0) return cudaGetLastError();
     VPGS_LAUNCH("preprocess_fwd", s,
-                preprocess_fwd_kernel<<<(unsigned)((VN + 255) / 256), 256, 0, s>>>(g, T_cw, V, cam, o,
-                                                                                    ws, zero_g2d));
+                preprocess_fwd_kernel<<<(unsigned)((VN + kPreThreads - 1) / kPreThreads), kPreThreads, 0, s>>>(
+                    g, T_cw, V, cam, o, ws, zero_g2d));
     return cudaGetLastError();
 }
 
 cudaError_t launch_preprocess_bwd(const GaussIn &g, const double *T_cw, int V, const CamParams &cam,
                                   const OptParams &o, const RenderWs &ws, const GaussGrad &gg,
-                                  double *dpose, const uint32_t *vis, cudaStream_t s) {
+                                  double *dpose, cudaStream_t s) {
     if (g.N == 0) return cudaSuccess;
-    const uint32_t *list = V == 1 ? vis : nullptr;
+    const uint32_t *list = V == 1 ? ws.vis_idx : nullptr;
     VPGS_LAUNCH("preprocess_bwd", s,
                 preprocess_bwd_kernel<<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>(
                     g, T_cw, V, cam, o, ws, gg, dpose, list, ws.counters + CNT_VISIBLE));

@@ -3,9 +3,10 @@
 `Renderer` owns the device workspace of a camera and passes tensors to the C
 entry points; `RenderFn` puts the forward/backward pair behind
 torch.autograd.  Only the final transmittance and the per-pixel list length
-are kept from the forward; the backward takes the projection and tile lists
-from the workspace when no other render call used it in between, and
-recomputes them otherwise.
+are kept from the forward: the backward recomputes the projection and the
+per-tile sorted lists.  A renderer built with reuse_binning=True lets the
+backward take them from the workspace instead, when no other render call
+replaced them in between (more memory traffic saved, nothing recomputed).
 """
 from __future__ import annotations
 
@@ -47,10 +48,11 @@ class Renderer:
 
     `opts` are fields of vpgs_render_opts (tile_w, tile_h, alpha_min,
     alpha_max, t_min, dilation, near_z, bg, persistent_ctas).
+    reuse_binning=True makes RenderFn's backward reuse the forward's tile lists.
     """
 
     def __init__(self, intr: Intrinsics, n_views: int = 1, device="cuda", instances_per_gaussian=24,
-                 **opts):
+                 reuse_binning: bool = False, **opts):
         self.intr = intr
         self.cam = intr.c()
         self.opts = C.default_opts(**opts)
@@ -63,6 +65,7 @@ class Renderer:
         self.inst_per_g = instances_per_gaussian
         self.last_stats = None
         self.generation = 0  # counts the calls that replace the workspace's tile lists
+        self.reuse_binning = bool(reuse_binning)
 
     # -- workspace -----------------------------------------------------------
     def reserve(self, n: int, max_instances: int | None = None):
@@ -213,10 +216,11 @@ class RenderFn(torch.autograd.Function):
         dpose = torch.zeros((r.V, 6), dtype=torch.float64, device=means.device) if need[5] else None
         fwd = {"t_final": t_final, "n_iter": n_iter}
         cont = lambda t: None if t is None else t.contiguous()  # noqa: E731
-        # saved tensors cannot have been changed in place (autograd checks their
-        # versions), so the lists are reusable unless another call replaced them
+        # recompute by default; with reuse_binning the lists are reusable unless another
+        # call replaced them (saved tensors cannot change in place: autograd checks)
+        reuse = r.reuse_binning and r.generation == ctx.generation
         r.backward(means, scales, quats, opacities, colors, T_cw, fwd, cont(g_rgb), cont(g_depth),
-                   cont(g_alpha), grads=grads, dpose=dpose, reuse=r.generation == ctx.generation)
+                   cont(g_alpha), grads=grads, dpose=dpose, reuse=reuse)
         return (grads.get("means"), grads.get("scales"), grads.get("quats"),
                 grads.get("opacities"), grads.get("colors"), dpose, None, None)
 

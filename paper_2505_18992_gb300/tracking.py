@@ -27,6 +27,7 @@ class Tracker:
         self.target_depth = target_depth
         self.lr = (ctypes.c_double * 2)(*lr)
         self.lambda_d = lambda_d
+        self.reuse = renderer.reuse_binning  # recompute the tile lists in the backward unless asked
         V = renderer.V
         dev = T_cw.device
         self.out = renderer.alloc_images()
@@ -56,7 +57,7 @@ class Tracker:
         torch.sub(self.out["depth"], self.target_depth, out=self.g_depth)
         self.g_depth.sign_().mul_(self.s_d)
         r.backward(*self.g, self.T, self.out, self.g_rgb, self.g_depth, None, grads=None,
-                   dpose=self.dpose, reuse=True)
+                   dpose=self.dpose, reuse=self.reuse)
         C.check(C.vpgs_pose_step(self.T.data_ptr(), self.dpose.data_ptr(), self.adam.data_ptr(),
                                  r.V, self.lr, current_stream_handle()), "vpgs_pose_step")
 

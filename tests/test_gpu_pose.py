@@ -61,7 +61,8 @@ def test_tracking_graph_converges_and_matches_eager():
     tr.reset(T0)
     tr.replay()
     torch.cuda.synchronize()
-    # same kernels, same order: the replay follows the eager trajectory (atomic
-    # summation order may differ in the last bits)
-    assert float((T - T_eager).abs().max()) < 1e-6
+    # same kernels, same order: the replay follows the eager trajectory.  Float
+    # atomics sum in a different order on every run, and 30 Adam steps carry that
+    # rounding along: equal to 10 um against the 3 cm start error
+    assert float((T - T_eager).abs().max()) < 1e-5
     assert r.stats().status == 0
