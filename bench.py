@@ -513,6 +513,7 @@ def decode_rows(dev):
     import torch
 
     from paper_2505_18992_gb300 import scenes
+    from paper_2505_18992_gb300 import vpgs as C
     from paper_2505_18992_gb300.decode import Decoder
     sc = scenes.street_anchors()
     t = lambda a, dt=torch.float32: torch.tensor(a, dtype=dt, device=dev).contiguous()  # noqa: E731
@@ -520,15 +521,26 @@ def decode_rows(dev):
     params = t(np.concatenate([np.asarray(p, np.float32).reshape(-1)
                                for name in ("opacity", "color", "cov") for p in sc.mlp[name]]))
     T = t(sc.camera.T_cw[0], torch.float64)
-    res = {"anchors": sc.n, "k": sc.k}
+    res = {"anchors": sc.n, "k": sc.k,
+           "timing": "library calls on preallocated buffers, no host sync inside the timed loop"}
     for name, bf in (("fp32", False), ("bf16", True)):
         d = Decoder(sc.k, bf16=bf, device=dev)
         out = d.forward(anchors, feats, scal, offs, params, sc.camera, T)
         grads = {k: torch.ones_like(out[k]) for k in ("means", "scales", "quats", "opacities", "colors")}
-        fwd_ms = _time_ms(lambda: d.forward(anchors, feats, scal, offs, params, sc.camera, T))
-        bwd_ms = _time_ms(lambda: d.backward(anchors, feats, scal, offs, params, sc.camera, T, out, grads))
+        gres = d.backward(anchors, feats, scal, offs, params, sc.camera, T, out, grads)
+        fwd_ms = _time_ms(lambda: d.forward(anchors, feats, scal, offs, params, sc.camera, T, out=out, sync=False))
+        bwd_ms = _time_ms(lambda: d.backward(anchors, feats, scal, offs, params, sc.camera, T, out, grads, res=gres))
+        # per-kernel device times (CUDA events on the launching stream)
+        C.vpgs_profile_enable(1)
+        for _ in range(10):
+            d.forward(anchors, feats, scal, offs, params, sc.camera, T, out=out, sync=False)
+            d.backward(anchors, feats, scal, offs, params, sc.camera, T, out, grads, res=gres)
+        torch.cuda.synchronize()
+        prof = C.profile_collect()
+        C.vpgs_profile_enable(0)
         res[name] = {"fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "gaussians_out": out["n"],
-                     "anchors_per_s_fwd": sc.n / (fwd_ms * 1e-3)}
+                     "anchors_per_s_fwd": sc.n / (fwd_ms * 1e-3),
+                     "kernels_us": {k: round(1000 * t / max(n, 1), 1) for k, (n, t) in prof.items()}}
     return res
 
 

@@ -76,15 +76,15 @@ bool make_layout(int64_t N, int V, const vpgs_camera *cam, const vpgs_render_opt
     L.off_ikey1 = take(4 * L.M_cap);
     L.off_ival1 = take(4 * L.M_cap);
     L.off_ranges = take(sizeof(uint2) * (size_t)V * L.T);
-    L.off_sort_hist = take(4 * kRadix * 4);
+    L.off_sort_hist = take(2 * 4 * kRadix * 4);
     const int64_t look_a = 4 * sort_blocks(VN1, kDepthSortItems);
-    const int64_t look_b = (int64_t)np_tile * sort_blocks(L.M_cap, kTileSortItems);
+    const int64_t look_b = (int64_t)std::max(np_tile, 1) * sort_blocks(L.M_cap, kTileSortItems);
     L.sort_blocks_max = look_a > look_b ? look_a : look_b;
-    L.off_sort_look = take(4 * kRadix * (size_t)L.sort_blocks_max);
-    // scans: visibility and offsets over V*N items, radix count matrices
-    const int64_t cm = kRadix * std::max(sort_blocks(VN1, kDepthSortItems), sort_blocks(L.M_cap, kTileSortItems));
-    L.scan_blocks_max = std::max(scan_blocks(VN1), scan_blocks(cm));
-    L.off_scan_look = take(8 * (size_t)L.scan_blocks_max);
+    L.off_sort_look = take(4 * kRadix * (size_t)look_a);
+    L.off_sort_look_t = take(4 * kRadix * (size_t)look_b);
+    // scans: visibility and offsets over V*N items
+    L.scan_blocks_max = scan_blocks(VN1);
+    L.off_scan_look = take(2 * 8 * (size_t)L.scan_blocks_max);
     L.off_g2d = take(4 * 10 * (size_t)VN1);
     L.off_posedf = take(4 * 24 * (size_t)V);
     L.off_bin = take(sizeof(BinRec) * (size_t)VN1);
@@ -109,9 +109,12 @@ RenderWs carve(void *base, const RenderLayout &L) {
     w.ikey[1] = reinterpret_cast<uint32_t *>(b + L.off_ikey1);
     w.ival[1] = reinterpret_cast<uint32_t *>(b + L.off_ival1);
     w.ranges = reinterpret_cast<uint2 *>(b + L.off_ranges);
-    w.sort_hist = reinterpret_cast<uint32_t *>(b + L.off_sort_hist);
-    w.sort_look = reinterpret_cast<uint32_t *>(b + L.off_sort_look);
-    w.scan_look = reinterpret_cast<unsigned long long *>(b + L.off_scan_look);
+    w.sort_hist[0] = reinterpret_cast<uint32_t *>(b + L.off_sort_hist);
+    w.sort_hist[1] = w.sort_hist[0] + 4 * kRadix;
+    w.sort_look[0] = reinterpret_cast<uint32_t *>(b + L.off_sort_look);
+    w.sort_look[1] = reinterpret_cast<uint32_t *>(b + L.off_sort_look_t);
+    w.scan_look[0] = reinterpret_cast<unsigned long long *>(b + L.off_scan_look);
+    w.scan_look[1] = w.scan_look[0] + L.scan_blocks_max;
     w.g2d = reinterpret_cast<float *>(b + L.off_g2d);
     w.posedf = reinterpret_cast<float *>(b + L.off_posedf);
     w.bin = reinterpret_cast<BinRec *>(b + L.off_bin);
@@ -278,9 +281,8 @@ vpgs_status vpgs_render_fwd(void *ws, size_t ws_bytes, const vpgs_gaussians *g,
     if (st != VPGS_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     tag_clear(ws);
-    cudaError_t e = cudaMemsetAsync(ws, 0, S.L.off_counters + 4 * CNT_N, s);
     // the 2D gradient slots of visible Gaussians start at zero for a backward that reuses this call
-    if (e == cudaSuccess) e = launch_preprocess_fwd(S.g, T_cw, n_views, S.cam, S.o, S.ws, true, s);
+    cudaError_t e = launch_preprocess_fwd(S.g, T_cw, n_views, S.cam, S.o, S.ws, S.L, true, s);
     int buf = 0;
     if (e == cudaSuccess) e = build_tile_lists(S.g, n_views, S.cam, S.ws, S.L, &buf, s);
     if (e == cudaSuccess)
@@ -314,8 +316,7 @@ vpgs_status vpgs_render_bwd(void *ws, size_t ws_bytes, const vpgs_gaussians *g,
         buf = tile_list_buffer(S.L);
     } else {
         // recompute projection, binning and per-tile sort
-        e = cudaMemsetAsync(ws, 0, S.L.off_counters + 4 * CNT_N, s);
-        if (e == cudaSuccess) e = launch_preprocess_fwd(S.g, T_cw, n_views, S.cam, S.o, S.ws, true, s);
+        e = launch_preprocess_fwd(S.g, T_cw, n_views, S.cam, S.o, S.ws, S.L, true, s);
         if (e == cudaSuccess) e = build_tile_lists(S.g, n_views, S.cam, S.ws, S.L, &buf, s);
         if (e == cudaSuccess) tag_set(tag);
         else tag_clear(ws);
@@ -338,8 +339,7 @@ vpgs_status vpgs_render_project(void *ws, size_t ws_bytes, const vpgs_gaussians 
     if (st != VPGS_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     tag_clear(ws);
-    cudaError_t e = cudaMemsetAsync(ws, 0, S.L.off_counters + 4 * CNT_N, s);
-    if (e == cudaSuccess) e = launch_preprocess_fwd(S.g, T_cw, n_views, S.cam, S.o, S.ws, false, s);
+    cudaError_t e = launch_preprocess_fwd(S.g, T_cw, n_views, S.cam, S.o, S.ws, S.L, false, s);
     if (e == cudaSuccess)
         e = launch_export_projection(S.ws, S.L.VN, tile_count, tile_rect, mean2d, depth, conic, s);
     return cuda_status(e);

@@ -253,7 +253,8 @@ struct RenderLayout {
     // offsets in bytes
     size_t off_status, off_counters, off_rec, off_tcount, off_dkey0,
         off_dval0, off_dkey1, off_dval1, off_ikey0, off_ival0, off_ikey1, off_ival1, off_ranges,
-        off_sort_hist, off_sort_look, off_scan_look, off_g2d, off_posedf, off_bin, off_vis_idx, total;
+        off_sort_hist, off_sort_look, off_sort_look_t, off_scan_look, off_g2d, off_posedf, off_bin,
+        off_vis_idx, total;
     int64_t sort_blocks_max, scan_blocks_max;
 };
 
@@ -261,10 +262,13 @@ struct RenderLayout {
 enum {
     CNT_VISIBLE = 0,   // number of visible (view, Gaussian) pairs
     CNT_INSTANCES = 1, // number of tile instances
-    CNT_TICKET_A = 2,  // decoupled look-back tickets (reset before each use)
-    CNT_TICKET_B = 3,  // 3..6: one ticket per sort pass
-    CNT_WORK = 7,      // persistent-kernel work queue
-    CNT_N = 12
+    CNT_TICKET_A = 2,  // decoupled look-back tickets: visibility scan
+    CNT_TICKET_O = 3,  // instance-offset scan
+    CNT_TICKET_D = 4,  // 4..7: depth sort passes
+    CNT_TICKET_T = 8,  // 8..11: tile sort passes
+    CNT_WORK = 12,     // persistent-kernel work queue
+    CNT_CAND = 13,     // pre-cull survivors of the projection pass
+    CNT_N = 16         // all zeroed by the prepare kernel at the start of a call
 };
 
 struct RenderWs {
@@ -275,10 +279,11 @@ struct RenderWs {
     uint32_t *dkey[2], *dval[2];
     uint32_t *ikey[2], *ival[2];
     uint2 *ranges;
-    uint32_t *sort_hist;  // [passes][256] global digit histograms
-    uint32_t *sort_look;  // look-back status words
-    unsigned long long *scan_look;
-    float *g2d;           // [VN,10] 2D gradients
+    uint32_t *sort_hist[2];            // depth / tile sort: [passes][256] global digit histograms
+    uint32_t *sort_look[2];            // depth / tile sort: [passes][tiles][256] look-back words
+    unsigned long long *scan_look[2];  // visibility / offset scan: look-back words
+    float *g2d;           // [VN,10] 2D gradient sums: u, v, conic a, b, c (without their
+                          // constant factors), opacity, r, g, b, z
     float *posedf;        // [V,24] poses as double-float pairs
     BinRec *bin;          // [VN] binning records of visible Gaussians
     uint32_t *vis_idx;    // [VN] visible (view, Gaussian) indices in index order
@@ -290,17 +295,10 @@ constexpr int kSortThreads = 256;
 #define VPGS_DEPTH_SORT_ITEMS 4
 #endif
 #ifndef VPGS_TILE_SORT_ITEMS
-#define VPGS_TILE_SORT_ITEMS 16
+#define VPGS_TILE_SORT_ITEMS 32
 #endif
 constexpr int kDepthSortItems = VPGS_DEPTH_SORT_ITEMS;  // keys per thread in the depth sort
 constexpr int kTileSortItems = VPGS_TILE_SORT_ITEMS;    // keys per thread in the tile-id sort
-// radix pass kind per sort: one-sweep (decoupled look-back) or count/scan/scatter
-#ifndef VPGS_DEPTH_LOOKBACK
-#define VPGS_DEPTH_LOOKBACK 1
-#endif
-#ifndef VPGS_TILE_LOOKBACK
-#define VPGS_TILE_LOOKBACK 1
-#endif
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kMaxSortPasses = 8;

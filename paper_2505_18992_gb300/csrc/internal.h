@@ -33,9 +33,12 @@ struct GaussGrad {
 int device_sm_count();
 
 // render_pre.cu
+// First launches of a render call: the prepare kernel (zeroes status, counters
+// and the scratch later kernels expect at zero; converts the poses), the
+// pre-cull and the exact projection.
 cudaError_t launch_preprocess_fwd(const GaussIn &g, const double *T_cw, int V, const CamParams &cam,
-                                  const OptParams &o, const RenderWs &ws, bool zero_g2d,
-                                  cudaStream_t s);
+                                  const OptParams &o, const RenderWs &ws, const RenderLayout &L,
+                                  bool zero_g2d, cudaStream_t s);
 cudaError_t launch_export_projection(const RenderWs &ws, int64_t VN, int32_t *tile_count,
                                      int32_t *tile_rect, float *mean2d, float *depth, float *conic,
                                      cudaStream_t s);

@@ -49,11 +49,14 @@ scan_kernel(Load load, Store store, int64_t n_cap, const uint32_t *n_dev, uint32
     __shared__ uint32_t s_warp[kScanThreads / kWarp];
     __shared__ uint32_t s_bid, s_excl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int64_t n = n_cap;
+    if (n_dev) n = min(n, (int64_t)*n_dev);
+    // tiles in ticket order until they run out (the grid is sized to what fits
+    // on the GPU at once, not to the capacity)
+    for (;;) {
     if (tid == 0) s_bid = atomicAdd(ticket, 1u);
     __syncthreads();
     const int64_t bid = s_bid;
-    int64_t n = n_cap;
-    if (n_dev) n = min(n, (int64_t)*n_dev);
     const int64_t base = bid * kScanTile;
     if (base >= n) {
         if (bid == 0 && tid == 0 && total) *total = 0;
@@ -146,25 +149,38 @@ scan_kernel(Load load, Store store, int64_t n_cap, const uint32_t *n_dev, uint32
         if (gi < n) store(gi, run, v[i]);
         run += v[i];
     }
+    __syncthreads();  // the next tile reuses the shared arrays
+    }
+}
+
+// Blocks of a kernel that fit on the GPU at once (cached per kernel).
+inline int resident_grid(const void *kernel, int threads, size_t smem, int64_t cap_blocks) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess || occ < 1) occ = 1;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t g = (int64_t)occ * std::max(sms, 1);
+    return (int)std::max<int64_t>(1, std::min(g, cap_blocks));
 }
 
 inline int64_t scan_blocks(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
 
-// Launch a scan over at most n_cap items.  ticket / look must be zero on entry;
-// this launcher clears them on `stream` first.
+// Launch a scan over at most n_cap items.  *ticket and the scan_blocks(n_cap)
+// look-back words must be zero on entry (the render's prepare kernel clears them).
 template <class Load, class Store>
 cudaError_t launch_scan(const char *name, Load load, Store store, int64_t n_cap, const uint32_t *n_dev,
                         uint32_t *ticket, unsigned long long *look, uint32_t *total,
                         uint32_t *status, cudaStream_t stream) {
     int64_t nb = scan_blocks(n_cap);
     if (nb == 0) nb = 1;
-    cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(uint32_t), stream);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(look, 0, nb * sizeof(unsigned long long), stream);
-    if (e != cudaSuccess) return e;
+    static int grid_cache = 0;  // per <Load, Store>: occupancy does not change within a process
+    if (grid_cache == 0)
+        grid_cache = resident_grid((const void *)scan_kernel<Load, Store>, kScanThreads, 0, int64_t(1) << 30);
+    const int grid = (int)std::min<int64_t>(grid_cache, nb);
     VPGS_LAUNCH(name, stream,
-                scan_kernel<<<(unsigned)nb, kScanThreads, 0, stream>>>(load, store, n_cap, n_dev,
-                                                                       ticket, look, total, status));
+                scan_kernel<<<(unsigned)grid, kScanThreads, 0, stream>>>(load, store, n_cap, n_dev,
+                                                                         ticket, look, total, status));
     return cudaGetLastError();
 }
 
@@ -177,30 +193,8 @@ struct SortPass {
     int shift, bits;
 };
 
-static __global__ void __launch_bounds__(256)
-radix_histogram_kernel(const uint32_t *keys, int64_t n_cap, const uint32_t *n_dev, int n_passes,
-                       SortPass p0, SortPass p1, SortPass p2, SortPass p3, uint32_t *hist) {
-    __shared__ uint32_t s_h[4][kRadix];
-    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0;
-    __syncthreads();
-    int64_t n = n_cap;
-    if (n_dev) n = min(n, (int64_t)*n_dev);
-    const SortPass ps[4] = {p0, p1, p2, p3};
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t k = keys[i];
-#pragma unroll
-        for (int p = 0; p < 4; ++p)
-            if (p < n_passes) atomicAdd(&s_h[p][(k >> ps[p].shift) & ((1u << ps[p].bits) - 1u)], 1u);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n_passes * kRadix; i += blockDim.x) {
-        uint32_t c = (&s_h[0][0])[i];
-        if (c) atomicAdd(hist + i, c);
-    }
-}
-
-// look-back status word: [31:30] flag (1 aggregate, 2 inclusive), [29:0] count
+// one-sweep look-back word: [31:30] flag (1 = block aggregate, 2 = inclusive
+// prefix), [29:0] count
 constexpr uint32_t kSFlagAgg = 1u << 30;
 constexpr uint32_t kSFlagPre = 2u << 30;
 constexpr uint32_t kSValMask = (1u << 30) - 1u;
@@ -211,7 +205,7 @@ radix_onesweep_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__res
                       uint32_t *__restrict__ key_out, uint32_t *__restrict__ val_out,
                       int64_t n_cap, const uint32_t *n_dev, SortPass pass,
                       const uint32_t *__restrict__ pass_hist, uint32_t *ticket, uint32_t *look,
-                      uint32_t *status) {
+                      uint32_t *next_look, uint32_t *status) {
     constexpr int kWarps = kSortThreads / kWarp;
     constexpr int kSeg = kWarp * ITEMS;  // contiguous items per warp
     constexpr int kTile = kSortThreads * ITEMS;
@@ -222,14 +216,9 @@ radix_onesweep_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__res
     __shared__ uint32_t s_key[kTile], s_val[kTile];
     __shared__ uint32_t s_bid;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_bid = atomicAdd(ticket, 1u);
-    for (int i = tid; i < kWarps * kRadix; i += kSortThreads) (&s_cnt[0][0])[i] = 0;
-    __syncthreads();
-    const int64_t bid = s_bid;
     int64_t n = n_cap;
     if (n_dev) n = min(n, (int64_t)*n_dev);
-    const int64_t base = bid * (int64_t)(kSortThreads * ITEMS);
-    if (base >= n) return;
+    if (n == 0) return;
     const uint32_t mask = (1u << pass.bits) - 1u;
 
     // global exclusive digit offsets of this pass (every block recomputes them)
@@ -251,6 +240,16 @@ radix_onesweep_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__res
         for (int w = 0; w < warp; ++w) add += s_glob[w * 32 + 31];
         glob_excl = s_glob[tid] - pass_hist[tid] + add;
     }
+
+    // tiles in ticket order until they run out (the grid is sized to what fits
+    // on the GPU at once; a tile only waits on lower tickets, held by running blocks)
+    for (;;) {
+    if (tid == 0) s_bid = atomicAdd(ticket, 1u);
+    for (int i = tid; i < kWarps * kRadix; i += kSortThreads) (&s_cnt[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t bid = s_bid;
+    const int64_t base = bid * (int64_t)(kSortThreads * ITEMS);
+    if (base >= n) return;
 
     // load this warp's contiguous segment, 32 consecutive keys per step
     uint32_t k[ITEMS], v[ITEMS], d[ITEMS];
@@ -367,130 +366,8 @@ radix_onesweep_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__res
             val_out[pos] = s_val[i];
         }
     }
-}
-
-// ---------------------------------------------------------------------------
-// Radix pass without look-back: count -> scan -> scatter.
-// The per-block digit counts are stored digit-major (counts[d * nb + b]), so an
-// exclusive scan of that matrix gives every (digit, block) its global output
-// position directly, and no block ever waits on another.
-// ---------------------------------------------------------------------------
-template <int ITEMS>
-static __global__ void __launch_bounds__(kSortThreads)
-radix_count_kernel(const uint32_t *__restrict__ key_in, int64_t n_cap, const uint32_t *n_dev, SortPass pass,
-                   uint32_t *__restrict__ counts, int64_t nb) {
-    constexpr int kTile = kSortThreads * ITEMS;
-    __shared__ uint32_t s_h[kRadix];
-    const int tid = threadIdx.x;
-    s_h[tid] = 0;
-    __syncthreads();
-    int64_t n = n_cap;
-    if (n_dev) n = min(n, (int64_t)*n_dev);
-    const int64_t base = (int64_t)blockIdx.x * kTile;
-    const uint32_t mask = (1u << pass.bits) - 1u;
-#pragma unroll
-    for (int s = 0; s < ITEMS; ++s) {
-        const int64_t i = base + s * kSortThreads + tid;
-        if (i < n) atomicAdd(&s_h[(key_in[i] >> pass.shift) & mask], 1u);
-    }
-    __syncthreads();
-    counts[(int64_t)tid * nb + blockIdx.x] = s_h[tid];
-}
-
-struct CountsLoad {
-    const uint32_t *c;
-    __device__ uint32_t operator()(int64_t i) const { return c[i]; }
-};
-struct CountsStore {
-    uint32_t *c;
-    __device__ void operator()(int64_t i, uint32_t excl, uint32_t) const { c[i] = excl; }
-};
-
-template <int ITEMS>
-static __global__ void __launch_bounds__(kSortThreads)
-radix_scatter_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__restrict__ val_in,
-                     uint32_t *__restrict__ key_out, uint32_t *__restrict__ val_out, int64_t n_cap,
-                     const uint32_t *n_dev, SortPass pass, const uint32_t *__restrict__ offsets, int64_t nb) {
-    constexpr int kWarps = kSortThreads / kWarp;
-    constexpr int kSeg = kWarp * ITEMS;
-    constexpr int kTile = kSortThreads * ITEMS;
-    __shared__ uint32_t s_cnt[kWarps][kRadix];
-    __shared__ uint32_t s_dstart[kRadix], s_gbase[kRadix], s_wsum[kWarps];
-    __shared__ uint32_t s_key[kTile], s_val[kTile];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < kWarps * kRadix; i += kSortThreads) (&s_cnt[0][0])[i] = 0;
-    int64_t n = n_cap;
-    if (n_dev) n = min(n, (int64_t)*n_dev);
-    const int64_t b = blockIdx.x;
-    const int64_t base = b * kTile;
-    if (base >= n) return;
-    const uint32_t mask = (1u << pass.bits) - 1u;
-    s_gbase[tid] = offsets[(int64_t)tid * nb + b];  // global slot of this block's first key with digit tid
-    __syncthreads();
-    uint32_t k[ITEMS], v[ITEMS], d[ITEMS];
-    const int64_t seg = base + (int64_t)warp * kSeg;
-#pragma unroll
-    for (int s = 0; s < ITEMS; ++s) {
-        const int64_t i = seg + s * kWarp + lane;
-        const bool ok = i < n;
-        k[s] = ok ? key_in[i] : 0u;
-        v[s] = ok ? val_in[i] : 0u;
-        d[s] = ok ? ((k[s] >> pass.shift) & mask) : (kRadix + lane);
-    }
-#pragma unroll
-    for (int s = 0; s < ITEMS; ++s) {
-        const uint32_t m = __match_any_sync(0xffffffffu, d[s]);
-        if (d[s] < kRadix && (m & lanemask_lt()) == 0) s_cnt[warp][d[s]] += __popc(m);
-        __syncwarp();
-    }
-    __syncthreads();
-    uint32_t c = 0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) c += s_cnt[w][tid];
-    {
-        uint32_t x = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) s_wsum[warp] = x;
-        __syncthreads();
-        uint32_t add = 0;
-        for (int w = 0; w < warp; ++w) add += s_wsum[w];
-        s_dstart[tid] = x - c + add;
-        uint32_t run = s_dstart[tid];
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            const uint32_t t = s_cnt[w][tid];
-            s_cnt[w][tid] = run;
-            run += t;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int s = 0; s < ITEMS; ++s) {
-        const uint32_t m = __match_any_sync(0xffffffffu, d[s]);
-        const uint32_t rank = __popc(m & lanemask_lt());
-        if (d[s] < kRadix) {
-            const uint32_t lp = s_cnt[warp][d[s]] + rank;
-            s_key[lp] = k[s];
-            s_val[lp] = v[s];
-        }
-        __syncwarp();
-        if (d[s] < kRadix && rank == 0) s_cnt[warp][d[s]] += __popc(m);
-        __syncwarp();
-    }
-    __syncthreads();
-    const int nbk = (int)min((int64_t)kTile, n - base);
-    for (int i = tid; i < nbk; i += kSortThreads) {
-        const uint32_t key = s_key[i];
-        const uint32_t dg = (key >> pass.shift) & mask;
-        const uint32_t pos = s_gbase[dg] + ((uint32_t)i - s_dstart[dg]);
-        if ((int64_t)pos < n) {
-            key_out[pos] = key;
-            val_out[pos] = s_val[i];
-        }
+    if (next_look) next_look[bid * kRadix + tid] = 0u;  // the next pass starts from zero
+    __syncthreads();  // the next tile reuses the shared arrays
     }
 }
 
@@ -514,86 +391,66 @@ inline int64_t sort_blocks(int64_t n, int items) {
 
 // Sort n (<= n_cap, or *n_dev) pairs from (k0, v0) using (k1, v1) as the other
 // buffer.  Returns in *result_in_1 whether the sorted data ended in buffer 1.
-// lookback = true: one-sweep passes (scratch: hist [4*256], ticket [4],
-//   look [passes * sort_blocks * 256]);
-// lookback = false: count / scan / scatter passes (scratch: look holds the
-//   [256 * sort_blocks] count matrix; scan_ticket/scan_look as for launch_scan).
+// On entry (the producers of the keys and the render's prepare kernel see to it):
+//   hist   [passes][256] global digit histograms of the n keys;
+//   ticket [passes] zero;
+//   look   [passes][sort_blocks(n_cap)][256], pass 0's words zero for the tiles
+//          that hold keys (each pass clears the next pass's words of its tiles).
 inline cudaError_t radix_sort_pairs(const char *name, uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
                                     int64_t n_cap, const uint32_t *n_dev, int lo_bit, int bits,
-                                    uint32_t *hist, uint32_t *ticket, uint32_t *look,
-                                    uint32_t *status, int sms, cudaStream_t stream,
-                                    bool *result_in_1, int items, bool lookback,
-                                    uint32_t *scan_ticket, unsigned long long *scan_look) {
+                                    const uint32_t *hist, uint32_t *ticket, uint32_t *look,
+                                    uint32_t *status, cudaStream_t stream, bool *result_in_1, int items) {
     SortPass ps[kMaxSortPasses];
     int np = plan_passes(lo_bit, bits, ps);
     *result_in_1 = (np & 1) != 0;
     if (np == 0 || n_cap == 0) return cudaSuccess;
     if (np > 4) return cudaErrorInvalidValue;
     if (items != 4 && items != 8 && items != 16 && items != 32) return cudaErrorInvalidValue;
-    if (!lookback && items == 32) return cudaErrorInvalidValue;  // count/scatter kernels exist for 4..16
     const int64_t nb = sort_blocks(n_cap, items);
+    const void *kern = items == 4 ? (const void *)radix_onesweep_kernel<4>
+                     : items == 8 ? (const void *)radix_onesweep_kernel<8>
+                     : items == 32 ? (const void *)radix_onesweep_kernel<32>
+                                   : (const void *)radix_onesweep_kernel<16>;
+    static int grids[33] = {0};  // by items: occupancy does not change within a process
+    if (grids[items] == 0) grids[items] = resident_grid(kern, kSortThreads, 0, int64_t(1) << 30);
+    const unsigned grid = (unsigned)std::min<int64_t>(grids[items], nb);
     cudaError_t e;
     uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
-    if (!lookback) {
-        for (int p = 0; p < np; ++p) {
-            if (items == 4)
-                VPGS_LAUNCH("radix_count", stream, radix_count_kernel<4><<<(unsigned)nb, kSortThreads, 0, stream>>>(ki, n_cap, n_dev, ps[p], look, nb));
-            else if (items == 8)
-                VPGS_LAUNCH("radix_count", stream, radix_count_kernel<8><<<(unsigned)nb, kSortThreads, 0, stream>>>(ki, n_cap, n_dev, ps[p], look, nb));
-            else
-                VPGS_LAUNCH("radix_count", stream, radix_count_kernel<16><<<(unsigned)nb, kSortThreads, 0, stream>>>(ki, n_cap, n_dev, ps[p], look, nb));
-            e = cudaGetLastError();
-            if (e != cudaSuccess) return e;
-            e = launch_scan("radix_offsets", CountsLoad{look}, CountsStore{look}, (int64_t)kRadix * nb, nullptr,
-                            scan_ticket, scan_look, nullptr, status, stream);
-            if (e != cudaSuccess) return e;
-            if (items == 4)
-                VPGS_LAUNCH(name, stream, radix_scatter_kernel<4><<<(unsigned)nb, kSortThreads, 0, stream>>>(ki, vi, ko, vo, n_cap, n_dev, ps[p], look, nb));
-            else if (items == 8)
-                VPGS_LAUNCH(name, stream, radix_scatter_kernel<8><<<(unsigned)nb, kSortThreads, 0, stream>>>(ki, vi, ko, vo, n_cap, n_dev, ps[p], look, nb));
-            else
-                VPGS_LAUNCH(name, stream, radix_scatter_kernel<16><<<(unsigned)nb, kSortThreads, 0, stream>>>(ki, vi, ko, vo, n_cap, n_dev, ps[p], look, nb));
-            e = cudaGetLastError();
-            if (e != cudaSuccess) return e;
-            uint32_t *tk = ki, *tv = vi;
-            ki = ko; vi = vo; ko = tk; vo = tv;
-        }
-        return cudaSuccess;
-    }
-    e = cudaMemsetAsync(hist, 0, np * kRadix * sizeof(uint32_t), stream);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(look, 0, (size_t)np * nb * kRadix * sizeof(uint32_t), stream);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(ticket, 0, np * sizeof(uint32_t), stream);
-    if (e != cudaSuccess) return e;
-    SortPass z{0, 1};
-    int hb = (int)std::min<int64_t>((int64_t)sms * 4, std::max<int64_t>(1, (n_cap + 4095) / 4096));
-    VPGS_LAUNCH("radix_histogram", stream,
-                radix_histogram_kernel<<<hb, 256, 0, stream>>>(k0, n_cap, n_dev, np, ps[0],
-                                                               np > 1 ? ps[1] : z, np > 2 ? ps[2] : z,
-                                                               np > 3 ? ps[3] : z, hist));
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
     for (int p = 0; p < np; ++p) {
         uint32_t *lk = look + (size_t)p * nb * kRadix;
+        uint32_t *nl = p + 1 < np ? lk + (size_t)nb * kRadix : nullptr;
+        const uint32_t *h = hist + p * kRadix;
         if (items == 4)
-            VPGS_LAUNCH(name, stream, radix_onesweep_kernel<4><<<(unsigned)nb, kSortThreads, 0, stream>>>(
-                                          ki, vi, ko, vo, n_cap, n_dev, ps[p], hist + p * kRadix, ticket + p, lk, status));
+            VPGS_LAUNCH(name, stream, radix_onesweep_kernel<4><<<grid, kSortThreads, 0, stream>>>(
+                                          ki, vi, ko, vo, n_cap, n_dev, ps[p], h, ticket + p, lk, nl, status));
         else if (items == 8)
-            VPGS_LAUNCH(name, stream, radix_onesweep_kernel<8><<<(unsigned)nb, kSortThreads, 0, stream>>>(
-                                          ki, vi, ko, vo, n_cap, n_dev, ps[p], hist + p * kRadix, ticket + p, lk, status));
+            VPGS_LAUNCH(name, stream, radix_onesweep_kernel<8><<<grid, kSortThreads, 0, stream>>>(
+                                          ki, vi, ko, vo, n_cap, n_dev, ps[p], h, ticket + p, lk, nl, status));
         else if (items == 32)
-            VPGS_LAUNCH(name, stream, radix_onesweep_kernel<32><<<(unsigned)nb, kSortThreads, 0, stream>>>(
-                                          ki, vi, ko, vo, n_cap, n_dev, ps[p], hist + p * kRadix, ticket + p, lk, status));
+            VPGS_LAUNCH(name, stream, radix_onesweep_kernel<32><<<grid, kSortThreads, 0, stream>>>(
+                                          ki, vi, ko, vo, n_cap, n_dev, ps[p], h, ticket + p, lk, nl, status));
         else
-            VPGS_LAUNCH(name, stream, radix_onesweep_kernel<16><<<(unsigned)nb, kSortThreads, 0, stream>>>(
-                                          ki, vi, ko, vo, n_cap, n_dev, ps[p], hist + p * kRadix, ticket + p, lk, status));
+            VPGS_LAUNCH(name, stream, radix_onesweep_kernel<16><<<grid, kSortThreads, 0, stream>>>(
+                                          ki, vi, ko, vo, n_cap, n_dev, ps[p], h, ticket + p, lk, nl, status));
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         uint32_t *tk = ki, *tv = vi;
         ki = ko; vi = vo; ko = tk; vo = tv;
     }
     return cudaSuccess;
+}
+
+// Adds the digits of key k to block-shared histograms of every pass (s_h [passes][256]).
+VPGS_D void add_digits(uint32_t (*s_h)[kRadix], const SortPass *ps, int np, uint32_t k) {
+    for (int p = 0; p < np; ++p) atomicAdd(&s_h[p][(k >> ps[p].shift) & ((1u << ps[p].bits) - 1u)], 1u);
+}
+
+// Adds block-shared histograms into the global ones (non-zero bins only).
+VPGS_D void flush_digits(const uint32_t (*s_h)[kRadix], int np, uint32_t *hist) {
+    for (int i = threadIdx.x; i < np * kRadix; i += blockDim.x) {
+        const uint32_t c = (&s_h[0][0])[i];
+        if (c) atomicAdd(hist + i, c);
+    }
 }
 
 }  // namespace vpgs

@@ -60,16 +60,24 @@ __global__ void __launch_bounds__(kEmitThreads)
 emit_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__ inst_off,
             const BinRec *__restrict__ bin, const uint32_t *n_vis, const uint32_t *n_inst, int64_t N,
             int64_t M_cap, CamParams cam, uint32_t *__restrict__ ikey, uint32_t *__restrict__ ival,
-            uint32_t *status) {
+            uint32_t *status, int n_pass, SortPass p0, SortPass p1, SortPass p2, SortPass p3,
+            uint32_t *hist) {
+    // digit histograms of the emitted tile ids, for the tile sort
+    __shared__ uint32_t s_h[4][kRadix];
+    const SortPass tps[4] = {p0, p1, p2, p3};
+    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0u;
     __shared__ uint32_t s_start[kEmitThreads], s_id[kEmitThreads], s_vb[kEmitThreads];
     __shared__ uint2 s_rect[kEmitThreads];
     __shared__ float4 s_uv[kEmitThreads];
     __shared__ Cover s_cv[kEmitThreads];
     __shared__ uint32_t s_total;
     const int64_t nv = *n_vis;
-    const int64_t r0 = (int64_t)blockIdx.x * kEmitThreads;
-    if (r0 >= nv) return;
     const int tid = threadIdx.x;
+    bool overflow = false;
+    // chunks of kEmitThreads depth-ranked Gaussians, grid-strided (the grid is
+    // sized to what fits on the GPU, not to the capacity)
+    for (int64_t r0 = (int64_t)blockIdx.x * kEmitThreads; r0 < nv && !overflow;
+         r0 += (int64_t)gridDim.x * kEmitThreads) {
     const int nb = (int)min((int64_t)kEmitThreads, nv - r0);
     const uint32_t base = inst_off[r0];
     if (tid < nb) {
@@ -89,7 +97,8 @@ emit_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__ inst
     const uint32_t total = s_total;
     if ((int64_t)base + total > M_cap) {
         if (tid == 0) set_status(status, VPGS_ERR_CAPACITY);
-        return;
+        overflow = true;  // block-uniform
+        continue;
     }
     for (uint32_t e = tid; e < total; e += kEmitThreads) {
         int lo = 0, hi = nb - 1;  // last Gaussian whose local start is <= e
@@ -140,7 +149,12 @@ emit_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__ inst
         }
         ikey[base + e] = key;
         ival[base + e] = s_id[lo];
+        add_digits(s_h, tps, n_pass, key);
     }
+    __syncthreads();  // the next chunk reuses the shared arrays
+    }
+    __syncthreads();
+    flush_digits(s_h, n_pass, hist);
 }
 
 __global__ void tile_ranges_kernel(const uint32_t *__restrict__ keys, int64_t cap, const uint32_t *n_dev,
@@ -175,43 +189,49 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
                              const RenderLayout &L, int *sorted_buf, cudaStream_t s) {
     cudaError_t e;
     const int sms = device_sm_count();
+    (void)sms;
     uint32_t *n_vis = ws.counters + CNT_VISIBLE;
     uint32_t *n_inst = ws.counters + CNT_INSTANCES;
     // 1. compaction of visible (view, Gaussian) pairs
     e = launch_scan("scan_visible", VisLoad{ws.tcount}, VisStore{ws.rec, ws.dkey[0], ws.dval[0], ws.vis_idx, L.VN},
-                    L.VN, nullptr, ws.counters + CNT_TICKET_A, ws.scan_look, n_vis, ws.status, s);
+                    L.VN, nullptr, ws.counters + CNT_TICKET_A, ws.scan_look[0], n_vis, ws.status, s);
     if (e != cudaSuccess) return e;
     // 2. depth sort
     bool in1 = false;
+    // (digit histograms from the projection kernel)
     e = radix_sort_pairs("sort_depth_pass", ws.dkey[0], ws.dval[0], ws.dkey[1], ws.dval[1], L.VN, n_vis,
-                         0, 32, ws.sort_hist, ws.counters + CNT_TICKET_B, ws.sort_look, ws.status, sms, s,
-                         &in1, kDepthSortItems, VPGS_DEPTH_LOOKBACK != 0, ws.counters + CNT_TICKET_A,
-                         ws.scan_look);
+                         0, 32, ws.sort_hist[0], ws.counters + CNT_TICKET_D, ws.sort_look[0], ws.status, s,
+                         &in1, kDepthSortItems);
     if (e != cudaSuccess) return e;
     const uint32_t *dval = in1 ? ws.dval[1] : ws.dval[0];  // visible records in depth order
     uint32_t *inst_off = in1 ? ws.dkey[0] : ws.dkey[1];  // the depth-sort buffer not holding the result
+    SortPass tps[kMaxSortPasses] = {};
+    const int np_tile = plan_passes(0, L.tile_bits, tps);
+    if (np_tile > 4) return cudaErrorInvalidValue;
     // 3. instance offsets, then emission
     e = launch_scan("scan_offsets", CountLoad{ws.tcount, dval}, OffsetStore{inst_off}, L.VN, n_vis,
-                    ws.counters + CNT_TICKET_A, ws.scan_look, n_inst, ws.status, s);
+                    ws.counters + CNT_TICKET_O, ws.scan_look[1], n_inst, ws.status, s);
     if (e != cudaSuccess) return e;
+    static int emit_grid = 0;
+    if (emit_grid == 0) emit_grid = resident_grid((const void *)emit_kernel, kEmitThreads, 0, int64_t(1) << 30);
     VPGS_LAUNCH("emit_instances", s,
-                emit_kernel<<<(unsigned)std::max<int64_t>((L.VN + kEmitThreads - 1) / kEmitThreads, 1),
+                emit_kernel<<<(unsigned)std::min<int64_t>(std::max<int64_t>((L.VN + kEmitThreads - 1) / kEmitThreads, 1),
+                                                          emit_grid),
                               kEmitThreads, 0, s>>>(dval, inst_off, ws.bin, n_vis, n_inst, L.N, L.M_cap,
-                                                    cam, ws.ikey[0], ws.ival[0], ws.status));
+                                                    cam, ws.ikey[0], ws.ival[0], ws.status, np_tile, tps[0],
+                                                    tps[1], tps[2], tps[3], ws.sort_hist[1]));
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // 4. stable sort by tile id
+    // (digit histograms from the emit kernel)
     e = radix_sort_pairs("sort_tile_pass", ws.ikey[0], ws.ival[0], ws.ikey[1], ws.ival[1], L.M_cap, n_inst, 0,
-                         L.tile_bits, ws.sort_hist, ws.counters + CNT_TICKET_B, ws.sort_look,
-                         ws.status, sms, s, &in1, kTileSortItems, VPGS_TILE_LOOKBACK != 0,
-                         ws.counters + CNT_TICKET_A, ws.scan_look);
+                         L.tile_bits, ws.sort_hist[1], ws.counters + CNT_TICKET_T, ws.sort_look[1],
+                         ws.status, s, &in1, kTileSortItems);
     if (e != cudaSuccess) return e;
     *sorted_buf = in1 ? 1 : 0;
     if (*sorted_buf != tile_list_buffer(L)) return cudaErrorUnknown;  // never: same pass plan
     // 5. tile ranges
-    const int n_tiles = V * cam.T;
-    e = cudaMemsetAsync(ws.ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);
-    if (e != cudaSuccess) return e;
+    const int n_tiles = V * cam.T;  // (ranges zeroed by the prepare kernel)
     const int64_t rb = std::min<int64_t>((L.M_cap + 255) / 256, (int64_t)sms * 16);
     VPGS_LAUNCH("tile_ranges", s,
                 tile_ranges_kernel<<<(unsigned)std::max<int64_t>(rb, 1), 256, 0, s>>>(

@@ -257,21 +257,23 @@ VPGS_D bool pair_grad(PixState &p, int jj, const PairEval &e, float dx, float dy
     v[7] = fmaf(w, p.gC1, v[7]);
     v[8] = fmaf(w, p.gC2, v[8]);
     v[9] = fmaf(w, p.gD, v[9]);
-    const float dA = (p.gC0 * (c.x - p.B0) + p.gC1 * (c.y - p.B1) + p.gC2 * (c.z - p.B2) +
-                      p.gD * (c.w - p.BD)) * p.T + p.gA * tfo;
-    p.B0 = fmaf(e.alpha, c.x, om * p.B0);
-    p.B1 = fmaf(e.alpha, c.y, om * p.B1);
-    p.B2 = fmaf(e.alpha, c.z, om * p.B2);
-    p.BD = fmaf(e.alpha, c.w, om * p.BD);
+    // colour / depth behind this Gaussian: B <- alpha c + (1 - alpha) B = B + alpha (c - B)
+    const float d0 = c.x - p.B0, d1 = c.y - p.B1, d2 = c.z - p.B2, dz = c.w - p.BD;
+    const float dA = (p.gC0 * d0 + p.gC1 * d1 + p.gC2 * d2 + p.gD * dz) * p.T + p.gA * tfo;
+    p.B0 = fmaf(e.alpha, d0, p.B0);
+    p.B1 = fmaf(e.alpha, d1, p.B1);
+    p.B2 = fmaf(e.alpha, d2, p.B2);
+    p.BD = fmaf(e.alpha, dz, p.BD);
     if (b.z * e.G <= o.alpha_max) {
+        // slots 0-4 hold sums without their constant factors (2 ln 2 for the mean,
+        // -1/2, -1, -1/2 for the conic), applied once per Gaussian by the preprocess backward
         const float dpow = dA * e.alpha;
-        const float dmu = dpow * kInvExp2Half;  // the rows carry sqrt(log2(e)/2)
         v[5] = fmaf(dA, e.G, v[5]);
-        v[0] = fmaf(dmu, a.z * e.t1 + b.x * e.t2, v[0]);
-        v[1] = fmaf(dmu, a.w * e.t1 + b.y * e.t2, v[1]);
-        v[2] = fmaf(-0.5f * dpow, dx * dx, v[2]);
-        v[3] = fmaf(-dpow, dx * dy, v[3]);
-        v[4] = fmaf(-0.5f * dpow, dy * dy, v[4]);
+        v[0] = fmaf(dpow, a.z * e.t1 + b.x * e.t2, v[0]);
+        v[1] = fmaf(dpow, a.w * e.t1 + b.y * e.t2, v[1]);
+        v[2] = fmaf(dpow, dx * dx, v[2]);
+        v[3] = fmaf(dpow, dx * dy, v[3]);
+        v[4] = fmaf(dpow, dy * dy, v[4]);
     }
     return true;
 }

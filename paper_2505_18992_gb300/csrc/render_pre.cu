@@ -14,6 +14,7 @@
 // 2D gradients (u, v, conic, opacity, colour, depth) back to mean, scale,
 // quaternion, opacity and colour, plus the per-view pose terms summed in FP64.
 #include "internal.h"
+#include "prims.cuh"
 #include "profiler.h"
 
 namespace vpgs {
@@ -93,22 +94,41 @@ VPGS_D bool maybe_in_view(const PoseDF &P, float mx, float my, float mz, float s
     if (pc[2] + tol[2] <= o.near_z) return false;
     const float zl = pc[2] - tol[2];
     if (!(zl > 1e-3f)) return true;  // too close to z = 0 for a bound: the exact path decides
-    const float iz = 1.0f / zl;
+    // approximate reciprocal and square roots (a few ulp): the 1 px and 1e-4 slack below cover them
+    const float iz = __fdividef(1.0f, zl);
     const float kqc = fmaxf(kq, 0.f);
     const float xr = (fabsf(pc[0]) + tol[0]) * iz, yr = (fabsf(pc[1]) + tol[1]) * iz;
-    const float rx = sqrtf(kqc * (cam.fx * cam.fx * iz * iz * (1.f + xr * xr) * smax * smax + o.dilation));
-    const float ry = sqrtf(kqc * (cam.fy * cam.fy * iz * iz * (1.f + yr * yr) * smax * smax + o.dilation));
+    const float qx = kqc * (cam.fx * cam.fx * iz * iz * (1.f + xr * xr) * smax * smax + o.dilation);
+    const float qy = kqc * (cam.fy * cam.fy * iz * iz * (1.f + yr * yr) * smax * smax + o.dilation);
+    const float rx = qx > 0.f ? qx * rsqrtf(qx) : 0.f, ry = qy > 0.f ? qy * rsqrtf(qy) : 0.f;
     // image mean and its error bound
-    const float u = fmaf(cam.fx, pc[0] / pc[2], cam.cx), v = fmaf(cam.fy, pc[1] / pc[2], cam.cy);
+    const float izc = __fdividef(1.0f, pc[2]);
+    const float u = fmaf(cam.fx, pc[0] * izc, cam.cx), v = fmaf(cam.fy, pc[1] * izc, cam.cy);
     const float eu = 2.f * cam.fx * (tol[0] + xr * tol[2]) * iz + 1e-4f * fabsf(u);
     const float ev = 2.f * cam.fy * (tol[1] + yr * tol[2]) * iz + 1e-4f * fabsf(v);
-    const float sx = rx + eu + 1.f, sy = ry + ev + 1.f;
+    const float sx = 1.001f * rx + eu + 1.f, sy = 1.001f * ry + ev + 1.f;
     return !(u + sx < 0.f || u - sx > (float)cam.W || v + sy < 0.f || v - sy > (float)cam.H);
 }
 
-__global__ void pose_prepare_kernel(const double *__restrict__ T_cw, int V, float *posedf) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v < V) pose_to_df(T_cw + 16 * v, posedf + 24 * v);
+// First kernel of a render call: zeroes the status word, the counters and the
+// scratch the later kernels expect at zero (scan look-back words, both sorts'
+// digit histograms and first-pass look-back words, tile ranges), and converts
+// the poses to double-float pairs.  One launch instead of a memset per array.
+struct PrepZero {
+    uint32_t *w32[6];
+    int64_t n32[6];
+    unsigned long long *w64;
+    int64_t n64;
+};
+
+__global__ void __launch_bounds__(256)
+prepare_kernel(const double *__restrict__ T_cw, int V, float *posedf, PrepZero z) {
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+        for (int64_t i = t0; i < z.n32[a]; i += stride) z.w32[a][i] = 0u;
+    for (int64_t i = t0; i < z.n64; i += stride) z.w64[i] = 0ull;
+    for (int64_t v = t0; v < V; v += stride) pose_to_df(T_cw + 16 * v, posedf + 24 * v);
 }
 
 // Exact projection, extent and tile cover of one (view, Gaussian) that passed
@@ -199,24 +219,22 @@ VPGS_D uint32_t project_one(const PoseDF &P, float mx, float my, float mz, float
     return cnt;
 }
 
-// One thread per (view, Gaussian) for the finiteness check and the FP32
-// pre-cull; the block then compacts its candidates so that the exact
-// projection runs on consecutive threads (full warps) instead of on the
-// scattered lanes that passed.
+// Pass 1, one thread per (view, Gaussian): finiteness check, opacity test and
+// the FP32 pre-cull.  Survivors are appended to a candidate list (block-level
+// ballot compaction, one atomic per block); everything else gets tile count 0.
 constexpr int kPreThreads = 256;
 
 __global__ void __launch_bounds__(kPreThreads)
-preprocess_fwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamParams cam, OptParams o,
-                      RenderWs ws, bool zero_g2d) {
-    __shared__ uint16_t s_cand[kPreThreads];
+precull_kernel(GaussIn g, int V, CamParams cam, OptParams o, RenderWs ws, uint32_t *cand,
+               uint32_t *n_cand) {
     __shared__ int s_wcnt[kPreThreads / 32];
+    __shared__ uint32_t s_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t i0 = (int64_t)blockIdx.x * kPreThreads;
-    const int64_t i = i0 + tid;
+    const int64_t i = (int64_t)blockIdx.x * kPreThreads + tid;
     const int64_t VN = (int64_t)V * g.N;
     int64_t nl = g.N;
     if (g.n_dev) nl = min(nl, (int64_t)*g.n_dev);
-    bool cand = false;
+    bool keep = false;
     if (i < VN) {
         const int v = (int)(i / g.N);
         const int64_t gi = i - (int64_t)v * g.N;
@@ -232,47 +250,70 @@ preprocess_fwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamPara
             } else if (op >= o.alpha_min) {
                 PoseDF P;
                 load_pose(ws.posedf + 24 * v, P);
-                cand = maybe_in_view(P, mx, my, mz, fmaxf(fabsf(sx), fmaxf(fabsf(sy), fabsf(sz))),
-                                     2.0f * logf(op / o.alpha_min), cam, o);
+                // fast log, widened by 1e-3 relative for the bound
+                keep = maybe_in_view(P, mx, my, mz, fmaxf(fabsf(sx), fmaxf(fabsf(sy), fabsf(sz))),
+                                     2.002f * __logf(op / o.alpha_min) + 1e-3f, cam, o);
             }
         }
-        if (!cand) ws.tcount[i] = 0u;
+        if (!keep) ws.tcount[i] = 0u;
     }
-    // block compaction of the candidates
-    const uint32_t m = __ballot_sync(0xffffffffu, cand);
+    const uint32_t m = __ballot_sync(0xffffffffu, keep);
     if (lane == 0) s_wcnt[warp] = __popc(m);
     __syncthreads();
-    int base = 0, total = 0;
+    if (tid == 0) {
+        int t = 0;
 #pragma unroll
-    for (int w = 0; w < kPreThreads / 32; ++w) {
-        const int c = s_wcnt[w];
-        base += w < warp ? c : 0;
-        total += c;
+        for (int w = 0; w < kPreThreads / 32; ++w) t += s_wcnt[w];
+        s_base = t ? atomicAdd(n_cand, (uint32_t)t) : 0u;
     }
-    if (cand) s_cand[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)tid;
     __syncthreads();
-    if (tid >= total) return;
-    const int64_t ic = i0 + s_cand[tid];
-    const int v = (int)(ic / g.N);
-    const int64_t gi = ic - (int64_t)v * g.N;
-    const float4 q = reinterpret_cast<const float4 *>(g.quats)[gi];
-    PoseDF P;
-    load_pose(ws.posedf + 24 * v, P);
-    Rec R;
-    BinRec B;
-    const uint32_t cnt = project_one(P, g.means[3 * gi], g.means[3 * gi + 1], g.means[3 * gi + 2], g.scales[3 * gi],
-                                     g.scales[3 * gi + 1], g.scales[3 * gi + 2], q, g.opac[gi], g.colors[3 * gi],
-                                     g.colors[3 * gi + 1], g.colors[3 * gi + 2], cam, o, ws.status, R, B);
-    ws.tcount[ic] = cnt;
-    if (cnt) {
-        ws.rec[ic] = R;
-        ws.bin[ic] = B;
-        if (zero_g2d) {
-            float2 *z2 = reinterpret_cast<float2 *>(ws.g2d + 10 * ic);
+    if (keep) {
+        int base = 0;
 #pragma unroll
-            for (int k = 0; k < 5; ++k) z2[k] = make_float2(0.f, 0.f);
+        for (int w = 0; w < kPreThreads / 32; ++w) base += w < warp ? s_wcnt[w] : 0;
+        cand[s_base + base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
+    }
+}
+
+// Pass 2, grid-strided over the candidates: the exact projection on full warps.
+// It also accumulates the digit histograms of the visible Gaussians' depth keys
+// for the depth sort.
+__global__ void __launch_bounds__(kPreThreads, 3)
+project_kernel(GaussIn g, CamParams cam, OptParams o, RenderWs ws, const uint32_t *__restrict__ cand,
+               const uint32_t *n_cand, bool zero_g2d) {
+    __shared__ uint32_t s_h[4][kRadix];
+    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0u;
+    __syncthreads();
+    const SortPass dps[4] = {{0, 8}, {8, 8}, {16, 8}, {24, 8}};  // the depth sort's passes over 32 bits
+    const int64_t nc = *n_cand;
+    for (int64_t k = (int64_t)blockIdx.x * kPreThreads + threadIdx.x; k < nc;
+         k += (int64_t)gridDim.x * kPreThreads) {
+        const int64_t ic = cand[k];
+        const int v = (int)(ic / g.N);
+        const int64_t gi = ic - (int64_t)v * g.N;
+        const float4 q = reinterpret_cast<const float4 *>(g.quats)[gi];
+        PoseDF P;
+        load_pose(ws.posedf + 24 * v, P);
+        Rec R;
+        BinRec B;
+        const uint32_t cnt = project_one(P, g.means[3 * gi], g.means[3 * gi + 1], g.means[3 * gi + 2],
+                                         g.scales[3 * gi], g.scales[3 * gi + 1], g.scales[3 * gi + 2], q,
+                                         g.opac[gi], g.colors[3 * gi], g.colors[3 * gi + 1], g.colors[3 * gi + 2],
+                                         cam, o, ws.status, R, B);
+        ws.tcount[ic] = cnt;
+        if (cnt) {
+            ws.rec[ic] = R;
+            ws.bin[ic] = B;
+            add_digits(s_h, dps, 4, __float_as_uint(R.r2.y));  // the depth key (camera z > 0)
+            if (zero_g2d) {
+                float2 *z2 = reinterpret_cast<float2 *>(ws.g2d + 10 * ic);
+#pragma unroll
+                for (int j = 0; j < 5; ++j) z2[j] = make_float2(0.f, 0.f);
+            }
         }
     }
+    __syncthreads();
+    flush_digits(s_h, 4, ws.sort_hist[0]);
 }
 
 VPGS_D float warp_sum(float x) {
@@ -329,7 +370,9 @@ preprocess_bwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamPara
             float2 *z2 = reinterpret_cast<float2 *>(ws.g2d + 10 * i);
 #pragma unroll
             for (int k = 0; k < 5; ++k) z2[k] = make_float2(0.f, 0.f);
-            const float gu = a01.x, gv = a01.y, ga = a23.x, gb = a23.y, gcn = a45.x;
+            // the compositing backward leaves out these constant factors (see pair_grad)
+            const float gu = a01.x * kInvExp2Half, gv = a01.y * kInvExp2Half;
+            const float ga = -0.5f * a23.x, gb = -a23.y, gcn = -0.5f * a45.x;
             go += a45.y;
             gc[0] += a67.x; gc[1] += a67.y; gc[2] += a89.x;
             const float gz = a89.y;
@@ -496,14 +539,40 @@ cudaError_t launch_export_projection(const RenderWs &ws, int64_t VN, int32_t *ti
 }
 
 cudaError_t launch_preprocess_fwd(const GaussIn &g, const double *T_cw, int V, const CamParams &cam,
-                                  const OptParams &o, const RenderWs &ws, bool zero_g2d,
-                                  cudaStream_t s) {
+                                  const OptParams &o, const RenderWs &ws, const RenderLayout &L,
+                                  bool zero_g2d, cudaStream_t s) {
     const int64_t VN = (int64_t)V * g.N;
-    VPGS_LAUNCH("pose_prepare", s, pose_prepare_kernel<<<(V + 63) / 64, 64, 0, s>>>(T_cw, V, ws.posedf));
+    PrepZero z;
+    z.w32[0] = ws.status;                      z.n32[0] = 1;
+    z.w32[1] = ws.counters;                    z.n32[1] = CNT_N;
+    z.w32[2] = ws.sort_hist[0];                z.n32[2] = 2 * 4 * kRadix;  // both sorts
+    z.w32[3] = ws.sort_look[0];                z.n32[3] = sort_blocks(std::max<int64_t>(L.VN, 1), kDepthSortItems) * kRadix;
+    z.w32[4] = ws.sort_look[1];                z.n32[4] = sort_blocks(L.M_cap, kTileSortItems) * kRadix;
+    z.w32[5] = reinterpret_cast<uint32_t *>(ws.ranges);  z.n32[5] = 2 * (int64_t)V * cam.T;
+    z.w64 = ws.scan_look[0];                   z.n64 = 2 * L.scan_blocks_max;  // both scans
+    static int prep_grid = 0;
+    if (prep_grid == 0) prep_grid = 8 * std::max(device_sm_count(), 1);
+    const int64_t words = std::max<int64_t>(z.n32[3] + z.n32[4] + z.n32[5], z.n64);
+    VPGS_LAUNCH("prepare", s,
+                prepare_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(prep_grid, (words + 255) / 256)),
+                                 256, 0, s>>>(T_cw, V, ws.posedf, z));
     if (VN == 0) return cudaGetLastError();
+    // the candidate list borrows the second depth-key buffer (free until the depth sort)
+    uint32_t *cand = ws.dkey[1], *n_cand = ws.counters + CNT_CAND;
     VPGS_LAUNCH("preprocess_fwd", s,
-                preprocess_fwd_kernel<<<(unsigned)((VN + kPreThreads - 1) / kPreThreads), kPreThreads, 0, s>>>(
-                    g, T_cw, V, cam, o, ws, zero_g2d));
+                precull_kernel<<<(unsigned)((VN + kPreThreads - 1) / kPreThreads), kPreThreads, 0, s>>>(
+                    g, V, cam, o, ws, cand, n_cand));
+    static int proj_grid = 0;
+    if (proj_grid == 0) {
+        int occ = 0, dev = 0, sms = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)project_kernel, kPreThreads, 0);
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        proj_grid = std::max(occ, 1) * std::max(sms, 1);
+    }
+    VPGS_LAUNCH("project", s,
+                project_kernel<<<(unsigned)std::min<int64_t>(proj_grid, (VN + kPreThreads - 1) / kPreThreads),
+                                 kPreThreads, 0, s>>>(g, cam, o, ws, cand, n_cand, zero_g2d));
     return cudaGetLastError();
 }
 

@@ -45,18 +45,24 @@ class Decoder:
         return C.vpgs_anchors(C.ptr(anchors), C.ptr(scaling), C.ptr(offsets), C.ptr(features),
                               anchors.shape[0], self.k, 1 if features.dtype == torch.bfloat16 else 0)
 
-    def forward(self, anchors, features, scaling, offsets, params, camera, T_cw):
-        """Returns dict: means/scales/quats/opacities/colors (capacity A*k rows),
-        n_dev (device int32 [1]), n (host int, synchronises) and src_index."""
+    def alloc_outputs(self, n_anchors: int):
+        """Output buffers for n_anchors anchors (A*k rows; only the first n_dev are written)."""
+        cap = max(n_anchors * self.k, 1)
+        dv = self.device
+        return {"means": torch.empty((cap, 3), device=dv), "scales": torch.empty((cap, 3), device=dv),
+                "quats": torch.empty((cap, 4), device=dv), "opacities": torch.empty((cap,), device=dv),
+                "colors": torch.empty((cap, 3), device=dv),
+                "n_dev": torch.empty((1,), dtype=torch.int32, device=dv),
+                "src_index": torch.empty((cap,), dtype=torch.int32, device=dv)}
+
+    def forward(self, anchors, features, scaling, offsets, params, camera, T_cw, out=None, sync=True):
+        """Returns dict: means/scales/quats/opacities/colors (capacity A*k rows, the
+        first n_dev written), n_dev (device int32 [1]), src_index, and with
+        sync=True n (host int; reading it synchronises).  `out` reuses buffers
+        from alloc_outputs."""
         A = anchors.shape[0]
         self._reserve(A)
-        cap = max(A * self.k, 1)
-        dv = self.device
-        out = {"means": torch.zeros((cap, 3), device=dv), "scales": torch.zeros((cap, 3), device=dv),
-               "quats": torch.zeros((cap, 4), device=dv), "opacities": torch.zeros((cap,), device=dv),
-               "colors": torch.zeros((cap, 3), device=dv),
-               "n_dev": torch.zeros((1,), dtype=torch.int32, device=dv),
-               "src_index": torch.full((cap,), -1, dtype=torch.int32, device=dv)}
+        out = self.alloc_outputs(A) if out is None else out
         a = self._anchors(anchors, features, scaling, offsets)
         mlp = C.vpgs_mlp(C.ptr(params), 1 if self.bf16 else 0)
         buf = C.vpgs_gaussian_buffers(C.ptr(out["means"]), C.ptr(out["scales"]), C.ptr(out["quats"]),
@@ -65,20 +71,23 @@ class Decoder:
                                       ctypes.byref(_cam(camera)), T_cw.data_ptr(), ctypes.byref(self.opts),
                                       ctypes.byref(buf), C.ptr(out["n_dev"]), C.ptr(out["src_index"]),
                                       current_stream_handle()), "vpgs_decode_anchors")
-        out["n"] = int(out["n_dev"].item())
+        if sync:
+            out["n"] = int(out["n_dev"].item())
         return out
 
-    def backward(self, anchors, features, scaling, offsets, params, camera, T_cw, fwd, grads):
+    def backward(self, anchors, features, scaling, offsets, params, camera, T_cw, fwd, grads, res=None):
         """grads: dict of dL/d{means,scales,quats,opacities,colors} shaped like fwd's
-        outputs.  Returns dict of features, offsets, scaling and params gradients."""
+        outputs.  Returns dict of features, offsets, scaling and params gradients,
+        accumulated (+=) into `res` when given, else into fresh zeroed tensors."""
         a = self._anchors(anchors, features, scaling, offsets)
         mlp = C.vpgs_mlp(C.ptr(params), 1 if self.bf16 else 0)
         cap = fwd["means"].shape[0]
         gl = C.vpgs_gaussians(C.ptr(grads["means"]), C.ptr(grads["scales"]), C.ptr(grads["quats"]),
                               C.ptr(grads["opacities"]), C.ptr(grads["colors"]), cap, C.ptr(fwd["n_dev"]))
-        res = {"features": torch.zeros(features.shape, dtype=torch.float32, device=self.device),
-               "offsets": torch.zeros_like(offsets), "scaling": torch.zeros_like(scaling),
-               "params": torch.zeros_like(params)}
+        if res is None:
+            res = {"features": torch.zeros(features.shape, dtype=torch.float32, device=self.device),
+                   "offsets": torch.zeros_like(offsets), "scaling": torch.zeros_like(scaling),
+                   "params": torch.zeros_like(params)}
         C.check(C.vpgs_decode_anchors_bwd(self.ws.data_ptr(), self.ws_bytes, ctypes.byref(a),
                                           ctypes.byref(mlp), ctypes.byref(_cam(camera)), T_cw.data_ptr(),
                                           ctypes.byref(self.opts), ctypes.byref(gl),
