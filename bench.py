@@ -195,14 +195,18 @@ def algorithmic_bytes(kernel: str, N: int, Nv: int, M: int, P: int):
 
     N Gaussians, Nv visible ones, M tile instances, P pixels."""
     table = {
-        # read 56 B of parameters per Gaussian; write the 52 B screen record per visible one
-        "preprocess_fwd": 56 * N + 52 * Nv,
+        # pre-cull: read 56 B of parameters and write a 4 B tile count per Gaussian
+        "preprocess_fwd": 60 * N,
+        # exact projection: write the 64 B screen record, the 64 B binning record and
+        # zero the 40 B of 2D gradient slots per visible Gaussian
+        "project": 168 * Nv,
         # gather id + 48 B record per instance; write RGB, depth, alpha, T, count (28 B/px)
         "composite_fwd": 52 * M + 28 * P,
         # same gather, read T, list length and 20 B of upstream gradient per pixel, write 40 B/visible
         "composite_bwd": 52 * M + 28 * P + 40 * Nv,
-        # read 2D grads + 56 B parameters per visible, read-modify-write 56 B of gradients per Gaussian
-        "preprocess_bwd": 96 * Nv + 112 * N,
+        # per visible Gaussian: read 40 B of mean / scale / rotation and the 40 B of 2D
+        # gradients, zero those slots, add 56 B of parameter gradients
+        "preprocess_bwd": 176 * Nv,
         # per pass: read and write one 8-byte (key, value) pair per item
         "radix_onesweep": None,
     }
@@ -235,6 +239,7 @@ KERNEL_SOURCES = {
     "composite_fwd": ["paper_2505_18992_gb300/csrc/render_comp.cu", "paper_2505_18992_gb300/csrc/common.cuh"],
     "composite_bwd": ["paper_2505_18992_gb300/csrc/render_comp.cu", "paper_2505_18992_gb300/csrc/common.cuh"],
     "preprocess_fwd": ["paper_2505_18992_gb300/csrc/render_pre.cu", "paper_2505_18992_gb300/csrc/common.cuh"],
+    "project": ["paper_2505_18992_gb300/csrc/render_pre.cu", "paper_2505_18992_gb300/csrc/common.cuh"],
     "preprocess_bwd": ["paper_2505_18992_gb300/csrc/render_pre.cu", "paper_2505_18992_gb300/csrc/common.cuh"],
     "radix_onesweep": ["paper_2505_18992_gb300/csrc/prims.cuh"],
     "scan_lookback": ["paper_2505_18992_gb300/csrc/prims.cuh", "paper_2505_18992_gb300/csrc/render_bin.cu"],

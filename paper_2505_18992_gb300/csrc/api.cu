@@ -25,10 +25,9 @@ bool valid_opts(const vpgs_render_opts *o) {
     // a warp covers whole rows of a tile: tile_w divides 32
     if (o->tile_w != 4 && o->tile_w != 8 && o->tile_w != 16 && o->tile_w != 32) return false;
     if (o->tile_h < 2 || o->tile_h > 64) return false;
-    // VPGS_PIX pixels per thread (rows y and y + tile_h/VPGS_PIX): whole warps
+    // at most 512 pixels per tile; VPGS_PIX adjacent rows per compositing thread, whole warps
     const int B = o->tile_w * o->tile_h;
-    // one compositing thread per VPGS_PIX pixels, at most 512 threads per tile
-    if (o->tile_h % 2 != 0 || B % 64 != 0 || B / VPGS_PIX > 512 || o->tile_h % VPGS_PIX != 0) return false;
+    if (o->tile_h % 2 != 0 || B % 64 != 0 || B > 512 || o->tile_h % VPGS_PIX != 0) return false;
     if (!(o->alpha_min > 0.f && o->alpha_min < 1.f)) return false;
     if (!(o->alpha_max > o->alpha_min && o->alpha_max < 1.f)) return false;
     if (!(o->t_min > 0.f && o->t_min < 1.f)) return false;

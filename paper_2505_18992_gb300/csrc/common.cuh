@@ -12,9 +12,9 @@
 #define VPGS_D __device__ __forceinline__
 
 // Compositing launch geometry (compile-time tuning knobs):
-//   VPGS_PIX    pixels per thread (rows y and y + tile_h/VPGS_PIX)
+//   VPGS_PIX    pixels per thread: VPGS_PIX adjacent rows of one column
 #ifndef VPGS_PIX
-#define VPGS_PIX 1
+#define VPGS_PIX 2
 #endif
 //   VPGS_BWD_ACC how the backward combines per-warp sums of a Gaussian's 2D
 //                gradient: 0 = one global atomic per warp, 1 = per-warp shared

@@ -39,7 +39,7 @@ VPGS_D TileCoord tile_coord(int t, const CamParams &cam) {
     return c;
 }
 
-// Each thread owns kPix pixels of its tile column: rows ly and ly + tile_h/kPix.
+// Each thread owns kPix pixels of its tile column: rows kPix*ly .. kPix*ly + kPix - 1.
 constexpr int kPix = VPGS_PIX;
 constexpr int kAcc = VPGS_BWD_ACC;  // combination of per-warp gradient sums (see common.cuh)
 constexpr int kMaxThreads = 512;
@@ -94,12 +94,11 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
     if (*status != 0u) return;
     const int tid = threadIdx.x, lane = tid & 31;
     uint16_t *wl = s_wl + (size_t)(tid >> 5) * NT;
-    const int half = cam.tile_h / kPix;
     const int lx = tid % cam.tile_w, ly = tid / cam.tile_w;
     const float pxl = (float)lx + 0.5f;
     float pyl[kPix];
 #pragma unroll
-    for (int q = 0; q < kPix; ++q) pyl[q] = (float)(ly + q * half) + 0.5f;
+    for (int q = 0; q < kPix; ++q) pyl[q] = (float)(kPix * ly + q) + 0.5f;
     const float2 band = warp_rows(pyl);
     int t = blockIdx.x;
     for (;;) {
@@ -121,7 +120,7 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
 #pragma unroll
         for (int q = 0; q < kPix; ++q) {
             T[q] = 1.f; C0[q] = C1[q] = C2[q] = D[q] = 0.f; cnt[q] = 0; last[q] = 0;
-            const int py = tc.ty * cam.tile_h + ly + q * half;
+            const int py = tc.ty * cam.tile_h + kPix * ly + q;
             done[q] = !(px < cam.W && py < cam.H);
         }
         bool all_done = true;
@@ -172,7 +171,7 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
         const int64_t HW = (int64_t)cam.H * cam.W;
 #pragma unroll
         for (int q = 0; q < kPix; ++q) {
-            const int py = tc.ty * cam.tile_h + ly + q * half;
+            const int py = tc.ty * cam.tile_h + kPix * ly + q;
             if (!(px < cam.W && py < cam.H)) continue;
             const int64_t pix = (int64_t)tc.v * HW + (int64_t)py * cam.W + px;
             if (out.rgb) {
@@ -298,12 +297,11 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
     __shared__ int s_max;
     if (*status != 0u) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int half = cam.tile_h / kPix;
     const int lx = tid % cam.tile_w, ly = tid / cam.tile_w;
     const float pxl = (float)lx + 0.5f;
     float pyl[kPix];
 #pragma unroll
-    for (int q = 0; q < kPix; ++q) pyl[q] = (float)(ly + q * half) + 0.5f;
+    for (int q = 0; q < kPix; ++q) pyl[q] = (float)(kPix * ly + q) + 0.5f;
     const float2 band = warp_rows(pyl);
     uint16_t *wl = s_wl + (size_t)warp * NT;
     float *my_part = s_part + (size_t)warp * NT * kPartStride;
@@ -341,7 +339,7 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
             PixState &p = ps[q];
             p.T = 1.f; p.gC0 = p.gC1 = p.gC2 = p.gD = p.gA = 0.f; p.last = 0;
             p.B0 = o.bg0; p.B1 = o.bg1; p.B2 = o.bg2; p.BD = 0.f;
-            const int py = tc.ty * cam.tile_h + ly + q * half;
+            const int py = tc.ty * cam.tile_h + kPix * ly + q;
             if (px < cam.W && py < cam.H) {
                 const int64_t pix = (int64_t)tc.v * HW + (int64_t)py * cam.W + px;
                 p.T = t_final[pix];
