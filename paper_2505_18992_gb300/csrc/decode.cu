@@ -23,6 +23,10 @@
 
 namespace vpgs {
 
+#ifndef VPGS_DECODE_BWD_MMA
+#define VPGS_DECODE_BWD_MMA 1  // BF16 form: backward on tensor cores (0: the FP32-FMA kernel)
+#endif
+
 constexpr int kDecAnchors = 128;   // anchors (and threads) per block
 constexpr int kFeat = 32, kIn = 36, kHid = 32, kMaxK = 10;
 constexpr int kOutStride = 121;    // per-anchor row of layer-2 outputs in shared memory
@@ -562,6 +566,382 @@ decode_bwd_kernel(DecParams p, const double *__restrict__ T, const int32_t *__re
 }
 
 // ---------------------------------------------------------------------------
+// BF16 backward on tensor cores.  Persistent blocks of 128 threads walk chunks
+// of 128 anchors; each warp owns 32 anchors (two 16-row tiles).  Per MLP:
+//   P = In W1^T + b1 and O = H W2^T + b2 are recomputed with BF16 operands
+//   (exact: inputs, weights and H are BF16 values), the head derivatives dO
+//   are formed per anchor, then
+//   dH = dO W2,  dPre = dH * [P > 0],  dIn += dPre W1,
+//   dW1 += dPre^T [In | 1],  dW2 += dO^T [H | 1]   (the ones give db1, db2).
+// dO and dPre are FP32; they enter the MMAs as hi + lo BF16 pairs (relative
+// error 2^-16 per term) with FP32 accumulation.  Weight gradients accumulate in
+// shared memory over the block's chunks and reach global memory once per block.
+// ---------------------------------------------------------------------------
+constexpr int kMA = 128;                 // anchors per chunk (= threads)
+constexpr int kAS = kMA + 8;             // row stride (bf16) of anchor-major staging
+constexpr int kOS = 81;                  // row stride (float) of per-anchor output rows
+constexpr int kW2T = 88;                 // row stride (bf16) of W2^T rows (outputs padded to 80)
+constexpr int kW1T = 40;                 // row stride (bf16) of W1^T rows (hidden 32 + pad)
+constexpr int kGW = 40;                  // columns of the weight-gradient accumulators
+VPGS_HD int out_pad16(int j) { return j == 0 ? 16 : (j == 1 ? 32 : 80); }  // per-MLP outputs padded to 16
+VPGS_HD int out_base(int j) { return j == 0 ? 0 : (j == 1 ? 16 : 48); }    // rows of MLP j in W2 / dW2 (K <= 10)
+
+struct DecBwdMmaSmem {
+    __nv_bfloat16 w1[96 * kInPad];       // [hid][in]  (forward layout)
+    __nv_bfloat16 w2[120 * kW2Pad];      // [out][hid] (forward layout)
+    __nv_bfloat16 w2t[96 * kW2T];        // [MLP*32 + hid][out]
+    __nv_bfloat16 w1t[3 * 40 * kW1T];    // [MLP][in][hid]
+    float b1[96], b2[120];
+    __nv_bfloat16 inrow[kMA * kInPad];   // [anchor][in]
+    __nv_bfloat16 inT[40 * kAS];         // [in | 1 | 0][anchor]
+    __nv_bfloat16 hT[40 * kAS];          // [hid | 1 | 0][anchor]
+    __nv_bfloat16 dpT[2][32 * kAS];      // dPre^T hi / lo: [hid][anchor]
+    __nv_bfloat16 doT[2][80 * kAS];      // dO^T hi / lo: [out][anchor]
+    float orow[kMA * kOS];               // per anchor: O, then dO, finally dIn
+    float gw1[3 * 32 * kGW];             // dW1 | db1 per MLP
+    float gw2[128 * kGW];                // dW2 | db2, rows out_base(j) + out
+};
+
+VPGS_D void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// A fragment pair (hi, lo) of two FP32 values
+VPGS_D void pack_split(float x0, float x1, uint32_t &hi, uint32_t &lo) {
+    __nv_bfloat16 h0, l0, h1, l1;
+    split_bf16(x0, h0, l0);
+    split_bf16(x1, h1, l1);
+    __nv_bfloat162 H = __halves2bfloat162(h0, h1), L = __halves2bfloat162(l0, l1);
+    hi = *reinterpret_cast<uint32_t *>(&H);
+    lo = *reinterpret_cast<uint32_t *>(&L);
+}
+
+VPGS_D uint32_t ld_u32(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
+
+__global__ void __launch_bounds__(kMA, 1)
+decode_bwd_mma_kernel(DecParams p, const double *__restrict__ T, const int32_t *__restrict__ inv,
+                      DecGradIn gin, DecGradOut gout) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    DecBwdMmaSmem &S = *reinterpret_cast<DecBwdMmaSmem *>(dsm);
+    __shared__ DecCam s_cam;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t4 = lane & 3;
+    const int K = p.K;
+    if (tid == 0) load_dec_cam(T, s_cam);
+    // effective weights (BF16-rounded matrices, FP32 biases) in the four layouts
+    for (int i = tid; i < 96 * kInPad; i += kMA) {
+        const int r = i / kInPad, c = i % kInPad;
+        S.w1[i] = __float2bfloat16_rn(c < kIn ? p.params[mlp_off(K, r / 32).w1 + (r % 32) * kIn + c] : 0.f);
+    }
+    for (int i = tid; i < 120 * kW2Pad; i += kMA) {
+        const int r = i / kW2Pad, c = i % kW2Pad;
+        const int j = r < kColCol ? 0 : (r < kColCov ? 1 : 2);
+        const MlpOff m = mlp_off(K, j);
+        const int n = r - out_base(j);
+        S.w2[i] = __float2bfloat16_rn((c < kHid && n < m.out) ? p.params[m.w2 + n * kHid + c] : 0.f);
+    }
+    for (int i = tid; i < 96 * kW2T; i += kMA) {
+        const int r = i / kW2T, n = i % kW2T, j = r / 32, q = r % 32;
+        const MlpOff m = mlp_off(K, j);
+        S.w2t[i] = __float2bfloat16_rn(n < m.out ? p.params[m.w2 + n * kHid + q] : 0.f);
+    }
+    for (int i = tid; i < 3 * 40 * kW1T; i += kMA) {
+        const int j = i / (40 * kW1T), rem = i % (40 * kW1T), k = rem / kW1T, q = rem % kW1T;
+        S.w1t[i] = __float2bfloat16_rn((k < kIn && q < kHid) ? p.params[mlp_off(K, j).w1 + q * kIn + k] : 0.f);
+    }
+    for (int i = tid; i < 96; i += kMA) S.b1[i] = p.params[mlp_off(K, i / 32).b1 + i % 32];
+    for (int i = tid; i < 120; i += kMA) {
+        const int j = i < kColCol ? 0 : (i < kColCov ? 1 : 2);
+        const MlpOff m = mlp_off(K, j);
+        S.b2[i] = (i - out_base(j) < m.out) ? p.params[m.b2 + i - out_base(j)] : 0.f;
+    }
+    // constant rows: the ones that turn the weight-gradient products into bias gradients
+    for (int i = tid; i < 4 * kAS; i += kMA) {
+        const __nv_bfloat16 v = __float2bfloat16_rn(i < kAS ? 1.f : 0.f);
+        S.inT[36 * kAS + i] = v;
+        S.hT[32 * kAS + i] = v;
+        S.hT[36 * kAS + i] = __float2bfloat16_rn(0.f);
+    }
+    for (int i = tid; i < 3 * 32 * kGW; i += kMA) S.gw1[i] = 0.f;
+    for (int i = tid; i < 128 * kGW; i += kMA) S.gw2[i] = 0.f;
+    __syncthreads();
+
+    const int64_t nchunks = (p.A + kMA - 1) / kMA;
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        // ---- per anchor: inputs, surviving Gaussians
+        const int64_t a = ch * kMA + tid;
+        const bool live = a < p.A;
+        float in[kIn];
+        bool keep = false;
+        if (live) keep = anchor_inputs(p, s_cam, a, in);
+        int idx[kMaxK];
+        bool any = false;
+        for (int m = 0; m < K; ++m) {
+            idx[m] = keep ? inv[a * K + m] : -1;
+            any |= idx[m] >= 0;
+        }
+        for (int k = 0; k < kInPad; ++k) {
+            const __nv_bfloat16 v = __float2bfloat16_rn(keep && k < kIn ? in[k] : 0.f);
+            S.inrow[tid * kInPad + k] = v;
+            if (k < kIn) S.inT[k * kAS + tid] = v;
+        }
+        float l[3] = {0, 0, 0}, dl[3] = {0, 0, 0};
+        if (live) {
+            l[0] = p.scaling[3 * a]; l[1] = p.scaling[3 * a + 1]; l[2] = p.scaling[3 * a + 2];
+        }
+        float dIn[2][5][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 5; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) dIn[mt][nt][e] = 0.f;
+        __syncthreads();
+#pragma unroll 1
+        for (int j = 0; j < 3; ++j) {
+            const int ntl2 = j == 0 ? 2 : (j == 1 ? 4 : 9);
+            const int kd_steps = out_pad16(j) / 16;
+            uint32_t mask[2] = {0u, 0u};
+            // ---- layer 1 and 2 on tensor cores (rows r0 .. r0 + 15 of the chunk)
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const int r0 = warp * 32 + mt * 16;
+                float acc[4][4];
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) {
+                    const float b0 = S.b1[32 * j + 8 * nt + 2 * t4], b1v = S.b1[32 * j + 8 * nt + 2 * t4 + 1];
+                    acc[nt][0] = b0; acc[nt][1] = b1v; acc[nt][2] = b0; acc[nt][3] = b1v;
+                }
+                const __nv_bfloat16 *A0 = S.inrow + (r0 + g) * kInPad, *A1 = S.inrow + (r0 + g + 8) * kInPad;
+#pragma unroll
+                for (int ks = 0; ks < 3; ++ks) {
+                    const int c0 = 16 * ks + 2 * t4;
+                    const uint32_t a0 = ld_u32(A0 + c0), a1 = ld_u32(A1 + c0), a2 = ld_u32(A0 + c0 + 8),
+                                   a3 = ld_u32(A1 + c0 + 8);
+#pragma unroll
+                    for (int nt = 0; nt < 4; ++nt) {
+                        const __nv_bfloat16 *B = S.w1 + (32 * j + 8 * nt + g) * kInPad;
+                        mma_bf16_16816(acc[nt], a0, a1, a2, a3, ld_u32(B + c0), ld_u32(B + c0 + 8));
+                    }
+                }
+                // ReLU mask, H (BF16) into hT and as layer-2 A fragments
+                uint32_t ha[2][4];
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (acc[nt][e] > 0.f) mask[mt] |= 1u << (4 * nt + e);
+                        const int q = 8 * nt + 2 * t4 + (e & 1), row = r0 + g + 8 * (e >> 1);
+                        S.hT[q * kAS + row] = __float2bfloat16_rn(fmaxf(acc[nt][e], 0.f));
+                    }
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {
+                    const float *x0 = acc[2 * kk], *x1 = acc[2 * kk + 1];
+                    ha[kk][0] = pack_bf16(fmaxf(x0[0], 0.f), fmaxf(x0[1], 0.f));
+                    ha[kk][1] = pack_bf16(fmaxf(x0[2], 0.f), fmaxf(x0[3], 0.f));
+                    ha[kk][2] = pack_bf16(fmaxf(x1[0], 0.f), fmaxf(x1[1], 0.f));
+                    ha[kk][3] = pack_bf16(fmaxf(x1[2], 0.f), fmaxf(x1[3], 0.f));
+                }
+                for (int nt = 0; nt < ntl2; ++nt) {
+                    const int col = out_base(j) + 8 * nt + 2 * t4;
+                    float d[4] = {S.b2[col], S.b2[col + 1], S.b2[col], S.b2[col + 1]};
+                    const __nv_bfloat16 *B = S.w2 + (out_base(j) + 8 * nt + g) * kW2Pad;
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const int c0 = 16 * kk + 2 * t4;
+                        mma_bf16_16816(d, ha[kk][0], ha[kk][1], ha[kk][2], ha[kk][3], ld_u32(B + c0),
+                                       ld_u32(B + c0 + 8));
+                    }
+                    const int lc = 8 * nt + 2 * t4;
+                    S.orow[(r0 + g) * kOS + lc] = d[0];
+                    S.orow[(r0 + g) * kOS + lc + 1] = d[1];
+                    S.orow[(r0 + g + 8) * kOS + lc] = d[2];
+                    S.orow[(r0 + g + 8) * kOS + lc + 1] = d[3];
+                }
+            }
+            __syncthreads();
+            // ---- per anchor: head derivatives dO (0 where no Gaussian survived)
+            {
+                float *orw = S.orow + tid * kOS;
+                const int w = j == 0 ? 1 : (j == 1 ? 3 : 7);
+                float dO[80];
+#pragma unroll
+                for (int n = 0; n < 80; ++n) dO[n] = 0.f;
+                for (int gm = 0; gm < K; ++gm) {
+                    const int i = idx[gm];
+                    if (i < 0) continue;
+                    const float *o = orw + w * gm;
+                    if (j == 0) {
+                        const float al = tanhf(o[0]);
+                        dO[gm] = gin.opac[i] * (1.f - al * al);
+                    } else if (j == 1) {
+                        for (int r = 0; r < 3; ++r) {
+                            const float c = sigmoidf_(o[r]);
+                            dO[3 * gm + r] = gin.colors[3 * i + r] * c * (1.f - c);
+                        }
+                    } else {
+                        for (int r = 0; r < 3; ++r) {
+                            const float sg = sigmoidf_(o[r]);
+                            const float gs = gin.scales[3 * i + r];
+                            dO[7 * gm + r] = gs * l[r] * sg * (1.f - sg);
+                            dl[r] += gs * sg;
+                        }
+                        const float nrm = sqrtf(o[3] * o[3] + o[4] * o[4] + o[5] * o[5] + o[6] * o[6]);
+                        const float inn = 1.0f / nrm;
+                        const float4 gq = reinterpret_cast<const float4 *>(gin.quats)[i];
+                        const float qn[4] = {o[3] * inn, o[4] * inn, o[5] * inn, o[6] * inn};
+                        const float gqv[4] = {gq.x, gq.y, gq.z, gq.w};
+                        const float dot = qn[0] * gqv[0] + qn[1] * gqv[1] + qn[2] * gqv[2] + qn[3] * gqv[3];
+                        for (int r = 0; r < 4; ++r) dO[7 * gm + 3 + r] = (gqv[r] - qn[r] * dot) * inn;
+                    }
+                }
+                for (int n = 0; n < out_pad16(j); ++n) {
+                    orw[n] = dO[n];
+                    split_bf16(dO[n], S.doT[0][n * kAS + tid], S.doT[1][n * kAS + tid]);
+                }
+            }
+            __syncthreads();
+            // ---- dH = dO W2, dPre = dH [P > 0], dIn += dPre W1, dPre^T staged
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const int r0 = warp * 32 + mt * 16;
+                float dh[4][4];
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) dh[nt][e] = 0.f;
+                const float *O0 = S.orow + (r0 + g) * kOS, *O1 = S.orow + (r0 + g + 8) * kOS;
+                for (int kd = 0; kd < kd_steps; ++kd) {
+                    const int c0 = 16 * kd + 2 * t4;
+                    uint32_t ah[4], alo[4];
+                    pack_split(O0[c0], O0[c0 + 1], ah[0], alo[0]);
+                    pack_split(O1[c0], O1[c0 + 1], ah[1], alo[1]);
+                    pack_split(O0[c0 + 8], O0[c0 + 9], ah[2], alo[2]);
+                    pack_split(O1[c0 + 8], O1[c0 + 9], ah[3], alo[3]);
+#pragma unroll
+                    for (int nt = 0; nt < 4; ++nt) {
+                        const __nv_bfloat16 *B = S.w2t + (32 * j + 8 * nt + g) * kW2T;
+                        const uint32_t b0 = ld_u32(B + c0), b1 = ld_u32(B + c0 + 8);
+                        mma_bf16_16816(dh[nt], ah[0], ah[1], ah[2], ah[3], b0, b1);
+                        mma_bf16_16816(dh[nt], alo[0], alo[1], alo[2], alo[3], b0, b1);
+                    }
+                }
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (!(mask[mt] >> (4 * nt + e) & 1u)) dh[nt][e] = 0.f;
+                        const int q = 8 * nt + 2 * t4 + (e & 1), row = r0 + g + 8 * (e >> 1);
+                        split_bf16(dh[nt][e], S.dpT[0][q * kAS + row], S.dpT[1][q * kAS + row]);
+                    }
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {
+                    uint32_t ah[4], alo[4];
+                    const float *x0 = dh[2 * kk], *x1 = dh[2 * kk + 1];
+                    pack_split(x0[0], x0[1], ah[0], alo[0]);
+                    pack_split(x0[2], x0[3], ah[1], alo[1]);
+                    pack_split(x1[0], x1[1], ah[2], alo[2]);
+                    pack_split(x1[2], x1[3], ah[3], alo[3]);
+                    const int c0 = 16 * kk + 2 * t4;
+#pragma unroll
+                    for (int nt = 0; nt < 5; ++nt) {
+                        const __nv_bfloat16 *B = S.w1t + (j * 40 + 8 * nt + g) * kW1T;
+                        const uint32_t b0 = ld_u32(B + c0), b1 = ld_u32(B + c0 + 8);
+                        mma_bf16_16816(dIn[mt][nt], ah[0], ah[1], ah[2], ah[3], b0, b1);
+                        mma_bf16_16816(dIn[mt][nt], alo[0], alo[1], alo[2], alo[3], b0, b1);
+                    }
+                }
+            }
+            __syncthreads();
+            // ---- weight gradients of MLP j over the chunk's anchors
+            if (gout.params) {
+                const int mt2 = out_pad16(j) / 16;
+                const int n1 = 2 * 5, n2 = mt2 * 5;
+                for (int t = warp; t < n1 + n2; t += kMA / 32) {
+                    const bool first = t < n1;
+                    const int tt = first ? t : t - n1;
+                    const int mt = tt / 5, nt = tt % 5;
+                    const __nv_bfloat16 *Ah = first ? S.dpT[0] : S.doT[0];
+                    const __nv_bfloat16 *Al = first ? S.dpT[1] : S.doT[1];
+                    const __nv_bfloat16 *Bm = first ? S.inT : S.hT;
+                    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+                    const int ra = (16 * mt + g) * kAS, rb = (16 * mt + g + 8) * kAS, rB = (8 * nt + g) * kAS;
+#pragma unroll 4
+                    for (int ks = 0; ks < kMA / 16; ++ks) {
+                        const int c0 = 16 * ks + 2 * t4;
+                        const uint32_t b0 = ld_u32(Bm + rB + c0), b1 = ld_u32(Bm + rB + c0 + 8);
+                        mma_bf16_16816(acc, ld_u32(Ah + ra + c0), ld_u32(Ah + rb + c0), ld_u32(Ah + ra + c0 + 8),
+                                       ld_u32(Ah + rb + c0 + 8), b0, b1);
+                        mma_bf16_16816(acc, ld_u32(Al + ra + c0), ld_u32(Al + rb + c0), ld_u32(Al + ra + c0 + 8),
+                                       ld_u32(Al + rb + c0 + 8), b0, b1);
+                    }
+                    float *G = first ? S.gw1 + j * 32 * kGW : S.gw2 + out_base(j) * kGW;
+                    const int c = 8 * nt + 2 * t4;
+                    G[(16 * mt + g) * kGW + c] += acc[0];
+                    G[(16 * mt + g) * kGW + c + 1] += acc[1];
+                    G[(16 * mt + g + 8) * kGW + c] += acc[2];
+                    G[(16 * mt + g + 8) * kGW + c + 1] += acc[3];
+                }
+            }
+            __syncthreads();
+        }
+        // ---- dIn rows, then per anchor: feature, offset and scaling gradients
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            const int r0 = warp * 32 + mt * 16;
+#pragma unroll
+            for (int nt = 0; nt < 5; ++nt) {
+                const int c = 8 * nt + 2 * t4;
+                S.orow[(r0 + g) * kOS + c] = dIn[mt][nt][0];
+                S.orow[(r0 + g) * kOS + c + 1] = dIn[mt][nt][1];
+                S.orow[(r0 + g + 8) * kOS + c] = dIn[mt][nt][2];
+                S.orow[(r0 + g + 8) * kOS + c + 1] = dIn[mt][nt][3];
+            }
+        }
+        __syncthreads();
+        if (live && any) {
+            if (gout.features)
+                for (int k = 0; k < kFeat; ++k) gout.features[kFeat * a + k] += S.orow[tid * kOS + k];
+            for (int gm = 0; gm < K; ++gm) {
+                const int i = idx[gm];
+                if (i < 0) continue;
+                const float *O = p.offsets + (a * K + gm) * 3;
+                const float gmn[3] = {gin.means[3 * i], gin.means[3 * i + 1], gin.means[3 * i + 2]};
+                for (int r = 0; r < 3; ++r) {
+                    if (gout.offsets) gout.offsets[(a * K + gm) * 3 + r] += gmn[r] * l[r];
+                    dl[r] += gmn[r] * O[r];
+                }
+            }
+            if (gout.scaling)
+                for (int r = 0; r < 3; ++r) gout.scaling[3 * a + r] += dl[r];
+        }
+        __syncthreads();  // orow and the staging rows are rewritten by the next chunk
+    }
+    // ---- the block's weight gradients, once
+    if (gout.params) {
+        for (int i = tid; i < 3 * 32 * kGW; i += kMA) {
+            const int j = i / (32 * kGW), q = (i / kGW) % 32, c = i % kGW;
+            const MlpOff m = mlp_off(K, j);
+            const float v = S.gw1[i];
+            if (v == 0.f) continue;
+            if (c < kIn) atomicAdd(gout.params + m.w1 + q * kIn + c, v);
+            else if (c == kIn) atomicAdd(gout.params + m.b1 + q, v);
+        }
+        for (int i = tid; i < 128 * kGW; i += kMA) {
+            const int r = i / kGW, c = i % kGW;
+            const int j = r < kColCol ? 0 : (r < kColCov ? 1 : 2);
+            const MlpOff m = mlp_off(K, j);
+            const int n = r - out_base(j);
+            const float v = S.gw2[i];
+            if (v == 0.f || n >= m.out) continue;
+            if (c < kHid) atomicAdd(gout.params + m.w2 + n * kHid + c, v);
+            else if (c == kHid) atomicAdd(gout.params + m.b2 + n, v);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // workspace: [0] status, [256] counters (ticket), [512] look-back words, inverse map
 // ---------------------------------------------------------------------------
 struct DecLayout {
@@ -674,6 +1054,19 @@ vpgs_status vpgs_decode_anchors_bwd(void *ws, size_t ws_bytes, const vpgs_anchor
     }
     DecGradIn gin{dL->means, dL->scales, dL->quats, dL->opacities, dL->colors};
     DecGradOut gout{dL_dfeatures, dL_doffsets, dL_dscaling, dL_dparams};
+    if (p.bf16 && VPGS_DECODE_BWD_MMA) {
+        static bool mma_attr = false;
+        const size_t msm = sizeof(DecBwdMmaSmem);
+        if (!mma_attr) {
+            cudaFuncSetAttribute((const void *)decode_bwd_mma_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm);
+            mma_attr = true;
+        }
+        const int64_t nch = (p.A + kMA - 1) / kMA;
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nch, sms));
+        VPGS_LAUNCH("decode_bwd", s, decode_bwd_mma_kernel<<<grid, kMA, msm, s>>>(p, T_cw, inv, gin, gout));
+        return cudaGetLastError() == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
+    }
     const unsigned nb = (unsigned)((p.A + kBwdAnchors - 1) / kBwdAnchors);
     VPGS_LAUNCH("decode_bwd", s, decode_bwd_kernel<<<nb, kBwdAnchors, smem, s>>>(p, T_cw, inv, gin, gout));
     return cudaGetLastError() == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
