@@ -10,3 +10,4 @@ from .raster import (Options, Margins, render, render_scene, project, extent, ti
 from .decode import decode, decode_scene, bf16_round, n_mlp_params, flatten_mlp, MLP_ORDER  # noqa: F401,E402
 from .pose import pose_step, se3_exp  # noqa: F401,E402
 from .loss import mapping_loss, ssim_map, gaussian_window  # noqa: F401,E402
+from .fusion import distill_loss, adam_step  # noqa: F401,E402
