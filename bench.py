@@ -486,7 +486,8 @@ def run_ours(a):
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
         # coarse tracking: 50 pose-only iterations, eager vs one captured CUDA graph
         for key, fn in (("tracking", lambda: tracking_rows(sc, g, dev)), ("decode", lambda: decode_rows(dev)),
-                        ("batched_keyframes", lambda: batched_rows(dev)), ("fusion", lambda: fusion_rows(dev))):
+                        ("batched_keyframes", lambda: batched_rows(dev)), ("fusion", lambda: fusion_rows(dev)),
+                        ("mapping", lambda: mapping_rows(sc, g, dev))):
             try:
                 line[key] = fn()
             except Exception as exc:  # reported, not fatal
@@ -549,6 +550,54 @@ def decode_rows(dev):
     return res
 
 
+def mapping_rows(sc, g, dev, steps=20):
+    """Mapping step of Sec. III-A on the room frame: render, the full loss L_m
+    (Eq. 7-9: L1 + SSIM colour, L1 depth, volume), backward through the renderer
+    (recomputing its tile lists) to every Gaussian parameter.  The target is the
+    render from the pose perturbed by 2 cm / 1 degree."""
+    import torch
+
+    from paper_2505_18992_gb300.loss import MappingLoss
+    from paper_2505_18992_gb300.render import Intrinsics, Renderer
+    cam = sc.camera
+    W, H = cam.width, cam.height
+    r = Renderer(Intrinsics(W, H, cam.fx, cam.fy, cam.cx, cam.cy), device=dev)
+    T = torch.tensor(cam.T_cw, dtype=torch.float64, device=dev).contiguous()
+    T1 = torch.tensor(sc.extra["T_track0"], dtype=torch.float64, device=dev).reshape(1, 4, 4).contiguous()
+    tgt = r.forward(*g, T1, check=True)
+    t_rgb, t_depth = tgt["rgb"].clone(), tgt["depth"].clone()
+    out = r.forward(*g, T, check=True)
+    L = MappingLoss(1, W, H)
+    names = ("means", "scales", "quats", "opacities", "colors")
+    grads = {k: torch.zeros_like(t) for k, t in zip(names, g)}
+    d_rgb = torch.empty_like(out["rgb"])
+    d_depth = torch.empty_like(out["depth"])
+
+    def loss_only():
+        L(out["rgb"], t_rgb, out["depth"], t_depth, g[1], d_rgb=d_rgb, d_depth=d_depth, d_scales=grads["scales"])
+
+    def step():
+        for t in grads.values():
+            t.zero_()
+        r.forward(*g, T, out=out, check=False)
+        loss_only()
+        r.backward(*g, T, out, d_rgb, d_depth, None, grads=grads)
+
+    loss_ms = _time_ms(loss_only, steps)
+    step_ms = _time_ms(step, steps)
+    lv = L.loss.cpu().numpy()
+    P = W * H
+    # loss kernels: read rgb + target (24 B/px), write A, B, C (36 B/px); read them
+    # with rgb + target again (60 B/px), write the colour gradient (12 B/px); depth
+    # terms 12 B/px; volume term 24 B per Gaussian
+    loss_bytes = 144 * P + 12 * P + 24 * sc.n
+    return {"loss_ms": loss_ms, "loss_hbm_gbs": loss_bytes / (loss_ms * 1e-3) / 1e9,
+            "loss_algorithmic_bytes": loss_bytes, "step_ms": step_ms,
+            "step_mpix_s": P / (step_ms * 1e-3) / 1e6,
+            "terms": {"L_m": float(lv[0]), "L_c": float(lv[1]), "L_SSIM": float(lv[2]), "L_d": float(lv[3]),
+                      "L_vol": float(lv[4])}}
+
+
 def batched_rows(dev, steps=10):
     """8 keyframes of a 2M-Gaussian submap: one 8-view call vs 8 one-view calls (fwd+bwd)."""
     import torch
@@ -603,60 +652,90 @@ def batched_rows(dev, steps=10):
     return row
 
 
-def fusion_rows(dev):
-    """Submap fusion (Eq. 14 shape): two overlapping 500k-Gaussian submaps of a
-    street (50,000 anchors x k = 10 each) decoded with BF16 MLPs, each rendered
-    at 1920x1080 from a camera in the overlap, L1 distillation between the two
-    renders, backward through both renders and both decoders."""
+def fusion_rows(dev, iters=10):
+    """Submap fusion by distillation (Sec. III-C, Eq. 14) as an optimisation loop:
+    two overlapping 500k-Gaussian submaps of a street (50,000 anchors x k = 10
+    each, BF16 decoders), m = 4 keyframes in the overlap at 1920x1080.  Each
+    iteration decodes both submaps, renders the keyframes (one 4-view call per
+    submap), takes the squared distillation loss between the two renders, runs
+    the render backward (recomputing its tile lists) and the decoder backward of
+    both submaps, and takes an Adam step on each submap's anchor features and
+    MLP weights."""
     import torch
 
     from paper_2505_18992_gb300 import scenes
     from paper_2505_18992_gb300.decode import Decoder
+    from paper_2505_18992_gb300.fusion import Adam, DistillLoss
     from paper_2505_18992_gb300.render import Intrinsics, Renderer
     torch.cuda.reset_peak_memory_stats(dev)
     subs = [scenes.street_anchors(n_anchors=50_000, length=62.5, x0=x0, seed=20 + i, width=1920, height=1080,
                                   f=1000.0, cam_x=495.0, mlp_seed=7)
             for i, x0 in enumerate((437.5, 490.0))]
     t = lambda a, dt=torch.float32: torch.tensor(a, dtype=dt, device=dev).contiguous()  # noqa: E731
-    # camera in the 10 m overlap, facing the facade, so both submaps are in view
-    T_np = scenes.look_at([495.0, 0.0, 1.7], [495.0, 10.0, 1.7], [0, 0, 1])
-    for sc in subs:
-        sc.camera.T_cw = T_np[None]
+    # keyframes in the 10 m overlap, facing the facade, so both submaps are in view
+    kfs = np.stack([scenes.look_at([x, 0.0, 1.7], [x, 10.0, 1.7], [0, 0, 1]) for x in (491.5, 494.0, 496.0, 498.5)])
+    m = len(kfs)
+    T = t(kfs, torch.float64)
     cam = subs[0].camera
-    T = t(cam.T_cw[0], torch.float64)
-    r = Renderer(Intrinsics(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy), device=dev)
+    W, H = cam.width, cam.height
+    r = Renderer(Intrinsics(W, H, cam.fx, cam.fy, cam.cx, cam.cy), n_views=m, device=dev)
+    dist = DistillLoss(m, W, H)
     state = []
     for sc in subs:
+        sc.camera.T_cw = kfs[:1]  # decode culls against the first keyframe
         params = t(np.concatenate([np.asarray(p, np.float32).reshape(-1)
                                    for name in ("opacity", "color", "cov") for p in sc.mlp[name]]))
-        inp = (t(sc.anchors), t(sc.features), t(sc.scaling), t(sc.offsets), params)
-        state.append((Decoder(sc.k, bf16=True, device=dev), inp, sc))
-    P = cam.width * cam.height
+        feats = t(sc.features)
+        inp = (t(sc.anchors), feats, t(sc.scaling), t(sc.offsets), params)
+        d = Decoder(sc.k, bf16=True, device=dev)
+        out = d.forward(*inp, sc.camera, T[0])
+        res = {"features": torch.zeros_like(feats), "offsets": torch.zeros_like(inp[3]),
+               "scaling": torch.zeros_like(inp[2]), "params": torch.zeros_like(params)}
+        opts = [Adam(feats, res["features"], lr=1e-3), Adam(params, res["params"], lr=1e-4)]
+        img = r.alloc_images()
+        grads = {k: torch.zeros_like(out[k]) for k in ("means", "scales", "quats", "opacities", "colors")}
+        state.append({"d": d, "inp": inp, "sc": sc, "out": out, "res": res, "opts": opts, "img": img,
+                      "grads": grads, "g_rgb": torch.empty_like(img["rgb"]), "g_d": torch.empty_like(img["depth"])})
+    for st in state:  # size the render workspace once (host sync, untimed)
+        o = st["out"]
+        r.forward(o["means"], o["scales"], o["quats"], o["opacities"], o["colors"], T, n_dev=o["n_dev"],
+                  out=st["img"], check=True)
+    P = W * H
 
-    def step():
-        outs, imgs = [], []
-        for d, inp, sc in state:
-            o = d.forward(*inp, sc.camera, T)
-            img = r.forward(o["means"], o["scales"], o["quats"], o["opacities"], o["colors"], T[None].contiguous(),
-                            n_dev=o["n_dev"], check=False)
-            outs.append(o)
-            imgs.append({k: v.clone() for k, v in img.items()})
-        # L1 distillation between the two submaps' colour and depth (caller-side)
-        g_rgb = torch.sign(imgs[0]["rgb"] - imgs[1]["rgb"]) / (3 * P)
-        g_d = torch.sign(imgs[0]["depth"] - imgs[1]["depth"]) / P
-        for i, ((d, inp, sc), o, img) in enumerate(zip(state, outs, imgs)):
-            sgn = 1.0 if i == 0 else -1.0
-            grads = {k: torch.zeros_like(o[k]) for k in ("means", "scales", "quats", "opacities", "colors")}
-            r.backward(o["means"], o["scales"], o["quats"], o["opacities"], o["colors"], T[None].contiguous(), img,
-                       sgn * g_rgb, sgn * g_d, None, grads=grads, n_dev=o["n_dev"])
-            d.backward(*inp, sc.camera, T, o, grads)
+    def iteration():
+        for st in state:
+            o = st["d"].forward(*st["inp"], st["sc"].camera, T[0], out=st["out"], sync=False)
+            r.forward(o["means"], o["scales"], o["quats"], o["opacities"], o["colors"], T, n_dev=o["n_dev"],
+                      out=st["img"], check=False)
+        a, b = state
+        dist(a["img"]["rgb"], b["img"]["rgb"], a["img"]["depth"], b["img"]["depth"], a["g_rgb"], b["g_rgb"],
+             a["g_d"], b["g_d"])
+        for st in state:
+            o, gr = st["out"], st["grads"]
+            for v in gr.values():
+                v.zero_()
+            r.backward(o["means"], o["scales"], o["quats"], o["opacities"], o["colors"], T, st["img"], st["g_rgb"],
+                       st["g_d"], None, grads=gr, n_dev=o["n_dev"])
+            st["d"].backward(*st["inp"], st["sc"].camera, T[0], o, gr, res=st["res"])
+            for opt in st["opts"]:
+                opt.step()
 
-    step()
+    losses = []
+    iteration()
     torch.cuda.synchronize()
-    ms = _time_ms(step, 5)
-    return {"submaps": 2, "gaussians_decoded": [int(s[0].forward(*s[1], s[2].camera, T)["n"]) for s in state],
-            "width": cam.width, "height": cam.height, "ms_per_step": ms,
-            "mpix_s": 2 * P / (ms * 1e-3) / 1e6,
+    losses.append(float(dist.loss[0]))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(iters):
+        iteration()
+    e1.record()
+    torch.cuda.synchronize()
+    losses.append(float(dist.loss[0]))
+    ms = e0.elapsed_time(e1) / iters
+    return {"submaps": 2, "keyframes": m, "width": W, "height": H,
+            "gaussians_decoded": [int(st["out"]["n_dev"].item()) for st in state],
+            "ms_per_iteration": ms, "mpix_s": 2 * m * P / (ms * 1e-3) / 1e6,
+            "loss": {"first": losses[0], f"after_{iters + 1}": losses[1]},
             "peak_hbm_gb": torch.cuda.max_memory_allocated(dev) / 1e9}
 
 

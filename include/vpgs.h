@@ -302,6 +302,75 @@ vpgs_status vpgs_decode_anchors_bwd(void *ws, size_t ws_bytes, const vpgs_anchor
                                     float *dL_dparams, vpgs_stream stream);
 
 /* ---------------------------------------------------------------------- */
+/* Mapping loss (Sec. III-A, Eq. 7-9)                                      */
+/* ---------------------------------------------------------------------- */
+
+/* Loss weights (host struct).  vpgs_loss_weights_default(): lambda_ssim 0.2 and
+ * lambda_vol 0.001 (the paper's values, Sec. IV), lambda_d 1 (not stated). */
+typedef struct {
+    float lambda_ssim;  /* in [0, 1] */
+    float lambda_d;     /* >= 0 */
+    float lambda_vol;   /* >= 0 */
+} vpgs_loss_weights;
+
+void vpgs_loss_weights_default(vpgs_loss_weights *w);                 /* w: host */
+
+/* Workspace bytes of vpgs_mapping_loss for n_views images of width x height
+ * (0 if invalid: sizes <= 0 or > 65535, more than 4096 views). */
+size_t vpgs_mapping_loss_workspace_bytes(int32_t n_views, int32_t width, int32_t height);
+
+/* Mapping loss L_m = L_c + L_SSIM + lambda_d L_d + lambda_vol L_vol (Eq. 7),
+ * L_SSIM = (1 - lambda_ssim) |I^ - I|_1 + lambda_ssim (1 - SSIM(I^, I)) (Eq. 8),
+ * L_vol = sum_i Prod(s_i) (Eq. 9), and its gradient.  Readings: L_c and |.|_1 are
+ * mean absolute colour differences; L_d sums |D^ - D| over pixels with target
+ * depth > 0 and divides by the pixel count; SSIM uses an 11x11 Gaussian window
+ * (sigma 1.5, zero padding, C1 = 0.01^2, C2 = 0.03^2), averaged over views,
+ * channels and pixels.
+ *   rgb, target_rgb [V,3,H,W] float32 device (required).
+ *   depth, target_depth [V,H,W] float32 device, both or neither (L_d = 0).
+ *   scales [n_gaussians,3] float32 device; n_dev optional device count
+ *     (as in vpgs_gaussians); n_gaussians 0 gives L_vol = 0.
+ *   loss_out [5] float64 device, written: L_m, L_c, L_SSIM, L_d, L_vol.
+ *   dL_drgb [V,3,H,W], dL_ddepth [V,H,W]: written (may be NULL);
+ *   dL_dscales [n,3]: accumulated (+=) (may be NULL).
+ * ws: 16-byte aligned, ws_bytes from vpgs_mapping_loss_workspace_bytes.
+ * Two kernel launches, no host synchronisation; graph-capturable. */
+vpgs_status vpgs_mapping_loss(void *ws, size_t ws_bytes, const float *rgb, const float *target_rgb,
+                              const float *depth, const float *target_depth, int32_t n_views,
+                              int32_t width, int32_t height, const float *scales, int64_t n_gaussians,
+                              const int32_t *n_dev, const vpgs_loss_weights *w, double *loss_out,
+                              float *dL_drgb, float *dL_ddepth, float *dL_dscales, vpgs_stream stream);
+
+/* ---------------------------------------------------------------------- */
+/* Submap fusion (Sec. III-C, Eq. 14) and the optimiser step              */
+/* ---------------------------------------------------------------------- */
+
+/* Workspace bytes of vpgs_distill_loss (32 KiB; 0 if the sizes are invalid). */
+size_t vpgs_distill_workspace_bytes(int32_t n_views, int32_t width, int32_t height);
+
+/* Distillation loss between the renders of m = n_views overlapping keyframes
+ * from two submaps a and b (Eq. 14):
+ *   L = 1/m sum_kf ( mean_{c,p} (c_a - c_b)^2 + mean_p (d_a - d_b)^2 )
+ * (reading: squared differences averaged over channels and pixels per image).
+ *   rgb_a, rgb_b [m,3,H,W], depth_a, depth_b [m,H,W] (both or neither) float32 device.
+ *   loss_out [3] float64 device, written: L, colour term, depth term.
+ *   dL_d* : written, each may be NULL.
+ * ws: 16-byte aligned.  Two launches, no host synchronisation. */
+vpgs_status vpgs_distill_loss(void *ws, size_t ws_bytes, const float *rgb_a, const float *rgb_b,
+                              const float *depth_a, const float *depth_b, int32_t n_views, int32_t width,
+                              int32_t height, double *loss_out, float *dL_drgb_a, float *dL_drgb_b,
+                              float *dL_ddepth_a, float *dL_ddepth_b, vpgs_stream stream);
+
+/* One Adam step (Kingma and Ba, bias-corrected) over n float32 device values:
+ * m <- b1 m + (1 - b1) g, v <- b2 v + (1 - b2) g^2,
+ * params <- params - lr m^ / (sqrt(v^) + eps) with m^ = m / (1 - b1^step),
+ * v^ = v / (1 - b2^step); grads is zeroed.  hyper (host) = {lr, b1, b2, eps};
+ * step >= 1 is the 1-based step number.  The paper optimises the overlapping
+ * submaps' parameters with the distillation loss; it names no optimiser. */
+vpgs_status vpgs_adam_step(float *params, float *grads, float *m, float *v, int64_t n, const float hyper[4],
+                           int32_t step, vpgs_stream stream);
+
+/* ---------------------------------------------------------------------- */
 /* Diagnostics (host)                                                      */
 /* ---------------------------------------------------------------------- */
 

@@ -193,6 +193,11 @@ struct SortPass {
     int shift, bits;
 };
 
+// predecessor tiles read per look-back step of a one-sweep pass
+#ifndef VPGS_LOOK_DEPTH
+#define VPGS_LOOK_DEPTH 16
+#endif
+
 // one-sweep look-back word: [31:30] flag (1 = block aggregate, 2 = inclusive
 // prefix), [29:0] count
 constexpr uint32_t kSFlagAgg = 1u << 30;
@@ -296,7 +301,7 @@ radix_onesweep_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__res
         } else {
             st_volatile_u32(my, kSFlagAgg | c);
             // kLookDepth independent loads per step shorten the dependent chain
-            constexpr int kLookDepth = 16;
+            constexpr int kLookDepth = VPGS_LOOK_DEPTH;
             int64_t j0 = bid - 1;
             bool done = false;
             while (!done) {

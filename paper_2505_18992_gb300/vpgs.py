@@ -70,6 +70,10 @@ class vpgs_decode_opts(ctypes.Structure):
     _fields_ = [("near_z", c_float), ("guard", c_float)]
 
 
+class vpgs_loss_weights(ctypes.Structure):
+    _fields_ = [("lambda_ssim", c_float), ("lambda_d", c_float), ("lambda_vol", c_float)]
+
+
 _SIGS = {
     "vpgs_render_opts_default": (None, [POINTER(vpgs_render_opts)]),
     "vpgs_render_workspace_bytes": (c_size_t, [c_int64, c_int32, POINTER(vpgs_camera),
@@ -99,6 +103,16 @@ _SIGS = {
                                           POINTER(vpgs_mlp), POINTER(vpgs_camera), c_void_p,
                                           POINTER(vpgs_decode_opts), POINTER(vpgs_gaussians),
                                           c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "vpgs_loss_weights_default": (None, [POINTER(vpgs_loss_weights)]),
+    "vpgs_mapping_loss_workspace_bytes": (c_size_t, [c_int32, c_int32, c_int32]),
+    "vpgs_mapping_loss": (c_int32, [c_void_p, c_size_t, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
+                                    c_int32, c_int32, c_void_p, c_int64, c_void_p, POINTER(vpgs_loss_weights),
+                                    c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "vpgs_distill_workspace_bytes": (c_size_t, [c_int32, c_int32, c_int32]),
+    "vpgs_distill_loss": (c_int32, [c_void_p, c_size_t, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32,
+                                    c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "vpgs_adam_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, POINTER(c_float), c_int32,
+                                 c_void_p]),
     "vpgs_launch_count": (c_int64, []),
     "vpgs_profile_enable": (None, [c_int32]),
     "vpgs_profile_collect": (c_int32, [c_char_p, c_size_t, POINTER(c_int64), POINTER(c_double),
@@ -159,6 +173,12 @@ vpgs_pose_step = _entry("vpgs_pose_step")
 vpgs_decode_workspace_bytes = _entry("vpgs_decode_workspace_bytes")
 vpgs_decode_anchors = _entry("vpgs_decode_anchors")
 vpgs_decode_anchors_bwd = _entry("vpgs_decode_anchors_bwd")
+vpgs_loss_weights_default = _entry("vpgs_loss_weights_default")
+vpgs_mapping_loss_workspace_bytes = _entry("vpgs_mapping_loss_workspace_bytes")
+vpgs_mapping_loss = _entry("vpgs_mapping_loss")
+vpgs_distill_workspace_bytes = _entry("vpgs_distill_workspace_bytes")
+vpgs_distill_loss = _entry("vpgs_distill_loss")
+vpgs_adam_step = _entry("vpgs_adam_step")
 vpgs_launch_count = _entry("vpgs_launch_count")
 vpgs_profile_enable = _entry("vpgs_profile_enable")
 vpgs_profile_collect = _entry("vpgs_profile_collect")
