@@ -11,3 +11,4 @@ from .decode import decode, decode_scene, bf16_round, n_mlp_params, flatten_mlp,
 from .pose import pose_step, se3_exp  # noqa: F401,E402
 from .loss import mapping_loss, ssim_map, gaussian_window  # noqa: F401,E402
 from .fusion import distill_loss, adam_step  # noqa: F401,E402
+from .icp import icp as voxel_icp, voxel_downsample  # noqa: F401,E402
