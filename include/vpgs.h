@@ -371,6 +371,103 @@ vpgs_status vpgs_adam_step(float *params, float *grads, float *m, float *v, int6
                            int32_t step, vpgs_stream stream);
 
 /* ---------------------------------------------------------------------- */
+/* Fine tracking: voxel-hash ICP against the Gaussian means (Sec. III-B,   */
+/* Eq. 10-12)                                                              */
+/* ---------------------------------------------------------------------- */
+
+/* The voxel of a point for an edge v is floor(x / v) per axis, evaluated in
+ * float32 with the correctly rounded division.  Every voxel index must lie in
+ * [-2^20, 2^20).  Poses here map the scan's local frame to the world (the
+ * inverse of the renderer's T_cw) and are row-major double[4][4]. */
+
+typedef struct {
+    float map_voxel;    /* edge of the map's voxels: the `voxel` of vpgs_icp_build_map */
+    float voxel_1;      /* first downsampling edge (the paper keeps one original point per voxel) */
+    float voxel_2;      /* second downsampling edge, applied to the survivors of the first */
+    float tau;          /* correspondence threshold tau_t (m), 0 < tau <= map_voxel */
+    float sigma;        /* Geman-McClure scale sigma_t > 0 (Eq. 12); the caller adapts it */
+    float eps;          /* stop once a step has |xi| < eps (>= 0) */
+    int32_t iterations; /* maximum Gauss-Newton iterations, 1..1000 */
+    int32_t pad;
+} vpgs_icp_opts;
+
+typedef struct {
+    int32_t status;     /* VPGS_OK or the first device-side error (map or scan) */
+    int32_t iterations; /* Gauss-Newton iterations run */
+    int32_t n_source;   /* scan points kept by the double downsampling */
+    int32_t n_corr;     /* correspondences of the last linearisation */
+    int32_t stop;       /* 0 iterations ran out, 1 |xi| < eps, 2 fewer than 6
+                           correspondences, 3 normal matrix not positive definite
+                           (2 and 3 leave that iteration's pose unchanged) */
+    int32_t pad;
+    double cost;        /* sum of rho(e) over the last linearisation */
+    double xi_norm;     /* |xi| of the last applied step */
+} vpgs_icp_report;
+
+typedef struct {
+    int64_t n_points;
+    int32_t n_voxels;   /* occupied voxels */
+    int32_t capacity;   /* hash slots */
+    int32_t status;     /* VPGS_ERR_NONFINITE / VPGS_ERR_INVALID_ARG: a point was
+                           non-finite / outside the voxel range and was left out */
+    float voxel;
+} vpgs_icp_map_info;
+
+/* Bytes of the map buffer for n_points points (0 if n_points < 0 or > 2^30). */
+size_t vpgs_icp_map_bytes(int64_t n_points);
+
+/* Builds the voxel hash map of the Gaussian means (the local map M of Sec.
+ * III-B): points [n_points,3] float32 device, world frame; voxel > 0 (m).
+ * map: device, 16-byte aligned, at least vpgs_icp_map_bytes(n_points); it holds
+ * a header, an open-addressing table of the occupied voxels with the range of
+ * their points, and the points grouped by voxel with their original index.
+ * Every point of a voxel is kept.  Four launches. */
+vpgs_status vpgs_icp_build_map(void *map, size_t map_bytes, const float *points, int64_t n_points, float voxel,
+                               vpgs_stream stream);
+
+/* Synchronises `stream` and copies the map header to the host. */
+vpgs_status vpgs_icp_map_query(const void *map, vpgs_icp_map_info *info, vpgs_stream stream);
+
+/* Workspace bytes of the ICP calls for scans of up to n_scan points (0 if
+ * n_scan < 0 or > 2^30).  vpgs_icp_linearize needs vpgs_icp_workspace_bytes(0). */
+size_t vpgs_icp_workspace_bytes(int64_t n_scan);
+
+/* Double downsampling of a scan [n_scan,3] float32 device: the lowest-index
+ * point of every voxel of edge voxel_1, then the lowest-index survivor of every
+ * voxel of edge voxel_2.  Writes *n_out (device int32) and the kept original
+ * indices, ascending, to idx_out[0 .. *n_out) (device, n_scan entries).
+ * Non-finite or out-of-range points are dropped and set the workspace status. */
+vpgs_status vpgs_icp_downsample(void *ws, size_t ws_bytes, const float *scan, int64_t n_scan, float voxel_1,
+                                float voxel_2, int32_t *idx_out, int32_t *n_out, vpgs_stream stream);
+
+/* One linearisation of Eq. 11 at pose T (device double[16]) for n_src source
+ * points src [n_src,3] float32 device (no downsampling): for every s = T p the
+ * nearest map point m with |s - m| < tau (float32 decision, ties to the lower
+ * map index) and, over those pairs, the Geman-McClure weighted Gauss-Newton
+ * system about the centre c (device double[3]):
+ *   H = sum w J^T J, b = sum w J^T r, r = s - m, J = [I, -[s - c]x],
+ *   w = k / (k + e^2)^2, k = sigma / 3, e = |r|.
+ * system (device double[29]) = H's upper triangle row by row (21), b (6),
+ * sum rho(e), the number of pairs.  corr (device int32[n_src] or NULL) = the
+ * map point's original index or -1.  0 < tau <= map_voxel. */
+vpgs_status vpgs_icp_linearize(void *ws, size_t ws_bytes, const void *map, size_t map_bytes, int64_t n_map,
+                               float map_voxel, const float *src, int64_t n_src, const double *T,
+                               const double *centre, float tau, float sigma, double *system, int32_t *corr,
+                               vpgs_stream stream);
+
+/* Registers a scan [n_scan,3] float32 device (local frame) against the map
+ * (Eq. 10-12): double downsampling, then up to opts->iterations reweighted
+ * Gauss-Newton steps T <- Tr(c) Exp(xi) Tr(-c) T (c = the translation of T on
+ * entry; the same iterates as the left perturbation Exp(xi) T).  T (device
+ * double[16]) holds the initial guess T_{i-1} T_pred on entry and the
+ * registered pose on return.  report (device) is rewritten by every
+ * iteration.  The launch sequence is fixed (2 + 4 + 2 * iterations kernels;
+ * the steps after the stop do no work), so the call can be captured. */
+vpgs_status vpgs_icp_register(void *ws, size_t ws_bytes, const void *map, size_t map_bytes, int64_t n_map,
+                              const float *scan, int64_t n_scan, const vpgs_icp_opts *opts, double *T,
+                              vpgs_icp_report *report, vpgs_stream stream);
+
+/* ---------------------------------------------------------------------- */
 /* Diagnostics (host)                                                      */
 /* ---------------------------------------------------------------------- */
 

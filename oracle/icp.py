@@ -119,12 +119,16 @@ def nearest_f32(s, map_points, tau, tree=None):
     return out
 
 
-def normal_equations(s, m, sigma, c=None):
+def normal_equations(s, m, sigma, c=None, magnitude=False):
     """Weighted Gauss-Newton system about centre c for residuals r = s - m
-    (s already transformed).  Returns H [6,6], b [6], sum rho."""
+    (s already transformed).  Returns H [6,6], b [6], sum rho; with
+    magnitude=True also the sums of the absolute per-pair terms (|H|, |b|),
+    the scale against which a rounding error in the sums is measured."""
     c = np.zeros(3) if c is None else np.asarray(c, np.float64)
     H = np.zeros((6, 6))
     b = np.zeros(6)
+    Ha = np.zeros((6, 6))
+    ba = np.zeros(6)
     cost = 0.0
     for si, mi in zip(np.asarray(s, np.float64), np.asarray(m, np.float64)):
         r = si - mi
@@ -133,8 +137,10 @@ def normal_equations(s, m, sigma, c=None):
         J = np.hstack([np.eye(3), -skew(si - c)])
         H += w * J.T @ J
         b += w * J.T @ r
+        Ha += np.abs(w * J.T @ J)
+        ba += np.abs(w * J.T @ r)
         cost += gm_rho(e, sigma)
-    return H, b, cost
+    return (H, b, cost, Ha, ba) if magnitude else (H, b, cost)
 
 
 def solve_step(H, b):

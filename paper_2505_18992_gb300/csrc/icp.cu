@@ -1,0 +1,870 @@
+// Voxel-hash ICP of fine tracking (Sec. III-B, Eq. 10-12).
+//
+// Map.  The Gaussian means go into an open-addressing hash of their voxels
+// (edge v, linear probing, at most half full).  Each occupied voxel records
+// the range of its points, which sit grouped by voxel as float4
+// (x, y, z, original index).  Built by insert -> scan of the per-voxel counts
+// -> scatter; every point of a voxel is kept.
+//
+// Registration of one scan (local frame) from an initial pose T (local ->
+// world, Eq. 10):
+//   1. double downsampling: the lowest-index point of each voxel of edge v1
+//      (hash insert + atomicMin, then an order-keeping compaction by scan),
+//      then the same at v2 over the survivors;
+//   2. a fixed number of Gauss-Newton steps, two launches each.  One warp per
+//      source point finds the nearest map point closer than tau among the 27
+//      voxels around it (lane k probes neighbour k; voxels whose box lies
+//      farther than tau are skipped before probing; the lanes then stride the
+//      candidates of the live voxels) and the warp's lanes accumulate the 29
+//      numbers of the Geman-McClure weighted normal equations (Eq. 11-12),
+//      lane l owning number l.  A one-block kernel adds the block partials in
+//      FP64, solves the 6x6 system by Cholesky and updates T in FP64.  A
+//      device flag ends the loop early, so the launch sequence is fixed and
+//      the call can be captured into a CUDA graph.
+// The linearisation is about the centre c = translation of T on entry:
+// J = [I, -[s - c]x], T <- Tr(c) Exp(xi) Tr(-c) T.  That gives the same
+// iterates as the left perturbation about the origin (Exp(Ad_X xi) =
+// X Exp(xi) X^-1) while keeping the FP32 lever arms |s - c| at scan range
+// instead of world range.
+//
+// Decisions are taken in float32 with correctly rounded operations, so that
+// they are reproducible off the GPU: the voxel of a coordinate x is
+// floor(x / v); the squared distance is (dx^2 + dy^2) + dz^2 of
+// d = m - float32(s), accepted when below tau^2, ties to the lower map index.
+#include <cmath>
+
+#include "internal.h"
+#include "prims.cuh"
+#include "profiler.h"
+
+namespace vpgs {
+namespace {
+
+constexpr unsigned long long kEmptyKey = ~0ull;
+constexpr uint32_t kNoSlot = 0xffffffffu;
+constexpr int kVoxRange = 1 << 20;  // |voxel index| < 2^20 on every axis
+constexpr uint32_t kMapMagic = 0x49435056u;
+constexpr int kIcpThreads = 256;
+constexpr int kIcpWarps = kIcpThreads / kWarp;
+constexpr int kSys = 29;  // H upper triangle (21), b (6), sum rho, count
+constexpr int kIcpMaxBlocks = 4096;
+constexpr int kMinCorr = 6;
+constexpr int kStopEps = 1, kStopFew = 2, kStopIndefinite = 3;
+
+struct MapHeader {
+    uint32_t magic, cap, n_voxels, status;
+    int64_t n;
+    float voxel;
+    uint32_t ticket, total, pad[7];
+};
+static_assert(sizeof(MapHeader) == 64, "map header is 64 bytes");
+
+// map: a = first point, b = point count; downsampling: a = lowest index
+struct VoxEntry {
+    unsigned long long key;
+    uint32_t a, b;
+};
+
+struct IcpState {
+    uint32_t ticket[2], n1, n2;
+    uint32_t status, done, stop, iter;
+    double c[3];
+};
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+inline uint32_t table_cap(int64_t n) {
+    uint64_t c = 1024;
+    while (c < 2 * (uint64_t)n) c <<= 1;
+    return (uint32_t)c;
+}
+
+struct MapLayout {
+    uint32_t cap;
+    size_t off_tab, off_pts, off_slot, off_look, n_look, total;
+};
+
+MapLayout map_layout(int64_t n) {
+    MapLayout L;
+    L.cap = table_cap(n);
+    size_t o = sizeof(MapHeader);
+    L.off_tab = o;
+    o += sizeof(VoxEntry) * (size_t)L.cap;
+    L.off_pts = o;
+    o += sizeof(float4) * (size_t)n;
+    L.off_slot = o;
+    o = align_up(o + sizeof(uint32_t) * (size_t)n, 16);
+    L.off_look = o;
+    L.n_look = (size_t)std::max<int64_t>(scan_blocks(L.cap), 1);
+    o += sizeof(unsigned long long) * L.n_look;
+    L.total = o;
+    return L;
+}
+
+struct IcpLayout {
+    uint32_t cap;
+    size_t off_state, off_partial, off_tab1, off_tab2, off_slot1, off_slot2, off_idx1, off_idx2, off_look,
+        n_look, total;
+};
+
+IcpLayout icp_layout(int64_t n) {
+    IcpLayout L;
+    L.cap = table_cap(n);
+    size_t o = 0;
+    L.off_state = o;
+    o += 128;
+    L.off_partial = o;
+    o += sizeof(float) * kWarp * kIcpMaxBlocks;
+    L.off_tab1 = o;
+    o += sizeof(VoxEntry) * (size_t)L.cap;
+    L.off_tab2 = o;
+    o += sizeof(VoxEntry) * (size_t)L.cap;
+    const size_t idx_bytes = align_up(sizeof(uint32_t) * (size_t)n, 16);
+    L.off_slot1 = o;
+    o += idx_bytes;
+    L.off_slot2 = o;
+    o += idx_bytes;
+    L.off_idx1 = o;
+    o += idx_bytes;
+    L.off_idx2 = o;
+    o += idx_bytes;
+    L.off_look = o;
+    L.n_look = 2 * (size_t)std::max<int64_t>(scan_blocks(n), 1);
+    o += sizeof(unsigned long long) * L.n_look;
+    L.total = o;
+    return L;
+}
+
+// ---------------------------------------------------------------------------
+// voxels and the hash
+// ---------------------------------------------------------------------------
+VPGS_D bool voxel_index(float x, float v, int &i) {
+    const float q = floorf(__fdiv_rn(x, v));
+    if (!(q >= -(float)kVoxRange && q < (float)kVoxRange)) return false;  // also rejects NaN
+    i = (int)q;
+    return true;
+}
+
+VPGS_D bool in_voxel_range(int i) { return i >= -kVoxRange && i < kVoxRange; }
+
+VPGS_D unsigned long long pack_voxel(int ix, int iy, int iz) {
+    return ((unsigned long long)(uint32_t)(ix + kVoxRange) << 42) |
+           ((unsigned long long)(uint32_t)(iy + kVoxRange) << 21) | (unsigned long long)(uint32_t)(iz + kVoxRange);
+}
+
+// the splitmix64 finaliser (Steele, Lea and Flood, "Fast splittable
+// pseudorandom number generators", 2014) as the hash of a packed voxel
+VPGS_D uint32_t hash_slot(unsigned long long k, uint32_t mask) {
+    k ^= k >> 30;
+    k *= 0xbf58476d1ce4e5b9ull;
+    k ^= k >> 27;
+    k *= 0x94d049bb133111ebull;
+    k ^= k >> 31;
+    return (uint32_t)k & mask;
+}
+
+// Slot of `key`, claimed if absent; kNoSlot if the table is full (it never
+// is: the capacity is at least twice the number of keys).
+VPGS_D uint32_t insert_voxel(VoxEntry *tab, uint32_t mask, unsigned long long key, bool &fresh) {
+    uint32_t h = hash_slot(key, mask);
+    for (uint32_t p = 0; p <= mask; ++p) {
+        const unsigned long long cur = __ldcg(&tab[h].key);
+        if (cur == key) {
+            fresh = false;
+            return h;
+        }
+        if (cur == kEmptyKey) {
+            const unsigned long long prev = atomicCAS(&tab[h].key, kEmptyKey, key);
+            if (prev == kEmptyKey || prev == key) {
+                fresh = prev == kEmptyKey;
+                return h;
+            }
+        }
+        h = (h + 1) & mask;
+    }
+    fresh = false;
+    return kNoSlot;
+}
+
+VPGS_D uint32_t find_voxel(const VoxEntry *tab, uint32_t mask, unsigned long long key) {
+    uint32_t h = hash_slot(key, mask);
+    for (uint32_t p = 0; p <= mask; ++p) {
+        const unsigned long long cur = tab[h].key;
+        if (cur == key) return h;
+        if (cur == kEmptyKey) return kNoSlot;
+        h = (h + 1) & mask;
+    }
+    return kNoSlot;
+}
+
+// ---------------------------------------------------------------------------
+// map build
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+map_clear_kernel(MapHeader *hdr, VoxEntry *tab, uint32_t cap, unsigned long long *look, int64_t n_look, int64_t n,
+                 float voxel) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = t0; i < cap; i += stride) tab[i] = VoxEntry{kEmptyKey, 0u, 0u};
+    for (int64_t i = t0; i < n_look; i += stride) look[i] = 0ull;
+    if (t0 == 0) {
+        MapHeader h = {};
+        h.magic = kMapMagic;
+        h.cap = cap;
+        h.n = n;
+        h.voxel = voxel;
+        *hdr = h;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+map_insert_kernel(const float *__restrict__ pts, int64_t n, float v, VoxEntry *tab, uint32_t mask,
+                  uint32_t *__restrict__ slot, MapHeader *hdr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
+        uint32_t s = kNoSlot;
+        int ix, iy, iz;
+        if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
+            set_status(&hdr->status, VPGS_ERR_NONFINITE);
+        } else if (!(voxel_index(x, v, ix) && voxel_index(y, v, iy) && voxel_index(z, v, iz))) {
+            set_status(&hdr->status, VPGS_ERR_INVALID_ARG);
+        } else {
+            bool fresh;
+            s = insert_voxel(tab, mask, pack_voxel(ix, iy, iz), fresh);
+            if (s == kNoSlot) {
+                set_status(&hdr->status, VPGS_ERR_INTERNAL);
+            } else {
+                if (fresh) atomicAdd(&hdr->n_voxels, 1u);
+                atomicAdd(&tab[s].b, 1u);
+            }
+        }
+        slot[i] = s;
+    }
+}
+
+struct MapCountLoad {
+    const VoxEntry *tab;
+    VPGS_D uint32_t operator()(int64_t i) const { return tab[i].b; }
+};
+struct MapStartStore {
+    VoxEntry *tab;
+    VPGS_D void operator()(int64_t i, uint32_t excl, uint32_t) const {
+        tab[i].a = excl;
+        tab[i].b = 0u;  // recounted by the scatter
+    }
+};
+
+__global__ void __launch_bounds__(256)
+map_scatter_kernel(const float *__restrict__ pts, int64_t n, const uint32_t *__restrict__ slot, VoxEntry *tab,
+                   float4 *__restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t s = slot[i];
+        if (s == kNoSlot) continue;
+        const uint32_t pos = tab[s].a + atomicAdd(&tab[s].b, 1u);
+        out[pos] = make_float4(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2], __int_as_float((int)i));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// double downsampling
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+icp_prepare_kernel(VoxEntry *tab1, VoxEntry *tab2, uint32_t cap, unsigned long long *look, int64_t n_look,
+                   IcpState *st, const double *T, const MapHeader *hdr, vpgs_icp_report *rep) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = t0; i < cap; i += stride) {
+        tab1[i] = VoxEntry{kEmptyKey, kNoSlot, 0u};
+        tab2[i] = VoxEntry{kEmptyKey, kNoSlot, 0u};
+    }
+    for (int64_t i = t0; i < n_look; i += stride) look[i] = 0ull;
+    if (t0 == 0) {
+        IcpState s = {};
+        if (T) {
+            s.c[0] = T[3];
+            s.c[1] = T[7];
+            s.c[2] = T[11];
+        }
+        if (hdr) s.status = hdr->magic == kMapMagic ? hdr->status : (uint32_t)VPGS_ERR_INVALID_ARG;
+        *st = s;
+        if (rep) {
+            vpgs_icp_report r = {};
+            r.status = (int32_t)s.status;
+            *rep = r;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+ds_insert_kernel(const float *__restrict__ pts, const uint32_t *__restrict__ idx_in, int64_t n_cap,
+                 const uint32_t *n_dev, float v, VoxEntry *tab, uint32_t mask, uint32_t *__restrict__ slot,
+                 uint32_t *status) {
+    int64_t n = n_cap;
+    if (n_dev) n = min(n, (int64_t)*n_dev);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        const int64_t i = idx_in ? (int64_t)idx_in[j] : j;
+        const float x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
+        uint32_t s = kNoSlot;
+        int ix, iy, iz;
+        if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
+            set_status(status, VPGS_ERR_NONFINITE);
+        } else if (!(voxel_index(x, v, ix) && voxel_index(y, v, iy) && voxel_index(z, v, iz))) {
+            set_status(status, VPGS_ERR_INVALID_ARG);
+        } else {
+            bool fresh;
+            s = insert_voxel(tab, mask, pack_voxel(ix, iy, iz), fresh);
+            if (s == kNoSlot)
+                set_status(status, VPGS_ERR_INTERNAL);
+            else
+                atomicMin(&tab[s].a, (uint32_t)j);
+        }
+        slot[j] = s;
+    }
+}
+
+struct DsFlagLoad {
+    const VoxEntry *tab;
+    const uint32_t *slot;
+    VPGS_D uint32_t operator()(int64_t j) const {
+        const uint32_t s = slot[j];
+        return (s != kNoSlot && tab[s].a == (uint32_t)j) ? 1u : 0u;
+    }
+};
+struct DsKeepStore {
+    const uint32_t *idx_in;
+    uint32_t *out;
+    VPGS_D void operator()(int64_t j, uint32_t excl, uint32_t v) const {
+        if (v) out[excl] = idx_in ? idx_in[j] : (uint32_t)j;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// correspondences + normal equations
+// ---------------------------------------------------------------------------
+struct MapView {
+    const MapHeader *hdr;
+    const VoxEntry *tab;
+    const float4 *pts;
+    uint32_t mask;
+    int64_t n;
+    float voxel;
+};
+
+// column a of the 3x6 Jacobian [I, -[q]x] of s' = c + Exp(xi)(s - c) at xi = 0
+VPGS_D float3 jac_col(int a, float qx, float qy, float qz) {
+    switch (a) {
+        case 0: return make_float3(1.f, 0.f, 0.f);
+        case 1: return make_float3(0.f, 1.f, 0.f);
+        case 2: return make_float3(0.f, 0.f, 1.f);
+        case 3: return make_float3(0.f, -qz, qy);
+        case 4: return make_float3(qz, 0.f, -qx);
+        default: return make_float3(-qy, qx, 0.f);
+    }
+}
+
+VPGS_D float dot3(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+
+// distance from x to the slab [lo, lo + v) of voxel i (0 inside)
+VPGS_D float slab_gap(int i, float v, float x) {
+    const float lo = (float)i * v;
+    return fmaxf(fmaxf(lo - x, x - (lo + v)), 0.f);
+}
+
+__global__ void __launch_bounds__(kIcpThreads)
+icp_corr_kernel(MapView map, const float *__restrict__ src, const uint32_t *__restrict__ idx, int64_t n_cap,
+                const uint32_t *n_dev, const double *__restrict__ T, const double *__restrict__ centre, float tau,
+                float sigma, float *__restrict__ partial, int32_t *__restrict__ corr, IcpState *st) {
+    __shared__ float s_acc[kIcpWarps][kWarp];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (st->done) return;  // uniform over the grid: set by an earlier solve
+    {
+        // a map buffer that was not built for this size and voxel is never
+        // indexed: its ranges could point anywhere
+        const MapHeader *h = map.hdr;
+        if (h->magic != kMapMagic || h->n != map.n || h->cap != map.mask + 1 ||
+            __float_as_uint(h->voxel) != __float_as_uint(map.voxel)) {
+            if (threadIdx.x < kWarp) partial[(int64_t)blockIdx.x * kWarp + threadIdx.x] = 0.f;
+            if (blockIdx.x == 0 && threadIdx.x == 0) set_status(&st->status, VPGS_ERR_INVALID_ARG);
+            return;
+        }
+    }
+    int64_t n = n_cap;
+    if (n_dev) n = min(n, (int64_t)*n_dev);
+    double t[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) t[k] = T[k];
+    const double c0 = centre[0], c1 = centre[1], c2 = centre[2];
+    const float v = map.voxel;
+    const float tau2 = __fmul_rn(tau, tau);
+    const float kk = sigma / 3.f;
+    // lane k < 27 probes neighbour (k % 3 - 1, k / 3 % 3 - 1, k / 9 - 1)
+    const int ox = lane % 3 - 1, oy = (lane / 3) % 3 - 1, oz = lane / 9 - 1;
+    // lane l < 21 owns H[a][b] (upper triangle, row-major), 21..26 b[l-21]
+    int ea = 0, eb = 0;
+    if (lane < 21) {
+        int rem = lane;
+        while (rem >= 6 - ea) {
+            rem -= 6 - ea;
+            ++ea;
+        }
+        eb = ea + rem;
+    } else if (lane < 27) {
+        ea = lane - 21;
+    }
+    float acc = 0.f;
+    const int64_t nw = (int64_t)gridDim.x * kIcpWarps;
+    for (int64_t j = (int64_t)blockIdx.x * kIcpWarps + warp; j < n; j += nw) {
+        const int64_t i = idx ? (int64_t)idx[j] : j;
+        const double px = src[3 * i], py = src[3 * i + 1], pz = src[3 * i + 2];
+        // s = T p, each coordinate ((T_r0 x + T_r1 y) + T_r2 z) + T_r3 in FP64
+        const double sx = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(t[0], px), __dmul_rn(t[1], py)),
+                                              __dmul_rn(t[2], pz)), t[3]);
+        const double sy = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(t[4], px), __dmul_rn(t[5], py)),
+                                              __dmul_rn(t[6], pz)), t[7]);
+        const double sz = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(t[8], px), __dmul_rn(t[9], py)),
+                                              __dmul_rn(t[10], pz)), t[11]);
+        const float fx = __double2float_rn(sx), fy = __double2float_rn(sy), fz = __double2float_rn(sz);
+        int cx = 0, cy = 0, cz = 0;
+        const bool in_range = voxel_index(fx, v, cx) && voxel_index(fy, v, cy) && voxel_index(fz, v, cz);
+        uint32_t start = 0, cnt = 0;
+        if (in_range && lane < 27) {
+            const int nx = cx + ox, ny = cy + oy, nz = cz + oz;
+            if (in_voxel_range(nx) && in_voxel_range(ny) && in_voxel_range(nz)) {
+                // skip voxels whose box is farther than tau; the slack covers
+                // the rounding of the box bounds (a few ulps of |s|)
+                const float gx = slab_gap(nx, v, fx), gy = slab_gap(ny, v, fy), gz = slab_gap(nz, v, fz);
+                const float slack = 1e-4f + 1e-6f * fmaxf(fmaxf(fabsf(fx), fabsf(fy)), fabsf(fz));
+                const float lim = tau + slack;
+                if (gx * gx + gy * gy + gz * gz <= lim * lim) {
+                    const uint32_t s = find_voxel(map.tab, map.mask, pack_voxel(nx, ny, nz));
+                    if (s != kNoSlot) {
+                        start = map.tab[s].a;
+                        cnt = map.tab[s].b;
+                    }
+                }
+            }
+        }
+        uint32_t live = __ballot_sync(0xffffffffu, cnt > 0);
+        float best = tau2;
+        uint32_t bidx = kNoSlot, bpos = 0;
+        while (live) {
+            const int k = __ffs(live) - 1;
+            live &= live - 1;
+            const uint32_t s0 = __shfl_sync(0xffffffffu, start, k), c = __shfl_sync(0xffffffffu, cnt, k);
+            for (uint32_t q = lane; q < c; q += kWarp) {
+                const float4 m = map.pts[s0 + q];
+                const float dx = __fsub_rn(m.x, fx), dy = __fsub_rn(m.y, fy), dz = __fsub_rn(m.z, fz);
+                const float d2 =
+                    __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+                const uint32_t mi = (uint32_t)__float_as_int(m.w);
+                if (d2 < best || (d2 == best && best < tau2 && mi < bidx)) {
+                    best = d2;
+                    bidx = mi;
+                    bpos = s0 + q;
+                }
+            }
+        }
+        // warp argmin of (d2, map index): every lane ends with the same winner
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const uint32_t oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+            const uint32_t op = __shfl_xor_sync(0xffffffffu, bpos, o);
+            if (ob < best || (ob == best && oi < bidx)) {
+                best = ob;
+                bidx = oi;
+                bpos = op;
+            }
+        }
+        if (corr && lane == 0) corr[j] = bidx == kNoSlot ? -1 : (int32_t)bidx;
+        if (bidx != kNoSlot) {
+            const float4 m = map.pts[bpos];
+            const float rx = (float)(sx - (double)m.x), ry = (float)(sy - (double)m.y),
+                        rz = (float)(sz - (double)m.z);
+            const float qx = (float)(sx - c0), qy = (float)(sy - c1), qz = (float)(sz - c2);
+            const float e2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+            const float den = kk + e2;
+            const float w = kk / (den * den);  // rho'(e) / e of Eq. 12
+            float val = 0.f;
+            if (lane < 21) {
+                val = w * dot3(jac_col(ea, qx, qy, qz), jac_col(eb, qx, qy, qz));
+            } else if (lane < 27) {
+                val = w * dot3(jac_col(ea, qx, qy, qz), make_float3(rx, ry, rz));
+            } else if (lane == 27) {
+                val = 0.5f * e2 / den;  // rho(e)
+            } else if (lane == 28) {
+                val = 1.f;
+            }
+            acc += val;
+        }
+    }
+    s_acc[warp][lane] = acc;
+    __syncthreads();
+    if (threadIdx.x < kWarp) {
+        float tot = 0.f;
+#pragma unroll
+        for (int w = 0; w < kIcpWarps; ++w) tot += s_acc[w][threadIdx.x];
+        partial[(int64_t)blockIdx.x * kWarp + threadIdx.x] = tot;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 solve and pose update
+// ---------------------------------------------------------------------------
+// Exp of se(3) for xi = (rho, phi): R = I + A K + B K^2, V = I + B K + C K^2,
+// t = V rho, with K = [phi]x, A = sin(th)/th, B = (1 - cos th)/th^2,
+// C = (th - sin th)/th^3 (Taylor terms below th = 1e-4).
+__device__ void se3_exp(const double xi[6], double R[3][3], double te[3]) {
+    const double wx = xi[3], wy = xi[4], wz = xi[5];
+    const double th2 = wx * wx + wy * wy + wz * wz, th = sqrt(th2);
+    double A, B, Cc;
+    if (th < 1e-4) {
+        A = 1.0 - th2 / 6.0;
+        B = 0.5 - th2 / 24.0;
+        Cc = 1.0 / 6.0 - th2 / 120.0;
+    } else {
+        const double sh = sin(0.5 * th);
+        A = sin(th) / th;
+        B = 2.0 * sh * sh / th2;
+        Cc = (th - sin(th)) / (th2 * th);
+    }
+    const double K[3][3] = {{0.0, -wz, wy}, {wz, 0.0, -wx}, {-wy, wx, 0.0}};
+    double K2[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) K2[r][c] = K[r][0] * K[0][c] + K[r][1] * K[1][c] + K[r][2] * K[2][c];
+    double V[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            const double id = r == c ? 1.0 : 0.0;
+            R[r][c] = id + A * K[r][c] + B * K2[r][c];
+            V[r][c] = id + B * K[r][c] + Cc * K2[r][c];
+        }
+    for (int r = 0; r < 3; ++r) te[r] = V[r][0] * xi[0] + V[r][1] * xi[1] + V[r][2] * xi[2];
+}
+
+__global__ void __launch_bounds__(256)
+icp_solve_kernel(const float *__restrict__ partial, int nb, double *T, IcpState *st, float eps,
+                 vpgs_icp_report *rep, double *sys_out) {
+    __shared__ double s_part[8][kWarp];
+    __shared__ double s_sys[kWarp];
+    if (st->done) return;
+    const int t = threadIdx.x, comp = t & 31, chunk = t >> 5;
+    double a = 0.0;
+    for (int b = chunk; b < nb; b += 8) a += (double)partial[(int64_t)b * kWarp + comp];
+    s_part[chunk][comp] = a;
+    __syncthreads();
+    if (t < kWarp) {
+        double s = 0.0;
+        for (int c = 0; c < 8; ++c) s += s_part[c][t];
+        s_sys[t] = s;
+    }
+    __syncthreads();
+    if (t != 0) return;
+    if (sys_out) {  // linearisation only
+        for (int k = 0; k < kSys; ++k) sys_out[k] = s_sys[k];
+        return;
+    }
+    const uint32_t it = st->iter + 1;
+    st->iter = it;
+    const double count = s_sys[28];
+    int stop = 0;
+    double xi_norm = 0.0;
+    if (count < kMinCorr) {
+        stop = kStopFew;
+    } else {
+        double H[6][6], b[6], L[6][6] = {};
+        int k = 0;
+        for (int r = 0; r < 6; ++r)
+            for (int c = r; c < 6; ++c, ++k) H[r][c] = H[c][r] = s_sys[k];
+        for (int r = 0; r < 6; ++r) b[r] = s_sys[21 + r];
+        bool ok = true;
+        for (int j = 0; j < 6 && ok; ++j) {
+            double d = H[j][j];
+            for (int q = 0; q < j; ++q) d -= L[j][q] * L[j][q];
+            if (!(d > 0.0)) {
+                ok = false;
+                break;
+            }
+            L[j][j] = sqrt(d);
+            for (int i = j + 1; i < 6; ++i) {
+                double s = H[i][j];
+                for (int q = 0; q < j; ++q) s -= L[i][q] * L[j][q];
+                L[i][j] = s / L[j][j];
+            }
+        }
+        if (!ok) {
+            stop = kStopIndefinite;
+        } else {
+            double y[6], xi[6];
+            for (int i = 0; i < 6; ++i) {
+                double s = -b[i];
+                for (int q = 0; q < i; ++q) s -= L[i][q] * y[q];
+                y[i] = s / L[i][i];
+            }
+            for (int i = 5; i >= 0; --i) {
+                double s = y[i];
+                for (int q = i + 1; q < 6; ++q) s -= L[q][i] * xi[q];
+                xi[i] = s / L[i][i];
+            }
+            double R[3][3], te[3];
+            se3_exp(xi, R, te);
+            const double c[3] = {st->c[0], st->c[1], st->c[2]};
+            double Rt[3][3], tt[3];
+            for (int r = 0; r < 3; ++r) {
+                for (int q = 0; q < 3; ++q) Rt[r][q] = T[4 * r + q];
+                tt[r] = T[4 * r + 3] - c[r];
+            }
+            // T <- Tr(c) Exp(xi) Tr(-c) T
+            for (int r = 0; r < 3; ++r) {
+                for (int q = 0; q < 3; ++q) T[4 * r + q] = R[r][0] * Rt[0][q] + R[r][1] * Rt[1][q] + R[r][2] * Rt[2][q];
+                T[4 * r + 3] = R[r][0] * tt[0] + R[r][1] * tt[1] + R[r][2] * tt[2] + te[r] + c[r];
+            }
+            for (int i = 0; i < 6; ++i) xi_norm += xi[i] * xi[i];
+            xi_norm = sqrt(xi_norm);
+            if (xi_norm < (double)eps) stop = kStopEps;
+        }
+    }
+    if (stop) {
+        st->stop = (uint32_t)stop;
+        st->done = 1u;
+    }
+    vpgs_icp_report r;
+    r.status = (int32_t)st->status;
+    r.iterations = (int32_t)it;
+    r.n_source = (int32_t)st->n2;
+    r.n_corr = (int32_t)count;
+    r.stop = stop;
+    r.pad = 0;
+    r.cost = s_sys[27];
+    r.xi_norm = xi_norm;
+    *rep = r;
+}
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+int fill_grid(int64_t n) {
+    const int64_t g = std::min<int64_t>((n + 255) / 256, (int64_t)device_sm_count() * 8);
+    return (int)std::max<int64_t>(g, 1);
+}
+
+int corr_grid() {
+    static int g = 0;
+    if (g == 0) g = resident_grid((const void *)icp_corr_kernel, kIcpThreads, 0, kIcpMaxBlocks);
+    return g;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+bool pos_finite(float x) { return std::isfinite(x) && x > 0.f; }
+
+struct IcpWsView {
+    IcpLayout L;
+    IcpState *st;
+    float *partial;
+    VoxEntry *tab1, *tab2;
+    uint32_t *slot1, *slot2, *idx1, *idx2;
+    unsigned long long *look;
+};
+
+IcpWsView carve_icp(void *ws, int64_t n) {
+    IcpWsView w;
+    w.L = icp_layout(n);
+    char *b = static_cast<char *>(ws);
+    w.st = reinterpret_cast<IcpState *>(b + w.L.off_state);
+    w.partial = reinterpret_cast<float *>(b + w.L.off_partial);
+    w.tab1 = reinterpret_cast<VoxEntry *>(b + w.L.off_tab1);
+    w.tab2 = reinterpret_cast<VoxEntry *>(b + w.L.off_tab2);
+    w.slot1 = reinterpret_cast<uint32_t *>(b + w.L.off_slot1);
+    w.slot2 = reinterpret_cast<uint32_t *>(b + w.L.off_slot2);
+    w.idx1 = reinterpret_cast<uint32_t *>(b + w.L.off_idx1);
+    w.idx2 = reinterpret_cast<uint32_t *>(b + w.L.off_idx2);
+    w.look = reinterpret_cast<unsigned long long *>(b + w.L.off_look);
+    return w;
+}
+
+cudaError_t launch_prepare(const IcpWsView &w, const double *T, const MapHeader *hdr, vpgs_icp_report *rep,
+                           cudaStream_t s) {
+    const int64_t n = std::max<int64_t>(w.L.cap, (int64_t)w.L.n_look);
+    VPGS_LAUNCH("icp_prepare", s,
+                icp_prepare_kernel<<<fill_grid(n), 256, 0, s>>>(w.tab1, w.tab2, w.L.cap, w.look,
+                                                                (int64_t)w.L.n_look, w.st, T, hdr, rep));
+    return cudaGetLastError();
+}
+
+// Two first-point passes; the kept original indices go to out[0 .. *count).
+cudaError_t launch_downsample(const IcpWsView &w, const float *scan, int64_t n, float v1, float v2, uint32_t *out,
+                              uint32_t *count, cudaStream_t s) {
+    const uint32_t mask = w.L.cap - 1;
+    const size_t half = w.L.n_look / 2;
+    VPGS_LAUNCH("icp_ds_insert", s,
+                ds_insert_kernel<<<fill_grid(n), 256, 0, s>>>(scan, nullptr, n, nullptr, v1, w.tab1, mask, w.slot1,
+                                                              &w.st->status));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_scan("icp_ds_compact", DsFlagLoad{w.tab1, w.slot1}, DsKeepStore{nullptr, w.idx1}, n, nullptr,
+                    &w.st->ticket[0], w.look, &w.st->n1, &w.st->status, s);
+    if (e != cudaSuccess) return e;
+    VPGS_LAUNCH("icp_ds_insert", s,
+                ds_insert_kernel<<<fill_grid(n), 256, 0, s>>>(scan, w.idx1, n, &w.st->n1, v2, w.tab2, mask, w.slot2,
+                                                              &w.st->status));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_scan("icp_ds_compact", DsFlagLoad{w.tab2, w.slot2}, DsKeepStore{w.idx1, out}, n, &w.st->n1,
+                       &w.st->ticket[1], w.look + half, count, &w.st->status, s);
+}
+
+bool map_args_ok(const void *map, size_t map_bytes, int64_t n_map, float voxel) {
+    if (!map || !aligned16(map) || n_map < 0 || n_map > (int64_t(1) << 30) || !pos_finite(voxel)) return false;
+    return map_bytes >= map_layout(n_map).total;
+}
+
+MapView map_view(const void *map, int64_t n_map, float voxel) {
+    const MapLayout L = map_layout(n_map);
+    const char *b = static_cast<const char *>(map);
+    MapView m;
+    m.hdr = reinterpret_cast<const MapHeader *>(b);
+    m.tab = reinterpret_cast<const VoxEntry *>(b + L.off_tab);
+    m.pts = reinterpret_cast<const float4 *>(b + L.off_pts);
+    m.mask = L.cap - 1;
+    m.n = n_map;
+    m.voxel = voxel;
+    return m;
+}
+
+}  // namespace
+}  // namespace vpgs
+
+using namespace vpgs;
+
+extern "C" {
+
+size_t vpgs_icp_map_bytes(int64_t n_points) {
+    if (n_points < 0 || n_points > (int64_t(1) << 30)) return 0;
+    return map_layout(n_points).total;
+}
+
+vpgs_status vpgs_icp_build_map(void *map, size_t map_bytes, const float *points, int64_t n_points, float voxel,
+                               vpgs_stream stream) {
+    if (!map_args_ok(map, map_bytes, n_points, voxel)) return VPGS_ERR_INVALID_ARG;
+    if (n_points > 0 && !points) return VPGS_ERR_INVALID_ARG;
+    const MapLayout L = map_layout(n_points);
+    char *b = static_cast<char *>(map);
+    MapHeader *hdr = reinterpret_cast<MapHeader *>(b);
+    VoxEntry *tab = reinterpret_cast<VoxEntry *>(b + L.off_tab);
+    float4 *pts = reinterpret_cast<float4 *>(b + L.off_pts);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(b + L.off_slot);
+    unsigned long long *look = reinterpret_cast<unsigned long long *>(b + L.off_look);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t nc = std::max<int64_t>(L.cap, (int64_t)L.n_look);
+    VPGS_LAUNCH("icp_map_clear", s,
+                map_clear_kernel<<<fill_grid(nc), 256, 0, s>>>(hdr, tab, L.cap, look, (int64_t)L.n_look, n_points,
+                                                               voxel));
+    if (cudaGetLastError() != cudaSuccess) return VPGS_ERR_CUDA;
+    if (n_points == 0) return VPGS_OK;
+    VPGS_LAUNCH("icp_map_insert", s,
+                map_insert_kernel<<<fill_grid(n_points), 256, 0, s>>>(points, n_points, voxel, tab, L.cap - 1, slot,
+                                                                      hdr));
+    if (cudaGetLastError() != cudaSuccess) return VPGS_ERR_CUDA;
+    if (launch_scan("icp_map_offsets", MapCountLoad{tab}, MapStartStore{tab}, (int64_t)L.cap, nullptr, &hdr->ticket,
+                    look, &hdr->total, &hdr->status, s) != cudaSuccess)
+        return VPGS_ERR_CUDA;
+    VPGS_LAUNCH("icp_map_scatter", s,
+                map_scatter_kernel<<<fill_grid(n_points), 256, 0, s>>>(points, n_points, slot, tab, pts));
+    return cudaGetLastError() == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
+}
+
+vpgs_status vpgs_icp_map_query(const void *map, vpgs_icp_map_info *info, vpgs_stream stream) {
+    if (!map || !info) return VPGS_ERR_INVALID_ARG;
+    MapHeader h;
+    if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return VPGS_ERR_CUDA;
+    if (cudaMemcpy(&h, map, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return VPGS_ERR_CUDA;
+    if (h.magic != kMapMagic) return VPGS_ERR_INVALID_ARG;
+    info->n_points = h.n;
+    info->n_voxels = (int32_t)h.n_voxels;
+    info->capacity = (int32_t)h.cap;
+    info->status = (int32_t)h.status;
+    info->voxel = h.voxel;
+    return VPGS_OK;
+}
+
+size_t vpgs_icp_workspace_bytes(int64_t n_scan) {
+    if (n_scan < 0 || n_scan > (int64_t(1) << 30)) return 0;
+    return icp_layout(n_scan).total;
+}
+
+vpgs_status vpgs_icp_downsample(void *ws, size_t ws_bytes, const float *scan, int64_t n_scan, float voxel_1,
+                                float voxel_2, int32_t *idx_out, int32_t *n_out, vpgs_stream stream) {
+    if (!ws || !aligned16(ws) || !idx_out || !n_out || n_scan < 0 || (n_scan > 0 && !scan)) return VPGS_ERR_INVALID_ARG;
+    if (!pos_finite(voxel_1) || !pos_finite(voxel_2)) return VPGS_ERR_INVALID_ARG;
+    const size_t need = vpgs_icp_workspace_bytes(n_scan);
+    if (need == 0 || ws_bytes < need) return VPGS_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const IcpWsView w = carve_icp(ws, n_scan);
+    if (launch_prepare(w, nullptr, nullptr, nullptr, s) != cudaSuccess) return VPGS_ERR_CUDA;
+    if (n_scan == 0) return cudaMemsetAsync(n_out, 0, sizeof(int32_t), s) == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
+    return launch_downsample(w, scan, n_scan, voxel_1, voxel_2, reinterpret_cast<uint32_t *>(idx_out),
+                             reinterpret_cast<uint32_t *>(n_out), s) == cudaSuccess
+               ? VPGS_OK
+               : VPGS_ERR_CUDA;
+}
+
+vpgs_status vpgs_icp_linearize(void *ws, size_t ws_bytes, const void *map, size_t map_bytes, int64_t n_map,
+                               float map_voxel, const float *src, int64_t n_src, const double *T,
+                               const double *centre, float tau, float sigma, double *system, int32_t *corr,
+                               vpgs_stream stream) {
+    if (!ws || !aligned16(ws) || !T || !centre || !system || n_src < 0 || (n_src > 0 && !src))
+        return VPGS_ERR_INVALID_ARG;
+    if (!map_args_ok(map, map_bytes, n_map, map_voxel)) return VPGS_ERR_INVALID_ARG;
+    if (!pos_finite(tau) || tau > map_voxel || !pos_finite(sigma)) return VPGS_ERR_INVALID_ARG;
+    const size_t need = vpgs_icp_workspace_bytes(0);
+    if (ws_bytes < need) return VPGS_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const IcpWsView w = carve_icp(ws, 0);
+    const MapView mv = map_view(map, n_map, map_voxel);
+    if (launch_prepare(w, nullptr, mv.hdr, nullptr, s) != cudaSuccess) return VPGS_ERR_CUDA;
+    const int nb = corr_grid();
+    VPGS_LAUNCH("icp_corr", s,
+                icp_corr_kernel<<<nb, kIcpThreads, 0, s>>>(mv, src, nullptr, n_src, nullptr, T, centre, tau, sigma,
+                                                           w.partial, corr, w.st));
+    if (cudaGetLastError() != cudaSuccess) return VPGS_ERR_CUDA;
+    VPGS_LAUNCH("icp_solve", s,
+                icp_solve_kernel<<<1, 256, 0, s>>>(w.partial, nb, nullptr, w.st, 0.f, nullptr, system));
+    return cudaGetLastError() == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
+}
+
+vpgs_status vpgs_icp_register(void *ws, size_t ws_bytes, const void *map, size_t map_bytes, int64_t n_map,
+                              const float *scan, int64_t n_scan, const vpgs_icp_opts *opts, double *T,
+                              vpgs_icp_report *report, vpgs_stream stream) {
+    if (!ws || !aligned16(ws) || !opts || !T || !report || n_scan < 0 || (n_scan > 0 && !scan))
+        return VPGS_ERR_INVALID_ARG;
+    const vpgs_icp_opts o = *opts;
+    if (!map_args_ok(map, map_bytes, n_map, o.map_voxel)) return VPGS_ERR_INVALID_ARG;
+    if (!pos_finite(o.voxel_1) || !pos_finite(o.voxel_2) || !pos_finite(o.tau) || o.tau > o.map_voxel ||
+        !pos_finite(o.sigma) || !(std::isfinite(o.eps) && o.eps >= 0.f) || o.iterations < 1 ||
+        o.iterations > 1000)
+        return VPGS_ERR_INVALID_ARG;
+    const size_t need = vpgs_icp_workspace_bytes(n_scan);
+    if (need == 0 || ws_bytes < need) return VPGS_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const IcpWsView w = carve_icp(ws, n_scan);
+    const MapView mv = map_view(map, n_map, o.map_voxel);
+    if (launch_prepare(w, T, mv.hdr, report, s) != cudaSuccess) return VPGS_ERR_CUDA;
+    if (n_scan > 0 && launch_downsample(w, scan, n_scan, o.voxel_1, o.voxel_2, w.idx2, &w.st->n2, s) != cudaSuccess)
+        return VPGS_ERR_CUDA;
+    const int nb = corr_grid();
+    for (int it = 0; it < o.iterations; ++it) {
+        VPGS_LAUNCH("icp_corr", s,
+                    icp_corr_kernel<<<nb, kIcpThreads, 0, s>>>(mv, scan, w.idx2, n_scan, &w.st->n2, T, w.st->c,
+                                                               o.tau, o.sigma, w.partial, nullptr, w.st));
+        if (cudaGetLastError() != cudaSuccess) return VPGS_ERR_CUDA;
+        VPGS_LAUNCH("icp_solve", s,
+                    icp_solve_kernel<<<1, 256, 0, s>>>(w.partial, nb, T, w.st, o.eps, report, nullptr));
+        if (cudaGetLastError() != cudaSuccess) return VPGS_ERR_CUDA;
+    }
+    return VPGS_OK;
+}
+
+}  // extern "C"

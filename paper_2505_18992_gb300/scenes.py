@@ -383,3 +383,117 @@ def upstream_grads(rng_seed: int, n_views: int, height: int, width: int):
     g_d = rng.normal(size=(n_views, height, width)).astype(np.float32)
     g_a = rng.normal(size=(n_views, height, width)).astype(np.float32)
     return g_rgb, g_d, g_a
+
+
+@dataclass
+class LidarScene:
+    """A street map (Gaussian means, world frame) and one LiDAR scan of it."""
+    name: str
+    map_points: np.ndarray  # [M,3] float32, world
+    scan: np.ndarray        # [P,3] float32, sensor frame
+    T_true: np.ndarray      # [4,4] float64, sensor -> world
+    T_init: np.ndarray      # [4,4] float64, the perturbed initial guess T_{i-1} T_pred
+
+
+def _street_boxes(rng, x0, length):
+    """Axis-aligned boxes (lo, hi) of a street: building blocks with set-backs
+    and gaps behind y = +-10 m, poles at +-8.5 m and parked cars at +-6.3 m."""
+    lo, hi = [], []
+    for side in (-1.0, 1.0):
+        x = x0 - 10.0
+        while x < x0 + length + 10.0:
+            run = rng.uniform(12.0, 30.0)
+            gap = rng.uniform(1.0, 4.0) if rng.random() < 0.5 else 0.0
+            near = 10.0 + rng.uniform(0.0, 2.5)
+            h = rng.uniform(6.0, 15.0)
+            y0, y1 = (near, near + 8.0) if side > 0 else (-near - 8.0, -near)
+            lo.append((x, y0, 0.0))
+            hi.append((x + run, y1, h))
+            x += run + gap
+        for px in np.arange(x0 + rng.uniform(0.0, 10.0), x0 + length, rng.uniform(15.0, 25.0)):
+            lo.append((px - 0.15, side * 8.5 - 0.15, 0.0))
+            hi.append((px + 0.15, side * 8.5 + 0.15, 6.0))
+        for cx in np.sort(rng.uniform(x0, x0 + length, size=int(length // 12))):
+            lo.append((cx - 2.25, side * 6.3 - 0.9, 0.0))
+            hi.append((cx + 2.25, side * 6.3 + 0.9, 1.5))
+    return np.asarray(lo, np.float64), np.asarray(hi, np.float64)
+
+
+def _box_surface_points(rng, lo, hi, n):
+    """n points uniform over the 4 sides and the top of each box (area-weighted)."""
+    d = hi - lo
+    faces = []  # (origin, e1, e2, normal) with e1, e2 spanning the face
+    for b in range(len(lo)):
+        x, y, z = lo[b]
+        dx, dy, dz = d[b]
+        faces += [((x, y, z), (dx, 0, 0), (0, 0, dz), (0, -1, 0)), ((x, y + dy, z), (dx, 0, 0), (0, 0, dz), (0, 1, 0)),
+                  ((x, y, z), (0, dy, 0), (0, 0, dz), (-1, 0, 0)), ((x + dx, y, z), (0, dy, 0), (0, 0, dz), (1, 0, 0)),
+                  ((x, y, z + dz), (dx, 0, 0), (0, dy, 0), (0, 0, 1))]
+    o = np.asarray([f[0] for f in faces], np.float64)
+    e1 = np.asarray([f[1] for f in faces], np.float64)
+    e2 = np.asarray([f[2] for f in faces], np.float64)
+    nrm = np.asarray([f[3] for f in faces], np.float64)
+    area = np.linalg.norm(e1, axis=1) * np.linalg.norm(e2, axis=1)
+    which = rng.choice(len(faces), size=n, p=area / area.sum())
+    u, v = rng.uniform(size=(2, n, 1))
+    return o[which] + u * e1[which] + v * e2[which] + rng.normal(0, 0.02, size=(n, 1)) * nrm[which]
+
+
+def _ray_cast(orig, dirs, lo, hi, max_range):
+    """Nearest hit distance of rays from orig along unit dirs with the ground
+    z = 0 and the boxes (slab test); inf where nothing is hit within range."""
+    d = np.where(np.abs(dirs) < 1e-12, 1e-12, dirs)
+    inv = 1.0 / d
+    t = np.full(len(dirs), np.inf)
+    down = dirs[:, 2] < 0
+    t[down] = -orig[2] / dirs[down, 2]
+    for b in range(len(lo)):
+        t1 = (lo[b] - orig) * inv
+        t2 = (hi[b] - orig) * inv
+        tn = np.minimum(t1, t2).max(axis=1)
+        tf = np.maximum(t1, t2).min(axis=1)
+        hit = (tf >= tn) & (tn > 0)
+        t = np.where(hit & (tn < t), tn, t)
+    t[t > max_range] = np.inf
+    return t
+
+
+def street_lidar(n_map: int = 1_000_000, beams: int = 64, azimuths: int = 1800, length: float = 200.0,
+                 x0: float = 0.0, max_range: float = 80.0, seed: int = 7) -> LidarScene:
+    """A 64-beam LiDAR sweep (1800 azimuths, elevations -24.8..2 deg, 1 cm
+    range noise, 80 m range) from 1.73 m above the middle of a street
+    corridor [x0, x0+length] x [-20, 20] m, and a map of n_map Gaussian means
+    (2 cm normal jitter) on the same ground, buildings, poles and cars.  The
+    initial guess is off by N(0, 0.15 m) per axis and a 1 degree rotation
+    (KITTI-like driving stands in for the paper's outdoor sequences)."""
+    rng = np.random.default_rng(seed)
+    lo, hi = _street_boxes(rng, x0, length)
+    ground_area = (length + 20.0) * 40.0
+    ext = hi - lo
+    box_area = float(np.sum(2 * ext[:, 2] * (ext[:, 0] + ext[:, 1]) + ext[:, 0] * ext[:, 1]))
+    n_ground = int(round(n_map * ground_area / (ground_area + box_area)))
+    ground = np.c_[rng.uniform(x0 - 10.0, x0 + length + 10.0, n_ground), rng.uniform(-20.0, 20.0, n_ground),
+                   rng.normal(0, 0.02, n_ground)]
+    pts = np.concatenate([ground, _box_surface_points(rng, lo, hi, n_map - n_ground)])
+    map_points = pts[rng.permutation(n_map)].astype(np.float32)
+    yaw = math.radians(2.0)
+    T_true = np.eye(4)
+    T_true[:3, :3] = [[math.cos(yaw), -math.sin(yaw), 0.0], [math.sin(yaw), math.cos(yaw), 0.0], [0.0, 0.0, 1.0]]
+    T_true[:3, 3] = (x0 + 0.5 * length, 0.5, 1.73)
+    el = np.radians(np.linspace(-24.8, 2.0, beams))
+    az = np.linspace(-math.pi, math.pi, azimuths, endpoint=False)
+    E, A = np.meshgrid(el, az, indexing="ij")
+    d_local = np.stack([np.cos(E) * np.cos(A), np.cos(E) * np.sin(A), np.sin(E)], -1).reshape(-1, 3)
+    t = _ray_cast(T_true[:3, 3], d_local @ T_true[:3, :3].T, lo, hi, max_range)
+    ok = np.isfinite(t)
+    r = t[ok] + rng.normal(0, 0.01, int(ok.sum()))
+    scan = (d_local[ok] * r[:, None]).astype(np.float32)
+    axis = rng.normal(size=3)
+    axis /= np.linalg.norm(axis)
+    ang = math.radians(1.0)
+    K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
+    dR = np.eye(3) + math.sin(ang) * K + (1 - math.cos(ang)) * K @ K
+    T_init = T_true.copy()
+    T_init[:3, :3] = dR @ T_true[:3, :3]
+    T_init[:3, 3] += rng.normal(0, 0.15, 3)
+    return LidarScene("street_lidar", map_points, scan, T_true, T_init)

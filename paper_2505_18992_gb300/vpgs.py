@@ -74,6 +74,21 @@ class vpgs_loss_weights(ctypes.Structure):
     _fields_ = [("lambda_ssim", c_float), ("lambda_d", c_float), ("lambda_vol", c_float)]
 
 
+class vpgs_icp_opts(ctypes.Structure):
+    _fields_ = [("map_voxel", c_float), ("voxel_1", c_float), ("voxel_2", c_float), ("tau", c_float),
+                ("sigma", c_float), ("eps", c_float), ("iterations", c_int32), ("pad", c_int32)]
+
+
+class vpgs_icp_report(ctypes.Structure):
+    _fields_ = [("status", c_int32), ("iterations", c_int32), ("n_source", c_int32), ("n_corr", c_int32),
+                ("stop", c_int32), ("pad", c_int32), ("cost", c_double), ("xi_norm", c_double)]
+
+
+class vpgs_icp_map_info(ctypes.Structure):
+    _fields_ = [("n_points", c_int64), ("n_voxels", c_int32), ("capacity", c_int32), ("status", c_int32),
+                ("voxel", c_float)]
+
+
 _SIGS = {
     "vpgs_render_opts_default": (None, [POINTER(vpgs_render_opts)]),
     "vpgs_render_workspace_bytes": (c_size_t, [c_int64, c_int32, POINTER(vpgs_camera),
@@ -113,6 +128,16 @@ _SIGS = {
                                     c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "vpgs_adam_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, POINTER(c_float), c_int32,
                                  c_void_p]),
+    "vpgs_icp_map_bytes": (c_size_t, [c_int64]),
+    "vpgs_icp_build_map": (c_int32, [c_void_p, c_size_t, c_void_p, c_int64, c_float, c_void_p]),
+    "vpgs_icp_map_query": (c_int32, [c_void_p, POINTER(vpgs_icp_map_info), c_void_p]),
+    "vpgs_icp_workspace_bytes": (c_size_t, [c_int64]),
+    "vpgs_icp_downsample": (c_int32, [c_void_p, c_size_t, c_void_p, c_int64, c_float, c_float, c_void_p, c_void_p,
+                                      c_void_p]),
+    "vpgs_icp_linearize": (c_int32, [c_void_p, c_size_t, c_void_p, c_size_t, c_int64, c_float, c_void_p, c_int64,
+                                     c_void_p, c_void_p, c_float, c_float, c_void_p, c_void_p, c_void_p]),
+    "vpgs_icp_register": (c_int32, [c_void_p, c_size_t, c_void_p, c_size_t, c_int64, c_void_p, c_int64,
+                                    POINTER(vpgs_icp_opts), c_void_p, c_void_p, c_void_p]),
     "vpgs_launch_count": (c_int64, []),
     "vpgs_profile_enable": (None, [c_int32]),
     "vpgs_profile_collect": (c_int32, [c_char_p, c_size_t, POINTER(c_int64), POINTER(c_double),
@@ -179,6 +204,13 @@ vpgs_mapping_loss = _entry("vpgs_mapping_loss")
 vpgs_distill_workspace_bytes = _entry("vpgs_distill_workspace_bytes")
 vpgs_distill_loss = _entry("vpgs_distill_loss")
 vpgs_adam_step = _entry("vpgs_adam_step")
+vpgs_icp_map_bytes = _entry("vpgs_icp_map_bytes")
+vpgs_icp_build_map = _entry("vpgs_icp_build_map")
+vpgs_icp_map_query = _entry("vpgs_icp_map_query")
+vpgs_icp_workspace_bytes = _entry("vpgs_icp_workspace_bytes")
+vpgs_icp_downsample = _entry("vpgs_icp_downsample")
+vpgs_icp_linearize = _entry("vpgs_icp_linearize")
+vpgs_icp_register = _entry("vpgs_icp_register")
 vpgs_launch_count = _entry("vpgs_launch_count")
 vpgs_profile_enable = _entry("vpgs_profile_enable")
 vpgs_profile_collect = _entry("vpgs_profile_collect")
