@@ -11,16 +11,18 @@
 //   1. double downsampling: the lowest-index point of each voxel of edge v1
 //      (hash insert + atomicMin, then an order-keeping compaction by scan),
 //      then the same at v2 over the survivors;
-//   2. a fixed number of Gauss-Newton steps, two launches each.  One warp per
+//   2. a fixed number of Gauss-Newton steps, one launch each.  One warp per
 //      source point finds the nearest map point closer than tau among the 27
-//      voxels around it (lane k probes neighbour k; voxels whose box lies
-//      farther than tau are skipped before probing; the lanes then stride the
-//      candidates of the live voxels) and the warp's lanes accumulate the 29
-//      numbers of the Geman-McClure weighted normal equations (Eq. 11-12),
-//      lane l owning number l.  A one-block kernel adds the block partials in
-//      FP64, solves the 6x6 system by Cholesky and updates T in FP64.  A
-//      device flag ends the loop early, so the launch sequence is fixed and
-//      the call can be captured into a CUDA graph.
+//      voxels around it: lane k probes neighbour k (voxels whose box lies
+//      farther than tau are skipped before probing), the home voxel is
+//      scanned first, and every other voxel is skipped once its box lies
+//      farther than the warp's best distance so far.  The warp's lanes then
+//      accumulate the 29 numbers of the Geman-McClure weighted normal
+//      equations (Eq. 11-12), lane l owning number l.  The last block to
+//      finish adds the block partials in FP64, solves the 6x6 system by
+//      Cholesky and updates T in FP64.  A device flag ends the loop early, so
+//      the launch sequence is fixed and the call can be captured into a CUDA
+//      graph.
 // The linearisation is about the centre c = translation of T on entry:
 // J = [I, -[s - c]x], T <- Tr(c) Exp(xi) Tr(-c) T.  That gives the same
 // iterates as the left perturbation about the origin (Exp(Ad_X xi) =
@@ -60,7 +62,7 @@ struct MapHeader {
 static_assert(sizeof(MapHeader) == 64, "map header is 64 bytes");
 
 // map: a = first point, b = point count; downsampling: a = lowest index
-struct VoxEntry {
+struct __align__(16) VoxEntry {
     unsigned long long key;
     uint32_t a, b;
 };
@@ -69,7 +71,9 @@ struct IcpState {
     uint32_t ticket[2], n1, n2;
     uint32_t status, done, stop, iter;
     double c[3];
+    uint32_t blocks_done, pad;
 };
+static_assert(sizeof(IcpState) <= 128, "state fits its slot");
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -103,8 +107,8 @@ MapLayout map_layout(int64_t n) {
 
 struct IcpLayout {
     uint32_t cap;
-    size_t off_state, off_partial, off_tab1, off_tab2, off_slot1, off_slot2, off_idx1, off_idx2, off_look,
-        n_look, total;
+    size_t off_state, off_partial, off_tab1, off_tab2, off_slot1, off_slot2, off_idx1, off_idx2, off_src4,
+        off_look, n_look, total;
 };
 
 IcpLayout icp_layout(int64_t n) {
@@ -128,6 +132,8 @@ IcpLayout icp_layout(int64_t n) {
     o += idx_bytes;
     L.off_idx2 = o;
     o += idx_bytes;
+    L.off_src4 = o;
+    o += sizeof(float4) * (size_t)n;
     L.off_look = o;
     L.n_look = 2 * (size_t)std::max<int64_t>(scan_blocks(n), 1);
     o += sizeof(unsigned long long) * L.n_look;
@@ -186,15 +192,16 @@ VPGS_D uint32_t insert_voxel(VoxEntry *tab, uint32_t mask, unsigned long long ke
     return kNoSlot;
 }
 
-VPGS_D uint32_t find_voxel(const VoxEntry *tab, uint32_t mask, unsigned long long key) {
+// The entry of `key` (one 16-byte load per probe); count 0 when absent.
+VPGS_D VoxEntry find_entry(const VoxEntry *tab, uint32_t mask, unsigned long long key) {
     uint32_t h = hash_slot(key, mask);
     for (uint32_t p = 0; p <= mask; ++p) {
-        const unsigned long long cur = tab[h].key;
-        if (cur == key) return h;
-        if (cur == kEmptyKey) return kNoSlot;
+        const ulonglong2 e = *reinterpret_cast<const ulonglong2 *>(&tab[h]);
+        if (e.x == key) return VoxEntry{e.x, (uint32_t)e.y, (uint32_t)(e.y >> 32)};
+        if (e.x == kEmptyKey) break;
         h = (h + 1) & mask;
     }
-    return kNoSlot;
+    return VoxEntry{kEmptyKey, 0u, 0u};
 }
 
 // ---------------------------------------------------------------------------
@@ -333,11 +340,18 @@ struct DsFlagLoad {
         return (s != kNoSlot && tab[s].a == (uint32_t)j) ? 1u : 0u;
     }
 };
+// keeps index j: its original index goes to out[excl] and, when src4 is
+// given, its point to src4[excl]
 struct DsKeepStore {
     const uint32_t *idx_in;
     uint32_t *out;
+    const float *pts;
+    float4 *src4;
     VPGS_D void operator()(int64_t j, uint32_t excl, uint32_t v) const {
-        if (v) out[excl] = idx_in ? idx_in[j] : (uint32_t)j;
+        if (!v) return;
+        const uint32_t i = idx_in ? idx_in[j] : (uint32_t)j;
+        out[excl] = i;
+        if (src4) src4[excl] = make_float4(pts[3 * (int64_t)i], pts[3 * (int64_t)i + 1], pts[3 * (int64_t)i + 2], 0.f);
     }
 };
 
@@ -373,34 +387,206 @@ VPGS_D float slab_gap(int i, float v, float x) {
     return fmaxf(fmaxf(lo - x, x - (lo + v)), 0.f);
 }
 
-__global__ void __launch_bounds__(kIcpThreads)
-icp_corr_kernel(MapView map, const float *__restrict__ src, const uint32_t *__restrict__ idx, int64_t n_cap,
-                const uint32_t *n_dev, const double *__restrict__ T, const double *__restrict__ centre, float tau,
-                float sigma, float *__restrict__ partial, int32_t *__restrict__ corr, IcpState *st) {
-    __shared__ float s_acc[kIcpWarps][kWarp];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (st->done) return;  // uniform over the grid: set by an earlier solve
-    {
-        // a map buffer that was not built for this size and voxel is never
-        // indexed: its ranges could point anywhere
-        const MapHeader *h = map.hdr;
-        if (h->magic != kMapMagic || h->n != map.n || h->cap != map.mask + 1 ||
-            __float_as_uint(h->voxel) != __float_as_uint(map.voxel)) {
-            if (threadIdx.x < kWarp) partial[(int64_t)blockIdx.x * kWarp + threadIdx.x] = 0.f;
-            if (blockIdx.x == 0 && threadIdx.x == 0) set_status(&st->status, VPGS_ERR_INVALID_ARG);
-            return;
+// Exp of se(3) for xi = (rho, phi) in FP32, returned as the increment
+// dR = R - I = A K + B K^2 and te = V rho, V = I + B K + C K^2, with K = [phi]x,
+// A = sin(th)/th, B = (1 - cos th)/th^2, C = (th - sin th)/th^3.  Below
+// th = 0.1 the three come from their Taylor series in th^2 (the first omitted
+// terms are under 1e-10 relative).  Keeping R - I rather than R lets the FP64
+// pose update T + dR T lose nothing to the rounding of the identity.
+VPGS_D void se3_exp_delta(const float xi[6], float dR[3][3], float te[3]) {
+    const float wx = xi[3], wy = xi[4], wz = xi[5];
+    const float t2 = wx * wx + wy * wy + wz * wz;
+    float A, B, Cc;
+    if (t2 < 1e-2f) {
+        A = fmaf(t2, fmaf(t2, fmaf(t2, -1.f / 5040.f, 1.f / 120.f), -1.f / 6.f), 1.f);
+        B = fmaf(t2, fmaf(t2, fmaf(t2, -1.f / 40320.f, 1.f / 720.f), -1.f / 24.f), 0.5f);
+        Cc = fmaf(t2, fmaf(t2, fmaf(t2, -1.f / 362880.f, 1.f / 5040.f), -1.f / 120.f), 1.f / 6.f);
+    } else {
+        const float th = sqrtf(t2);
+        float sn, cs;
+        sincosf(0.5f * th, &sn, &cs);
+        const float inv = 1.f / th;
+        A = 2.f * sn * cs * inv;
+        B = 2.f * sn * sn * inv * inv;
+        Cc = (th - 2.f * sn * cs) * inv * inv * inv;
+    }
+    const float K[3][3] = {{0.f, -wz, wy}, {wz, 0.f, -wx}, {-wy, wx, 0.f}};
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        float acc = xi[r];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float k2 = K[r][0] * K[0][c] + K[r][1] * K[1][c] + K[r][2] * K[2][c];
+            dR[r][c] = A * K[r][c] + B * k2;
+            acc += (B * K[r][c] + Cc * k2) * xi[c];
+        }
+        te[r] = acc;
+    }
+}
+
+// One Gauss-Newton step from the summed system (one thread).  H xi = -b is
+// solved in FP32 after Jacobi scaling (H~ = S H S, S = diag(H)^-1/2) by an
+// LDL^T factorisation: H is taken as positive definite when every pivot of
+// H~ is > 0.  The solve's rounding only perturbs the step, not the fixed point
+// b = 0, whose sums come in at double-float precision.  Then
+// T <- Tr(c) Exp(xi) Tr(-c) T in FP64, the stop flags and the report.
+// T_in, c, iter, n2 and status were loaded into shared memory beforehand.
+__device__ void solve_step(const double *sys, const double *T_in, const double *c, uint32_t iter, uint32_t n2,
+                           uint32_t status, double *T, IcpState *st, float eps, vpgs_icp_report *rep) {
+    const uint32_t it = iter + 1;
+    st->iter = it;
+    const double count = sys[28];
+    int stop = 0;
+    float n2xi = 0.f;
+    if (count < kMinCorr) {
+        stop = kStopFew;
+    } else {
+        float H[6][6], L[6][6], D[6], inv[6], sc[6];
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const int d = i * 6 - i * (i - 1) / 2;  // index of H[i][i] in the upper triangle
+            const float hii = (float)sys[d];
+            ok = ok && hii > 0.f;
+            sc[i] = rsqrtf(hii);
+        }
+        int k = 0;
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+#pragma unroll
+            for (int q = r; q < 6; ++q, ++k) H[r][q] = H[q][r] = (float)sys[k] * sc[r] * sc[q];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            float d = H[j][j];
+#pragma unroll
+            for (int q = 0; q < j; ++q) d -= L[j][q] * L[j][q] * D[q];
+            ok = ok && d > 0.f;  // also false for NaN
+            D[j] = d;
+            inv[j] = __frcp_rn(d);
+#pragma unroll
+            for (int i = j + 1; i < 6; ++i) {
+                float s = H[i][j];
+#pragma unroll
+                for (int q = 0; q < j; ++q) s -= L[i][q] * L[j][q] * D[q];
+                L[i][j] = s * inv[j];
+            }
+        }
+        if (!ok) {
+            stop = kStopIndefinite;
+        } else {
+            float y[6], x[6], xi[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                float s = -(float)sys[21 + i] * sc[i];
+#pragma unroll
+                for (int q = 0; q < i; ++q) s -= L[i][q] * y[q];
+                y[i] = s;
+            }
+#pragma unroll
+            for (int i = 5; i >= 0; --i) {
+                float s = y[i] * inv[i];
+#pragma unroll
+                for (int q = i + 1; q < 6; ++q) s -= L[q][i] * x[q];
+                x[i] = s;
+            }
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                xi[i] = x[i] * sc[i];
+                n2xi = fmaf(xi[i], xi[i], n2xi);
+            }
+            float dR[3][3], te[3];
+            se3_exp_delta(xi, dR, te);
+            // T <- Tr(c) Exp(xi) Tr(-c) T = T + dR (T - c) + te in the rotation
+            // and translation parts
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    double a = T_in[4 * r + q];
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) a = fma((double)dR[r][m], T_in[4 * m + q], a);
+                    T[4 * r + q] = a;
+                }
+                double a = T_in[4 * r + 3] + (double)te[r];
+#pragma unroll
+                for (int m = 0; m < 3; ++m) a = fma((double)dR[r][m], T_in[4 * m + 3] - c[m], a);
+                T[4 * r + 3] = a;
+            }
+            if (n2xi < eps * eps) stop = kStopEps;
         }
     }
-    int64_t n = n_cap;
-    if (n_dev) n = min(n, (int64_t)*n_dev);
+    if (stop) {
+        st->stop = (uint32_t)stop;
+        st->done = 1u;
+    }
+    vpgs_icp_report r;
+    r.status = (int32_t)status;
+    r.iterations = (int32_t)it;
+    r.n_source = (int32_t)n2;
+    r.n_corr = (int32_t)count;
+    r.stop = stop;
+    r.pad = 0;
+    r.cost = sys[27];
+    r.xi_norm = (double)sqrtf(n2xi);
+    *rep = r;
+}
+
+VPGS_D float warp_min(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+// Source points of one step: float4 (x, y, z, -) when src4 is given, else
+// src [n,3] (optionally through idx).
+struct SrcView {
+    const float4 *src4;
+    const float *src;
+    const uint32_t *idx;
+};
+
+// One linearisation (and, unless sys_out is given, one step) of Eq. 11.
+// Blocks whose warps have no source point return at once; the others write
+// a partial sum each, and the last of them to finish adds the partials
+// (double-float) and solves.
+__global__ void __launch_bounds__(kIcpThreads)
+icp_step_kernel(MapView map, SrcView sv, int64_t n_cap, const uint32_t *n_dev, double *T,
+                const double *__restrict__ centre, float tau, float sigma, float eps, float *partial,
+                int32_t *__restrict__ corr, IcpState *st, vpgs_icp_report *rep, double *sys_out) {
+    __shared__ float s_acc[kIcpWarps][kWarp];
+    __shared__ float2 s_part[kIcpWarps][kWarp];
+    __shared__ double s_sys[kWarp], s_T[12], s_c[3];
+    __shared__ uint32_t s_meta[3];
+    __shared__ bool s_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // every load the prologue needs, issued together
+    const uint32_t done = st->done;
+    const uint32_t n_seen = n_dev ? *n_dev : 0u;
+    const MapHeader *h = map.hdr;
+    const uint32_t h_magic = h->magic, h_cap = h->cap, h_voxel = __float_as_uint(h->voxel);
+    const int64_t h_n = h->n;
     double t[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) t[k] = T[k];
     const double c0 = centre[0], c1 = centre[1], c2 = centre[2];
+    if (done) return;  // uniform over the grid: set by an earlier step
+    int64_t n = n_cap;
+    if (n_dev) n = min(n, (int64_t)n_seen);
+    const int64_t nb_active =
+        (int64_t)max(1ll, min((long long)gridDim.x, (long long)((n + kIcpWarps - 1) / kIcpWarps)));
+    if ((int64_t)blockIdx.x >= nb_active) return;
+    // a map buffer that was not built for this size and voxel is never
+    // indexed: its ranges could point anywhere
+    if (!(h_magic == kMapMagic && h_n == map.n && h_cap == map.mask + 1 && h_voxel == __float_as_uint(map.voxel))) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(&st->status, VPGS_ERR_INVALID_ARG);
+        n = 0;
+    }
     const float v = map.voxel;
     const float tau2 = __fmul_rn(tau, tau);
     const float kk = sigma / 3.f;
-    // lane k < 27 probes neighbour (k % 3 - 1, k / 3 % 3 - 1, k / 9 - 1)
+    // lane k < 27 probes neighbour (k % 3 - 1, k / 3 % 3 - 1, k / 9 - 1);
+    // lane 13 is the home voxel
+    constexpr int kHome = 13;
     const int ox = lane % 3 - 1, oy = (lane / 3) % 3 - 1, oz = lane / 9 - 1;
     // lane l < 21 owns H[a][b] (upper triangle, row-major), 21..26 b[l-21]
     int ea = 0, eb = 0;
@@ -417,8 +603,18 @@ icp_corr_kernel(MapView map, const float *__restrict__ src, const uint32_t *__re
     float acc = 0.f;
     const int64_t nw = (int64_t)gridDim.x * kIcpWarps;
     for (int64_t j = (int64_t)blockIdx.x * kIcpWarps + warp; j < n; j += nw) {
-        const int64_t i = idx ? (int64_t)idx[j] : j;
-        const double px = src[3 * i], py = src[3 * i + 1], pz = src[3 * i + 2];
+        double px, py, pz;
+        if (sv.src4) {
+            const float4 p = sv.src4[j];
+            px = p.x;
+            py = p.y;
+            pz = p.z;
+        } else {
+            const int64_t i = sv.idx ? (int64_t)sv.idx[j] : j;
+            px = sv.src[3 * i];
+            py = sv.src[3 * i + 1];
+            pz = sv.src[3 * i + 2];
+        }
         // s = T p, each coordinate ((T_r0 x + T_r1 y) + T_r2 z) + T_r3 in FP64
         const double sx = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(t[0], px), __dmul_rn(t[1], py)),
                                               __dmul_rn(t[2], pz)), t[3]);
@@ -429,61 +625,73 @@ icp_corr_kernel(MapView map, const float *__restrict__ src, const uint32_t *__re
         const float fx = __double2float_rn(sx), fy = __double2float_rn(sy), fz = __double2float_rn(sz);
         int cx = 0, cy = 0, cz = 0;
         const bool in_range = voxel_index(fx, v, cx) && voxel_index(fy, v, cy) && voxel_index(fz, v, cz);
+        // the slack covers the rounding of the box bounds (a few ulps of |s|)
+        const float slack = 1e-4f + 1e-6f * fmaxf(fmaxf(fabsf(fx), fabsf(fy)), fabsf(fz));
         uint32_t start = 0, cnt = 0;
+        float gap = 0.f;
         if (in_range && lane < 27) {
             const int nx = cx + ox, ny = cy + oy, nz = cz + oz;
             if (in_voxel_range(nx) && in_voxel_range(ny) && in_voxel_range(nz)) {
-                // skip voxels whose box is farther than tau; the slack covers
-                // the rounding of the box bounds (a few ulps of |s|)
                 const float gx = slab_gap(nx, v, fx), gy = slab_gap(ny, v, fy), gz = slab_gap(nz, v, fz);
-                const float slack = 1e-4f + 1e-6f * fmaxf(fmaxf(fabsf(fx), fabsf(fy)), fabsf(fz));
-                const float lim = tau + slack;
-                if (gx * gx + gy * gy + gz * gz <= lim * lim) {
-                    const uint32_t s = find_voxel(map.tab, map.mask, pack_voxel(nx, ny, nz));
-                    if (s != kNoSlot) {
-                        start = map.tab[s].a;
-                        cnt = map.tab[s].b;
-                    }
+                gap = sqrtf(gx * gx + gy * gy + gz * gz);
+                if (gap <= tau + slack) {  // voxels beyond tau are never probed
+                    const VoxEntry e = find_entry(map.tab, map.mask, pack_voxel(nx, ny, nz));
+                    start = e.a;
+                    cnt = e.b;
                 }
             }
         }
         uint32_t live = __ballot_sync(0xffffffffu, cnt > 0);
         float best = tau2;
-        uint32_t bidx = kNoSlot, bpos = 0;
+        uint32_t bidx = kNoSlot;
+        float bx = 0.f, by = 0.f, bz = 0.f;
+        float wbest = tau2;  // warp-uniform: the best squared distance so far
         while (live) {
-            const int k = __ffs(live) - 1;
-            live &= live - 1;
+            const int k = (live >> kHome) & 1u ? kHome : __ffs(live) - 1;
+            live &= ~(1u << k);
+            const float gk = __shfl_sync(0xffffffffu, gap, k);
+            if (gk > sqrtf(wbest) + slack) continue;  // every point of voxel k is farther than the best
             const uint32_t s0 = __shfl_sync(0xffffffffu, start, k), c = __shfl_sync(0xffffffffu, cnt, k);
-            for (uint32_t q = lane; q < c; q += kWarp) {
-                const float4 m = map.pts[s0 + q];
-                const float dx = __fsub_rn(m.x, fx), dy = __fsub_rn(m.y, fy), dz = __fsub_rn(m.z, fz);
-                const float d2 =
-                    __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-                const uint32_t mi = (uint32_t)__float_as_int(m.w);
-                if (d2 < best || (d2 == best && best < tau2 && mi < bidx)) {
-                    best = d2;
-                    bidx = mi;
-                    bpos = s0 + q;
+            for (uint32_t q = lane; q < c; q += 2 * kWarp) {
+                const bool two = q + kWarp < c;
+                const float4 m0 = map.pts[s0 + q];
+                const float4 m1 = two ? map.pts[s0 + q + kWarp] : m0;
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const float4 m = u ? m1 : m0;
+                    const float dx = __fsub_rn(m.x, fx), dy = __fsub_rn(m.y, fy), dz = __fsub_rn(m.z, fz);
+                    const float d2 =
+                        __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+                    const uint32_t mi = (uint32_t)__float_as_int(m.w);
+                    if ((u == 0 || two) && (d2 < best || (d2 == best && best < tau2 && mi < bidx))) {
+                        best = d2;
+                        bidx = mi;
+                        bx = m.x;
+                        by = m.y;
+                        bz = m.z;
+                    }
                 }
             }
+            wbest = warp_min(best);
         }
         // warp argmin of (d2, map index): every lane ends with the same winner
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const float ob = __shfl_xor_sync(0xffffffffu, best, o);
             const uint32_t oi = __shfl_xor_sync(0xffffffffu, bidx, o);
-            const uint32_t op = __shfl_xor_sync(0xffffffffu, bpos, o);
+            const float ox2 = __shfl_xor_sync(0xffffffffu, bx, o), oy2 = __shfl_xor_sync(0xffffffffu, by, o),
+                        oz2 = __shfl_xor_sync(0xffffffffu, bz, o);
             if (ob < best || (ob == best && oi < bidx)) {
                 best = ob;
                 bidx = oi;
-                bpos = op;
+                bx = ox2;
+                by = oy2;
+                bz = oz2;
             }
         }
         if (corr && lane == 0) corr[j] = bidx == kNoSlot ? -1 : (int32_t)bidx;
         if (bidx != kNoSlot) {
-            const float4 m = map.pts[bpos];
-            const float rx = (float)(sx - (double)m.x), ry = (float)(sy - (double)m.y),
-                        rz = (float)(sz - (double)m.z);
+            const float rx = (float)(sx - (double)bx), ry = (float)(sy - (double)by), rz = (float)(sz - (double)bz);
             const float qx = (float)(sx - c0), qy = (float)(sy - c1), qz = (float)(sz - c2);
             const float e2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
             const float den = kk + e2;
@@ -509,138 +717,45 @@ icp_corr_kernel(MapView map, const float *__restrict__ src, const uint32_t *__re
         for (int w = 0; w < kIcpWarps; ++w) tot += s_acc[w][threadIdx.x];
         partial[(int64_t)blockIdx.x * kWarp + threadIdx.x] = tot;
     }
-}
-
-// ---------------------------------------------------------------------------
-// FP64 solve and pose update
-// ---------------------------------------------------------------------------
-// Exp of se(3) for xi = (rho, phi): R = I + A K + B K^2, V = I + B K + C K^2,
-// t = V rho, with K = [phi]x, A = sin(th)/th, B = (1 - cos th)/th^2,
-// C = (th - sin th)/th^3 (Taylor terms below th = 1e-4).
-__device__ void se3_exp(const double xi[6], double R[3][3], double te[3]) {
-    const double wx = xi[3], wy = xi[4], wz = xi[5];
-    const double th2 = wx * wx + wy * wy + wz * wz, th = sqrt(th2);
-    double A, B, Cc;
-    if (th < 1e-4) {
-        A = 1.0 - th2 / 6.0;
-        B = 0.5 - th2 / 24.0;
-        Cc = 1.0 / 6.0 - th2 / 120.0;
-    } else {
-        const double sh = sin(0.5 * th);
-        A = sin(th) / th;
-        B = 2.0 * sh * sh / th2;
-        Cc = (th - sin(th)) / (th2 * th);
-    }
-    const double K[3][3] = {{0.0, -wz, wy}, {wz, 0.0, -wx}, {-wy, wx, 0.0}};
-    double K2[3][3];
-    for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) K2[r][c] = K[r][0] * K[0][c] + K[r][1] * K[1][c] + K[r][2] * K[2][c];
-    double V[3][3];
-    for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) {
-            const double id = r == c ? 1.0 : 0.0;
-            R[r][c] = id + A * K[r][c] + B * K2[r][c];
-            V[r][c] = id + B * K[r][c] + Cc * K2[r][c];
-        }
-    for (int r = 0; r < 3; ++r) te[r] = V[r][0] * xi[0] + V[r][1] * xi[1] + V[r][2] * xi[2];
-}
-
-__global__ void __launch_bounds__(256)
-icp_solve_kernel(const float *__restrict__ partial, int nb, double *T, IcpState *st, float eps,
-                 vpgs_icp_report *rep, double *sys_out) {
-    __shared__ double s_part[8][kWarp];
-    __shared__ double s_sys[kWarp];
-    if (st->done) return;
-    const int t = threadIdx.x, comp = t & 31, chunk = t >> 5;
-    double a = 0.0;
-    for (int b = chunk; b < nb; b += 8) a += (double)partial[(int64_t)b * kWarp + comp];
-    s_part[chunk][comp] = a;
+    __threadfence();
     __syncthreads();
-    if (t < kWarp) {
-        double s = 0.0;
-        for (int c = 0; c < 8; ++c) s += s_part[c][t];
-        s_sys[t] = s;
+    if (threadIdx.x == 0) s_last = atomicAdd(&st->blocks_done, 1u) == (uint32_t)(nb_active - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // the last block: what the solve reads, fetched while the partials are summed
+    if (threadIdx.x >= kWarp && threadIdx.x < kWarp + 12) s_T[threadIdx.x - kWarp] = t[threadIdx.x - kWarp];
+    if (threadIdx.x == kWarp + 12) {
+        s_c[0] = c0;
+        s_c[1] = c1;
+        s_c[2] = c2;
+        s_meta[0] = st->iter;
+        s_meta[1] = st->n2;
+        s_meta[2] = st->status;
+    }
+    {
+        // double-float sum of the partials in a fixed order
+        const int comp = threadIdx.x & 31, chunk = threadIdx.x >> 5;
+        df a = {0.f, 0.f};
+#pragma unroll 4
+        for (int64_t b = chunk; b < nb_active; b += kIcpWarps) a = df_add(a, df{__ldcg(&partial[b * kWarp + comp]), 0.f});
+        s_part[chunk][comp] = make_float2(a.hi, a.lo);
     }
     __syncthreads();
-    if (t != 0) return;
-    if (sys_out) {  // linearisation only
+    if (threadIdx.x < kWarp) {
+        df a = {0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < kIcpWarps; ++c) a = df_add(a, df{s_part[c][threadIdx.x].x, s_part[c][threadIdx.x].y});
+        s_sys[threadIdx.x] = (double)a.hi + (double)a.lo;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    st->blocks_done = 0u;  // ready for the next step
+    if (sys_out) {         // linearisation only
         for (int k = 0; k < kSys; ++k) sys_out[k] = s_sys[k];
         return;
     }
-    const uint32_t it = st->iter + 1;
-    st->iter = it;
-    const double count = s_sys[28];
-    int stop = 0;
-    double xi_norm = 0.0;
-    if (count < kMinCorr) {
-        stop = kStopFew;
-    } else {
-        double H[6][6], b[6], L[6][6] = {};
-        int k = 0;
-        for (int r = 0; r < 6; ++r)
-            for (int c = r; c < 6; ++c, ++k) H[r][c] = H[c][r] = s_sys[k];
-        for (int r = 0; r < 6; ++r) b[r] = s_sys[21 + r];
-        bool ok = true;
-        for (int j = 0; j < 6 && ok; ++j) {
-            double d = H[j][j];
-            for (int q = 0; q < j; ++q) d -= L[j][q] * L[j][q];
-            if (!(d > 0.0)) {
-                ok = false;
-                break;
-            }
-            L[j][j] = sqrt(d);
-            for (int i = j + 1; i < 6; ++i) {
-                double s = H[i][j];
-                for (int q = 0; q < j; ++q) s -= L[i][q] * L[j][q];
-                L[i][j] = s / L[j][j];
-            }
-        }
-        if (!ok) {
-            stop = kStopIndefinite;
-        } else {
-            double y[6], xi[6];
-            for (int i = 0; i < 6; ++i) {
-                double s = -b[i];
-                for (int q = 0; q < i; ++q) s -= L[i][q] * y[q];
-                y[i] = s / L[i][i];
-            }
-            for (int i = 5; i >= 0; --i) {
-                double s = y[i];
-                for (int q = i + 1; q < 6; ++q) s -= L[q][i] * xi[q];
-                xi[i] = s / L[i][i];
-            }
-            double R[3][3], te[3];
-            se3_exp(xi, R, te);
-            const double c[3] = {st->c[0], st->c[1], st->c[2]};
-            double Rt[3][3], tt[3];
-            for (int r = 0; r < 3; ++r) {
-                for (int q = 0; q < 3; ++q) Rt[r][q] = T[4 * r + q];
-                tt[r] = T[4 * r + 3] - c[r];
-            }
-            // T <- Tr(c) Exp(xi) Tr(-c) T
-            for (int r = 0; r < 3; ++r) {
-                for (int q = 0; q < 3; ++q) T[4 * r + q] = R[r][0] * Rt[0][q] + R[r][1] * Rt[1][q] + R[r][2] * Rt[2][q];
-                T[4 * r + 3] = R[r][0] * tt[0] + R[r][1] * tt[1] + R[r][2] * tt[2] + te[r] + c[r];
-            }
-            for (int i = 0; i < 6; ++i) xi_norm += xi[i] * xi[i];
-            xi_norm = sqrt(xi_norm);
-            if (xi_norm < (double)eps) stop = kStopEps;
-        }
-    }
-    if (stop) {
-        st->stop = (uint32_t)stop;
-        st->done = 1u;
-    }
-    vpgs_icp_report r;
-    r.status = (int32_t)st->status;
-    r.iterations = (int32_t)it;
-    r.n_source = (int32_t)st->n2;
-    r.n_corr = (int32_t)count;
-    r.stop = stop;
-    r.pad = 0;
-    r.cost = s_sys[27];
-    r.xi_norm = xi_norm;
-    *rep = r;
+    solve_step(s_sys, s_T, s_c, s_meta[0], s_meta[1], s_meta[2], T, st, eps, rep);
 }
 
 // ---------------------------------------------------------------------------
@@ -653,7 +768,7 @@ int fill_grid(int64_t n) {
 
 int corr_grid() {
     static int g = 0;
-    if (g == 0) g = resident_grid((const void *)icp_corr_kernel, kIcpThreads, 0, kIcpMaxBlocks);
+    if (g == 0) g = resident_grid((const void *)icp_step_kernel, kIcpThreads, 0, kIcpMaxBlocks);
     return g;
 }
 
@@ -666,6 +781,7 @@ struct IcpWsView {
     float *partial;
     VoxEntry *tab1, *tab2;
     uint32_t *slot1, *slot2, *idx1, *idx2;
+    float4 *src4;
     unsigned long long *look;
 };
 
@@ -681,6 +797,7 @@ IcpWsView carve_icp(void *ws, int64_t n) {
     w.slot2 = reinterpret_cast<uint32_t *>(b + w.L.off_slot2);
     w.idx1 = reinterpret_cast<uint32_t *>(b + w.L.off_idx1);
     w.idx2 = reinterpret_cast<uint32_t *>(b + w.L.off_idx2);
+    w.src4 = reinterpret_cast<float4 *>(b + w.L.off_src4);
     w.look = reinterpret_cast<unsigned long long *>(b + w.L.off_look);
     return w;
 }
@@ -694,9 +811,10 @@ cudaError_t launch_prepare(const IcpWsView &w, const double *T, const MapHeader 
     return cudaGetLastError();
 }
 
-// Two first-point passes; the kept original indices go to out[0 .. *count).
+// Two first-point passes; the kept original indices go to out[0 .. *count)
+// and, when src4 is given, the kept points to src4[0 .. *count).
 cudaError_t launch_downsample(const IcpWsView &w, const float *scan, int64_t n, float v1, float v2, uint32_t *out,
-                              uint32_t *count, cudaStream_t s) {
+                              float4 *src4, uint32_t *count, cudaStream_t s) {
     const uint32_t mask = w.L.cap - 1;
     const size_t half = w.L.n_look / 2;
     VPGS_LAUNCH("icp_ds_insert", s,
@@ -704,7 +822,7 @@ cudaError_t launch_downsample(const IcpWsView &w, const float *scan, int64_t n, 
                                                               &w.st->status));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = launch_scan("icp_ds_compact", DsFlagLoad{w.tab1, w.slot1}, DsKeepStore{nullptr, w.idx1}, n, nullptr,
+    e = launch_scan("icp_ds_compact", DsFlagLoad{w.tab1, w.slot1}, DsKeepStore{nullptr, w.idx1, scan, nullptr}, n, nullptr,
                     &w.st->ticket[0], w.look, &w.st->n1, &w.st->status, s);
     if (e != cudaSuccess) return e;
     VPGS_LAUNCH("icp_ds_insert", s,
@@ -712,7 +830,7 @@ cudaError_t launch_downsample(const IcpWsView &w, const float *scan, int64_t n, 
                                                               &w.st->status));
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_scan("icp_ds_compact", DsFlagLoad{w.tab2, w.slot2}, DsKeepStore{w.idx1, out}, n, &w.st->n1,
+    return launch_scan("icp_ds_compact", DsFlagLoad{w.tab2, w.slot2}, DsKeepStore{w.idx1, out, scan, src4}, n, &w.st->n1,
                        &w.st->ticket[1], w.look + half, count, &w.st->status, s);
 }
 
@@ -805,7 +923,7 @@ vpgs_status vpgs_icp_downsample(void *ws, size_t ws_bytes, const float *scan, in
     const IcpWsView w = carve_icp(ws, n_scan);
     if (launch_prepare(w, nullptr, nullptr, nullptr, s) != cudaSuccess) return VPGS_ERR_CUDA;
     if (n_scan == 0) return cudaMemsetAsync(n_out, 0, sizeof(int32_t), s) == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
-    return launch_downsample(w, scan, n_scan, voxel_1, voxel_2, reinterpret_cast<uint32_t *>(idx_out),
+    return launch_downsample(w, scan, n_scan, voxel_1, voxel_2, reinterpret_cast<uint32_t *>(idx_out), nullptr,
                              reinterpret_cast<uint32_t *>(n_out), s) == cudaSuccess
                ? VPGS_OK
                : VPGS_ERR_CUDA;
@@ -825,13 +943,10 @@ vpgs_status vpgs_icp_linearize(void *ws, size_t ws_bytes, const void *map, size_
     const IcpWsView w = carve_icp(ws, 0);
     const MapView mv = map_view(map, n_map, map_voxel);
     if (launch_prepare(w, nullptr, mv.hdr, nullptr, s) != cudaSuccess) return VPGS_ERR_CUDA;
-    const int nb = corr_grid();
-    VPGS_LAUNCH("icp_corr", s,
-                icp_corr_kernel<<<nb, kIcpThreads, 0, s>>>(mv, src, nullptr, n_src, nullptr, T, centre, tau, sigma,
-                                                           w.partial, corr, w.st));
-    if (cudaGetLastError() != cudaSuccess) return VPGS_ERR_CUDA;
-    VPGS_LAUNCH("icp_solve", s,
-                icp_solve_kernel<<<1, 256, 0, s>>>(w.partial, nb, nullptr, w.st, 0.f, nullptr, system));
+    VPGS_LAUNCH("icp_step", s,
+                icp_step_kernel<<<corr_grid(), kIcpThreads, 0, s>>>(mv, SrcView{nullptr, src, nullptr}, n_src, nullptr,
+                                                                    const_cast<double *>(T), centre, tau, sigma, 0.f,
+                                                                    w.partial, corr, w.st, nullptr, system));
     return cudaGetLastError() == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
 }
 
@@ -852,16 +967,15 @@ vpgs_status vpgs_icp_register(void *ws, size_t ws_bytes, const void *map, size_t
     const IcpWsView w = carve_icp(ws, n_scan);
     const MapView mv = map_view(map, n_map, o.map_voxel);
     if (launch_prepare(w, T, mv.hdr, report, s) != cudaSuccess) return VPGS_ERR_CUDA;
-    if (n_scan > 0 && launch_downsample(w, scan, n_scan, o.voxel_1, o.voxel_2, w.idx2, &w.st->n2, s) != cudaSuccess)
+    if (n_scan > 0 && launch_downsample(w, scan, n_scan, o.voxel_1, o.voxel_2, w.idx2, w.src4, &w.st->n2, s) != cudaSuccess)
         return VPGS_ERR_CUDA;
     const int nb = corr_grid();
     for (int it = 0; it < o.iterations; ++it) {
-        VPGS_LAUNCH("icp_corr", s,
-                    icp_corr_kernel<<<nb, kIcpThreads, 0, s>>>(mv, scan, w.idx2, n_scan, &w.st->n2, T, w.st->c,
-                                                               o.tau, o.sigma, w.partial, nullptr, w.st));
-        if (cudaGetLastError() != cudaSuccess) return VPGS_ERR_CUDA;
-        VPGS_LAUNCH("icp_solve", s,
-                    icp_solve_kernel<<<1, 256, 0, s>>>(w.partial, nb, T, w.st, o.eps, report, nullptr));
+        VPGS_LAUNCH("icp_step", s,
+                    icp_step_kernel<<<nb, kIcpThreads, 0, s>>>(mv, SrcView{w.src4, nullptr, nullptr}, n_scan,
+                                                               &w.st->n2, T, w.st->c,
+                                                               o.tau, o.sigma, o.eps, w.partial, nullptr, w.st,
+                                                               report, nullptr));
         if (cudaGetLastError() != cudaSuccess) return VPGS_ERR_CUDA;
     }
     return VPGS_OK;
