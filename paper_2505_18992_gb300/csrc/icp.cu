@@ -367,16 +367,11 @@ struct MapView {
     float voxel;
 };
 
-// column a of the 3x6 Jacobian [I, -[q]x] of s' = c + Exp(xi)(s - c) at xi = 0
+// column a of the 3x6 Jacobian [I, -[q]x] of s' = c + Exp(xi)(s - c) at xi = 0:
+// e_a for a < 3, e_(a-3) x q for a >= 3 (selected without branches)
 VPGS_D float3 jac_col(int a, float qx, float qy, float qz) {
-    switch (a) {
-        case 0: return make_float3(1.f, 0.f, 0.f);
-        case 1: return make_float3(0.f, 1.f, 0.f);
-        case 2: return make_float3(0.f, 0.f, 1.f);
-        case 3: return make_float3(0.f, -qz, qy);
-        case 4: return make_float3(qz, 0.f, -qx);
-        default: return make_float3(-qy, qx, 0.f);
-    }
+    const float u0 = a == 0, u1 = a == 1, u2 = a == 2, r0 = a == 3, r1 = a == 4, r2 = a == 5;
+    return make_float3(u0 + r1 * qz - r2 * qy, u1 + r2 * qx - r0 * qz, u2 + r0 * qy - r1 * qx);
 }
 
 VPGS_D float dot3(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
@@ -431,7 +426,7 @@ VPGS_D void se3_exp_delta(const float xi[6], float dR[3][3], float te[3]) {
 // b = 0, whose sums come in at double-float precision.  Then
 // T <- Tr(c) Exp(xi) Tr(-c) T in FP64, the stop flags and the report.
 // T_in, c, iter, n2 and status were loaded into shared memory beforehand.
-__device__ void solve_step(const double *sys, const double *T_in, const double *c, uint32_t iter, uint32_t n2,
+VPGS_D void solve_step(const double *sys, const double *T_in, const double *c, uint32_t iter, uint32_t n2,
                            uint32_t status, double *T, IcpState *st, float eps, vpgs_icp_report *rep) {
     const uint32_t it = iter + 1;
     st->iter = it;
@@ -641,39 +636,63 @@ icp_step_kernel(MapView map, SrcView sv, int64_t n_cap, const uint32_t *n_dev, d
                 }
             }
         }
-        uint32_t live = __ballot_sync(0xffffffffu, cnt > 0);
         float best = tau2;
         uint32_t bidx = kNoSlot;
         float bx = 0.f, by = 0.f, bz = 0.f;
-        float wbest = tau2;  // warp-uniform: the best squared distance so far
-        while (live) {
-            const int k = (live >> kHome) & 1u ? kHome : __ffs(live) - 1;
-            live &= ~(1u << k);
-            const float gk = __shfl_sync(0xffffffffu, gap, k);
-            if (gk > sqrtf(wbest) + slack) continue;  // every point of voxel k is farther than the best
-            const uint32_t s0 = __shfl_sync(0xffffffffu, start, k), c = __shfl_sync(0xffffffffu, cnt, k);
-            for (uint32_t q = lane; q < c; q += 2 * kWarp) {
-                const bool two = q + kWarp < c;
-                const float4 m0 = map.pts[s0 + q];
-                const float4 m1 = two ? map.pts[s0 + q + kWarp] : m0;
+        // Scans the points of the voxels of the lanes in `set` as one list:
+        // lane l takes list entries l, l + 32, ...; the voxel of an entry is
+        // found by a binary search over the lanes' inclusive count prefix.
+        auto scan_set = [&](uint32_t set) {
+            const uint32_t ck = (set >> lane) & 1u ? cnt : 0u;
+            uint32_t incl = ck;
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const float4 m = u ? m1 : m0;
-                    const float dx = __fsub_rn(m.x, fx), dy = __fsub_rn(m.y, fy), dz = __fsub_rn(m.z, fz);
+            for (int o = 1; o < kWarp; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const uint32_t excl = incl - ck;
+            const uint32_t total = __shfl_sync(0xffffffffu, incl, kWarp - 1);
+            constexpr int kU = 4;  // list entries per lane in flight
+            for (uint32_t q0 = 0; q0 < total; q0 += kU * kWarp) {
+                float4 m[kU];
+                bool ok[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const uint32_t q = q0 + u * kWarp + lane;
+                    int k = 0;
+#pragma unroll
+                    for (int b = 16; b > 0; b >>= 1)
+                        if (__shfl_sync(0xffffffffu, incl, k + b - 1) <= q) k += b;
+                    const uint32_t s0 = __shfl_sync(0xffffffffu, start, k);
+                    const uint32_t e0 = __shfl_sync(0xffffffffu, excl, k);
+                    ok[u] = q < total;
+                    m[u] = ok[u] ? map.pts[s0 + (q - e0)] : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const float dx = __fsub_rn(m[u].x, fx), dy = __fsub_rn(m[u].y, fy), dz = __fsub_rn(m[u].z, fz);
                     const float d2 =
                         __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-                    const uint32_t mi = (uint32_t)__float_as_int(m.w);
-                    if ((u == 0 || two) && (d2 < best || (d2 == best && best < tau2 && mi < bidx))) {
+                    const uint32_t mi = (uint32_t)__float_as_int(m[u].w);
+                    if (ok[u] && (d2 < best || (d2 == best && best < tau2 && mi < bidx))) {
                         best = d2;
                         bidx = mi;
-                        bx = m.x;
-                        by = m.y;
-                        bz = m.z;
+                        bx = m[u].x;
+                        by = m[u].y;
+                        bz = m[u].z;
                     }
                 }
             }
-            wbest = warp_min(best);
-        }
+        };
+        // round 1: the home voxel (every live voxel when it is empty);
+        // round 2: the other live voxels not farther than the best so far.
+        // A voxel left out of both lies farther than the final best.
+        const uint32_t live = __ballot_sync(0xffffffffu, cnt > 0);
+        const uint32_t first = (live >> kHome) & 1u ? (1u << kHome) : live;
+        if (first) scan_set(first);
+        const float lim = sqrtf(warp_min(best)) + slack;
+        const uint32_t second = __ballot_sync(0xffffffffu, cnt > 0 && gap <= lim) & ~first;
+        if (second) scan_set(second);
         // warp argmin of (d2, map index): every lane ends with the same winner
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -734,11 +753,20 @@ icp_step_kernel(MapView map, SrcView sv, int64_t n_cap, const uint32_t *n_dev, d
         s_meta[2] = st->status;
     }
     {
-        // double-float sum of the partials in a fixed order
+        // double-float sum of the partials in a fixed order; up to 16 loads
+        // per thread are in flight at once
         const int comp = threadIdx.x & 31, chunk = threadIdx.x >> 5;
         df a = {0.f, 0.f};
-#pragma unroll 4
-        for (int64_t b = chunk; b < nb_active; b += kIcpWarps) a = df_add(a, df{__ldcg(&partial[b * kWarp + comp]), 0.f});
+        for (int64_t b0 = chunk; b0 < nb_active; b0 += 16 * kIcpWarps) {
+            float x[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int64_t b = b0 + (int64_t)u * kIcpWarps;
+                x[u] = b < nb_active ? __ldcg(&partial[b * kWarp + comp]) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) a = df_add(a, df{x[u], 0.f});
+        }
         s_part[chunk][comp] = make_float2(a.hi, a.lo);
     }
     __syncthreads();
