@@ -49,6 +49,8 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip tracking/e2e/profile passes")
     p.add_argument("--no-rows", action="store_true", help="keep the kernel profile, skip the other rows")
+    p.add_argument("--row", choices=("tracking", "decode", "batched_keyframes", "fusion", "mapping", "icp"),
+                   help="run only this secondary row and print it (a profiling entry point, not a bench line)")
     p.add_argument("--persistent", type=int, default=0, help="persistent CTAs per SM (0 = per tile)")
     p.add_argument("--tile", default="8x16", help="tile shape WxH")
     p.add_argument("--scale", type=float, default=1.0,
@@ -857,9 +859,33 @@ def tracking_rows(sc, g, dev):
             "trans_err_m_eager": err_eager, "trans_err_m_graph": err_graph}
 
 
+def run_row(a):
+    """One secondary row alone, on cuda:0, printed as JSON."""
+    import torch
+
+    from paper_2505_18992_gb300 import scenes
+    from paper_2505_18992_gb300 import vpgs as C
+    from paper_2505_18992_gb300.build import build
+    build()
+    C.lib()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    if a.row in ("tracking", "mapping"):
+        sc = scenes.indoor_room()
+        g = [torch.tensor(x, device=dev).contiguous() for x in sc.arrays()]
+        out = tracking_rows(sc, g, dev) if a.row == "tracking" else mapping_rows(sc, g, dev)
+    else:
+        out = {"decode": decode_rows, "batched_keyframes": batched_rows, "fusion": fusion_rows,
+               "icp": icp_rows}[a.row](dev)
+    out.pop("_T", None)
+    print(json.dumps({"row": a.row, **out}), flush=True)
+
+
 def main():
     a = _args()
-    if a.impl == "reference":
+    if a.row:
+        run_row(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)
