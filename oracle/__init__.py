@@ -12,3 +12,4 @@ from .pose import pose_step, se3_exp  # noqa: F401,E402
 from .loss import mapping_loss, ssim_map, gaussian_window  # noqa: F401,E402
 from .fusion import distill_loss, adam_step  # noqa: F401,E402
 from .icp import icp as voxel_icp, voxel_downsample  # noqa: F401,E402
+from .anchors import spawn as spawn_anchors, accumulate_stats, prune as prune_anchors, grow as grow_anchors  # noqa: F401,E402
