@@ -468,6 +468,104 @@ vpgs_status vpgs_icp_register(void *ws, size_t ws_bytes, const void *map, size_t
                               vpgs_icp_report *report, vpgs_stream stream);
 
 /* ---------------------------------------------------------------------- */
+/* Submap expansion and anchor maintenance (Sec. III-A, "Voxel-Based      */
+/* Submap Expansion and Activation")                                       */
+/* ---------------------------------------------------------------------- */
+
+/* Per-anchor statistics, one caller-owned device buffer of
+ * vpgs_anchor_stats_bytes(A) bytes, 16-byte aligned.  With a4 = 4 A rounded
+ * up to 16: float g_sum[A] at 0, float o_sum[A] at a4, uint32 g_cnt[A] at
+ * 2 a4, uint32 visits[A] at 3 a4, uint32 status at 4 a4.  0 if A < 0 or > 2^30. */
+size_t vpgs_anchor_stats_bytes(int64_t n_anchors);
+
+/* Zeroes the statistics (one memset on `stream`). */
+vpgs_status vpgs_anchor_stats_reset(void *stats, size_t stats_bytes, int64_t n_anchors, vpgs_stream stream);
+
+/* Adds one training step: for every decoded neural Gaussian i < n (n =
+ * min(n_cap, *n_dev), or n_cap when n_dev is NULL) of anchor a =
+ * src_index[i] / k (the decoder's src_index, ascending):
+ *   o_sum[a] += opacities[i];
+ *   when visible[i] != 0 (or visible is NULL): g_sum[a] += |grad_means[i]|
+ *     (the gradient of the 3D mean, [n,3]) and g_cnt[a] += 1;
+ *   visits[a] += 1 for the first i of each anchor's run.
+ * The paper averages the neural Gaussians' gradients per voxel and
+ * accumulates their opacities; the gradient of the 3D mean and the
+ * visibility (a non-empty tile cover) are readings.  FP32 atomics: the sums'
+ * rounding order is not fixed.  An index outside [0, A k) sets the status. */
+vpgs_status vpgs_anchor_stats_accumulate(void *stats, size_t stats_bytes, int64_t n_anchors, int32_t k,
+                                         const int32_t *src_index, const int32_t *n_dev, int64_t n_cap,
+                                         const float *grad_means, const float *opacities, const int32_t *visible,
+                                         vpgs_stream stream);
+
+typedef struct {
+    float tau_g;      /* grow from anchors whose average gradient g_sum / g_cnt exceeds tau_g */
+    float tau_o;      /* prune anchors with visits > 0 and o_sum < tau_o * visits */
+    float grow_voxel; /* voxel edge of the grown anchors (> 0) */
+    int32_t pad;
+} vpgs_anchor_update_opts;
+
+/* Workspace bytes of vpgs_anchor_update (0 if a size is negative or > 2^30). */
+size_t vpgs_anchor_update_workspace_bytes(int64_t n_anchors, int64_t n_gaussians);
+
+/* Pruning and growth from the statistics.
+ *   keep_index [A] int32 device: the kept anchors, ascending, count in *n_keep
+ *   (device int32).  An anchor is dropped when visits > 0 and
+ *   o_sum < tau_o * visits (float32).
+ *   grown [n_cap,3] float32 device: voxel centres (edge grow_voxel) of the
+ *   decoded Gaussian means means[i] ([n_cap,3], the decoder's output) of
+ *   anchors with g_cnt > 0 and g_sum > tau_g * g_cnt, whose voxel holds no
+ *   anchor; each voxel once, in the order of its first i; count in *n_grown.
+ *   anchor_map: vpgs_icp_build_map of the A anchor centres with voxel =
+ *   grow_voxel (it answers "does a voxel hold an anchor").
+ * Four launches; the status word of the workspace (vpgs_anchor_status kind 1)
+ * reports non-finite means or a map that does not match. */
+vpgs_status vpgs_anchor_update(void *ws, size_t ws_bytes, const void *stats, size_t stats_bytes, int64_t n_anchors,
+                               int32_t k, const int32_t *src_index, const int32_t *n_dev, int64_t n_cap,
+                               const float *means, const void *anchor_map, size_t anchor_map_bytes,
+                               const vpgs_anchor_update_opts *opts, int32_t *keep_index, int32_t *n_keep,
+                               float *grown, int32_t *n_grown, vpgs_stream stream);
+
+typedef struct {
+    float tau_alpha;   /* spawn where the rendered alpha is below this ... */
+    float delta_depth; /* ... or where |rendered depth - input depth| exceeds this (>= 0) */
+    float voxel;       /* voxel edge of the new anchors (> 0) */
+    float rho;         /* no new anchor within rho of a Gaussian mean; 0 < rho <= map voxel */
+    int32_t max_samples; /* M_k, pixels back-projected per keyframe, 1..2^26 */
+    int32_t pad;
+} vpgs_spawn_opts;
+
+/* Workspace bytes of vpgs_spawn_anchors (0 if the sizes are invalid). */
+size_t vpgs_spawn_workspace_bytes(int32_t width, int32_t height, int32_t max_samples);
+
+/* New anchors of one keyframe (Sec. III-A): the pixels with input depth > 0
+ * whose rendered alpha < tau_alpha or |rendered depth - input depth| >
+ * delta_depth (float32); of their C (raster order) the rank r is kept iff
+ * floor((r+1) M / C) > floor(r M / C) (all when C <= M), as sample
+ * floor((r+1) M / C) - 1; each sample is back-projected through the pixel
+ * centre with its input depth and the world-to-camera pose T_cw (device
+ * double[16]) in FP64, rounded to float32; its voxel (edge voxel) becomes an
+ * anchor at the voxel centre if it is the voxel's first sample and no point of
+ * gauss_map (vpgs_icp_build_map of the Gaussian means, n_map points, edge
+ * map_voxel >= rho) lies closer than rho to that centre.
+ *   alpha, depth, depth_in [H,W] float32 device (W, H from cam).
+ *   anchors_out [max_samples,3] float32 device: the new anchors in sample order;
+ *   *n_out (device int32) their number.  samples_out [max_samples,3] and
+ *   *n_samples (device) receive the back-projected samples; either may be NULL.
+ * The paper samples M_k points at random; the even spread is a reading.  Five
+ * launches; status: vpgs_anchor_status kind 2. */
+vpgs_status vpgs_spawn_anchors(void *ws, size_t ws_bytes, const float *alpha, const float *depth,
+                               const float *depth_in, const vpgs_camera *cam, const double *T_cw,
+                               const void *gauss_map, size_t map_bytes, int64_t n_map, float map_voxel,
+                               const vpgs_spawn_opts *opts, float *anchors_out, int32_t *n_out, float *samples_out,
+                               int32_t *n_samples, vpgs_stream stream);
+
+/* Synchronises `stream` and reads a device status word: kind 0 = statistics
+ * buffer (n_anchors gives its layout), 1 = vpgs_anchor_update workspace,
+ * 2 = vpgs_spawn_anchors workspace. */
+vpgs_status vpgs_anchor_status(const void *ws_or_stats, int32_t kind, int64_t n_anchors, int32_t *status_out,
+                               vpgs_stream stream);
+
+/* ---------------------------------------------------------------------- */
 /* Diagnostics (host)                                                      */
 /* ---------------------------------------------------------------------- */
 

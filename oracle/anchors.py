@@ -18,7 +18,8 @@ trivial anchors can be removed.
 
 Readings where the paper is silent:
   * mask(p) = D_in(p) > 0 and (alpha(p) < tau_alpha or |D(p) - D_in(p)| >
-    delta_d): only pixels with an input depth can be back-projected.
+    delta_d), decided in float32: only pixels with an input depth can be
+    back-projected.
   * Sampling: of the C masked pixels in raster order, the pixel of rank r is
     kept iff floor((r+1) M / C) > floor(r M / C) (M evenly spaced ranks; all
     of them when C <= M); sample j is the one with floor((r+1) M / C) = j + 1.
@@ -36,7 +37,7 @@ Readings where the paper is silent:
     that are visible (rendered with a non-empty tile cover), g_cnt += 1 for
     each of them, o_sum += o_i over all its decoded Gaussians, visits += 1
     when it decoded any Gaussian.  The gradient is that of the 3D mean.
-  * Growth: anchors with g_cnt > 0 and g_sum / g_cnt > tau_g; candidates are
+  * Growth: anchors with g_cnt > 0 and g_sum > tau_g g_cnt; candidates are
     the voxels (edge v_g) of those anchors' decoded Gaussian means that hold
     no existing anchor, as voxel centres, in the order of the first decoded
     Gaussian that reaches them.
@@ -57,11 +58,11 @@ from .icp import voxel_keys
 
 
 def spawn_mask(alpha, depth, depth_in, tau_alpha, delta_d):
-    """Boolean [H,W] mask of the pixels that may spawn anchors."""
-    a = np.asarray(alpha, np.float64)
-    d = np.asarray(depth, np.float64)
-    di = np.asarray(depth_in, np.float64)
-    return (di > 0) & ((a < tau_alpha) | (np.abs(d - di) > delta_d))
+    """Boolean [H,W] mask of the pixels that may spawn anchors (decided in float32)."""
+    a = np.asarray(alpha, np.float32)
+    d = np.asarray(depth, np.float32)
+    di = np.asarray(depth_in, np.float32)
+    return (di > 0) & ((a < np.float32(tau_alpha)) | (np.abs(d - di) > np.float32(delta_d)))
 
 
 def sample_ranks(count: int, budget: int) -> np.ndarray:

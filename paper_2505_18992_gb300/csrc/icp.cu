@@ -38,34 +38,17 @@
 #include "internal.h"
 #include "prims.cuh"
 #include "profiler.h"
+#include "voxhash.cuh"
 
 namespace vpgs {
 namespace {
 
-constexpr unsigned long long kEmptyKey = ~0ull;
-constexpr uint32_t kNoSlot = 0xffffffffu;
-constexpr int kVoxRange = 1 << 20;  // |voxel index| < 2^20 on every axis
-constexpr uint32_t kMapMagic = 0x49435056u;
 constexpr int kIcpThreads = 256;
 constexpr int kIcpWarps = kIcpThreads / kWarp;
 constexpr int kSys = 29;  // H upper triangle (21), b (6), sum rho, count
 constexpr int kIcpMaxBlocks = 4096;
 constexpr int kMinCorr = 6;
 constexpr int kStopEps = 1, kStopFew = 2, kStopIndefinite = 3;
-
-struct MapHeader {
-    uint32_t magic, cap, n_voxels, status;
-    int64_t n;
-    float voxel;
-    uint32_t ticket, total, pad[7];
-};
-static_assert(sizeof(MapHeader) == 64, "map header is 64 bytes");
-
-// map: a = first point, b = point count; downsampling: a = lowest index
-struct __align__(16) VoxEntry {
-    unsigned long long key;
-    uint32_t a, b;
-};
 
 struct IcpState {
     uint32_t ticket[2], n1, n2;
@@ -74,36 +57,6 @@ struct IcpState {
     uint32_t blocks_done, pad;
 };
 static_assert(sizeof(IcpState) <= 128, "state fits its slot");
-
-inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-inline uint32_t table_cap(int64_t n) {
-    uint64_t c = 1024;
-    while (c < 2 * (uint64_t)n) c <<= 1;
-    return (uint32_t)c;
-}
-
-struct MapLayout {
-    uint32_t cap;
-    size_t off_tab, off_pts, off_slot, off_look, n_look, total;
-};
-
-MapLayout map_layout(int64_t n) {
-    MapLayout L;
-    L.cap = table_cap(n);
-    size_t o = sizeof(MapHeader);
-    L.off_tab = o;
-    o += sizeof(VoxEntry) * (size_t)L.cap;
-    L.off_pts = o;
-    o += sizeof(float4) * (size_t)n;
-    L.off_slot = o;
-    o = align_up(o + sizeof(uint32_t) * (size_t)n, 16);
-    L.off_look = o;
-    L.n_look = (size_t)std::max<int64_t>(scan_blocks(L.cap), 1);
-    o += sizeof(unsigned long long) * L.n_look;
-    L.total = o;
-    return L;
-}
 
 struct IcpLayout {
     uint32_t cap;
@@ -139,69 +92,6 @@ IcpLayout icp_layout(int64_t n) {
     o += sizeof(unsigned long long) * L.n_look;
     L.total = o;
     return L;
-}
-
-// ---------------------------------------------------------------------------
-// voxels and the hash
-// ---------------------------------------------------------------------------
-VPGS_D bool voxel_index(float x, float v, int &i) {
-    const float q = floorf(__fdiv_rn(x, v));
-    if (!(q >= -(float)kVoxRange && q < (float)kVoxRange)) return false;  // also rejects NaN
-    i = (int)q;
-    return true;
-}
-
-VPGS_D bool in_voxel_range(int i) { return i >= -kVoxRange && i < kVoxRange; }
-
-VPGS_D unsigned long long pack_voxel(int ix, int iy, int iz) {
-    return ((unsigned long long)(uint32_t)(ix + kVoxRange) << 42) |
-           ((unsigned long long)(uint32_t)(iy + kVoxRange) << 21) | (unsigned long long)(uint32_t)(iz + kVoxRange);
-}
-
-// the splitmix64 finaliser (Steele, Lea and Flood, "Fast splittable
-// pseudorandom number generators", 2014) as the hash of a packed voxel
-VPGS_D uint32_t hash_slot(unsigned long long k, uint32_t mask) {
-    k ^= k >> 30;
-    k *= 0xbf58476d1ce4e5b9ull;
-    k ^= k >> 27;
-    k *= 0x94d049bb133111ebull;
-    k ^= k >> 31;
-    return (uint32_t)k & mask;
-}
-
-// Slot of `key`, claimed if absent; kNoSlot if the table is full (it never
-// is: the capacity is at least twice the number of keys).
-VPGS_D uint32_t insert_voxel(VoxEntry *tab, uint32_t mask, unsigned long long key, bool &fresh) {
-    uint32_t h = hash_slot(key, mask);
-    for (uint32_t p = 0; p <= mask; ++p) {
-        const unsigned long long cur = __ldcg(&tab[h].key);
-        if (cur == key) {
-            fresh = false;
-            return h;
-        }
-        if (cur == kEmptyKey) {
-            const unsigned long long prev = atomicCAS(&tab[h].key, kEmptyKey, key);
-            if (prev == kEmptyKey || prev == key) {
-                fresh = prev == kEmptyKey;
-                return h;
-            }
-        }
-        h = (h + 1) & mask;
-    }
-    fresh = false;
-    return kNoSlot;
-}
-
-// The entry of `key` (one 16-byte load per probe); count 0 when absent.
-VPGS_D VoxEntry find_entry(const VoxEntry *tab, uint32_t mask, unsigned long long key) {
-    uint32_t h = hash_slot(key, mask);
-    for (uint32_t p = 0; p <= mask; ++p) {
-        const ulonglong2 e = *reinterpret_cast<const ulonglong2 *>(&tab[h]);
-        if (e.x == key) return VoxEntry{e.x, (uint32_t)e.y, (uint32_t)(e.y >> 32)};
-        if (e.x == kEmptyKey) break;
-        h = (h + 1) & mask;
-    }
-    return VoxEntry{kEmptyKey, 0u, 0u};
 }
 
 // ---------------------------------------------------------------------------
@@ -358,15 +248,6 @@ struct DsKeepStore {
 // ---------------------------------------------------------------------------
 // correspondences + normal equations
 // ---------------------------------------------------------------------------
-struct MapView {
-    const MapHeader *hdr;
-    const VoxEntry *tab;
-    const float4 *pts;
-    uint32_t mask;
-    int64_t n;
-    float voxel;
-};
-
 // column a of the 3x6 Jacobian [I, -[q]x] of s' = c + Exp(xi)(s - c) at xi = 0:
 // e_a for a < 3, e_(a-3) x q for a >= 3 (selected without branches)
 VPGS_D float3 jac_col(int a, float qx, float qy, float qz) {
@@ -375,12 +256,6 @@ VPGS_D float3 jac_col(int a, float qx, float qy, float qz) {
 }
 
 VPGS_D float dot3(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
-
-// distance from x to the slab [lo, lo + v) of voxel i (0 inside)
-VPGS_D float slab_gap(int i, float v, float x) {
-    const float lo = (float)i * v;
-    return fmaxf(fmaxf(lo - x, x - (lo + v)), 0.f);
-}
 
 // Exp of se(3) for xi = (rho, phi) in FP32, returned as the increment
 // dR = R - I = A K + B K^2 and te = V rho, V = I + B K + C K^2, with K = [phi]x,
@@ -800,9 +675,6 @@ int corr_grid() {
     return g;
 }
 
-bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
-bool pos_finite(float x) { return std::isfinite(x) && x > 0.f; }
-
 struct IcpWsView {
     IcpLayout L;
     IcpState *st;
@@ -860,24 +732,6 @@ cudaError_t launch_downsample(const IcpWsView &w, const float *scan, int64_t n, 
     if (e != cudaSuccess) return e;
     return launch_scan("icp_ds_compact", DsFlagLoad{w.tab2, w.slot2}, DsKeepStore{w.idx1, out, scan, src4}, n, &w.st->n1,
                        &w.st->ticket[1], w.look + half, count, &w.st->status, s);
-}
-
-bool map_args_ok(const void *map, size_t map_bytes, int64_t n_map, float voxel) {
-    if (!map || !aligned16(map) || n_map < 0 || n_map > (int64_t(1) << 30) || !pos_finite(voxel)) return false;
-    return map_bytes >= map_layout(n_map).total;
-}
-
-MapView map_view(const void *map, int64_t n_map, float voxel) {
-    const MapLayout L = map_layout(n_map);
-    const char *b = static_cast<const char *>(map);
-    MapView m;
-    m.hdr = reinterpret_cast<const MapHeader *>(b);
-    m.tab = reinterpret_cast<const VoxEntry *>(b + L.off_tab);
-    m.pts = reinterpret_cast<const float4 *>(b + L.off_pts);
-    m.mask = L.cap - 1;
-    m.n = n_map;
-    m.voxel = voxel;
-    return m;
 }
 
 }  // namespace

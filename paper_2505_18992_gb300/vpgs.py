@@ -89,6 +89,15 @@ class vpgs_icp_map_info(ctypes.Structure):
                 ("voxel", c_float)]
 
 
+class vpgs_anchor_update_opts(ctypes.Structure):
+    _fields_ = [("tau_g", c_float), ("tau_o", c_float), ("grow_voxel", c_float), ("pad", c_int32)]
+
+
+class vpgs_spawn_opts(ctypes.Structure):
+    _fields_ = [("tau_alpha", c_float), ("delta_depth", c_float), ("voxel", c_float), ("rho", c_float),
+                ("max_samples", c_int32), ("pad", c_int32)]
+
+
 _SIGS = {
     "vpgs_render_opts_default": (None, [POINTER(vpgs_render_opts)]),
     "vpgs_render_workspace_bytes": (c_size_t, [c_int64, c_int32, POINTER(vpgs_camera),
@@ -138,6 +147,19 @@ _SIGS = {
                                      c_void_p, c_void_p, c_float, c_float, c_void_p, c_void_p, c_void_p]),
     "vpgs_icp_register": (c_int32, [c_void_p, c_size_t, c_void_p, c_size_t, c_int64, c_void_p, c_int64,
                                     POINTER(vpgs_icp_opts), c_void_p, c_void_p, c_void_p]),
+    "vpgs_anchor_stats_bytes": (c_size_t, [c_int64]),
+    "vpgs_anchor_stats_reset": (c_int32, [c_void_p, c_size_t, c_int64, c_void_p]),
+    "vpgs_anchor_stats_accumulate": (c_int32, [c_void_p, c_size_t, c_int64, c_int32, c_void_p, c_void_p, c_int64,
+                                               c_void_p, c_void_p, c_void_p, c_void_p]),
+    "vpgs_anchor_update_workspace_bytes": (c_size_t, [c_int64, c_int64]),
+    "vpgs_anchor_update": (c_int32, [c_void_p, c_size_t, c_void_p, c_size_t, c_int64, c_int32, c_void_p, c_void_p,
+                                     c_int64, c_void_p, c_void_p, c_size_t, POINTER(vpgs_anchor_update_opts),
+                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "vpgs_spawn_workspace_bytes": (c_size_t, [c_int32, c_int32, c_int32]),
+    "vpgs_spawn_anchors": (c_int32, [c_void_p, c_size_t, c_void_p, c_void_p, c_void_p, POINTER(vpgs_camera),
+                                     c_void_p, c_void_p, c_size_t, c_int64, c_float, POINTER(vpgs_spawn_opts),
+                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "vpgs_anchor_status": (c_int32, [c_void_p, c_int32, c_int64, POINTER(c_int32), c_void_p]),
     "vpgs_launch_count": (c_int64, []),
     "vpgs_profile_enable": (None, [c_int32]),
     "vpgs_profile_collect": (c_int32, [c_char_p, c_size_t, POINTER(c_int64), POINTER(c_double),
@@ -211,6 +233,14 @@ vpgs_icp_workspace_bytes = _entry("vpgs_icp_workspace_bytes")
 vpgs_icp_downsample = _entry("vpgs_icp_downsample")
 vpgs_icp_linearize = _entry("vpgs_icp_linearize")
 vpgs_icp_register = _entry("vpgs_icp_register")
+vpgs_anchor_stats_bytes = _entry("vpgs_anchor_stats_bytes")
+vpgs_anchor_stats_reset = _entry("vpgs_anchor_stats_reset")
+vpgs_anchor_stats_accumulate = _entry("vpgs_anchor_stats_accumulate")
+vpgs_anchor_update_workspace_bytes = _entry("vpgs_anchor_update_workspace_bytes")
+vpgs_anchor_update = _entry("vpgs_anchor_update")
+vpgs_spawn_workspace_bytes = _entry("vpgs_spawn_workspace_bytes")
+vpgs_spawn_anchors = _entry("vpgs_spawn_anchors")
+vpgs_anchor_status = _entry("vpgs_anchor_status")
 vpgs_launch_count = _entry("vpgs_launch_count")
 vpgs_profile_enable = _entry("vpgs_profile_enable")
 vpgs_profile_collect = _entry("vpgs_profile_collect")

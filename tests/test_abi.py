@@ -49,7 +49,8 @@ def test_struct_layouts_match_the_header(lib, tmp_path):
         pytest.skip("no C compiler")
     structs = ["vpgs_camera", "vpgs_render_opts", "vpgs_gaussians", "vpgs_gaussian_buffers",
                "vpgs_images", "vpgs_render_stats", "vpgs_anchors", "vpgs_mlp", "vpgs_decode_opts",
-               "vpgs_icp_opts", "vpgs_icp_report", "vpgs_icp_map_info"]
+               "vpgs_icp_opts", "vpgs_icp_report", "vpgs_icp_map_info", "vpgs_anchor_update_opts",
+               "vpgs_spawn_opts"]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "vpgs.h"', "int main(void) {"]
     for st in structs:
         lines.append(f'printf("{st} %zu\\n", sizeof({st}));')

@@ -1,0 +1,158 @@
+"""GPU parity of submap expansion and anchor maintenance (Sec. III-A) against the FP64 oracle.
+
+Tolerances.  Counts, kept indices, spawning samples, new-anchor and grown
+positions are bit-exact: both sides take every decision in float32 and
+back-project in FP64 with the same operation order.  The statistics' sums are
+FP32 atomics against FP64: within 1e-5 of the value (plus 1e-6 absolute).
+Threshold decisions on those sums are compared on the GPU's own sums, with
+thresholds chosen at least 1e-5 (relative) away from every anchor's value.
+"""
+import importlib
+
+import numpy as np
+import pytest
+import torch
+
+from tests.helpers import dev
+
+A = importlib.import_module("oracle.anchors")
+pytestmark = pytest.mark.gpu
+
+
+def _decode_like(rng, n_anchors, k, frac=0.6):
+    """Anchors, and an (anchor, m)-ordered subset of their k slots with means, grads, opacities, visibility."""
+    anchors = (np.floor(rng.uniform(-20, 20, size=(n_anchors, 3)) / 0.2) * 0.2 + 0.1).astype(np.float32)
+    src = np.sort(rng.choice(n_anchors * k, size=int(frac * n_anchors * k), replace=False)).astype(np.int32)
+    means = (anchors[src // k] + rng.uniform(-0.3, 0.3, size=(len(src), 3))).astype(np.float32)
+    grads = (rng.normal(size=(len(src), 3)) * rng.uniform(0, 2e-3, size=(len(src), 1))).astype(np.float32)
+    opac = rng.uniform(0, 1, len(src)).astype(np.float32)
+    vis = rng.integers(0, 4, len(src)).astype(np.int32)
+    return anchors, src, means, grads, opac, vis
+
+
+def _stats_np(st):
+    arr = st.arrays()
+    return {k: v.cpu().numpy() for k, v in arr.items()}
+
+
+def test_statistics_match_the_oracle():
+    from paper_2505_18992_gb300.anchors import AnchorStats
+    rng = np.random.default_rng(0)
+    n_anchors, k = 20_011, 10
+    anchors, src, means, grads, opac, vis = _decode_like(rng, n_anchors, k)
+    st = AnchorStats(n_anchors)
+    ref = A.new_stats(n_anchors)
+    for step in range(3):
+        sl = slice(0, len(src) - 997 * step)  # a ragged prefix each step
+        st.accumulate(k, dev(src[sl], torch.int32), dev(grads[sl]), dev(opac[sl]), dev(vis[sl], torch.int32))
+        A.accumulate_stats(ref, src[sl], k, grads[sl], opac[sl], vis[sl])
+    got = _stats_np(st)
+    assert st.status() == 0
+    assert np.array_equal(got["g_cnt"], ref["g_cnt"]) and np.array_equal(got["visits"], ref["visits"])
+    assert np.all(np.abs(got["g_sum"] - ref["g_sum"]) <= 1e-5 * np.abs(ref["g_sum"]) + 1e-6)
+    assert np.all(np.abs(got["o_sum"] - ref["o_sum"]) <= 1e-5 * np.abs(ref["o_sum"]) + 1e-6)
+
+
+def test_statistics_edge_cases():
+    from paper_2505_18992_gb300.anchors import AnchorStats
+    st = AnchorStats(10)
+    st.accumulate(4, torch.zeros(0, dtype=torch.int32, device="cuda"), torch.zeros((0, 3), device="cuda"),
+                  torch.zeros(0, device="cuda"))
+    assert st.status() == 0 and int(st.arrays()["visits"].sum()) == 0
+    bad = torch.tensor([3, 41], dtype=torch.int32, device="cuda")  # 41 // 4 = 10 is out of range
+    st.accumulate(4, bad, torch.ones((2, 3), device="cuda"), torch.ones(2, device="cuda"))
+    assert st.status() == 1
+    assert int(st.arrays()["visits"][0]) == 1
+
+
+def _pick_threshold(values, lo, hi):
+    """A threshold in [lo, hi] at least 1e-5 (relative) away from every value, so
+    that the float32 comparison (rounding ~1e-7) decides as the FP64 one."""
+    for t in np.linspace(lo, hi, 5000):
+        if np.all(np.abs(values - t) > 1e-5 * t):
+            return float(t)
+    raise AssertionError("no clean threshold")
+
+
+@pytest.mark.parametrize("n_anchors", [1, 3_001, 20_011])
+def test_prune_and_grow_match_the_oracle(n_anchors):
+    from paper_2505_18992_gb300.anchors import AnchorStats, AnchorUpdate
+    from paper_2505_18992_gb300.icp import VoxelMap
+    rng = np.random.default_rng(n_anchors)
+    k = 10
+    anchors, src, means, grads, opac, vis = _decode_like(rng, n_anchors, k)
+    st = AnchorStats(n_anchors)
+    for _ in range(2):
+        st.accumulate(k, dev(src, torch.int32), dev(grads), dev(opac), dev(vis, torch.int32))
+    s = {key: v.astype(np.float64) for key, v in _stats_np(st).items()}
+    s["g_cnt"] = s["g_cnt"].astype(np.int64)
+    s["visits"] = s["visits"].astype(np.int64)
+    avg = s["g_sum"][s["g_cnt"] > 0] / s["g_cnt"][s["g_cnt"] > 0]
+    per_visit = s["o_sum"][s["visits"] > 0] / s["visits"][s["visits"] > 0]
+    if len(avg) > 10:
+        tau_g = _pick_threshold(avg, np.percentile(avg, 50), np.percentile(avg, 90))
+    else:  # one anchor: make it hot
+        tau_g = 0.5 * float(avg.min()) if len(avg) else 1.0
+    tau_o = _pick_threshold(per_visit, 0.5, 2.0) if len(per_visit) > 10 else 0.1
+    grow_voxel = 0.2
+    amap = VoxelMap(dev(anchors), grow_voxel)
+    up = AnchorUpdate(n_anchors, len(src), tau_g, tau_o, grow_voxel)
+    up(st, k, dev(src, torch.int32), dev(means), amap)
+    keep, grown = (x.cpu().numpy() for x in up.results())
+    assert up.status() == 0
+    assert np.array_equal(keep, A.prune(s, tau_o))
+    want = A.grow(s, src, k, means, tau_g, grow_voxel, anchors)
+    assert len(want) > 0 or n_anchors == 1
+    assert np.array_equal(grown, want)
+
+
+def _spawn_inputs(rng, W, H, frac_low=0.15):
+    from oracle.pose import se3_exp
+    alpha = np.where(rng.uniform(size=(H, W)) < frac_low, rng.uniform(0, 0.4, (H, W)), rng.uniform(0.6, 1, (H, W)))
+    depth_in = rng.uniform(0.5, 8.0, (H, W)).astype(np.float32)
+    depth_in[rng.uniform(size=(H, W)) < 0.05] = 0.0  # holes in the input depth
+    depth = depth_in + np.where(rng.uniform(size=(H, W)) < 0.05, rng.uniform(-1, 1, (H, W)), 0).astype(np.float32)
+    T = se3_exp(np.r_[rng.normal(scale=0.5, size=3), rng.normal(scale=0.3, size=3)])
+    return alpha.astype(np.float32), depth.astype(np.float32), depth_in, T
+
+
+@pytest.mark.parametrize("W,H,budget", [(97, 61, 100_000), (320, 240, 3_001), (1200, 680, 50_000)])
+def test_spawning_matches_the_oracle(W, H, budget):
+    from paper_2505_18992_gb300.anchors import Spawner
+    from paper_2505_18992_gb300.icp import VoxelMap
+    rng = np.random.default_rng(W)
+    alpha, depth, depth_in, T = _spawn_inputs(rng, W, H)
+    fx = fy = 0.8 * W
+    cx, cy = W / 2.0, H / 2.0
+    voxel, rho, map_voxel = 0.1, 0.08, 0.1
+    # Gaussian means: a back-projection of a few pixels with jitter, so that the radius rule bites
+    ii, jj = rng.integers(0, W, 4000), rng.integers(0, H, 4000)
+    gm = A.back_project(ii, jj, rng.uniform(0.5, 8.0, 4000), fx, fy, cx, cy, T)
+    gm = (gm + rng.normal(0, 0.05, gm.shape)).astype(np.float32)
+    gmap = VoxelMap(dev(gm), map_voxel)
+    sp = Spawner(W, H, fx, fy, cx, cy, 0.5, 0.1, voxel, rho, budget)
+    sp(dev(alpha), dev(depth), dev(depth_in), dev(T, torch.float64), gmap, keep_samples=True)
+    got, samples = (x.cpu().numpy() for x in sp.results())
+    want, want_samples = A.spawn(alpha, depth, depth_in, fx, fy, cx, cy, T, 0.5, 0.1, budget, voxel, rho, gm)
+    assert sp.status() == 0
+    assert np.array_equal(samples, want_samples)
+    assert np.array_equal(got, want)
+    assert 0 < len(got) < len(samples)
+
+
+def test_spawning_degenerate_cases():
+    from paper_2505_18992_gb300.anchors import Spawner
+    from paper_2505_18992_gb300.icp import VoxelMap
+    W, H = 64, 48
+    ones = np.ones((H, W), np.float32)
+    empty = VoxelMap(torch.zeros((0, 3), dtype=torch.float32, device="cuda"), 0.2)
+    sp = Spawner(W, H, 50.0, 50.0, 32.0, 24.0, 0.5, 0.1, 0.2, 0.1, 500)
+    # nothing to spawn: opaque and consistent
+    sp(dev(ones), dev(2 * ones), dev(2 * ones), dev(np.eye(4), torch.float64), empty)
+    assert [int(x) for x in sp.counts.cpu()][0] == 0
+    # transparent everywhere, empty map: every first voxel of the 500 samples is kept
+    sp(dev(0 * ones), dev(2 * ones), dev(2 * ones), dev(np.eye(4), torch.float64), empty, keep_samples=True)
+    got, samples = (x.cpu().numpy() for x in sp.results())
+    want, ws = A.spawn(0 * ones, 2 * ones, 2 * ones, 50.0, 50.0, 32.0, 24.0, np.eye(4), 0.5, 0.1, 500, 0.2, 0.1,
+                       np.zeros((0, 3), np.float32))
+    assert len(samples) == 500 and np.array_equal(got, want)
