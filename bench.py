@@ -49,7 +49,8 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip tracking/e2e/profile passes")
     p.add_argument("--no-rows", action="store_true", help="keep the kernel profile, skip the other rows")
-    p.add_argument("--row", choices=("tracking", "decode", "batched_keyframes", "fusion", "mapping", "icp"),
+    p.add_argument("--row", choices=("tracking", "decode", "batched_keyframes", "fusion", "mapping", "icp",
+                                     "anchors"),
                    help="run only this secondary row and print it (a profiling entry point, not a bench line)")
     p.add_argument("--persistent", type=int, default=0, help="persistent CTAs per SM (0 = per tile)")
     p.add_argument("--tile", default="8x16", help="tile shape WxH")
@@ -489,7 +490,8 @@ def run_ours(a):
         # coarse tracking: 50 pose-only iterations, eager vs one captured CUDA graph
         for key, fn in (("tracking", lambda: tracking_rows(sc, g, dev)), ("decode", lambda: decode_rows(dev)),
                         ("batched_keyframes", lambda: batched_rows(dev)), ("fusion", lambda: fusion_rows(dev)),
-                        ("mapping", lambda: mapping_rows(sc, g, dev)), ("icp", lambda: icp_rows(dev))):
+                        ("mapping", lambda: mapping_rows(sc, g, dev)), ("icp", lambda: icp_rows(dev)),
+                        ("anchors", lambda: anchor_rows(dev))):
             try:
                 line[key] = fn()
             except Exception as exc:  # reported, not fatal
@@ -502,6 +504,11 @@ def run_ours(a):
                 line["cpu_baseline"]["icp"] = icp_oracle(T_icp)
             except Exception as exc:  # reported, not fatal
                 line["cpu_baseline"]["icp"] = {"error": repr(exc)[:300]}
+        if "anchors" in line:
+            try:
+                line["cpu_baseline"]["anchors"] = anchor_oracle()
+            except Exception as exc:  # reported, not fatal
+                line["cpu_baseline"]["anchors"] = {"error": repr(exc)[:300]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -818,6 +825,84 @@ def icp_oracle(T_gpu):
     return out
 
 
+SPAWN = dict(tau_alpha=0.5, delta_depth=0.1, voxel=0.05, rho=0.04, map_voxel=0.05, max_samples=50_000)
+ANCHOR_UPDATE = dict(tau_g=2.5e-3, tau_o=0.3, grow_voxel=0.2)
+
+
+def anchor_rows(dev, reps=20):
+    """Submap expansion and anchor maintenance (Sec. III-A): statistics of one
+    training step of 100,000 street anchors (500,000 decoded Gaussians),
+    pruning + growth from them, and spawning from one 1200x680 room keyframe
+    (142k masked pixels, 50,000 samples, 5 cm voxels, rho = 4 cm against
+    300,000 Gaussian means)."""
+    import torch
+
+    from paper_2505_18992_gb300 import scenes
+    from paper_2505_18992_gb300 import vpgs as C
+    from paper_2505_18992_gb300.anchors import AnchorStats, AnchorUpdate, Spawner
+    from paper_2505_18992_gb300.icp import VoxelMap
+    t = lambda a, dt=torch.float32: torch.tensor(a, dtype=dt, device=dev).contiguous()  # noqa: E731
+    stp = scenes.anchor_step()
+    A, N = len(stp.anchors), len(stp.src_index)
+    src, grads, opac, vis, means = (t(stp.src_index, torch.int32), t(stp.grads), t(stp.opacities),
+                                    t(stp.visible, torch.int32), t(stp.means))
+    st = AnchorStats(A, device=dev)
+    acc_ms = _time_ms(lambda: st.accumulate(stp.k, src, grads, opac, vis), reps)
+    st.reset()
+    st.accumulate(stp.k, src, grads, opac, vis)
+    amap = VoxelMap(t(stp.anchors), ANCHOR_UPDATE["grow_voxel"])
+    amap_ms = _time_ms(lambda: amap.rebuild(), reps)
+    up = AnchorUpdate(A, N, device=dev, **ANCHOR_UPDATE)
+    upd_ms = _time_ms(lambda: up(st, stp.k, src, means, amap), reps)
+    keep, grown = up.results()
+    fr = scenes.keyframe_spawn()
+    gmap = VoxelMap(t(fr.gauss_means), SPAWN["map_voxel"])
+    sp = Spawner(fr.width, fr.height, fr.fx, fr.fy, fr.cx, fr.cy, SPAWN["tau_alpha"], SPAWN["delta_depth"],
+                 SPAWN["voxel"], SPAWN["rho"], SPAWN["max_samples"], device=dev)
+    ins = (t(fr.alpha), t(fr.depth), t(fr.depth_in), t(fr.T_cw, torch.float64))
+    spawn_ms = _time_ms(lambda: sp(*ins, gmap), reps)
+    new, _ = sp.results()
+    C.vpgs_profile_enable(1)
+    for _ in range(5):
+        st.accumulate(stp.k, src, grads, opac, vis)
+        up(st, stp.k, src, means, amap)
+        sp(*ins, gmap)
+    torch.cuda.synchronize()
+    prof = C.profile_collect()
+    C.vpgs_profile_enable(0)
+    acc_bytes = N * (4 + 12 + 4 + 4)
+    return {"anchors": A, "decoded_gaussians": N, "stats_accumulate_ms": acc_ms,
+            "stats_accumulate_gbs": acc_bytes / (acc_ms * 1e-3) / 1e9,
+            "anchor_map_build_ms": amap_ms, "prune_grow_ms": upd_ms, "kept": int(len(keep)), "grown": int(len(grown)),
+            "spawn_ms": spawn_ms, "spawn_pixels": fr.width * fr.height, "spawned": int(len(new)),
+            "kernels_us": {k: round(1000 * tt / 5, 1) for k, (n, tt) in prof.items()
+                           if k.startswith(("anchor", "spawn"))}}
+
+
+def anchor_oracle():
+    """The FP64 oracle on the anchor row's inputs (one host core): statistics,
+    pruning + growth and spawning."""
+    import importlib
+    import time
+
+    from paper_2505_18992_gb300 import scenes
+    O = importlib.import_module("oracle.anchors")
+    stp = scenes.anchor_step()
+    fr = scenes.keyframe_spawn()
+    t0 = time.perf_counter()
+    s = O.accumulate_stats(O.new_stats(len(stp.anchors)), stp.src_index, stp.k, stp.grads, stp.opacities, stp.visible)
+    t1 = time.perf_counter()
+    O.prune(s, ANCHOR_UPDATE["tau_o"])
+    O.grow(s, stp.src_index, stp.k, stp.means, ANCHOR_UPDATE["tau_g"], ANCHOR_UPDATE["grow_voxel"], stp.anchors)
+    t2 = time.perf_counter()
+    new, _ = O.spawn(fr.alpha, fr.depth, fr.depth_in, fr.fx, fr.fy, fr.cx, fr.cy, fr.T_cw, SPAWN["tau_alpha"],
+                     SPAWN["delta_depth"], SPAWN["max_samples"], SPAWN["voxel"], SPAWN["rho"], fr.gauss_means)
+    t3 = time.perf_counter()
+    return {"value": (t3 - t0) * 1e3, "unit": "ms (statistics + prune/grow + spawn)", "cores": 1, "kind": "oracle",
+            "sample": "the full anchor row workload", "stats_ms": (t1 - t0) * 1e3, "prune_grow_ms": (t2 - t1) * 1e3,
+            "spawn_ms": (t3 - t2) * 1e3, "spawned": int(len(new))}
+
+
 def tracking_rows(sc, g, dev):
     import torch
 
@@ -876,7 +961,7 @@ def run_row(a):
         out = tracking_rows(sc, g, dev) if a.row == "tracking" else mapping_rows(sc, g, dev)
     else:
         out = {"decode": decode_rows, "batched_keyframes": batched_rows, "fusion": fusion_rows,
-               "icp": icp_rows}[a.row](dev)
+               "icp": icp_rows, "anchors": anchor_rows}[a.row](dev)
     out.pop("_T", None)
     print(json.dumps({"row": a.row, **out}), flush=True)
 

@@ -37,6 +37,8 @@ Readings where the paper is silent:
     that are visible (rendered with a non-empty tile cover), g_cnt += 1 for
     each of them, o_sum += o_i over all its decoded Gaussians, visits += 1
     when it decoded any Gaussian.  The gradient is that of the 3D mean.
+  * The statistics are float32 numbers (as the training keeps them) and both
+    threshold tests below are decided in float32.
   * Growth: anchors with g_cnt > 0 and g_sum > tau_g g_cnt; candidates are
     the voxels (edge v_g) of those anchors' decoded Gaussian means that hold
     no existing anchor, as voxel centres, in the order of the first decoded
@@ -153,15 +155,17 @@ def new_stats(n_anchors):
 
 def prune(stats, tau_o) -> np.ndarray:
     """Indices (ascending) of the anchors kept."""
-    v = stats["visits"]
-    drop = (v > 0) & (stats["o_sum"] < tau_o * v)
+    v = np.asarray(stats["visits"])
+    o = np.asarray(stats["o_sum"]).astype(np.float32)
+    drop = (v > 0) & (o < np.float32(tau_o) * v.astype(np.float32))
     return np.nonzero(~drop)[0]
 
 
 def grow(stats, src_index, k, means, tau_g, voxel, anchors) -> np.ndarray:
     """Voxel centres (float32 [n,3]) of the new anchors grown from high-gradient anchors."""
-    cnt = stats["g_cnt"]
-    hot = (cnt > 0) & (stats["g_sum"] > tau_g * np.maximum(cnt, 1))
+    cnt = np.asarray(stats["g_cnt"])
+    g = np.asarray(stats["g_sum"]).astype(np.float32)
+    hot = (cnt > 0) & (g > np.float32(tau_g) * cnt.astype(np.float32))
     a = np.asarray(src_index, np.int64) // k
     pts = np.asarray(means, np.float32)[hot[a]]
     keys, _ = first_voxels(pts, voxel)

@@ -497,3 +497,80 @@ def street_lidar(n_map: int = 1_000_000, beams: int = 64, azimuths: int = 1800, 
     T_init[:3, :3] = dR @ T_true[:3, :3]
     T_init[:3, 3] += rng.normal(0, 0.15, 3)
     return LidarScene("street_lidar", map_points, scan, T_true, T_init)
+
+
+@dataclass
+class SpawnFrame:
+    """One keyframe for anchor spawning: rendered alpha/depth of the current
+    map, the sensor's depth, the pose and the map's Gaussian means."""
+    width: int
+    height: int
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    T_cw: np.ndarray        # [4,4] float64
+    alpha: np.ndarray       # [H,W] float32
+    depth: np.ndarray       # [H,W] float32
+    depth_in: np.ndarray    # [H,W] float32, 0 = no measurement
+    gauss_means: np.ndarray  # [G,3] float32
+
+
+def keyframe_spawn(width: int = 1200, height: int = 680, f: float = 600.0, n_gauss: int = 300_000,
+                   seed: int = 11) -> SpawnFrame:
+    """A keyframe inside the 6x5x3 m room (camera at the centre looking +x):
+    the input depth is the ray-cast room (1 mm noise, 2 % missing); the map
+    misses the region behind image columns 700-999, rows 150-499 (rendered
+    alpha U(0, 0.3) there, 1 elsewhere) and an object moved by 0.3 m in
+    columns 100-299, rows 400-599 (rendered depth off by 0.3 m); the map's
+    Gaussian means are 1 cm-jittered surface points seen outside the hole."""
+    rng = np.random.default_rng(seed)
+    T = look_at([3.0, 2.5, 1.5], [4.0, 2.5, 1.5], [0, 0, 1])
+    R, t = T[:3, :3], T[:3, 3]
+    o = -R.T @ t  # camera centre
+    cx, cy = width / 2.0, height / 2.0
+    jj, ii = np.mgrid[0:height, 0:width]
+    rc = np.stack([(ii + 0.5 - cx) / f, (jj + 0.5 - cy) / f, np.ones_like(ii, dtype=np.float64)], -1)
+    dw = rc @ R  # world direction of each pixel ray (z_c = 1)
+    hi = np.array([6.0, 5.0, 3.0])
+    with np.errstate(divide="ignore", invalid="ignore"):
+        tb = np.where(dw > 0, (hi - o) / dw, np.where(dw < 0, -o / dw, np.inf))
+    z = tb.min(-1)  # depth along the optical axis
+    depth_in = (z + rng.normal(0, 1e-3, z.shape)).astype(np.float32)
+    depth_in[rng.uniform(size=z.shape) < 0.02] = 0.0
+    hole = (ii >= 700) & (ii < 1000) & (jj >= 150) & (jj < 500)
+    moved = (ii >= 100) & (ii < 300) & (jj >= 400) & (jj < 600)
+    alpha = np.where(hole, rng.uniform(0, 0.3, z.shape), 1.0).astype(np.float32)
+    depth = (z + rng.normal(0, 1e-3, z.shape) + np.where(moved, 0.3, 0.0)).astype(np.float32)
+    seen = np.flatnonzero(~hole.ravel())
+    pick = rng.choice(seen, size=n_gauss)
+    pts = o + (z.ravel()[pick] + rng.normal(0, 0.01, n_gauss))[:, None] * dw.reshape(-1, 3)[pick]
+    return SpawnFrame(width, height, f, f, cx, cy, T, alpha, depth, depth_in, pts.astype(np.float32))
+
+
+@dataclass
+class AnchorStep:
+    """Decode-shaped inputs of one training step for the anchor statistics."""
+    anchors: np.ndarray     # [A,3] float32
+    k: int
+    src_index: np.ndarray   # [N] int32, ascending (anchor, slot)
+    means: np.ndarray       # [N,3] float32
+    grads: np.ndarray       # [N,3] float32, dL/dmu
+    opacities: np.ndarray   # [N] float32
+    visible: np.ndarray     # [N] int32 (tile counts)
+
+
+def anchor_step(n_anchors: int = 100_000, k: int = K_PER_ANCHOR, keep: float = 0.5, seed: int = 12) -> AnchorStep:
+    """The street's anchors (0.2 m voxels) with half of their k slots decoded:
+    means within 0.2 m of the anchor, gradient norms U(0, 2e-3) in random
+    directions, opacities U(0, 1), tile counts 0-3."""
+    rng = np.random.default_rng(seed)
+    anchors = street_anchors(n_anchors=n_anchors, seed=seed).anchors
+    A = len(anchors)
+    src = np.sort(rng.choice(A * k, size=int(keep * A * k), replace=False)).astype(np.int32)
+    n = len(src)
+    means = (anchors[src // k] + rng.uniform(-0.2, 0.2, size=(n, 3))).astype(np.float32)
+    grads = (rng.normal(size=(n, 3)) * rng.uniform(0, 2e-3, size=(n, 1))).astype(np.float32)
+    opac = rng.uniform(0, 1, n).astype(np.float32)
+    vis = rng.integers(0, 4, n).astype(np.int32)
+    return AnchorStep(anchors, k, src, means, grads, opac, vis)

@@ -156,3 +156,41 @@ def test_spawning_degenerate_cases():
     want, ws = A.spawn(0 * ones, 2 * ones, 2 * ones, 50.0, 50.0, 32.0, 24.0, np.eye(4), 0.5, 0.1, 500, 0.2, 0.1,
                        np.zeros((0, 3), np.float32))
     assert len(samples) == 500 and np.array_equal(got, want)
+
+
+def test_bench_workloads_match_the_oracle():
+    """The anchor row's own inputs and thresholds (100k anchors, 500k decoded
+    Gaussians; the 1200x680 room keyframe with 50,000 samples)."""
+    import bench
+    from paper_2505_18992_gb300 import scenes
+    from paper_2505_18992_gb300.anchors import AnchorStats, AnchorUpdate, Spawner
+    from paper_2505_18992_gb300.icp import VoxelMap
+    stp = scenes.anchor_step()
+    st = AnchorStats(len(stp.anchors))
+    st.accumulate(stp.k, dev(stp.src_index, torch.int32), dev(stp.grads), dev(stp.opacities),
+                  dev(stp.visible, torch.int32))
+    ref = A.accumulate_stats(A.new_stats(len(stp.anchors)), stp.src_index, stp.k, stp.grads, stp.opacities,
+                             stp.visible)
+    got = _stats_np(st)
+    assert np.array_equal(got["g_cnt"], ref["g_cnt"]) and np.array_equal(got["visits"], ref["visits"])
+    assert np.all(np.abs(got["g_sum"] - ref["g_sum"]) <= 1e-5 * np.abs(ref["g_sum"]) + 1e-6)
+    u = bench.ANCHOR_UPDATE
+    amap = VoxelMap(dev(stp.anchors), u["grow_voxel"])
+    up = AnchorUpdate(len(stp.anchors), len(stp.src_index), **u)
+    up(st, stp.k, dev(stp.src_index, torch.int32), dev(stp.means), amap)
+    keep, grown = (x.cpu().numpy() for x in up.results())
+    assert np.array_equal(keep, A.prune(got, u["tau_o"]))  # decisions on the GPU's own float32 sums
+    assert np.array_equal(grown, A.grow(got, stp.src_index, stp.k, stp.means, u["tau_g"], u["grow_voxel"],
+                                        stp.anchors))
+    fr = scenes.keyframe_spawn()
+    sp_ = bench.SPAWN
+    gmap = VoxelMap(dev(fr.gauss_means), sp_["map_voxel"])
+    sp = Spawner(fr.width, fr.height, fr.fx, fr.fy, fr.cx, fr.cy, sp_["tau_alpha"], sp_["delta_depth"], sp_["voxel"],
+                 sp_["rho"], sp_["max_samples"])
+    sp(dev(fr.alpha), dev(fr.depth), dev(fr.depth_in), dev(fr.T_cw, torch.float64), gmap, keep_samples=True)
+    new, samples = (x.cpu().numpy() for x in sp.results())
+    want, want_samples = A.spawn(fr.alpha, fr.depth, fr.depth_in, fr.fx, fr.fy, fr.cx, fr.cy, fr.T_cw,
+                                 sp_["tau_alpha"], sp_["delta_depth"], sp_["max_samples"], sp_["voxel"], sp_["rho"],
+                                 fr.gauss_means)
+    assert np.array_equal(samples, want_samples) and np.array_equal(new, want)
+    assert len(keep) < len(stp.anchors) and len(grown) > 0 and len(new) > 0
