@@ -42,6 +42,10 @@ VPGS_D TileCoord tile_coord(int t, const CamParams &cam) {
 // Each thread owns kPix pixels of its tile column: rows kPix*ly .. kPix*ly + kPix - 1.
 constexpr int kPix = VPGS_PIX;
 constexpr int kAcc = VPGS_BWD_ACC;  // combination of per-warp gradient sums (see common.cuh)
+#ifndef VPGS_BWD_DIRECT
+#define VPGS_BWD_DIRECT 2
+#endif
+constexpr int kDirect = VPGS_BWD_DIRECT;  // at most this many active lanes: per-lane atomics, no reduction
 constexpr int kMaxThreads = 512;
 
 // Centre and half height of the band of tile-local pixel-centre rows held by
@@ -392,8 +396,8 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                     act |= pair_grad(ps[q], jj, e, dx, dy, a, b, c, o, v);
                 }
                 const uint32_t am = __ballot_sync(0xffffffffu, act);
-                if (kAcc == 0 && am != 0u && __popc(am) <= 2) {
-                    // one or two active lanes: their own atomics beat a reduction
+                if (kAcc == 0 && am != 0u && __popc(am) <= kDirect) {
+                    // few active lanes: their own atomics beat a reduction
                     if (act) {
                         float *dst = g2d + 10 * (int64_t)s_id[kk];
 #pragma unroll
