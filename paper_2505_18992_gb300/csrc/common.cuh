@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <utility>
 
 #include "../../include/vpgs.h"
 
@@ -35,6 +36,48 @@ constexpr int kWarp = 32;
 // ---------------------------------------------------------------------------
 // status word: the first error wins (atomicCAS from OK)
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// programmatic dependent launch (VPGS_PDL: 0 off, 1 the render kernels are
+// launched so that they may be scheduled while their predecessor finishes,
+// 2 and they also let their own successor be scheduled at once).  Every such
+// kernel starts with grid_dep_enter(), which waits for the predecessor grid to
+// complete and its memory to be visible before anything else runs.
+// ---------------------------------------------------------------------------
+#ifndef VPGS_PDL
+#define VPGS_PDL 1
+#endif
+VPGS_D void grid_dep_enter() {
+#if VPGS_PDL
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#if VPGS_PDL >= 2
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+#endif
+}
+
+// Kernel launch used by the render path: with VPGS_PDL the launch allows
+// programmatic stream serialisation (the kernel must begin with
+// grid_dep_enter()); errors surface through cudaGetLastError as for <<< >>>.
+template <typename... P, typename... A>
+inline cudaError_t launch_k(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A &&...args) {
+#if VPGS_PDL
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+#else
+    k<<<grid, block, smem, s>>>(std::forward<A>(args)...);
+    return cudaSuccess;
+#endif
+}
+
 VPGS_D void set_status(uint32_t *status, uint32_t code) {
     atomicCAS(status, (uint32_t)VPGS_OK, code);
 }

@@ -170,6 +170,7 @@ map_scatter_kernel(const float *__restrict__ pts, int64_t n, const uint32_t *__r
 __global__ void __launch_bounds__(256)
 icp_prepare_kernel(VoxEntry *tab1, VoxEntry *tab2, uint32_t cap, unsigned long long *look, int64_t n_look,
                    IcpState *st, const double *T, const MapHeader *hdr, vpgs_icp_report *rep) {
+    grid_dep_enter();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t i = t0; i < cap; i += stride) {
@@ -198,6 +199,7 @@ __global__ void __launch_bounds__(256)
 ds_insert_kernel(const float *__restrict__ pts, const uint32_t *__restrict__ idx_in, int64_t n_cap,
                  const uint32_t *n_dev, float v, VoxEntry *tab, uint32_t mask, uint32_t *__restrict__ slot,
                  uint32_t *status) {
+    grid_dep_enter();
     int64_t n = n_cap;
     if (n_dev) n = min(n, (int64_t)*n_dev);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -423,6 +425,7 @@ __global__ void __launch_bounds__(kIcpThreads)
 icp_step_kernel(MapView map, SrcView sv, int64_t n_cap, const uint32_t *n_dev, double *T,
                 const double *__restrict__ centre, float tau, float sigma, float eps, float *partial,
                 int32_t *__restrict__ corr, IcpState *st, vpgs_icp_report *rep, double *sys_out) {
+    grid_dep_enter();
     __shared__ float s_acc[kIcpWarps][kWarp];
     __shared__ float2 s_part[kIcpWarps][kWarp];
     __shared__ double s_sys[kWarp], s_T[12], s_c[3];
@@ -706,7 +709,7 @@ cudaError_t launch_prepare(const IcpWsView &w, const double *T, const MapHeader 
                            cudaStream_t s) {
     const int64_t n = std::max<int64_t>(w.L.cap, (int64_t)w.L.n_look);
     VPGS_LAUNCH("icp_prepare", s,
-                icp_prepare_kernel<<<fill_grid(n), 256, 0, s>>>(w.tab1, w.tab2, w.L.cap, w.look,
+                launch_k(icp_prepare_kernel, fill_grid(n), 256, 0, s, w.tab1, w.tab2, w.L.cap, w.look,
                                                                 (int64_t)w.L.n_look, w.st, T, hdr, rep));
     return cudaGetLastError();
 }
@@ -718,7 +721,7 @@ cudaError_t launch_downsample(const IcpWsView &w, const float *scan, int64_t n, 
     const uint32_t mask = w.L.cap - 1;
     const size_t half = w.L.n_look / 2;
     VPGS_LAUNCH("icp_ds_insert", s,
-                ds_insert_kernel<<<fill_grid(n), 256, 0, s>>>(scan, nullptr, n, nullptr, v1, w.tab1, mask, w.slot1,
+                launch_k(ds_insert_kernel, fill_grid(n), 256, 0, s, scan, nullptr, n, nullptr, v1, w.tab1, mask, w.slot1,
                                                               &w.st->status));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -726,7 +729,7 @@ cudaError_t launch_downsample(const IcpWsView &w, const float *scan, int64_t n, 
                     &w.st->ticket[0], w.look, &w.st->n1, &w.st->status, s);
     if (e != cudaSuccess) return e;
     VPGS_LAUNCH("icp_ds_insert", s,
-                ds_insert_kernel<<<fill_grid(n), 256, 0, s>>>(scan, w.idx1, n, &w.st->n1, v2, w.tab2, mask, w.slot2,
+                launch_k(ds_insert_kernel, fill_grid(n), 256, 0, s, scan, w.idx1, n, &w.st->n1, v2, w.tab2, mask, w.slot2,
                                                               &w.st->status));
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -826,7 +829,7 @@ vpgs_status vpgs_icp_linearize(void *ws, size_t ws_bytes, const void *map, size_
     const MapView mv = map_view(map, n_map, map_voxel);
     if (launch_prepare(w, nullptr, mv.hdr, nullptr, s) != cudaSuccess) return VPGS_ERR_CUDA;
     VPGS_LAUNCH("icp_step", s,
-                icp_step_kernel<<<corr_grid(), kIcpThreads, 0, s>>>(mv, SrcView{nullptr, src, nullptr}, n_src, nullptr,
+                launch_k(icp_step_kernel, corr_grid(), kIcpThreads, 0, s, mv, SrcView{nullptr, src, nullptr}, n_src, nullptr,
                                                                     const_cast<double *>(T), centre, tau, sigma, 0.f,
                                                                     w.partial, corr, w.st, nullptr, system));
     return cudaGetLastError() == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
@@ -854,7 +857,7 @@ vpgs_status vpgs_icp_register(void *ws, size_t ws_bytes, const void *map, size_t
     const int nb = corr_grid();
     for (int it = 0; it < o.iterations; ++it) {
         VPGS_LAUNCH("icp_step", s,
-                    icp_step_kernel<<<nb, kIcpThreads, 0, s>>>(mv, SrcView{w.src4, nullptr, nullptr}, n_scan,
+                    launch_k(icp_step_kernel, nb, kIcpThreads, 0, s, mv, SrcView{w.src4, nullptr, nullptr}, n_scan,
                                                                &w.st->n2, T, w.st->c,
                                                                o.tau, o.sigma, o.eps, w.partial, nullptr, w.st,
                                                                report, nullptr));

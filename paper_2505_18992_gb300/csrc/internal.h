@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "common.cuh"
 
 namespace vpgs {
@@ -31,6 +33,7 @@ struct GaussGrad {
 };
 
 int device_sm_count();
+
 
 // render_pre.cu
 // First launches of a render call: the prepare kernel (zeroes status, counters

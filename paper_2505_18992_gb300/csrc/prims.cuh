@@ -45,6 +45,7 @@ template <class Load, class Store>
 __global__ void __launch_bounds__(kScanThreads)
 scan_kernel(Load load, Store store, int64_t n_cap, const uint32_t *n_dev, uint32_t *ticket,
             unsigned long long *look, uint32_t *total, uint32_t *status) {
+    grid_dep_enter();
     __shared__ uint32_t s_items[kScanTile + kScanTile / 32];
     __shared__ uint32_t s_warp[kScanThreads / kWarp];
     __shared__ uint32_t s_bid, s_excl;
@@ -179,7 +180,7 @@ cudaError_t launch_scan(const char *name, Load load, Store store, int64_t n_cap,
         grid_cache = resident_grid((const void *)scan_kernel<Load, Store>, kScanThreads, 0, int64_t(1) << 30);
     const int grid = (int)std::min<int64_t>(grid_cache, nb);
     VPGS_LAUNCH(name, stream,
-                scan_kernel<<<(unsigned)grid, kScanThreads, 0, stream>>>(load, store, n_cap, n_dev,
+                launch_k(scan_kernel<Load, Store>, (unsigned)grid, kScanThreads, 0, stream, load, store, n_cap, n_dev,
                                                                          ticket, look, total, status));
     return cudaGetLastError();
 }
@@ -211,6 +212,7 @@ radix_onesweep_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__res
                       int64_t n_cap, const uint32_t *n_dev, SortPass pass,
                       const uint32_t *__restrict__ pass_hist, uint32_t *ticket, uint32_t *look,
                       uint32_t *next_look, uint32_t *status) {
+    grid_dep_enter();
     constexpr int kWarps = kSortThreads / kWarp;
     constexpr int kSeg = kWarp * ITEMS;  // contiguous items per warp
     constexpr int kTile = kSortThreads * ITEMS;
@@ -426,16 +428,16 @@ inline cudaError_t radix_sort_pairs(const char *name, uint32_t *k0, uint32_t *v0
         uint32_t *nl = p + 1 < np ? lk + (size_t)nb * kRadix : nullptr;
         const uint32_t *h = hist + p * kRadix;
         if (items == 4)
-            VPGS_LAUNCH(name, stream, radix_onesweep_kernel<4><<<grid, kSortThreads, 0, stream>>>(
+            VPGS_LAUNCH(name, stream, launch_k(radix_onesweep_kernel<4>, grid, kSortThreads, 0, stream,
                                           ki, vi, ko, vo, n_cap, n_dev, ps[p], h, ticket + p, lk, nl, status));
         else if (items == 8)
-            VPGS_LAUNCH(name, stream, radix_onesweep_kernel<8><<<grid, kSortThreads, 0, stream>>>(
+            VPGS_LAUNCH(name, stream, launch_k(radix_onesweep_kernel<8>, grid, kSortThreads, 0, stream,
                                           ki, vi, ko, vo, n_cap, n_dev, ps[p], h, ticket + p, lk, nl, status));
         else if (items == 32)
-            VPGS_LAUNCH(name, stream, radix_onesweep_kernel<32><<<grid, kSortThreads, 0, stream>>>(
+            VPGS_LAUNCH(name, stream, launch_k(radix_onesweep_kernel<32>, grid, kSortThreads, 0, stream,
                                           ki, vi, ko, vo, n_cap, n_dev, ps[p], h, ticket + p, lk, nl, status));
         else
-            VPGS_LAUNCH(name, stream, radix_onesweep_kernel<16><<<grid, kSortThreads, 0, stream>>>(
+            VPGS_LAUNCH(name, stream, launch_k(radix_onesweep_kernel<16>, grid, kSortThreads, 0, stream,
                                           ki, vi, ko, vo, n_cap, n_dev, ps[p], h, ticket + p, lk, nl, status));
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;

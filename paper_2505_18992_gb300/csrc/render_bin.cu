@@ -62,6 +62,7 @@ emit_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__ inst
             int64_t M_cap, CamParams cam, uint32_t *__restrict__ ikey, uint32_t *__restrict__ ival,
             uint32_t *status, int n_pass, SortPass p0, SortPass p1, SortPass p2, SortPass p3,
             uint32_t *hist) {
+    grid_dep_enter();
     // digit histograms of the emitted tile ids, for the tile sort
     __shared__ uint32_t s_h[4][kRadix];
     const SortPass tps[4] = {p0, p1, p2, p3};
@@ -159,6 +160,7 @@ emit_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__ inst
 
 __global__ void tile_ranges_kernel(const uint32_t *__restrict__ keys, int64_t cap, const uint32_t *n_dev,
                                    uint32_t n_tiles, uint2 *ranges) {
+    grid_dep_enter();
     int64_t n = min(cap, (int64_t)*n_dev);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -215,9 +217,9 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
     static int emit_grid = 0;
     if (emit_grid == 0) emit_grid = resident_grid((const void *)emit_kernel, kEmitThreads, 0, int64_t(1) << 30);
     VPGS_LAUNCH("emit_instances", s,
-                emit_kernel<<<(unsigned)std::min<int64_t>(std::max<int64_t>((L.VN + kEmitThreads - 1) / kEmitThreads, 1),
+                launch_k(emit_kernel, (unsigned)std::min<int64_t>(std::max<int64_t>((L.VN + kEmitThreads - 1) / kEmitThreads, 1),
                                                           emit_grid),
-                              kEmitThreads, 0, s>>>(dval, inst_off, ws.bin, n_vis, n_inst, L.N, L.M_cap,
+                              kEmitThreads, 0, s, dval, inst_off, ws.bin, n_vis, n_inst, L.N, L.M_cap,
                                                     cam, ws.ikey[0], ws.ival[0], ws.status, np_tile, tps[0],
                                                     tps[1], tps[2], tps[3], ws.sort_hist[1]));
     e = cudaGetLastError();
@@ -234,7 +236,7 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
     const int n_tiles = V * cam.T;  // (ranges zeroed by the prepare kernel)
     const int64_t rb = std::min<int64_t>((L.M_cap + 255) / 256, (int64_t)sms * 16);
     VPGS_LAUNCH("tile_ranges", s,
-                tile_ranges_kernel<<<(unsigned)std::max<int64_t>(rb, 1), 256, 0, s>>>(
+                launch_k(tile_ranges_kernel, (unsigned)std::max<int64_t>(rb, 1), 256, 0, s,
                     in1 ? ws.ikey[1] : ws.ikey[0], L.M_cap, n_inst, (uint32_t)n_tiles, ws.ranges));
     return cudaGetLastError();
 }

@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(kMaxThreads)
 composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ ival,
                      const uint2 *__restrict__ ranges, int n_tiles, CamParams cam, OptParams o,
                      vpgs_images out, const uint32_t *status, uint32_t *work) {
+    grid_dep_enter();
     extern __shared__ float4 smem[];
     const int NT = blockDim.x;
     float4 *s0 = smem, *s1 = smem + NT, *s2 = smem + 2 * NT;
@@ -290,6 +291,7 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                      const float *__restrict__ dL_drgb, const float *__restrict__ dL_ddepth,
                      const float *__restrict__ dL_dalpha, float *__restrict__ g2d,
                      const uint32_t *status, uint32_t *work) {
+    grid_dep_enter();
     extern __shared__ float4 smem[];
     const int NT = blockDim.x;
     const int NW = NT >> 5;
@@ -465,7 +467,7 @@ cudaError_t launch_composite_fwd(const RenderWs &ws, const uint32_t *ival, int V
         cudaFuncSetAttribute((const void *)composite_fwd_kernel,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     VPGS_LAUNCH("composite_fwd", s,
-                composite_fwd_kernel<<<grid, B, sm, s>>>(ws.rec, ival, ws.ranges, n_tiles, cam, o, out,
+                launch_k(composite_fwd_kernel, grid, B, sm, s, ws.rec, ival, ws.ranges, n_tiles, cam, o, out,
                                                          ws.status, work));
     return cudaGetLastError();
 }
@@ -490,7 +492,7 @@ cudaError_t launch_composite_bwd(const RenderWs &ws, const uint32_t *ival, int V
         cudaFuncSetAttribute((const void *)composite_bwd_kernel,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     VPGS_LAUNCH("composite_bwd", s,
-                composite_bwd_kernel<<<grid, B, sm, s>>>(ws.rec, ival, ws.ranges, n_tiles, cam, o,
+                launch_k(composite_bwd_kernel, grid, B, sm, s, ws.rec, ival, ws.ranges, n_tiles, cam, o,
                                                          fwd.t_final, fwd.n_iter, dL_drgb, dL_ddepth,
                                                          dL_dalpha, ws.g2d, ws.status, work));
     return cudaGetLastError();

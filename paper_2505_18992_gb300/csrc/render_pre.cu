@@ -123,6 +123,7 @@ struct PrepZero {
 
 __global__ void __launch_bounds__(256)
 prepare_kernel(const double *__restrict__ T_cw, int V, float *posedf, PrepZero z) {
+    grid_dep_enter();
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
 #pragma unroll
     for (int a = 0; a < 6; ++a)
@@ -227,6 +228,7 @@ constexpr int kPreThreads = 256;
 __global__ void __launch_bounds__(kPreThreads)
 precull_kernel(GaussIn g, int V, CamParams cam, OptParams o, RenderWs ws, uint32_t *cand,
                uint32_t *n_cand) {
+    grid_dep_enter();
     __shared__ int s_wcnt[kPreThreads / 32];
     __shared__ uint32_t s_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -281,6 +283,7 @@ precull_kernel(GaussIn g, int V, CamParams cam, OptParams o, RenderWs ws, uint32
 __global__ void __launch_bounds__(kPreThreads, 3)
 project_kernel(GaussIn g, CamParams cam, OptParams o, RenderWs ws, const uint32_t *__restrict__ cand,
                const uint32_t *n_cand, bool zero_g2d) {
+    grid_dep_enter();
     __shared__ uint32_t s_h[4][kRadix];
     for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0u;
     __syncthreads();
@@ -330,6 +333,7 @@ __global__ void __launch_bounds__(256, VPGS_PRE_BWD_MINB)
 preprocess_bwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamParams cam, OptParams o,
                       RenderWs ws, GaussGrad gg, double *dpose, const uint32_t *__restrict__ vis,
                       const uint32_t *n_vis) {
+    grid_dep_enter();
     __shared__ double s_pose[8][6];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t tix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -503,6 +507,7 @@ preprocess_bwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamPara
 __global__ void export_projection_kernel(RenderWs ws, int64_t VN, int32_t *tile_count,
                                          int32_t *tile_rect, float *mean2d, float *depth,
                                          float *conic) {
+    grid_dep_enter();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= VN) return;
     const uint32_t cnt = ws.tcount[i];
@@ -533,7 +538,7 @@ cudaError_t launch_export_projection(const RenderWs &ws, int64_t VN, int32_t *ti
                                      cudaStream_t s) {
     if (VN == 0) return cudaSuccess;
     VPGS_LAUNCH("export_projection", s,
-                export_projection_kernel<<<(unsigned)((VN + 255) / 256), 256, 0, s>>>(
+                launch_k(export_projection_kernel, (unsigned)((VN + 255) / 256), 256, 0, s,
                     ws, VN, tile_count, tile_rect, mean2d, depth, conic));
     return cudaGetLastError();
 }
@@ -554,13 +559,13 @@ cudaError_t launch_preprocess_fwd(const GaussIn &g, const double *T_cw, int V, c
     if (prep_grid == 0) prep_grid = 8 * std::max(device_sm_count(), 1);
     const int64_t words = std::max<int64_t>(z.n32[3] + z.n32[4] + z.n32[5], z.n64);
     VPGS_LAUNCH("prepare", s,
-                prepare_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(prep_grid, (words + 255) / 256)),
-                                 256, 0, s>>>(T_cw, V, ws.posedf, z));
+                launch_k(prepare_kernel, (unsigned)std::max<int64_t>(1, std::min<int64_t>(prep_grid, (words + 255) / 256)),
+                                 256, 0, s, T_cw, V, ws.posedf, z));
     if (VN == 0) return cudaGetLastError();
     // the candidate list borrows the second depth-key buffer (free until the depth sort)
     uint32_t *cand = ws.dkey[1], *n_cand = ws.counters + CNT_CAND;
     VPGS_LAUNCH("preprocess_fwd", s,
-                precull_kernel<<<(unsigned)((VN + kPreThreads - 1) / kPreThreads), kPreThreads, 0, s>>>(
+                launch_k(precull_kernel, (unsigned)((VN + kPreThreads - 1) / kPreThreads), kPreThreads, 0, s,
                     g, V, cam, o, ws, cand, n_cand));
     static int proj_grid = 0;
     if (proj_grid == 0) {
@@ -571,8 +576,8 @@ cudaError_t launch_preprocess_fwd(const GaussIn &g, const double *T_cw, int V, c
         proj_grid = std::max(occ, 1) * std::max(sms, 1);
     }
     VPGS_LAUNCH("project", s,
-                project_kernel<<<(unsigned)std::min<int64_t>(proj_grid, (VN + kPreThreads - 1) / kPreThreads),
-                                 kPreThreads, 0, s>>>(g, cam, o, ws, cand, n_cand, zero_g2d));
+                launch_k(project_kernel, (unsigned)std::min<int64_t>(proj_grid, (VN + kPreThreads - 1) / kPreThreads),
+                                 kPreThreads, 0, s, g, cam, o, ws, cand, n_cand, zero_g2d));
     return cudaGetLastError();
 }
 
@@ -582,7 +587,7 @@ cudaError_t launch_preprocess_bwd(const GaussIn &g, const double *T_cw, int V, c
     if (g.N == 0) return cudaSuccess;
     const uint32_t *list = V == 1 ? ws.vis_idx : nullptr;
     VPGS_LAUNCH("preprocess_bwd", s,
-                preprocess_bwd_kernel<<<(unsigned)((g.N + 255) / 256), 256, 0, s>>>(
+                launch_k(preprocess_bwd_kernel, (unsigned)((g.N + 255) / 256), 256, 0, s,
                     g, T_cw, V, cam, o, ws, gg, dpose, list, ws.counters + CNT_VISIBLE));
     return cudaGetLastError();
 }
