@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(kAThreads)
 stats_accumulate_kernel(StatsView sv, int64_t A, int k, const int32_t *__restrict__ src, const int32_t *n_dev,
                         int64_t n_cap, const float *__restrict__ grad, const float *__restrict__ opac,
                         const int32_t *__restrict__ visible) {
+    grid_dep_enter();
     const int64_t n = clamp_count(n_cap, n_dev);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -137,6 +138,7 @@ inline UpdLayout upd_layout(int64_t A, int64_t N) {
 __global__ void __launch_bounds__(kAThreads)
 first_table_clear_kernel(VoxEntry *tab, uint32_t cap, unsigned long long *look, int64_t n_look, uint32_t *state,
                          int n_state) {
+    grid_dep_enter();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t i = t0; i < cap; i += stride) tab[i] = VoxEntry{kEmptyKey, kNoSlot, 0u};
@@ -165,6 +167,7 @@ __global__ void __launch_bounds__(kAThreads)
 grow_insert_kernel(StatsView sv, int k, const int32_t *__restrict__ src, const int32_t *n_dev, int64_t n_cap,
                    const float *__restrict__ means, MapView anchors, float tau_g, VoxEntry *tab, uint32_t mask,
                    uint32_t *__restrict__ slot, uint32_t *status) {
+    grid_dep_enter();
     const int64_t n = clamp_count(n_cap, n_dev);
     const bool map_ok = map_header_ok(anchors);
     if (!map_ok && blockIdx.x == 0 && threadIdx.x == 0) set_status(status, VPGS_ERR_INVALID_ARG);
@@ -287,6 +290,7 @@ spawn_sample_kernel(const uint32_t *__restrict__ list, SpawnState *st, int64_t M
                     const float *__restrict__ depth_in, const double *__restrict__ T, float v,
                     float4 *__restrict__ samples, VoxEntry *tab, uint32_t mask, uint32_t *__restrict__ slot,
                     float *samples_out, int32_t *n_samples) {
+    grid_dep_enter();
     const uint64_t C = st->count;
     const uint64_t S = C < (uint64_t)M ? C : (uint64_t)M;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -346,6 +350,7 @@ spawn_sample_kernel(const uint32_t *__restrict__ list, SpawnState *st, int64_t M
 __global__ void __launch_bounds__(kAThreads)
 spawn_flag_kernel(SpawnState *st, const float4 *__restrict__ samples, const uint32_t *__restrict__ slot,
                   const VoxEntry *tab, MapView gmap, float v, float rho, uint32_t *__restrict__ flag) {
+    grid_dep_enter();
     const int lane = threadIdx.x & 31;
     const int64_t S = st->samples;
     const bool map_ok = map_header_ok(gmap);
@@ -407,7 +412,7 @@ vpgs_status vpgs_anchor_stats_accumulate(void *stats, size_t stats_bytes, int64_
     if (n_cap == 0) return VPGS_OK;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     VPGS_LAUNCH("anchor_stats", s,
-                stats_accumulate_kernel<<<agrid(n_cap), kAThreads, 0, s>>>(stats_view(stats, n_anchors), n_anchors, k,
+                launch_k(stats_accumulate_kernel, agrid(n_cap), kAThreads, 0, s, stats_view(stats, n_anchors), n_anchors, k,
                                                                            src_index, n_dev, n_cap, grad_means,
                                                                            opacities, visible));
     return cudaGetLastError() == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
@@ -442,7 +447,7 @@ vpgs_status vpgs_anchor_update(void *ws, size_t ws_bytes, const void *stats, siz
     const StatsView sv = stats_view(const_cast<void *>(stats), n_anchors);
     const int64_t nc = std::max<int64_t>(L.cap, (int64_t)(L.n_look_a + L.n_look_n));
     VPGS_LAUNCH("anchor_update_clear", s,
-                first_table_clear_kernel<<<agrid(nc), kAThreads, 0, s>>>(tab, L.cap, look,
+                launch_k(first_table_clear_kernel, agrid(nc), kAThreads, 0, s, tab, L.cap, look,
                                                                          (int64_t)(L.n_look_a + L.n_look_n),
                                                                          reinterpret_cast<uint32_t *>(st), 16));
     if (cudaGetLastError() != cudaSuccess) return VPGS_ERR_CUDA;
@@ -452,7 +457,7 @@ vpgs_status vpgs_anchor_update(void *ws, size_t ws_bytes, const void *stats, siz
     if (n_cap == 0) return cudaMemsetAsync(n_grown, 0, 4, s) == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
     const MapView am = map_view(anchor_map, n_anchors, o.grow_voxel);
     VPGS_LAUNCH("anchor_grow_insert", s,
-                grow_insert_kernel<<<agrid(n_cap), kAThreads, 0, s>>>(sv, k, src_index, n_dev, n_cap, means, am, o.tau_g,
+                launch_k(grow_insert_kernel, agrid(n_cap), kAThreads, 0, s, sv, k, src_index, n_dev, n_cap, means, am, o.tau_g,
                                                                       tab, L.cap - 1, slot, &st->status));
     if (cudaGetLastError() != cudaSuccess) return VPGS_ERR_CUDA;
     if (launch_scan("anchor_grow_compact", FirstLoad{tab, slot}, CentreStore{means, 3, o.grow_voxel, grown}, n_cap,
@@ -497,7 +502,7 @@ vpgs_status vpgs_spawn_anchors(void *ws, size_t ws_bytes, const float *alpha, co
     unsigned long long *look = reinterpret_cast<unsigned long long *>(b + L.off_look);
     const int64_t nl = (int64_t)(L.n_look_p + L.n_look_m);
     VPGS_LAUNCH("spawn_clear", s,
-                first_table_clear_kernel<<<agrid(std::max<int64_t>(L.cap, nl)), kAThreads, 0, s>>>(
+                launch_k(first_table_clear_kernel, agrid(std::max<int64_t>(L.cap, nl)), kAThreads, 0, s, 
                     tab, L.cap, look, nl, reinterpret_cast<uint32_t *>(st), 16));
     if (cudaGetLastError() != cudaSuccess) return VPGS_ERR_CUDA;
     if (launch_scan("spawn_mask", MaskLoad{alpha, depth, depth_in, o.tau_alpha, o.delta_depth}, ListStore{list}, P,
@@ -505,12 +510,12 @@ vpgs_status vpgs_spawn_anchors(void *ws, size_t ws_bytes, const float *alpha, co
         return VPGS_ERR_CUDA;
     const SpawnCam sc{cam->width, cam->fx, cam->fy, cam->cx, cam->cy};
     VPGS_LAUNCH("spawn_sample", s,
-                spawn_sample_kernel<<<agrid(P), kAThreads, 0, s>>>(list, st, M, sc, depth_in, T_cw, o.voxel, samples,
+                launch_k(spawn_sample_kernel, agrid(P), kAThreads, 0, s, list, st, M, sc, depth_in, T_cw, o.voxel, samples,
                                                                    tab, L.cap - 1, slot, samples_out, n_samples));
     if (cudaGetLastError() != cudaSuccess) return VPGS_ERR_CUDA;
     const MapView gm = map_view(gauss_map, n_map, map_voxel);
     VPGS_LAUNCH("spawn_flag", s,
-                spawn_flag_kernel<<<warp_grid(M), kAThreads, 0, s>>>(st, samples, slot, tab, gm, o.voxel, o.rho, flag));
+                launch_k(spawn_flag_kernel, warp_grid(M), kAThreads, 0, s, st, samples, slot, tab, gm, o.voxel, o.rho, flag));
     if (cudaGetLastError() != cudaSuccess) return VPGS_ERR_CUDA;
     if (launch_scan("spawn_compact", FlagLoad{flag},
                     CentreStore{reinterpret_cast<const float *>(samples), 4, o.voxel, anchors_out}, M, &st->samples,

@@ -160,6 +160,7 @@ struct DecFwdSmem {
 __global__ void __launch_bounds__(kDecAnchors)
 decode_fwd_kernel(DecParams p, const double *__restrict__ T, DecOut o, uint32_t *ticket,
                   unsigned long long *look, uint32_t *status) {
+    grid_dep_enter();
     extern __shared__ __align__(16) unsigned char dsm[];
     DecFwdSmem &S = *reinterpret_cast<DecFwdSmem *>(dsm);
     __shared__ uint32_t s_bid, s_base;
@@ -374,6 +375,7 @@ decode_fwd_kernel(DecParams p, const double *__restrict__ T, DecOut o, uint32_t 
 
 __global__ void inverse_index_kernel(const int32_t *src_index, const int32_t *n_out, int64_t n_cap,
                                      int64_t inv_size, int32_t *inv) {
+    grid_dep_enter();
     const int64_t n = min(n_cap, (int64_t)*n_out);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -405,6 +407,7 @@ struct DecBwdSmem {
 __global__ void __launch_bounds__(kBwdAnchors)
 decode_bwd_kernel(DecParams p, const double *__restrict__ T, const int32_t *__restrict__ inv,
                   DecGradIn gin, DecGradOut gout) {
+    grid_dep_enter();
     extern __shared__ __align__(16) unsigned char dsm[];
     DecBwdSmem &S = *reinterpret_cast<DecBwdSmem *>(dsm);
     __shared__ DecCam s_cam;
@@ -622,6 +625,7 @@ VPGS_D uint32_t ld_u32(const __nv_bfloat16 *p) { return *reinterpret_cast<const 
 __global__ void __launch_bounds__(kMA, 1)
 decode_bwd_mma_kernel(DecParams p, const double *__restrict__ T, const int32_t *__restrict__ inv,
                       DecGradIn gin, DecGradOut gout) {
+    grid_dep_enter();
     extern __shared__ __align__(16) unsigned char dsm[];
     DecBwdMmaSmem &S = *reinterpret_cast<DecBwdMmaSmem *>(dsm);
     __shared__ DecCam s_cam;
@@ -1016,7 +1020,7 @@ vpgs_status vpgs_decode_anchors(void *ws, size_t ws_bytes, const vpgs_anchors *a
     uint32_t *ticket = reinterpret_cast<uint32_t *>(b + L.off_counters + 4 * CNT_TICKET_A);
     unsigned long long *look = reinterpret_cast<unsigned long long *>(b + L.off_look);
     VPGS_LAUNCH("decode_fwd", s,
-                decode_fwd_kernel<<<(unsigned)L.nblocks, kDecAnchors, smem, s>>>(p, T_cw, o, ticket,
+                launch_k(decode_fwd_kernel, (unsigned)L.nblocks, kDecAnchors, smem, s, p, T_cw, o, ticket,
                                                                                  look, status));
     return cudaGetLastError() == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
 }
@@ -1044,7 +1048,7 @@ vpgs_status vpgs_decode_anchors_bwd(void *ws, size_t ws_bytes, const vpgs_anchor
     const int sms = device_sm_count();
     const int ib = (int)std::min<int64_t>((cap + 255) / 256, (int64_t)sms * 8);
     VPGS_LAUNCH("decode_inverse_index", s,
-                inverse_index_kernel<<<ib, 256, 0, s>>>(src_index, dL->n_dev, dL->n, cap, inv));
+                launch_k(inverse_index_kernel, ib, 256, 0, s, src_index, dL->n_dev, dL->n, cap, inv));
     static bool attr_set = false;
     const size_t smem = sizeof(DecBwdSmem);
     if (!attr_set) {
@@ -1064,11 +1068,11 @@ vpgs_status vpgs_decode_anchors_bwd(void *ws, size_t ws_bytes, const vpgs_anchor
         }
         const int64_t nch = (p.A + kMA - 1) / kMA;
         const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nch, sms));
-        VPGS_LAUNCH("decode_bwd", s, decode_bwd_mma_kernel<<<grid, kMA, msm, s>>>(p, T_cw, inv, gin, gout));
+        VPGS_LAUNCH("decode_bwd", s, launch_k(decode_bwd_mma_kernel, grid, kMA, msm, s, p, T_cw, inv, gin, gout));
         return cudaGetLastError() == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
     }
     const unsigned nb = (unsigned)((p.A + kBwdAnchors - 1) / kBwdAnchors);
-    VPGS_LAUNCH("decode_bwd", s, decode_bwd_kernel<<<nb, kBwdAnchors, smem, s>>>(p, T_cw, inv, gin, gout));
+    VPGS_LAUNCH("decode_bwd", s, launch_k(decode_bwd_kernel, nb, kBwdAnchors, smem, s, p, T_cw, inv, gin, gout));
     return cudaGetLastError() == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
 }
 

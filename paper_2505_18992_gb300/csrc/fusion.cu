@@ -25,6 +25,7 @@ __global__ void __launch_bounds__(kFuseThreads)
 distill_kernel(const float *__restrict__ ca, const float *__restrict__ cb, const float *__restrict__ da,
                const float *__restrict__ db, int64_t n_col, int64_t n_dep, float gc, float gd, float *gca,
                float *gcb, float *gda, float *gdb, float2 *partial) {
+    grid_dep_enter();
     __shared__ float s_red[2][kFuseThreads / 32];
     const int64_t stride = (int64_t)gridDim.x * kFuseThreads;
     float sc = 0.f, sd = 0.f;
@@ -64,6 +65,7 @@ distill_kernel(const float *__restrict__ ca, const float *__restrict__ cb, const
 
 __global__ void __launch_bounds__(kFuseThreads)
 distill_finalize_kernel(const float2 *__restrict__ partial, int nb, double inv_c, double inv_d, double *loss) {
+    grid_dep_enter();
     __shared__ double s_red[2][kFuseThreads / 32];
     double sc = 0.0, sd = 0.0;
     for (int i = threadIdx.x; i < nb; i += kFuseThreads) {
@@ -96,6 +98,7 @@ distill_finalize_kernel(const float2 *__restrict__ partial, int nb, double inv_c
 __global__ void __launch_bounds__(kFuseThreads)
 adam_kernel(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m, float *__restrict__ v, int64_t n,
             float lr, float b1, float b2, float eps, float c1, float c2) {
+    grid_dep_enter();
     const int64_t stride = (int64_t)gridDim.x * kFuseThreads;
     for (int64_t i = (int64_t)blockIdx.x * kFuseThreads + threadIdx.x; i < n; i += stride) {
         const float gi = g[i];
@@ -139,11 +142,11 @@ vpgs_status vpgs_distill_loss(void *ws, size_t ws_bytes, const float *rgb_a, con
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     float2 *partial = static_cast<float2 *>(ws);
     VPGS_LAUNCH("distill", s,
-                distill_kernel<<<nb, kFuseThreads, 0, s>>>(rgb_a, rgb_b, depth_a, depth_b, n_col, n_dep, gc, gd,
+                launch_k(distill_kernel, nb, kFuseThreads, 0, s, rgb_a, rgb_b, depth_a, depth_b, n_col, n_dep, gc, gd,
                                                            dL_drgb_a, dL_drgb_b, dL_ddepth_a, dL_ddepth_b, partial));
     if (cudaGetLastError() != cudaSuccess) return VPGS_ERR_CUDA;
     VPGS_LAUNCH("distill_finalize", s,
-                distill_finalize_kernel<<<1, kFuseThreads, 0, s>>>(partial, nb, 1.0 / (double)n_col,
+                launch_k(distill_finalize_kernel, 1, kFuseThreads, 0, s, partial, nb, 1.0 / (double)n_col,
                                                                    depth_a ? 1.0 / (double)(P * n_views) : 0.0,
                                                                    loss_out));
     return cudaGetLastError() == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
@@ -160,7 +163,7 @@ vpgs_status vpgs_adam_step(float *params, float *grads, float *m, float *v, int6
     const float c1 = (float)(1.0 / (1.0 - std::pow((double)b1, step)));
     const float c2 = (float)(1.0 / (1.0 - std::pow((double)b2, step)));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    VPGS_LAUNCH("adam", s, adam_kernel<<<fuse_grid(n), kFuseThreads, 0, s>>>(params, grads, m, v, n, lr, b1, b2,
+    VPGS_LAUNCH("adam", s, launch_k(adam_kernel, fuse_grid(n), kFuseThreads, 0, s, params, grads, m, v, n, lr, b1, b2,
                                                                            eps, c1, c2));
     return cudaGetLastError() == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
 }

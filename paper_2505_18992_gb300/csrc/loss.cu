@@ -101,6 +101,7 @@ VPGS_D double block_sum_f64(double v, double *s_red) {
 
 __global__ void __launch_bounds__(kLT * kLT)
 ssim_moments_kernel(LossArgs a) {
+    grid_dep_enter();
     __shared__ float s_in[5][kLH][kLH + 1];  // x, y, x^2, y^2, xy
     __shared__ float s_h[5][kLH][kLT];
     __shared__ float s_red[8];
@@ -178,6 +179,7 @@ ssim_moments_kernel(LossArgs a) {
 
 __global__ void __launch_bounds__(kLT * kLT)
 ssim_grad_kernel(LossArgs a, int64_t n_partial) {
+    grid_dep_enter();
     __shared__ float s_in[3][kLH][kLH + 1];
     __shared__ float s_h[3][kLH][kLT];
     __shared__ double s_red[8];
@@ -260,10 +262,10 @@ cudaError_t launch_mapping_loss(void *ws, const float *rgb, const float *target,
     a.partial = reinterpret_cast<double *>(b + up(3 * sizeof(float) * (size_t)planes * HW));
     a.loss = loss; a.d_rgb = d_rgb; a.d_depth = d_depth; a.d_scales = d_scales;
     const dim3 grid((unsigned)a.tiles_x, (unsigned)a.tiles_y, (unsigned)planes);
-    VPGS_LAUNCH("ssim_moments", s, ssim_moments_kernel<<<grid, kLT * kLT, 0, s>>>(a));
+    VPGS_LAUNCH("ssim_moments", s, launch_k(ssim_moments_kernel, grid, kLT * kLT, 0, s, a));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    VPGS_LAUNCH("ssim_grad", s, ssim_grad_kernel<<<grid, kLT * kLT, 0, s>>>(a, (int64_t)grid.x * grid.y * grid.z));
+    VPGS_LAUNCH("ssim_grad", s, launch_k(ssim_grad_kernel, grid, kLT * kLT, 0, s, a, (int64_t)grid.x * grid.y * grid.z));
     return cudaGetLastError();
 }
 

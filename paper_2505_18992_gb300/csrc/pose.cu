@@ -38,6 +38,7 @@ __device__ void se3_exp(const double xi[6], double R[9], double t[3]) {
 
 __global__ void pose_step_kernel(double *T_cw, double *dpose, double *adam, int V, double lr_rho,
                                  double lr_phi) {
+    grid_dep_enter();
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
     double xi[6];
@@ -74,7 +75,7 @@ __global__ void pose_step_kernel(double *T_cw, double *dpose, double *adam, int 
 
 cudaError_t launch_pose_step(double *T_cw, double *dpose, double *adam, int V, double lr_rho,
                              double lr_phi, cudaStream_t s) {
-    VPGS_LAUNCH("pose_step", s, pose_step_kernel<<<(V + 63) / 64, 64, 0, s>>>(T_cw, dpose, adam, V,
+    VPGS_LAUNCH("pose_step", s, launch_k(pose_step_kernel, (V + 63) / 64, 64, 0, s, T_cw, dpose, adam, V,
                                                                               lr_rho, lr_phi));
     return cudaGetLastError();
 }
