@@ -86,7 +86,17 @@ VPGS_D void stage(const Rec &r, float ox, float oy, float4 &a, float4 &b, float4
     c = make_float4(r.r2.z, r.r2.w, r.r3.x, r.r2.y);
 }
 
-__global__ void __launch_bounds__(kMaxThreads)
+// register cap of the forward (0: only the 512-thread launch bound)
+#ifndef VPGS_FWD_MAXREG
+#define VPGS_FWD_MAXREG 0
+#endif
+#if VPGS_FWD_MAXREG > 0
+#define VPGS_FWD_BOUNDS __maxnreg__(VPGS_FWD_MAXREG)
+#else
+#define VPGS_FWD_BOUNDS __launch_bounds__(kMaxThreads)
+#endif
+
+__global__ void VPGS_FWD_BOUNDS
 composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ ival,
                      const uint2 *__restrict__ ranges, int n_tiles, CamParams cam, OptParams o,
                      vpgs_images out, const uint32_t *status, uint32_t *work) {
@@ -284,7 +294,18 @@ VPGS_D bool pair_grad(PixState &p, int jj, const PairEval &e, float dx, float dy
 
 constexpr int kPartStride = 11;  // floats per (warp, Gaussian) partial, padded against bank conflicts
 
-__global__ void __launch_bounds__(kMaxThreads)
+// register cap of the backward (0: only the 512-thread launch bound); 80
+// allows 25 resident warps per SM instead of 21 and loses nothing to spills
+#ifndef VPGS_BWD_MAXREG
+#define VPGS_BWD_MAXREG 80
+#endif
+#if VPGS_BWD_MAXREG > 0
+#define VPGS_BWD_BOUNDS __maxnreg__(VPGS_BWD_MAXREG)
+#else
+#define VPGS_BWD_BOUNDS __launch_bounds__(kMaxThreads)
+#endif
+
+__global__ void VPGS_BWD_BOUNDS
 composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ ival,
                      const uint2 *__restrict__ ranges, int n_tiles, CamParams cam, OptParams o,
                      const float *__restrict__ t_final, const int32_t *__restrict__ n_iter,
