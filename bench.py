@@ -220,9 +220,10 @@ def algorithmic_bytes(kernel: str, N: int, Nv: int, M: int, P: int):
 # arithmetic: evaluating alpha (offset 2, whitened form 6, power 4, exp 2,
 # opacity 1, clamp 1 = 17) and, for blended pairs, the blend (forward: 1 - alpha,
 # T update, weight, 4 accumulations = 11) or the gradient (backward: T recovery 4,
-# weight 1, colour/depth grads 8, dalpha 18, behind-colour update 12, opacity
-# and power 3, mean 8, conic 9 = 63).
-PAIR_FLOPS = {"eval": 17, "blend_fwd": 11, "blend_bwd": 63}
+# weight 1, colour/depth grads 8, dalpha 13, behind-colour update 8, opacity
+# and power 3, mean 4, conic 8 = 49; the whitening rows of the mean gradient
+# are applied once per Gaussian, not per pair).
+PAIR_FLOPS = {"eval": 17, "blend_fwd": 11, "blend_bwd": 49}
 
 
 def alu_peak_tflops(sm_mhz):

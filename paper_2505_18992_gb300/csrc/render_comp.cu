@@ -18,9 +18,9 @@
 // T_{i+1} / (1 - alpha_i), and keeps the colour/depth "behind" each Gaussian,
 //   B <- alpha c + (1 - alpha) B   (B starts at the background),
 // giving dC/dalpha_i = T_i (c_i - B_i), dA/dalpha_i = T_final / (1 - alpha_i).
-// Per-Gaussian 2D gradients (u, v, conic a b c, opacity, rgb, z) of a warp are
-// summed by a transpose reduction (16 shuffles for 10 values) and added with
-// one atomic per value per warp.
+// Per-Gaussian 2D gradient sums (mean terms sum dpow t1 and sum dpow t2, conic
+// a b c, opacity, rgb, z) of a warp are summed by a transpose reduction (12
+// shuffles for 10 values) and added with one atomic per value per warp.
 #include "internal.h"
 #include "profiler.h"
 
@@ -248,7 +248,7 @@ VPGS_D void warp_reduce10(float (&a)[10], int lane) {
 
 // per-pixel backward state
 struct PixState {
-    float T, T_fin, gC0, gC1, gC2, gD, gA, B0, B1, B2, BD;
+    float T, gAT, gC0, gC1, gC2, gD, B0, B1, B2, BD;  // gAT = dL/dalpha_pixel * T_final
     int last;
 };
 
@@ -261,10 +261,10 @@ VPGS_D bool pair_grad(PixState &p, int jj, const PairEval &e, float dx, float dy
 #if VPGS_BWD_RCP
     const float iom = __fdividef(1.f, om);  // om >= 1 - alpha_max > 0
     p.T *= iom;
-    const float tfo = p.T_fin * iom;
+    const float gat = p.gAT * iom;  // dA/dalpha_i = T_final / (1 - alpha_i)
 #else
     p.T = p.T / om;
-    const float tfo = p.T_fin / om;
+    const float gat = p.gAT / om;
 #endif
     const float w = e.alpha * p.T;
     v[6] = fmaf(w, p.gC0, v[6]);
@@ -273,21 +273,23 @@ VPGS_D bool pair_grad(PixState &p, int jj, const PairEval &e, float dx, float dy
     v[9] = fmaf(w, p.gD, v[9]);
     // colour / depth behind this Gaussian: B <- alpha c + (1 - alpha) B = B + alpha (c - B)
     const float d0 = c.x - p.B0, d1 = c.y - p.B1, d2 = c.z - p.B2, dz = c.w - p.BD;
-    const float dA = (p.gC0 * d0 + p.gC1 * d1 + p.gC2 * d2 + p.gD * dz) * p.T + p.gA * tfo;
+    const float dA = (p.gC0 * d0 + p.gC1 * d1 + p.gC2 * d2 + p.gD * dz) * p.T + gat;
     p.B0 = fmaf(e.alpha, d0, p.B0);
     p.B1 = fmaf(e.alpha, d1, p.B1);
     p.B2 = fmaf(e.alpha, d2, p.B2);
     p.BD = fmaf(e.alpha, dz, p.BD);
     if (b.z * e.G <= o.alpha_max) {
-        // slots 0-4 hold sums without their constant factors (2 ln 2 for the mean,
-        // -1/2, -1, -1/2 for the conic), applied once per Gaussian by the preprocess backward
+        // slots 0-4 hold sums without their per-Gaussian factors, applied once per
+        // Gaussian by the preprocess backward: the whitening rows and 2 ln 2 for the
+        // mean (slots 0, 1 = sum dpow t1, sum dpow t2), -1/2, -1, -1/2 for the conic
         const float dpow = dA * e.alpha;
         v[5] = fmaf(dA, e.G, v[5]);
-        v[0] = fmaf(dpow, a.z * e.t1 + b.x * e.t2, v[0]);
-        v[1] = fmaf(dpow, a.w * e.t1 + b.y * e.t2, v[1]);
-        v[2] = fmaf(dpow, dx * dx, v[2]);
-        v[3] = fmaf(dpow, dx * dy, v[3]);
-        v[4] = fmaf(dpow, dy * dy, v[4]);
+        v[0] = fmaf(dpow, e.t1, v[0]);
+        v[1] = fmaf(dpow, e.t2, v[1]);
+        const float pdx = dpow * dx;
+        v[2] = fmaf(pdx, dx, v[2]);
+        v[3] = fmaf(pdx, dy, v[3]);
+        v[4] = fmaf(dpow * dy, dy, v[4]);
     }
     return true;
 }
@@ -364,7 +366,8 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
 #pragma unroll
         for (int q = 0; q < kPix; ++q) {
             PixState &p = ps[q];
-            p.T = 1.f; p.gC0 = p.gC1 = p.gC2 = p.gD = p.gA = 0.f; p.last = 0;
+            p.T = 1.f; p.gC0 = p.gC1 = p.gC2 = p.gD = 0.f; p.last = 0;
+            float gA = 0.f;
             p.B0 = o.bg0; p.B1 = o.bg1; p.B2 = o.bg2; p.BD = 0.f;
             const int py = tc.ty * cam.tile_h + kPix * ly + q;
             if (px < cam.W && py < cam.H) {
@@ -376,9 +379,9 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                     p.gC0 = gp[0]; p.gC1 = gp[HW]; p.gC2 = gp[2 * HW];
                 }
                 if (dL_ddepth) p.gD = dL_ddepth[pix];
-                if (dL_dalpha) p.gA = dL_dalpha[pix];
+                if (dL_dalpha) gA = dL_dalpha[pix];
             }
-            p.T_fin = p.T;
+            p.gAT = gA * p.T;  // p.T holds T_final here
             my_max = max(my_max, p.last);
         }
         // the warp's own list length: warps whose pixels stop early skip the tail

@@ -374,8 +374,12 @@ preprocess_bwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamPara
             float2 *z2 = reinterpret_cast<float2 *>(ws.g2d + 10 * i);
 #pragma unroll
             for (int k = 0; k < 5; ++k) z2[k] = make_float2(0.f, 0.f);
-            // the compositing backward leaves out these constant factors (see pair_grad)
-            const float gu = a01.x * kInvExp2Half, gv = a01.y * kInvExp2Half;
+            // the compositing backward leaves out these per-Gaussian factors (see
+            // pair_grad): the mean's slots hold sum dpow t1 and sum dpow t2, turned
+            // into d/du, d/dv by the whitening rows of the record the pixels saw
+            const float4 w = ws.rec[i].r1;  // (w1x, w1y, w2x, w2y)
+            const float gu = (w.x * a01.x + w.z * a01.y) * kInvExp2Half;
+            const float gv = (w.y * a01.x + w.w * a01.y) * kInvExp2Half;
             const float ga = -0.5f * a23.x, gb = -a23.y, gcn = -0.5f * a45.x;
             go += a45.y;
             gc[0] += a67.x; gc[1] += a67.y; gc[2] += a89.x;
