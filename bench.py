@@ -220,10 +220,10 @@ def algorithmic_bytes(kernel: str, N: int, Nv: int, M: int, P: int):
 # arithmetic: evaluating alpha (offset 2, whitened form 6, power 4, exp 2,
 # opacity 1, clamp 1 = 17) and, for blended pairs, the blend (forward: 1 - alpha,
 # T update, weight, 4 accumulations = 11) or the gradient (backward: T recovery 4,
-# weight 1, colour/depth grads 8, dalpha 13, behind-colour update 8, opacity
-# and power 3, mean 4, conic 8 = 49; the whitening rows of the mean gradient
-# are applied once per Gaussian, not per pair).
-PAIR_FLOPS = {"eval": 17, "blend_fwd": 11, "blend_bwd": 49}
+# weight 1, colour/depth grads 8, dalpha 10 (g . c, minus g . B, times T plus
+# the alpha term), update of g . B 2, opacity and power 3, mean 4, conic 8 = 40;
+# the whitening rows of the mean gradient are applied once per Gaussian).
+PAIR_FLOPS = {"eval": 17, "blend_fwd": 11, "blend_bwd": 40}
 
 
 def alu_peak_tflops(sm_mhz):

@@ -18,6 +18,8 @@
 // T_{i+1} / (1 - alpha_i), and keeps the colour/depth "behind" each Gaussian,
 //   B <- alpha c + (1 - alpha) B   (B starts at the background),
 // giving dC/dalpha_i = T_i (c_i - B_i), dA/dalpha_i = T_final / (1 - alpha_i).
+// Only g . B enters dL/dalpha (g the pixel's upstream gradient), so each pixel
+// carries that scalar instead of B.
 // Per-Gaussian 2D gradient sums (mean terms sum dpow t1 and sum dpow t2, conic
 // a b c, opacity, rgb, z) of a warp are summed by a transpose reduction (12
 // shuffles for 10 values) and added with one atomic per value per warp.
@@ -247,8 +249,10 @@ VPGS_D void warp_reduce10(float (&a)[10], int lane) {
 }
 
 // per-pixel backward state
+// beta = g . B: the upstream gradient (colour, depth) dotted with the colour /
+// depth "behind" the current Gaussian, the only way B enters the gradient
 struct PixState {
-    float T, gAT, gC0, gC1, gC2, gD, B0, B1, B2, BD;  // gAT = dL/dalpha_pixel * T_final
+    float T, gAT, gC0, gC1, gC2, gD, beta;  // gAT = dL/dalpha_pixel * T_final
     int last;
 };
 
@@ -271,13 +275,11 @@ VPGS_D bool pair_grad(PixState &p, int jj, const PairEval &e, float dx, float dy
     v[7] = fmaf(w, p.gC1, v[7]);
     v[8] = fmaf(w, p.gC2, v[8]);
     v[9] = fmaf(w, p.gD, v[9]);
-    // colour / depth behind this Gaussian: B <- alpha c + (1 - alpha) B = B + alpha (c - B)
-    const float d0 = c.x - p.B0, d1 = c.y - p.B1, d2 = c.z - p.B2, dz = c.w - p.BD;
-    const float dA = (p.gC0 * d0 + p.gC1 * d1 + p.gC2 * d2 + p.gD * dz) * p.T + gat;
-    p.B0 = fmaf(e.alpha, d0, p.B0);
-    p.B1 = fmaf(e.alpha, d1, p.B1);
-    p.B2 = fmaf(e.alpha, d2, p.B2);
-    p.BD = fmaf(e.alpha, dz, p.BD);
+    // dL/dalpha_i = T_i g . (c_i - B_i) + gat; behind this Gaussian
+    // B <- B + alpha (c - B), so beta = g . B <- beta + alpha (g . c - beta)
+    const float diff = fmaf(p.gC0, c.x, fmaf(p.gC1, c.y, fmaf(p.gC2, c.z, p.gD * c.w))) - p.beta;
+    const float dA = fmaf(diff, p.T, gat);
+    p.beta = fmaf(e.alpha, diff, p.beta);
     if (b.z * e.G <= o.alpha_max) {
         // slots 0-4 hold sums without their per-Gaussian factors, applied once per
         // Gaussian by the preprocess backward: the whitening rows and 2 ln 2 for the
@@ -368,7 +370,6 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
             PixState &p = ps[q];
             p.T = 1.f; p.gC0 = p.gC1 = p.gC2 = p.gD = 0.f; p.last = 0;
             float gA = 0.f;
-            p.B0 = o.bg0; p.B1 = o.bg1; p.B2 = o.bg2; p.BD = 0.f;
             const int py = tc.ty * cam.tile_h + kPix * ly + q;
             if (px < cam.W && py < cam.H) {
                 const int64_t pix = (int64_t)tc.v * HW + (int64_t)py * cam.W + px;
@@ -382,6 +383,7 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                 if (dL_dalpha) gA = dL_dalpha[pix];
             }
             p.gAT = gA * p.T;  // p.T holds T_final here
+            p.beta = fmaf(p.gC0, o.bg0, fmaf(p.gC1, o.bg1, p.gC2 * o.bg2));  // B starts at the background
             my_max = max(my_max, p.last);
         }
         // the warp's own list length: warps whose pixels stop early skip the tail
