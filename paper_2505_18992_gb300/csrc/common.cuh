@@ -338,7 +338,7 @@ constexpr int kSortThreads = 256;
 #define VPGS_DEPTH_SORT_ITEMS 4
 #endif
 #ifndef VPGS_TILE_SORT_ITEMS
-#define VPGS_TILE_SORT_ITEMS 32
+#define VPGS_TILE_SORT_ITEMS 16
 #endif
 constexpr int kDepthSortItems = VPGS_DEPTH_SORT_ITEMS;  // keys per thread in the depth sort
 constexpr int kTileSortItems = VPGS_TILE_SORT_ITEMS;    // keys per thread in the tile-id sort

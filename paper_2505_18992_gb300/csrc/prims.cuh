@@ -194,6 +194,21 @@ struct SortPass {
     int shift, bits;
 };
 
+// Lanes of the warp holding the same digit: one ballot per digit bit (a lane
+// keeps the lanes that agree with it on every bit), which is cheaper than the
+// hardware match for digits of up to 8 bits.  Items past the end (valid =
+// false) match only themselves.
+VPGS_D uint32_t match_digit(uint32_t d, bool valid, int bits, int lane) {
+    uint32_t m = __ballot_sync(0xffffffffu, valid);
+    if (!valid) m = 1u << lane;
+    for (int b = 0; b < bits; ++b) {
+        const uint32_t bit = (d >> b) & 1u;
+        const uint32_t bb = __ballot_sync(0xffffffffu, bit != 0u);
+        m &= bit ? bb : ~bb;
+    }
+    return m;
+}
+
 // predecessor tiles read per look-back step of a one-sweep pass
 #ifndef VPGS_LOOK_DEPTH
 #define VPGS_LOOK_DEPTH 16
@@ -272,7 +287,7 @@ radix_onesweep_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__res
     // per-warp digit counts
 #pragma unroll
     for (int s = 0; s < ITEMS; ++s) {
-        uint32_t m = __match_any_sync(0xffffffffu, d[s]);
+        const uint32_t m = match_digit(d[s], d[s] < kRadix, pass.bits, lane);
         if (d[s] < kRadix && (m & lanemask_lt()) == 0) s_cnt[warp][d[s]] += __popc(m);
         __syncwarp();
     }
@@ -350,7 +365,7 @@ radix_onesweep_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__res
     // order, warps in order
 #pragma unroll
     for (int s = 0; s < ITEMS; ++s) {
-        const uint32_t m = __match_any_sync(0xffffffffu, d[s]);
+        const uint32_t m = match_digit(d[s], d[s] < kRadix, pass.bits, lane);
         const uint32_t rank = __popc(m & lanemask_lt());
         if (d[s] < kRadix) {
             const uint32_t lp = s_cnt[warp][d[s]] + rank;
