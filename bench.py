@@ -472,15 +472,36 @@ def run_ours(a):
         h_pose = torch.empty((1, 6), dtype=torch.float64).pin_memory()
         d_in = g + [T, g_rgb, g_d]
 
+        side = torch.cuda.Stream(device=dev)
+        n_fwd = len(g) + 1  # the Gaussians and the pose feed the forward
+
         def e2e_step():
-            for d_t, h_t in zip(d_in, h_in):
+            # every copy of the step stays inside it: the upstream gradients
+            # (needed by the backward only) go in beside the forward, the
+            # images come back beside the backward
+            cur = torch.cuda.current_stream()
+            for d_t, h_t in zip(d_in[:n_fwd], h_in[:n_fwd]):
                 d_t.copy_(h_t, non_blocking=True)
-            step()
-            for k in h_out:
-                h_out[k].copy_(out[k], non_blocking=True)
+            side.wait_stream(cur)
+            with torch.cuda.stream(side):
+                for d_t, h_t in zip(d_in[n_fwd:], h_in[n_fwd:]):
+                    d_t.copy_(h_t, non_blocking=True)
+                grads_in = torch.cuda.Event()
+                grads_in.record(side)
+            for t in grads.values():
+                t.zero_()
+            dpose.zero_()
+            r.forward(*g, T, out=out, check=False)
+            side.wait_stream(cur)
+            with torch.cuda.stream(side):
+                for k in h_out:
+                    h_out[k].copy_(out[k], non_blocking=True)
+            cur.wait_event(grads_in)
+            r.backward(*g, T, out, g_rgb, g_d, None, grads=grads, dpose=dpose)
             for k in h_gr:
                 h_gr[k].copy_(grads[k], non_blocking=True)
             h_pose.copy_(dpose, non_blocking=True)
+            cur.wait_stream(side)
 
         ms_e = timed(e2e_step, min(a.steps, 50))
         e_ms = sum(ms_e) / len(ms_e)
