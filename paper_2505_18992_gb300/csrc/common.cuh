@@ -348,7 +348,10 @@ constexpr int kMaxSortPasses = 8;
 
 // scan geometry
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 16;
+#ifndef VPGS_SCAN_ITEMS
+#define VPGS_SCAN_ITEMS 8
+#endif
+constexpr int kScanItems = VPGS_SCAN_ITEMS;  // items per thread of a scan tile
 constexpr int kScanTile = kScanThreads * kScanItems;
 
 // bounded spin for decoupled look-back: the predecessor always holds an
