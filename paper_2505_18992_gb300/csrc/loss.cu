@@ -14,7 +14,8 @@
 //   A = dS/dm1, B = dS/dm2, C = dS/dm3 at each p,
 // so the gradient is a second blur, of A, B, C.  Two kernels, one 16x16 output
 // tile per block and channel, separable 11-tap blurs from a shared-memory tile
-// with a 5-pixel halo:
+// with a 5-pixel halo, each thread producing kU neighbouring outputs per pass
+// from one (kU + 10)-value window (the blurs are bound by shared-memory loads):
 //   1. moments -> S, A, B, C (A, B, C to the workspace), block sums of S and
 //      |x - y|; the same blocks also take the depth term and the volume term
 //      (grid-strided) and write their gradients;
@@ -31,6 +32,11 @@ constexpr int kLT = 16;             // output tile edge
 constexpr int kLR = 5;              // window radius
 constexpr int kLH = kLT + 2 * kLR;  // tile edge with halo (26)
 constexpr float kC1 = 0.01f * 0.01f, kC2 = 0.03f * 0.03f;
+#ifndef VPGS_SSIM_U
+#define VPGS_SSIM_U 2
+#endif
+constexpr int kU = VPGS_SSIM_U;          // neighbouring outputs per thread and blur pass
+constexpr int kWin = kU + 10;            // their window
 
 struct LossArgs {
     const float *rgb, *target, *depth, *tdepth, *scales;
@@ -45,29 +51,46 @@ struct LossArgs {
     float *d_rgb, *d_depth, *d_scales;
 };
 
-// separable blur of n maps held in s_in[n][kLH][kLH + 1] into out[n] for
-// thread (ty, tx); s_h is scratch [n][kLH][kLT]
+// Separable 11-tap blurs, register-blocked: each thread produces kU
+// neighbouring outputs from one (kU + 10)-value window, so a tap costs one
+// shared load per kU outputs instead of one per output.
+//   horizontal: s_src[NM][kLH][kLH + 1] -> s_h[NM][kLH][kLT + 1] (26 x 16)
+//   vertical:   s_h -> kU vertically adjacent outputs (r0 .. r0 + kU - 1, c)
+//               for the kLT * kLT / kU work items (threads tid < kLT * kLT / kU)
 template <int NM>
-VPGS_D void blur_tile(const float (*s_in)[kLH][kLH + 1], float (*s_h)[kLH][kLT], const float *g, int tid,
-                      float (&out)[NM]) {
-    for (int i = tid; i < kLH * kLT; i += kLT * kLT) {
-        const int r = i / kLT, c = i % kLT;
+VPGS_D void hblur(const float (*s_src)[kLH][kLH + 1], float (*s_h)[kLH][kLT + 1], const float *g, int tid) {
+    for (int w = tid; w < kLH * (kLT / kU); w += kLT * kLT) {
+        const int r = w / (kLT / kU), c0 = kU * (w % (kLT / kU));
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
-            float acc = 0.f;
+            float v[kWin];
 #pragma unroll
-            for (int k = 0; k < 11; ++k) acc = fmaf(g[k], s_in[m][r][c + k], acc);
-            s_h[m][r][c] = acc;
+            for (int j = 0; j < kWin; ++j) v[j] = s_src[m][r][c0 + j];
+            float o[kU] = {};
+#pragma unroll
+            for (int k = 0; k < 11; ++k)
+#pragma unroll
+                for (int u = 0; u < kU; ++u) o[u] = fmaf(g[k], v[k + u], o[u]);
+#pragma unroll
+            for (int u = 0; u < kU; ++u) s_h[m][r][c0 + u] = o[u];
         }
     }
-    __syncthreads();
-    const int ty = tid / kLT, tx = tid % kLT;
+}
+
+template <int NM>
+VPGS_D void vblur(const float (*s_h)[kLH][kLT + 1], const float *g, int r0, int c, float (&o)[kU][NM]) {
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
-        float acc = 0.f;
+        float v[kWin];
 #pragma unroll
-        for (int k = 0; k < 11; ++k) acc = fmaf(g[k], s_h[m][ty + k][tx], acc);
-        out[m] = acc;
+        for (int j = 0; j < kWin; ++j) v[j] = s_h[m][r0 + j][c];
+        float acc[kU] = {};
+#pragma unroll
+        for (int k = 0; k < 11; ++k)
+#pragma unroll
+            for (int u = 0; u < kU; ++u) acc[u] = fmaf(g[k], v[k + u], acc[u]);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) o[u][m] = acc[u];
     }
 }
 
@@ -102,8 +125,8 @@ VPGS_D double block_sum_f64(double v, double *s_red) {
 __global__ void __launch_bounds__(kLT * kLT)
 ssim_moments_kernel(LossArgs a) {
     grid_dep_enter();
-    __shared__ float s_in[5][kLH][kLH + 1];  // x, y, x^2, y^2, xy
-    __shared__ float s_h[5][kLH][kLT];
+    __shared__ float s_in[2][kLH][kLH + 1];   // x, y with the halo
+    __shared__ float s_h[5][kLH][kLT + 1];    // horizontal blurs of x, y, x^2, y^2, xy
     __shared__ float s_red[8];
     const int tid = threadIdx.x;
     const int plane = blockIdx.z;            // view * 3 + channel
@@ -117,27 +140,62 @@ ssim_moments_kernel(LossArgs a) {
             xv = X[(int64_t)gy * a.W + gx];
             yv = Y[(int64_t)gy * a.W + gx];
         }
-        s_in[0][r][c] = xv; s_in[1][r][c] = yv;
-        s_in[2][r][c] = xv * xv; s_in[3][r][c] = yv * yv; s_in[4][r][c] = xv * yv;
+        s_in[0][r][c] = xv;
+        s_in[1][r][c] = yv;
     }
     __syncthreads();
-    float m[5];
-    blur_tile<5>(s_in, s_h, a.g, tid, m);
-    const int ty = tid / kLT, tx = tid % kLT, px = blockIdx.x * kLT + tx, py = blockIdx.y * kLT + ty;
+    // horizontal: the five moment maps from one window of x and y
+    for (int w = tid; w < kLH * (kLT / kU); w += kLT * kLT) {
+        const int r = w / (kLT / kU), c0 = kU * (w % (kLT / kU));
+        float xs[kWin], ys[kWin];
+#pragma unroll
+        for (int j = 0; j < kWin; ++j) {
+            xs[j] = s_in[0][r][c0 + j];
+            ys[j] = s_in[1][r][c0 + j];
+        }
+        float o[5][kU] = {};
+#pragma unroll
+        for (int k = 0; k < 11; ++k) {
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const float xv = xs[k + u], yv = ys[k + u], gk = a.g[k];
+                o[0][u] = fmaf(gk, xv, o[0][u]);
+                o[1][u] = fmaf(gk, yv, o[1][u]);
+                o[2][u] = fmaf(gk, xv * xv, o[2][u]);
+                o[3][u] = fmaf(gk, yv * yv, o[3][u]);
+                o[4][u] = fmaf(gk, xv * yv, o[4][u]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < 5; ++m)
+#pragma unroll
+            for (int u = 0; u < kU; ++u) s_h[m][r][c0 + u] = o[m][u];
+    }
+    __syncthreads();
     float ssum = 0.f, l1 = 0.f;
-    if (px < a.W && py < a.H) {
-        const float mx = m[0], my = m[1];
-        const float sxx = m[2] - mx * mx, syy = m[3] - my * my, sxy = m[4] - mx * my;
-        const float n1 = 2.f * mx * my + kC1, n2 = 2.f * sxy + kC2;
-        const float d1 = mx * mx + my * my + kC1, d2 = sxx + syy + kC2;
-        const float id = 1.f / (d1 * d2);
-        const float S = n1 * n2 * id;
-        const int64_t o = plane * HW + (int64_t)py * a.W + px;
-        a.A[o] = (2.f * my * (n2 - n1) - 2.f * mx * S * (d2 - d1)) * id;
-        a.B[o] = -S / d2;
-        a.C[o] = 2.f * n1 * id;
-        ssum = S;
-        l1 = fabsf(s_in[0][ty + kLR][tx + kLR] - s_in[1][ty + kLR][tx + kLR]);
+    if (tid < kLT * kLT / kU) {
+        const int tx = tid % kLT, r0 = kU * (tid / kLT);
+        float mm[kU][5];
+        vblur<5>(s_h, a.g, r0, tx, mm);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const float *m = mm[u];
+            const int ty = r0 + u, px = blockIdx.x * kLT + tx, py = blockIdx.y * kLT + ty;
+            if (px < a.W && py < a.H) {
+                const float mx = m[0], my = m[1];
+                const float sxx = m[2] - mx * mx, syy = m[3] - my * my, sxy = m[4] - mx * my;
+                const float n1 = 2.f * mx * my + kC1, n2 = 2.f * sxy + kC2;
+                const float d1 = mx * mx + my * my + kC1, d2 = sxx + syy + kC2;
+                const float id = 1.f / (d1 * d2);
+                const float S = n1 * n2 * id;
+                const int64_t o = plane * HW + (int64_t)py * a.W + px;
+                a.A[o] = (2.f * my * (n2 - n1) - 2.f * mx * S * (d2 - d1)) * id;
+                a.B[o] = -S / d2;
+                a.C[o] = 2.f * n1 * id;
+                ssum += S;
+                l1 += fabsf(s_in[0][ty + kLR][tx + kLR] - s_in[1][ty + kLR][tx + kLR]);
+            }
+        }
     }
     // depth and volume terms, grid-strided over all blocks of this launch
     const int64_t nblk = (int64_t)gridDim.x * gridDim.y * gridDim.z;
@@ -181,7 +239,7 @@ __global__ void __launch_bounds__(kLT * kLT)
 ssim_grad_kernel(LossArgs a, int64_t n_partial) {
     grid_dep_enter();
     __shared__ float s_in[3][kLH][kLH + 1];
-    __shared__ float s_h[3][kLH][kLT];
+    __shared__ float s_h[3][kLH][kLT + 1];
     __shared__ double s_red[8];
     const int tid = threadIdx.x;
     const int plane = blockIdx.z;
@@ -216,17 +274,25 @@ ssim_grad_kernel(LossArgs a, int64_t n_partial) {
         s_in[0][r][c] = va; s_in[1][r][c] = vb; s_in[2][r][c] = vc;
     }
     __syncthreads();
-    float m[3];
-    blur_tile<3>(s_in, s_h, a.g, tid, m);
-    const int ty = tid / kLT, tx = tid % kLT, px = blockIdx.x * kLT + tx, py = blockIdx.y * kLT + ty;
-    if (px < a.W && py < a.H) {
-        const int64_t o = plane * HW + (int64_t)py * a.W + px;
-        const float x = a.rgb[o], y = a.target[o];
-        const float dssim = m[0] + 2.f * x * m[1] + y * m[2];
-        const float e = x - y;
-        const float inv_n = (float)(1.0 / n_col);
-        // L_c + (1 - lambda) L1 share the sign term; the SSIM term enters as -lambda mean(S)
-        a.d_rgb[o] = ((2.f - a.lambda_ssim) * (float)((e > 0.f) - (e < 0.f)) - a.lambda_ssim * dssim) * inv_n;
+    hblur<3>(s_in, s_h, a.g, tid);
+    __syncthreads();
+    if (tid >= kLT * kLT / kU) return;
+    const int tx = tid % kLT, r0 = kU * (tid / kLT);
+    float mm[kU][3];
+    vblur<3>(s_h, a.g, r0, tx, mm);
+    const float inv_n = (float)(1.0 / n_col);
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+        const float *m = mm[u];
+        const int px = blockIdx.x * kLT + tx, py = blockIdx.y * kLT + r0 + u;
+        if (px < a.W && py < a.H) {
+            const int64_t o = plane * HW + (int64_t)py * a.W + px;
+            const float x = a.rgb[o], y = a.target[o];
+            const float dssim = m[0] + 2.f * x * m[1] + y * m[2];
+            const float e = x - y;
+            // L_c + (1 - lambda) L1 share the sign term; the SSIM term enters as -lambda mean(S)
+            a.d_rgb[o] = ((2.f - a.lambda_ssim) * (float)((e > 0.f) - (e < 0.f)) - a.lambda_ssim * dssim) * inv_n;
+        }
     }
 }
 
