@@ -341,6 +341,25 @@ vpgs_status vpgs_mapping_loss(void *ws, size_t ws_bytes, const float *rgb, const
                               const int32_t *n_dev, const vpgs_loss_weights *w, double *loss_out,
                               float *dL_drgb, float *dL_ddepth, float *dL_dscales, vpgs_stream stream);
 
+/* Coarse-tracking loss (Sec. III-B): the photometric and depth L1 errors of
+ * the render at the current pose, per view v (the colour and depth terms of
+ * the mapping loss, normalised per view):
+ *   L_t(v) = (1/3HW) sum_{c,p} |I^ - I| + lambda_d (1/HW) sum_{p: D(p) > 0} |D^ - D|
+ * and the gradient of sum_v L_t(v): sign(I^ - I) / 3HW and, where D > 0,
+ * lambda_d sign(D^ - D) / HW (sign(0) = 0; 0 where D <= 0).
+ *   rgb, target_rgb [V,3,H,W] float32 device (required).
+ *   depth, target_depth [V,H,W] float32 device, both or neither (no depth term).
+ *   lambda_d >= 0, finite.
+ *   loss_out [V] float64 device, overwritten (may be NULL).
+ *   dL_drgb [V,3,H,W], dL_ddepth [V,H,W] float32 device: overwritten (each may
+ *     be NULL; dL_ddepth is not touched without depths).
+ * Sizes: 1..65535 pixels per side, 1..4096 views; else VPGS_ERR_INVALID_ARG.
+ * One kernel launch (plus a memset of loss_out); graph-capturable. */
+vpgs_status vpgs_tracking_loss(const float *rgb, const float *target_rgb, const float *depth,
+                               const float *target_depth, int32_t n_views, int32_t width, int32_t height,
+                               float lambda_d, double *loss_out, float *dL_drgb, float *dL_ddepth,
+                               vpgs_stream stream);
+
 /* ---------------------------------------------------------------------- */
 /* Submap fusion (Sec. III-C, Eq. 14) and the optimiser step              */
 /* ---------------------------------------------------------------------- */

@@ -9,7 +9,7 @@ from .raster import (Options, Margins, render, render_scene, project, extent, ti
                      rect_min_quadratic, quat_to_rotmat)
 from .decode import decode, decode_scene, bf16_round, n_mlp_params, flatten_mlp, MLP_ORDER  # noqa: F401,E402
 from .pose import pose_step, se3_exp  # noqa: F401,E402
-from .loss import mapping_loss, ssim_map, gaussian_window  # noqa: F401,E402
+from .loss import mapping_loss, tracking_loss, ssim_map, gaussian_window  # noqa: F401,E402
 from .fusion import distill_loss, adam_step  # noqa: F401,E402
 from .icp import icp as voxel_icp, voxel_downsample  # noqa: F401,E402
 from .anchors import spawn as spawn_anchors, accumulate_stats, prune as prune_anchors, grow as grow_anchors  # noqa: F401,E402

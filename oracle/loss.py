@@ -21,9 +21,16 @@ paper is silent:
 Gradients are those of torch autograd through this code (|x| has derivative
 sign(x), 0 at 0).
 
+Coarse tracking (Sec. III-B) minimises the photometric and depth L1 errors of
+the render at the current pose.  Reading: for each view v separately,
+  L_t(v) = (1 / 3HW) sum_{c,p} |I^ - I| + lambda_d (1 / HW) sum_{p: D(p) > 0} |D^ - D|,
+the same colour and depth terms as the mapping loss, normalised per view so
+that a view's pose gradient does not depend on how many views share a call.
+
 Pins (tests/test_oracle_loss.py): SSIM(x, x) = 1, a constant-image closed form,
 brute-force windows on tiny images, the window's normalisation and symmetry,
-the volume term in closed form, and central differences of every gradient.
+the volume term in closed form, and central differences of every gradient;
+for the tracking loss a hand-worked 2x2 example and central differences.
 """
 from __future__ import annotations
 
@@ -93,4 +100,25 @@ def mapping_loss(rgb, target_rgb, depth=None, target_depth=None, scales=None, la
     return out
 
 
-__all__ = ["gaussian_window", "ssim_map", "mapping_loss", "C1", "C2"]
+def tracking_loss(rgb, target_rgb, depth=None, target_depth=None, lambda_d=1.0, grads=True):
+    """rgb, target_rgb [V,3,H,W]; depth, target_depth [V,H,W] (optional).
+    Returns a dict with the per-view losses "L_t" [V] and, with grads, d_rgb and
+    d_depth (the gradient of sum_v L_t(v))."""
+    x = torch.as_tensor(np.asarray(rgb), dtype=F64).clone().requires_grad_(grads)
+    y = torch.as_tensor(np.asarray(target_rgb), dtype=F64)
+    V, _, H, W = x.shape
+    L = (x - y).abs().reshape(V, -1).sum(1) / (3 * H * W)
+    d = None
+    if depth is not None:
+        d = torch.as_tensor(np.asarray(depth), dtype=F64).clone().requires_grad_(grads)
+        td = torch.as_tensor(np.asarray(target_depth), dtype=F64)
+        L = L + lambda_d * ((d - td).abs() * (td > 0)).reshape(V, -1).sum(1) / (H * W)
+    out = {"L_t": L.detach().numpy().copy()}
+    if grads:
+        L.sum().backward()
+        out["d_rgb"] = x.grad.numpy().copy()
+        out["d_depth"] = d.grad.numpy().copy() if d is not None else None
+    return out
+
+
+__all__ = ["gaussian_window", "ssim_map", "mapping_loss", "tracking_loss", "C1", "C2"]

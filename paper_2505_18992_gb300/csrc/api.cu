@@ -320,9 +320,12 @@ vpgs_status vpgs_render_bwd(void *ws, size_t ws_bytes, const vpgs_gaussians *g,
         if (e == cudaSuccess) tag_set(tag);
         else tag_clear(ws);
     }
+    // no opacity or colour gradient asked for (pose tracking): the compositing
+    // backward sums only the slots the means, covariances, depths and pose need
+    const bool geometric_only = !gg.opac && !gg.colors;
     if (e == cudaSuccess)
         e = launch_composite_bwd(S.ws, S.ws.ival[buf], n_views, S.cam, S.o, *fwd, dL_drgb, dL_ddepth,
-                                 dL_dalpha, opts->persistent_ctas, s);
+                                 dL_dalpha, geometric_only, opts->persistent_ctas, s);
     if (e == cudaSuccess && (grads || dL_dpose))
         e = launch_preprocess_bwd(S.g, T_cw, n_views, S.cam, S.o, S.ws, gg, dL_dpose, s);
     return cuda_status(e);

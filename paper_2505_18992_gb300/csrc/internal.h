@@ -63,7 +63,8 @@ cudaError_t launch_composite_fwd(const RenderWs &ws, const uint32_t *ival, int V
 cudaError_t launch_composite_bwd(const RenderWs &ws, const uint32_t *ival, int V,
                                  const CamParams &cam, const OptParams &o, const vpgs_images &fwd,
                                  const float *dL_drgb, const float *dL_ddepth,
-                                 const float *dL_dalpha, int persistent_ctas, cudaStream_t s);
+                                 const float *dL_dalpha, bool geometric_only, int persistent_ctas,
+                                 cudaStream_t s);
 
 // pose.cu
 cudaError_t launch_pose_step(double *T_cw, double *dpose, double *adam, int V, double lr_rho,

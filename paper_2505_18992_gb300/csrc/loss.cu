@@ -21,6 +21,8 @@
 //      (grid-strided) and write their gradients;
 //   2. blur of A, B, C -> colour gradient; block 0 sums the block partials
 //      into the loss terms.
+// The coarse-tracking loss (the colour and depth L1 terms per view) is a third,
+// single-pass kernel further down.
 #include <cmath>
 
 #include "internal.h"
@@ -335,6 +337,72 @@ cudaError_t launch_mapping_loss(void *ws, const float *rgb, const float *target,
     return cudaGetLastError();
 }
 
+// Coarse-tracking loss of each view (Sec. III-B), the per-view colour and depth
+// L1 terms of the mapping loss:
+//   L_t(v) = w_c sum_{c,p} |x - y| + w_d sum_{p: D(p) > 0} |D^ - D|,
+//   w_c = 1 / 3HW, w_d = lambda_d / HW,
+// with its gradient sign(e) w (0 at e = 0, and at pixels without a target
+// depth) written for every pixel.  One thread per kTlItems pixels of a view
+// (blockIdx.y); block sums in FP32, added across blocks in FP64.
+constexpr int kTlThreads = 256, kTlItems = 4;
+
+VPGS_D float sgn(float e) { return (float)((e > 0.f) - (e < 0.f)); }
+
+__global__ void __launch_bounds__(kTlThreads)
+tracking_loss_kernel(const float *__restrict__ rgb, const float *__restrict__ target,
+                     const float *__restrict__ depth, const float *__restrict__ tdepth, int64_t HW, float w_c,
+                     float w_d, float *__restrict__ d_rgb, float *__restrict__ d_depth, double *loss) {
+    grid_dep_enter();
+    __shared__ float s_red[kTlThreads / 32];
+    const int v = blockIdx.y;
+    const int64_t p0 = (int64_t)blockIdx.x * kTlThreads * kTlItems + threadIdx.x;
+    const int64_t cbase = (int64_t)v * 3 * HW, dbase = (int64_t)v * HW;
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < kTlItems; ++k) {
+        const int64_t p = p0 + (int64_t)k * kTlThreads;
+        if (p < HW) {
+            float l = 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int64_t o = cbase + c * HW + p;
+                const float e = rgb[o] - target[o];
+                if (d_rgb) d_rgb[o] = w_c * sgn(e);
+                l += fabsf(e);
+            }
+            acc = fmaf(w_c, l, acc);
+            if (depth) {
+                const float t = tdepth[dbase + p];
+                const float e = depth[dbase + p] - t;
+                const bool ok = t > 0.f;
+                if (d_depth) d_depth[dbase + p] = ok ? w_d * sgn(e) : 0.f;
+                if (ok) acc = fmaf(w_d, fabsf(e), acc);
+            }
+        }
+    }
+    if (loss) {
+        const float t = block_sum(acc, s_red);
+        if (threadIdx.x == 0) atomicAdd(loss + v, (double)t);
+    }
+}
+
+cudaError_t launch_tracking_loss(const float *rgb, const float *target, const float *depth, const float *tdepth,
+                                 int V, int W, int H, float lambda_d, double *loss, float *d_rgb,
+                                 float *d_depth, cudaStream_t s) {
+    const int64_t HW = (int64_t)W * H;
+    if (loss) {
+        const cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(double) * (size_t)V, s);
+        if (e != cudaSuccess) return e;
+    }
+    const float w_c = (float)(1.0 / (3.0 * (double)HW));
+    const float w_d = (float)((double)lambda_d / (double)HW);
+    const dim3 grid((unsigned)((HW + kTlThreads * kTlItems - 1) / (kTlThreads * kTlItems)), (unsigned)V);
+    VPGS_LAUNCH("tracking_loss", s,
+                launch_k(tracking_loss_kernel, grid, kTlThreads, 0, s, rgb, target, depth, tdepth, HW, w_c, w_d,
+                         d_rgb, d_depth, loss));
+    return cudaGetLastError();
+}
+
 }  // namespace vpgs
 
 using namespace vpgs;
@@ -370,6 +438,21 @@ vpgs_status vpgs_mapping_loss(void *ws, size_t ws_bytes, const float *rgb, const
                                               n_gaussians > 0 ? scales : nullptr, n_gaussians, n_dev,
                                               w->lambda_ssim, w->lambda_d, w->lambda_vol, loss_out, dL_drgb,
                                               dL_ddepth, dL_dscales, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
+}
+
+vpgs_status vpgs_tracking_loss(const float *rgb, const float *target_rgb, const float *depth,
+                               const float *target_depth, int32_t n_views, int32_t width, int32_t height,
+                               float lambda_d, double *loss_out, float *dL_drgb, float *dL_ddepth,
+                               vpgs_stream stream) {
+    if (!rgb || !target_rgb) return VPGS_ERR_INVALID_ARG;
+    if (n_views <= 0 || width <= 0 || height <= 0 || width > 65535 || height > 65535 || n_views > 4096)
+        return VPGS_ERR_INVALID_ARG;
+    if ((depth == nullptr) != (target_depth == nullptr)) return VPGS_ERR_INVALID_ARG;
+    if (!(lambda_d >= 0.f) || !std::isfinite(lambda_d)) return VPGS_ERR_INVALID_ARG;
+    const cudaError_t e = launch_tracking_loss(rgb, target_rgb, depth, target_depth, n_views, width, height,
+                                               lambda_d, loss_out, dL_drgb, dL_ddepth,
+                                               reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
 }
 

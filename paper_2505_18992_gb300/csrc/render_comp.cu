@@ -208,13 +208,15 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
     }
 }
 
-// Transpose reduction of 10 values over a warp.  Each halving step keeps
-// ceil(R/2) live values per lane: one half of the lanes keeps the low slots,
-// its partners the high slots, and each adds what the partner sent (5+3+2+1
-// shuffles, then one more to sum lane pairs).  Afterwards lane l holds the warp
-// total of slot red_slot(l) in v[0] (or nothing, red_slot = -1).
-template <int R, int O>
-VPGS_D void half_step(float (&v)[10], int lane) {
+// Transpose reduction of R values over a warp (R = 10: all 2D gradient slots;
+// R = 6: the geometric ones).  Each halving step keeps ceil(R/2) live values
+// per lane: one half of the lanes keeps the low slots, its partners the high
+// slots, and each adds what the partner sent (5+3+2+1 shuffles for R = 10,
+// 3+2+1 for R = 6), then the lane groups that hold the same slot are summed.
+// Afterwards lane l holds the warp total of slot red_slot<R>(l) in v[0] (or
+// nothing, red_slot = -1).
+template <int R, int O, int N>
+VPGS_D void half_step(float (&v)[N], int lane) {
     constexpr int S = (R + 1) / 2;
     const bool up = (lane & O) != 0;
 #pragma unroll
@@ -225,27 +227,46 @@ VPGS_D void half_step(float (&v)[10], int lane) {
     }
 }
 
+template <int R>
 VPGS_D int red_slot(int lane) {
-    int n = 10, off = 0;
-    const int S[4] = {5, 3, 2, 1}, bit[4] = {16, 8, 4, 2};
+    int n = R, off = 0, r = R, bit = 16;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        if (lane & bit[i]) {
-            off += S[i];
-            n = max(n - S[i], 0);
+    for (int i = 0; i < 5; ++i) {
+        if (r <= 1) break;
+        const int S = (r + 1) / 2;
+        if (lane & bit) {
+            off += S;
+            n = max(n - S, 0);
         } else {
-            n = min(n, S[i]);
+            n = min(n, S);
         }
+        r = S;
+        bit >>= 1;
     }
-    return (n >= 1 && !(lane & 1)) ? off : -1;
+    return (n >= 1 && (lane & (2 * bit - 1)) == 0) ? off : -1;
 }
 
-VPGS_D void warp_reduce10(float (&a)[10], int lane) {
+VPGS_D void warp_reduce(float (&a)[10], int lane) {
     half_step<10, 16>(a, lane);
     half_step<5, 8>(a, lane);
     half_step<3, 4>(a, lane);
     half_step<2, 2>(a, lane);
     a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
+}
+
+VPGS_D void warp_reduce(float (&a)[6], int lane) {
+    half_step<6, 16>(a, lane);
+    half_step<3, 8>(a, lane);
+    half_step<2, 4>(a, lane);
+    a[0] += __shfl_xor_sync(0xffffffffu, a[0], 2);
+    a[0] += __shfl_xor_sync(0xffffffffu, a[0], 1);
+}
+
+// 2D gradient slot [u, v, a, b, c, o, r, g, b, z] of accumulator q: the
+// geometric form (NV = 6) keeps u, v, a, b, c and the depth z in q = 0..5
+template <int NV>
+VPGS_D int g2d_slot(int q) {
+    return (NV == 6 && q == 5) ? 9 : q;
 }
 
 // per-pixel backward state
@@ -257,9 +278,13 @@ struct PixState {
 };
 
 // gradient of one pixel-Gaussian pair (Gaussian at list position jj), added to v;
-// updates the pixel's transmittance and behind-colour; returns whether it blended
+// updates the pixel's transmittance and behind-colour; returns whether it blended.
+// NV = 10: every 2D slot; NV = 6: only what the means, covariances and pose need
+// (no opacity or colour sums), the form taken when no opacity or colour
+// gradient is asked for
+template <int NV>
 VPGS_D bool pair_grad(PixState &p, int jj, const PairEval &e, float dx, float dy, const float4 &a,
-                      const float4 &b, const float4 &c, const OptParams &o, float (&v)[10]) {
+                      const float4 &b, const float4 &c, const OptParams &o, float (&v)[NV]) {
     if (jj >= p.last || e.alpha < o.alpha_min) return false;
     const float om = 1.f - e.alpha;
 #if VPGS_BWD_RCP
@@ -271,10 +296,14 @@ VPGS_D bool pair_grad(PixState &p, int jj, const PairEval &e, float dx, float dy
     const float gat = p.gAT / om;
 #endif
     const float w = e.alpha * p.T;
-    v[6] = fmaf(w, p.gC0, v[6]);
-    v[7] = fmaf(w, p.gC1, v[7]);
-    v[8] = fmaf(w, p.gC2, v[8]);
-    v[9] = fmaf(w, p.gD, v[9]);
+    if constexpr (NV == 10) {
+        v[6] = fmaf(w, p.gC0, v[6]);
+        v[7] = fmaf(w, p.gC1, v[7]);
+        v[8] = fmaf(w, p.gC2, v[8]);
+        v[9] = fmaf(w, p.gD, v[9]);
+    } else {
+        v[5] = fmaf(w, p.gD, v[5]);
+    }
     // dL/dalpha_i = T_i g . (c_i - B_i) + gat; behind this Gaussian
     // B <- B + alpha (c - B), so beta = g . B <- beta + alpha (g . c - beta)
     const float diff = fmaf(p.gC0, c.x, fmaf(p.gC1, c.y, fmaf(p.gC2, c.z, p.gD * c.w))) - p.beta;
@@ -285,7 +314,7 @@ VPGS_D bool pair_grad(PixState &p, int jj, const PairEval &e, float dx, float dy
         // Gaussian by the preprocess backward: the whitening rows and 2 ln 2 for the
         // mean (slots 0, 1 = sum dpow t1, sum dpow t2), -1/2, -1, -1/2 for the conic
         const float dpow = dA * e.alpha;
-        v[5] = fmaf(dA, e.G, v[5]);
+        if constexpr (NV == 10) v[5] = fmaf(dA, e.G, v[5]);
         v[0] = fmaf(dpow, e.t1, v[0]);
         v[1] = fmaf(dpow, e.t2, v[1]);
         const float pdx = dpow * dx;
@@ -309,6 +338,7 @@ constexpr int kPartStride = 11;  // floats per (warp, Gaussian) partial, padded 
 #define VPGS_BWD_BOUNDS __launch_bounds__(kMaxThreads)
 #endif
 
+template <int NV>
 __global__ void VPGS_BWD_BOUNDS
 composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ ival,
                      const uint2 *__restrict__ ranges, int n_tiles, CamParams cam, OptParams o,
@@ -336,7 +366,8 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
     const float2 band = warp_rows(pyl);
     uint16_t *wl = s_wl + (size_t)warp * NT;
     float *my_part = s_part + (size_t)warp * NT * kPartStride;
-    const int slot = red_slot(lane);
+    const int rs = red_slot<NV>(lane);
+    const int slot = rs >= 0 ? g2d_slot<NV>(rs) : -1;
     // hands one warp total (this lane's slot) of Gaussian k to the combination scheme
     auto put = [&](int k, float val) {
         if (kAcc == 0) {
@@ -412,9 +443,9 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
             for (int i = nl - 1; i >= 0; --i) {
                 const int kk = wl[i];
                 const float4 a = s0[kk], b = s1[kk], c = s2[kk];
-                float v[10];
+                float v[NV];
 #pragma unroll
-                for (int q = 0; q < 10; ++q) v[q] = 0.f;
+                for (int q = 0; q < NV; ++q) v[q] = 0.f;
                 const int jj = b0 + kk - start;
                 bool act = false;
 #pragma unroll
@@ -429,11 +460,11 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                     if (act) {
                         float *dst = g2d + 10 * (int64_t)s_id[kk];
 #pragma unroll
-                        for (int q = 0; q < 10; ++q)
-                            if (v[q] != 0.f) atomicAdd(dst + q, v[q]);
+                        for (int q = 0; q < NV; ++q)
+                            if (v[q] != 0.f) atomicAdd(dst + g2d_slot<NV>(q), v[q]);
                     }
                 } else if (am != 0u) {
-                    warp_reduce10(v, lane);
+                    warp_reduce(v, lane);
                     if (slot >= 0) put(kk, v[0]);
                 }
             }
@@ -498,30 +529,39 @@ cudaError_t launch_composite_fwd(const RenderWs &ws, const uint32_t *ival, int V
     return cudaGetLastError();
 }
 
-cudaError_t launch_composite_bwd(const RenderWs &ws, const uint32_t *ival, int V,
-                                 const CamParams &cam, const OptParams &o, const vpgs_images &fwd,
-                                 const float *dL_drgb, const float *dL_ddepth,
-                                 const float *dL_dalpha, int persistent_ctas, cudaStream_t s) {
+template <int NV>
+static cudaError_t composite_bwd_as(const RenderWs &ws, const uint32_t *ival, int V, const CamParams &cam,
+                                    const OptParams &o, const vpgs_images &fwd, const float *dL_drgb,
+                                    const float *dL_ddepth, const float *dL_dalpha, int persistent_ctas,
+                                    cudaStream_t s) {
     const int B = cam.tile_w * cam.tile_h / kPix;
     const int n_tiles = V * cam.T;
     const size_t sm = comp_smem(B, true);
+    const void *kern = (const void *)composite_bwd_kernel<NV>;
     uint32_t *work = nullptr;
     int grid = n_tiles;
     if (persistent_ctas > 0) {
         work = ws.counters + CNT_WORK;
         cudaError_t e = cudaMemsetAsync(work, 0, sizeof(uint32_t), s);
         if (e != cudaSuccess) return e;
-        grid = persistent_grid((const void *)composite_bwd_kernel, B, sm, persistent_ctas, n_tiles);
+        grid = persistent_grid(kern, B, sm, persistent_ctas, n_tiles);
     }
     if (grid == 0) return cudaSuccess;
-    if (sm > 48 * 1024)
-        cudaFuncSetAttribute((const void *)composite_bwd_kernel,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     VPGS_LAUNCH("composite_bwd", s,
-                launch_k(composite_bwd_kernel, grid, B, sm, s, ws.rec, ival, ws.ranges, n_tiles, cam, o,
-                                                         fwd.t_final, fwd.n_iter, dL_drgb, dL_ddepth,
-                                                         dL_dalpha, ws.g2d, ws.status, work));
+                launch_k(composite_bwd_kernel<NV>, grid, B, sm, s, ws.rec, ival, ws.ranges, n_tiles, cam, o,
+                         fwd.t_final, fwd.n_iter, dL_drgb, dL_ddepth, dL_dalpha, ws.g2d, ws.status, work));
     return cudaGetLastError();
+}
+
+cudaError_t launch_composite_bwd(const RenderWs &ws, const uint32_t *ival, int V,
+                                 const CamParams &cam, const OptParams &o, const vpgs_images &fwd,
+                                 const float *dL_drgb, const float *dL_ddepth,
+                                 const float *dL_dalpha, bool geometric_only, int persistent_ctas,
+                                 cudaStream_t s) {
+    return geometric_only
+               ? composite_bwd_as<6>(ws, ival, V, cam, o, fwd, dL_drgb, dL_ddepth, dL_dalpha, persistent_ctas, s)
+               : composite_bwd_as<10>(ws, ival, V, cam, o, fwd, dL_drgb, dL_ddepth, dL_dalpha, persistent_ctas, s);
 }
 
 }  // namespace vpgs

@@ -1,8 +1,10 @@
 """Coarse pose tracking by photometric + depth L1 (Sec. III-B), replayed from a CUDA graph.
 
 One iteration: render the current pose, take the L1 gradients against the
-frame (colour, and depth weighted by lambda_d), back-propagate to the pose
-only, and step the pose on the device (vpgs_pose_step, Adam).  The paper gives
+frame (vpgs_tracking_loss: colour, and depth weighted by lambda_d where the
+frame has a depth), back-propagate to the pose only (the compositing backward
+then sums only the geometric 2D gradients), and step the pose on the device
+(vpgs_pose_step, Adam).  The paper gives
 neither the iteration count nor the step rule; 50 Adam iterations is the
 tracking workload used here.  All buffers are preallocated, so `iters`
 iterations can be captured once and replayed with a single host call.
@@ -23,8 +25,8 @@ class Tracker:
         self.r = renderer
         self.g = [t.contiguous() for t in gaussians]
         self.T = T_cw  # [V,4,4] float64, updated in place
-        self.target_rgb = target_rgb
-        self.target_depth = target_depth
+        self.target_rgb = target_rgb.contiguous()
+        self.target_depth = None if target_depth is None else target_depth.contiguous()
         self.lr = (ctypes.c_double * 2)(*lr)
         self.lambda_d = lambda_d
         self.reuse = renderer.reuse_binning  # recompute the tile lists in the backward unless asked
@@ -32,13 +34,11 @@ class Tracker:
         dev = T_cw.device
         self.out = renderer.alloc_images()
         self.g_rgb = torch.empty_like(self.out["rgb"])
-        self.g_depth = torch.empty_like(self.out["depth"])
+        self.g_depth = None if target_depth is None else torch.empty_like(self.out["depth"])
         self.dpose = torch.zeros((V, 6), dtype=torch.float64, device=dev)
         self.adam = torch.zeros((V, 13), dtype=torch.float64, device=dev)
         self.graph = None
-        P = renderer.intr.width * renderer.intr.height
-        self.s_rgb = 1.0 / (3 * P)
-        self.s_d = lambda_d / P
+        self.loss = torch.zeros(V, dtype=torch.float64, device=dev)  # L_t per view, last iteration
 
     def reset(self, T0: torch.Tensor):
         self.T.copy_(T0)
@@ -52,10 +52,11 @@ class Tracker:
     def iteration(self):
         r = self.r
         r.forward(*self.g, self.T, out=self.out, check=False)
-        torch.sub(self.out["rgb"], self.target_rgb, out=self.g_rgb)
-        self.g_rgb.sign_().mul_(self.s_rgb)
-        torch.sub(self.out["depth"], self.target_depth, out=self.g_depth)
-        self.g_depth.sign_().mul_(self.s_d)
+        depth = None if self.target_depth is None else self.out["depth"]
+        C.check(C.vpgs_tracking_loss(C.ptr(self.out["rgb"]), C.ptr(self.target_rgb), C.ptr(depth),
+                                     C.ptr(self.target_depth), r.V, r.intr.width, r.intr.height, self.lambda_d,
+                                     C.ptr(self.loss), C.ptr(self.g_rgb), C.ptr(self.g_depth),
+                                     current_stream_handle()), "vpgs_tracking_loss")
         r.backward(*self.g, self.T, self.out, self.g_rgb, self.g_depth, None, grads=None,
                    dpose=self.dpose, reuse=self.reuse)
         C.check(C.vpgs_pose_step(self.T.data_ptr(), self.dpose.data_ptr(), self.adam.data_ptr(),

@@ -132,6 +132,8 @@ _SIGS = {
     "vpgs_mapping_loss": (c_int32, [c_void_p, c_size_t, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
                                     c_int32, c_int32, c_void_p, c_int64, c_void_p, POINTER(vpgs_loss_weights),
                                     c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "vpgs_tracking_loss": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_float,
+                                     c_void_p, c_void_p, c_void_p, c_void_p]),
     "vpgs_distill_workspace_bytes": (c_size_t, [c_int32, c_int32, c_int32]),
     "vpgs_distill_loss": (c_int32, [c_void_p, c_size_t, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32,
                                     c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -223,6 +225,7 @@ vpgs_decode_anchors_bwd = _entry("vpgs_decode_anchors_bwd")
 vpgs_loss_weights_default = _entry("vpgs_loss_weights_default")
 vpgs_mapping_loss_workspace_bytes = _entry("vpgs_mapping_loss_workspace_bytes")
 vpgs_mapping_loss = _entry("vpgs_mapping_loss")
+vpgs_tracking_loss = _entry("vpgs_tracking_loss")
 vpgs_distill_workspace_bytes = _entry("vpgs_distill_workspace_bytes")
 vpgs_distill_loss = _entry("vpgs_distill_loss")
 vpgs_adam_step = _entry("vpgs_adam_step")

@@ -89,3 +89,50 @@ def test_bad_arguments_are_rejected():
     code = C.vpgs_mapping_loss(L.ws.data_ptr(), L.ws.numel(), t.data_ptr(), t.data_ptr(), None, None, 1, 8, 8,
                                None, 0, None, ctypes.byref(bad), L.loss.data_ptr(), None, None, None, None)
     assert code == 1
+
+
+def _tracking_gpu(x, y, d, td, lambda_d, with_depth=True):
+    V, _, H, W = x.shape
+    loss = torch.full((V,), -1.0, dtype=torch.float64, device="cuda")
+    gr = torch.full((V, 3, H, W), 7.0, device="cuda")
+    gd = torch.full((V, H, W), 7.0, device="cuda")
+    xt, yt = dev(x), dev(y)  # held: the call takes raw addresses
+    dt, tdt = (dev(d), dev(td)) if with_depth else (None, None)
+    code = C.vpgs_tracking_loss(C.ptr(xt), C.ptr(yt), C.ptr(dt), C.ptr(tdt), V, W, H, lambda_d, C.ptr(loss),
+                                C.ptr(gr), C.ptr(gd), None)
+    assert code == 0
+    torch.cuda.synchronize()
+    return loss.cpu().numpy(), gr.cpu().numpy(), gd.cpu().numpy()
+
+
+@pytest.mark.parametrize("shape", [(2, 45, 70), (3, 17, 5), (1, 680, 1200)])
+def test_tracking_loss_matches_the_oracle(shape):
+    """Per-view colour + depth L1 of coarse tracking: the gradients are sign x
+    weight, so both sides agree bit for bit once the FP64 weights are rounded
+    to float32 (the sign of a float32 difference is exact); the per-view loss
+    is an FP32 / FP64 sum, 2e-6 relative."""
+    V, H, W = shape
+    x, y, d, td, _ = _case(V, H, W, 1, seed=H * W)
+    y[0, 1, 0, :3] = x[0, 1, 0, :3]  # exact ties: zero gradient
+    d[0, 2, :5] = td[0, 2, :5]
+    ref = oracle.tracking_loss(x, y, d, td, lambda_d=0.5)
+    loss, gr, gd = _tracking_gpu(x, y, d, td, 0.5)
+    assert np.all(np.abs(loss - ref["L_t"]) <= 2e-6 * np.maximum(1.0, np.abs(ref["L_t"])))
+    assert np.array_equal(gr, ref["d_rgb"].astype(np.float32))
+    assert np.array_equal(gd, ref["d_depth"].astype(np.float32))
+    assert gr[0, 1, 0, 0] == 0.0 and gd[0, 0, 0] == 0.0  # a tie, a pixel without a target depth
+
+
+def test_tracking_loss_without_depth_and_bad_arguments():
+    x, y, d, td, _ = _case(2, 19, 33, 1, seed=3)
+    ref = oracle.tracking_loss(x, y)
+    loss, gr, gd = _tracking_gpu(x, y, d, td, 1.0, with_depth=False)
+    assert np.all(np.abs(loss - ref["L_t"]) <= 2e-6)
+    assert np.array_equal(gr, ref["d_rgb"].astype(np.float32))
+    assert np.all(gd == 7.0)  # untouched without depths
+    t = torch.zeros((1, 3, 8, 8), device="cuda")
+    assert C.vpgs_tracking_loss(None, t.data_ptr(), None, None, 1, 8, 8, 1.0, None, None, None, None) == 1
+    assert C.vpgs_tracking_loss(t.data_ptr(), t.data_ptr(), t.data_ptr(), None, 1, 8, 8, 1.0, None, None, None,
+                                None) == 1
+    assert C.vpgs_tracking_loss(t.data_ptr(), t.data_ptr(), None, None, 0, 8, 8, 1.0, None, None, None, None) == 1
+    assert C.vpgs_tracking_loss(t.data_ptr(), t.data_ptr(), None, None, 1, 8, 8, -1.0, None, None, None, None) == 1

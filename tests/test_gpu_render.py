@@ -95,6 +95,28 @@ def test_backward_parity(planes, planes_ref):
     assert_pose_close(dpose, ref["d_pose"])
 
 
+@pytest.mark.parametrize("keys", [(), ("means",), ("means", "scales", "quats")])
+def test_geometric_backward_without_colour_or_opacity(planes, planes_ref, keys):
+    """Asking for no opacity or colour gradient (pose tracking) selects the
+    compositing backward that sums only the geometric 2D slots: the pose and
+    the geometric gradients still match the oracle, and a full backward after
+    it still does (the slots it leaves alone stay zero between calls)."""
+    ref, gm = planes_ref
+    r, g, T, out = _gpu_forward(planes)
+    fwd = {"t_final": dev(out["t_final"]), "n_iter": dev(out["n_iter"], torch.int32)}
+    gr = {k: torch.zeros_like(t) for k, t in zip(GRAD_KEYS, g) if k in keys}
+    dpose = torch.zeros((r.V, 6), dtype=torch.float64, device="cuda")
+    r.backward(*g, T, fwd, dev(gm[0]), dev(gm[1]), dev(gm[2]), grads=gr or None, dpose=dpose, check=True)
+    torch.cuda.synchronize()
+    for k in keys:
+        assert_grad_close(gr[k].cpu().numpy(), ref["d_" + k], k)
+    assert_pose_close(dpose.cpu().numpy(), ref["d_pose"])
+    grads, dpose2 = _gpu_backward(r, g, T, out, gm)
+    for k in GRAD_KEYS:
+        assert_grad_close(grads[k], ref["d_" + k], k)
+    assert_pose_close(dpose2, ref["d_pose"])
+
+
 @pytest.mark.parametrize("tile", [(16, 16), (8, 16), (32, 8), (8, 32), (16, 8), (8, 8)])
 def test_tile_shape_does_not_change_the_image(planes, planes_ref, tile):
     ref, _ = planes_ref

@@ -108,3 +108,48 @@ def test_gradients_central_differences(seed):
         num = (oracle.mapping_loss(x, y, dp, td, s, grads=False)["L_m"] -
                oracle.mapping_loss(x, y, dm, td, s, grads=False)["L_m"]) / (2 * h)
         assert abs(num - out["d_depth"][idx]) < 1e-6
+
+
+def test_tracking_loss_hand_worked():
+    # view 0: one colour channel differs at two pixels, one depth pixel has no target
+    x = np.full((2, 3, 2, 2), 0.5)
+    y = x.copy()
+    y[0, 0] = [[0.25, 0.5], [1.0, 0.5]]
+    d = np.full((2, 2, 2), 2.0)
+    td = np.array([[[1.0, 0.0], [3.0, 2.0]], [[2.0, 2.0], [2.0, 2.0]]])
+    out = oracle.tracking_loss(x, y, d, td, lambda_d=0.5)
+    # colour: (0.25 + 0.5) / 12; depth: 0.5 * (1 + 1) / 4 (the pixel without a target is left out)
+    assert np.allclose(out["L_t"], [0.75 / 12 + 0.25, 0.0], atol=1e-15)
+    g = np.zeros_like(x)
+    g[0, 0, 0, 0], g[0, 0, 1, 0] = 1 / 12, -1 / 12
+    assert np.array_equal(out["d_rgb"], g)
+    gd = np.zeros_like(d)
+    gd[0, 0, 0], gd[0, 1, 0] = 0.125, -0.125
+    assert np.array_equal(out["d_depth"], gd)
+    # no depth: the colour term alone
+    assert np.allclose(oracle.tracking_loss(x, y)["L_t"], [0.75 / 12, 0.0], atol=1e-15)
+
+
+def test_tracking_loss_central_differences():
+    rng = np.random.default_rng(5)
+    x = rng.uniform(size=(2, 3, 5, 7))
+    y = rng.uniform(size=(2, 3, 5, 7))
+    d = rng.uniform(1, 3, size=(2, 5, 7))
+    td = rng.uniform(1, 3, size=(2, 5, 7))
+    td[0, 1, 2] = 0.0
+    out = oracle.tracking_loss(x, y, d, td, lambda_d=0.7)
+    h = 1e-7
+    total = lambda *a: oracle.tracking_loss(*a, lambda_d=0.7, grads=False)["L_t"].sum()  # noqa: E731
+    for _ in range(6):
+        idx = tuple(rng.integers(0, n) for n in x.shape)
+        xp, xm = x.copy(), x.copy()
+        xp[idx] += h
+        xm[idx] -= h
+        num = (total(xp, y, d, td) - total(xm, y, d, td)) / (2 * h)
+        assert abs(num - out["d_rgb"][idx]) < 1e-6
+    for idx in [(0, 1, 2), (1, 4, 6), (0, 0, 0)]:
+        dp, dm = d.copy(), d.copy()
+        dp[idx] += h
+        dm[idx] -= h
+        num = (total(x, y, dp, td) - total(x, y, dm, td)) / (2 * h)
+        assert abs(num - out["d_depth"][idx]) < 1e-6
