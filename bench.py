@@ -928,6 +928,7 @@ def anchor_oracle():
 def tracking_rows(sc, g, dev):
     import torch
 
+    from paper_2505_18992_gb300 import vpgs as C
     from paper_2505_18992_gb300.render import Intrinsics, Renderer
     from paper_2505_18992_gb300.tracking import Tracker
     cam = sc.camera
@@ -951,6 +952,14 @@ def tracking_rows(sc, g, dev):
     eager_ms = e0.elapsed_time(e1)
     err0 = float(torch.linalg.norm(T0[0, :3, 3] - T_true[0, :3, 3]))
     err_eager = float(torch.linalg.norm(T[0, :3, 3] - T_true[0, :3, 3]))
+    # per-kernel device times of an iteration (CUDA events on the launching stream)
+    tr.reset(T0)
+    C.vpgs_profile_enable(1)
+    tr.run_eager(10)
+    torch.cuda.synchronize()
+    prof = C.profile_collect()
+    C.vpgs_profile_enable(0)
+    kernels_us = {k: round(1000 * t / max(n, 1), 1) for k, (n, t) in prof.items()}
     tr.reset(T0)
     tr.capture(iters)
     tr.reset(T0)
@@ -963,7 +972,8 @@ def tracking_rows(sc, g, dev):
     err_graph = float(torch.linalg.norm(T[0, :3, 3] - T_true[0, :3, 3]))
     return {"iters": iters, "eager_ms": eager_ms, "graph_ms": graph_ms,
             "ms_per_iter_graph": graph_ms / iters, "trans_err_m_start": err0,
-            "trans_err_m_eager": err_eager, "trans_err_m_graph": err_graph}
+            "trans_err_m_eager": err_eager, "trans_err_m_graph": err_graph,
+            "kernels_us_per_launch": kernels_us}
 
 
 def run_row(a):
