@@ -88,6 +88,7 @@ bool make_layout(int64_t N, int V, const vpgs_camera *cam, const vpgs_render_opt
     L.off_posedf = take(4 * 24 * (size_t)V);
     L.off_bin = take(sizeof(BinRec) * (size_t)VN1);
     L.off_vis_idx = take(4 * (size_t)VN1);
+    L.off_tile_order = take(4 * (size_t)V * L.T);
     L.total = off;
     return true;
 }
@@ -118,6 +119,7 @@ RenderWs carve(void *base, const RenderLayout &L) {
     w.posedf = reinterpret_cast<float *>(b + L.off_posedf);
     w.bin = reinterpret_cast<BinRec *>(b + L.off_bin);
     w.vis_idx = reinterpret_cast<uint32_t *>(b + L.off_vis_idx);
+    w.tile_order = reinterpret_cast<uint32_t *>(b + L.off_tile_order);
     return w;
 }
 

@@ -297,7 +297,7 @@ struct RenderLayout {
     size_t off_status, off_counters, off_rec, off_tcount, off_dkey0,
         off_dval0, off_dkey1, off_dval1, off_ikey0, off_ival0, off_ikey1, off_ival1, off_ranges,
         off_sort_hist, off_sort_look, off_sort_look_t, off_scan_look, off_g2d, off_posedf, off_bin,
-        off_vis_idx, total;
+        off_vis_idx, off_tile_order, total;
     int64_t sort_blocks_max, scan_blocks_max;
 };
 
@@ -330,6 +330,7 @@ struct RenderWs {
     float *posedf;        // [V,24] poses as double-float pairs
     BinRec *bin;          // [VN] binning records of visible Gaussians
     uint32_t *vis_idx;    // [VN] visible (view, Gaussian) indices in index order
+    uint32_t *tile_order; // [V*T] global tile ids, most instances first (compositing launch order)
 };
 
 // radix sort geometry
@@ -345,6 +346,12 @@ constexpr int kTileSortItems = VPGS_TILE_SORT_ITEMS;    // keys per thread in th
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kMaxSortPasses = 8;
+
+// compositing launch order: 1 = tiles with the most instances first (a
+// bucketed counting sort after the tile ranges), 0 = tile-id order
+#ifndef VPGS_TILE_ORDER
+#define VPGS_TILE_ORDER 1
+#endif
 
 // scan geometry
 constexpr int kScanThreads = 256;

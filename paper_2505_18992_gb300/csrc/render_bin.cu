@@ -10,6 +10,7 @@
 //   4. stable radix sort of the instances by global tile id (only the bits a
 //      tile id needs); instances stay in depth order inside each tile
 //   5. [start, end) of every tile from the sorted keys
+//   6. the compositing launch order: tiles by descending instance count
 //
 // Sorting the visible Gaussians once by depth and then the instances by tile
 // id only moves 32-bit depth keys over N_visible items and a 12-14 bit tile key
@@ -171,6 +172,80 @@ __global__ void tile_ranges_kernel(const uint32_t *__restrict__ keys, int64_t ca
     }
 }
 
+// Launch order of the compositing kernels: global tile ids by descending
+// instance count, so the longest tiles start first and the short ones fill the
+// tail of the grid (tiles are independent: the order changes no pixel).  One
+// block: tiles are bucketed by count / 4 (the last bucket takes every count
+// beyond), buckets are laid out from the heaviest down, and each tile takes a
+// slot in its bucket by a shared-memory atomic.  Up to kOrderPer tiles per
+// thread are loaded at once and kept in registers between the two passes.
+constexpr int kOrderThreads = 1024;
+constexpr int kOrderBins = 1024;
+constexpr int kOrderPer = 8;
+
+VPGS_D uint32_t order_bucket(uint2 r) {
+    const uint32_t c = r.y > r.x ? r.y - r.x : 0u;
+    return min(c >> 2, (uint32_t)kOrderBins - 1u);
+}
+
+__global__ void __launch_bounds__(kOrderThreads)
+tile_order_kernel(const uint2 *__restrict__ ranges, int n_tiles, uint32_t *__restrict__ order) {
+    grid_dep_enter();
+    __shared__ uint32_t s_bin[kOrderBins];
+    __shared__ uint32_t s_warp[kOrderThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool fits = n_tiles <= kOrderThreads * kOrderPer;  // block-uniform
+    uint32_t bk[kOrderPer];  // bucket of tile tid + k * kOrderThreads (kOrderBins: none)
+    if (fits) {
+#pragma unroll
+        for (int k = 0; k < kOrderPer; ++k) {
+            const int i = tid + k * kOrderThreads;
+            bk[k] = i < n_tiles ? order_bucket(ranges[i]) : (uint32_t)kOrderBins;
+        }
+    }
+    for (int i = tid; i < kOrderBins; i += kOrderThreads) s_bin[i] = 0u;
+    __syncthreads();
+    if (fits) {
+#pragma unroll
+        for (int k = 0; k < kOrderPer; ++k)
+            if (bk[k] < (uint32_t)kOrderBins) atomicAdd(&s_bin[bk[k]], 1u);
+    } else {
+        for (int i = tid; i < n_tiles; i += kOrderThreads) atomicAdd(&s_bin[order_bucket(ranges[i])], 1u);
+    }
+    __syncthreads();
+    // exclusive scan over the buckets from the heaviest (thread j holds bucket kOrderBins-1-j)
+    const int b = kOrderBins - 1 - tid;
+    const uint32_t c = s_bin[b];
+    uint32_t x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = s_warp[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_warp[lane] = w;  // inclusive totals of warps 0..lane
+    }
+    __syncthreads();
+    s_bin[b] = x - c + (warp > 0 ? s_warp[warp - 1] : 0u);  // every thread read its count before the barrier
+    __syncthreads();
+    if (fits) {
+#pragma unroll
+        for (int k = 0; k < kOrderPer; ++k)
+            if (bk[k] < (uint32_t)kOrderBins) order[atomicAdd(&s_bin[bk[k]], 1u)] = (uint32_t)(tid + k * kOrderThreads);
+    } else {
+        for (int i = tid; i < n_tiles; i += kOrderThreads)
+            order[atomicAdd(&s_bin[order_bucket(ranges[i])], 1u)] = (uint32_t)i;
+    }
+}
+
 int tile_list_buffer(const RenderLayout &L) {
     SortPass ps[kMaxSortPasses];
     return (plan_passes(0, L.tile_bits, ps) & 1) != 0 ? 1 : 0;
@@ -238,6 +313,10 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
     VPGS_LAUNCH("tile_ranges", s,
                 launch_k(tile_ranges_kernel, (unsigned)std::max<int64_t>(rb, 1), 256, 0, s,
                     in1 ? ws.ikey[1] : ws.ikey[0], L.M_cap, n_inst, (uint32_t)n_tiles, ws.ranges));
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !VPGS_TILE_ORDER) return e;
+    // 6. compositing launch order
+    VPGS_LAUNCH("tile_order", s, launch_k(tile_order_kernel, 1, kOrderThreads, 0, s, ws.ranges, n_tiles, ws.tile_order));
     return cudaGetLastError();
 }
 

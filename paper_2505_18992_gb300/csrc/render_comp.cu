@@ -100,7 +100,8 @@ VPGS_D void stage(const Rec &r, float ox, float oy, float4 &a, float4 &b, float4
 
 __global__ void VPGS_FWD_BOUNDS
 composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ ival,
-                     const uint2 *__restrict__ ranges, int n_tiles, CamParams cam, OptParams o,
+                     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ order, int n_tiles,
+                     CamParams cam, OptParams o,
                      vpgs_images out, const uint32_t *status, uint32_t *work) {
     grid_dep_enter();
     extern __shared__ float4 smem[];
@@ -126,10 +127,11 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
             __syncthreads();
         }
         if (t >= n_tiles) return;
-        const TileCoord tc = tile_coord(t, cam);
+        const int tile = order ? (int)order[t] : t;  // launch order -> global tile id
+        const TileCoord tc = tile_coord(tile, cam);
         const int px = tc.tx * cam.tile_w + lx;
         const float ox = (float)(tc.tx * cam.tile_w), oy = (float)(tc.ty * cam.tile_h);
-        const uint2 rg = ranges[t];
+        const uint2 rg = ranges[tile];
         const int start = (int)rg.x, end = (int)rg.y;
         float T[kPix], C0[kPix], C1[kPix], C2[kPix], D[kPix];
         int cnt[kPix], last[kPix];
@@ -341,7 +343,8 @@ constexpr int kPartStride = 11;  // floats per (warp, Gaussian) partial, padded 
 template <int NV>
 __global__ void VPGS_BWD_BOUNDS
 composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ ival,
-                     const uint2 *__restrict__ ranges, int n_tiles, CamParams cam, OptParams o,
+                     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ order, int n_tiles,
+                     CamParams cam, OptParams o,
                      const float *__restrict__ t_final, const int32_t *__restrict__ n_iter,
                      const float *__restrict__ dL_drgb, const float *__restrict__ dL_ddepth,
                      const float *__restrict__ dL_dalpha, float *__restrict__ g2d,
@@ -388,10 +391,11 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
         if (tid == 0) s_max = 0;
         __syncthreads();
         if (t >= n_tiles) return;
-        const TileCoord tc = tile_coord(t, cam);
+        const int tile = order ? (int)order[t] : t;  // launch order -> global tile id
+        const TileCoord tc = tile_coord(tile, cam);
         const int px = tc.tx * cam.tile_w + lx;
         const float ox = (float)(tc.tx * cam.tile_w), oy = (float)(tc.ty * cam.tile_h);
-        const uint2 rg = ranges[t];
+        const uint2 rg = ranges[tile];
         const int start = (int)rg.x;
         const int64_t HW = (int64_t)cam.H * cam.W;
         PixState ps[kPix];
@@ -524,8 +528,9 @@ cudaError_t launch_composite_fwd(const RenderWs &ws, const uint32_t *ival, int V
         cudaFuncSetAttribute((const void *)composite_fwd_kernel,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     VPGS_LAUNCH("composite_fwd", s,
-                launch_k(composite_fwd_kernel, grid, B, sm, s, ws.rec, ival, ws.ranges, n_tiles, cam, o, out,
-                                                         ws.status, work));
+                launch_k(composite_fwd_kernel, grid, B, sm, s, ws.rec, ival, ws.ranges,
+                         VPGS_TILE_ORDER ? (const uint32_t *)ws.tile_order : nullptr, n_tiles, cam, o, out,
+                         ws.status, work));
     return cudaGetLastError();
 }
 
@@ -549,7 +554,8 @@ static cudaError_t composite_bwd_as(const RenderWs &ws, const uint32_t *ival, in
     if (grid == 0) return cudaSuccess;
     if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     VPGS_LAUNCH("composite_bwd", s,
-                launch_k(composite_bwd_kernel<NV>, grid, B, sm, s, ws.rec, ival, ws.ranges, n_tiles, cam, o,
+                launch_k(composite_bwd_kernel<NV>, grid, B, sm, s, ws.rec, ival, ws.ranges,
+                         VPGS_TILE_ORDER ? (const uint32_t *)ws.tile_order : nullptr, n_tiles, cam, o,
                          fwd.t_final, fwd.n_iter, dL_drgb, dL_ddepth, dL_dalpha, ws.g2d, ws.status, work));
     return cudaGetLastError();
 }

@@ -233,11 +233,13 @@ def test_backward_reusing_the_forward_lists(planes, planes_ref):
     for k in GRAD_KEYS:
         assert_grad_close(a[k], ref["d_" + k], k)
     assert_pose_close(pa, ref["d_pose"])
-    # a second reusing backward sees zeroed 2D gradient slots again (float atomics
-    # sum in a different order on every run: equal up to rounding of the array scale)
+    # a second reusing backward sees zeroed 2D gradient slots again.  Float atomics
+    # sum in a schedule-dependent order on every run: a Gaussian's 2D sums gather
+    # hundreds of per-(warp, pixel) terms, each up to the array scale, so two runs
+    # agree to about sqrt(terms) FP32 roundings of that scale (1e-5 of it)
     b, pb = _gpu_backward(r, g, T, out, gm, reuse=True)
     for k in GRAD_KEYS:
-        np.testing.assert_allclose(b[k], a[k], rtol=0, atol=1e-6 * np.abs(a[k]).max(), err_msg=k)
+        np.testing.assert_allclose(b[k], a[k], rtol=0, atol=1e-5 * np.abs(a[k]).max(), err_msg=k)
     np.testing.assert_allclose(pb, pa, rtol=1e-5, atol=1e-9 * np.abs(pa).max())
 
 
