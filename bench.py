@@ -53,7 +53,7 @@ def _args():
                                      "anchors"),
                    help="run only this secondary row and print it (a profiling entry point, not a bench line)")
     p.add_argument("--persistent", type=int, default=0, help="persistent CTAs per SM (0 = per tile)")
-    p.add_argument("--tile", default="8x16", help="tile shape WxH")
+    p.add_argument("--tile", default="16x16", help="tile shape WxH")
     p.add_argument("--scale", type=float, default=1.0,
                    help="shrink the workload for profiling: N x scale^2 Gaussians, image x scale")
     return p.parse_args()

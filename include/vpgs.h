@@ -65,7 +65,7 @@ typedef struct {
 } vpgs_camera;
 
 /* Rasterizer options (host struct).  vpgs_render_opts_default() fills these defaults:
- *   tile 8x16, alpha_min 1/255, alpha_max 0.99, t_min 1e-4, dilation 0.3 px^2,
+ *   tile 16x16, alpha_min 1/255, alpha_max 0.99, t_min 1e-4, dilation 0.3 px^2,
  *   near_z 0.2, background black.
  * The paper cites 3D Gaussian Splatting for all of these (Sec. I, Sec. II) and
  * states none of them. */

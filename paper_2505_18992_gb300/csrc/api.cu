@@ -254,8 +254,8 @@ extern "C" {
 
 void vpgs_render_opts_default(vpgs_render_opts *o) {
     if (!o) return;
-    o->tile_w = 8;   // 8x16 tiles: measured fastest fwd+bwd on GB300 (the image
-    o->tile_h = 16;  // does not depend on the tile shape)
+    o->tile_w = 16;  // 16x16 tiles: measured fastest fwd+bwd on GB300 with the tiles
+    o->tile_h = 16;  // launched heaviest first (the image does not depend on the tile shape)
     o->alpha_min = 1.0f / 255.0f;
     o->alpha_max = 0.99f;
     o->t_min = 1e-4f;

@@ -73,7 +73,7 @@ def test_struct_layouts_match_the_header(lib, tmp_path):
 def test_host_side_validation_without_a_gpu(lib):
     from paper_2505_18992_gb300 import vpgs as C
     o = C.default_opts()
-    assert (o.tile_w, o.tile_h) == (8, 16)
+    assert (o.tile_w, o.tile_h) == (16, 16)
     assert abs(o.alpha_min - 1 / 255) < 1e-9 and abs(o.alpha_max - 0.99) < 1e-7
     cam = C.vpgs_camera(1200, 680, 600.0, 600.0, 600.0, 340.0)
     n1 = C.vpgs_render_workspace_bytes(1000, 1, ctypes.byref(cam), ctypes.byref(o), 10000)
