@@ -19,9 +19,11 @@
 #endif
 //   VPGS_BWD_ACC how the backward combines per-warp sums of a Gaussian's 2D
 //                gradient: 0 = one global atomic per warp, 1 = per-warp shared
-//                slots summed per batch, 2 = shared-memory atomics per batch
+//                slots summed per batch, 2 = shared-memory atomics per batch,
+//                -1 = by the tile's warps (1 from 2 warps per tile up, 0 for a
+//                one-warp tile, which has no warps' sums to combine)
 #ifndef VPGS_BWD_ACC
-#define VPGS_BWD_ACC 0
+#define VPGS_BWD_ACC -1
 #endif
 //   VPGS_BWD_RCP 1: the backward takes one approximate reciprocal of 1 - alpha
 //                per blended pair (relative error ~1e-7 per step), 0: IEEE divisions

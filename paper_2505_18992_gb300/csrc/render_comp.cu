@@ -43,7 +43,6 @@ VPGS_D TileCoord tile_coord(int t, const CamParams &cam) {
 
 // Each thread owns kPix pixels of its tile column: rows kPix*ly .. kPix*ly + kPix - 1.
 constexpr int kPix = VPGS_PIX;
-constexpr int kAcc = VPGS_BWD_ACC;  // combination of per-warp gradient sums (see common.cuh)
 #ifndef VPGS_BWD_DIRECT
 #define VPGS_BWD_DIRECT 2
 #endif
@@ -340,7 +339,11 @@ constexpr int kPartStride = 11;  // floats per (warp, Gaussian) partial, padded 
 #define VPGS_BWD_BOUNDS __launch_bounds__(kMaxThreads)
 #endif
 
-template <int NV>
+// ACC: how the warps' sums of a Gaussian are combined (VPGS_BWD_ACC): 0 = one
+// global atomic per (warp, Gaussian, slot); 1 = each warp stores its sums in its
+// own shared slots and one thread per Gaussian adds the warps' slots into one
+// global atomic per batch; 2 = shared-memory atomics per batch
+template <int NV, int ACC>
 __global__ void VPGS_BWD_BOUNDS
 composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ ival,
                      const uint2 *__restrict__ ranges, const uint32_t *__restrict__ order, int n_tiles,
@@ -373,9 +376,9 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
     const int slot = rs >= 0 ? g2d_slot<NV>(rs) : -1;
     // hands one warp total (this lane's slot) of Gaussian k to the combination scheme
     auto put = [&](int k, float val) {
-        if (kAcc == 0) {
+        if (ACC == 0) {
             if (val != 0.f) atomicAdd(g2d + 10 * (int64_t)s_id[k] + slot, val);
-        } else if (kAcc == 1) {
+        } else if (ACC == 1) {
             my_part[k * kPartStride + slot] = val;
         } else {
             if (val != 0.f) atomicAdd(s_part + k * kPartStride + slot, val);
@@ -436,9 +439,9 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                 stage(rec[id], ox, oy, s0[tid], s1[tid], s2[tid]);
                 s_id[tid] = id;
             }
-            if (kAcc == 1)
+            if (ACC == 1)
                 for (int e = lane; e < nb * kPartStride; e += 32) my_part[e] = 0.f;
-            if (kAcc == 2)
+            if (ACC == 2)
                 for (int e = tid; e < nb * kPartStride; e += NT) s_part[e] = 0.f;
             __syncthreads();
             const int k_end = min(nb, warp_max - (b0 - start));  // warp-uniform
@@ -459,7 +462,7 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                     act |= pair_grad(ps[q], jj, e, dx, dy, a, b, c, o, v);
                 }
                 const uint32_t am = __ballot_sync(0xffffffffu, act);
-                if (kAcc == 0 && am != 0u && __popc(am) <= kDirect) {
+                if (ACC == 0 && am != 0u && __popc(am) <= kDirect) {
                     // few active lanes: their own atomics beat a reduction
                     if (act) {
                         float *dst = g2d + 10 * (int64_t)s_id[kk];
@@ -472,7 +475,7 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                     if (slot >= 0) put(kk, v[0]);
                 }
             }
-            if (kAcc != 0) {
+            if (ACC != 0) {
                 __syncthreads();
                 // one thread per Gaussian of the batch: one global atomic per value
                 for (int k = tid; k < nb; k += NT) {
@@ -480,7 +483,7 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
 #pragma unroll
                     for (int sl = 0; sl < 10; ++sl) {
                         float acc = 0.f;
-                        if (kAcc == 1) {
+                        if (ACC == 1) {
                             for (int w = 0; w < NW; ++w) acc += s_part[((size_t)w * NT + k) * kPartStride + sl];
                         } else {
                             acc = s_part[k * kPartStride + sl];
@@ -495,8 +498,8 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
     }
 }
 
-static size_t comp_smem(int NT, bool bwd) {
-    const size_t parts = kAcc == 1 ? (size_t)(NT / 32) * NT * kPartStride : (kAcc == 2 ? (size_t)NT * kPartStride : 0);
+static size_t comp_smem(int NT, bool bwd, int acc = 0) {
+    const size_t parts = acc == 1 ? (size_t)(NT / 32) * NT * kPartStride : (acc == 2 ? (size_t)NT * kPartStride : 0);
     const size_t lists = sizeof(uint16_t) * (size_t)(NT / 32) * NT;
     return sizeof(float4) * 3 * NT + lists + (bwd ? sizeof(uint32_t) * NT + sizeof(float) * parts : 0);
 }
@@ -534,15 +537,15 @@ cudaError_t launch_composite_fwd(const RenderWs &ws, const uint32_t *ival, int V
     return cudaGetLastError();
 }
 
-template <int NV>
+template <int NV, int ACC>
 static cudaError_t composite_bwd_as(const RenderWs &ws, const uint32_t *ival, int V, const CamParams &cam,
                                     const OptParams &o, const vpgs_images &fwd, const float *dL_drgb,
                                     const float *dL_ddepth, const float *dL_dalpha, int persistent_ctas,
                                     cudaStream_t s) {
     const int B = cam.tile_w * cam.tile_h / kPix;
     const int n_tiles = V * cam.T;
-    const size_t sm = comp_smem(B, true);
-    const void *kern = (const void *)composite_bwd_kernel<NV>;
+    const size_t sm = comp_smem(B, true, ACC);
+    const void *kern = (const void *)composite_bwd_kernel<NV, ACC>;
     uint32_t *work = nullptr;
     int grid = n_tiles;
     if (persistent_ctas > 0) {
@@ -554,10 +557,22 @@ static cudaError_t composite_bwd_as(const RenderWs &ws, const uint32_t *ival, in
     if (grid == 0) return cudaSuccess;
     if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     VPGS_LAUNCH("composite_bwd", s,
-                launch_k(composite_bwd_kernel<NV>, grid, B, sm, s, ws.rec, ival, ws.ranges,
+                launch_k(composite_bwd_kernel<NV, ACC>, grid, B, sm, s, ws.rec, ival, ws.ranges,
                          VPGS_TILE_ORDER ? (const uint32_t *)ws.tile_order : nullptr, n_tiles, cam, o,
                          fwd.t_final, fwd.n_iter, dL_drgb, dL_ddepth, dL_dalpha, ws.g2d, ws.status, work));
     return cudaGetLastError();
+}
+
+template <int NV>
+static cudaError_t composite_bwd_nv(int acc, const RenderWs &ws, const uint32_t *ival, int V,
+                                    const CamParams &cam, const OptParams &o, const vpgs_images &fwd,
+                                    const float *dL_drgb, const float *dL_ddepth, const float *dL_dalpha,
+                                    int persistent_ctas, cudaStream_t s) {
+    switch (acc) {
+    case 1: return composite_bwd_as<NV, 1>(ws, ival, V, cam, o, fwd, dL_drgb, dL_ddepth, dL_dalpha, persistent_ctas, s);
+    case 2: return composite_bwd_as<NV, 2>(ws, ival, V, cam, o, fwd, dL_drgb, dL_ddepth, dL_dalpha, persistent_ctas, s);
+    default: return composite_bwd_as<NV, 0>(ws, ival, V, cam, o, fwd, dL_drgb, dL_ddepth, dL_dalpha, persistent_ctas, s);
+    }
 }
 
 cudaError_t launch_composite_bwd(const RenderWs &ws, const uint32_t *ival, int V,
@@ -565,9 +580,12 @@ cudaError_t launch_composite_bwd(const RenderWs &ws, const uint32_t *ival, int V
                                  const float *dL_drgb, const float *dL_ddepth,
                                  const float *dL_dalpha, bool geometric_only, int persistent_ctas,
                                  cudaStream_t s) {
+    // per-warp shared slots pay off as soon as a tile has warps' sums to combine
+    const int warps = cam.tile_w * cam.tile_h / kPix / 32;
+    const int acc = VPGS_BWD_ACC >= 0 ? VPGS_BWD_ACC : (warps >= 2 ? 1 : 0);
     return geometric_only
-               ? composite_bwd_as<6>(ws, ival, V, cam, o, fwd, dL_drgb, dL_ddepth, dL_dalpha, persistent_ctas, s)
-               : composite_bwd_as<10>(ws, ival, V, cam, o, fwd, dL_drgb, dL_ddepth, dL_dalpha, persistent_ctas, s);
+               ? composite_bwd_nv<6>(acc, ws, ival, V, cam, o, fwd, dL_drgb, dL_ddepth, dL_dalpha, persistent_ctas, s)
+               : composite_bwd_nv<10>(acc, ws, ival, V, cam, o, fwd, dL_drgb, dL_ddepth, dL_dalpha, persistent_ctas, s);
 }
 
 }  // namespace vpgs

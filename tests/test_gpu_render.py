@@ -117,6 +117,19 @@ def test_geometric_backward_without_colour_or_opacity(planes, planes_ref, keys):
     assert_pose_close(dpose2, ref["d_pose"])
 
 
+@pytest.mark.parametrize("tile", [(8, 16), (8, 8), (32, 8)])
+def test_backward_parity_other_tile_shapes(planes, planes_ref, tile):
+    """A one-warp tile (8x8, two pixels per thread) adds its sums of a Gaussian by
+    global atomics, larger tiles combine their warps' sums through per-warp
+    shared slots first: both match the oracle."""
+    ref, gm = planes_ref
+    r, g, T, out = _gpu_forward(planes, tile_w=tile[0], tile_h=tile[1])
+    grads, dpose = _gpu_backward(r, g, T, out, gm)
+    for k in GRAD_KEYS:
+        assert_grad_close(grads[k], ref["d_" + k], k)
+    assert_pose_close(dpose, ref["d_pose"])
+
+
 @pytest.mark.parametrize("tile", [(16, 16), (8, 16), (32, 8), (8, 32), (16, 8), (8, 8)])
 def test_tile_shape_does_not_change_the_image(planes, planes_ref, tile):
     ref, _ = planes_ref
