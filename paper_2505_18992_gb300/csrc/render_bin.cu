@@ -62,8 +62,17 @@ emit_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__ inst
             const BinRec *__restrict__ bin, const uint32_t *n_vis, const uint32_t *n_inst, int64_t N,
             int64_t M_cap, CamParams cam, uint32_t *__restrict__ ikey, uint32_t *__restrict__ ival,
             uint32_t *status, int n_pass, SortPass p0, SortPass p1, SortPass p2, SortPass p3,
-            uint32_t *hist) {
+            uint32_t *hist, uint32_t *look0) {
     grid_dep_enter();
+    {
+        // the tile sort's first-pass look-back words, for the tiles that will hold
+        // instances (the instance count is known from here on)
+        const int64_t ni = min((int64_t)*n_inst, M_cap);
+        const int64_t tile = (int64_t)kSortThreads * kTileSortItems;
+        const int64_t nw = (ni + tile - 1) / tile * kRadix;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += (int64_t)gridDim.x * blockDim.x)
+            look0[i] = 0u;
+    }
     // digit histograms of the emitted tile ids, for the tile sort
     __shared__ uint32_t s_h[4][kRadix];
     const SortPass tps[4] = {p0, p1, p2, p3};
@@ -296,7 +305,7 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
                                                           emit_grid),
                               kEmitThreads, 0, s, dval, inst_off, ws.bin, n_vis, n_inst, L.N, L.M_cap,
                                                     cam, ws.ikey[0], ws.ival[0], ws.status, np_tile, tps[0],
-                                                    tps[1], tps[2], tps[3], ws.sort_hist[1]));
+                                                    tps[1], tps[2], tps[3], ws.sort_hist[1], ws.sort_look[1]));
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // 4. stable sort by tile id

@@ -556,7 +556,7 @@ cudaError_t launch_preprocess_fwd(const GaussIn &g, const double *T_cw, int V, c
     z.w32[1] = ws.counters;                    z.n32[1] = CNT_N;
     z.w32[2] = ws.sort_hist[0];                z.n32[2] = 2 * 4 * kRadix;  // both sorts
     z.w32[3] = ws.sort_look[0];                z.n32[3] = sort_blocks(std::max<int64_t>(L.VN, 1), kDepthSortItems) * kRadix;
-    z.w32[4] = ws.sort_look[1];                z.n32[4] = sort_blocks(L.M_cap, kTileSortItems) * kRadix;
+    z.w32[4] = ws.sort_look[1];                z.n32[4] = 0;  // zeroed by emit, sized by the instance count
     z.w32[5] = reinterpret_cast<uint32_t *>(ws.ranges);  z.n32[5] = 2 * (int64_t)V * cam.T;
     z.w64 = ws.scan_look[0];                   z.n64 = 2 * L.scan_blocks_max;  // both scans
     static int prep_grid = 0;
