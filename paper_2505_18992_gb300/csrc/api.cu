@@ -89,6 +89,7 @@ bool make_layout(int64_t N, int V, const vpgs_camera *cam, const vpgs_render_opt
     L.off_bin = take(sizeof(BinRec) * (size_t)VN1);
     L.off_vis_idx = take(4 * (size_t)VN1);
     L.off_tile_order = take(4 * (size_t)V * L.T);
+    L.off_tile_work = take(4 * (size_t)V * L.T);
     L.total = off;
     return true;
 }
@@ -120,6 +121,7 @@ RenderWs carve(void *base, const RenderLayout &L) {
     w.bin = reinterpret_cast<BinRec *>(b + L.off_bin);
     w.vis_idx = reinterpret_cast<uint32_t *>(b + L.off_vis_idx);
     w.tile_order = reinterpret_cast<uint32_t *>(b + L.off_tile_order);
+    w.tile_work = reinterpret_cast<uint32_t *>(b + L.off_tile_work);
     return w;
 }
 
@@ -318,10 +320,15 @@ vpgs_status vpgs_render_bwd(void *ws, size_t ws_bytes, const vpgs_gaussians *g,
     } else {
         // recompute projection, binning and per-tile sort
         e = launch_preprocess_fwd(S.g, T_cw, n_views, S.cam, S.o, S.ws, S.L, true, s);
-        if (e == cudaSuccess) e = build_tile_lists(S.g, n_views, S.cam, S.ws, S.L, &buf, s);
+        if (e == cudaSuccess)
+            e = build_tile_lists(S.g, n_views, S.cam, S.ws, S.L, &buf, s, !(VPGS_TILE_ORDER && VPGS_BWD_ORDER_NITER));
         if (e == cudaSuccess) tag_set(tag);
         else tag_clear(ws);
     }
+    // the backward walks each tile's list only as far as its pixels' n_iter: launch
+    // the tiles with the most steps first
+    if (e == cudaSuccess && VPGS_TILE_ORDER && VPGS_BWD_ORDER_NITER)
+        e = order_tiles_by_steps(S.ws, fwd->n_iter, n_views, S.cam, s);
     // no opacity or colour gradient asked for (pose tracking): the compositing
     // backward sums only the slots the means, covariances, depths and pose need
     const bool geometric_only = !gg.opac && !gg.colors;

@@ -299,7 +299,7 @@ struct RenderLayout {
     size_t off_status, off_counters, off_rec, off_tcount, off_dkey0,
         off_dval0, off_dkey1, off_dval1, off_ikey0, off_ival0, off_ikey1, off_ival1, off_ranges,
         off_sort_hist, off_sort_look, off_sort_look_t, off_scan_look, off_g2d, off_posedf, off_bin,
-        off_vis_idx, off_tile_order, total;
+        off_vis_idx, off_tile_order, off_tile_work, total;
     int64_t sort_blocks_max, scan_blocks_max;
 };
 
@@ -332,7 +332,8 @@ struct RenderWs {
     float *posedf;        // [V,24] poses as double-float pairs
     BinRec *bin;          // [VN] binning records of visible Gaussians
     uint32_t *vis_idx;    // [VN] visible (view, Gaussian) indices in index order
-    uint32_t *tile_order; // [V*T] global tile ids, most instances first (compositing launch order)
+    uint32_t *tile_order; // [V*T] global tile ids, most work first (compositing launch order)
+    uint32_t *tile_work;  // [V*T] the backward's list steps per tile (the forward's largest n_iter)
 };
 
 // radix sort geometry
@@ -353,6 +354,11 @@ constexpr int kMaxSortPasses = 8;
 // bucketed counting sort after the tile ranges), 0 = tile-id order
 #ifndef VPGS_TILE_ORDER
 #define VPGS_TILE_ORDER 1
+#endif
+// backward launch order: 1 = by the steps each tile's backward walks (the
+// largest n_iter of its pixels, from the forward), 0 = by instance count
+#ifndef VPGS_BWD_ORDER_NITER
+#define VPGS_BWD_ORDER_NITER 1
 #endif
 
 // scan geometry

@@ -52,7 +52,11 @@ cudaError_t launch_preprocess_bwd(const GaussIn &g, const double *T_cw, int V, c
 // render_bin.cu: visibility compaction, depth sort, instance emission, tile
 // sort and tile ranges.  On return ws.ival[*sorted_buf] holds the tile lists.
 cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, const RenderWs &ws,
-                             const RenderLayout &L, int *sorted_buf, cudaStream_t s);
+                             const RenderLayout &L, int *sorted_buf, cudaStream_t s, bool order_by_count = true);
+// Compositing launch order from the forward's n_iter: tiles by the backward's
+// list steps, most first (ws.tile_work, ws.tile_order).
+cudaError_t order_tiles_by_steps(const RenderWs &ws, const int32_t *n_iter, int V, const CamParams &cam,
+                                 cudaStream_t s);
 // Which ival buffer build_tile_lists leaves the tile lists in (host only, no launch).
 int tile_list_buffer(const RenderLayout &L);
 

@@ -192,13 +192,21 @@ constexpr int kOrderThreads = 1024;
 constexpr int kOrderBins = 1024;
 constexpr int kOrderPer = 8;
 
-VPGS_D uint32_t order_bucket(uint2 r) {
-    const uint32_t c = r.y > r.x ? r.y - r.x : 0u;
+// work of tile i: its step count if given, else its instance count
+VPGS_D uint32_t order_bucket(const uint2 *ranges, const uint32_t *work, int i) {
+    uint32_t c;
+    if (work) {
+        c = work[i];
+    } else {
+        const uint2 r = ranges[i];
+        c = r.y > r.x ? r.y - r.x : 0u;
+    }
     return min(c >> 2, (uint32_t)kOrderBins - 1u);
 }
 
 __global__ void __launch_bounds__(kOrderThreads)
-tile_order_kernel(const uint2 *__restrict__ ranges, int n_tiles, uint32_t *__restrict__ order) {
+tile_order_kernel(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ work, int n_tiles,
+                  uint32_t *__restrict__ order) {
     grid_dep_enter();
     __shared__ uint32_t s_bin[kOrderBins];
     __shared__ uint32_t s_warp[kOrderThreads / 32];
@@ -209,7 +217,7 @@ tile_order_kernel(const uint2 *__restrict__ ranges, int n_tiles, uint32_t *__res
 #pragma unroll
         for (int k = 0; k < kOrderPer; ++k) {
             const int i = tid + k * kOrderThreads;
-            bk[k] = i < n_tiles ? order_bucket(ranges[i]) : (uint32_t)kOrderBins;
+            bk[k] = i < n_tiles ? order_bucket(ranges, work, i) : (uint32_t)kOrderBins;
         }
     }
     for (int i = tid; i < kOrderBins; i += kOrderThreads) s_bin[i] = 0u;
@@ -219,7 +227,7 @@ tile_order_kernel(const uint2 *__restrict__ ranges, int n_tiles, uint32_t *__res
         for (int k = 0; k < kOrderPer; ++k)
             if (bk[k] < (uint32_t)kOrderBins) atomicAdd(&s_bin[bk[k]], 1u);
     } else {
-        for (int i = tid; i < n_tiles; i += kOrderThreads) atomicAdd(&s_bin[order_bucket(ranges[i])], 1u);
+        for (int i = tid; i < n_tiles; i += kOrderThreads) atomicAdd(&s_bin[order_bucket(ranges, work, i)], 1u);
     }
     __syncthreads();
     // exclusive scan over the buckets from the heaviest (thread j holds bucket kOrderBins-1-j)
@@ -251,8 +259,46 @@ tile_order_kernel(const uint2 *__restrict__ ranges, int n_tiles, uint32_t *__res
             if (bk[k] < (uint32_t)kOrderBins) order[atomicAdd(&s_bin[bk[k]], 1u)] = (uint32_t)(tid + k * kOrderThreads);
     } else {
         for (int i = tid; i < n_tiles; i += kOrderThreads)
-            order[atomicAdd(&s_bin[order_bucket(ranges[i])], 1u)] = (uint32_t)i;
+            order[atomicAdd(&s_bin[order_bucket(ranges, work, i)], 1u)] = (uint32_t)i;
     }
+}
+
+// The backward's steps per tile: the largest n_iter (list position of the last
+// Gaussian a pixel blended, from the forward) over the tile's pixels.  One warp
+// per tile.
+constexpr int kWorkThreads = 256;
+
+__global__ void __launch_bounds__(kWorkThreads)
+tile_work_kernel(const int32_t *__restrict__ n_iter, CamParams cam, int n_tiles, uint32_t *__restrict__ work) {
+    grid_dep_enter();
+    const int t = (int)((blockIdx.x * (unsigned)kWorkThreads + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (t >= n_tiles) return;  // whole warps
+    const int v = t / cam.T, lt = t - v * cam.T;
+    const int ty = lt / cam.tiles_x, tx = lt - ty * cam.tiles_x;
+    const int64_t base = (int64_t)v * cam.H * cam.W;
+    int m = 0;
+    for (int i = lane; i < cam.tile_w * cam.tile_h; i += 32) {
+        const int px = tx * cam.tile_w + i % cam.tile_w, py = ty * cam.tile_h + i / cam.tile_w;
+        if (px < cam.W && py < cam.H) m = max(m, n_iter[base + (int64_t)py * cam.W + px]);
+    }
+    m = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(m, 0));
+    if (lane == 0) work[t] = (uint32_t)m;
+}
+
+cudaError_t order_tiles_by_steps(const RenderWs &ws, const int32_t *n_iter, int V, const CamParams &cam,
+                                 cudaStream_t s) {
+    const int n_tiles = V * cam.T;
+    if (n_tiles == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)(((int64_t)n_tiles * 32 + kWorkThreads - 1) / kWorkThreads);
+    VPGS_LAUNCH("tile_work", s, launch_k(tile_work_kernel, blocks, kWorkThreads, 0, s, n_iter, cam, n_tiles,
+                                         ws.tile_work));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    VPGS_LAUNCH("tile_order", s, launch_k(tile_order_kernel, 1, kOrderThreads, 0, s,
+                                          (const uint2 *)ws.ranges, (const uint32_t *)ws.tile_work, n_tiles,
+                                          ws.tile_order));
+    return cudaGetLastError();
 }
 
 int tile_list_buffer(const RenderLayout &L) {
@@ -272,7 +318,7 @@ int device_sm_count() {
 }
 
 cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, const RenderWs &ws,
-                             const RenderLayout &L, int *sorted_buf, cudaStream_t s) {
+                             const RenderLayout &L, int *sorted_buf, cudaStream_t s, bool order_by_count) {
     cudaError_t e;
     const int sms = device_sm_count();
     (void)sms;
@@ -323,9 +369,10 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
                 launch_k(tile_ranges_kernel, (unsigned)std::max<int64_t>(rb, 1), 256, 0, s,
                     in1 ? ws.ikey[1] : ws.ikey[0], L.M_cap, n_inst, (uint32_t)n_tiles, ws.ranges));
     e = cudaGetLastError();
-    if (e != cudaSuccess || !VPGS_TILE_ORDER) return e;
+    if (e != cudaSuccess || !VPGS_TILE_ORDER || !order_by_count) return e;
     // 6. compositing launch order
-    VPGS_LAUNCH("tile_order", s, launch_k(tile_order_kernel, 1, kOrderThreads, 0, s, ws.ranges, n_tiles, ws.tile_order));
+    VPGS_LAUNCH("tile_order", s, launch_k(tile_order_kernel, 1, kOrderThreads, 0, s, (const uint2 *)ws.ranges,
+                                          (const uint32_t *)nullptr, n_tiles, ws.tile_order));
     return cudaGetLastError();
 }
 
