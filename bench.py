@@ -640,6 +640,7 @@ def batched_rows(dev, steps=10):
     import torch
 
     from paper_2505_18992_gb300 import scenes
+    from paper_2505_18992_gb300 import vpgs as C
     from paper_2505_18992_gb300.render import Intrinsics, Renderer
     sc = scenes.batched_keyframes()
     cam = sc.camera
@@ -671,9 +672,17 @@ def batched_rows(dev, steps=10):
     mb = _time_ms(batched, steps)
     ms = _time_ms(separate, steps)
     px = V * H * W
+    # per-kernel device times of a batched call (CUDA events on the launching stream)
+    C.vpgs_profile_enable(1)
+    for _ in range(3):
+        batched()
+    torch.cuda.synchronize()
+    prof = C.profile_collect()
+    C.vpgs_profile_enable(0)
     row = {"views": V, "gaussians": sc.n, "width": W, "height": H,
            "batched_ms": mb, "separate_ms": ms, "batched_mpix_s": px / (mb * 1e-3) / 1e6,
-           "separate_mpix_s": px / (ms * 1e-3) / 1e6}
+           "separate_mpix_s": px / (ms * 1e-3) / 1e6,
+           "kernels_us_per_call": {k: round(1000 * t / 3, 1) for k, (n, t) in prof.items()}}
     # launch shape picked by the autotuner (tile shape x persistent CTAs x views per call)
     from paper_2505_18992_gb300 import autotune
     del outb, outs
@@ -685,7 +694,7 @@ def batched_rows(dev, steps=10):
                                   "views_per_call": best.views_per_call},
                         "ms": timings[best], "mpix_s": px / (timings[best] * 1e-3) / 1e6,
                         "candidates": len(timings),
-                        "default_ms": timings.get(autotune.LaunchShape(8, 16, 0, V))}
+                        "default_ms": timings.get(autotune.LaunchShape(16, 16, 0, V))}
     return row
 
 

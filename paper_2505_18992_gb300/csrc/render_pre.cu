@@ -335,35 +335,24 @@ preprocess_bwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamPara
                       const uint32_t *n_vis) {
     grid_dep_enter();
     __shared__ double s_pose[8][6];
+    __shared__ int s_views[2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t tix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t gi = tix;
-    bool live;
-    if (vis) {
-        // one view: walk the visible list (index order), so every lane of a warp has work
-        const int64_t nv = *n_vis;
-        if ((int64_t)blockIdx.x * blockDim.x >= nv) return;  // whole block past the list
-        live = tix < nv;
-        gi = live ? (int64_t)vis[tix] : 0;
-    } else {
-        int64_t nl = g.N;
-        if (g.n_dev) nl = min(nl, (int64_t)*g.n_dev);
-        live = gi < nl;
-    }
-    float gm[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, go = 0.f, gc[3] = {0, 0, 0};
-    float mx = 0, my = 0, mz = 0, sx = 1, sy = 1, sz = 1;
-    float4 q = make_float4(1, 0, 0, 0);
-    if (live) {
-        mx = g.means[3 * gi]; my = g.means[3 * gi + 1]; mz = g.means[3 * gi + 2];
-        sx = g.scales[3 * gi]; sy = g.scales[3 * gi + 1]; sz = g.scales[3 * gi + 2];
-        q = reinterpret_cast<const float4 *>(g.quats)[gi];
-    }
-    bool any = false;  // visible in some view
-    for (int v = 0; v < V; ++v) {
+    // one thread per visible (view, Gaussian) pair of the compacted list (ascending
+    // pair index, so views come in order and a block spans one or two of them);
+    // block-uniform grid-stride loop
+    const int64_t nv = min((int64_t)*n_vis, (int64_t)V * g.N);
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nv; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t kk = base + threadIdx.x;
+        const bool live = kk < nv;
+        const int64_t i = live ? (int64_t)vis[kk] : 0;
+        const int v = (int)(i / g.N);
+        const int64_t gi = i - (int64_t)v * g.N;
+        float gm[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, go = 0.f, gc[3] = {0, 0, 0};
         float pv[6] = {0, 0, 0, 0, 0, 0};
-        const int64_t i = (int64_t)v * g.N + gi;
-        if (live && ws.tcount[i] > 0) {
-            any = true;
+        if (live) {
+            const float mx = g.means[3 * gi], my = g.means[3 * gi + 1], mz = g.means[3 * gi + 2];
+            const float sx = g.scales[3 * gi], sy = g.scales[3 * gi + 1], sz = g.scales[3 * gi + 2];
+            const float4 q = reinterpret_cast<const float4 *>(g.quats)[gi];
             const float *g2 = ws.g2d + 10 * i;  // [u, v, a, b, c, o, r, g, b, z]
             const float2 a01 = reinterpret_cast<const float2 *>(g2)[0];
             const float2 a23 = reinterpret_cast<const float2 *>(g2)[1];
@@ -471,40 +460,48 @@ preprocess_bwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamPara
             pv[5] = p.px * gpy - p.py * gpx + (A[3] - A[1]);
         }
         if (dpose) {
-            // FP32 within a warp (32 terms), FP64 across warps and blocks
+            // FP32 within a warp (32 terms), FP64 across warps and blocks, per view
+            if (threadIdx.x == 0) {
+                s_views[0] = (int)((int64_t)vis[base] / g.N);
+                s_views[1] = (int)((int64_t)vis[min(base + (int64_t)blockDim.x, nv) - 1] / g.N);
+            }
+            __syncthreads();
+            const int v_lo = s_views[0], v_hi = s_views[1];
+            for (int vv = v_lo; vv <= v_hi; ++vv) {
 #pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                float s = warp_sum(pv[k]);
-                if (lane == 0) s_pose[warp][k] = (double)s;
+                for (int k = 0; k < 6; ++k) {
+                    const float sm = warp_sum(live && v == vv ? pv[k] : 0.f);
+                    if (lane == 0) s_pose[warp][k] = (double)sm;
+                }
+                __syncthreads();
+                if (threadIdx.x < 6) {
+                    double t = 0.0;
+                    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_pose[w][threadIdx.x];
+                    if (t != 0.0) atomicAdd(dpose + 6 * vv + threadIdx.x, t);
+                }
+                __syncthreads();
             }
-            __syncthreads();
-            if (threadIdx.x < 6) {
-                double t = 0.0;
-                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_pose[w][threadIdx.x];
-                if (t != 0.0) atomicAdd(dpose + 6 * v + threadIdx.x, t);
-            }
-            __syncthreads();
         }
-    }
-    if (!live || !any) return;
-    // += as fire-and-forget reductions: no load round trip (one thread per Gaussian,
-    // so nothing contends)
-    auto add = [](float *p, float x) {
-        if (x != 0.f) atomicAdd(p, x);
-    };
-    if (gg.means) {
-        add(gg.means + 3 * gi, gm[0]); add(gg.means + 3 * gi + 1, gm[1]); add(gg.means + 3 * gi + 2, gm[2]);
-    }
-    if (gg.scales) {
-        add(gg.scales + 3 * gi, gs[0]); add(gg.scales + 3 * gi + 1, gs[1]); add(gg.scales + 3 * gi + 2, gs[2]);
-    }
-    if (gg.quats) {
+        if (!live) continue;
+        // += as fire-and-forget reductions: no load round trip (a Gaussian seen by
+        // several views gets one reduction per view)
+        auto add = [](float *p, float x) {
+            if (x != 0.f) atomicAdd(p, x);
+        };
+        if (gg.means) {
+            add(gg.means + 3 * gi, gm[0]); add(gg.means + 3 * gi + 1, gm[1]); add(gg.means + 3 * gi + 2, gm[2]);
+        }
+        if (gg.scales) {
+            add(gg.scales + 3 * gi, gs[0]); add(gg.scales + 3 * gi + 1, gs[1]); add(gg.scales + 3 * gi + 2, gs[2]);
+        }
+        if (gg.quats) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) add(gg.quats + 4 * gi + k, gq[k]);
-    }
-    if (gg.opac) add(gg.opac + gi, go);
-    if (gg.colors) {
-        add(gg.colors + 3 * gi, gc[0]); add(gg.colors + 3 * gi + 1, gc[1]); add(gg.colors + 3 * gi + 2, gc[2]);
+            for (int k = 0; k < 4; ++k) add(gg.quats + 4 * gi + k, gq[k]);
+        }
+        if (gg.opac) add(gg.opac + gi, go);
+        if (gg.colors) {
+            add(gg.colors + 3 * gi, gc[0]); add(gg.colors + 3 * gi + 1, gc[1]); add(gg.colors + 3 * gi + 2, gc[2]);
+        }
     }
 }
 
@@ -589,10 +586,14 @@ cudaError_t launch_preprocess_bwd(const GaussIn &g, const double *T_cw, int V, c
                                   const OptParams &o, const RenderWs &ws, const GaussGrad &gg,
                                   double *dpose, cudaStream_t s) {
     if (g.N == 0) return cudaSuccess;
-    const uint32_t *list = V == 1 ? ws.vis_idx : nullptr;
+    // enough blocks for the visible pairs of a large frame at full occupancy; the
+    // live count is read on the device
+    static int bwd_grid = 0;
+    if (bwd_grid == 0) bwd_grid = 8 * std::max(device_sm_count(), 1) * VPGS_PRE_BWD_MINB;
+    const int64_t VN = (int64_t)V * g.N;
     VPGS_LAUNCH("preprocess_bwd", s,
-                launch_k(preprocess_bwd_kernel, (unsigned)((g.N + 255) / 256), 256, 0, s,
-                    g, T_cw, V, cam, o, ws, gg, dpose, list, ws.counters + CNT_VISIBLE));
+                launch_k(preprocess_bwd_kernel, (unsigned)std::min<int64_t>((VN + 255) / 256, bwd_grid), 256, 0, s,
+                    g, T_cw, V, cam, o, ws, gg, dpose, (const uint32_t *)ws.vis_idx, ws.counters + CNT_VISIBLE));
     return cudaGetLastError();
 }
 
