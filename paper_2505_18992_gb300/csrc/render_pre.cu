@@ -220,60 +220,83 @@ VPGS_D uint32_t project_one(const PoseDF &P, float mx, float my, float mz, float
     return cnt;
 }
 
-// Pass 1, one thread per (view, Gaussian): finiteness check, opacity test and
-// the FP32 pre-cull.  Survivors are appended to a candidate list (block-level
-// ballot compaction, one atomic per block); everything else gets tile count 0.
+// Pass 1, one thread per Gaussian over all views: finiteness check, opacity test
+// and the FP32 pre-cull of each (view, Gaussian) pair.  Survivors are appended
+// to a candidate list (block-level compaction, one atomic per block and round
+// of 8 views); every other pair gets tile count 0.
 constexpr int kPreThreads = 256;
 
 __global__ void __launch_bounds__(kPreThreads)
 precull_kernel(GaussIn g, int V, CamParams cam, OptParams o, RenderWs ws, uint32_t *cand,
                uint32_t *n_cand) {
     grid_dep_enter();
+    // one thread per Gaussian: its parameters are read once and tested against up
+    // to 8 views per round; the block appends all its kept (view, Gaussian) pairs
+    // with one scan and one atomic per round
     __shared__ int s_wcnt[kPreThreads / 32];
     __shared__ uint32_t s_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t i = (int64_t)blockIdx.x * kPreThreads + tid;
-    const int64_t VN = (int64_t)V * g.N;
+    const int64_t gi = (int64_t)blockIdx.x * kPreThreads + tid;
     int64_t nl = g.N;
     if (g.n_dev) nl = min(nl, (int64_t)*g.n_dev);
-    bool keep = false;
-    if (i < VN) {
-        const int v = (int)(i / g.N);
-        const int64_t gi = i - (int64_t)v * g.N;
-        if (gi < nl) {
-            const float mx = g.means[3 * gi], my = g.means[3 * gi + 1], mz = g.means[3 * gi + 2];
-            const float sx = g.scales[3 * gi], sy = g.scales[3 * gi + 1], sz = g.scales[3 * gi + 2];
-            const float4 q = reinterpret_cast<const float4 *>(g.quats)[gi];
-            const float op = g.opac[gi];
-            const float cr = g.colors[3 * gi], cg = g.colors[3 * gi + 1], cb = g.colors[3 * gi + 2];
-            const float chk = mx + my + mz + sx + sy + sz + q.x + q.y + q.z + q.w + op + cr + cg + cb;
-            if (!isfinite(chk)) {
-                set_status(ws.status, VPGS_ERR_NONFINITE);
-            } else if (op >= o.alpha_min) {
-                PoseDF P;
-                load_pose(ws.posedf + 24 * v, P);
-                // fast log, widened by 1e-3 relative for the bound
-                keep = maybe_in_view(P, mx, my, mz, fmaxf(fabsf(sx), fmaxf(fabsf(sy), fabsf(sz))),
-                                     2.002f * __logf(op / o.alpha_min) + 1e-3f, cam, o);
+    bool ok = false;  // live, finite and opaque enough
+    float mx = 0, my = 0, mz = 0, smax = 0, kq = 0;
+    if (gi < g.N && gi < nl) {
+        mx = g.means[3 * gi]; my = g.means[3 * gi + 1]; mz = g.means[3 * gi + 2];
+        const float sx = g.scales[3 * gi], sy = g.scales[3 * gi + 1], sz = g.scales[3 * gi + 2];
+        const float4 q = reinterpret_cast<const float4 *>(g.quats)[gi];
+        const float op = g.opac[gi];
+        const float cr = g.colors[3 * gi], cg = g.colors[3 * gi + 1], cb = g.colors[3 * gi + 2];
+        const float chk = mx + my + mz + sx + sy + sz + q.x + q.y + q.z + q.w + op + cr + cg + cb;
+        if (!isfinite(chk)) {
+            set_status(ws.status, VPGS_ERR_NONFINITE);
+        } else if (op >= o.alpha_min) {
+            ok = true;
+            smax = fmaxf(fabsf(sx), fmaxf(fabsf(sy), fabsf(sz)));
+            // fast log, widened by 1e-3 relative for the bound
+            kq = 2.002f * __logf(op / o.alpha_min) + 1e-3f;
+        }
+    }
+    for (int v0 = 0; v0 < V; v0 += 8) {  // block-uniform
+        const int nv = min(8, V - v0);
+        uint32_t keep = 0u;  // bit dv: view v0 + dv kept
+        if (gi < g.N) {
+            for (int dv = 0; dv < nv; ++dv) {
+                bool k = false;
+                if (ok) {
+                    PoseDF P;
+                    load_pose(ws.posedf + 24 * (v0 + dv), P);
+                    k = maybe_in_view(P, mx, my, mz, smax, kq, cam, o);
+                }
+                if (k) keep |= 1u << dv;
+                else ws.tcount[(int64_t)(v0 + dv) * g.N + gi] = 0u;
             }
         }
-        if (!keep) ws.tcount[i] = 0u;
-    }
-    const uint32_t m = __ballot_sync(0xffffffffu, keep);
-    if (lane == 0) s_wcnt[warp] = __popc(m);
-    __syncthreads();
-    if (tid == 0) {
-        int t = 0;
+        // block exclusive scan of the kept counts
+        const int c = __popc(keep);
+        int x = c;
 #pragma unroll
-        for (int w = 0; w < kPreThreads / 32; ++w) t += s_wcnt[w];
-        s_base = t ? atomicAdd(n_cand, (uint32_t)t) : 0u;
-    }
-    __syncthreads();
-    if (keep) {
-        int base = 0;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) s_wcnt[warp] = x;
+        __syncthreads();
+        if (tid == 0) {
+            int t = 0;
 #pragma unroll
-        for (int w = 0; w < kPreThreads / 32; ++w) base += w < warp ? s_wcnt[w] : 0;
-        cand[s_base + base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
+            for (int w = 0; w < kPreThreads / 32; ++w) t += s_wcnt[w];
+            s_base = t ? atomicAdd(n_cand, (uint32_t)t) : 0u;
+        }
+        __syncthreads();
+        if (keep) {
+            int pos = x - c;
+#pragma unroll
+            for (int w = 0; w < kPreThreads / 32; ++w) pos += w < warp ? s_wcnt[w] : 0;
+            for (int dv = 0; dv < nv; ++dv)
+                if (keep & (1u << dv)) cand[s_base + pos++] = (uint32_t)((int64_t)(v0 + dv) * g.N + gi);
+        }
+        __syncthreads();  // s_wcnt and s_base are reused by the next round
     }
 }
 
@@ -566,7 +589,7 @@ cudaError_t launch_preprocess_fwd(const GaussIn &g, const double *T_cw, int V, c
     // the candidate list borrows the second depth-key buffer (free until the depth sort)
     uint32_t *cand = ws.dkey[1], *n_cand = ws.counters + CNT_CAND;
     VPGS_LAUNCH("preprocess_fwd", s,
-                launch_k(precull_kernel, (unsigned)((VN + kPreThreads - 1) / kPreThreads), kPreThreads, 0, s,
+                launch_k(precull_kernel, (unsigned)((g.N + kPreThreads - 1) / kPreThreads), kPreThreads, 0, s,
                     g, V, cam, o, ws, cand, n_cand));
     static int proj_grid = 0;
     if (proj_grid == 0) {
