@@ -344,7 +344,8 @@ constexpr int kSortThreads = 256;
 #ifndef VPGS_TILE_SORT_ITEMS
 #define VPGS_TILE_SORT_ITEMS 16
 #endif
-constexpr int kDepthSortItems = VPGS_DEPTH_SORT_ITEMS;  // keys per thread in the depth sort
+constexpr int kDepthSortItems = VPGS_DEPTH_SORT_ITEMS;  // keys per thread in the depth sort (<= 16)
+static_assert(kDepthSortItems <= 16, "the depth sort's look-back space must cover the 16-key form");
 constexpr int kTileSortItems = VPGS_TILE_SORT_ITEMS;    // keys per thread in the tile-id sort
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;

@@ -331,9 +331,13 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
     // 2. depth sort
     bool in1 = false;
     // (digit histograms from the projection kernel)
+    // keys per thread: few for a frame's worth of visible Gaussians (short tiles
+    // start the look-back chain sooner), more for many views' worth (fewer tiles
+    // in the chain); the look-back space is sized for kDepthSortItems, the most tiles
+    const int depth_items = L.VN > (int64_t(4) << 20) ? 16 : kDepthSortItems;
     e = radix_sort_pairs("sort_depth_pass", ws.dkey[0], ws.dval[0], ws.dkey[1], ws.dval[1], L.VN, n_vis,
                          0, 32, ws.sort_hist[0], ws.counters + CNT_TICKET_D, ws.sort_look[0], ws.status, s,
-                         &in1, kDepthSortItems);
+                         &in1, depth_items);
     if (e != cudaSuccess) return e;
     const uint32_t *dval = in1 ? ws.dval[1] : ws.dval[0];  // visible records in depth order
     uint32_t *inst_off = in1 ? ws.dkey[0] : ws.dkey[1];  // the depth-sort buffer not holding the result
