@@ -710,6 +710,7 @@ def fusion_rows(dev, iters=10):
     import torch
 
     from paper_2505_18992_gb300 import scenes
+    from paper_2505_18992_gb300 import vpgs as C
     from paper_2505_18992_gb300.decode import Decoder
     from paper_2505_18992_gb300.fusion import Adam, DistillLoss
     from paper_2505_18992_gb300.render import Intrinsics, Renderer
@@ -778,11 +779,19 @@ def fusion_rows(dev, iters=10):
     torch.cuda.synchronize()
     losses.append(float(dist.loss[0]))
     ms = e0.elapsed_time(e1) / iters
+    # per-kernel device times of an iteration (CUDA events on the launching stream)
+    C.vpgs_profile_enable(1)
+    for _ in range(2):
+        iteration()
+    torch.cuda.synchronize()
+    prof = C.profile_collect()
+    C.vpgs_profile_enable(0)
     return {"submaps": 2, "keyframes": m, "width": W, "height": H,
             "gaussians_decoded": [int(st["out"]["n_dev"].item()) for st in state],
             "ms_per_iteration": ms, "mpix_s": 2 * m * P / (ms * 1e-3) / 1e6,
             "loss": {"first": losses[0], f"after_{iters + 1}": losses[1]},
-            "peak_hbm_gb": torch.cuda.max_memory_allocated(dev) / 1e9}
+            "peak_hbm_gb": torch.cuda.max_memory_allocated(dev) / 1e9,
+            "kernels_us_per_iteration": {k: round(1000 * t / 2, 1) for k, (n, t) in prof.items()}}
 
 
 def icp_rows(dev, reps=20):

@@ -50,14 +50,17 @@ struct OffsetStore {
 };
 
 // Emits the (global tile id, record) instances of 256 consecutive depth-ranked
-// Gaussians per block.  The block's instances are spread evenly over its
-// threads; each finds its Gaussian by binary search over the block's local
-// offsets, so a Gaussian covering thousands of tiles does not serialise, and
-// then its tile by walking the Gaussian's tile rows with the same row-span
-// function that counted them.
+// Gaussians per block.  The instances of Gaussians spanning at most kCoverRows
+// tile rows are spread evenly over the block's threads; each finds its Gaussian
+// by binary search over the block's local offsets, so a Gaussian covering many
+// tiles does not serialise, and then its tile from the row spans the counting
+// pass stored.  A Gaussian spanning more rows takes one warp: one row per lane,
+// its span from the same row-span function that counted it, a warp prefix of
+// the rows' counts, and each lane writing its row's run of tiles.
 constexpr int kEmitThreads = 256;
 
-__global__ void __launch_bounds__(kEmitThreads)
+// 6 blocks per SM (40 registers): the instance loop is latency-bound and wants them
+__global__ void __launch_bounds__(kEmitThreads, 6)
 emit_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__ inst_off,
             const BinRec *__restrict__ bin, const uint32_t *n_vis, const uint32_t *n_inst, int64_t N,
             int64_t M_cap, CamParams cam, uint32_t *__restrict__ ikey, uint32_t *__restrict__ ival,
@@ -78,12 +81,15 @@ emit_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__ inst
     const SortPass tps[4] = {p0, p1, p2, p3};
     for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0u;
     __shared__ uint32_t s_start[kEmitThreads], s_id[kEmitThreads], s_vb[kEmitThreads];
+    __shared__ uint32_t s_sstart[kEmitThreads];  // starts counting only the small Gaussians' instances
+    __shared__ uint16_t s_large[kEmitThreads];   // chunk positions of the large Gaussians
+    __shared__ uint32_t s_wsum[kEmitThreads / 32][2];
     __shared__ uint2 s_rect[kEmitThreads];
     __shared__ float4 s_uv[kEmitThreads];
     __shared__ Cover s_cv[kEmitThreads];
-    __shared__ uint32_t s_total;
+    __shared__ uint32_t s_total, s_small, s_nlarge;
     const int64_t nv = *n_vis;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     bool overflow = false;
     // chunks of kEmitThreads depth-ranked Gaussians, grid-strided (the grid is
     // sized to what fits on the GPU, not to the capacity)
@@ -111,56 +117,128 @@ emit_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__ inst
         overflow = true;  // block-uniform
         continue;
     }
-    for (uint32_t e = tid; e < total; e += kEmitThreads) {
-        int lo = 0, hi = nb - 1;  // last Gaussian whose local start is <= e
+    // Gaussians spanning more than kCoverRows tile rows are emitted row-parallel
+    // below; the instance loop covers the others, through a prefix of their counts
+    // (the chunk's own offsets when it has no large Gaussian, the common case)
+    bool large = false;
+    uint32_t cnt = 0u;
+    if (tid < nb) {
+        const uint2 rc = s_rect[tid];
+        large = (int)(rc.y >> 16) - (int)(rc.y & 0xffffu) + 1 > kCoverRows;
+        cnt = (tid + 1 < nb ? s_start[tid + 1] : total) - s_start[tid];
+    }
+    const bool any_large = __syncthreads_or(large) != 0;
+    if (any_large) {
+        uint32_t xs = large ? 0u : cnt, xl = large ? 1u : 0u;  // inclusive scans
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t ys = __shfl_up_sync(0xffffffffu, xs, o), yl = __shfl_up_sync(0xffffffffu, xl, o);
+            if (lane >= o) {
+                xs += ys;
+                xl += yl;
+            }
+        }
+        if (lane == 31) {
+            s_wsum[warp][0] = xs;
+            s_wsum[warp][1] = xl;
+        }
+        __syncthreads();
+        uint32_t ps = 0u, pl = 0u, ts = 0u, tl = 0u;
+#pragma unroll
+        for (int w = 0; w < kEmitThreads / 32; ++w) {
+            if (w < warp) {
+                ps += s_wsum[w][0];
+                pl += s_wsum[w][1];
+            }
+            ts += s_wsum[w][0];
+            tl += s_wsum[w][1];
+        }
+        s_sstart[tid] = ps + xs - (large ? 0u : cnt);
+        if (large) s_large[pl + xl - 1u] = (uint16_t)tid;
+        if (tid == 0) {
+            s_small = ts;
+            s_nlarge = tl;
+        }
+        __syncthreads();
+    }
+    const uint32_t *pref = any_large ? s_sstart : s_start;
+    const uint32_t total_small = any_large ? s_small : total;
+    for (uint32_t e = tid; e < total_small; e += kEmitThreads) {
+        int lo = 0, hi = nb - 1;  // last Gaussian whose (small-instance) start is <= e
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (s_start[mid] <= e) lo = mid;
+            if (pref[mid] <= e) lo = mid;
             else hi = mid - 1;
         }
-        uint32_t local = e - s_start[lo];
+        uint32_t local = e - pref[lo];
+        const uint32_t at = s_start[lo] + local;
         const uint2 rc = s_rect[lo];
         const Cover cv = s_cv[lo];
-        const int tx_lo = (int)(rc.x & 0xffffu), tx_hi = (int)(rc.x >> 16);
         const int ty_lo = (int)(rc.y & 0xffffu), ty_hi = (int)(rc.y >> 16);
         uint32_t key = 0xffffffffu;
-        if (ty_hi - ty_lo + 1 <= kCoverRows) {
-            // spans stored by the counting pass
-            const uint32_t pk[kCoverRows] = {__float_as_uint(cv.a.x), __float_as_uint(cv.a.y),
-                                             __float_as_uint(cv.a.z), __float_as_uint(cv.a.w),
-                                             __float_as_uint(cv.b.x), __float_as_uint(cv.b.y),
-                                             __float_as_uint(cv.b.z), __float_as_uint(cv.b.w)};
+        // spans stored by the counting pass
+        const uint32_t pk[kCoverRows] = {__float_as_uint(cv.a.x), __float_as_uint(cv.a.y),
+                                         __float_as_uint(cv.a.z), __float_as_uint(cv.a.w),
+                                         __float_as_uint(cv.b.x), __float_as_uint(cv.b.y),
+                                         __float_as_uint(cv.b.z), __float_as_uint(cv.b.w)};
 #pragma unroll
-            for (int r = 0; r < kCoverRows; ++r) {
-                const uint32_t t0 = pk[r] & 0xffffu, t1 = pk[r] >> 16;
-                const uint32_t n = t0 <= t1 ? t1 - t0 + 1u : 0u;
-                if (key == 0xffffffffu && r <= ty_hi - ty_lo) {
-                    if (local < n)
-                        key = s_vb[lo] + (uint32_t)(ty_lo + r) * (uint32_t)cam.tiles_x + t0 + local;
-                    else
-                        local -= n;
-                }
-            }
-        } else {
-            const float4 uv = s_uv[lo];
-            for (int ty = ty_lo; ty <= ty_hi; ++ty) {
-                const int2 sp = cover_row(cv, uv.x, uv.z, uv.y, uv.w, ty, tx_lo, tx_hi, cam.tw_shift,
-                                          cam.tile_h, cam.W, cam.H);
-                const uint32_t n = sp.x <= sp.y ? (uint32_t)(sp.y - sp.x + 1) : 0u;
-                if (local < n) {
-                    key = s_vb[lo] + (uint32_t)ty * (uint32_t)cam.tiles_x + (uint32_t)sp.x + local;
-                    break;
-                }
-                local -= n;
+        for (int r = 0; r < kCoverRows; ++r) {
+            const uint32_t t0 = pk[r] & 0xffffu, t1 = pk[r] >> 16;
+            const uint32_t n = t0 <= t1 ? t1 - t0 + 1u : 0u;
+            if (key == 0xffffffffu && r <= ty_hi - ty_lo) {
+                if (local < n)
+                    key = s_vb[lo] + (uint32_t)(ty_lo + r) * (uint32_t)cam.tiles_x + t0 + local;
+                else
+                    local -= n;
             }
         }
         if (key == 0xffffffffu) {  // the rows hold fewer tiles than were counted: never in a sound build
             set_status(status, VPGS_ERR_INTERNAL);
             key = 0u;
         }
-        ikey[base + e] = key;
-        ival[base + e] = s_id[lo];
+        ikey[base + at] = key;
+        ival[base + at] = s_id[lo];
         add_digits(s_h, tps, n_pass, key);
+    }
+    // large Gaussians: one warp each, one tile row per lane, a warp prefix of the
+    // rows' counts, each lane writing its row's run of tiles
+    const uint32_t n_large = any_large ? s_nlarge : 0u;
+    for (uint32_t j = warp; j < n_large; j += kEmitThreads / 32) {
+        const int t = s_large[j];
+        const uint2 rc = s_rect[t];
+        const Cover cv = s_cv[t];
+        const float4 uv = s_uv[t];
+        const int tx_lo = (int)(rc.x & 0xffffu), tx_hi = (int)(rc.x >> 16);
+        const int ty_lo = (int)(rc.y & 0xffffu), ty_hi = (int)(rc.y >> 16);
+        const uint32_t start = s_start[t], end = (t + 1 < nb ? s_start[t + 1] : total);
+        const uint32_t vb = s_vb[t], id = s_id[t];
+        uint32_t running = start;
+        for (int ty0 = ty_lo; ty0 <= ty_hi; ty0 += 32) {  // warp-uniform
+            const int ty = ty0 + lane;
+            int2 sp = make_int2(1, 0);
+            if (ty <= ty_hi)
+                sp = cover_row(cv, uv.x, uv.z, uv.y, uv.w, ty, tx_lo, tx_hi, cam.tw_shift, cam.tile_h, cam.W, cam.H);
+            const uint32_t n = sp.x <= sp.y ? (uint32_t)(sp.y - sp.x + 1) : 0u;
+            uint32_t x = n;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            const uint32_t at = running + x - n;
+            for (uint32_t k = 0; k < n; ++k) {
+                if (at + k >= end) {  // more tiles than were counted: never in a sound build
+                    set_status(status, VPGS_ERR_INTERNAL);
+                    break;
+                }
+                const uint32_t key = vb + (uint32_t)ty * (uint32_t)cam.tiles_x + (uint32_t)sp.x + k;
+                ikey[base + at + k] = key;
+                ival[base + at + k] = id;
+                add_digits(s_h, tps, n_pass, key);
+            }
+            running += __shfl_sync(0xffffffffu, x, 31);
+        }
+        if (lane == 0 && running != end) set_status(status, VPGS_ERR_INTERNAL);
     }
     __syncthreads();  // the next chunk reuses the shared arrays
     }
@@ -187,10 +265,10 @@ __global__ void tile_ranges_kernel(const uint32_t *__restrict__ keys, int64_t ca
 // block: tiles are bucketed by count / 4 (the last bucket takes every count
 // beyond), buckets are laid out from the heaviest down, and each tile takes a
 // slot in its bucket by a shared-memory atomic.  Up to kOrderPer tiles per
-// thread are loaded at once and kept in registers between the two passes.
+// thread are loaded at once and kept in registers (packed) between the passes.
 constexpr int kOrderThreads = 1024;
 constexpr int kOrderBins = 1024;
-constexpr int kOrderPer = 8;
+constexpr int kOrderPer = 32;
 
 // work of tile i: its step count if given, else its instance count
 VPGS_D uint32_t order_bucket(const uint2 *ranges, const uint32_t *work, int i) {
@@ -212,12 +290,17 @@ tile_order_kernel(const uint2 *__restrict__ ranges, const uint32_t *__restrict__
     __shared__ uint32_t s_warp[kOrderThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool fits = n_tiles <= kOrderThreads * kOrderPer;  // block-uniform
-    uint32_t bk[kOrderPer];  // bucket of tile tid + k * kOrderThreads (kOrderBins: none)
+    // bucket of tile tid + k * kOrderThreads (kOrderBins: none), two 16-bit buckets
+    // per register (a 1,024-thread block has 64 registers per thread)
+    uint32_t bk[kOrderPer / 2];
+    auto bucket_of = [&](int k) { return (bk[k >> 1] >> (16 * (k & 1))) & 0xffffu; };
     if (fits) {
 #pragma unroll
         for (int k = 0; k < kOrderPer; ++k) {
             const int i = tid + k * kOrderThreads;
-            bk[k] = i < n_tiles ? order_bucket(ranges, work, i) : (uint32_t)kOrderBins;
+            const uint32_t b = i < n_tiles ? order_bucket(ranges, work, i) : (uint32_t)kOrderBins;
+            if (k & 1) bk[k >> 1] |= b << 16;
+            else bk[k >> 1] = b;
         }
     }
     for (int i = tid; i < kOrderBins; i += kOrderThreads) s_bin[i] = 0u;
@@ -225,7 +308,7 @@ tile_order_kernel(const uint2 *__restrict__ ranges, const uint32_t *__restrict__
     if (fits) {
 #pragma unroll
         for (int k = 0; k < kOrderPer; ++k)
-            if (bk[k] < (uint32_t)kOrderBins) atomicAdd(&s_bin[bk[k]], 1u);
+            if (bucket_of(k) < (uint32_t)kOrderBins) atomicAdd(&s_bin[bucket_of(k)], 1u);
     } else {
         for (int i = tid; i < n_tiles; i += kOrderThreads) atomicAdd(&s_bin[order_bucket(ranges, work, i)], 1u);
     }
@@ -256,7 +339,8 @@ tile_order_kernel(const uint2 *__restrict__ ranges, const uint32_t *__restrict__
     if (fits) {
 #pragma unroll
         for (int k = 0; k < kOrderPer; ++k)
-            if (bk[k] < (uint32_t)kOrderBins) order[atomicAdd(&s_bin[bk[k]], 1u)] = (uint32_t)(tid + k * kOrderThreads);
+            if (bucket_of(k) < (uint32_t)kOrderBins)
+                order[atomicAdd(&s_bin[bucket_of(k)], 1u)] = (uint32_t)(tid + k * kOrderThreads);
     } else {
         for (int i = tid; i < n_tiles; i += kOrderThreads)
             order[atomicAdd(&s_bin[order_bucket(ranges, work, i)], 1u)] = (uint32_t)i;

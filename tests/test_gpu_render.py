@@ -158,6 +158,30 @@ def test_multiview_pose_gradients_and_ragged_image():
     assert_pose_close(dpose, ref["d_pose"])
 
 
+@pytest.mark.parametrize("tile,height", [((8, 8), 123), ((16, 16), 290)])
+def test_large_gaussians_spanning_many_tile_rows(tile, height):
+    """Gaussians taller than 8 tile rows are emitted row-parallel (one warp per
+    Gaussian): their tile counts, image and gradients still match the oracle."""
+    sc = scenes.random_gaussians(40, 161, height, 90.0, seed=17, scale_range=(0.15, 0.6), depth=(1.2, 3.0))
+    r, g, T, out = _gpu_forward(sc, tile_w=tile[0], tile_h=tile[1])
+    p = {k: v.cpu().numpy() for k, v in r.project(*g, T).items()}
+    cnt, rect = p["tile_count"][0], p["tile_rect"][0]  # rect: tx0, tx1, ty0, ty1
+    assert ((rect[:, 3] - rect[:, 2] + 1)[cnt > 0] > 8).sum() >= 5  # the row-parallel path is taken
+    ref0 = oracle.render_scene(sc)
+    cover = oracle.tile_cover(ref0["proj"][0], sc.opacities, sc.camera.width, sc.camera.height,
+                              Options(tile_w=tile[0], tile_h=tile[1]))
+    mask = tile_count_mask(ref0["extent"][0], sc.opacities) | cover["flags"]
+    assert np.array_equal(cnt[~mask], cover["count"][~mask])
+    assert_images_close(out, ref0, ref0["flags"], what=f"large {tile}")
+    g_up = scenes.upstream_grads(19, 1, height, 161)
+    gm = masked_upstream(g_up, ref0["flags"])
+    ref = oracle.render_scene(sc, grads=gm)
+    grads, dpose = _gpu_backward(r, g, T, out, gm)
+    for k in GRAD_KEYS:
+        assert_grad_close(grads[k], ref["d_" + k], k)
+    assert_pose_close(dpose, ref["d_pose"])
+
+
 def test_background_and_depth_only_upstream():
     sc = scenes.random_gaussians(200, 64, 48, 60.0, seed=5, scale_range=(0.02, 0.2))
     bg = (0.2, 0.4, 0.6)
