@@ -265,10 +265,10 @@ __global__ void tile_ranges_kernel(const uint32_t *__restrict__ keys, int64_t ca
 // block: tiles are bucketed by count / 4 (the last bucket takes every count
 // beyond), buckets are laid out from the heaviest down, and each tile takes a
 // slot in its bucket by a shared-memory atomic.  Up to kOrderPer tiles per
-// thread are loaded at once and kept in registers (packed) between the passes.
+// thread (8, or 32 past 8,192 tiles) are loaded at once and kept in registers
+// (packed) between the passes.
 constexpr int kOrderThreads = 1024;
 constexpr int kOrderBins = 1024;
-constexpr int kOrderPer = 32;
 
 // work of tile i: its step count if given, else its instance count
 VPGS_D uint32_t order_bucket(const uint2 *ranges, const uint32_t *work, int i) {
@@ -282,6 +282,7 @@ VPGS_D uint32_t order_bucket(const uint2 *ranges, const uint32_t *work, int i) {
     return min(c >> 2, (uint32_t)kOrderBins - 1u);
 }
 
+template <int kOrderPer>
 __global__ void __launch_bounds__(kOrderThreads)
 tile_order_kernel(const uint2 *__restrict__ ranges, const uint32_t *__restrict__ work, int n_tiles,
                   uint32_t *__restrict__ order) {
@@ -379,9 +380,14 @@ cudaError_t order_tiles_by_steps(const RenderWs &ws, const int32_t *n_iter, int 
                                          ws.tile_work));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    VPGS_LAUNCH("tile_order", s, launch_k(tile_order_kernel, 1, kOrderThreads, 0, s,
-                                          (const uint2 *)ws.ranges, (const uint32_t *)ws.tile_work, n_tiles,
-                                          ws.tile_order));
+    if (n_tiles <= kOrderThreads * 8)
+        VPGS_LAUNCH("tile_order", s, launch_k(tile_order_kernel<8>, 1, kOrderThreads, 0, s,
+                                              (const uint2 *)ws.ranges, (const uint32_t *)ws.tile_work, n_tiles,
+                                              ws.tile_order));
+    else
+        VPGS_LAUNCH("tile_order", s, launch_k(tile_order_kernel<32>, 1, kOrderThreads, 0, s,
+                                              (const uint2 *)ws.ranges, (const uint32_t *)ws.tile_work, n_tiles,
+                                              ws.tile_order));
     return cudaGetLastError();
 }
 
@@ -459,8 +465,12 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
     e = cudaGetLastError();
     if (e != cudaSuccess || !VPGS_TILE_ORDER || !order_by_count) return e;
     // 6. compositing launch order
-    VPGS_LAUNCH("tile_order", s, launch_k(tile_order_kernel, 1, kOrderThreads, 0, s, (const uint2 *)ws.ranges,
-                                          (const uint32_t *)nullptr, n_tiles, ws.tile_order));
+    if (n_tiles <= kOrderThreads * 8)
+        VPGS_LAUNCH("tile_order", s, launch_k(tile_order_kernel<8>, 1, kOrderThreads, 0, s, (const uint2 *)ws.ranges,
+                                              (const uint32_t *)nullptr, n_tiles, ws.tile_order));
+    else
+        VPGS_LAUNCH("tile_order", s, launch_k(tile_order_kernel<32>, 1, kOrderThreads, 0, s, (const uint2 *)ws.ranges,
+                                              (const uint32_t *)nullptr, n_tiles, ws.tile_order));
     return cudaGetLastError();
 }
 
