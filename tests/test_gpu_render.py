@@ -182,6 +182,24 @@ def test_large_gaussians_spanning_many_tile_rows(tile, height):
     assert_pose_close(dpose, ref["d_pose"])
 
 
+def test_many_tiles_render_every_tile_once():
+    """43,200 tiles (3 views of 1280x720 in 8x8 tiles) are more than the
+    launch-order kernel keeps in registers (32 per thread): every tile is still
+    composited once, forward (full images against the oracle) and backward
+    (against the same render in 16x16 tiles, 10,800 tiles)."""
+    sc = scenes.random_gaussians(1500, 1280, 720, 700.0, seed=23, scale_range=(0.005, 0.03), n_views=3)
+    ref = oracle.render_scene(sc)
+    r8, g, T, out8 = _gpu_forward(sc, tile_w=8, tile_h=8, instances_per_gaussian=64)
+    assert_images_close(out8, ref, ref["flags"], what="8x8, 43,200 tiles")
+    r16, _, _, out16 = _gpu_forward(sc, tile_w=16, tile_h=16)
+    gm = masked_upstream(scenes.upstream_grads(29, 3, 720, 1280), ref["flags"])
+    a, pa = _gpu_backward(r8, g, T, out8, gm)
+    b, pb = _gpu_backward(r16, g, T, out16, gm)
+    for k in GRAD_KEYS:
+        assert_grad_close(a[k], b[k], k)
+    assert_pose_close(pa, pb)
+
+
 def test_background_and_depth_only_upstream():
     sc = scenes.random_gaussians(200, 64, 48, 60.0, seed=5, scale_range=(0.02, 0.2))
     bg = (0.2, 0.4, 0.6)
