@@ -1,6 +1,7 @@
 // Per-Gaussian projection (EWA splatting) and its backward pass.
 //
-// Forward, one thread per (view, Gaussian):
+// Forward (a pre-cull with one thread per Gaussian over all views, then the
+// exact projection with one thread per surviving (view, Gaussian)):
 //   p_c = R mu + t (double-float), u = fx x/z + cx, v = fy y/z + cy (double-float)
 //   Sigma' = J R Sigma R^T J^T + dilation I = K K^T + dilation I,  K = J R R(q) S
 //   det(Sigma') via the Lagrange identity |K0 x K1|^2 + ... (no cancellation)
@@ -10,8 +11,8 @@
 //           exact one; the alpha test at each pixel then decides membership
 //   tile count: the tiles of that box whose pixel-centre rectangle (widened
 //           by the same margins) meets the alpha_min ellipse, row by row
-// Backward, one thread per Gaussian, looping over views: chain rule from the
-// 2D gradients (u, v, conic, opacity, colour, depth) back to mean, scale,
+// Backward, one thread per visible (view, Gaussian): chain rule from the 2D
+// gradients (u, v, conic, opacity, colour, depth) back to mean, scale,
 // quaternion, opacity and colour, plus the per-view pose terms summed in FP64.
 #include "internal.h"
 #include "prims.cuh"
