@@ -236,6 +236,7 @@ precull_kernel(GaussIn g, int V, CamParams cam, OptParams o, RenderWs ws, uint32
     // with one scan and one atomic per round
     __shared__ int s_wcnt[kPreThreads / 32];
     __shared__ uint32_t s_base;
+    __shared__ float s_pose[8 * 24];  // the round's poses (double-float pairs)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t gi = (int64_t)blockIdx.x * kPreThreads + tid;
     int64_t nl = g.N;
@@ -260,13 +261,19 @@ precull_kernel(GaussIn g, int V, CamParams cam, OptParams o, RenderWs ws, uint32
     }
     for (int v0 = 0; v0 < V; v0 += 8) {  // block-uniform
         const int nv = min(8, V - v0);
+        for (int i = tid; i < nv * 24; i += kPreThreads) s_pose[i] = ws.posedf[24 * v0 + i];
+        __syncthreads();
         uint32_t keep = 0u;  // bit dv: view v0 + dv kept
         if (gi < g.N) {
             for (int dv = 0; dv < nv; ++dv) {
                 bool k = false;
                 if (ok) {
+                    const float *pd = s_pose + 24 * dv;
                     PoseDF P;
-                    load_pose(ws.posedf + 24 * (v0 + dv), P);
+#pragma unroll
+                    for (int j = 0; j < 9; ++j) P.R[j] = df{pd[2 * j], pd[2 * j + 1]};
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) P.t[r] = df{pd[18 + 2 * r], pd[19 + 2 * r]};
                     k = maybe_in_view(P, mx, my, mz, smax, kq, cam, o);
                 }
                 if (k) keep |= 1u << dv;
