@@ -164,7 +164,10 @@ vpgs_status vpgs_render_fwd(void *ws, size_t ws_bytes, const vpgs_gaussians *g,
  *   xi = (rho_x, rho_y, rho_z, phi_x, phi_y, phi_z).  The pose is optimised in
  *   the coarse tracking stage (Sec. III-B).  Per-Gaussian pose terms are summed
  *   in float64.
- * Decisions (skips, clamp, stop) are held fixed, as in the forward pass. */
+ * Decisions (skips, clamp, stop) are held fixed, as in the forward pass.
+ * When neither grads->opacities nor grads->colors is asked for (grads NULL, or
+ * both fields NULL, as in pose tracking), the compositing pass sums only the
+ * geometric 2D terms; the requested results are the same. */
 vpgs_status vpgs_render_bwd(void *ws, size_t ws_bytes, const vpgs_gaussians *g,
                             const vpgs_camera *cam, const double *T_cw, int32_t n_views,
                             const vpgs_render_opts *opts, const vpgs_images *fwd,
