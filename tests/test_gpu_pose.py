@@ -15,10 +15,9 @@ from tests.helpers import dev, intrinsics, scene_tensors
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("adam", [False, True])
-def test_pose_step_matches_the_oracle(adam):
+@pytest.mark.parametrize("adam,V", [(False, 3), (True, 3), (True, 40)])
+def test_pose_step_matches_the_oracle(adam, V):
     rng = np.random.default_rng(4)
-    V = 3
     T = np.stack([scenes.perturb_pose(np.eye(4), rng, 0.5, 20.0) for _ in range(V)])
     T_d = dev(T, torch.float64)
     state = np.zeros((V, 13))
