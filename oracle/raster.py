@@ -79,6 +79,10 @@ class Margins:
     clamp: float = 2e-5
     t_stop: float = 2e-4
     depth_tie: float = 1e-6
+    # Exactly equal depths are ordered by Gaussian index on both sides (the
+    # reading of the order rule).  Only Gaussians with bit-identical camera z
+    # on the device as well (identical means) may leave them unflagged.
+    exact_ties: bool = False
 
 
 def _t(x):
@@ -311,6 +315,8 @@ def _composite_block(px, py, cand, g2, opts: Options, margins: Margins, want_fla
             prev = torch.cat([torch.full((P, 1), -math.inf, dtype=F64),
                               torch.cummax(zsel, dim=1).values[:, :-1]], 1)
             gap = (zz - prev) <= margins.depth_tie * zz.abs()
+            if margins.exact_ties:
+                gap &= zz != prev
             flags |= (sel & gap).any(1)
     return rgb, depth, T_fin, n_contrib, flags
 

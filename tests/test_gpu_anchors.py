@@ -4,8 +4,15 @@ Tolerances.  Counts, kept indices, spawning samples, new-anchor and grown
 positions are bit-exact: both sides take every decision in float32 and
 back-project in FP64 with the same operation order.  The statistics' sums are
 FP32 atomics against FP64: within 1e-5 of the value (plus 1e-6 absolute).
-Threshold decisions on those sums are compared on the GPU's own sums, with
-thresholds chosen at least 1e-5 (relative) away from every anchor's value.
+
+Pruning and growth are decided by the oracle on its own FP64 statistics (the
+same decode and render inputs, accumulated by `oracle.anchors`), never on the
+GPU's sums.  An anchor's float32 statistics differ from the FP64 ones by at
+most a few ulps (a float32 norm, a sum of at most k terms, the float32
+product tau * count: under 1e-6 relative for k = 10), so a threshold at least
+1e-5 (relative) away from an anchor's oracle average decides the same on both
+sides.  Thresholds are picked that way; where a fixed threshold lands closer
+than that to some anchor, both decisions of that anchor are accepted.
 """
 import importlib
 
@@ -74,6 +81,26 @@ def _pick_threshold(values, lo, hi):
     raise AssertionError("no clean threshold")
 
 
+def _near_threshold(stats, tau_g, tau_o, rel=1e-5):
+    """Anchors whose oracle average lies within rel of the growth / pruning threshold."""
+    c, v = stats["g_cnt"], stats["visits"]
+    avg = np.where(c > 0, stats["g_sum"] / np.maximum(c, 1), np.inf)
+    per_visit = np.where(v > 0, stats["o_sum"] / np.maximum(v, 1), np.inf)
+    return np.abs(avg - tau_g) <= rel * tau_g, np.abs(per_visit - tau_o) <= rel * tau_o
+
+
+def _grow_either_way(stats, near, src, k, means, tau_g, voxel, anchors):
+    """The oracle's grown anchors for every decision of the anchors in `near`."""
+    idx = np.nonzero(near)[0]
+    outs = []
+    for bits in range(1 << len(idx)):
+        s = {key: np.array(val, copy=True) for key, val in stats.items()}
+        for n, a in enumerate(idx):  # force the decision clearly to one side
+            s["g_sum"][a] = (2.0 if (bits >> n) & 1 else 0.5) * tau_g * s["g_cnt"][a]
+        outs.append(A.grow(s, src, k, means, tau_g, voxel, anchors))
+    return outs
+
+
 @pytest.mark.parametrize("n_anchors", [1, 3_001, 20_011])
 def test_prune_and_grow_match_the_oracle(n_anchors):
     from paper_2505_18992_gb300.anchors import AnchorStats, AnchorUpdate
@@ -82,11 +109,10 @@ def test_prune_and_grow_match_the_oracle(n_anchors):
     k = 10
     anchors, src, means, grads, opac, vis = _decode_like(rng, n_anchors, k)
     st = AnchorStats(n_anchors)
+    s = A.new_stats(n_anchors)  # the oracle's own FP64 statistics of the same two steps
     for _ in range(2):
         st.accumulate(k, dev(src, torch.int32), dev(grads), dev(opac), dev(vis, torch.int32))
-    s = {key: v.astype(np.float64) for key, v in _stats_np(st).items()}
-    s["g_cnt"] = s["g_cnt"].astype(np.int64)
-    s["visits"] = s["visits"].astype(np.int64)
+        A.accumulate_stats(s, src, k, grads, opac, vis)
     avg = s["g_sum"][s["g_cnt"] > 0] / s["g_cnt"][s["g_cnt"] > 0]
     per_visit = s["o_sum"][s["visits"] > 0] / s["visits"][s["visits"] > 0]
     if len(avg) > 10:
@@ -179,9 +205,15 @@ def test_bench_workloads_match_the_oracle():
     up = AnchorUpdate(len(stp.anchors), len(stp.src_index), **u)
     up(st, stp.k, dev(stp.src_index, torch.int32), dev(stp.means), amap)
     keep, grown = (x.cpu().numpy() for x in up.results())
-    assert np.array_equal(keep, A.prune(got, u["tau_o"]))  # decisions on the GPU's own float32 sums
-    assert np.array_equal(grown, A.grow(got, stp.src_index, stp.k, stp.means, u["tau_g"], u["grow_voxel"],
-                                        stp.anchors))
+    # decisions on the oracle's own FP64 statistics; an anchor whose average lies
+    # within 1e-5 (relative) of a fixed threshold may go either way
+    near_g, near_o = _near_threshold(ref, u["tau_g"], u["tau_o"])
+    assert near_g.sum() + near_o.sum() <= 5
+    assert np.array_equal(np.setdiff1d(keep, np.nonzero(near_o)[0]),
+                          np.setdiff1d(A.prune(ref, u["tau_o"]), np.nonzero(near_o)[0]))
+    assert any(np.array_equal(grown, w) for w in
+               _grow_either_way(ref, near_g, stp.src_index, stp.k, stp.means, u["tau_g"], u["grow_voxel"],
+                                stp.anchors))
     fr = scenes.keyframe_spawn()
     sp_ = bench.SPAWN
     gmap = VoxelMap(dev(fr.gauss_means), sp_["map_voxel"])

@@ -232,6 +232,33 @@ def test_two_gaussians_hand_worked_and_depth_order():
     assert np.allclose(out["rgb"][0, :, 4, 4], [0.5 * 0.6, 0.5, 0.0], atol=1e-15)
 
 
+def test_equal_depths_are_ordered_by_index():
+    # Two isotropic Gaussians at the identical mean (equal z): the lower index
+    # composites first, C = o0 c0 + (1 - o0) o1 c1 at the shared pixel centre.
+    # The pixel is flagged as a possible depth tie unless exact ties are accepted.
+    from oracle.raster import Margins
+    W = H = 9
+    f = 10.0
+    means = np.array([[0.0, 0.0, 2.5], [0.0, 0.0, 2.5]])
+    scales = np.array([[0.05] * 3, [0.08] * 3])
+    quats = np.tile([1.0, 0, 0, 0], (2, 1))
+    opac = np.array([0.6, 0.5])
+    cols = np.array([[1.0, 0, 0], [0, 1.0, 0]])
+    args = (np.eye(4)[None], f, f, 4.5, 4.5, W, H)
+    out = oracle.render(means, scales, quats, opac, cols, *args)
+    assert np.allclose(out["rgb"][0, :, 4, 4], [0.6, 0.4 * 0.5, 0.0], atol=1e-15)
+    assert out["flags"][0, 4, 4]
+    out = oracle.render(means, scales, quats, opac, cols, *args, margins=Margins(exact_ties=True))
+    assert not out["flags"][0, 4, 4]
+    # the same two Gaussians listed the other way round: green first
+    out = oracle.render(means[::-1].copy(), scales[::-1].copy(), quats, opac[::-1].copy(), cols[::-1].copy(), *args)
+    assert np.allclose(out["rgb"][0, :, 4, 4], [0.5 * 0.6, 0.5, 0.0], atol=1e-15)
+    # a depth 1e-9 apart is still flagged with exact ties accepted
+    means[1, 2] += 1e-9
+    out = oracle.render(means, scales, quats, opac, cols, *args, margins=Margins(exact_ties=True))
+    assert out["flags"][0, 4, 4]
+
+
 def test_stop_rule_clamp_and_skip():
     W = H = 5
     f = 10.0
