@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 #include <utility>
 
 #include "../../include/vpgs.h"
@@ -34,6 +35,25 @@
 namespace vpgs {
 
 constexpr int kWarp = 32;
+
+// A launch-geometry value that depends only on the device (an occupancy, a grid
+// size): computed by f() once per device ordinal and kept in `cache` (zero-
+// initialised, one slot per ordinal); ordinals beyond the cache compute it on
+// every call.  Safe to call from several host threads.
+constexpr int kDeviceCache = 64;
+template <typename F>
+int per_device(std::atomic<int> (&cache)[kDeviceCache], F f) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+    if (dev >= 0 && dev < kDeviceCache) {
+        const int v = cache[dev].load(std::memory_order_relaxed);
+        if (v > 0) return v;
+        const int w = std::max(f(), 1);
+        cache[dev].store(w, std::memory_order_relaxed);
+        return w;
+    }
+    return std::max(f(), 1);
+}
 
 // ---------------------------------------------------------------------------
 // status word: the first error wins (atomicCAS from OK)
@@ -191,10 +211,11 @@ VPGS_D void quat_to_rot(float w, float x, float y, float z, float R[9]) {
 //   r1 = (w1x, w1y, w2x, w2y)       whitening rows times sqrt(log2(e)/2):
 //                                   (w1.d)^2 + (w2.d)^2 = log2(e)/2 d^T Sigma'^-1 d
 //   r2 = (opacity, z, r, g)
-//   r3 = (b, rx, ry, kq)            conservative pixel half-extents (alpha >= alpha_min
-//                                   is impossible farther than this from the mean) and
-//                                   kq = 2 ln(o / alpha_min), the largest quadratic form
-//                                   at which alpha >= alpha_min is possible
+//   r3 = (b, w2x_lo, +-ry, w2y_lo)  ry: conservative pixel half-extent in y (alpha >=
+//                                   alpha_min is impossible farther than this from the
+//                                   mean), negative for a near-degenerate Gaussian, whose
+//                                   second whitening row is the double-float pair
+//                                   (w2x + w2x_lo, w2y + w2y_lo) (zero low parts otherwise)
 // The whitening rows are the eigenvectors of Sigma' scaled by 1/sqrt(lambda) (and
 // by sqrt(log2(e)/2), so that alpha needs a single ex2),
 // which evaluates the quadratic form without the cancellation the
@@ -224,6 +245,31 @@ VPGS_D PairEval eval_pair(float dx, float dy, float w1x, float w1y, float w2x, f
     PairEval e;
     e.t1 = fmaf(w1x, dx, w1y * dy);
     e.t2 = fmaf(w2x, dx, w2y * dy);
+    e.G = ex2_approx(-fmaf(e.t1, e.t1, e.t2 * e.t2));
+    e.alpha = fminf(alpha_max, opac * e.G);
+    return e;
+}
+
+// The same for a near-degenerate record: d = (px - ux - rx, py - uy - ry) in
+// double-float (ux, uy the staged tile-local mean, (rx, ry) its rounding
+// residual) and t2 = w2 . d with w2 = (w2x + w2x_lo, w2y + w2y_lo) as an
+// error-free dot product of the high parts plus the low-order terms; t1 stays
+// FP32 (its error is not amplified by the condition number).
+VPGS_D PairEval eval_pair_fine(float px, float py, float ux, float uy, float rx, float ry, float w1x, float w1y,
+                               float w2x, float w2y, float w2x_lo, float w2y_lo, float opac, float alpha_max) {
+    df dx = two_sum(px, -ux), dy = two_sum(py, -uy);
+    dx.lo -= rx;
+    dy.lo -= ry;
+    PairEval e;
+    e.t1 = fmaf(w1x, dx.hi, w1y * dy.hi);
+    const df p1 = two_prod(w2x, dx.hi), p2 = two_prod(w2y, dy.hi);
+    const df sh = two_sum(p1.hi, p2.hi);
+    float lo = sh.lo + (p1.lo + p2.lo);
+    lo = fmaf(w2x, dx.lo, lo);
+    lo = fmaf(w2y, dy.lo, lo);
+    lo = fmaf(w2x_lo, dx.hi, lo);
+    lo = fmaf(w2y_lo, dy.hi, lo);
+    e.t2 = sh.hi + lo;
     e.G = ex2_approx(-fmaf(e.t1, e.t1, e.t2 * e.t2));
     e.alpha = fminf(alpha_max, opac * e.G);
     return e;

@@ -20,9 +20,14 @@
 // giving dC/dalpha_i = T_i (c_i - B_i), dA/dalpha_i = T_final / (1 - alpha_i).
 // Only g . B enters dL/dalpha (g the pixel's upstream gradient), so each pixel
 // carries that scalar instead of B.
-// Per-Gaussian 2D gradient sums (mean terms sum dpow t1 and sum dpow t2, conic
-// a b c, opacity, rgb, z) of a warp are summed by a transpose reduction (12
-// shuffles for 10 values) and added with one atomic per value per warp.
+// Per-Gaussian 2D gradient sums of a warp (in the Gaussian's whitened frame
+// t = W d: sum dpow t1, sum dpow t2, sum dpow t1^2, sum dpow t1 t2, sum dpow
+// t2^2; then opacity, rgb, z) are summed by a transpose reduction (12 shuffles
+// for 10 values) and added with one atomic per value per warp.
+// Near-degenerate records (negative y half extent) take the double-float pair
+// evaluation (eval_pair_fine): one warp-uniform branch per list entry.
+#include <type_traits>
+
 #include "internal.h"
 #include "profiler.h"
 
@@ -64,27 +69,52 @@ VPGS_D float2 warp_rows(const float (&pyl)[kPix]) {
 // Compacts the batch positions [0, n) whose Gaussian's widened y extent reaches
 // the warp's pixel rows into list, in ascending order; returns how many
 // (warp-uniform).  All 32 lanes take part.
-VPGS_D int warp_list(const float4 *s0, const float4 *s1, int n, float2 band, uint16_t *list, int lane) {
+// `fine` tells (warp-uniform) whether a listed record is near-degenerate.
+VPGS_D int warp_list(const float4 *s0, const float4 *s1, int n, float2 band, uint16_t *list, int lane,
+                     bool &fine) {
     const uint32_t below = (1u << lane) - 1u;
     int cnt = 0;
+    bool any = false;
     for (int c0 = 0; c0 < n; c0 += 32) {
         const int k = c0 + lane;
-        bool touch = false;
-        if (k < n) touch = fabsf(s0[k].y - band.x) <= s1[k].w + band.y;
+        bool touch = false, f = false;
+        if (k < n) {
+            const float ry = s1[k].w;
+            touch = fabsf(s0[k].y - band.x) <= fabsf(ry) + band.y;
+            f = touch && ry < 0.f;
+        }
         const uint32_t m = __ballot_sync(0xffffffffu, touch);
+        any |= __any_sync(0xffffffffu, f);
         if (touch) list[cnt + __popc(m & below)] = (uint16_t)k;
         cnt += __popc(m);
     }
     __syncwarp();
+    fine = any;
     return cnt;
 }
 
 // record -> shared staging: s0 = (u, v) tile-local, w1; s1 = w2, opacity, widened
-// y half extent; s2 = colour, camera z
-VPGS_D void stage(const Rec &r, float ox, float oy, float4 &a, float4 &b, float4 &c) {
+// y half extent (negative: near-degenerate); s2 = colour, camera z; and for a
+// near-degenerate record only, s3 = the rounding residual of the tile-local
+// mean and the low parts of w2
+VPGS_D void stage(const Rec &r, float ox, float oy, float4 &a, float4 &b, float4 &c, float4 &f) {
     a = make_float4((r.r0.x - ox) + r.r0.z, (r.r0.y - oy) + r.r0.w, r.r1.x, r.r1.y);
     b = make_float4(r.r1.z, r.r1.w, r.r2.x, r.r3.z);
     c = make_float4(r.r2.z, r.r2.w, r.r3.x, r.r2.y);
+    if (r.r3.z < 0.f) {
+        // (u_hi - ox) + u_lo = a.x + residual, the subtraction split exactly
+        const df ex = two_sum(r.r0.x, -ox), ey = two_sum(r.r0.y, -oy);
+        f = make_float4(((ex.hi - a.x) + r.r0.z) + ex.lo, ((ey.hi - a.y) + r.r0.w) + ey.lo, r.r3.y, r.r3.w);
+    }
+}
+
+// alpha of pixel (px, py) (tile-local) for the staged Gaussian (a, b[, f])
+template <bool kFine>
+VPGS_D PairEval eval_staged(float px, float py, const float4 &a, const float4 &b, const float4 &f, float alpha_max) {
+    if constexpr (kFine)
+        return eval_pair_fine(px, py, a.x, a.y, f.x, f.y, a.z, a.w, b.x, b.y, f.z, f.w, b.z, alpha_max);
+    else
+        return eval_pair(px - a.x, py - a.y, a.z, a.w, b.x, b.y, b.z, alpha_max);
 }
 
 // register cap of the forward (0: only the 512-thread launch bound)
@@ -105,8 +135,8 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
     grid_dep_enter();
     extern __shared__ float4 smem[];
     const int NT = blockDim.x;
-    float4 *s0 = smem, *s1 = smem + NT, *s2 = smem + 2 * NT;
-    uint16_t *s_wl = reinterpret_cast<uint16_t *>(smem + 3 * NT);  // [NW][NT] per-warp lists
+    float4 *s0 = smem, *s1 = smem + NT, *s2 = smem + 2 * NT, *s3 = smem + 3 * NT;
+    uint16_t *s_wl = reinterpret_cast<uint16_t *>(smem + 4 * NT);  // [NW][NT] per-warp lists
     __shared__ int s_tile;
     if (*status != 0u) return;
     const int tid = threadIdx.x, lane = tid & 31;
@@ -147,19 +177,20 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
         for (int b0 = start; b0 < end; b0 += NT) {
             if (__syncthreads_count(all_done) == NT) break;
             const int j = b0 + tid;
-            if (j < end) stage(rec[ival[j]], ox, oy, s0[tid], s1[tid], s2[tid]);
+            if (j < end) stage(rec[ival[j]], ox, oy, s0[tid], s1[tid], s2[tid], s3[tid]);
             __syncthreads();
-            const int nl = warp_list(s0, s1, min(NT, end - b0), band, wl, lane);
-            if (!all_done) {
-                for (int i = 0; i < nl; ++i) {
-                    const int k = wl[i];
-                    const float4 a = s0[k], b = s1[k];
+            bool any_fine;
+            const int nl = warp_list(s0, s1, min(NT, end - b0), band, wl, lane, any_fine);
+            // one blend step of this thread's pixels against list entry k
+            auto blend = [&](int k, const float4 &a, const float4 &b, auto fine) -> bool {
+                    constexpr bool kFine = decltype(fine)::value;
+                    float4 f;
+                    if constexpr (kFine) f = s3[k];
                     bool fin = true;
 #pragma unroll
                     for (int q = 0; q < kPix; ++q) {
                         if (!done[q]) {
-                            const PairEval e = eval_pair(pxl - a.x, pyl[q] - a.y, a.z, a.w, b.x, b.y, b.z,
-                                                         o.alpha_max);
+                            const PairEval e = eval_staged<kFine>(pxl, pyl[q], a, b, f, o.alpha_max);
                             if (e.alpha >= o.alpha_min) {
                                 const float nt = T[q] * (1.f - e.alpha);
                                 if (nt < o.t_min) {
@@ -179,11 +210,29 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                         }
                         fin = fin && done[q];
                     }
+                    return fin;
+            };
+            // the list walk; a batch with a near-degenerate record takes the walk that
+            // chooses the precision form per entry (a warp-uniform branch), the others
+            // the plain one
+            auto walk = [&](auto maybe_fine) {
+                for (int i = 0; i < nl; ++i) {
+                    const int k = wl[i];
+                    const float4 a = s0[k], b = s1[k];
+                    bool fin;
+                    if constexpr (decltype(maybe_fine)::value)
+                        fin = b.w < 0.f ? blend(k, a, b, std::true_type{}) : blend(k, a, b, std::false_type{});
+                    else
+                        fin = blend(k, a, b, std::false_type{});
                     if (fin) {
                         all_done = true;
                         break;
                     }
                 }
+            };
+            if (!all_done) {
+                if (any_fine) walk(std::true_type{});
+                else walk(std::false_type{});
             }
         }
         const int64_t HW = (int64_t)cam.H * cam.W;
@@ -284,8 +333,8 @@ struct PixState {
 // (no opacity or colour sums), the form taken when no opacity or colour
 // gradient is asked for
 template <int NV>
-VPGS_D bool pair_grad(PixState &p, int jj, const PairEval &e, float dx, float dy, const float4 &a,
-                      const float4 &b, const float4 &c, const OptParams &o, float (&v)[NV]) {
+VPGS_D bool pair_grad(PixState &p, int jj, const PairEval &e, const float4 &b, const float4 &c,
+                      const OptParams &o, float (&v)[NV]) {
     if (jj >= p.last || e.alpha < o.alpha_min) return false;
     const float om = 1.f - e.alpha;
 #if VPGS_BWD_RCP
@@ -311,27 +360,32 @@ VPGS_D bool pair_grad(PixState &p, int jj, const PairEval &e, float dx, float dy
     const float dA = fmaf(diff, p.T, gat);
     p.beta = fmaf(e.alpha, diff, p.beta);
     if (b.z * e.G <= o.alpha_max) {
-        // slots 0-4 hold sums without their per-Gaussian factors, applied once per
-        // Gaussian by the preprocess backward: the whitening rows and 2 ln 2 for the
-        // mean (slots 0, 1 = sum dpow t1, sum dpow t2), -1/2, -1, -1/2 for the conic
+        // slots 0-4 hold sums in the Gaussian's whitened frame t = W d, turned into
+        // gradients once per Gaussian by the preprocess backward: sum dpow t1 and
+        // sum dpow t2 for the mean (through the whitening rows and 2 ln 2), and
+        // sum dpow t t^T (t1^2, t1 t2, t2^2) for the covariance (dL/dSigma' =
+        // 2 ln^2 2 W^T S W).  t is O(1) where alpha matters, so these sums keep
+        // their precision however elongated the Gaussian is.
         const float dpow = dA * e.alpha;
         if constexpr (NV == 10) v[5] = fmaf(dA, e.G, v[5]);
-        v[0] = fmaf(dpow, e.t1, v[0]);
-        v[1] = fmaf(dpow, e.t2, v[1]);
-        const float pdx = dpow * dx;
-        v[2] = fmaf(pdx, dx, v[2]);
-        v[3] = fmaf(pdx, dy, v[3]);
-        v[4] = fmaf(dpow * dy, dy, v[4]);
+        const float pt1 = dpow * e.t1, pt2 = dpow * e.t2;
+        v[0] += pt1;
+        v[1] += pt2;
+        v[2] = fmaf(pt1, e.t1, v[2]);
+        v[3] = fmaf(pt1, e.t2, v[3]);
+        v[4] = fmaf(pt2, e.t2, v[4]);
     }
     return true;
 }
 
 constexpr int kPartStride = 11;  // floats per (warp, Gaussian) partial, padded against bank conflicts
 
-// register cap of the backward (0: only the 512-thread launch bound); 80
-// allows 25 resident warps per SM instead of 21 and loses nothing to spills
+// register cap of the backward (0: only the 512-thread launch bound).  72
+// registers keep 7 blocks of 4 warps (28 warps) resident per SM: registers are
+// granted in units of 8 per thread, so 73-80 would leave room for 6 blocks.
+// The backward needs no spill under this cap.
 #ifndef VPGS_BWD_MAXREG
-#define VPGS_BWD_MAXREG 80
+#define VPGS_BWD_MAXREG 72
 #endif
 #if VPGS_BWD_MAXREG > 0
 #define VPGS_BWD_BOUNDS __maxnreg__(VPGS_BWD_MAXREG)
@@ -356,8 +410,8 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
     extern __shared__ float4 smem[];
     const int NT = blockDim.x;
     const int NW = NT >> 5;
-    float4 *s0 = smem, *s1 = smem + NT, *s2 = smem + 2 * NT;
-    uint32_t *s_id = reinterpret_cast<uint32_t *>(smem + 3 * NT);
+    float4 *s0 = smem, *s1 = smem + NT, *s2 = smem + 2 * NT, *s3 = smem + 3 * NT;
+    uint32_t *s_id = reinterpret_cast<uint32_t *>(smem + 4 * NT);
     uint16_t *s_wl = reinterpret_cast<uint16_t *>(s_id + NT);             // [NW][NT] per-warp lists
     float *s_part = reinterpret_cast<float *>(s_wl + (size_t)NW * NT);  // [NW][NT][kPartStride]
     __shared__ int s_tile;
@@ -436,7 +490,7 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
             const int j = b0 + tid;
             if (j < b1) {
                 const uint32_t id = ival[j];
-                stage(rec[id], ox, oy, s0[tid], s1[tid], s2[tid]);
+                stage(rec[id], ox, oy, s0[tid], s1[tid], s2[tid], s3[tid]);
                 s_id[tid] = id;
             }
             if (ACC == 1)
@@ -445,8 +499,12 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                 for (int e = tid; e < nb * kPartStride; e += NT) s_part[e] = 0.f;
             __syncthreads();
             const int k_end = min(nb, warp_max - (b0 - start));  // warp-uniform
-            const int nl = warp_list(s0, s1, k_end, band, wl, lane);
-            // back to front
+            bool any_fine;
+            const int nl = warp_list(s0, s1, k_end, band, wl, lane, any_fine);
+            // back to front; a batch with a near-degenerate record takes the walk that
+            // chooses the precision form per entry (a warp-uniform branch), the others
+            // the plain one
+            auto walk = [&](auto maybe_fine) {
             for (int i = nl - 1; i >= 0; --i) {
                 const int kk = wl[i];
                 const float4 a = s0[kk], b = s1[kk], c = s2[kk];
@@ -454,13 +512,24 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
 #pragma unroll
                 for (int q = 0; q < NV; ++q) v[q] = 0.f;
                 const int jj = b0 + kk - start;
-                bool act = false;
+                // this thread's pixels against the Gaussian
+                auto grads = [&](auto fine) -> bool {
+                    constexpr bool kFine = decltype(fine)::value;
+                    float4 f;
+                    if constexpr (kFine) f = s3[kk];
+                    bool any = false;
 #pragma unroll
-                for (int q = 0; q < kPix; ++q) {
-                    const float dx = pxl - a.x, dy = pyl[q] - a.y;
-                    const PairEval e = eval_pair(dx, dy, a.z, a.w, b.x, b.y, b.z, o.alpha_max);
-                    act |= pair_grad(ps[q], jj, e, dx, dy, a, b, c, o, v);
-                }
+                    for (int q = 0; q < kPix; ++q) {
+                        const PairEval e = eval_staged<kFine>(pxl, pyl[q], a, b, f, o.alpha_max);
+                        any |= pair_grad(ps[q], jj, e, b, c, o, v);
+                    }
+                    return any;
+                };
+                bool act;
+                if constexpr (decltype(maybe_fine)::value)
+                    act = b.w < 0.f ? grads(std::true_type{}) : grads(std::false_type{});
+                else
+                    act = grads(std::false_type{});
                 const uint32_t am = __ballot_sync(0xffffffffu, act);
                 if (ACC == 0 && am != 0u && __popc(am) <= kDirect) {
                     // few active lanes: their own atomics beat a reduction
@@ -475,6 +544,9 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                     if (slot >= 0) put(kk, v[0]);
                 }
             }
+            };
+            if (any_fine) walk(std::true_type{});
+            else walk(std::false_type{});
             if (ACC != 0) {
                 __syncthreads();
                 // one thread per Gaussian of the batch: one global atomic per value
@@ -501,7 +573,7 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
 static size_t comp_smem(int NT, bool bwd, int acc = 0) {
     const size_t parts = acc == 1 ? (size_t)(NT / 32) * NT * kPartStride : (acc == 2 ? (size_t)NT * kPartStride : 0);
     const size_t lists = sizeof(uint16_t) * (size_t)(NT / 32) * NT;
-    return sizeof(float4) * 3 * NT + lists + (bwd ? sizeof(uint32_t) * NT + sizeof(float) * parts : 0);
+    return sizeof(float4) * 4 * NT + lists + (bwd ? sizeof(uint32_t) * NT + sizeof(float) * parts : 0);
 }
 
 static int persistent_grid(const void *kernel, int B, size_t smem, int per_sm, int n_tiles) {

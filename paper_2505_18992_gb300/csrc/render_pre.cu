@@ -133,13 +133,94 @@ prepare_kernel(const double *__restrict__ T_cw, int V, float *posedf, PrepZero z
     for (int64_t v = t0; v < V; v += stride) pose_to_df(T_cw + 16 * v, posedf + 24 * v);
 }
 
+// Near-degenerate 2D covariances.  The FP32 whitening rows carry a direction
+// error of ~1e-7 rad; along a Gaussian of condition number kappa = l1/l2 that
+// moves the second whitened coordinate t2 = w2.d by ~1e-7 sqrt(kappa) at the
+// pixels where alpha matters, and alpha by about that much relative.  Above
+// kFineKappa the covariance and its inverse square root are therefore taken
+// in FP64 from the FP32 inputs, the second row is kept as a double-float pair
+// (its low parts in the record), and the compositing kernels evaluate t2 in
+// double-float for such records (flagged by a negative y half extent).
+constexpr float kFineKappa = 256.f;
+
+struct FineCov {
+    float A, B, C, det;       // Sigma' rounded from FP64
+    float w1x, w1y;           // first whitening row (times kRowScale)
+    df w2x, w2y;              // second whitening row (times kRowScale), double-float
+};
+
+VPGS_D double dsum(const df &x) { return (double)x.hi + (double)x.lo; }
+
+// pd: the view's pose as double-float pairs (re-read here, so that the common
+// path holds no pose registers across this rare one)
+VPGS_D void fine_cov(const float *pd, const df pc[3], float sx, float sy, float sz, float qw, float qx,
+                     float qy, float qz, const CamParams &cam, float dil, FineCov &fc) {
+    const double x = dsum(pc[0]), y = dsum(pc[1]), z = dsum(pc[2]);
+    const double iz = 1.0 / z;
+    const double fx = cam.fx, fy = cam.fy;
+    const double j00 = fx * iz, j02 = -fx * x * iz * iz, j11 = fy * iz, j12 = -fy * y * iz * iz;
+    double w = qw, a = qx, b = qy, c = qz;
+    const double inv = 1.0 / sqrt(w * w + a * a + b * b + c * c);
+    w *= inv; a *= inv; b *= inv; c *= inv;
+    const double Rq[9] = {1.0 - 2.0 * (b * b + c * c), 2.0 * (a * b - w * c), 2.0 * (a * c + w * b),
+                          2.0 * (a * b + w * c), 1.0 - 2.0 * (a * a + c * c), 2.0 * (b * c - w * a),
+                          2.0 * (a * c - w * b), 2.0 * (b * c + w * a), 1.0 - 2.0 * (a * a + b * b)};
+    const double sv[3] = {sx, sy, sz};
+    double K0[3], K1[3];
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+        double wr[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const double R0 = (double)pd[2 * (3 * r)] + (double)pd[2 * (3 * r) + 1];
+            const double R1 = (double)pd[2 * (3 * r + 1)] + (double)pd[2 * (3 * r + 1) + 1];
+            const double R2 = (double)pd[2 * (3 * r + 2)] + (double)pd[2 * (3 * r + 2) + 1];
+            wr[r] = R0 * Rq[col] + R1 * Rq[3 + col] + R2 * Rq[6 + col];
+        }
+        K0[col] = (j00 * wr[0] + j02 * wr[2]) * sv[col];
+        K1[col] = (j11 * wr[1] + j12 * wr[2]) * sv[col];
+    }
+    const double n0 = K0[0] * K0[0] + K0[1] * K0[1] + K0[2] * K0[2];
+    const double n1 = K1[0] * K1[0] + K1[1] * K1[1] + K1[2] * K1[2];
+    const double B = K0[0] * K1[0] + K0[1] * K1[1] + K0[2] * K1[2];
+    const double e = dil, A = n0 + e, C = n1 + e;
+    const double c0 = K0[1] * K1[2] - K0[2] * K1[1], c1 = K0[2] * K1[0] - K0[0] * K1[2],
+                 c2 = K0[0] * K1[1] - K0[1] * K1[0];
+    const double det = (c0 * c0 + c1 * c1 + c2 * c2) + e * (n0 + n1) + e * e;
+    const double h = 0.5 * (A - C), r = sqrt(h * h + B * B);
+    const double l1 = 0.5 * (A + C) + r, l2 = det / l1;
+    double ex, ey;
+    if (r == 0.0) {
+        ex = 1.0; ey = 0.0;
+    } else if (h >= 0.0) {
+        ex = h + r; ey = B;
+    } else {
+        ex = B; ey = r - h;
+    }
+    const double en = 1.0 / sqrt(ex * ex + ey * ey);
+    ex *= en; ey *= en;
+    const double s1 = (double)kRowScale / sqrt(l1), s2 = (double)kRowScale / sqrt(l2);
+    fc.A = (float)A; fc.B = (float)B; fc.C = (float)C; fc.det = (float)det;
+    fc.w1x = (float)(ex * s1);
+    fc.w1y = (float)(ey * s1);
+    fc.w2x = df_from_double(-ey * s2);
+    fc.w2y = df_from_double(ex * s2);
+}
+
 // Exact projection, extent and tile cover of one (view, Gaussian) that passed
-// the pre-cull.  Returns its tile count (0: culled) and fills R and B when > 0.
-VPGS_D uint32_t project_one(const PoseDF &P, float mx, float my, float mz, float sx, float sy, float sz,
+// the pre-cull.  Returns its tile count (0: culled); the screen record is
+// written to *R as soon as it is known (its contents do not matter when the
+// count is 0, and writing early keeps it out of registers across the cover),
+// B is filled when the count is > 0.
+VPGS_D uint32_t project_one(const float *pd, float mx, float my, float mz, float sx, float sy, float sz,
                             float4 q, float op, float cr, float cg, float cb, const CamParams &cam,
-                            const OptParams &o, uint32_t *status, Rec &R, BinRec &B) {
+                            const OptParams &o, uint32_t *status, Rec *R, BinRec &B, float &depth) {
     Proj p;
-    project(P, mx, my, mz, sx, sy, sz, q.x, q.y, q.z, q.w, cam, o.dilation, p);
+    {
+        PoseDF P;
+        load_pose(pd, P);
+        project(P, mx, my, mz, sx, sy, sz, q.x, q.y, q.z, q.w, cam, o.dilation, p);
+    }
     const bool in_front = p.pc[2].hi > o.near_z || (p.pc[2].hi == o.near_z && p.pc[2].lo > 0.f);
     if (!in_front) return 0u;
     // eigen-decomposition of Sigma' (2x2 symmetric) for the whitening rows
@@ -158,6 +239,17 @@ VPGS_D uint32_t project_one(const PoseDF &P, float mx, float my, float mz, float
     const float en = 1.0f / sqrtf(ex * ex + ey * ey);
     ex *= en; ey *= en;
     const float s1 = kRowScale / sqrtf(lam1), s2 = kRowScale / sqrtf(lam2);
+    float4 w = make_float4(ex * s1, ey * s1, -ey * s2, ex * s2);
+    float w2x_lo = 0.f, w2y_lo = 0.f;
+    const bool fine = lam1 > kFineKappa * lam2;  // near-degenerate (NaN: the finiteness test below)
+    if (fine) {
+        FineCov fc;
+        fine_cov(pd, p.pc, sx, sy, sz, q.x, q.y, q.z, q.w, cam, o.dilation, fc);
+        p.A = fc.A; p.B = fc.B; p.C = fc.C; p.det = fc.det;
+        w = make_float4(fc.w1x, fc.w1y, fc.w2x.hi, fc.w2y.hi);
+        w2x_lo = fc.w2x.lo;
+        w2y_lo = fc.w2y.lo;
+    }
     // opacity-aware extent
     const float kq = 2.0f * logf(op / o.alpha_min);
     const float rx = sqrtf(fmaxf(kq, 0.f) * p.A), ry = sqrtf(fmaxf(kq, 0.f) * p.C);
@@ -165,10 +257,14 @@ VPGS_D uint32_t project_one(const PoseDF &P, float mx, float my, float mz, float
     const float uf = p.u.hi, vf = p.v.hi;
     float lx = (uf - 0.5f - rxe) + p.u.lo, hx = (uf - 0.5f + rxe) + p.u.lo;
     float ly = (vf - 0.5f - rye) + p.v.lo, hy = (vf - 0.5f + rye) + p.v.lo;
-    if (!isfinite(lx + hx + ly + hy + s1 + s2 + ex + ey)) {
+    if (!isfinite(lx + hx + ly + hy + w.x + w.y + w.z + w.w + w2x_lo + w2y_lo)) {
         set_status(status, VPGS_ERR_NONFINITE);
         return 0u;
     }
+    R->r0 = make_float4(p.u.hi, p.v.hi, p.u.lo, p.v.lo);
+    R->r1 = w;
+    R->r2 = make_float4(op, p.pz, cr, cg);
+    R->r3 = make_float4(cb, w2x_lo, fine ? -rye : rye, w2y_lo);
     lx = fmaxf(lx, -1.f); hx = fminf(hx, (float)cam.W);
     ly = fmaxf(ly, -1.f); hy = fminf(hy, (float)cam.H);
     const int x0 = max(0, (int)ceilf(lx)), x1 = min(cam.W - 1, (int)floorf(hx));
@@ -209,11 +305,8 @@ VPGS_D uint32_t project_one(const PoseDF &P, float mx, float my, float mz, float
         }
     }
     if (cnt == 0u) return 0u;
-    R.r0 = make_float4(p.u.hi, p.v.hi, p.u.lo, p.v.lo);
-    R.r1 = make_float4(ex * s1, ey * s1, -ey * s2, ex * s2);
-    R.r2 = make_float4(op, p.pz, cr, cg);
-    R.r3 = make_float4(cb, rxe, rye, kq);
-    B.uv = R.r0;
+    depth = p.pz;
+    B.uv = make_float4(p.u.hi, p.v.hi, p.u.lo, p.v.lo);
     B.rect = make_uint2((uint32_t)tx0 | ((uint32_t)tx1 << 16), (uint32_t)ty0 | ((uint32_t)ty1 << 16));
     B.cnt = cnt;
     B.pad = 0u;
@@ -326,19 +419,16 @@ project_kernel(GaussIn g, CamParams cam, OptParams o, RenderWs ws, const uint32_
         const int v = (int)(ic / g.N);
         const int64_t gi = ic - (int64_t)v * g.N;
         const float4 q = reinterpret_cast<const float4 *>(g.quats)[gi];
-        PoseDF P;
-        load_pose(ws.posedf + 24 * v, P);
-        Rec R;
         BinRec B;
-        const uint32_t cnt = project_one(P, g.means[3 * gi], g.means[3 * gi + 1], g.means[3 * gi + 2],
+        float depth = 0.f;
+        const uint32_t cnt = project_one(ws.posedf + 24 * v, g.means[3 * gi], g.means[3 * gi + 1], g.means[3 * gi + 2],
                                          g.scales[3 * gi], g.scales[3 * gi + 1], g.scales[3 * gi + 2], q,
                                          g.opac[gi], g.colors[3 * gi], g.colors[3 * gi + 1], g.colors[3 * gi + 2],
-                                         cam, o, ws.status, R, B);
+                                         cam, o, ws.status, ws.rec + ic, B, depth);
         ws.tcount[ic] = cnt;
         if (cnt) {
-            ws.rec[ic] = R;
             ws.bin[ic] = B;
-            add_digits(s_h, dps, 4, __float_as_uint(R.r2.y));  // the depth key (camera z > 0)
+            add_digits(s_h, dps, 4, __float_as_uint(depth));  // the depth key (camera z > 0)
             if (zero_g2d) {
                 float2 *z2 = reinterpret_cast<float2 *>(ws.g2d + 10 * ic);
 #pragma unroll
@@ -365,6 +455,7 @@ preprocess_bwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamPara
                       RenderWs ws, GaussGrad gg, double *dpose, const uint32_t *__restrict__ vis,
                       const uint32_t *n_vis) {
     grid_dep_enter();
+    if (*ws.status != 0u) return;  // the binning failed: vis may hold stale entries
     __shared__ double s_pose[8][6];
     __shared__ int s_views[2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -396,11 +487,32 @@ preprocess_bwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamPara
             for (int k = 0; k < 5; ++k) z2[k] = make_float2(0.f, 0.f);
             // the compositing backward leaves out these per-Gaussian factors (see
             // pair_grad): the mean's slots hold sum dpow t1 and sum dpow t2, turned
-            // into d/du, d/dv by the whitening rows of the record the pixels saw
-            const float4 w = ws.rec[i].r1;  // (w1x, w1y, w2x, w2y)
+            // into d/du, d/dv by the whitening rows W of the record the pixels saw,
+            // and the covariance's slots S = sum dpow t t^T, whence
+            // dL/dSigma' = 2 ln^2 2 W^T S W (FP64 for a near-degenerate record)
+            const Rec &rc = ws.rec[i];
+            const float4 w = rc.r1;  // (w1x, w1y, w2x, w2y)
             const float gu = (w.x * a01.x + w.z * a01.y) * kInvExp2Half;
             const float gv = (w.y * a01.x + w.w * a01.y) * kInvExp2Half;
-            const float ga = -0.5f * a23.x, gb = -a23.y, gcn = -0.5f * a45.x;
+            float S00, S01, S11;
+            {
+                constexpr float kc = 0.5f * kInvExp2Half * kInvExp2Half;  // 2 ln^2 2
+                const float s11 = a23.x, s12 = a23.y, s22 = a45.x;
+                const float4 r3 = rc.r3;
+                if (r3.z < 0.f) {
+                    const double w1x = w.x, w1y = w.y, w2x = (double)w.z + r3.y, w2y = (double)w.w + r3.w;
+                    const double m00 = s11 * w1x * w1x + 2.0 * s12 * w1x * w2x + s22 * w2x * w2x;
+                    const double m01 = s11 * w1x * w1y + s12 * (w1x * w2y + w2x * w1y) + s22 * w2x * w2y;
+                    const double m11 = s11 * w1y * w1y + 2.0 * s12 * w1y * w2y + s22 * w2y * w2y;
+                    S00 = (float)(kc * m00);
+                    S01 = (float)(kc * m01);
+                    S11 = (float)(kc * m11);
+                } else {
+                    S00 = kc * (s11 * w.x * w.x + 2.f * s12 * w.x * w.z + s22 * w.z * w.z);
+                    S01 = kc * (s11 * w.x * w.y + s12 * (w.x * w.w + w.z * w.y) + s22 * w.z * w.w);
+                    S11 = kc * (s11 * w.y * w.y + 2.f * s12 * w.y * w.w + s22 * w.w * w.w);
+                }
+            }
             go += a45.y;
             gc[0] += a67.x; gc[1] += a67.y; gc[2] += a89.x;
             const float gz = a89.y;
@@ -408,15 +520,6 @@ preprocess_bwd_kernel(GaussIn g, const double *__restrict__ T_cw, int V, CamPara
             load_pose(ws.posedf + 24 * v, P);
             Proj p;
             project(P, mx, my, mz, sx, sy, sz, q.x, q.y, q.z, q.w, cam, o.dilation, p);
-            // conic M = Sigma'^-1 and G_Sigma' = -M G M, G = [[ga, gb/2], [gb/2, gc]]
-            const float id = 1.0f / p.det;
-            const float ma = p.C * id, mb = -p.B * id, mc = p.A * id;
-            const float hb = 0.5f * gb;
-            const float t00 = ma * ga + mb * hb, t01 = ma * hb + mb * gcn;
-            const float t10 = mb * ga + mc * hb, t11 = mb * hb + mc * gcn;
-            const float S00 = -(t00 * ma + t01 * mb);
-            const float S01 = -(t00 * mb + t01 * mc);
-            const float S11 = -(t10 * mb + t11 * mc);
             // Sigma' = K K^T + eps I  ->  G_K = 2 G_S K
             float GK0[3], GK1[3];
 #pragma unroll
@@ -587,8 +690,7 @@ cudaError_t launch_preprocess_fwd(const GaussIn &g, const double *T_cw, int V, c
     z.w32[4] = ws.sort_look[1];                z.n32[4] = 0;  // zeroed by emit, sized by the instance count
     z.w32[5] = reinterpret_cast<uint32_t *>(ws.ranges);  z.n32[5] = 2 * (int64_t)V * cam.T;
     z.w64 = ws.scan_look[0];                   z.n64 = 2 * L.scan_blocks_max;  // both scans
-    static int prep_grid = 0;
-    if (prep_grid == 0) prep_grid = 8 * std::max(device_sm_count(), 1);
+    const int prep_grid = 8 * device_sm_count();
     const int64_t words = std::max<int64_t>(z.n32[3] + z.n32[4] + z.n32[5], z.n64);
     VPGS_LAUNCH("prepare", s,
                 launch_k(prepare_kernel, (unsigned)std::max<int64_t>(1, std::min<int64_t>(prep_grid, (words + 255) / 256)),
@@ -599,14 +701,12 @@ cudaError_t launch_preprocess_fwd(const GaussIn &g, const double *T_cw, int V, c
     VPGS_LAUNCH("preprocess_fwd", s,
                 launch_k(precull_kernel, (unsigned)((g.N + kPreThreads - 1) / kPreThreads), kPreThreads, 0, s,
                     g, V, cam, o, ws, cand, n_cand));
-    static int proj_grid = 0;
-    if (proj_grid == 0) {
-        int occ = 0, dev = 0, sms = 1;
+    static std::atomic<int> proj_cache[kDeviceCache];
+    const int proj_grid = per_device(proj_cache, [] {
+        int occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)project_kernel, kPreThreads, 0);
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        proj_grid = std::max(occ, 1) * std::max(sms, 1);
-    }
+        return std::max(occ, 1) * device_sm_count();
+    });
     VPGS_LAUNCH("project", s,
                 launch_k(project_kernel, (unsigned)std::min<int64_t>(proj_grid, (VN + kPreThreads - 1) / kPreThreads),
                                  kPreThreads, 0, s, g, cam, o, ws, cand, n_cand, zero_g2d));
@@ -619,8 +719,7 @@ cudaError_t launch_preprocess_bwd(const GaussIn &g, const double *T_cw, int V, c
     if (g.N == 0) return cudaSuccess;
     // enough blocks for the visible pairs of a large frame at full occupancy; the
     // live count is read on the device
-    static int bwd_grid = 0;
-    if (bwd_grid == 0) bwd_grid = 8 * std::max(device_sm_count(), 1) * VPGS_PRE_BWD_MINB;
+    const int bwd_grid = 8 * device_sm_count() * VPGS_PRE_BWD_MINB;
     const int64_t VN = (int64_t)V * g.N;
     VPGS_LAUNCH("preprocess_bwd", s,
                 launch_k(preprocess_bwd_kernel, (unsigned)std::min<int64_t>((VN + 255) / 256, bwd_grid), 256, 0, s,
