@@ -79,6 +79,11 @@ typedef struct {
     float bg[3];              /* C = sum_i alpha_i T_i c_i + T_final bg */
     int32_t persistent_ctas;  /* 0 = one CTA per tile; >0 = that many persistent CTAs per SM */
     int32_t flags;            /* VPGS_RENDER_* bits below; 0 by default */
+    int32_t spin_limit;       /* polls a bounded look-back wait of the binning (scans, sorts) makes
+                               * before it gives up and records VPGS_ERR_TIMEOUT; 0 = the default,
+                               * 2^22, never reached in a healthy run.  A few polls make the timeout
+                               * path testable: the render's outputs are then undefined, nothing is
+                               * written out of range, and the next call starts clean. */
 } vpgs_render_opts;
 
 /* vpgs_render_bwd: take the projection and tile lists from the workspace
@@ -199,8 +204,8 @@ vpgs_status vpgs_render_project(void *ws, size_t ws_bytes, const vpgs_gaussians 
 /* vpgs_render_fwd for callers that cannot allocate device memory.  The paper
  * has no counterpart: this is an interface for hosts whose device memory is
  * not theirs to allocate.  Examples are a plugin handed only a stream and the
- * tensors it must read and write, a process whose memory pool reserved the GPU
- * up front, and code that must not allocate while a CUDA graph is captured.
+ * tensors it must read and write, and a process whose memory pool reserved the
+ * GPU up front and forbids further allocations.
  *
  * Same inputs and outputs as vpgs_render_fwd, without the workspace.  The
  * scratch space is a VPGS_NOALLOC_SCRATCH_BYTES array compiled into the library.
@@ -213,8 +218,13 @@ vpgs_status vpgs_render_project(void *ws, size_t ws_bytes, const vpgs_gaussians 
  *     of the render.  VPGS_ERR_CAPACITY there means that the tile instances
  *     did not fit in the array.
  *   - The first call on each device looks the array's device address up
- *     (cudaGetSymbolAddress) with that device current.  Make that first call
- *     before capturing any stream.
+ *     (cudaGetSymbolAddress) with that device current, and keeps it for the
+ *     later calls on that device.  Make that first call before capturing any
+ *     stream.  The address belongs to the device's primary context (the one
+ *     the CUDA runtime uses): after cudaDeviceReset, or with another driver
+ *     context current on the device, it no longer names the array, so do not
+ *     call this entry point in either situation.
+ *   - Device ordinals from 64 up return VPGS_ERR_UNSUPPORTED.
  *   - Every call shares the one array, and a call leaves its contents behind.
  *     The render clears what it needs zeroed.  Calls that overlap on the GPU
  *     (other streams, other threads) race on the array, so serialise them. */
@@ -226,6 +236,16 @@ vpgs_status vpgs_render_fwd_noalloc(const vpgs_gaussians *g, const vpgs_camera *
 /* Reads the status word and counters of a render workspace (host `stats`).  It
  * synchronises `stream` first, and is the one call here that blocks. */
 vpgs_status vpgs_workspace_status(const void *ws, vpgs_render_stats *stats, vpgs_stream stream);
+
+/* Queues a copy of a render workspace's status word (int32, a vpgs_status
+ * value) into `dst` on `stream`, after the work queued before it, and returns
+ * without waiting.  `dst` is caller-owned device memory or page-locked host
+ * memory (4 bytes); it holds the status once the stream reaches the copy.  The
+ * way to check renders without stalling the host: copy, record an event, read
+ * `dst` once the event has completed.  No counterpart in the paper (error
+ * reporting).  Errors: VPGS_ERR_INVALID_ARG for a NULL pointer, VPGS_ERR_CUDA if
+ * the copy cannot be queued. */
+vpgs_status vpgs_workspace_status_copy(const void *ws, int32_t *dst, vpgs_stream stream);
 
 /* One step of the camera pose on the device (coarse tracking, Sec. III-B;
  * the step rule is not given in the paper).  For each view v:

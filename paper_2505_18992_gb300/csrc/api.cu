@@ -34,6 +34,7 @@ bool valid_opts(const vpgs_render_opts *o) {
     if (!(o->dilation >= 0.f) || !(o->near_z >= 0.f)) return false;
     if (o->persistent_ctas < 0 || o->persistent_ctas > 32) return false;
     if ((o->flags & ~VPGS_RENDER_REUSE_BINNING) != 0) return false;
+    if (o->spin_limit < 0) return false;
     return true;
 }
 
@@ -170,7 +171,7 @@ vpgs_status setup(void *ws, size_t ws_bytes, const vpgs_gaussians *g, const vpgs
                       opts->tile_w, opts->tile_h, S.L.tiles_x, S.L.tiles_y, S.L.T,
                       __builtin_ctz((unsigned)opts->tile_w)};
     S.o = OptParams{opts->alpha_min, opts->alpha_max, opts->t_min, opts->dilation, opts->near_z,
-                    opts->bg[0], opts->bg[1], opts->bg[2]};
+                    opts->bg[0], opts->bg[1], opts->bg[2], opts->spin_limit > 0 ? opts->spin_limit : kSpinLimit};
     S.g = GaussIn{g->means, g->scales, g->quats, g->opacities, g->colors, g->n, g->n_dev};
     return VPGS_OK;
 }
@@ -266,6 +267,7 @@ void vpgs_render_opts_default(vpgs_render_opts *o) {
     o->bg[0] = o->bg[1] = o->bg[2] = 0.f;
     o->persistent_ctas = 0;
     o->flags = 0;
+    o->spin_limit = 0;
 }
 
 size_t vpgs_render_workspace_bytes(int64_t max_gaussians, int32_t n_views, const vpgs_camera *cam,
@@ -287,7 +289,7 @@ vpgs_status vpgs_render_fwd(void *ws, size_t ws_bytes, const vpgs_gaussians *g,
     // the 2D gradient slots of visible Gaussians start at zero for a backward that reuses this call
     cudaError_t e = launch_preprocess_fwd(S.g, T_cw, n_views, S.cam, S.o, S.ws, S.L, true, s);
     int buf = 0;
-    if (e == cudaSuccess) e = build_tile_lists(S.g, n_views, S.cam, S.ws, S.L, &buf, s);
+    if (e == cudaSuccess) e = build_tile_lists(S.g, n_views, S.cam, S.o, S.ws, S.L, &buf, s);
     if (e == cudaSuccess)
         e = launch_composite_fwd(S.ws, S.ws.ival[buf], n_views, S.cam, S.o, *out, opts->persistent_ctas, s);
     if (e == cudaSuccess) tag_set(make_tag(ws, ws_bytes, g, cam, T_cw, n_views, opts));
@@ -321,7 +323,8 @@ vpgs_status vpgs_render_bwd(void *ws, size_t ws_bytes, const vpgs_gaussians *g,
         // recompute projection, binning and per-tile sort
         e = launch_preprocess_fwd(S.g, T_cw, n_views, S.cam, S.o, S.ws, S.L, true, s);
         if (e == cudaSuccess)
-            e = build_tile_lists(S.g, n_views, S.cam, S.ws, S.L, &buf, s, !(VPGS_TILE_ORDER && VPGS_BWD_ORDER_NITER));
+            e = build_tile_lists(S.g, n_views, S.cam, S.o, S.ws, S.L, &buf, s,
+                                 !(VPGS_TILE_ORDER && VPGS_BWD_ORDER_NITER));
         if (e == cudaSuccess) tag_set(tag);
         else tag_clear(ws);
     }
@@ -372,6 +375,15 @@ vpgs_status vpgs_workspace_status(const void *ws, vpgs_render_stats *stats, vpgs
     stats->n_visible = host[1 + CNT_VISIBLE];
     stats->n_instances = host[1 + CNT_INSTANCES];
     return VPGS_OK;
+}
+
+vpgs_status vpgs_workspace_status_copy(const void *ws, int32_t *dst, vpgs_stream stream) {
+    if (!ws || !dst) return VPGS_ERR_INVALID_ARG;
+    // the status word sits at offset 0 of every render layout
+    return cudaMemcpyAsync(dst, ws, sizeof(int32_t), cudaMemcpyDefault, reinterpret_cast<cudaStream_t>(stream)) ==
+                   cudaSuccess
+               ? VPGS_OK
+               : VPGS_ERR_CUDA;
 }
 
 vpgs_status vpgs_pose_step(double *T_cw, double *dL_dpose, double *adam_state, int32_t n_views,

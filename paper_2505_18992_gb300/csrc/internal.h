@@ -20,6 +20,7 @@ struct CamParams {
 struct OptParams {
     float alpha_min, alpha_max, t_min, dilation, near_z;
     float bg0, bg1, bg2;
+    int spin_limit;  // polls of a look-back wait before VPGS_ERR_TIMEOUT
 };
 
 struct GaussIn {
@@ -33,6 +34,7 @@ struct GaussGrad {
 };
 
 int device_sm_count();
+
 
 
 // render_pre.cu
@@ -51,7 +53,7 @@ cudaError_t launch_preprocess_bwd(const GaussIn &g, const double *T_cw, int V, c
 
 // render_bin.cu: visibility compaction, depth sort, instance emission, tile
 // sort and tile ranges.  On return ws.ival[*sorted_buf] holds the tile lists.
-cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, const RenderWs &ws,
+cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, const OptParams &o, const RenderWs &ws,
                              const RenderLayout &L, int *sorted_buf, cudaStream_t s, bool order_by_count = true);
 // Compositing launch order from the forward's n_iter: tiles by the backward's
 // list steps, most first (ws.tile_work, ws.tile_order).

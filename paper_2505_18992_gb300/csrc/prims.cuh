@@ -2,8 +2,10 @@
 // sort, both with decoupled look-back (Merrill & Garland, "Single-pass Parallel
 // Prefix Scan with Decoupled Look-back", 2016; Adinets & Merrill, "Onesweep",
 // 2022).  Logical block ids come from an atomic ticket, so a block only ever
-// waits on blocks that started before it.  Every wait is bounded (kSpinLimit);
-// running out records VPGS_ERR_TIMEOUT and the kernel carries on.
+// waits on blocks that started before it.  Every wait is bounded (LookBack's
+// spin_limit, by default kSpinLimit); running out records VPGS_ERR_TIMEOUT and
+// the kernel carries on with a partial prefix, whose scatter positions are
+// still bounds-checked.
 #pragma once
 
 #include "common.cuh"
@@ -37,6 +39,14 @@ VPGS_D uint32_t lanemask_lt() {
 // n = min(n_cap, *n_dev) if n_dev else n_cap.
 // Status word layout (64 bit): [63:62] flag 1 = aggregate, 2 = inclusive prefix.
 // ---------------------------------------------------------------------------
+// How a look-back kernel waits: polls before it gives up (VPGS_ERR_TIMEOUT), and
+// whether it returns at entry when the status word already holds an error (the
+// render's binning chain, whose later kernels index with earlier outputs).
+struct LookBack {
+    int spin_limit = kSpinLimit;
+    bool stop_on_error = false;
+};
+
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagPre = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
@@ -44,8 +54,9 @@ constexpr unsigned long long kValMask = (1ull << 62) - 1;
 template <class Load, class Store>
 __global__ void __launch_bounds__(kScanThreads)
 scan_kernel(Load load, Store store, int64_t n_cap, const uint32_t *n_dev, uint32_t *ticket,
-            unsigned long long *look, uint32_t *total, uint32_t *status) {
+            unsigned long long *look, uint32_t *total, uint32_t *status, LookBack lb) {
     grid_dep_enter();
+    if (lb.stop_on_error && *status != 0u) return;
     __shared__ uint32_t s_items[kScanTile + kScanTile / 32];
     __shared__ uint32_t s_warp[kScanThreads / kWarp];
     __shared__ uint32_t s_bid, s_excl;
@@ -115,7 +126,7 @@ scan_kernel(Load load, Store store, int64_t n_cap, const uint32_t *n_dev, uint32
                 int spins = 0;
                 bool timed_out = false;
                 while (!__all_sync(0xffffffffu, (w >> 62) != 0)) {
-                    if (++spins > kSpinLimit) {
+                    if (++spins > lb.spin_limit) {
                         timed_out = true;
                         break;
                     }
@@ -154,7 +165,7 @@ scan_kernel(Load load, Store store, int64_t n_cap, const uint32_t *n_dev, uint32
     }
 }
 
-// Blocks of a kernel that fit on the GPU at once (cached per kernel).
+// Blocks of a kernel that fit on the current GPU at once.
 inline int resident_grid(const void *kernel, int threads, size_t smem, int64_t cap_blocks) {
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess || occ < 1) occ = 1;
@@ -172,16 +183,17 @@ inline int64_t scan_blocks(int64_t n) { return (n + kScanTile - 1) / kScanTile; 
 template <class Load, class Store>
 cudaError_t launch_scan(const char *name, Load load, Store store, int64_t n_cap, const uint32_t *n_dev,
                         uint32_t *ticket, unsigned long long *look, uint32_t *total,
-                        uint32_t *status, cudaStream_t stream) {
+                        uint32_t *status, cudaStream_t stream, LookBack lb = LookBack{}) {
     int64_t nb = scan_blocks(n_cap);
     if (nb == 0) nb = 1;
-    static int grid_cache = 0;  // per <Load, Store>: occupancy does not change within a process
-    if (grid_cache == 0)
-        grid_cache = resident_grid((const void *)scan_kernel<Load, Store>, kScanThreads, 0, int64_t(1) << 30);
-    const int grid = (int)std::min<int64_t>(grid_cache, nb);
+    static std::atomic<int> grid_cache[kDeviceCache];  // per <Load, Store> and device
+    const int grid_res = per_device(grid_cache, [] {
+        return resident_grid((const void *)scan_kernel<Load, Store>, kScanThreads, 0, int64_t(1) << 30);
+    });
+    const int grid = (int)std::min<int64_t>(grid_res, nb);
     VPGS_LAUNCH(name, stream,
                 launch_k(scan_kernel<Load, Store>, (unsigned)grid, kScanThreads, 0, stream, load, store, n_cap, n_dev,
-                                                                         ticket, look, total, status));
+                                                                         ticket, look, total, status, lb));
     return cudaGetLastError();
 }
 
@@ -226,8 +238,9 @@ radix_onesweep_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__res
                       uint32_t *__restrict__ key_out, uint32_t *__restrict__ val_out,
                       int64_t n_cap, const uint32_t *n_dev, SortPass pass,
                       const uint32_t *__restrict__ pass_hist, uint32_t *ticket, uint32_t *look,
-                      uint32_t *next_look, uint32_t *status) {
+                      uint32_t *next_look, uint32_t *status, LookBack lb) {
     grid_dep_enter();
+    if (lb.stop_on_error && *status != 0u) return;
     constexpr int kWarps = kSortThreads / kWarp;
     constexpr int kSeg = kWarp * ITEMS;  // contiguous items per warp
     constexpr int kTile = kSortThreads * ITEMS;
@@ -335,7 +348,7 @@ radix_onesweep_kernel(const uint32_t *__restrict__ key_in, const uint32_t *__res
                     uint32_t x = w[i];
                     int spins = 0;
                     while ((x >> 30) == 0) {
-                        if (++spins > kSpinLimit) {
+                        if (++spins > lb.spin_limit) {
                             set_status(status, VPGS_ERR_TIMEOUT);
                             x = kSFlagPre;
                             break;
@@ -421,7 +434,8 @@ inline int64_t sort_blocks(int64_t n, int items) {
 inline cudaError_t radix_sort_pairs(const char *name, uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
                                     int64_t n_cap, const uint32_t *n_dev, int lo_bit, int bits,
                                     const uint32_t *hist, uint32_t *ticket, uint32_t *look,
-                                    uint32_t *status, cudaStream_t stream, bool *result_in_1, int items) {
+                                    uint32_t *status, cudaStream_t stream, bool *result_in_1, int items,
+                                    LookBack lb = LookBack{}) {
     SortPass ps[kMaxSortPasses];
     int np = plan_passes(lo_bit, bits, ps);
     *result_in_1 = (np & 1) != 0;
@@ -433,9 +447,10 @@ inline cudaError_t radix_sort_pairs(const char *name, uint32_t *k0, uint32_t *v0
                      : items == 8 ? (const void *)radix_onesweep_kernel<8>
                      : items == 32 ? (const void *)radix_onesweep_kernel<32>
                                    : (const void *)radix_onesweep_kernel<16>;
-    static int grids[33] = {0};  // by items: occupancy does not change within a process
-    if (grids[items] == 0) grids[items] = resident_grid(kern, kSortThreads, 0, int64_t(1) << 30);
-    const unsigned grid = (unsigned)std::min<int64_t>(grids[items], nb);
+    static std::atomic<int> grids[4][kDeviceCache];  // by items (4, 8, 16, 32) and device
+    const int gi = items == 4 ? 0 : items == 8 ? 1 : items == 16 ? 2 : 3;
+    const int grid_res = per_device(grids[gi], [kern] { return resident_grid(kern, kSortThreads, 0, int64_t(1) << 30); });
+    const unsigned grid = (unsigned)std::min<int64_t>(grid_res, nb);
     cudaError_t e;
     uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
     for (int p = 0; p < np; ++p) {
@@ -444,16 +459,16 @@ inline cudaError_t radix_sort_pairs(const char *name, uint32_t *k0, uint32_t *v0
         const uint32_t *h = hist + p * kRadix;
         if (items == 4)
             VPGS_LAUNCH(name, stream, launch_k(radix_onesweep_kernel<4>, grid, kSortThreads, 0, stream,
-                                          ki, vi, ko, vo, n_cap, n_dev, ps[p], h, ticket + p, lk, nl, status));
+                                          ki, vi, ko, vo, n_cap, n_dev, ps[p], h, ticket + p, lk, nl, status, lb));
         else if (items == 8)
             VPGS_LAUNCH(name, stream, launch_k(radix_onesweep_kernel<8>, grid, kSortThreads, 0, stream,
-                                          ki, vi, ko, vo, n_cap, n_dev, ps[p], h, ticket + p, lk, nl, status));
+                                          ki, vi, ko, vo, n_cap, n_dev, ps[p], h, ticket + p, lk, nl, status, lb));
         else if (items == 32)
             VPGS_LAUNCH(name, stream, launch_k(radix_onesweep_kernel<32>, grid, kSortThreads, 0, stream,
-                                          ki, vi, ko, vo, n_cap, n_dev, ps[p], h, ticket + p, lk, nl, status));
+                                          ki, vi, ko, vo, n_cap, n_dev, ps[p], h, ticket + p, lk, nl, status, lb));
         else
             VPGS_LAUNCH(name, stream, launch_k(radix_onesweep_kernel<16>, grid, kSortThreads, 0, stream,
-                                          ki, vi, ko, vo, n_cap, n_dev, ps[p], h, ticket + p, lk, nl, status));
+                                          ki, vi, ko, vo, n_cap, n_dev, ps[p], h, ticket + p, lk, nl, status, lb));
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         uint32_t *tk = ki, *tv = vi;

@@ -67,6 +67,7 @@ emit_kernel(const uint32_t *__restrict__ dval, const uint32_t *__restrict__ inst
             uint32_t *status, int n_pass, SortPass p0, SortPass p1, SortPass p2, SortPass p3,
             uint32_t *hist, uint32_t *look0) {
     grid_dep_enter();
+    if (*status != 0u) return;  // an earlier kernel failed: dval may hold stale entries
     {
         // the tile sort's first-pass look-back words, for the tiles that will hold
         // instances (the instance count is known from here on)
@@ -396,19 +397,23 @@ int tile_list_buffer(const RenderLayout &L) {
     return (plan_passes(0, L.tile_bits, ps) & 1) != 0 ? 1 : 0;
 }
 
+// SM count of the current device, looked up once per device ordinal.
 int device_sm_count() {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
+    static std::atomic<int> cache[kDeviceCache];
+    return per_device(cache, [] {
+        int dev = 0, sms = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
-    return sms;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 1;
+        return sms;
+    });
 }
 
-cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, const RenderWs &ws,
+cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, const OptParams &o, const RenderWs &ws,
                              const RenderLayout &L, int *sorted_buf, cudaStream_t s, bool order_by_count) {
+    // every binning kernel stops at entry once a predecessor recorded an error: after
+    // a timed-out look-back the compacted and sorted arrays hold holes whose stale
+    // contents must not be used as indices
+    const LookBack lb{o.spin_limit, true};
     cudaError_t e;
     const int sms = device_sm_count();
     (void)sms;
@@ -416,7 +421,7 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
     uint32_t *n_inst = ws.counters + CNT_INSTANCES;
     // 1. compaction of visible (view, Gaussian) pairs
     e = launch_scan("scan_visible", VisLoad{ws.tcount}, VisStore{ws.rec, ws.dkey[0], ws.dval[0], ws.vis_idx, L.VN},
-                    L.VN, nullptr, ws.counters + CNT_TICKET_A, ws.scan_look[0], n_vis, ws.status, s);
+                    L.VN, nullptr, ws.counters + CNT_TICKET_A, ws.scan_look[0], n_vis, ws.status, s, lb);
     if (e != cudaSuccess) return e;
     // 2. depth sort
     bool in1 = false;
@@ -427,7 +432,7 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
     const int depth_items = L.VN > (int64_t(4) << 20) ? 16 : kDepthSortItems;
     e = radix_sort_pairs("sort_depth_pass", ws.dkey[0], ws.dval[0], ws.dkey[1], ws.dval[1], L.VN, n_vis,
                          0, 32, ws.sort_hist[0], ws.counters + CNT_TICKET_D, ws.sort_look[0], ws.status, s,
-                         &in1, depth_items);
+                         &in1, depth_items, lb);
     if (e != cudaSuccess) return e;
     const uint32_t *dval = in1 ? ws.dval[1] : ws.dval[0];  // visible records in depth order
     uint32_t *inst_off = in1 ? ws.dkey[0] : ws.dkey[1];  // the depth-sort buffer not holding the result
@@ -436,10 +441,12 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
     if (np_tile > 4) return cudaErrorInvalidValue;
     // 3. instance offsets, then emission
     e = launch_scan("scan_offsets", CountLoad{ws.tcount, dval}, OffsetStore{inst_off}, L.VN, n_vis,
-                    ws.counters + CNT_TICKET_O, ws.scan_look[1], n_inst, ws.status, s);
+                    ws.counters + CNT_TICKET_O, ws.scan_look[1], n_inst, ws.status, s, lb);
     if (e != cudaSuccess) return e;
-    static int emit_grid = 0;
-    if (emit_grid == 0) emit_grid = resident_grid((const void *)emit_kernel, kEmitThreads, 0, int64_t(1) << 30);
+    static std::atomic<int> emit_cache[kDeviceCache];
+    const int emit_grid = per_device(emit_cache, [] {
+        return resident_grid((const void *)emit_kernel, kEmitThreads, 0, int64_t(1) << 30);
+    });
     VPGS_LAUNCH("emit_instances", s,
                 launch_k(emit_kernel, (unsigned)std::min<int64_t>(std::max<int64_t>((L.VN + kEmitThreads - 1) / kEmitThreads, 1),
                                                           emit_grid),
@@ -452,7 +459,7 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
     // (digit histograms from the emit kernel)
     e = radix_sort_pairs("sort_tile_pass", ws.ikey[0], ws.ival[0], ws.ikey[1], ws.ival[1], L.M_cap, n_inst, 0,
                          L.tile_bits, ws.sort_hist[1], ws.counters + CNT_TICKET_T, ws.sort_look[1],
-                         ws.status, s, &in1, kTileSortItems);
+                         ws.status, s, &in1, kTileSortItems, lb);
     if (e != cudaSuccess) return e;
     *sorted_buf = in1 ? 1 : 0;
     if (*sorted_buf != tile_list_buffer(L)) return cudaErrorUnknown;  // never: same pass plan

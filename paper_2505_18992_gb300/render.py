@@ -66,6 +66,8 @@ class Renderer:
         self.last_stats = None
         self.generation = 0  # counts the calls that replace the workspace's tile lists
         self.reuse_binning = bool(reuse_binning)
+        self._pending = []  # status words of unchecked renders: (event, pinned int32, what)
+        self._slots = []
 
     # -- workspace -----------------------------------------------------------
     def reserve(self, n: int, max_instances: int | None = None):
@@ -88,6 +90,39 @@ class Renderer:
                                         current_stream_handle()), "vpgs_workspace_status")
         self.last_stats = st
         return st
+
+    # -- deferred status checks ------------------------------------------------
+    def queue_status_check(self, what: str):
+        """Queues an asynchronous copy of the workspace's status word (no host
+        wait); a later `poll_status` or `check` raises if it was an error."""
+        self.poll_status()
+        if len(self._pending) >= 4:  # the GPU runs far behind: wait for the oldest
+            self._pending[0][0].synchronize()
+            self.poll_status()
+        slot = self._slots.pop() if self._slots else torch.zeros(1, dtype=torch.int32, pin_memory=True)
+        C.check(C.vpgs_workspace_status_copy(self.ws.data_ptr(), slot.data_ptr(), current_stream_handle()),
+                "vpgs_workspace_status_copy")
+        ev = torch.cuda.Event()
+        ev.record()
+        self._pending.append((ev, slot, what))
+
+    def poll_status(self):
+        """Raises for the first completed deferred check that found an error;
+        leaves the ones still in flight alone (never waits)."""
+        while self._pending and self._pending[0][0].query():
+            ev, slot, what = self._pending.pop(0)
+            code = int(slot[0])
+            self._slots.append(slot)
+            if code == 2:
+                raise RuntimeError(f"{what}: tile-instance capacity exceeded (outputs undefined); "
+                                   "call Renderer.reserve with a larger max_instances")
+            C.check(code, what + " (device)")
+
+    def check(self):
+        """Waits for every deferred status check and raises if one found an error."""
+        for ev, _, _ in self._pending:
+            ev.synchronize()
+        self.poll_status()
 
     # -- calls ---------------------------------------------------------------
     def _gauss(self, means, scales, quats, opacities, colors, n_dev=None) -> C.vpgs_gaussians:
@@ -193,11 +228,18 @@ class RenderFn(torch.autograd.Function):
 
     xi [V,6] float64 is a zero-valued handle for the camera-pose gradient: its
     .grad is dL/dxi for the left perturbation T_cw <- Exp(xi) T_cw at xi = 0.
+
+    Neither pass waits for the GPU: each queues a copy of the workspace status
+    word, and a device error (instance capacity, non-finite input) raises at a
+    later render on the same renderer or at renderer.check().
     """
 
     @staticmethod
     def forward(ctx, means, scales, quats, opacities, colors, xi, T_cw, renderer):
-        out = renderer.forward(means, scales, quats, opacities, colors, T_cw)
+        # no host wait in an autograd step: the status word is checked later
+        # (renderer.poll_status at the next render, renderer.check on request)
+        out = renderer.forward(means, scales, quats, opacities, colors, T_cw, check=False)
+        renderer.queue_status_check("render forward")
         ctx.renderer = renderer
         ctx.generation = renderer.generation
         ctx.save_for_backward(means, scales, quats, opacities, colors, T_cw, out["t_final"],
@@ -221,6 +263,7 @@ class RenderFn(torch.autograd.Function):
         reuse = r.reuse_binning and r.generation == ctx.generation
         r.backward(means, scales, quats, opacities, colors, T_cw, fwd, cont(g_rgb), cont(g_depth),
                    cont(g_alpha), grads=grads, dpose=dpose, reuse=reuse)
+        r.queue_status_check("render backward")
         return (grads.get("means"), grads.get("scales"), grads.get("quats"),
                 grads.get("opacities"), grads.get("colors"), dpose, None, None)
 

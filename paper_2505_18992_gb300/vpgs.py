@@ -32,7 +32,8 @@ class vpgs_render_opts(ctypes.Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("alpha_min", c_float),
                 ("alpha_max", c_float), ("t_min", c_float), ("dilation", c_float),
                 ("near_z", c_float), ("bg", c_float * 3), ("persistent_ctas", c_int32),
-                ("flags", c_int32)]
+                ("flags", c_int32),
+        ("spin_limit", c_int32)]
 
 
 RENDER_REUSE_BINNING = 1
@@ -117,6 +118,7 @@ _SIGS = {
                                           c_int32, POINTER(vpgs_render_opts), POINTER(vpgs_images),
                                           c_void_p, c_void_p]),
     "vpgs_workspace_status": (c_int32, [c_void_p, POINTER(vpgs_render_stats), c_void_p]),
+    "vpgs_workspace_status_copy": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "vpgs_pose_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, POINTER(c_double),
                                  c_void_p]),
     "vpgs_decode_workspace_bytes": (c_size_t, [c_int64, c_int32]),
@@ -218,6 +220,7 @@ vpgs_render_bwd = _entry("vpgs_render_bwd")
 vpgs_render_project = _entry("vpgs_render_project")
 vpgs_render_fwd_noalloc = _entry("vpgs_render_fwd_noalloc")
 vpgs_workspace_status = _entry("vpgs_workspace_status")
+vpgs_workspace_status_copy = _entry("vpgs_workspace_status_copy")
 vpgs_pose_step = _entry("vpgs_pose_step")
 vpgs_decode_workspace_bytes = _entry("vpgs_decode_workspace_bytes")
 vpgs_decode_anchors = _entry("vpgs_decode_anchors")

@@ -261,6 +261,41 @@ def test_capacity_overflow_is_reported_then_grown(planes):
     del out
 
 
+def test_lookback_wait_limit_reports_timeout():
+    """A look-back wait limit of one poll makes the binning's scans and sorts give
+    up on predecessors that have not published yet: the call records
+    VPGS_ERR_TIMEOUT, writes nothing outside its workspace and images, and the
+    next call with the default limit renders exactly as a fresh renderer does."""
+    sc = scenes.random_gaussians(300_000, 640, 480, 500.0, seed=33, scale_range=(0.005, 0.02))
+    g, T = scene_tensors(sc)
+    r = Renderer(intrinsics(sc), spin_limit=1)
+    r.reserve(sc.n)
+    guard = 1 << 16
+    ws = torch.full((r.ws_bytes + guard,), 0xA5, dtype=torch.uint8, device="cuda")
+    r.ws = ws[:r.ws_bytes]  # same base address, so still 16-byte aligned
+    bigs, out = {}, {}
+    for k, t in r.alloc_images().items():
+        big = torch.full((t.numel() + guard,), -7, dtype=t.dtype, device="cuda")
+        bigs[k] = big
+        out[k] = big[:t.numel()].view(t.shape)
+    codes = []
+    for _ in range(20):
+        r.forward(*g, T, out=out, check=False)
+        codes.append(int(r.stats().status))
+        if codes[-1] == 4:
+            break
+    assert codes[-1] == 4 and set(codes) <= {0, 4}, codes
+    assert bool((ws[r.ws_bytes:] == 0xA5).all())
+    for k, big in bigs.items():
+        assert bool((big[-guard:] == -7).all()), k
+    r.opts.spin_limit = 0
+    a = _np(r.forward(*g, T))
+    assert r.stats().status == 0
+    b = _np(Renderer(intrinsics(sc)).forward(*g, T))
+    for k in ("rgb", "depth", "alpha", "t_final", "n_contrib", "n_iter"):
+        assert np.array_equal(a[k], b[k]), k
+
+
 def test_nonfinite_input_sets_status():
     sc = scenes.random_gaussians(20, 32, 24, 30.0, seed=2)
     sc.means[3, 0] = np.nan
@@ -297,6 +332,23 @@ def test_autograd_function_matches_direct_calls(planes, planes_ref):
     for k, leaf in zip(GRAD_KEYS, leaves):
         assert_grad_close(leaf.grad.cpu().numpy(), ref["d_" + k], k)
     assert_pose_close(xi.grad.cpu().numpy(), ref["d_pose"])
+
+
+def test_autograd_render_checks_status_without_waiting(planes):
+    """render() queues the status word instead of waiting for it: an instance
+    overflow surfaces at renderer.check() (or a later render), not silently."""
+    r = Renderer(intrinsics(planes))
+    g, T = scene_tensors(planes)
+    r.reserve(planes.n, max_instances=100)
+    leaves = [t.clone().requires_grad_(True) for t in g]
+    rgb, depth, alpha = render(*leaves, T, r)
+    with pytest.raises(RuntimeError, match="capacity"):
+        r.check()
+    r.reserve(planes.n, max_instances=24 * planes.n)
+    rgb, depth, alpha = render(*leaves, T, r)
+    (rgb.sum() + depth.sum()).backward()
+    r.check()
+    assert not r._pending
 
 
 def test_backward_reusing_the_forward_lists(planes, planes_ref):
