@@ -4,8 +4,13 @@ Picks, for one workload on one GPU, the tile shape (tile_w x tile_h), the
 persistent CTAs per SM (0 = one CTA per tile) and how many views go into one
 render call, by timing fwd+bwd steps with CUDA events.  The image does not
 depend on any of these (the tile cover is a superset of every contributing
-pixel), so the choice is about time only.  Results are cached in a JSON file
-keyed by the GPU name and the workload's shape.
+pixel), so the choice is about time only -- and each candidate is checked
+before it may win: on the tuning frame its contributor counts must equal the
+default shape's bit for bit and its images (colour, depth, alpha, final
+transmittance) must lie within 1e-5 of them; its list positions (n_iter) must
+equal those of the same tile shape rendered one call, one CTA per tile.
+Candidates that fail are rejected with the reason.  Results are cached in a
+JSON file keyed by the GPU name and the workload's shape.
 """
 from __future__ import annotations
 
@@ -57,6 +62,29 @@ def workload_key(n_gaussians: int, width: int, height: int, n_views: int) -> str
         e = len(str(n)) - 2
         n = round(n / 10 ** e) * 10 ** e
     return f"n{n}_{width}x{height}_v{n_views}"
+
+
+DEFAULT_SHAPE = LaunchShape(16, 16, 0, 0)  # views_per_call 0: all views in one call
+IMAGE_TOL = 1e-5
+
+
+def compare_outputs(cand: dict, ref: dict, ref_same_tile: dict | None = None, tol: float = IMAGE_TOL):
+    """None when the candidate's render matches the reference, else the reason.
+
+    cand/ref: dicts of numpy arrays rgb, depth, alpha, t_final, n_contrib (and
+    n_iter).  n_contrib must be identical; the images within tol; n_iter is
+    compared (identical) only with ref_same_tile, a render with the same tile
+    shape, since list positions depend on the tiles."""
+    import numpy as np
+    if not np.array_equal(cand["n_contrib"], ref["n_contrib"]):
+        return f"n_contrib differs at {int((cand['n_contrib'] != ref['n_contrib']).sum())} pixels"
+    for k in ("rgb", "depth", "alpha", "t_final"):
+        err = float(np.abs(np.asarray(cand[k], np.float64) - np.asarray(ref[k], np.float64)).max())
+        if not err <= tol:
+            return f"{k} differs by {err:.3g}"
+    if ref_same_tile is not None and not np.array_equal(cand["n_iter"], ref_same_tile["n_iter"]):
+        return "n_iter differs from the same tile shape's render"
+    return None
 
 
 def pick(timings: dict) -> LaunchShape:
@@ -127,10 +155,41 @@ def time_shape(shape: LaunchShape, gaussians, T_cw, intr, g_rgb, steps: int = 5,
     return statistics.median(times)
 
 
+def render_shape(shape: LaunchShape, gaussians, T_cw, intr) -> dict:
+    """Forward render of every view of T_cw with the given launch shape (numpy outputs)."""
+    import numpy as np
+    import torch
+
+    from .render import Renderer
+
+    V = int(T_cw.shape[0])
+    vpc = shape.views_per_call or V
+    r = Renderer(intr, n_views=vpc, tile_w=shape.tile_w, tile_h=shape.tile_h,
+                 persistent_ctas=shape.persistent_ctas)
+    parts = [r.forward(*gaussians, T_cw[c:c + vpc].contiguous(), check=True) for c in range(0, V, vpc)]
+    torch.cuda.synchronize()
+    return {k: np.concatenate([p[k].cpu().numpy() for p in parts], 0) for k in parts[0]}
+
+
+def validate(shapes, gaussians, T_cw, intr) -> dict:
+    """{shape: None (valid) or the reason it was rejected} on the tuning frame."""
+    ref = render_shape(DEFAULT_SHAPE, gaussians, T_cw, intr)
+    same_tile = {}
+    out = {}
+    for s in shapes:
+        tile = (s.tile_w, s.tile_h)
+        if tile not in same_tile:
+            same_tile[tile] = render_shape(LaunchShape(s.tile_w, s.tile_h, 0, 0), gaussians, T_cw, intr)
+        out[s] = compare_outputs(render_shape(s, gaussians, T_cw, intr), ref, same_tile[tile])
+    return out
+
+
 def tune(gaussians, T_cw, intr, g_rgb, shapes=None, steps: int = 5, cache_path: str | None = None,
-         key: str | None = None):
-    """Times every candidate shape (or returns the cached winner); returns
-    (best LaunchShape, {shape: ms})."""
+         key: str | None = None, return_rejected: bool = False):
+    """Times every candidate shape that renders the tuning frame as the default
+    shape does (or returns the cached winner); returns (best LaunchShape,
+    {shape: ms}) and, with return_rejected, also {shape: reason} of the
+    candidates left out."""
     import torch
 
     V = int(T_cw.shape[0])
@@ -139,9 +198,11 @@ def tune(gaussians, T_cw, intr, g_rgb, shapes=None, steps: int = 5, cache_path: 
     cache = Cache(cache_path)
     hit = cache.get(gpu, key)
     if hit is not None and shapes is None:
-        return hit[0], {hit[0]: hit[1]}
+        return (hit[0], {hit[0]: hit[1]}, {}) if return_rejected else (hit[0], {hit[0]: hit[1]})
     shapes = shapes or candidates(V)
-    timings = {s: time_shape(s, gaussians, T_cw, intr, g_rgb, steps=steps) for s in shapes}
+    checks = validate(shapes, gaussians, T_cw, intr)
+    rejected = {s: why for s, why in checks.items() if why is not None}
+    timings = {s: time_shape(s, gaussians, T_cw, intr, g_rgb, steps=steps) for s in shapes if s not in rejected}
     best = pick(timings)
     cache.put(gpu, key, best, timings[best])
-    return best, timings
+    return (best, timings, rejected) if return_rejected else (best, timings)

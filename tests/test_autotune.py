@@ -44,6 +44,31 @@ def test_pick_and_cache_roundtrip(tmp_path):
     json.loads(open(path).read())  # plain JSON on disk
 
 
+def test_validation_rejects_changed_counts_images_or_list_positions():
+    rng = np.random.default_rng(0)
+    ref = {"rgb": rng.uniform(size=(1, 3, 4, 5)).astype(np.float32),
+           "depth": rng.uniform(size=(1, 4, 5)).astype(np.float32),
+           "alpha": rng.uniform(size=(1, 4, 5)).astype(np.float32),
+           "t_final": rng.uniform(size=(1, 4, 5)).astype(np.float32),
+           "n_contrib": rng.integers(0, 9, (1, 4, 5)).astype(np.int32),
+           "n_iter": rng.integers(0, 20, (1, 4, 5)).astype(np.int32)}
+    same = {k: v.copy() for k, v in ref.items()}
+    assert at.compare_outputs(same, ref, ref) is None
+    near = {k: v.copy() for k, v in ref.items()}
+    near["rgb"] = near["rgb"] + np.float32(8e-6)  # within 1e-5
+    near["n_iter"] = near["n_iter"] + 1            # another tile shape's list positions
+    assert at.compare_outputs(near, ref) is None
+    assert "n_iter" in at.compare_outputs(near, ref, ref)
+    bad = {k: v.copy() for k, v in ref.items()}
+    bad["n_contrib"][0, 2, 3] += 1
+    assert "n_contrib" in at.compare_outputs(bad, ref)
+    bad = {k: v.copy() for k, v in ref.items()}
+    bad["depth"][0, 1, 1] += 2e-5
+    assert "depth" in at.compare_outputs(bad, ref)
+    bad["depth"][0, 1, 1] = np.nan
+    assert "depth" in at.compare_outputs(bad, ref)
+
+
 @pytest.mark.gpu
 def test_tuning_picks_a_valid_shape_and_the_image_does_not_depend_on_it(tmp_path):
     import torch
@@ -57,7 +82,9 @@ def test_tuning_picks_a_valid_shape_and_the_image_does_not_depend_on_it(tmp_path
     intr = intrinsics(sc)
     g_rgb = torch.full((2, 3, 192, 256), 1e-5, device="cuda")
     shapes = at.candidates(2, tiles=((8, 16), (16, 16)), persistent=(0, 2))
-    best, timings = at.tune(g, T, intr, g_rgb, shapes=shapes, steps=2, cache_path=str(tmp_path / "t.json"))
+    best, timings, rejected = at.tune(g, T, intr, g_rgb, shapes=shapes, steps=2,
+                                      cache_path=str(tmp_path / "t.json"), return_rejected=True)
+    assert not rejected, rejected  # every launch shape renders this frame as the default does
     assert best in shapes and len(timings) == len(shapes)
     assert all(t > 0 for t in timings.values())
     # the tuned shape renders the same image as the default shape (up to the rounding
