@@ -2,7 +2,8 @@
 
 Each CUDA translation unit is compiled in parallel into _build/, then linked
 with the static CUDA runtime into paper_2505_18992_gb300/libvpgs.so.  A unit is
-rebuilt when it or any header is newer than its object.
+rebuilt when it or any header is newer than its object, or when the flags it
+was compiled with (VPGS_NVCC_FLAGS included) have changed.
 """
 from __future__ import annotations
 
@@ -41,16 +42,25 @@ def _env_flags():
 
 
 def _compile(src: str, extra) -> str:
+    """Compiles src unless its object is newer than every source and header and
+    was built with the same flags (VPGS_NVCC_FLAGS included: the stamp file
+    beside the object records them)."""
     obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
+    stamp = obj + ".flags"
+    flags = [*ARCH, *NVCC_FLAGS, *_env_flags(), *extra]
+    key = "\n".join(flags)
     newest = max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in _headers()])
-    if os.path.exists(obj) and os.path.getmtime(obj) >= newest and not extra:
+    same_flags = os.path.exists(stamp) and open(stamp).read() == key
+    if os.path.exists(obj) and os.path.getmtime(obj) >= newest and same_flags and not extra:
         return obj
-    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *_env_flags(), *extra, "-c", src, "-o", obj]
+    cmd = [nvcc(), *flags, "-c", src, "-o", obj]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{res.stderr}")
     if extra and res.stderr:
         sys.stderr.write(res.stderr)
+    with open(stamp, "w") as fh:
+        fh.write(key)
     return obj
 
 

@@ -1008,13 +1008,9 @@ vpgs_status vpgs_decode_anchors(void *ws, size_t ws_bytes, const vpgs_anchors *a
     cudaError_t e = cudaMemsetAsync(b, 0, L.off_look + 8 * (size_t)std::max<int64_t>(L.nblocks, 1), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(n_out, 0, sizeof(int32_t), s);
     if (e != cudaSuccess || p.A == 0) return e == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
-    static bool attr_set = false;
+    // the shared-memory opt-in is a per-device attribute: set on every call, on the current device
     const size_t smem = sizeof(DecFwdSmem);
-    if (!attr_set) {
-        cudaFuncSetAttribute((const void *)decode_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        attr_set = true;
-    }
+    cudaFuncSetAttribute((const void *)decode_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     DecOut o{out->means, out->scales, out->quats, out->opacities, out->colors, n_out, src_index};
     uint32_t *status = reinterpret_cast<uint32_t *>(b + L.off_status);
     uint32_t *ticket = reinterpret_cast<uint32_t *>(b + L.off_counters + 4 * CNT_TICKET_A);
@@ -1049,23 +1045,15 @@ vpgs_status vpgs_decode_anchors_bwd(void *ws, size_t ws_bytes, const vpgs_anchor
     const int ib = (int)std::min<int64_t>((cap + 255) / 256, (int64_t)sms * 8);
     VPGS_LAUNCH("decode_inverse_index", s,
                 launch_k(inverse_index_kernel, ib, 256, 0, s, src_index, dL->n_dev, dL->n, cap, inv));
-    static bool attr_set = false;
+    // the shared-memory opt-in is a per-device attribute: set on every call, on the current device
     const size_t smem = sizeof(DecBwdSmem);
-    if (!attr_set) {
-        cudaFuncSetAttribute((const void *)decode_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        attr_set = true;
-    }
+    cudaFuncSetAttribute((const void *)decode_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     DecGradIn gin{dL->means, dL->scales, dL->quats, dL->opacities, dL->colors};
     DecGradOut gout{dL_dfeatures, dL_doffsets, dL_dscaling, dL_dparams};
     if (p.bf16 && VPGS_DECODE_BWD_MMA) {
-        static bool mma_attr = false;
         const size_t msm = sizeof(DecBwdMmaSmem);
-        if (!mma_attr) {
-            cudaFuncSetAttribute((const void *)decode_bwd_mma_kernel,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msm);
-            mma_attr = true;
-        }
+        cudaFuncSetAttribute((const void *)decode_bwd_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)msm);
         const int64_t nch = (p.A + kMA - 1) / kMA;
         const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nch, sms));
         VPGS_LAUNCH("decode_bwd", s, launch_k(decode_bwd_mma_kernel, grid, kMA, msm, s, p, T_cw, inv, gin, gout));

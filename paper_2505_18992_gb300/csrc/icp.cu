@@ -673,9 +673,8 @@ int fill_grid(int64_t n) {
 }
 
 int corr_grid() {
-    static int g = 0;
-    if (g == 0) g = resident_grid((const void *)icp_step_kernel, kIcpThreads, 0, kIcpMaxBlocks);
-    return g;
+    static std::atomic<int> cache[kDeviceCache];
+    return per_device(cache, [] { return resident_grid((const void *)icp_step_kernel, kIcpThreads, 0, kIcpMaxBlocks); });
 }
 
 struct IcpWsView {
