@@ -3,8 +3,7 @@
 // vpgs_render_fwd carves its scratch space from a workspace the caller
 // allocates.  Some callers cannot allocate: a plugin handed only a stream and
 // the tensors it must read and write; a process whose memory pool reserved
-// the GPU's memory up front and forbids further cudaMalloc calls; code that
-// must not allocate while a CUDA graph is being captured.  For them,
+// the GPU's memory up front and forbids further cudaMalloc calls.  For them,
 // vpgs_render_fwd_noalloc takes its scratch from a fixed array that is
 // compiled into this library and lives as long as the library is loaded.
 #include <mutex>

@@ -1,10 +1,10 @@
 """vpgs_render_fwd_noalloc, the render for callers that cannot allocate device memory.
 
 Such callers (a plugin given only a stream and tensors, a process whose memory
-pool owns the GPU, code running under graph capture) get the same render
-through a scratch array compiled into the library.  Its output must match the
-workspace entry point's, call after call.  This file is collected last so a
-failure here cannot hide the other tests.
+pool owns the GPU) get the same render through a scratch array compiled into
+the library.  Its output must match the workspace entry point's, call after
+call.  This file is collected last so a failure here cannot hide the other
+tests.
 """
 import ctypes
 
@@ -57,3 +57,22 @@ def test_noalloc_render_rejects_a_request_beyond_its_scratch():
                                      ctypes.byref(opts), ctypes.byref(Renderer._images(out)), None,
                                      current_stream_handle())
     assert code == 6
+
+
+def test_noalloc_render_reports_tile_instances_beyond_its_scratch():
+    """The Gaussians' own arrays fit the scratch, but their tile instances do
+    not: the call is accepted and the device status reads VPGS_ERR_CAPACITY."""
+    build()
+    sc = scenes.random_gaussians(20_000, 320, 240, 300.0, seed=4, depth=(1.5, 2.0), spread=0.2,
+                                 scale_range=(0.5, 0.8))  # each covers most of the image's 300 tiles
+    r = Renderer(intrinsics(sc))
+    g, T = scene_tensors(sc)
+    gs = r._gauss(*g)
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    out = r.alloc_images()
+    code = C.vpgs_render_fwd_noalloc(ctypes.byref(gs), ctypes.byref(r.cam), T.data_ptr(), 1,
+                                     ctypes.byref(r.opts), ctypes.byref(r._images(out)),
+                                     status.data_ptr(), current_stream_handle())
+    assert code == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == 2
