@@ -94,18 +94,21 @@ VPGS_D int warp_list(const float4 *s0, const float4 *s1, int n, float2 band, uin
 }
 
 // record -> shared staging: s0 = (u, v) tile-local, w1; s1 = w2, opacity, widened
-// y half extent (negative: near-degenerate); s2 = colour, camera z; and for a
-// near-degenerate record only, s3 = the rounding residual of the tile-local
-// mean and the low parts of w2
-VPGS_D void stage(const Rec &r, float ox, float oy, float4 &a, float4 &b, float4 &c, float4 &f) {
+// y half extent (negative: near-degenerate); s2 = colour, camera z.  The
+// forward also stages fine_extra of a near-degenerate record (s3); the
+// backward, whose shared memory sets its occupancy, reads it from the record.
+// what a near-degenerate record adds to its staged a = (ux, uy, ...): the
+// rounding residual of the tile-local mean ((u_hi - ox) + u_lo = ux + residual,
+// the subtraction split exactly) and the low parts of w2
+VPGS_D float4 fine_extra(const Rec &r, float ox, float oy, float ux, float uy) {
+    const df ex = two_sum(r.r0.x, -ox), ey = two_sum(r.r0.y, -oy);
+    return make_float4(((ex.hi - ux) + r.r0.z) + ex.lo, ((ey.hi - uy) + r.r0.w) + ey.lo, r.r3.y, r.r3.w);
+}
+
+VPGS_D void stage(const Rec &r, float ox, float oy, float4 &a, float4 &b, float4 &c) {
     a = make_float4((r.r0.x - ox) + r.r0.z, (r.r0.y - oy) + r.r0.w, r.r1.x, r.r1.y);
     b = make_float4(r.r1.z, r.r1.w, r.r2.x, r.r3.z);
     c = make_float4(r.r2.z, r.r2.w, r.r3.x, r.r2.y);
-    if (r.r3.z < 0.f) {
-        // (u_hi - ox) + u_lo = a.x + residual, the subtraction split exactly
-        const df ex = two_sum(r.r0.x, -ox), ey = two_sum(r.r0.y, -oy);
-        f = make_float4(((ex.hi - a.x) + r.r0.z) + ex.lo, ((ey.hi - a.y) + r.r0.w) + ey.lo, r.r3.y, r.r3.w);
-    }
 }
 
 // alpha of pixel (px, py) (tile-local) for the staged Gaussian (a, b[, f])
@@ -177,7 +180,11 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
         for (int b0 = start; b0 < end; b0 += NT) {
             if (__syncthreads_count(all_done) == NT) break;
             const int j = b0 + tid;
-            if (j < end) stage(rec[ival[j]], ox, oy, s0[tid], s1[tid], s2[tid], s3[tid]);
+            if (j < end) {
+                const Rec r = rec[ival[j]];
+                stage(r, ox, oy, s0[tid], s1[tid], s2[tid]);
+                if (r.r3.z < 0.f) s3[tid] = fine_extra(r, ox, oy, s0[tid].x, s0[tid].y);
+            }
             __syncthreads();
             bool any_fine;
             const int nl = warp_list(s0, s1, min(NT, end - b0), band, wl, lane, any_fine);
@@ -410,8 +417,8 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
     extern __shared__ float4 smem[];
     const int NT = blockDim.x;
     const int NW = NT >> 5;
-    float4 *s0 = smem, *s1 = smem + NT, *s2 = smem + 2 * NT, *s3 = smem + 3 * NT;
-    uint32_t *s_id = reinterpret_cast<uint32_t *>(smem + 4 * NT);
+    float4 *s0 = smem, *s1 = smem + NT, *s2 = smem + 2 * NT;
+    uint32_t *s_id = reinterpret_cast<uint32_t *>(smem + 3 * NT);
     uint16_t *s_wl = reinterpret_cast<uint16_t *>(s_id + NT);             // [NW][NT] per-warp lists
     float *s_part = reinterpret_cast<float *>(s_wl + (size_t)NW * NT);  // [NW][NT][kPartStride]
     __shared__ int s_tile;
@@ -490,7 +497,7 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
             const int j = b0 + tid;
             if (j < b1) {
                 const uint32_t id = ival[j];
-                stage(rec[id], ox, oy, s0[tid], s1[tid], s2[tid], s3[tid]);
+                stage(rec[id], ox, oy, s0[tid], s1[tid], s2[tid]);
                 s_id[tid] = id;
             }
             if (ACC == 1)
@@ -516,7 +523,7 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                 auto grads = [&](auto fine) -> bool {
                     constexpr bool kFine = decltype(fine)::value;
                     float4 f;
-                    if constexpr (kFine) f = s3[kk];
+                    if constexpr (kFine) f = fine_extra(rec[s_id[kk]], ox, oy, a.x, a.y);
                     bool any = false;
 #pragma unroll
                     for (int q = 0; q < kPix; ++q) {
@@ -573,7 +580,8 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
 static size_t comp_smem(int NT, bool bwd, int acc = 0) {
     const size_t parts = acc == 1 ? (size_t)(NT / 32) * NT * kPartStride : (acc == 2 ? (size_t)NT * kPartStride : 0);
     const size_t lists = sizeof(uint16_t) * (size_t)(NT / 32) * NT;
-    return sizeof(float4) * 4 * NT + lists + (bwd ? sizeof(uint32_t) * NT + sizeof(float) * parts : 0);
+    // forward: s0-s3 and the lists; backward: s0-s2, the ids, the lists and the parts
+    return sizeof(float4) * (bwd ? 3 : 4) * NT + lists + (bwd ? sizeof(uint32_t) * NT + sizeof(float) * parts : 0);
 }
 
 static int persistent_grid(const void *kernel, int B, size_t smem, int per_sm, int n_tiles) {
