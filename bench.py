@@ -717,15 +717,21 @@ def batched_rows(dev, steps=10):
     return row
 
 
+FUSION_SUBMAPS, FUSION_PAIR = 16, (7, 8)
+
+
 def fusion_rows(dev, iters=10):
-    """Submap fusion by distillation (Sec. III-C, Eq. 14) as an optimisation loop:
-    two overlapping 500k-Gaussian submaps of a street (50,000 anchors x k = 10
-    each, BF16 decoders), m = 4 keyframes in the overlap at 1920x1080.  Each
-    iteration decodes both submaps, renders the keyframes (one 4-view call per
-    submap), takes the squared distillation loss between the two renders, runs
-    the render backward (recomputing its tile lists) and the decoder backward of
-    both submaps, and takes an Adam step on each submap's anchor features and
-    MLP weights."""
+    """Submap fusion by distillation (Sec. III-C, Eq. 14) as an optimisation loop,
+    on a 1 km street held as 16 submaps resident on the GPU: submap i holds
+    50,000 anchors (k = 10: 500,000 neural Gaussians, 8M in all) over
+    [62.5 i - 10, 62.5 (i + 1)] m, so neighbours overlap by 10 m, each with its
+    own BF16 decoder.  Every submap is decoded once from a camera at its
+    centre.  The loop then works on submaps 7 and 8, with m = 4 keyframes in
+    their overlap at 1920x1080: each iteration decodes both, renders the
+    keyframes (one 4-view call per submap), takes the squared distillation loss
+    between the two renders, runs the render backward (recomputing its tile
+    lists) and the decoder backward of both submaps, and takes an Adam step on
+    each submap's anchor features and MLP weights."""
     import torch
 
     from paper_2505_18992_gb300 import scenes
@@ -734,10 +740,22 @@ def fusion_rows(dev, iters=10):
     from paper_2505_18992_gb300.fusion import Adam, DistillLoss
     from paper_2505_18992_gb300.render import Intrinsics, Renderer
     torch.cuda.reset_peak_memory_stats(dev)
-    subs = [scenes.street_anchors(n_anchors=50_000, length=62.5, x0=x0, seed=20 + i, width=1920, height=1080,
-                                  f=1000.0, cam_x=495.0, mlp_seed=7)
-            for i, x0 in enumerate((437.5, 490.0))]
     t = lambda a, dt=torch.float32: torch.tensor(a, dtype=dt, device=dev).contiguous()  # noqa: E731
+    # the whole street, resident: anchors, features, scalings, offsets, decoder
+    # weights and the decoded Gaussians of every submap
+    street = []
+    for i in range(FUSION_SUBMAPS):
+        x0 = 62.5 * i - (10.0 if i > 0 else 0.0)
+        sc = scenes.street_anchors(n_anchors=50_000, length=62.5 * (i + 1) - x0, x0=x0, seed=20 + i, width=1920,
+                                   height=1080, f=1000.0, cam_x=x0 + 2.0, mlp_seed=7)
+        params = t(np.concatenate([np.asarray(p, np.float32).reshape(-1)
+                                   for name in ("opacity", "color", "cov") for p in sc.mlp[name]]))
+        inp = (t(sc.anchors), t(sc.features), t(sc.scaling), t(sc.offsets), params)
+        d = Decoder(sc.k, bf16=True, device=dev)
+        out = d.forward(*inp, sc.camera, t(sc.camera.T_cw[0], torch.float64))
+        street.append({"sc": sc, "inp": inp, "d": d, "out": out})
+    resident = [int(s["out"]["n_dev"].item()) for s in street]
+    subs = [street[j]["sc"] for j in FUSION_PAIR]
     # keyframes in the 10 m overlap, facing the facade, so both submaps are in view
     kfs = np.stack([scenes.look_at([x, 0.0, 1.7], [x, 10.0, 1.7], [0, 0, 1]) for x in (491.5, 494.0, 496.0, 498.5)])
     m = len(kfs)
@@ -747,14 +765,11 @@ def fusion_rows(dev, iters=10):
     r = Renderer(Intrinsics(W, H, cam.fx, cam.fy, cam.cx, cam.cy), n_views=m, device=dev)
     dist = DistillLoss(m, W, H)
     state = []
-    for sc in subs:
+    for j in FUSION_PAIR:
+        sc, inp, d = street[j]["sc"], street[j]["inp"], street[j]["d"]
         sc.camera.T_cw = kfs[:1]  # decode culls against the first keyframe
-        params = t(np.concatenate([np.asarray(p, np.float32).reshape(-1)
-                                   for name in ("opacity", "color", "cov") for p in sc.mlp[name]]))
-        feats = t(sc.features)
-        inp = (t(sc.anchors), feats, t(sc.scaling), t(sc.offsets), params)
-        d = Decoder(sc.k, bf16=True, device=dev)
-        out = d.forward(*inp, sc.camera, T[0])
+        feats, params = inp[1], inp[4]
+        out = d.forward(*inp, sc.camera, T[0], out=street[j]["out"])
         res = {"features": torch.zeros_like(feats), "offsets": torch.zeros_like(inp[3]),
                "scaling": torch.zeros_like(inp[2]), "params": torch.zeros_like(params)}
         opts = [Adam(feats, res["features"], lr=1e-3), Adam(params, res["params"], lr=1e-4)]
@@ -805,7 +820,10 @@ def fusion_rows(dev, iters=10):
     torch.cuda.synchronize()
     prof = C.profile_collect()
     C.vpgs_profile_enable(0)
-    return {"submaps": 2, "keyframes": m, "width": W, "height": H,
+    return {"submaps_resident": FUSION_SUBMAPS, "anchors_resident": sum(s["sc"].n for s in street),
+            "gaussian_capacity_resident": sum(s["sc"].n * s["sc"].k for s in street),
+            "gaussians_decoded_per_submap": resident, "fused_pair": list(FUSION_PAIR), "keyframes": m,
+            "width": W, "height": H,
             "gaussians_decoded": [int(st["out"]["n_dev"].item()) for st in state],
             "ms_per_iteration": ms, "mpix_s": 2 * m * P / (ms * 1e-3) / 1e6,
             "loss": {"first": losses[0], f"after_{iters + 1}": losses[1]},
