@@ -240,17 +240,7 @@ VPGS_D float ex2_approx(float x) {
     return y;
 }
 
-VPGS_D PairEval eval_pair(float dx, float dy, float w1x, float w1y, float w2x, float w2y,
-                          float opac, float alpha_max) {
-    PairEval e;
-    e.t1 = fmaf(w1x, dx, w1y * dy);
-    e.t2 = fmaf(w2x, dx, w2y * dy);
-    e.G = ex2_approx(-fmaf(e.t1, e.t1, e.t2 * e.t2));
-    e.alpha = fminf(alpha_max, opac * e.G);
-    return e;
-}
-
-// The same for a near-degenerate record: d = (px - ux - rx, py - uy - ry) in
+// alpha of a near-degenerate record at pixel (px, py): d = (px - ux - rx, py - uy - ry) in
 // double-float (ux, uy the staged tile-local mean, (rx, ry) its rounding
 // residual) and t2 = w2 . d with w2 = (w2x + w2x_lo, w2y + w2y_lo) as an
 // error-free dot product of the high parts plus the low-order terms; t1 stays

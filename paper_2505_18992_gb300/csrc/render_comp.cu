@@ -111,13 +111,30 @@ VPGS_D void stage(const Rec &r, float ox, float oy, float4 &a, float4 &b, float4
     c = make_float4(r.r2.z, r.r2.w, r.r3.x, r.r2.y);
 }
 
-// alpha of pixel (px, py) (tile-local) for the staged Gaussian (a, b[, f])
+// alpha of the thread's pixel q (tile-local (px, py)) for the staged Gaussian
+// (a, b[, f]).  A thread's pixels are kPix consecutive rows of one column, so in
+// the plain form the whitened coordinates of row q are those of its first row
+// (t1_0, t2_0) plus q times the rows' y coefficients (w1y, w2y); the
+// near-degenerate form evaluates each row in double-float.
 template <bool kFine>
-VPGS_D PairEval eval_staged(float px, float py, const float4 &a, const float4 &b, const float4 &f, float alpha_max) {
-    if constexpr (kFine)
+VPGS_D PairEval eval_staged(int q, float t1_0, float t2_0, float px, float py, const float4 &a, const float4 &b,
+                            const float4 &f, float alpha_max) {
+    if constexpr (kFine) {
         return eval_pair_fine(px, py, a.x, a.y, f.x, f.y, a.z, a.w, b.x, b.y, f.z, f.w, b.z, alpha_max);
-    else
-        return eval_pair(px - a.x, py - a.y, a.z, a.w, b.x, b.y, b.z, alpha_max);
+    } else {
+        PairEval e;
+        e.t1 = fmaf((float)q, a.w, t1_0);
+        e.t2 = fmaf((float)q, b.y, t2_0);
+        e.G = ex2_approx(-fmaf(e.t1, e.t1, e.t2 * e.t2));
+        e.alpha = fminf(alpha_max, b.z * e.G);
+        return e;
+    }
+}
+
+// whitened coordinates of the first of the thread's rows (plain form)
+VPGS_D float2 first_row(float px, float py0, const float4 &a, const float4 &b) {
+    const float dx = px - a.x, dy = py0 - a.y;
+    return make_float2(fmaf(a.z, dx, a.w * dy), fmaf(b.x, dx, b.y * dy));
 }
 
 // register cap of the forward (0: only the 512-thread launch bound)
@@ -193,11 +210,12 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                     constexpr bool kFine = decltype(fine)::value;
                     float4 f;
                     if constexpr (kFine) f = s3[k];
+                    const float2 t0 = kFine ? make_float2(0.f, 0.f) : first_row(pxl, pyl[0], a, b);
                     bool fin = true;
 #pragma unroll
                     for (int q = 0; q < kPix; ++q) {
                         if (!done[q]) {
-                            const PairEval e = eval_staged<kFine>(pxl, pyl[q], a, b, f, o.alpha_max);
+                            const PairEval e = eval_staged<kFine>(q, t0.x, t0.y, pxl, pyl[q], a, b, f, o.alpha_max);
                             if (e.alpha >= o.alpha_min) {
                                 const float nt = T[q] * (1.f - e.alpha);
                                 if (nt < o.t_min) {
@@ -524,10 +542,11 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                     constexpr bool kFine = decltype(fine)::value;
                     float4 f;
                     if constexpr (kFine) f = fine_extra(rec[s_id[kk]], ox, oy, a.x, a.y);
+                    const float2 t0 = kFine ? make_float2(0.f, 0.f) : first_row(pxl, pyl[0], a, b);
                     bool any = false;
 #pragma unroll
                     for (int q = 0; q < kPix; ++q) {
-                        const PairEval e = eval_staged<kFine>(pxl, pyl[q], a, b, f, o.alpha_max);
+                        const PairEval e = eval_staged<kFine>(q, t0.x, t0.y, pxl, pyl[q], a, b, f, o.alpha_max);
                         any |= pair_grad(ps[q], jj, e, b, c, o, v);
                     }
                     return any;
