@@ -143,23 +143,64 @@ struct DecOut {
 };
 
 // dynamic shared memory of the forward kernel
+// The forward's weights in the layout its blocks use: BF16 W1 rows [3 x 32]
+// [kInPad], BF16 W2 rows [120][kW2Pad] (outputs padded per MLP), FP32 biases.
+// Prepared once per call by decode_weights_kernel (the FP32 form keeps the
+// flat FP32 parameters in the same region) and copied into each block's
+// shared memory as 16-byte words.
+struct DecWts {
+    __nv_bfloat16 w1[96 * kInPad];
+    __nv_bfloat16 w2[120 * kW2Pad];
+    float b1[96];
+    float b2[120];
+};
+constexpr int kDecWtsBytes = 48 * 1024;  // room for the forward's forms and the backward's layouts
+static_assert(sizeof(DecWts) % 16 == 0 && sizeof(DecWts) <= kDecWtsBytes, "prepared weights: 16-byte words");
+
 struct DecFwdSmem {
     float out[kDecAnchors * kOutStride];
     union {
         float w[8192];  // FP32 weights (n_params(10) = 7182)
         struct {
-            __nv_bfloat16 w1[96 * kInPad];
-            __nv_bfloat16 w2[120 * kW2Pad];
+            DecWts wt;
             __nv_bfloat16 in[kDecAnchors * kInPad];
-            float b1[96];
-            float b2[120];
         } h;
     } u;
 };
 
+__global__ void __launch_bounds__(256) decode_weights_kernel(DecParams p, DecWts *wts) {
+    grid_dep_enter();
+    const int K = p.K, tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    if (!p.bf16) {
+        float *w = reinterpret_cast<float *>(wts);
+        for (int i = tid; i < n_params(K); i += stride) w[i] = p.params[i];
+        return;
+    }
+    for (int i = tid; i < 96 * kInPad; i += stride) {
+        const int r = i / kInPad, c = i % kInPad;
+        const MlpOff m = mlp_off(K, r / 32);
+        wts->w1[i] = __float2bfloat16_rn(c < kIn ? p.params[m.w1 + (r % 32) * kIn + c] : 0.f);
+    }
+    for (int i = tid; i < 120 * kW2Pad; i += stride) {
+        const int r = i / kW2Pad, c = i % kW2Pad;
+        const int j = r < kColCol ? 0 : (r < kColCov ? 1 : 2);
+        const int base = j == 0 ? kColOpa : (j == 1 ? kColCol : kColCov);
+        const MlpOff m = mlp_off(K, j);
+        const int n = r - base;
+        wts->w2[i] = __float2bfloat16_rn((c < kHid && n < m.out) ? p.params[m.w2 + n * kHid + c] : 0.f);
+    }
+    for (int i = tid; i < 96; i += stride) wts->b1[i] = p.params[mlp_off(K, i / 32).b1 + i % 32];
+    for (int i = tid; i < 120; i += stride) {
+        const int j = i < kColCol ? 0 : (i < kColCov ? 1 : 2);
+        const int base = j == 0 ? kColOpa : (j == 1 ? kColCol : kColCov);
+        const MlpOff m = mlp_off(K, j);
+        wts->b2[i] = (i - base < m.out) ? p.params[m.b2 + i - base] : 0.f;
+    }
+}
+
 __global__ void __launch_bounds__(kDecAnchors)
-decode_fwd_kernel(DecParams p, const double *__restrict__ T, DecOut o, uint32_t *ticket,
-                  unsigned long long *look, uint32_t *status) {
+decode_fwd_kernel(DecParams p, const double *__restrict__ T, DecOut o, const DecWts *__restrict__ wts,
+                  uint32_t *ticket, unsigned long long *look, uint32_t *status) {
     grid_dep_enter();
     extern __shared__ __align__(16) unsigned char dsm[];
     DecFwdSmem &S = *reinterpret_cast<DecFwdSmem *>(dsm);
@@ -172,31 +213,13 @@ decode_fwd_kernel(DecParams p, const double *__restrict__ T, DecOut o, uint32_t 
         load_dec_cam(T, s_cam);
     }
     const int K = p.K;
-    const int np = n_params(K);
-    // weights to shared memory
-    if (!p.bf16) {
-        for (int i = tid; i < np; i += kDecAnchors) S.u.w[i] = p.params[i];
-    } else {
-        for (int i = tid; i < 96 * kInPad; i += kDecAnchors) {
-            const int r = i / kInPad, c = i % kInPad;
-            const MlpOff m = mlp_off(K, r / 32);
-            S.u.h.w1[i] = __float2bfloat16_rn(c < kIn ? p.params[m.w1 + (r % 32) * kIn + c] : 0.f);
-        }
-        for (int i = tid; i < 120 * kW2Pad; i += kDecAnchors) {
-            const int r = i / kW2Pad, c = i % kW2Pad;
-            const int j = r < kColCol ? 0 : (r < kColCov ? 1 : 2);
-            const int base = j == 0 ? kColOpa : (j == 1 ? kColCol : kColCov);
-            const MlpOff m = mlp_off(K, j);
-            const int n = r - base;
-            S.u.h.w2[i] = __float2bfloat16_rn((c < kHid && n < m.out) ? p.params[m.w2 + n * kHid + c] : 0.f);
-        }
-        for (int i = tid; i < 96; i += kDecAnchors) S.u.h.b1[i] = p.params[mlp_off(K, i / 32).b1 + i % 32];
-        for (int i = tid; i < 120; i += kDecAnchors) {
-            const int j = i < kColCol ? 0 : (i < kColCov ? 1 : 2);
-            const int base = j == 0 ? kColOpa : (j == 1 ? kColCol : kColCov);
-            const MlpOff m = mlp_off(K, j);
-            S.u.h.b2[i] = (i - base < m.out) ? p.params[m.b2 + i - base] : 0.f;
-        }
+    {
+        // the prepared weights into shared memory, 16-byte words (both forms start
+        // at the union's first byte)
+        const int words = p.bf16 ? (int)(sizeof(DecWts) / 16) : (n_params(K) + 3) / 4;
+        const uint4 *src = reinterpret_cast<const uint4 *>(wts);
+        uint4 *dst = reinterpret_cast<uint4 *>(&S.u);
+        for (int i = tid; i < words; i += kDecAnchors) dst[i] = src[i];
     }
     __syncthreads();
     const int64_t bid = s_bid;
@@ -240,7 +263,7 @@ decode_fwd_kernel(DecParams p, const double *__restrict__ T, DecOut o, uint32_t 
             float acc[12][4];
 #pragma unroll
             for (int nt = 0; nt < 12; ++nt) {
-                const float b0 = S.u.h.b1[8 * nt + 2 * t4], b1v = S.u.h.b1[8 * nt + 2 * t4 + 1];
+                const float b0 = S.u.h.wt.b1[8 * nt + 2 * t4], b1v = S.u.h.wt.b1[8 * nt + 2 * t4 + 1];
                 acc[nt][0] = b0; acc[nt][1] = b1v; acc[nt][2] = b0; acc[nt][3] = b1v;
             }
             const __nv_bfloat16 *A0 = S.u.h.in + (r0 + g) * kInPad, *A1 = S.u.h.in + (r0 + g + 8) * kInPad;
@@ -253,7 +276,7 @@ decode_fwd_kernel(DecParams p, const double *__restrict__ T, DecOut o, uint32_t 
                 const uint32_t a3 = *reinterpret_cast<const uint32_t *>(A1 + c0 + 8);
 #pragma unroll
                 for (int nt = 0; nt < 12; ++nt) {
-                    const __nv_bfloat16 *Brow = S.u.h.w1 + (8 * nt + g) * kInPad;
+                    const __nv_bfloat16 *Brow = S.u.h.wt.w1 + (8 * nt + g) * kInPad;
                     mma_bf16_16816(acc[nt], a0, a1, a2, a3, *reinterpret_cast<const uint32_t *>(Brow + c0),
                                    *reinterpret_cast<const uint32_t *>(Brow + c0 + 8));
                 }
@@ -274,8 +297,8 @@ decode_fwd_kernel(DecParams p, const double *__restrict__ T, DecOut o, uint32_t 
                 }
                 for (int nt = 0; nt < ntiles; ++nt) {
                     const int col = base + 8 * nt + 2 * t4;
-                    float d[4] = {S.u.h.b2[col], S.u.h.b2[col + 1], S.u.h.b2[col], S.u.h.b2[col + 1]};
-                    const __nv_bfloat16 *Brow = S.u.h.w2 + (base + 8 * nt + g) * kW2Pad;
+                    float d[4] = {S.u.h.wt.b2[col], S.u.h.wt.b2[col + 1], S.u.h.wt.b2[col], S.u.h.wt.b2[col + 1]};
+                    const __nv_bfloat16 *Brow = S.u.h.wt.w2 + (base + 8 * nt + g) * kW2Pad;
 #pragma unroll
                     for (int kk = 0; kk < 2; ++kk) {
                         const int c0 = 16 * kk + 2 * t4;
@@ -311,34 +334,46 @@ decode_fwd_kernel(DecParams p, const double *__restrict__ T, DecOut o, uint32_t 
         if (w < warp) wbase += s_wsum[w];
         total += s_wsum[w];
     }
-    if (tid == 0) {
-        uint32_t excl = 0;
+    // decoupled look-back over earlier blocks, one warp: 32 predecessors per step
+    if (warp == 0) {
+        unsigned long long excl = 0;
         if (bid == 0) {
-            st_volatile_u64(look, kFlagPre | total);
+            if (lane == 0) st_volatile_u64(look, kFlagPre | total);
         } else {
-            st_volatile_u64(look + bid, kFlagAgg | total);
-            int64_t j = bid - 1;
-            unsigned long long acc = 0;
-            while (j >= 0) {
-                unsigned long long w = ld_volatile_u64(look + j);
+            if (lane == 0) st_volatile_u64(look + bid, kFlagAgg | total);
+            int64_t j0 = bid - 1;
+            for (;;) {
+                const int64_t j = j0 - lane;
+                unsigned long long w = j >= 0 ? ld_volatile_u64(look + j) : kFlagPre;
                 int spins = 0;
-                while ((w >> 62) == 0) {
+                bool timed_out = false;
+                while (!__all_sync(0xffffffffu, (w >> 62) != 0)) {
                     if (++spins > kSpinLimit) {
-                        set_status(status, VPGS_ERR_TIMEOUT);
+                        timed_out = true;
                         break;
                     }
                     __nanosleep(64);
-                    w = ld_volatile_u64(look + j);
+                    if ((w >> 62) == 0) w = ld_volatile_u64(look + j);
                 }
-                acc += w & kValMask;
-                if ((w >> 62) == 2 || spins > kSpinLimit) break;
-                --j;
+                if (timed_out) {
+                    if (lane == 0) set_status(status, VPGS_ERR_TIMEOUT);
+                    break;
+                }
+                const uint32_t pre = __ballot_sync(0xffffffffu, (w >> 62) == 2);
+                const int last = pre ? __ffs(pre) - 1 : 31;  // nearest inclusive prefix
+                unsigned long long v = lane <= last ? (w & kValMask) : 0ull;
+#pragma unroll
+                for (int q = 16; q > 0; q >>= 1) v += __shfl_xor_sync(0xffffffffu, v, q);
+                excl += v;
+                if (pre) break;
+                j0 -= 32;
             }
-            excl = (uint32_t)acc;
-            st_volatile_u64(look + bid, kFlagPre | (acc + total));
+            if (lane == 0) st_volatile_u64(look + bid, kFlagPre | (excl + total));
         }
-        s_base = excl;
-        if ((bid + 1) * kDecAnchors >= p.A) *o.n_out = (int32_t)(excl + total);
+        if (lane == 0) {
+            s_base = (uint32_t)excl;
+            if ((bid + 1) * kDecAnchors >= p.A) *o.n_out = (int32_t)(excl + total);
+        }
     }
     __syncthreads();
     if (!mask) return;
@@ -589,12 +624,21 @@ constexpr int kGW = 40;                  // columns of the weight-gradient accum
 VPGS_HD int out_pad16(int j) { return j == 0 ? 16 : (j == 1 ? 32 : 80); }  // per-MLP outputs padded to 16
 VPGS_HD int out_base(int j) { return j == 0 ? 0 : (j == 1 ? 16 : 48); }    // rows of MLP j in W2 / dW2 (K <= 10)
 
-struct DecBwdMmaSmem {
+// The backward's effective weights (BF16-rounded matrices, FP32 biases) in
+// the four layouts its MMAs read; prepared once per call by
+// decode_bwd_weights_kernel and copied into each block's shared memory as
+// 16-byte words.
+struct DecBwdWts {
     __nv_bfloat16 w1[96 * kInPad];       // [hid][in]  (forward layout)
     __nv_bfloat16 w2[120 * kW2Pad];      // [out][hid] (forward layout)
     __nv_bfloat16 w2t[96 * kW2T];        // [MLP*32 + hid][out]
     __nv_bfloat16 w1t[3 * 40 * kW1T];    // [MLP][in][hid]
     float b1[96], b2[120];
+};
+static_assert(sizeof(DecBwdWts) % 16 == 0 && sizeof(DecBwdWts) <= kDecWtsBytes, "prepared weights: 16-byte words");
+
+struct DecBwdMmaSmem {
+    DecBwdWts wt;
     __nv_bfloat16 inrow[kMA * kInPad];   // [anchor][in]
     __nv_bfloat16 inT[40 * kAS];         // [in | 1 | 0][anchor]
     __nv_bfloat16 hT[40 * kAS];          // [hid | 1 | 0][anchor]
@@ -622,9 +666,40 @@ VPGS_D void pack_split(float x0, float x1, uint32_t &hi, uint32_t &lo) {
 
 VPGS_D uint32_t ld_u32(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
 
+__global__ void __launch_bounds__(256) decode_bwd_weights_kernel(DecParams p, DecBwdWts *wts) {
+    grid_dep_enter();
+    const int K = p.K, tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    for (int i = tid; i < 96 * kInPad; i += stride) {
+        const int r = i / kInPad, c = i % kInPad;
+        wts->w1[i] = __float2bfloat16_rn(c < kIn ? p.params[mlp_off(K, r / 32).w1 + (r % 32) * kIn + c] : 0.f);
+    }
+    for (int i = tid; i < 120 * kW2Pad; i += stride) {
+        const int r = i / kW2Pad, c = i % kW2Pad;
+        const int j = r < kColCol ? 0 : (r < kColCov ? 1 : 2);
+        const MlpOff m = mlp_off(K, j);
+        const int n = r - out_base(j);
+        wts->w2[i] = __float2bfloat16_rn((c < kHid && n < m.out) ? p.params[m.w2 + n * kHid + c] : 0.f);
+    }
+    for (int i = tid; i < 96 * kW2T; i += stride) {
+        const int r = i / kW2T, n = i % kW2T, j = r / 32, q = r % 32;
+        const MlpOff m = mlp_off(K, j);
+        wts->w2t[i] = __float2bfloat16_rn(n < m.out ? p.params[m.w2 + n * kHid + q] : 0.f);
+    }
+    for (int i = tid; i < 3 * 40 * kW1T; i += stride) {
+        const int j = i / (40 * kW1T), rem = i % (40 * kW1T), k = rem / kW1T, q = rem % kW1T;
+        wts->w1t[i] = __float2bfloat16_rn((k < kIn && q < kHid) ? p.params[mlp_off(K, j).w1 + q * kIn + k] : 0.f);
+    }
+    for (int i = tid; i < 96; i += stride) wts->b1[i] = p.params[mlp_off(K, i / 32).b1 + i % 32];
+    for (int i = tid; i < 120; i += stride) {
+        const int j = i < kColCol ? 0 : (i < kColCov ? 1 : 2);
+        const MlpOff m = mlp_off(K, j);
+        wts->b2[i] = (i - out_base(j) < m.out) ? p.params[m.b2 + i - out_base(j)] : 0.f;
+    }
+}
+
 __global__ void __launch_bounds__(kMA, 1)
 decode_bwd_mma_kernel(DecParams p, const double *__restrict__ T, const int32_t *__restrict__ inv,
-                      DecGradIn gin, DecGradOut gout) {
+                      const DecBwdWts *__restrict__ wts, DecGradIn gin, DecGradOut gout) {
     grid_dep_enter();
     extern __shared__ __align__(16) unsigned char dsm[];
     DecBwdMmaSmem &S = *reinterpret_cast<DecBwdMmaSmem *>(dsm);
@@ -633,32 +708,11 @@ decode_bwd_mma_kernel(DecParams p, const double *__restrict__ T, const int32_t *
     const int g = lane >> 2, t4 = lane & 3;
     const int K = p.K;
     if (tid == 0) load_dec_cam(T, s_cam);
-    // effective weights (BF16-rounded matrices, FP32 biases) in the four layouts
-    for (int i = tid; i < 96 * kInPad; i += kMA) {
-        const int r = i / kInPad, c = i % kInPad;
-        S.w1[i] = __float2bfloat16_rn(c < kIn ? p.params[mlp_off(K, r / 32).w1 + (r % 32) * kIn + c] : 0.f);
-    }
-    for (int i = tid; i < 120 * kW2Pad; i += kMA) {
-        const int r = i / kW2Pad, c = i % kW2Pad;
-        const int j = r < kColCol ? 0 : (r < kColCov ? 1 : 2);
-        const MlpOff m = mlp_off(K, j);
-        const int n = r - out_base(j);
-        S.w2[i] = __float2bfloat16_rn((c < kHid && n < m.out) ? p.params[m.w2 + n * kHid + c] : 0.f);
-    }
-    for (int i = tid; i < 96 * kW2T; i += kMA) {
-        const int r = i / kW2T, n = i % kW2T, j = r / 32, q = r % 32;
-        const MlpOff m = mlp_off(K, j);
-        S.w2t[i] = __float2bfloat16_rn(n < m.out ? p.params[m.w2 + n * kHid + q] : 0.f);
-    }
-    for (int i = tid; i < 3 * 40 * kW1T; i += kMA) {
-        const int j = i / (40 * kW1T), rem = i % (40 * kW1T), k = rem / kW1T, q = rem % kW1T;
-        S.w1t[i] = __float2bfloat16_rn((k < kIn && q < kHid) ? p.params[mlp_off(K, j).w1 + q * kIn + k] : 0.f);
-    }
-    for (int i = tid; i < 96; i += kMA) S.b1[i] = p.params[mlp_off(K, i / 32).b1 + i % 32];
-    for (int i = tid; i < 120; i += kMA) {
-        const int j = i < kColCol ? 0 : (i < kColCov ? 1 : 2);
-        const MlpOff m = mlp_off(K, j);
-        S.b2[i] = (i - out_base(j) < m.out) ? p.params[m.b2 + i - out_base(j)] : 0.f;
+    {
+        // the prepared weights into shared memory, 16-byte words
+        const uint4 *src = reinterpret_cast<const uint4 *>(wts);
+        uint4 *dst = reinterpret_cast<uint4 *>(&S.wt);
+        for (int i = tid; i < (int)(sizeof(DecBwdWts) / 16); i += kMA) dst[i] = src[i];
     }
     // constant rows: the ones that turn the weight-gradient products into bias gradients
     for (int i = tid; i < 4 * kAS; i += kMA) {
@@ -714,7 +768,7 @@ decode_bwd_mma_kernel(DecParams p, const double *__restrict__ T, const int32_t *
                 float acc[4][4];
 #pragma unroll
                 for (int nt = 0; nt < 4; ++nt) {
-                    const float b0 = S.b1[32 * j + 8 * nt + 2 * t4], b1v = S.b1[32 * j + 8 * nt + 2 * t4 + 1];
+                    const float b0 = S.wt.b1[32 * j + 8 * nt + 2 * t4], b1v = S.wt.b1[32 * j + 8 * nt + 2 * t4 + 1];
                     acc[nt][0] = b0; acc[nt][1] = b1v; acc[nt][2] = b0; acc[nt][3] = b1v;
                 }
                 const __nv_bfloat16 *A0 = S.inrow + (r0 + g) * kInPad, *A1 = S.inrow + (r0 + g + 8) * kInPad;
@@ -725,7 +779,7 @@ decode_bwd_mma_kernel(DecParams p, const double *__restrict__ T, const int32_t *
                                    a3 = ld_u32(A1 + c0 + 8);
 #pragma unroll
                     for (int nt = 0; nt < 4; ++nt) {
-                        const __nv_bfloat16 *B = S.w1 + (32 * j + 8 * nt + g) * kInPad;
+                        const __nv_bfloat16 *B = S.wt.w1 + (32 * j + 8 * nt + g) * kInPad;
                         mma_bf16_16816(acc[nt], a0, a1, a2, a3, ld_u32(B + c0), ld_u32(B + c0 + 8));
                     }
                 }
@@ -749,8 +803,8 @@ decode_bwd_mma_kernel(DecParams p, const double *__restrict__ T, const int32_t *
                 }
                 for (int nt = 0; nt < ntl2; ++nt) {
                     const int col = out_base(j) + 8 * nt + 2 * t4;
-                    float d[4] = {S.b2[col], S.b2[col + 1], S.b2[col], S.b2[col + 1]};
-                    const __nv_bfloat16 *B = S.w2 + (out_base(j) + 8 * nt + g) * kW2Pad;
+                    float d[4] = {S.wt.b2[col], S.wt.b2[col + 1], S.wt.b2[col], S.wt.b2[col + 1]};
+                    const __nv_bfloat16 *B = S.wt.w2 + (out_base(j) + 8 * nt + g) * kW2Pad;
 #pragma unroll
                     for (int kk = 0; kk < 2; ++kk) {
                         const int c0 = 16 * kk + 2 * t4;
@@ -825,7 +879,7 @@ decode_bwd_mma_kernel(DecParams p, const double *__restrict__ T, const int32_t *
                     pack_split(O1[c0 + 8], O1[c0 + 9], ah[3], alo[3]);
 #pragma unroll
                     for (int nt = 0; nt < 4; ++nt) {
-                        const __nv_bfloat16 *B = S.w2t + (32 * j + 8 * nt + g) * kW2T;
+                        const __nv_bfloat16 *B = S.wt.w2t + (32 * j + 8 * nt + g) * kW2T;
                         const uint32_t b0 = ld_u32(B + c0), b1 = ld_u32(B + c0 + 8);
                         mma_bf16_16816(dh[nt], ah[0], ah[1], ah[2], ah[3], b0, b1);
                         mma_bf16_16816(dh[nt], alo[0], alo[1], alo[2], alo[3], b0, b1);
@@ -850,7 +904,7 @@ decode_bwd_mma_kernel(DecParams p, const double *__restrict__ T, const int32_t *
                     const int c0 = 16 * kk + 2 * t4;
 #pragma unroll
                     for (int nt = 0; nt < 5; ++nt) {
-                        const __nv_bfloat16 *B = S.w1t + (j * 40 + 8 * nt + g) * kW1T;
+                        const __nv_bfloat16 *B = S.wt.w1t + (j * 40 + 8 * nt + g) * kW1T;
                         const uint32_t b0 = ld_u32(B + c0), b1 = ld_u32(B + c0 + 8);
                         mma_bf16_16816(dIn[mt][nt], ah[0], ah[1], ah[2], ah[3], b0, b1);
                         mma_bf16_16816(dIn[mt][nt], alo[0], alo[1], alo[2], alo[3], b0, b1);
@@ -949,7 +1003,7 @@ decode_bwd_mma_kernel(DecParams p, const double *__restrict__ T, const int32_t *
 // workspace: [0] status, [256] counters (ticket), [512] look-back words, inverse map
 // ---------------------------------------------------------------------------
 struct DecLayout {
-    size_t off_status, off_counters, off_look, off_inv, total;
+    size_t off_status, off_counters, off_look, off_inv, off_wts, total;
     int64_t nblocks;
 };
 
@@ -961,7 +1015,8 @@ static DecLayout dec_layout(int64_t A, int K) {
     L.off_counters = 256;
     L.off_look = 512;
     L.off_inv = up(L.off_look + 8 * (size_t)std::max<int64_t>(L.nblocks, 1));
-    L.total = up(L.off_inv + 4 * (size_t)std::max<int64_t>(A * K, 1));
+    L.off_wts = up(L.off_inv + 4 * (size_t)std::max<int64_t>(A * K, 1));
+    L.total = up(L.off_wts + kDecWtsBytes);
     return L;
 }
 
@@ -1015,9 +1070,11 @@ vpgs_status vpgs_decode_anchors(void *ws, size_t ws_bytes, const vpgs_anchors *a
     uint32_t *status = reinterpret_cast<uint32_t *>(b + L.off_status);
     uint32_t *ticket = reinterpret_cast<uint32_t *>(b + L.off_counters + 4 * CNT_TICKET_A);
     unsigned long long *look = reinterpret_cast<unsigned long long *>(b + L.off_look);
+    DecWts *wts = reinterpret_cast<DecWts *>(b + L.off_wts);
+    VPGS_LAUNCH("decode_weights", s, launch_k(decode_weights_kernel, 8, 256, 0, s, p, wts));
     VPGS_LAUNCH("decode_fwd", s,
-                launch_k(decode_fwd_kernel, (unsigned)L.nblocks, kDecAnchors, smem, s, p, T_cw, o, ticket,
-                                                                                 look, status));
+                launch_k(decode_fwd_kernel, (unsigned)L.nblocks, kDecAnchors, smem, s, p, T_cw, o,
+                         (const DecWts *)wts, ticket, look, status));
     return cudaGetLastError() == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
 }
 
@@ -1056,7 +1113,10 @@ vpgs_status vpgs_decode_anchors_bwd(void *ws, size_t ws_bytes, const vpgs_anchor
                              (int)msm);
         const int64_t nch = (p.A + kMA - 1) / kMA;
         const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nch, sms));
-        VPGS_LAUNCH("decode_bwd", s, launch_k(decode_bwd_mma_kernel, grid, kMA, msm, s, p, T_cw, inv, gin, gout));
+        DecBwdWts *wts = reinterpret_cast<DecBwdWts *>(b + L.off_wts);
+        VPGS_LAUNCH("decode_bwd_weights", s, launch_k(decode_bwd_weights_kernel, 8, 256, 0, s, p, wts));
+        VPGS_LAUNCH("decode_bwd", s, launch_k(decode_bwd_mma_kernel, grid, kMA, msm, s, p, T_cw, inv,
+                                              (const DecBwdWts *)wts, gin, gout));
         return cudaGetLastError() == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
     }
     const unsigned nb = (unsigned)((p.A + kBwdAnchors - 1) / kBwdAnchors);
