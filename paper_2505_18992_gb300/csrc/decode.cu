@@ -27,7 +27,8 @@ namespace vpgs {
 #define VPGS_DECODE_BWD_MMA 1  // BF16 form: backward on tensor cores (0: the FP32-FMA kernel)
 #endif
 
-constexpr int kDecAnchors = 128;   // anchors (and threads) per block
+constexpr int kDecAnchors = 64;    // anchors per forward block
+constexpr int kDecThreads = 128;   // threads per forward block (two per anchor)
 constexpr int kFeat = 32, kIn = 36, kHid = 32, kMaxK = 10;
 constexpr int kOutStride = 121;    // per-anchor row of layer-2 outputs in shared memory
 constexpr int kColOpa = 0, kColCol = 16, kColCov = 48;  // column bases (padded to n8 tiles)
@@ -166,6 +167,7 @@ struct DecFwdSmem {
             __nv_bfloat16 in[kDecAnchors * kInPad];
         } h;
     } u;
+    uint16_t slot[kDecAnchors * kMaxK];  // per output slot of the block: local anchor << 4 | m
 };
 
 __global__ void __launch_bounds__(256) decode_weights_kernel(DecParams p, DecWts *wts) {
@@ -198,14 +200,43 @@ __global__ void __launch_bounds__(256) decode_weights_kernel(DecParams p, DecWts
     }
 }
 
-__global__ void __launch_bounds__(kDecAnchors)
+// FP32 form: MLP j of one anchor, outputs into its row
+VPGS_D void mlp_fp32(const float *w, int K, int j, const float (&in)[kIn], float *orow) {
+    const MlpOff m = mlp_off(K, j);
+    float h[kHid];
+#pragma unroll
+    for (int q = 0; q < kHid; ++q) {
+        const float *wr = w + m.w1 + q * kIn;
+        float acc = w[m.b1 + q];
+#pragma unroll
+        for (int k = 0; k < kIn; ++k) acc = fmaf(wr[k], in[k], acc);
+        h[q] = fmaxf(acc, 0.f);
+    }
+    const int base = j == 0 ? kColOpa : (j == 1 ? kColCol : kColCov);
+    for (int n = 0; n < m.out; ++n) {
+        const float *wr = w + m.w2 + n * kHid;
+        float acc = w[m.b2 + n];
+#pragma unroll
+        for (int k = 0; k < kHid; ++k) acc = fmaf(wr[k], h[k], acc);
+        orow[base + n] = acc;
+    }
+}
+
+// Blocks of kDecThreads threads decode kDecAnchors anchors: thread t < 64 owns
+// anchor t for its inputs and its valid-Gaussian count; in the FP32 form
+// threads t and t + 64 split its three MLPs (0 and 1 / 2: nearly equal
+// work); in the BF16 form each warp runs one 16-anchor tile on tensor cores.
+// After the block's compaction offset is known, the outputs are made one
+// Gaussian per thread in output order, so consecutive threads write
+// consecutive entries.
+__global__ void __launch_bounds__(kDecThreads)
 decode_fwd_kernel(DecParams p, const double *__restrict__ T, DecOut o, const DecWts *__restrict__ wts,
                   uint32_t *ticket, unsigned long long *look, uint32_t *status) {
     grid_dep_enter();
     extern __shared__ __align__(16) unsigned char dsm[];
     DecFwdSmem &S = *reinterpret_cast<DecFwdSmem *>(dsm);
-    __shared__ uint32_t s_bid, s_base;
-    __shared__ uint32_t s_wsum[kDecAnchors / 32];
+    __shared__ uint32_t s_bid, s_base, s_total;
+    __shared__ uint32_t s_wsum[kDecThreads / 32];
     __shared__ DecCam s_cam;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
@@ -219,108 +250,94 @@ decode_fwd_kernel(DecParams p, const double *__restrict__ T, DecOut o, const Dec
         const int words = p.bf16 ? (int)(sizeof(DecWts) / 16) : (n_params(K) + 3) / 4;
         const uint4 *src = reinterpret_cast<const uint4 *>(wts);
         uint4 *dst = reinterpret_cast<uint4 *>(&S.u);
-        for (int i = tid; i < words; i += kDecAnchors) dst[i] = src[i];
+        for (int i = tid; i < words; i += kDecThreads) dst[i] = src[i];
     }
     __syncthreads();
     const int64_t bid = s_bid;
-    const int64_t a = bid * kDecAnchors + tid;
+    const int la = tid & (kDecAnchors - 1);  // the block-local anchor this thread reads
+    const int64_t a = bid * kDecAnchors + la;
     const bool live = a < p.A;
     float in[kIn];
     bool keep = false;
-    if (live) keep = anchor_inputs(p, s_cam, a, in);
-    float *orow = S.out + tid * kOutStride;
+    if (live && (!p.bf16 || tid < kDecAnchors)) keep = anchor_inputs(p, s_cam, a, in);
+    float *orow = S.out + la * kOutStride;
     if (!p.bf16) {
         if (keep) {
-            for (int j = 0; j < 3; ++j) {
-                const MlpOff m = mlp_off(K, j);
-                float h[kHid];
-#pragma unroll
-                for (int q = 0; q < kHid; ++q) {
-                    const float *w = S.u.w + m.w1 + q * kIn;
-                    float acc = S.u.w[m.b1 + q];
-#pragma unroll
-                    for (int k = 0; k < kIn; ++k) acc = fmaf(w[k], in[k], acc);
-                    h[q] = fmaxf(acc, 0.f);
-                }
-                const int base = j == 0 ? kColOpa : (j == 1 ? kColCol : kColCov);
-                for (int n = 0; n < m.out; ++n) {
-                    const float *w = S.u.w + m.w2 + n * kHid;
-                    float acc = S.u.w[m.b2 + n];
-#pragma unroll
-                    for (int k = 0; k < kHid; ++k) acc = fmaf(w[k], h[k], acc);
-                    orow[base + n] = acc;
-                }
+            if (tid < kDecAnchors) {
+                mlp_fp32(S.u.w, K, 0, in, orow);
+                mlp_fp32(S.u.w, K, 1, in, orow);
+            } else {
+                mlp_fp32(S.u.w, K, 2, in, orow);
             }
         }
     } else {
         // stage the (already BF16-rounded) inputs, then tensor-core tiles
-        __nv_bfloat16 *irow = S.u.h.in + tid * kInPad;
-        for (int k = 0; k < kInPad; ++k) irow[k] = __float2bfloat16_rn(live && k < kIn ? in[k] : 0.f);
-        __syncwarp();
+        if (tid < kDecAnchors) {
+            __nv_bfloat16 *irow = S.u.h.in + tid * kInPad;
+            for (int k = 0; k < kInPad; ++k) irow[k] = __float2bfloat16_rn(live && k < kIn ? in[k] : 0.f);
+        }
+        __syncthreads();
         const int g = lane >> 2, t4 = lane & 3;
-        for (int mt = 0; mt < 2; ++mt) {
-            const int r0 = warp * 32 + mt * 16;
-            float acc[12][4];
+        const int r0 = warp * 16;
+        float acc[12][4];
+#pragma unroll
+        for (int nt = 0; nt < 12; ++nt) {
+            const float b0 = S.u.h.wt.b1[8 * nt + 2 * t4], b1v = S.u.h.wt.b1[8 * nt + 2 * t4 + 1];
+            acc[nt][0] = b0; acc[nt][1] = b1v; acc[nt][2] = b0; acc[nt][3] = b1v;
+        }
+        const __nv_bfloat16 *A0 = S.u.h.in + (r0 + g) * kInPad, *A1 = S.u.h.in + (r0 + g + 8) * kInPad;
+#pragma unroll
+        for (int ks = 0; ks < 3; ++ks) {
+            const int c0 = 16 * ks + 2 * t4;
+            const uint32_t a0 = *reinterpret_cast<const uint32_t *>(A0 + c0);
+            const uint32_t a1 = *reinterpret_cast<const uint32_t *>(A1 + c0);
+            const uint32_t a2 = *reinterpret_cast<const uint32_t *>(A0 + c0 + 8);
+            const uint32_t a3 = *reinterpret_cast<const uint32_t *>(A1 + c0 + 8);
 #pragma unroll
             for (int nt = 0; nt < 12; ++nt) {
-                const float b0 = S.u.h.wt.b1[8 * nt + 2 * t4], b1v = S.u.h.wt.b1[8 * nt + 2 * t4 + 1];
-                acc[nt][0] = b0; acc[nt][1] = b1v; acc[nt][2] = b0; acc[nt][3] = b1v;
+                const __nv_bfloat16 *Brow = S.u.h.wt.w1 + (8 * nt + g) * kInPad;
+                mma_bf16_16816(acc[nt], a0, a1, a2, a3, *reinterpret_cast<const uint32_t *>(Brow + c0),
+                               *reinterpret_cast<const uint32_t *>(Brow + c0 + 8));
             }
-            const __nv_bfloat16 *A0 = S.u.h.in + (r0 + g) * kInPad, *A1 = S.u.h.in + (r0 + g + 8) * kInPad;
+        }
+        // layer 2 per MLP: hidden (ReLU, BF16) comes straight from the accumulators
 #pragma unroll
-            for (int ks = 0; ks < 3; ++ks) {
-                const int c0 = 16 * ks + 2 * t4;
-                const uint32_t a0 = *reinterpret_cast<const uint32_t *>(A0 + c0);
-                const uint32_t a1 = *reinterpret_cast<const uint32_t *>(A1 + c0);
-                const uint32_t a2 = *reinterpret_cast<const uint32_t *>(A0 + c0 + 8);
-                const uint32_t a3 = *reinterpret_cast<const uint32_t *>(A1 + c0 + 8);
+        for (int j = 0; j < 3; ++j) {
+            const int ntiles = j == 0 ? 2 : (j == 1 ? 4 : 9);
+            const int base = j == 0 ? kColOpa : (j == 1 ? kColCol : kColCov);
+            uint32_t ha[2][4];
 #pragma unroll
-                for (int nt = 0; nt < 12; ++nt) {
-                    const __nv_bfloat16 *Brow = S.u.h.wt.w1 + (8 * nt + g) * kInPad;
-                    mma_bf16_16816(acc[nt], a0, a1, a2, a3, *reinterpret_cast<const uint32_t *>(Brow + c0),
-                                   *reinterpret_cast<const uint32_t *>(Brow + c0 + 8));
-                }
+            for (int kk = 0; kk < 2; ++kk) {
+                const float *x0 = acc[4 * j + 2 * kk], *x1 = acc[4 * j + 2 * kk + 1];
+                ha[kk][0] = pack_bf16(fmaxf(x0[0], 0.f), fmaxf(x0[1], 0.f));
+                ha[kk][1] = pack_bf16(fmaxf(x0[2], 0.f), fmaxf(x0[3], 0.f));
+                ha[kk][2] = pack_bf16(fmaxf(x1[0], 0.f), fmaxf(x1[1], 0.f));
+                ha[kk][3] = pack_bf16(fmaxf(x1[2], 0.f), fmaxf(x1[3], 0.f));
             }
-            // layer 2 per MLP: hidden (ReLU, BF16) comes straight from the accumulators
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const int ntiles = j == 0 ? 2 : (j == 1 ? 4 : 9);
-                const int base = j == 0 ? kColOpa : (j == 1 ? kColCol : kColCov);
-                uint32_t ha[2][4];
+            for (int nt = 0; nt < ntiles; ++nt) {
+                const int col = base + 8 * nt + 2 * t4;
+                float d[4] = {S.u.h.wt.b2[col], S.u.h.wt.b2[col + 1], S.u.h.wt.b2[col], S.u.h.wt.b2[col + 1]};
+                const __nv_bfloat16 *Brow = S.u.h.wt.w2 + (base + 8 * nt + g) * kW2Pad;
 #pragma unroll
                 for (int kk = 0; kk < 2; ++kk) {
-                    const float *x0 = acc[4 * j + 2 * kk], *x1 = acc[4 * j + 2 * kk + 1];
-                    ha[kk][0] = pack_bf16(fmaxf(x0[0], 0.f), fmaxf(x0[1], 0.f));
-                    ha[kk][1] = pack_bf16(fmaxf(x0[2], 0.f), fmaxf(x0[3], 0.f));
-                    ha[kk][2] = pack_bf16(fmaxf(x1[0], 0.f), fmaxf(x1[1], 0.f));
-                    ha[kk][3] = pack_bf16(fmaxf(x1[2], 0.f), fmaxf(x1[3], 0.f));
+                    const int c0 = 16 * kk + 2 * t4;
+                    mma_bf16_16816(d, ha[kk][0], ha[kk][1], ha[kk][2], ha[kk][3],
+                                   *reinterpret_cast<const uint32_t *>(Brow + c0),
+                                   *reinterpret_cast<const uint32_t *>(Brow + c0 + 8));
                 }
-                for (int nt = 0; nt < ntiles; ++nt) {
-                    const int col = base + 8 * nt + 2 * t4;
-                    float d[4] = {S.u.h.wt.b2[col], S.u.h.wt.b2[col + 1], S.u.h.wt.b2[col], S.u.h.wt.b2[col + 1]};
-                    const __nv_bfloat16 *Brow = S.u.h.wt.w2 + (base + 8 * nt + g) * kW2Pad;
-#pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-                        const int c0 = 16 * kk + 2 * t4;
-                        mma_bf16_16816(d, ha[kk][0], ha[kk][1], ha[kk][2], ha[kk][3],
-                                       *reinterpret_cast<const uint32_t *>(Brow + c0),
-                                       *reinterpret_cast<const uint32_t *>(Brow + c0 + 8));
-                    }
-                    float *o0 = S.out + (r0 + g) * kOutStride + col;
-                    float *o1 = S.out + (r0 + g + 8) * kOutStride + col;
-                    o0[0] = d[0]; o0[1] = d[1]; o1[0] = d[2]; o1[1] = d[3];
-                }
+                float *o0 = S.out + (r0 + g) * kOutStride + col;
+                float *o1 = S.out + (r0 + g + 8) * kOutStride + col;
+                o0[0] = d[0]; o0[1] = d[1]; o1[0] = d[2]; o1[1] = d[3];
             }
         }
     }
     __syncthreads();
-    // valid Gaussians of this anchor and their count
+    // valid Gaussians of each anchor (threads < kDecAnchors), their block-local starts
     uint32_t mask = 0;
-    if (keep)
+    if (tid < kDecAnchors && keep)
         for (int m = 0; m < K; ++m)
             if (orow[kColOpa + m] > 0.f) mask |= 1u << m;
     const uint32_t cnt = __popc(mask);
-    // block exclusive scan of the counts
     uint32_t x = cnt;
 #pragma unroll
     for (int q = 1; q < 32; q <<= 1) {
@@ -330,9 +347,15 @@ decode_fwd_kernel(DecParams p, const double *__restrict__ T, DecOut o, const Dec
     if (lane == 31) s_wsum[warp] = x;
     __syncthreads();
     uint32_t wbase = 0, total = 0;
-    for (int w = 0; w < kDecAnchors / 32; ++w) {
+    for (int w = 0; w < kDecThreads / 32; ++w) {
         if (w < warp) wbase += s_wsum[w];
         total += s_wsum[w];
+    }
+    // the (anchor, m) of each of the block's output slots, in (anchor, m) order
+    {
+        uint32_t at = wbase + (x - cnt);
+        for (int m = 0; m < K; ++m)
+            if (mask >> m & 1u) S.slot[at++] = (uint16_t)((tid << 4) | m);
     }
     // decoupled look-back over earlier blocks, one warp: 32 predecessors per step
     if (warp == 0) {
@@ -372,35 +395,38 @@ decode_fwd_kernel(DecParams p, const double *__restrict__ T, DecOut o, const Dec
         }
         if (lane == 0) {
             s_base = (uint32_t)excl;
+            s_total = total;
             if ((bid + 1) * kDecAnchors >= p.A) *o.n_out = (int32_t)(excl + total);
         }
     }
     __syncthreads();
-    if (!mask) return;
+    // one output Gaussian per thread, in output order
     const int64_t cap = p.A * K;
-    int64_t pos = (int64_t)s_base + wbase + (x - cnt);
-    const float l0 = p.scaling[3 * a], l1 = p.scaling[3 * a + 1], l2 = p.scaling[3 * a + 2];
-    const float xa = p.anchors[3 * a], ya = p.anchors[3 * a + 1], za = p.anchors[3 * a + 2];
-    for (int m = 0; m < K; ++m) {
-        if (!(mask >> m & 1u)) continue;
+    const uint32_t tot = s_total;
+    for (uint32_t sl = tid; sl < tot; sl += kDecThreads) {
+        const int64_t pos = (int64_t)s_base + sl;
         if (pos >= cap) break;  // only after a timed-out look-back
-        const float *O = p.offsets + (a * K + m) * 3;
-        o.means[3 * pos] = fmaf(O[0], l0, xa);
-        o.means[3 * pos + 1] = fmaf(O[1], l1, ya);
-        o.means[3 * pos + 2] = fmaf(O[2], l2, za);
-        o.opac[pos] = tanhf(orow[kColOpa + m]);
-        const float *cc = orow + kColCol + 3 * m;
+        const uint32_t e = S.slot[sl];
+        const int al = (int)(e >> 4), m = (int)(e & 15u);
+        const int64_t aa = bid * kDecAnchors + al;
+        const float *orw = S.out + al * kOutStride;
+        const float l0 = p.scaling[3 * aa], l1 = p.scaling[3 * aa + 1], l2 = p.scaling[3 * aa + 2];
+        const float *O = p.offsets + (aa * K + m) * 3;
+        o.means[3 * pos] = fmaf(O[0], l0, p.anchors[3 * aa]);
+        o.means[3 * pos + 1] = fmaf(O[1], l1, p.anchors[3 * aa + 1]);
+        o.means[3 * pos + 2] = fmaf(O[2], l2, p.anchors[3 * aa + 2]);
+        o.opac[pos] = tanhf(orw[kColOpa + m]);
+        const float *cc = orw + kColCol + 3 * m;
         o.colors[3 * pos] = sigmoidf_(cc[0]);
         o.colors[3 * pos + 1] = sigmoidf_(cc[1]);
         o.colors[3 * pos + 2] = sigmoidf_(cc[2]);
-        const float *cv = orow + kColCov + 7 * m;
+        const float *cv = orw + kColCov + 7 * m;
         o.scales[3 * pos] = sigmoidf_(cv[0]) * l0;
         o.scales[3 * pos + 1] = sigmoidf_(cv[1]) * l1;
         o.scales[3 * pos + 2] = sigmoidf_(cv[2]) * l2;
         const float inv = 1.0f / sqrtf(cv[3] * cv[3] + cv[4] * cv[4] + cv[5] * cv[5] + cv[6] * cv[6]);
         reinterpret_cast<float4 *>(o.quats)[pos] = make_float4(cv[3] * inv, cv[4] * inv, cv[5] * inv, cv[6] * inv);
-        o.src_index[pos] = (int32_t)(a * K + m);
-        ++pos;
+        o.src_index[pos] = (int32_t)(aa * K + m);
     }
 }
 
@@ -1073,7 +1099,7 @@ vpgs_status vpgs_decode_anchors(void *ws, size_t ws_bytes, const vpgs_anchors *a
     DecWts *wts = reinterpret_cast<DecWts *>(b + L.off_wts);
     VPGS_LAUNCH("decode_weights", s, launch_k(decode_weights_kernel, 8, 256, 0, s, p, wts));
     VPGS_LAUNCH("decode_fwd", s,
-                launch_k(decode_fwd_kernel, (unsigned)L.nblocks, kDecAnchors, smem, s, p, T_cw, o,
+                launch_k(decode_fwd_kernel, (unsigned)L.nblocks, kDecThreads, smem, s, p, T_cw, o,
                          (const DecWts *)wts, ticket, look, status));
     return cudaGetLastError() == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
 }
