@@ -239,3 +239,53 @@ def test_stop_rule_and_clamp_at_pixel_centres():
     assert out["t_final"][0, 60, 80] == np.float32(0.5) ** 13       # exact in float32
     one_minus = np.float32(1.0) - np.float32(0.99)
     assert out["t_final"][0, 40, 100] == one_minus * np.float32(0.5) ** 6
+
+
+# ---------------------------------------------------------------------------
+# tile lists of thousands of entries
+# ---------------------------------------------------------------------------
+
+def _long_list_scene(seed=21, n=5000, groups=10, per=4, W=96, H=72, f=100.0):
+    """n Gaussians of about 5 px sigma, centred within 6 px of the corner shared
+    by four 16x16 tiles, so each is listed in all four and every list runs past
+    4,096 entries (many sort tiles of the tile-id sort, and compositing batches).
+    Depth falls with the index, so the depth order reverses the index order.
+    In front of them, `groups` groups of `per` Gaussians with identical means
+    (bit-identical camera z), faint enough that the crowd behind still shows."""
+    rng = np.random.default_rng(seed)
+    cx, cy = 48.0, 32.0  # pixel (48, 32) is the corner of tiles (2..3, 1..2)
+    z = np.linspace(4.0, 1.5, n) + rng.uniform(-1e-4, 1e-4, n)  # 5e-4 apart: no near-ties
+    du, dv = rng.uniform(-6, 6, n), rng.uniform(-6, 6, n)
+    means = np.stack([du * z / f, dv * z / f, z], 1)
+    scales = np.exp(rng.uniform(np.log(0.04), np.log(0.06), (n, 3))) * z[:, None]
+    opac = rng.uniform(0.3, 0.8, n)
+    zt = rng.uniform(1.2, 1.45, groups)
+    dt = rng.uniform(-6, 6, (groups, 2))
+    tmeans = np.repeat(np.stack([dt[:, 0] * zt / f, dt[:, 1] * zt / f, zt], 1), per, 0)
+    tscales = np.exp(rng.uniform(np.log(0.03), np.log(0.05), (groups * per, 3))) * np.repeat(zt, per)[:, None]
+    topac = rng.uniform(0.05, 0.1, groups * per)
+    m = n + groups * per
+    parts = [(np.concatenate([means, tmeans]), np.concatenate([scales, tscales]), rng.normal(size=(m, 4)),
+              np.concatenate([opac, topac]), rng.uniform(0, 1, (m, 3)))]
+    allv = _with_background(rng, parts, 100, W, H, f, depth=(4.5, 6.0))
+    return _scene("long lists", *allv, W, H, f, [np.eye(4)], cx=cx, cy=cy), m
+
+
+def test_long_tile_lists_keep_depth_order_with_ties_by_index():
+    sc, m = _long_list_scene()
+    exact = Margins(exact_ties=True)
+    out, ref0, p = _parity(sc, margins=exact)
+    counts = p["tile_count"][0]
+    # every centre lies within 1.5 sigma of the four tiles' shared corner, so each
+    # of the crowd is listed in all four: their lists run past 4,096 entries
+    assert (counts[:m] >= 4).all()
+    # the tie rule shows: with the crowd's index order reversed (the depth order
+    # unchanged but for the tie groups) the oracle's image changes, and the GPU's
+    # image is not that one
+    perm = np.arange(sc.n)
+    perm[:m] = perm[:m][::-1]
+    rev = scenes.GaussianScene("long lists reversed", *(np.ascontiguousarray(a[perm]) for a in sc.arrays()),
+                               sc.camera)
+    b = oracle.render_scene(rev, margins=exact)
+    assert np.abs(ref0["rgb"] - b["rgb"]).max() > 1e-2
+    assert np.abs(out["rgb"] - b["rgb"]).max() > 1e-2
