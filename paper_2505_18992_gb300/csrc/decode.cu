@@ -630,8 +630,10 @@ decode_bwd_kernel(DecParams p, const double *__restrict__ T, const int32_t *__re
 }
 
 // ---------------------------------------------------------------------------
-// BF16 backward on tensor cores.  Persistent blocks of 128 threads walk chunks
-// of 128 anchors; each warp owns 32 anchors (two 16-row tiles).  Per MLP:
+// BF16 backward on tensor cores.  Persistent blocks of 256 threads walk chunks
+// of 128 anchors; in the tensor-core phases each of the 8 warps owns one 16-row
+// tile of anchors, in the per-anchor phases two threads serve each anchor
+// (alternate Gaussians, halves of the features).  Per MLP:
 //   P = In W1^T + b1 and O = H W2^T + b2 are recomputed with BF16 operands
 //   (exact: inputs, weights and H are BF16 values), the head derivatives dO
 //   are formed per anchor, then
@@ -641,7 +643,8 @@ decode_bwd_kernel(DecParams p, const double *__restrict__ T, const int32_t *__re
 // error 2^-16 per term) with FP32 accumulation.  Weight gradients accumulate in
 // shared memory over the block's chunks and reach global memory once per block.
 // ---------------------------------------------------------------------------
-constexpr int kMA = 128;                 // anchors per chunk (= threads)
+constexpr int kMA = 128;                 // anchors per chunk
+constexpr int kMT = 2 * kMA;             // threads: two per anchor, 16 chunk rows per warp
 constexpr int kAS = kMA + 8;             // row stride (bf16) of anchor-major staging
 constexpr int kOS = 81;                  // row stride (float) of per-anchor output rows
 constexpr int kW2T = 88;                 // row stride (bf16) of W2^T rows (outputs padded to 80)
@@ -723,13 +726,15 @@ __global__ void __launch_bounds__(256) decode_bwd_weights_kernel(DecParams p, De
     }
 }
 
-__global__ void __launch_bounds__(kMA, 1)
+__global__ void __launch_bounds__(kMT, 1)
 decode_bwd_mma_kernel(DecParams p, const double *__restrict__ T, const int32_t *__restrict__ inv,
                       const DecBwdWts *__restrict__ wts, DecGradIn gin, DecGradOut gout) {
     grid_dep_enter();
     extern __shared__ __align__(16) unsigned char dsm[];
     DecBwdMmaSmem &S = *reinterpret_cast<DecBwdMmaSmem *>(dsm);
     __shared__ DecCam s_cam;
+    __shared__ float s_dl[kMA][3];
+    __shared__ uint8_t s_keep[kMA];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = lane >> 2, t4 = lane & 3;
     const int K = p.K;
@@ -738,59 +743,63 @@ decode_bwd_mma_kernel(DecParams p, const double *__restrict__ T, const int32_t *
         // the prepared weights into shared memory, 16-byte words
         const uint4 *src = reinterpret_cast<const uint4 *>(wts);
         uint4 *dst = reinterpret_cast<uint4 *>(&S.wt);
-        for (int i = tid; i < (int)(sizeof(DecBwdWts) / 16); i += kMA) dst[i] = src[i];
+        for (int i = tid; i < (int)(sizeof(DecBwdWts) / 16); i += kMT) dst[i] = src[i];
     }
     // constant rows: the ones that turn the weight-gradient products into bias gradients
-    for (int i = tid; i < 4 * kAS; i += kMA) {
+    for (int i = tid; i < 4 * kAS; i += kMT) {
         const __nv_bfloat16 v = __float2bfloat16_rn(i < kAS ? 1.f : 0.f);
         S.inT[36 * kAS + i] = v;
         S.hT[32 * kAS + i] = v;
         S.hT[36 * kAS + i] = __float2bfloat16_rn(0.f);
     }
-    for (int i = tid; i < 3 * 32 * kGW; i += kMA) S.gw1[i] = 0.f;
-    for (int i = tid; i < 128 * kGW; i += kMA) S.gw2[i] = 0.f;
+    for (int i = tid; i < 3 * 32 * kGW; i += kMT) S.gw1[i] = 0.f;
+    for (int i = tid; i < 128 * kGW; i += kMT) S.gw2[i] = 0.f;
     __syncthreads();
 
     const int64_t nchunks = (p.A + kMA - 1) / kMA;
+    // the anchor row this thread serves in the per-anchor phases (two threads per
+    // anchor), and the warp's 16 chunk rows in the tensor-core phases
+    const int ta = tid & (kMA - 1), half = tid / kMA;
+    const int r0 = warp * 16;
     for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-        // ---- per anchor: inputs, surviving Gaussians
-        const int64_t a = ch * kMA + tid;
+        // ---- per anchor: inputs (first thread of the pair), surviving Gaussians
+        const int64_t a = ch * kMA + ta;
         const bool live = a < p.A;
-        float in[kIn];
-        bool keep = false;
-        if (live) keep = anchor_inputs(p, s_cam, a, in);
+        if (half == 0) {
+            float in[kIn];
+            bool kp = false;
+            if (live) kp = anchor_inputs(p, s_cam, a, in);
+            for (int k = 0; k < kInPad; ++k) {
+                const __nv_bfloat16 v = __float2bfloat16_rn(kp && k < kIn ? in[k] : 0.f);
+                S.inrow[ta * kInPad + k] = v;
+                if (k < kIn) S.inT[k * kAS + ta] = v;
+            }
+            s_keep[ta] = kp ? 1 : 0;
+        }
+        float l[3] = {0, 0, 0}, dl[3] = {0, 0, 0};
+        if (live) {
+            l[0] = p.scaling[3 * a]; l[1] = p.scaling[3 * a + 1]; l[2] = p.scaling[3 * a + 2];
+        }
+        float dIn[5][4];
+#pragma unroll
+        for (int nt = 0; nt < 5; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) dIn[nt][e] = 0.f;
+        __syncthreads();
+        const bool keep = s_keep[ta] != 0;
         int idx[kMaxK];
         bool any = false;
         for (int m = 0; m < K; ++m) {
             idx[m] = keep ? inv[a * K + m] : -1;
             any |= idx[m] >= 0;
         }
-        for (int k = 0; k < kInPad; ++k) {
-            const __nv_bfloat16 v = __float2bfloat16_rn(keep && k < kIn ? in[k] : 0.f);
-            S.inrow[tid * kInPad + k] = v;
-            if (k < kIn) S.inT[k * kAS + tid] = v;
-        }
-        float l[3] = {0, 0, 0}, dl[3] = {0, 0, 0};
-        if (live) {
-            l[0] = p.scaling[3 * a]; l[1] = p.scaling[3 * a + 1]; l[2] = p.scaling[3 * a + 2];
-        }
-        float dIn[2][5][4];
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < 5; ++nt)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) dIn[mt][nt][e] = 0.f;
-        __syncthreads();
 #pragma unroll 1
         for (int j = 0; j < 3; ++j) {
             const int ntl2 = j == 0 ? 2 : (j == 1 ? 4 : 9);
             const int kd_steps = out_pad16(j) / 16;
-            uint32_t mask[2] = {0u, 0u};
+            uint32_t mask = 0u;
             // ---- layer 1 and 2 on tensor cores (rows r0 .. r0 + 15 of the chunk)
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int r0 = warp * 32 + mt * 16;
+            {
                 float acc[4][4];
 #pragma unroll
                 for (int nt = 0; nt < 4; ++nt) {
@@ -815,7 +824,7 @@ decode_bwd_mma_kernel(DecParams p, const double *__restrict__ T, const int32_t *
                 for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        if (acc[nt][e] > 0.f) mask[mt] |= 1u << (4 * nt + e);
+                        if (acc[nt][e] > 0.f) mask |= 1u << (4 * nt + e);
                         const int q = 8 * nt + 2 * t4 + (e & 1), row = r0 + g + 8 * (e >> 1);
                         S.hT[q * kAS + row] = __float2bfloat16_rn(fmaxf(acc[nt][e], 0.f));
                     }
@@ -845,51 +854,71 @@ decode_bwd_mma_kernel(DecParams p, const double *__restrict__ T, const int32_t *
                 }
             }
             __syncthreads();
-            // ---- per anchor: head derivatives dO (0 where no Gaussian survived)
+            // ---- per anchor: head derivatives dO (0 where no Gaussian survived); the
+            // pair's two threads take alternate Gaussians, each reading its outputs
+            // before overwriting them with their derivatives
             {
-                float *orw = S.orow + tid * kOS;
-                const int w = j == 0 ? 1 : (j == 1 ? 3 : 7);
-                float dO[80];
-#pragma unroll
-                for (int n = 0; n < 80; ++n) dO[n] = 0.f;
-                for (int gm = 0; gm < K; ++gm) {
+                float *orw = S.orow + ta * kOS;
+                auto put = [&](int n, float v) {
+                    orw[n] = v;
+                    split_bf16(v, S.doT[0][n * kAS + ta], S.doT[1][n * kAS + ta]);
+                };
+                for (int gm = half; gm < K; gm += 2) {
                     const int i = idx[gm];
-                    if (i < 0) continue;
-                    const float *o = orw + w * gm;
                     if (j == 0) {
-                        const float al = tanhf(o[0]);
-                        dO[gm] = gin.opac[i] * (1.f - al * al);
+                        float v = 0.f;
+                        if (i >= 0) {
+                            const float al = tanhf(orw[gm]);
+                            v = gin.opac[i] * (1.f - al * al);
+                        }
+                        put(gm, v);
                     } else if (j == 1) {
+                        float o[3];
+#pragma unroll
+                        for (int r = 0; r < 3; ++r) o[r] = orw[3 * gm + r];
+#pragma unroll
                         for (int r = 0; r < 3; ++r) {
-                            const float c = sigmoidf_(o[r]);
-                            dO[3 * gm + r] = gin.colors[3 * i + r] * c * (1.f - c);
+                            float v = 0.f;
+                            if (i >= 0) {
+                                const float c = sigmoidf_(o[r]);
+                                v = gin.colors[3 * i + r] * c * (1.f - c);
+                            }
+                            put(3 * gm + r, v);
                         }
                     } else {
-                        for (int r = 0; r < 3; ++r) {
-                            const float sg = sigmoidf_(o[r]);
-                            const float gs = gin.scales[3 * i + r];
-                            dO[7 * gm + r] = gs * l[r] * sg * (1.f - sg);
-                            dl[r] += gs * sg;
+                        float o[7];
+#pragma unroll
+                        for (int r = 0; r < 7; ++r) o[r] = orw[7 * gm + r];
+                        float v[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                        if (i >= 0) {
+#pragma unroll
+                            for (int r = 0; r < 3; ++r) {
+                                const float sg = sigmoidf_(o[r]);
+                                const float gs = gin.scales[3 * i + r];
+                                v[r] = gs * l[r] * sg * (1.f - sg);
+                                dl[r] += gs * sg;
+                            }
+                            const float nrm = sqrtf(o[3] * o[3] + o[4] * o[4] + o[5] * o[5] + o[6] * o[6]);
+                            const float inn = 1.0f / nrm;
+                            const float4 gq = reinterpret_cast<const float4 *>(gin.quats)[i];
+                            const float qn[4] = {o[3] * inn, o[4] * inn, o[5] * inn, o[6] * inn};
+                            const float gqv[4] = {gq.x, gq.y, gq.z, gq.w};
+                            const float dot = qn[0] * gqv[0] + qn[1] * gqv[1] + qn[2] * gqv[2] + qn[3] * gqv[3];
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) v[3 + r] = (gqv[r] - qn[r] * dot) * inn;
                         }
-                        const float nrm = sqrtf(o[3] * o[3] + o[4] * o[4] + o[5] * o[5] + o[6] * o[6]);
-                        const float inn = 1.0f / nrm;
-                        const float4 gq = reinterpret_cast<const float4 *>(gin.quats)[i];
-                        const float qn[4] = {o[3] * inn, o[4] * inn, o[5] * inn, o[6] * inn};
-                        const float gqv[4] = {gq.x, gq.y, gq.z, gq.w};
-                        const float dot = qn[0] * gqv[0] + qn[1] * gqv[1] + qn[2] * gqv[2] + qn[3] * gqv[3];
-                        for (int r = 0; r < 4; ++r) dO[7 * gm + 3 + r] = (gqv[r] - qn[r] * dot) * inn;
+#pragma unroll
+                        for (int r = 0; r < 7; ++r) put(7 * gm + r, v[r]);
                     }
                 }
-                for (int n = 0; n < out_pad16(j); ++n) {
-                    orw[n] = dO[n];
-                    split_bf16(dO[n], S.doT[0][n * kAS + tid], S.doT[1][n * kAS + tid]);
+                if (half == 0) {  // the padding columns of the 16-wide output tiles
+                    const int w = j == 0 ? 1 : (j == 1 ? 3 : 7);
+                    for (int n = w * K; n < out_pad16(j); ++n) put(n, 0.f);
                 }
             }
             __syncthreads();
             // ---- dH = dO W2, dPre = dH [P > 0], dIn += dPre W1, dPre^T staged
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int r0 = warp * 32 + mt * 16;
+            {
                 float dh[4][4];
 #pragma unroll
                 for (int nt = 0; nt < 4; ++nt)
@@ -915,7 +944,7 @@ decode_bwd_mma_kernel(DecParams p, const double *__restrict__ T, const int32_t *
                 for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        if (!(mask[mt] >> (4 * nt + e) & 1u)) dh[nt][e] = 0.f;
+                        if (!(mask >> (4 * nt + e) & 1u)) dh[nt][e] = 0.f;
                         const int q = 8 * nt + 2 * t4 + (e & 1), row = r0 + g + 8 * (e >> 1);
                         split_bf16(dh[nt][e], S.dpT[0][q * kAS + row], S.dpT[1][q * kAS + row]);
                     }
@@ -932,8 +961,8 @@ decode_bwd_mma_kernel(DecParams p, const double *__restrict__ T, const int32_t *
                     for (int nt = 0; nt < 5; ++nt) {
                         const __nv_bfloat16 *B = S.wt.w1t + (j * 40 + 8 * nt + g) * kW1T;
                         const uint32_t b0 = ld_u32(B + c0), b1 = ld_u32(B + c0 + 8);
-                        mma_bf16_16816(dIn[mt][nt], ah[0], ah[1], ah[2], ah[3], b0, b1);
-                        mma_bf16_16816(dIn[mt][nt], alo[0], alo[1], alo[2], alo[3], b0, b1);
+                        mma_bf16_16816(dIn[nt], ah[0], ah[1], ah[2], ah[3], b0, b1);
+                        mma_bf16_16816(dIn[nt], alo[0], alo[1], alo[2], alo[3], b0, b1);
                     }
                 }
             }
@@ -942,7 +971,7 @@ decode_bwd_mma_kernel(DecParams p, const double *__restrict__ T, const int32_t *
             if (gout.params) {
                 const int mt2 = out_pad16(j) / 16;
                 const int n1 = 2 * 5, n2 = mt2 * 5;
-                for (int t = warp; t < n1 + n2; t += kMA / 32) {
+                for (int t = warp; t < n1 + n2; t += kMT / 32) {
                     const bool first = t < n1;
                     const int tt = first ? t : t - n1;
                     const int mt = tt / 5, nt = tt % 5;
@@ -972,22 +1001,20 @@ decode_bwd_mma_kernel(DecParams p, const double *__restrict__ T, const int32_t *
         }
         // ---- dIn rows, then per anchor: feature, offset and scaling gradients
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-            const int r0 = warp * 32 + mt * 16;
-#pragma unroll
-            for (int nt = 0; nt < 5; ++nt) {
-                const int c = 8 * nt + 2 * t4;
-                S.orow[(r0 + g) * kOS + c] = dIn[mt][nt][0];
-                S.orow[(r0 + g) * kOS + c + 1] = dIn[mt][nt][1];
-                S.orow[(r0 + g + 8) * kOS + c] = dIn[mt][nt][2];
-                S.orow[(r0 + g + 8) * kOS + c + 1] = dIn[mt][nt][3];
-            }
+        for (int nt = 0; nt < 5; ++nt) {
+            const int c = 8 * nt + 2 * t4;
+            S.orow[(r0 + g) * kOS + c] = dIn[nt][0];
+            S.orow[(r0 + g) * kOS + c + 1] = dIn[nt][1];
+            S.orow[(r0 + g + 8) * kOS + c] = dIn[nt][2];
+            S.orow[(r0 + g + 8) * kOS + c + 1] = dIn[nt][3];
         }
         __syncthreads();
         if (live && any) {
+            // the pair splits the features in halves and the Gaussians by parity
             if (gout.features)
-                for (int k = 0; k < kFeat; ++k) gout.features[kFeat * a + k] += S.orow[tid * kOS + k];
-            for (int gm = 0; gm < K; ++gm) {
+                for (int k = half * (kFeat / 2); k < (half + 1) * (kFeat / 2); ++k)
+                    gout.features[kFeat * a + k] += S.orow[ta * kOS + k];
+            for (int gm = half; gm < K; gm += 2) {
                 const int i = idx[gm];
                 if (i < 0) continue;
                 const float *O = p.offsets + (a * K + gm) * 3;
@@ -997,14 +1024,20 @@ decode_bwd_mma_kernel(DecParams p, const double *__restrict__ T, const int32_t *
                     dl[r] += gmn[r] * O[r];
                 }
             }
-            if (gout.scaling)
-                for (int r = 0; r < 3; ++r) gout.scaling[3 * a + r] += dl[r];
         }
-        __syncthreads();  // orow and the staging rows are rewritten by the next chunk
+        if (half == 1) {
+            s_dl[ta][0] = dl[0];
+            s_dl[ta][1] = dl[1];
+            s_dl[ta][2] = dl[2];
+        }
+        __syncthreads();
+        if (half == 0 && live && any && gout.scaling)
+            for (int r = 0; r < 3; ++r) gout.scaling[3 * a + r] += dl[r] + s_dl[ta][r];
+        __syncthreads();  // orow, the staging rows and s_dl are rewritten by the next chunk
     }
     // ---- the block's weight gradients, once
     if (gout.params) {
-        for (int i = tid; i < 3 * 32 * kGW; i += kMA) {
+        for (int i = tid; i < 3 * 32 * kGW; i += kMT) {
             const int j = i / (32 * kGW), q = (i / kGW) % 32, c = i % kGW;
             const MlpOff m = mlp_off(K, j);
             const float v = S.gw1[i];
@@ -1012,7 +1045,7 @@ decode_bwd_mma_kernel(DecParams p, const double *__restrict__ T, const int32_t *
             if (c < kIn) atomicAdd(gout.params + m.w1 + q * kIn + c, v);
             else if (c == kIn) atomicAdd(gout.params + m.b1 + q, v);
         }
-        for (int i = tid; i < 128 * kGW; i += kMA) {
+        for (int i = tid; i < 128 * kGW; i += kMT) {
             const int r = i / kGW, c = i % kGW;
             const int j = r < kColCol ? 0 : (r < kColCov ? 1 : 2);
             const MlpOff m = mlp_off(K, j);
@@ -1141,7 +1174,7 @@ vpgs_status vpgs_decode_anchors_bwd(void *ws, size_t ws_bytes, const vpgs_anchor
         const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nch, sms));
         DecBwdWts *wts = reinterpret_cast<DecBwdWts *>(b + L.off_wts);
         VPGS_LAUNCH("decode_bwd_weights", s, launch_k(decode_bwd_weights_kernel, 8, 256, 0, s, p, wts));
-        VPGS_LAUNCH("decode_bwd", s, launch_k(decode_bwd_mma_kernel, grid, kMA, msm, s, p, T_cw, inv,
+        VPGS_LAUNCH("decode_bwd", s, launch_k(decode_bwd_mma_kernel, grid, kMT, msm, s, p, T_cw, inv,
                                               (const DecBwdWts *)wts, gin, gout));
         return cudaGetLastError() == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
     }
