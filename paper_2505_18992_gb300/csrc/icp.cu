@@ -562,8 +562,8 @@ icp_step_kernel(MapView map, SrcView sv, int64_t n_cap, const uint32_t *n_dev, d
                 }
             }
         };
-        // round 1: the home voxel (every live voxel when it is empty);
-        // round 2: the other live voxels not farther than the best so far.
+        // first sweep: the home voxel (every live voxel when it is empty);
+        // second sweep: the other live voxels not farther than the best so far.
         // A voxel left out of both lies farther than the final best.
         const uint32_t live = __ballot_sync(0xffffffffu, cnt > 0);
         const uint32_t first = (live >> kHome) & 1u ? (1u << kHome) : live;
