@@ -168,6 +168,7 @@ struct DecFwdSmem {
         } h;
     } u;
     uint16_t slot[kDecAnchors * kMaxK];  // per output slot of the block: local anchor << 4 | m
+    float mean[kDecAnchors * 3 * kMaxK]; // per anchor: the means of its Gaussians
 };
 
 __global__ void __launch_bounds__(256) decode_weights_kernel(DecParams p, DecWts *wts) {
@@ -357,8 +358,39 @@ decode_fwd_kernel(DecParams p, const double *__restrict__ T, DecOut o, const Dec
         for (int m = 0; m < K; ++m)
             if (mask >> m & 1u) S.slot[at++] = (uint16_t)((tid << 4) | m);
     }
-    // decoupled look-back over earlier blocks, one warp: 32 predecessors per step
-    if (warp == 0) {
+    __syncthreads();
+    // decoupled look-back over earlier blocks, one warp: 32 predecessors per step;
+    // meanwhile the other warps turn the head outputs of every slot into the
+    // Gaussian's values in place (activations, normalised quaternion, mean), so
+    // that once the block's offset is known the outputs are plain copies
+    if (warp != 0) {
+        for (uint32_t sl = tid - 32; sl < total; sl += kDecThreads - 32) {
+            const uint32_t e = S.slot[sl];
+            const int al = (int)(e >> 4), m = (int)(e & 15u);
+            const int64_t aa = bid * kDecAnchors + al;
+            float *orw = S.out + al * kOutStride;
+            const float l0 = p.scaling[3 * aa], l1 = p.scaling[3 * aa + 1], l2 = p.scaling[3 * aa + 2];
+            const float *O = p.offsets + (aa * K + m) * 3;
+            float *mw = S.mean + al * 3 * kMaxK + 3 * m;
+            mw[0] = fmaf(O[0], l0, p.anchors[3 * aa]);
+            mw[1] = fmaf(O[1], l1, p.anchors[3 * aa + 1]);
+            mw[2] = fmaf(O[2], l2, p.anchors[3 * aa + 2]);
+            orw[kColOpa + m] = tanhf(orw[kColOpa + m]);
+            float *cc = orw + kColCol + 3 * m;
+            cc[0] = sigmoidf_(cc[0]);
+            cc[1] = sigmoidf_(cc[1]);
+            cc[2] = sigmoidf_(cc[2]);
+            float *cv = orw + kColCov + 7 * m;
+            cv[0] = sigmoidf_(cv[0]) * l0;
+            cv[1] = sigmoidf_(cv[1]) * l1;
+            cv[2] = sigmoidf_(cv[2]) * l2;
+            const float inv = 1.0f / sqrtf(cv[3] * cv[3] + cv[4] * cv[4] + cv[5] * cv[5] + cv[6] * cv[6]);
+            cv[3] *= inv;
+            cv[4] *= inv;
+            cv[5] *= inv;
+            cv[6] *= inv;
+        }
+    } else {
         unsigned long long excl = 0;
         if (bid == 0) {
             if (lane == 0) st_volatile_u64(look, kFlagPre | total);
@@ -410,22 +442,20 @@ decode_fwd_kernel(DecParams p, const double *__restrict__ T, DecOut o, const Dec
         const int al = (int)(e >> 4), m = (int)(e & 15u);
         const int64_t aa = bid * kDecAnchors + al;
         const float *orw = S.out + al * kOutStride;
-        const float l0 = p.scaling[3 * aa], l1 = p.scaling[3 * aa + 1], l2 = p.scaling[3 * aa + 2];
-        const float *O = p.offsets + (aa * K + m) * 3;
-        o.means[3 * pos] = fmaf(O[0], l0, p.anchors[3 * aa]);
-        o.means[3 * pos + 1] = fmaf(O[1], l1, p.anchors[3 * aa + 1]);
-        o.means[3 * pos + 2] = fmaf(O[2], l2, p.anchors[3 * aa + 2]);
-        o.opac[pos] = tanhf(orw[kColOpa + m]);
+        const float *mw = S.mean + al * 3 * kMaxK + 3 * m;
+        o.means[3 * pos] = mw[0];
+        o.means[3 * pos + 1] = mw[1];
+        o.means[3 * pos + 2] = mw[2];
+        o.opac[pos] = orw[kColOpa + m];
         const float *cc = orw + kColCol + 3 * m;
-        o.colors[3 * pos] = sigmoidf_(cc[0]);
-        o.colors[3 * pos + 1] = sigmoidf_(cc[1]);
-        o.colors[3 * pos + 2] = sigmoidf_(cc[2]);
+        o.colors[3 * pos] = cc[0];
+        o.colors[3 * pos + 1] = cc[1];
+        o.colors[3 * pos + 2] = cc[2];
         const float *cv = orw + kColCov + 7 * m;
-        o.scales[3 * pos] = sigmoidf_(cv[0]) * l0;
-        o.scales[3 * pos + 1] = sigmoidf_(cv[1]) * l1;
-        o.scales[3 * pos + 2] = sigmoidf_(cv[2]) * l2;
-        const float inv = 1.0f / sqrtf(cv[3] * cv[3] + cv[4] * cv[4] + cv[5] * cv[5] + cv[6] * cv[6]);
-        reinterpret_cast<float4 *>(o.quats)[pos] = make_float4(cv[3] * inv, cv[4] * inv, cv[5] * inv, cv[6] * inv);
+        o.scales[3 * pos] = cv[0];
+        o.scales[3 * pos + 1] = cv[1];
+        o.scales[3 * pos + 2] = cv[2];
+        reinterpret_cast<float4 *>(o.quats)[pos] = make_float4(cv[3], cv[4], cv[5], cv[6]);
         o.src_index[pos] = (int32_t)(aa * K + m);
     }
 }
