@@ -17,6 +17,8 @@
 // block's anchors in shared memory (one atomic per parameter per block).
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "internal.h"
 #include "prims.cuh"
 #include "profiler.h"
@@ -226,8 +228,10 @@ VPGS_D void mlp_fp32(const float *w, int K, int j, const float (&in)[kIn], float
 // Blocks of kDecThreads threads decode kDecAnchors anchors: thread t < 64 owns
 // anchor t for its inputs and its valid-Gaussian count; in the FP32 form
 // threads t and t + 64 split its three MLPs (0 and 1 / 2: nearly equal
-// work); in the BF16 form each warp runs one 16-anchor tile on tensor cores.
-// After the block's compaction offset is known, the outputs are made one
+// work); in the BF16 form each warp runs one 16-anchor tile on tensor cores,
+// the opacity head before the others so that the block's count is published
+// early.  The head outputs become the Gaussians' values in shared memory while
+// the block's compaction offset is resolved; then the outputs are copied one
 // Gaussian per thread in output order, so consecutive threads write
 // consecutive entries.
 __global__ void __launch_bounds__(kDecThreads)
@@ -262,25 +266,16 @@ decode_fwd_kernel(DecParams p, const double *__restrict__ T, DecOut o, const Dec
     bool keep = false;
     if (live && (!p.bf16 || tid < kDecAnchors)) keep = anchor_inputs(p, s_cam, a, in);
     float *orow = S.out + la * kOutStride;
-    if (!p.bf16) {
-        if (keep) {
-            if (tid < kDecAnchors) {
-                mlp_fp32(S.u.w, K, 0, in, orow);
-                mlp_fp32(S.u.w, K, 1, in, orow);
-            } else {
-                mlp_fp32(S.u.w, K, 2, in, orow);
-            }
-        }
-    } else {
+    const int g = lane >> 2, t4 = lane & 3;
+    const int r0 = warp * 16;
+    float acc[12][4];  // BF16 form: layer 1 of the three MLPs for rows r0 .. r0 + 15
+    if (p.bf16) {
         // stage the (already BF16-rounded) inputs, then tensor-core tiles
         if (tid < kDecAnchors) {
             __nv_bfloat16 *irow = S.u.h.in + tid * kInPad;
             for (int k = 0; k < kInPad; ++k) irow[k] = __float2bfloat16_rn(live && k < kIn ? in[k] : 0.f);
         }
         __syncthreads();
-        const int g = lane >> 2, t4 = lane & 3;
-        const int r0 = warp * 16;
-        float acc[12][4];
 #pragma unroll
         for (int nt = 0; nt < 12; ++nt) {
             const float b0 = S.u.h.wt.b1[8 * nt + 2 * t4], b1v = S.u.h.wt.b1[8 * nt + 2 * t4 + 1];
@@ -301,36 +296,53 @@ decode_fwd_kernel(DecParams p, const double *__restrict__ T, DecOut o, const Dec
                                *reinterpret_cast<const uint32_t *>(Brow + c0 + 8));
             }
         }
-        // layer 2 per MLP: hidden (ReLU, BF16) comes straight from the accumulators
+    }
+    // head of MLP j into the anchors' rows (BF16 form: layer 2 on tensor cores,
+    // the hidden layer (ReLU, BF16) straight from the accumulators)
+    auto head = [&](auto J) {
+        constexpr int j = decltype(J)::value;
+        constexpr int ntiles = j == 0 ? 2 : (j == 1 ? 4 : 9);
+        constexpr int base = j == 0 ? kColOpa : (j == 1 ? kColCol : kColCov);
+        uint32_t ha[2][4];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const int ntiles = j == 0 ? 2 : (j == 1 ? 4 : 9);
-            const int base = j == 0 ? kColOpa : (j == 1 ? kColCol : kColCov);
-            uint32_t ha[2][4];
+        for (int kk = 0; kk < 2; ++kk) {
+            const float *x0 = acc[4 * j + 2 * kk], *x1 = acc[4 * j + 2 * kk + 1];
+            ha[kk][0] = pack_bf16(fmaxf(x0[0], 0.f), fmaxf(x0[1], 0.f));
+            ha[kk][1] = pack_bf16(fmaxf(x0[2], 0.f), fmaxf(x0[3], 0.f));
+            ha[kk][2] = pack_bf16(fmaxf(x1[0], 0.f), fmaxf(x1[1], 0.f));
+            ha[kk][3] = pack_bf16(fmaxf(x1[2], 0.f), fmaxf(x1[3], 0.f));
+        }
+        for (int nt = 0; nt < ntiles; ++nt) {
+            const int col = base + 8 * nt + 2 * t4;
+            float d[4] = {S.u.h.wt.b2[col], S.u.h.wt.b2[col + 1], S.u.h.wt.b2[col], S.u.h.wt.b2[col + 1]};
+            const __nv_bfloat16 *Brow = S.u.h.wt.w2 + (base + 8 * nt + g) * kW2Pad;
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk) {
-                const float *x0 = acc[4 * j + 2 * kk], *x1 = acc[4 * j + 2 * kk + 1];
-                ha[kk][0] = pack_bf16(fmaxf(x0[0], 0.f), fmaxf(x0[1], 0.f));
-                ha[kk][1] = pack_bf16(fmaxf(x0[2], 0.f), fmaxf(x0[3], 0.f));
-                ha[kk][2] = pack_bf16(fmaxf(x1[0], 0.f), fmaxf(x1[1], 0.f));
-                ha[kk][3] = pack_bf16(fmaxf(x1[2], 0.f), fmaxf(x1[3], 0.f));
+                const int c0 = 16 * kk + 2 * t4;
+                mma_bf16_16816(d, ha[kk][0], ha[kk][1], ha[kk][2], ha[kk][3],
+                               *reinterpret_cast<const uint32_t *>(Brow + c0),
+                               *reinterpret_cast<const uint32_t *>(Brow + c0 + 8));
             }
-            for (int nt = 0; nt < ntiles; ++nt) {
-                const int col = base + 8 * nt + 2 * t4;
-                float d[4] = {S.u.h.wt.b2[col], S.u.h.wt.b2[col + 1], S.u.h.wt.b2[col], S.u.h.wt.b2[col + 1]};
-                const __nv_bfloat16 *Brow = S.u.h.wt.w2 + (base + 8 * nt + g) * kW2Pad;
-#pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {
-                    const int c0 = 16 * kk + 2 * t4;
-                    mma_bf16_16816(d, ha[kk][0], ha[kk][1], ha[kk][2], ha[kk][3],
-                                   *reinterpret_cast<const uint32_t *>(Brow + c0),
-                                   *reinterpret_cast<const uint32_t *>(Brow + c0 + 8));
-                }
-                float *o0 = S.out + (r0 + g) * kOutStride + col;
-                float *o1 = S.out + (r0 + g + 8) * kOutStride + col;
-                o0[0] = d[0]; o0[1] = d[1]; o1[0] = d[2]; o1[1] = d[3];
+            float *o0 = S.out + (r0 + g) * kOutStride + col;
+            float *o1 = S.out + (r0 + g + 8) * kOutStride + col;
+            o0[0] = d[0]; o0[1] = d[1]; o1[0] = d[2]; o1[1] = d[3];
+        }
+    };
+    // BF16 form: the opacity head first (its outputs decide which Gaussians
+    // survive), so the block publishes its count before the colour and covariance
+    // heads.  FP32 form: threads t and t + 64 split the three MLPs of anchor t
+    // (0 and 1 / 2: nearly equal work), all before the count
+    if (!p.bf16) {
+        if (keep) {
+            if (tid < kDecAnchors) {
+                mlp_fp32(S.u.w, K, 0, in, orow);
+                mlp_fp32(S.u.w, K, 1, in, orow);
+            } else {
+                mlp_fp32(S.u.w, K, 2, in, orow);
             }
         }
+    } else {
+        head(std::integral_constant<int, 0>{});
     }
     __syncthreads();
     // valid Gaussians of each anchor (threads < kDecAnchors), their block-local starts
@@ -352,6 +364,13 @@ decode_fwd_kernel(DecParams p, const double *__restrict__ T, DecOut o, const Dec
         if (w < warp) wbase += s_wsum[w];
         total += s_wsum[w];
     }
+    // the block's count for its successors' look-back (its own prefix when first)
+    if (tid == 0) st_volatile_u64(look + bid, (bid == 0 ? kFlagPre : kFlagAgg) | total);
+    // the colour and covariance heads (BF16 form) while predecessors publish theirs
+    if (p.bf16) {
+        head(std::integral_constant<int, 1>{});
+        head(std::integral_constant<int, 2>{});
+    }
     // the (anchor, m) of each of the block's output slots, in (anchor, m) order
     {
         uint32_t at = wbase + (x - cnt);
@@ -359,12 +378,13 @@ decode_fwd_kernel(DecParams p, const double *__restrict__ T, DecOut o, const Dec
             if (mask >> m & 1u) S.slot[at++] = (uint16_t)((tid << 4) | m);
     }
     __syncthreads();
-    // decoupled look-back over earlier blocks, one warp: 32 predecessors per step;
-    // meanwhile the other warps turn the head outputs of every slot into the
-    // Gaussian's values in place (activations, normalised quaternion, mean), so
-    // that once the block's offset is known the outputs are plain copies
-    if (warp != 0) {
-        for (uint32_t sl = tid - 32; sl < total; sl += kDecThreads - 32) {
+    // every slot's head outputs turned into the Gaussian's values in place
+    // (activations, normalised quaternion, mean), so that once the block's offset
+    // is known the outputs are plain copies; then the decoupled look-back over
+    // earlier blocks (one warp, 32 predecessors per step), which by now mostly
+    // finds their counts published
+    {
+        for (uint32_t sl = tid; sl < total; sl += kDecThreads) {
             const uint32_t e = S.slot[sl];
             const int al = (int)(e >> 4), m = (int)(e & 15u);
             const int64_t aa = bid * kDecAnchors + al;
@@ -390,12 +410,10 @@ decode_fwd_kernel(DecParams p, const double *__restrict__ T, DecOut o, const Dec
             cv[5] *= inv;
             cv[6] *= inv;
         }
-    } else {
+    }
+    if (warp == 0) {
         unsigned long long excl = 0;
-        if (bid == 0) {
-            if (lane == 0) st_volatile_u64(look, kFlagPre | total);
-        } else {
-            if (lane == 0) st_volatile_u64(look + bid, kFlagAgg | total);
+        if (bid != 0) {
             int64_t j0 = bid - 1;
             for (;;) {
                 const int64_t j = j0 - lane;
