@@ -53,6 +53,11 @@ constexpr int kPix = VPGS_PIX;
 #endif
 constexpr int kDirect = VPGS_BWD_DIRECT;  // at most this many active lanes: per-lane atomics, no reduction
 constexpr int kMaxThreads = 512;
+// list entries whose alphas the forward evaluates before blending them
+#ifndef VPGS_FWD_WALK
+#define VPGS_FWD_WALK 2
+#endif
+constexpr int kWalk = VPGS_FWD_WALK;
 
 // Centre and half height of the band of tile-local pixel-centre rows held by
 // this thread's warp.
@@ -239,7 +244,55 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
             };
             // the list walk; a batch with a near-degenerate record takes the walk that
             // chooses the precision form per entry (a warp-uniform branch), the others
-            // the plain one
+            // the plain one, kWalk entries at a time: their alphas (which do not depend
+            // on the transmittance) are evaluated before the blends, so the pixels'
+            // blend chains overlap with independent work
+            auto walk_plain = [&]() {
+                for (int i = 0; i < nl; i += kWalk) {
+                    float al[kWalk][kPix];
+                    int kk[kWalk];
+#pragma unroll
+                    for (int u = 0; u < kWalk; ++u) kk[u] = wl[min(i + u, nl - 1)];
+#pragma unroll
+                    for (int u = 0; u < kWalk; ++u) {
+                        const float4 a = s0[kk[u]], b = s1[kk[u]];
+                        const float2 t0 = first_row(pxl, pyl[0], a, b);
+#pragma unroll
+                        for (int q = 0; q < kPix; ++q)
+                            al[u][q] = eval_staged<false>(q, t0.x, t0.y, pxl, pyl[q], a, b, a, o.alpha_max).alpha;
+                    }
+                    bool fin = false;
+#pragma unroll
+                    for (int u = 0; u < kWalk; ++u) {
+                        if (fin || i + u >= nl) break;
+                        fin = true;
+#pragma unroll
+                        for (int q = 0; q < kPix; ++q) {
+                            if (!done[q] && al[u][q] >= o.alpha_min) {
+                                const float nt = T[q] * (1.f - al[u][q]);
+                                if (nt < o.t_min) {
+                                    done[q] = true;
+                                } else {
+                                    const float w = al[u][q] * T[q];
+                                    const float4 col = s2[kk[u]];
+                                    C0[q] = fmaf(w, col.x, C0[q]);
+                                    C1[q] = fmaf(w, col.y, C1[q]);
+                                    C2[q] = fmaf(w, col.z, C2[q]);
+                                    D[q] = fmaf(w, col.w, D[q]);
+                                    T[q] = nt;
+                                    ++cnt[q];
+                                    last[q] = b0 + kk[u] - start + 1;
+                                }
+                            }
+                            fin = fin && done[q];
+                        }
+                    }
+                    if (fin) {
+                        all_done = true;
+                        break;
+                    }
+                }
+            };
             auto walk = [&](auto maybe_fine) {
                 for (int i = 0; i < nl; ++i) {
                     const int k = wl[i];
@@ -257,7 +310,7 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
             };
             if (!all_done) {
                 if (any_fine) walk(std::true_type{});
-                else walk(std::false_type{});
+                else walk_plain();
             }
         }
         const int64_t HW = (int64_t)cam.H * cam.W;
