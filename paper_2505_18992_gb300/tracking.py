@@ -7,7 +7,9 @@ then sums only the geometric 2D gradients), and step the pose on the device
 (vpgs_pose_step, Adam).  The paper gives
 neither the iteration count nor the step rule; 50 Adam iterations is the
 tracking workload used here.  All buffers are preallocated, so `iters`
-iterations can be captured once and replayed with a single host call.
+iterations can be captured once and replayed with a single host call.  The
+backward of an iteration takes the forward's tile lists (same pose, same
+workspace) unless reuse_binning=False.
 """
 from __future__ import annotations
 
@@ -21,7 +23,7 @@ from .render import Renderer, current_stream_handle
 
 class Tracker:
     def __init__(self, renderer: Renderer, gaussians, T_cw: torch.Tensor, target_rgb: torch.Tensor,
-                 target_depth: torch.Tensor, lr=(1e-3, 1e-3), lambda_d: float = 1.0):
+                 target_depth: torch.Tensor, lr=(1e-3, 1e-3), lambda_d: float = 1.0, reuse_binning: bool = True):
         self.r = renderer
         self.g = [t.contiguous() for t in gaussians]
         self.T = T_cw  # [V,4,4] float64, updated in place
@@ -29,7 +31,11 @@ class Tracker:
         self.target_depth = None if target_depth is None else target_depth.contiguous()
         self.lr = (ctypes.c_double * 2)(*lr)
         self.lambda_d = lambda_d
-        self.reuse = renderer.reuse_binning  # recompute the tile lists in the backward unless asked
+        # within an iteration the forward and the backward see one pose and run back to
+        # back on this renderer's workspace, so by default the backward takes the
+        # forward's projection and tile lists (exactly what it would recompute);
+        # reuse_binning=False recomputes them
+        self.reuse = bool(reuse_binning)
         V = renderer.V
         dev = T_cw.device
         self.out = renderer.alloc_images()

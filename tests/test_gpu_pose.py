@@ -65,3 +65,28 @@ def test_tracking_graph_converges_and_matches_eager():
     # rounding along: equal to 10 um against the 3 cm start error
     assert float((T - T_eager).abs().max()) < 1e-5
     assert r.stats().status == 0
+
+
+def test_tracking_with_and_without_binning_reuse_follow_one_trajectory():
+    """The tracker's backward takes the forward's tile lists by default (one pose
+    per iteration); recomputing them must give the same steps up to the order
+    in which float atomics sum."""
+    sc = scenes.tiny_planes(n=8000, width=160, height=120, f=150.0)
+    g, T_true = scene_tensors(sc)
+    ref = Renderer(intrinsics(sc)).forward(*g, T_true)
+    T0 = dev(scenes.perturb_pose(sc.camera.T_cw[0], np.random.default_rng(11), 0.03, 1.5)[None],
+             torch.float64)
+    poses = []
+    for reuse in (True, False):
+        r = Renderer(intrinsics(sc))
+        T = T0.clone()
+        tr = Tracker(r, g, T, ref["rgb"].clone(), ref["depth"].clone(), lr=(3e-3, 3e-3), reuse_binning=reuse)
+        tr.prepare()
+        tr.reset(T0)
+        tr.run_eager(20)
+        torch.cuda.synchronize()
+        assert r.stats().status == 0
+        poses.append(T.clone())
+    assert float((poses[0] - poses[1]).abs().max()) < 1e-5
+    err0 = float(torch.linalg.norm(T0[0, :3, 3] - T_true[0, :3, 3]))
+    assert float(torch.linalg.norm(poses[0][0, :3, 3] - T_true[0, :3, 3])) < 0.5 * err0
