@@ -804,15 +804,23 @@ decode_bwd_mma_kernel(DecParams p, const double *__restrict__ T, const int32_t *
     for (int i = tid; i < 128 * kGW; i += kMT) S.gw2[i] = 0.f;
     __syncthreads();
 
-    const int64_t nchunks = (p.A + kMA - 1) / kMA;
+    // work: full chunks of kMA anchors in whole rounds over the grid, then the
+    // anchors left over split evenly into one short chunk per block (rows past
+    // its length are masked), so that the last round leaves no block idle
+    const int64_t full = (p.A / kMA) / gridDim.x * gridDim.x;
+    const int64_t rest = p.A - full * kMA;
+    const int64_t unit = rest > 0 ? min((int64_t)kMA, (rest + gridDim.x - 1) / gridDim.x) : 1;
+    const int64_t n_work = full + (rest + unit - 1) / unit;
     // the anchor row this thread serves in the per-anchor phases (two threads per
     // anchor), and the warp's 16 chunk rows in the tensor-core phases
     const int ta = tid & (kMA - 1), half = tid / kMA;
     const int r0 = warp * 16;
-    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    for (int64_t wk = blockIdx.x; wk < n_work; wk += gridDim.x) {
+        const int64_t base = wk < full ? wk * kMA : full * kMA + (wk - full) * unit;
+        const int64_t rows = wk < full ? (int64_t)kMA : min(unit, p.A - base);
         // ---- per anchor: inputs (first thread of the pair), surviving Gaussians
-        const int64_t a = ch * kMA + ta;
-        const bool live = a < p.A;
+        const int64_t a = base + ta;
+        const bool live = ta < rows && a < p.A;
         if (half == 0) {
             float in[kIn];
             bool kp = false;
