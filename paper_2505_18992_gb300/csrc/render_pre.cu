@@ -427,11 +427,14 @@ VPGS_D void project_write(int64_t ic, int v, float mx, float my, float mz, float
 
 // Pre-cull and exact projection in one pass, for calls of several views.  Each
 // block walks chunks of kPreThreads consecutive Gaussians, one per thread: it
-// reads their parameters once (coalesced), pre-culls each (view, Gaussian)
-// pair view by view, and appends the survivors with their parameters to a
-// queue in shared memory; whenever the queue holds kPreThreads pairs, every
-// thread projects one of them.  The exact projection thus runs on full warps
-// without gathering the survivors' parameters from memory again.  Measured:
+// reads their parameters once (coalesced) and pre-culls its Gaussian against
+// each view of a round of up to 8; one block scan numbers the round's
+// survivors (thread order, then view), and they are staged with their
+// parameters in shared memory kPreThreads at a time, every thread projecting
+// one.  The exact projection thus runs on full warps without gathering the
+// survivors' parameters from memory again, with a few barriers per round
+// (the projection of a pair depends on nothing but the pair, so its order is
+// free).  Measured:
 // 8 keyframes x 2M Gaussians 803 us against 172 + 753 us for the two-kernel
 // form; one 1200x680 view of 1M Gaussians 53.8 us against 20.8 + 30.3 us,
 // where the two kernels' overlap under programmatic dependent launch wins.
@@ -439,7 +442,6 @@ VPGS_D void project_write(int64_t ic, int v, float mx, float my, float mz, float
 #ifndef VPGS_CULL_PROJECT
 #define VPGS_CULL_PROJECT 2
 #endif
-constexpr int kQueueCap = 2 * kPreThreads;  // at most kPreThreads - 1 left over + kPreThreads pushed
 
 struct QItem {
     float4 a;  // mx, my, mz, sx
@@ -452,32 +454,14 @@ __global__ void __launch_bounds__(kPreThreads, 3)
 cull_project_kernel(GaussIn g, int V, CamParams cam, OptParams o, RenderWs ws, bool zero_g2d) {
     grid_dep_enter();
     __shared__ uint32_t s_h[4][kRadix];
-    __shared__ QItem s_q[kQueueCap];
+    __shared__ QItem s_q[kPreThreads];
     __shared__ float s_pose[8 * 24];  // the round's poses (double-float pairs)
     __shared__ int s_wcnt[kPreThreads / 32];
-    __shared__ int s_qn;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < 4 * kRadix; i += kPreThreads) (&s_h[0][0])[i] = 0u;
-    if (tid == 0) s_qn = 0;
     __syncthreads();
     int64_t nl = g.N;
     if (g.n_dev) nl = min(nl, (int64_t)*g.n_dev);
-    // projects the queue's first m pairs (m <= kPreThreads), then moves the rest to the front
-    auto drain = [&](int m) {
-        if (tid < m) {
-            const QItem it = s_q[tid];
-            const uint32_t v = __float_as_uint(it.c.w);
-            const int64_t ic = (int64_t)v * g.N + __float_as_uint(it.c.z);
-            project_write(ic, (int)v, it.a.x, it.a.y, it.a.z, it.a.w, it.b.x, it.b.y, it.q, it.b.z, it.b.w, it.c.x,
-                          it.c.y, cam, o, ws, zero_g2d, s_h);
-        }
-        const int n = s_qn;
-        __syncthreads();
-        if (m + tid < n) s_q[tid] = s_q[m + tid];  // the rest (< kPreThreads) to the front
-        __syncthreads();
-        if (tid == 0) s_qn = n - m;
-        __syncthreads();
-    };
     const int64_t n_chunks = (g.N + kPreThreads - 1) / kPreThreads;
     for (int64_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {  // block-uniform
         const int64_t gi = ch * kPreThreads + tid;
@@ -504,6 +488,8 @@ cull_project_kernel(GaussIn g, int V, CamParams cam, OptParams o, RenderWs ws, b
             const int nv = min(8, V - v0);
             for (int i = tid; i < nv * 24; i += kPreThreads) s_pose[i] = ws.posedf[24 * v0 + i];
             __syncthreads();
+            // this thread's Gaussian against the round's views
+            uint32_t keep = 0u;
             for (int dv = 0; dv < nv; ++dv) {
                 bool k = false;
                 if (ok) {
@@ -515,34 +501,53 @@ cull_project_kernel(GaussIn g, int V, CamParams cam, OptParams o, RenderWs ws, b
                     for (int r = 0; r < 3; ++r) P.t[r] = df{pd[18 + 2 * r], pd[19 + 2 * r]};
                     k = maybe_in_view(P, mx, my, mz, smax, kq, cam, o);
                 }
-                if (gi < g.N && !k) ws.tcount[(int64_t)(v0 + dv) * g.N + gi] = 0u;
-                // append the survivors of this view to the queue, in thread order
-                const uint32_t m = __ballot_sync(0xffffffffu, k);
-                if (lane == 0) s_wcnt[warp] = __popc(m);
-                __syncthreads();
-                int pos = s_qn, tot = 0;
-#pragma unroll
-                for (int w = 0; w < kPreThreads / 32; ++w) {
-                    pos += w < warp ? s_wcnt[w] : 0;
-                    tot += s_wcnt[w];
-                }
-                if (k) {
-                    QItem it;
-                    it.a = make_float4(mx, my, mz, sx);
-                    it.b = make_float4(sy, sz, op, cr);
-                    it.q = q;
-                    it.c = make_float4(cg, cb, __uint_as_float((uint32_t)gi), __uint_as_float((uint32_t)(v0 + dv)));
-                    s_q[pos + __popc(m & ((1u << lane) - 1u))] = it;
-                }
-                __syncthreads();
-                if (tid == 0) s_qn += tot;
-                __syncthreads();
-                if (s_qn >= kPreThreads) drain(kPreThreads);  // block-uniform
+                if (k) keep |= 1u << dv;
+                else if (gi < g.N) ws.tcount[(int64_t)(v0 + dv) * g.N + gi] = 0u;
             }
-            __syncthreads();  // s_pose is reloaded by the next round
+            // the block's survivors numbered by one scan (thread order, then view)
+            const int c = __popc(keep);
+            int x = c;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, off);
+                if (lane >= off) x += y;
+            }
+            if (lane == 31) s_wcnt[warp] = x;
+            __syncthreads();
+            int first = x - c, total = 0;
+#pragma unroll
+            for (int w = 0; w < kPreThreads / 32; ++w) {
+                first += w < warp ? s_wcnt[w] : 0;
+                total += s_wcnt[w];
+            }
+            // projected kPreThreads at a time on full warps: each owner stages its
+            // survivors that fall in the batch, then thread t projects item t
+            for (int b0 = 0; b0 < total; b0 += kPreThreads) {  // block-uniform
+                int p = first;
+                for (int dv = 0; dv < nv; ++dv) {
+                    if (!(keep >> dv & 1u)) continue;
+                    if (p >= b0 && p < b0 + kPreThreads) {
+                        QItem it;
+                        it.a = make_float4(mx, my, mz, sx);
+                        it.b = make_float4(sy, sz, op, cr);
+                        it.q = q;
+                        it.c = make_float4(cg, cb, __uint_as_float((uint32_t)gi), __uint_as_float((uint32_t)(v0 + dv)));
+                        s_q[p - b0] = it;
+                    }
+                    ++p;
+                }
+                __syncthreads();
+                if (tid < min(kPreThreads, total - b0)) {
+                    const QItem it = s_q[tid];
+                    const uint32_t v = __float_as_uint(it.c.w);
+                    const int64_t ic = (int64_t)v * g.N + __float_as_uint(it.c.z);
+                    project_write(ic, (int)v, it.a.x, it.a.y, it.a.z, it.a.w, it.b.x, it.b.y, it.q, it.b.z, it.b.w,
+                                  it.c.x, it.c.y, cam, o, ws, zero_g2d, s_h);
+                }
+                __syncthreads();  // the staging slots are rewritten by the next batch
+            }
         }
     }
-    if (s_qn > 0) drain(s_qn);
     __syncthreads();
     flush_digits(s_h, 4, ws.sort_hist[0]);
 }
