@@ -176,6 +176,28 @@ def test_multiview_pose_gradients_and_ragged_image():
     assert_pose_close(dpose, ref["d_pose"])
 
 
+def test_more_views_than_one_cull_round():
+    """Ten views in one call: the pre-cull and the merged cull-and-projection
+    take views in rounds of eight, so the second round holds two.  The images
+    equal separate one-view renders bit for bit; gradients and poses match the
+    oracle."""
+    sc = scenes.random_gaussians(800, 96, 72, 90.0, seed=23, scale_range=(0.02, 0.15), n_views=10)
+    r, g, T, out = _gpu_forward(sc)
+    for v in (0, 7, 8, 9):
+        o1 = _np(Renderer(intrinsics(sc), n_views=1).forward(*g, T[v:v + 1].contiguous()))
+        for k in ("rgb", "depth", "alpha", "t_final", "n_contrib", "n_iter"):
+            assert np.array_equal(out[k][v:v + 1], o1[k]), (v, k)
+    g_up = scenes.upstream_grads(5, 10, 72, 96)
+    ref0 = oracle.render_scene(sc)
+    gm = masked_upstream(g_up, ref0["flags"])
+    ref = oracle.render_scene(sc, grads=gm)
+    assert_images_close(out, ref, ref["flags"], what="10 views")
+    grads, dpose = _gpu_backward(r, g, T, out, gm)
+    for k in GRAD_KEYS:
+        assert_grad_close(grads[k], ref["d_" + k], k)
+    assert_pose_close(dpose, ref["d_pose"])
+
+
 @pytest.mark.parametrize("tile,height", [((8, 8), 123), ((16, 16), 290)])
 def test_large_gaussians_spanning_many_tile_rows(tile, height):
     """Gaussians taller than 8 tile rows are emitted row-parallel (one warp per
