@@ -77,7 +77,24 @@ def test_decode_bf16_features_input():
 
 @pytest.mark.parametrize("bf16", [False, True])
 def test_decode_backward_parity(bf16):
-    sc = _street(n=2000, seed=6)
+    _backward_parity(_street(n=2000, seed=6), bf16)
+
+
+@pytest.mark.parametrize("k", [1, 4, 7])
+@pytest.mark.parametrize("bf16", [False, True])
+def test_decode_other_gaussians_per_anchor(bf16, k):
+    """k below 10: the heads' outputs (k, 3k, 7k) pad to the tensor-core tiles
+    differently; forward and backward still match the oracle."""
+    sc = scenes.street_anchors(n_anchors=1500, length=20.0, seed=9, k=k)
+    ref = _oracle(sc, bf16)
+    _, _, _, out = _gpu(sc, bf16)
+    assert ref["n"] > (20 if k == 1 else 1000)  # one Gaussian an anchor: few survive
+    assert ref["flags"].mean() < (0.15 if bf16 else 0.02)
+    _compare_outputs(out, ref, ref["flags"], sc.k, 1e-5)
+    _backward_parity(sc, bf16)
+
+
+def _backward_parity(sc, bf16):
     ref0 = _oracle(sc, bf16)
     rng = np.random.default_rng(3)
     n = ref0["n"]
