@@ -12,8 +12,8 @@
 // y = I): m1 = w*x, m2 = w*x^2, m3 = w*xy.  Hence
 //   d mean(S) / dx(q) = (1/n) [ (w*A)(q) + 2 x(q) (w*B)(q) + y(q) (w*C)(q) ],
 //   A = dS/dm1, B = dS/dm2, C = dS/dm3 at each p,
-// so the gradient is a second blur, of A, B, C.  Two kernels, one 16x16 output
-// tile per block and channel, separable 11-tap blurs from a shared-memory tile
+// so the gradient is a second blur, of A, B, C.  Two kernels, one kLT x kLT
+// output tile per block and channel (256 threads), separable 11-tap blurs from a shared-memory tile
 // with a 5-pixel halo, each thread producing kU neighbouring outputs per pass
 // from one (kU + 10)-value window (the blurs are bound by shared-memory loads):
 //   1. moments -> S, A, B, C (A, B, C to the workspace), block sums of S and
@@ -30,7 +30,11 @@
 
 namespace vpgs {
 
-constexpr int kLT = 16;             // output tile edge
+#ifndef VPGS_SSIM_TILE
+#define VPGS_SSIM_TILE 32
+#endif
+constexpr int kLT = VPGS_SSIM_TILE;  // output tile edge
+constexpr int kLThreads = 256;      // threads per block
 constexpr int kLR = 5;              // window radius
 constexpr int kLH = kLT + 2 * kLR;  // tile edge with halo (26)
 constexpr float kC1 = 0.01f * 0.01f, kC2 = 0.03f * 0.03f;
@@ -56,12 +60,12 @@ struct LossArgs {
 // Separable 11-tap blurs, register-blocked: each thread produces kU
 // neighbouring outputs from one (kU + 10)-value window, so a tap costs one
 // shared load per kU outputs instead of one per output.
-//   horizontal: s_src[NM][kLH][kLH + 1] -> s_h[NM][kLH][kLT + 1] (26 x 16)
+//   horizontal: s_src[NM][kLH][kLH + 1] -> s_h[NM][kLH][kLT + 1] (42 x 32)
 //   vertical:   s_h -> kU vertically adjacent outputs (r0 .. r0 + kU - 1, c)
-//               for the kLT * kLT / kU work items (threads tid < kLT * kLT / kU)
+//               for the kLT * kLT / kU work items, looped over the block's threads
 template <int NM>
 VPGS_D void hblur(const float (*s_src)[kLH][kLH + 1], float (*s_h)[kLH][kLT + 1], const float *g, int tid) {
-    for (int w = tid; w < kLH * (kLT / kU); w += kLT * kLT) {
+    for (int w = tid; w < kLH * (kLT / kU); w += kLThreads) {
         const int r = w / (kLT / kU), c0 = kU * (w % (kLT / kU));
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
@@ -124,7 +128,7 @@ VPGS_D double block_sum_f64(double v, double *s_red) {
     return t;  // valid in thread 0
 }
 
-__global__ void __launch_bounds__(kLT * kLT)
+__global__ void __launch_bounds__(kLThreads)
 ssim_moments_kernel(LossArgs a) {
     grid_dep_enter();
     __shared__ float s_in[2][kLH][kLH + 1];   // x, y with the halo
@@ -135,7 +139,7 @@ ssim_moments_kernel(LossArgs a) {
     const int x0 = blockIdx.x * kLT - kLR, y0 = blockIdx.y * kLT - kLR;
     const int64_t HW = (int64_t)a.H * a.W;
     const float *X = a.rgb + plane * HW, *Y = a.target + plane * HW;
-    for (int i = tid; i < kLH * kLH; i += kLT * kLT) {
+    for (int i = tid; i < kLH * kLH; i += kLThreads) {
         const int r = i / kLH, c = i % kLH, gy = y0 + r, gx = x0 + c;
         float xv = 0.f, yv = 0.f;
         if (gx >= 0 && gx < a.W && gy >= 0 && gy < a.H) {
@@ -147,7 +151,7 @@ ssim_moments_kernel(LossArgs a) {
     }
     __syncthreads();
     // horizontal: the five moment maps from one window of x and y
-    for (int w = tid; w < kLH * (kLT / kU); w += kLT * kLT) {
+    for (int w = tid; w < kLH * (kLT / kU); w += kLThreads) {
         const int r = w / (kLT / kU), c0 = kU * (w % (kLT / kU));
         float xs[kWin], ys[kWin];
 #pragma unroll
@@ -175,8 +179,8 @@ ssim_moments_kernel(LossArgs a) {
     }
     __syncthreads();
     float ssum = 0.f, l1 = 0.f;
-    if (tid < kLT * kLT / kU) {
-        const int tx = tid % kLT, r0 = kU * (tid / kLT);
+    for (int it = tid; it < kLT * kLT / kU; it += kLThreads) {
+        const int tx = it % kLT, r0 = kU * (it / kLT);
         float mm[kU][5];
         vblur<5>(s_h, a.g, r0, tx, mm);
 #pragma unroll
@@ -202,7 +206,7 @@ ssim_moments_kernel(LossArgs a) {
     // depth and volume terms, grid-strided over all blocks of this launch
     const int64_t nblk = (int64_t)gridDim.x * gridDim.y * gridDim.z;
     const int64_t bid = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    const int64_t stride = nblk * kLT * kLT, t0 = bid * kLT * kLT + tid;
+    const int64_t stride = nblk * kLThreads, t0 = bid * kLThreads + tid;
     float dsum = 0.f, vsum = 0.f;
     if (a.depth) {
         const int64_t P = (int64_t)a.V * HW;
@@ -237,7 +241,7 @@ ssim_moments_kernel(LossArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(kLT * kLT)
+__global__ void __launch_bounds__(kLThreads)
 ssim_grad_kernel(LossArgs a, int64_t n_partial) {
     grid_dep_enter();
     __shared__ float s_in[3][kLH][kLH + 1];
@@ -250,7 +254,7 @@ ssim_grad_kernel(LossArgs a, int64_t n_partial) {
     if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) {
         // loss terms from the first kernel's block sums
         double s[4] = {0, 0, 0, 0};
-        for (int64_t i = tid; i < n_partial; i += kLT * kLT)
+        for (int64_t i = tid; i < n_partial; i += kLThreads)
 #pragma unroll
             for (int k = 0; k < 4; ++k) s[k] += a.partial[4 * i + k];
         double t[4];
@@ -266,7 +270,7 @@ ssim_grad_kernel(LossArgs a, int64_t n_partial) {
     }
     if (!a.d_rgb) return;
     const int x0 = blockIdx.x * kLT - kLR, y0 = blockIdx.y * kLT - kLR;
-    for (int i = tid; i < kLH * kLH; i += kLT * kLT) {
+    for (int i = tid; i < kLH * kLH; i += kLThreads) {
         const int r = i / kLH, c = i % kLH, gy = y0 + r, gx = x0 + c;
         float va = 0.f, vb = 0.f, vc = 0.f;
         if (gx >= 0 && gx < a.W && gy >= 0 && gy < a.H) {
@@ -278,11 +282,11 @@ ssim_grad_kernel(LossArgs a, int64_t n_partial) {
     __syncthreads();
     hblur<3>(s_in, s_h, a.g, tid);
     __syncthreads();
-    if (tid >= kLT * kLT / kU) return;
-    const int tx = tid % kLT, r0 = kU * (tid / kLT);
+    const float inv_n = (float)(1.0 / n_col);
+    for (int it = tid; it < kLT * kLT / kU; it += kLThreads) {
+    const int tx = it % kLT, r0 = kU * (it / kLT);
     float mm[kU][3];
     vblur<3>(s_h, a.g, r0, tx, mm);
-    const float inv_n = (float)(1.0 / n_col);
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
         const float *m = mm[u];
@@ -295,6 +299,7 @@ ssim_grad_kernel(LossArgs a, int64_t n_partial) {
             // L_c + (1 - lambda) L1 share the sign term; the SSIM term enters as -lambda mean(S)
             a.d_rgb[o] = ((2.f - a.lambda_ssim) * (float)((e > 0.f) - (e < 0.f)) - a.lambda_ssim * dssim) * inv_n;
         }
+    }
     }
 }
 
@@ -330,10 +335,10 @@ cudaError_t launch_mapping_loss(void *ws, const float *rgb, const float *target,
     a.partial = reinterpret_cast<double *>(b + up(3 * sizeof(float) * (size_t)planes * HW));
     a.loss = loss; a.d_rgb = d_rgb; a.d_depth = d_depth; a.d_scales = d_scales;
     const dim3 grid((unsigned)a.tiles_x, (unsigned)a.tiles_y, (unsigned)planes);
-    VPGS_LAUNCH("ssim_moments", s, launch_k(ssim_moments_kernel, grid, kLT * kLT, 0, s, a));
+    VPGS_LAUNCH("ssim_moments", s, launch_k(ssim_moments_kernel, grid, kLThreads, 0, s, a));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    VPGS_LAUNCH("ssim_grad", s, launch_k(ssim_grad_kernel, grid, kLT * kLT, 0, s, a, (int64_t)grid.x * grid.y * grid.z));
+    VPGS_LAUNCH("ssim_grad", s, launch_k(ssim_grad_kernel, grid, kLThreads, 0, s, a, (int64_t)grid.x * grid.y * grid.z));
     return cudaGetLastError();
 }
 
