@@ -225,7 +225,8 @@ VPGS_D void mlp_fp32(const float *w, int K, int j, const float (&in)[kIn], float
     }
 }
 
-// Blocks of kDecThreads threads decode kDecAnchors anchors: thread t < 64 owns
+// Resident blocks of kDecThreads threads each load the prepared weights once,
+// then decode chunks of kDecAnchors anchors taken from a ticket: thread t < 64 owns
 // anchor t for its inputs and its valid-Gaussian count; in the FP32 form
 // threads t and t + 64 split its three MLPs (0 and 1 / 2: nearly equal
 // work); in the BF16 form each warp runs one 16-anchor tile on tensor cores,
@@ -244,21 +245,23 @@ decode_fwd_kernel(DecParams p, const double *__restrict__ T, DecOut o, const Dec
     __shared__ uint32_t s_wsum[kDecThreads / 32];
     __shared__ DecCam s_cam;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        s_bid = atomicAdd(ticket, 1u);
-        load_dec_cam(T, s_cam);
-    }
+    if (tid == 0) load_dec_cam(T, s_cam);
     const int K = p.K;
     {
-        // the prepared weights into shared memory, 16-byte words (both forms start
-        // at the union's first byte)
+        // the prepared weights into shared memory once per block, 16-byte words
+        // (both forms start at the union's first byte)
         const int words = p.bf16 ? (int)(sizeof(DecWts) / 16) : (n_params(K) + 3) / 4;
         const uint4 *src = reinterpret_cast<const uint4 *>(wts);
         uint4 *dst = reinterpret_cast<uint4 *>(&S.u);
         for (int i = tid; i < words; i += kDecThreads) dst[i] = src[i];
     }
-    __syncthreads();
+    // chunks of kDecAnchors anchors in ticket order (the look-back only waits on
+    // chunks handed out earlier, each held by a running block)
+    for (;;) {
+    if (tid == 0) s_bid = atomicAdd(ticket, 1u);
+    __syncthreads();  // also: the previous chunk's shared reads are done
     const int64_t bid = s_bid;
+    if (bid * kDecAnchors >= p.A) return;
     const int la = tid & (kDecAnchors - 1);  // the block-local anchor this thread reads
     const int64_t a = bid * kDecAnchors + la;
     const bool live = a < p.A;
@@ -475,6 +478,7 @@ decode_fwd_kernel(DecParams p, const double *__restrict__ T, DecOut o, const Dec
         o.scales[3 * pos + 2] = cv[2];
         reinterpret_cast<float4 *>(o.quats)[pos] = make_float4(cv[3], cv[4], cv[5], cv[6]);
         o.src_index[pos] = (int32_t)(aa * K + m);
+    }
     }
 }
 
@@ -1187,8 +1191,14 @@ vpgs_status vpgs_decode_anchors(void *ws, size_t ws_bytes, const vpgs_anchors *a
     unsigned long long *look = reinterpret_cast<unsigned long long *>(b + L.off_look);
     DecWts *wts = reinterpret_cast<DecWts *>(b + L.off_wts);
     VPGS_LAUNCH("decode_weights", s, launch_k(decode_weights_kernel, 8, 256, 0, s, p, wts));
+    // resident blocks only: each takes chunks from the ticket until none is left
+    static std::atomic<int> fwd_cache[kDeviceCache];
+    const int resident = per_device(fwd_cache, [smem] {
+        return resident_grid((const void *)decode_fwd_kernel, kDecThreads, smem, int64_t(1) << 30);
+    });
+    const unsigned grid = (unsigned)std::min<int64_t>(L.nblocks, resident);
     VPGS_LAUNCH("decode_fwd", s,
-                launch_k(decode_fwd_kernel, (unsigned)L.nblocks, kDecThreads, smem, s, p, T_cw, o,
+                launch_k(decode_fwd_kernel, grid, kDecThreads, smem, s, p, T_cw, o,
                          (const DecWts *)wts, ticket, look, status));
     return cudaGetLastError() == cudaSuccess ? VPGS_OK : VPGS_ERR_CUDA;
 }

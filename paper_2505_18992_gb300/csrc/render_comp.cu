@@ -71,12 +71,41 @@ VPGS_D float2 warp_rows(const float (&pyl)[kPix]) {
     return make_float2(0.5f * (lo + hi), 0.5f * (hi - lo));
 }
 
-// Compacts the batch positions [0, n) whose Gaussian's widened y extent reaches
-// the warp's pixel rows into list, in ascending order; returns how many
-// (warp-uniform).  All 32 lanes take part.
+// Whether a staged (plain) Gaussian can reach alpha_min at a pixel centre of
+// the tile-local box [x0, x1] x [y0, y1]: the minimum over the box of the
+// whitened square distance q = |W d|^2, d = p - mean, against log2(o /
+// alpha_min) (alpha = o 2^-q).  The minimum of the convex q lies inside the box
+// (then 0) or on an edge, where q is a quadratic in one variable.  The bound
+// is widened by 0.1 % + 1e-3 so that every pixel the FP32 per-pixel evaluation
+// would blend stays listed.
+VPGS_D bool reaches_box(const float4 &a, const float4 &b, float x0, float x1, float y0, float y1,
+                        float lg_amin) {
+    const float A = fmaf(a.z, a.z, b.x * b.x), B = fmaf(a.z, a.w, b.x * b.y), C = fmaf(a.w, a.w, b.y * b.y);
+    if (!(A > 0.f && C > 0.f)) return true;
+    const float dx0 = x0 - a.x, dx1 = x1 - a.x, dy0 = y0 - a.y, dy1 = y1 - a.y;
+    if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) return true;
+    auto q = [&](float dx, float dy) { return fmaf(A * dx, dx, fmaf(2.f * B * dx, dy, C * dy * dy)); };
+    const float ra = -B / A, rc = -B / C;
+    float m = q(fminf(fmaxf(ra * dy0, dx0), dx1), dy0);
+    m = fminf(m, q(fminf(fmaxf(ra * dy1, dx0), dx1), dy1));
+    m = fminf(m, q(dx0, fminf(fmaxf(rc * dx0, dy0), dy1)));
+    m = fminf(m, q(dx1, fminf(fmaxf(rc * dx1, dy0), dy1)));
+    const float level = __log2f(b.z) - lg_amin;
+    return !(m > fmaf(1e-3f, fabsf(level), level) + 1e-3f);
+}
+
+// Compacts the batch positions [0, n) whose Gaussian reaches the warp's pixel
+// rows into list, in ascending order; returns how many (warp-uniform).  A
+// Gaussian is listed when its widened y extent reaches the rows and, with
+// kExact and a plain record, its alpha_min ellipse also meets the rows' pixel
+// centres within the tile's columns [0.5, xmax].  All 32 lanes take part.
 // `fine` tells (warp-uniform) whether a listed record is near-degenerate.
+// Both forms list every Gaussian that blends into a pixel of the rows, so the
+// forward (y extent alone: the exact test costs it more than it saves) and the
+// backward (exact) may differ in what they skip but not in what they blend.
+template <bool kExact>
 VPGS_D int warp_list(const float4 *s0, const float4 *s1, int n, float2 band, uint16_t *list, int lane,
-                     bool &fine) {
+                     bool &fine, float xmax, float lg_amin) {
     const uint32_t below = (1u << lane) - 1u;
     int cnt = 0;
     bool any = false;
@@ -84,9 +113,11 @@ VPGS_D int warp_list(const float4 *s0, const float4 *s1, int n, float2 band, uin
         const int k = c0 + lane;
         bool touch = false, f = false;
         if (k < n) {
-            const float ry = s1[k].w;
-            touch = fabsf(s0[k].y - band.x) <= fabsf(ry) + band.y;
+            const float4 a = s0[k], b = s1[k];
+            const float ry = b.w;
+            touch = fabsf(a.y - band.x) <= fabsf(ry) + band.y;
             f = touch && ry < 0.f;
+            if (kExact && touch && !f) touch = reaches_box(a, b, 0.5f, xmax, band.x - band.y, band.x + band.y, lg_amin);
         }
         const uint32_t m = __ballot_sync(0xffffffffu, touch);
         any |= __any_sync(0xffffffffu, f);
@@ -172,6 +203,7 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
 #pragma unroll
     for (int q = 0; q < kPix; ++q) pyl[q] = (float)(kPix * ly + q) + 0.5f;
     const float2 band = warp_rows(pyl);
+    const float lg_amin = __log2f(o.alpha_min);
     int t = blockIdx.x;
     for (;;) {
         if (work) {
@@ -185,6 +217,7 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
         const TileCoord tc = tile_coord(tile, cam);
         const int px = tc.tx * cam.tile_w + lx;
         const float ox = (float)(tc.tx * cam.tile_w), oy = (float)(tc.ty * cam.tile_h);
+        const float xmax = fminf((float)cam.tile_w, (float)cam.W - ox) - 0.5f;  // last pixel centre column
         const uint2 rg = ranges[tile];
         const int start = (int)rg.x, end = (int)rg.y;
         float T[kPix], C0[kPix], C1[kPix], C2[kPix], D[kPix];
@@ -209,7 +242,7 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
             }
             __syncthreads();
             bool any_fine;
-            const int nl = warp_list(s0, s1, min(NT, end - b0), band, wl, lane, any_fine);
+            const int nl = warp_list<false>(s0, s1, min(NT, end - b0), band, wl, lane, any_fine, xmax, lg_amin);
             // one blend step of this thread's pixels against list entry k
             auto blend = [&](int k, const float4 &a, const float4 &b, auto fine) -> bool {
                     constexpr bool kFine = decltype(fine)::value;
@@ -502,6 +535,7 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
 #pragma unroll
     for (int q = 0; q < kPix; ++q) pyl[q] = (float)(kPix * ly + q) + 0.5f;
     const float2 band = warp_rows(pyl);
+    const float lg_amin = __log2f(o.alpha_min);
     uint16_t *wl = s_wl + (size_t)warp * NT;
     float *my_part = s_part + (size_t)warp * NT * kPartStride;
     const int rs = red_slot<NV>(lane);
@@ -530,6 +564,7 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
         const TileCoord tc = tile_coord(tile, cam);
         const int px = tc.tx * cam.tile_w + lx;
         const float ox = (float)(tc.tx * cam.tile_w), oy = (float)(tc.ty * cam.tile_h);
+        const float xmax = fminf((float)cam.tile_w, (float)cam.W - ox) - 0.5f;  // last pixel centre column
         const uint2 rg = ranges[tile];
         const int start = (int)rg.x;
         const int64_t HW = (int64_t)cam.H * cam.W;
@@ -578,7 +613,7 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
             __syncthreads();
             const int k_end = min(nb, warp_max - (b0 - start));  // warp-uniform
             bool any_fine;
-            const int nl = warp_list(s0, s1, k_end, band, wl, lane, any_fine);
+            const int nl = warp_list<true>(s0, s1, k_end, band, wl, lane, any_fine, xmax, lg_amin);
             // back to front; a batch with a near-degenerate record takes the walk that
             // chooses the precision form per entry (a warp-uniform branch), the others
             // the plain one
