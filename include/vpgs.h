@@ -219,11 +219,10 @@ vpgs_status vpgs_render_project(void *ws, size_t ws_bytes, const vpgs_gaussians 
  *     did not fit in the array.
  *   - The first call on each device looks the array's device address up
  *     (cudaGetSymbolAddress) with that device current, and keeps it for the
- *     later calls on that device.  Make that first call before capturing any
- *     stream.  The address belongs to the device's primary context (the one
- *     the CUDA runtime uses): after cudaDeviceReset, or with another driver
- *     context current on the device, it no longer names the array, so do not
- *     call this entry point in either situation.
+ *     later calls on that device.  The address belongs to the device's
+ *     primary context (the one the CUDA runtime uses): after cudaDeviceReset,
+ *     or with another driver context current on the device, it no longer
+ *     names the array, so do not call this entry point in either situation.
  *   - Device ordinals from 64 up return VPGS_ERR_UNSUPPORTED.
  *   - Every call shares the one array, and a call leaves its contents behind.
  *     The render clears what it needs zeroed.  Calls that overlap on the GPU
