@@ -26,6 +26,18 @@
 #ifndef VPGS_BWD_ACC
 #define VPGS_BWD_ACC -1
 #endif
+//   VPGS_DEPTH_SORT_GRID, VPGS_OFFSET_SCAN_GRID  blocks per SM of the depth
+//                sort's passes and of the instance-offset scan (0: what is
+//                resident).  Their item count, the visible pairs, is usually far
+//                below the capacity (every pair visible) that the resident grid
+//                is sized for, and every block past the last tile still
+//                launches, takes a ticket and leaves
+#ifndef VPGS_DEPTH_SORT_GRID
+#define VPGS_DEPTH_SORT_GRID 2
+#endif
+#ifndef VPGS_OFFSET_SCAN_GRID
+#define VPGS_OFFSET_SCAN_GRID 2
+#endif
 //   VPGS_BWD_RCP 1: the backward takes one approximate reciprocal of 1 - alpha
 //                per blended pair (relative error ~1e-7 per step), 0: IEEE divisions
 #ifndef VPGS_BWD_RCP

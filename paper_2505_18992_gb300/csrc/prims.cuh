@@ -178,19 +178,27 @@ inline int resident_grid(const void *kernel, int threads, size_t smem, int64_t c
 
 inline int64_t scan_blocks(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
 
+// A ticket-loop grid: what is resident, or at most per_sm blocks per SM (per_sm
+// > 0; for passes whose item count is usually far below its capacity, where
+// blocks past the last tile only launch, take a ticket and leave).
+int device_sm_count();
+inline int grid_cap(int resident, int per_sm) {
+    return per_sm > 0 ? std::max(1, std::min(resident, per_sm * device_sm_count())) : resident;
+}
+
 // Launch a scan over at most n_cap items.  *ticket and the scan_blocks(n_cap)
 // look-back words must be zero on entry (the render's prepare kernel clears them).
 template <class Load, class Store>
 cudaError_t launch_scan(const char *name, Load load, Store store, int64_t n_cap, const uint32_t *n_dev,
                         uint32_t *ticket, unsigned long long *look, uint32_t *total,
-                        uint32_t *status, cudaStream_t stream, LookBack lb = LookBack{}) {
+                        uint32_t *status, cudaStream_t stream, LookBack lb = LookBack{}, int per_sm = 0) {
     int64_t nb = scan_blocks(n_cap);
     if (nb == 0) nb = 1;
     static std::atomic<int> grid_cache[kDeviceCache];  // per <Load, Store> and device
     const int grid_res = per_device(grid_cache, [] {
         return resident_grid((const void *)scan_kernel<Load, Store>, kScanThreads, 0, int64_t(1) << 30);
     });
-    const int grid = (int)std::min<int64_t>(grid_res, nb);
+    const int grid = (int)std::min<int64_t>(grid_cap(grid_res, per_sm), nb);
     VPGS_LAUNCH(name, stream,
                 launch_k(scan_kernel<Load, Store>, (unsigned)grid, kScanThreads, 0, stream, load, store, n_cap, n_dev,
                                                                          ticket, look, total, status, lb));
@@ -435,7 +443,7 @@ inline cudaError_t radix_sort_pairs(const char *name, uint32_t *k0, uint32_t *v0
                                     int64_t n_cap, const uint32_t *n_dev, int lo_bit, int bits,
                                     const uint32_t *hist, uint32_t *ticket, uint32_t *look,
                                     uint32_t *status, cudaStream_t stream, bool *result_in_1, int items,
-                                    LookBack lb = LookBack{}) {
+                                    LookBack lb = LookBack{}, int per_sm = 0) {
     SortPass ps[kMaxSortPasses];
     int np = plan_passes(lo_bit, bits, ps);
     *result_in_1 = (np & 1) != 0;
@@ -450,7 +458,7 @@ inline cudaError_t radix_sort_pairs(const char *name, uint32_t *k0, uint32_t *v0
     static std::atomic<int> grids[4][kDeviceCache];  // by items (4, 8, 16, 32) and device
     const int gi = items == 4 ? 0 : items == 8 ? 1 : items == 16 ? 2 : 3;
     const int grid_res = per_device(grids[gi], [kern] { return resident_grid(kern, kSortThreads, 0, int64_t(1) << 30); });
-    const unsigned grid = (unsigned)std::min<int64_t>(grid_res, nb);
+    const unsigned grid = (unsigned)std::min<int64_t>(grid_cap(grid_res, per_sm), nb);
     cudaError_t e;
     uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
     for (int p = 0; p < np; ++p) {

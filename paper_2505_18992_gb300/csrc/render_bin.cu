@@ -432,7 +432,7 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
     const int depth_items = L.VN > (int64_t(4) << 20) ? 16 : kDepthSortItems;
     e = radix_sort_pairs("sort_depth_pass", ws.dkey[0], ws.dval[0], ws.dkey[1], ws.dval[1], L.VN, n_vis,
                          0, 32, ws.sort_hist[0], ws.counters + CNT_TICKET_D, ws.sort_look[0], ws.status, s,
-                         &in1, depth_items, lb);
+                         &in1, depth_items, lb, VPGS_DEPTH_SORT_GRID);
     if (e != cudaSuccess) return e;
     const uint32_t *dval = in1 ? ws.dval[1] : ws.dval[0];  // visible records in depth order
     uint32_t *inst_off = in1 ? ws.dkey[0] : ws.dkey[1];  // the depth-sort buffer not holding the result
@@ -441,7 +441,7 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
     if (np_tile > 4) return cudaErrorInvalidValue;
     // 3. instance offsets, then emission
     e = launch_scan("scan_offsets", CountLoad{ws.tcount, dval}, OffsetStore{inst_off}, L.VN, n_vis,
-                    ws.counters + CNT_TICKET_O, ws.scan_look[1], n_inst, ws.status, s, lb);
+                    ws.counters + CNT_TICKET_O, ws.scan_look[1], n_inst, ws.status, s, lb, VPGS_OFFSET_SCAN_GRID);
     if (e != cudaSuccess) return e;
     static std::atomic<int> emit_cache[kDeviceCache];
     const int emit_grid = per_device(emit_cache, [] {
