@@ -413,7 +413,7 @@ constexpr int kMaxSortPasses = 8;
 // scan geometry
 constexpr int kScanThreads = 256;
 #ifndef VPGS_SCAN_ITEMS
-#define VPGS_SCAN_ITEMS 8
+#define VPGS_SCAN_ITEMS 4
 #endif
 constexpr int kScanItems = VPGS_SCAN_ITEMS;  // items per thread of a scan tile
 constexpr int kScanTile = kScanThreads * kScanItems;
