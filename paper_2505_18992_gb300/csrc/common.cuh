@@ -417,6 +417,8 @@ constexpr int kScanThreads = 256;
 #endif
 constexpr int kScanItems = VPGS_SCAN_ITEMS;  // items per thread of a scan tile
 constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kScanItemsWide = 8;  // the same for scans of many millions of items
+static_assert(kScanItemsWide >= kScanItems, "look-back space is sized for the narrower tiles");
 
 // bounded spin for decoupled look-back: the predecessor always holds an
 // earlier ticket and is therefore resident, so this bound is never reached in

@@ -51,13 +51,14 @@ constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagPre = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
 
-template <class Load, class Store>
+template <class Load, class Store, int ITEMS>
 __global__ void __launch_bounds__(kScanThreads)
 scan_kernel(Load load, Store store, int64_t n_cap, const uint32_t *n_dev, uint32_t *ticket,
             unsigned long long *look, uint32_t *total, uint32_t *status, LookBack lb) {
+    constexpr int kTile = kScanThreads * ITEMS;
     grid_dep_enter();
     if (lb.stop_on_error && *status != 0u) return;
-    __shared__ uint32_t s_items[kScanTile + kScanTile / 32];
+    __shared__ uint32_t s_items[kTile + kTile / 32];
     __shared__ uint32_t s_warp[kScanThreads / kWarp];
     __shared__ uint32_t s_bid, s_excl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -69,25 +70,25 @@ scan_kernel(Load load, Store store, int64_t n_cap, const uint32_t *n_dev, uint32
     if (tid == 0) s_bid = atomicAdd(ticket, 1u);
     __syncthreads();
     const int64_t bid = s_bid;
-    const int64_t base = bid * kScanTile;
+    const int64_t base = bid * kTile;
     if (base >= n) {
         if (bid == 0 && tid == 0 && total) *total = 0;
         return;
     }
     // striped, coalesced loads into a padded shared tile
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
+    for (int j = 0; j < ITEMS; ++j) {
         int idx = j * kScanThreads + tid;
         int64_t gi = base + idx;
         s_items[idx + (idx >> 5)] = gi < n ? load(gi) : 0u;
     }
     __syncthreads();
-    // blocked: thread t owns items t*16 .. t*16+15
-    uint32_t v[kScanItems];
+    // blocked: thread t owns items t*ITEMS .. t*ITEMS+ITEMS-1
+    uint32_t v[ITEMS];
     uint32_t tsum = 0;
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        int idx = tid * kScanItems + i;
+    for (int i = 0; i < ITEMS; ++i) {
+        int idx = tid * ITEMS + i;
         v[i] = s_items[idx + (idx >> 5)];
         tsum += v[i];
     }
@@ -150,14 +151,14 @@ scan_kernel(Load load, Store store, int64_t n_cap, const uint32_t *n_dev, uint32
         }
         if (lane == 0) {
             s_excl = (uint32_t)excl;
-            if (base + kScanTile >= n && total) *total = (uint32_t)excl + block_agg;
+            if (base + kTile >= n && total) *total = (uint32_t)excl + block_agg;
         }
     }
     __syncthreads();
     uint32_t run = s_excl + texcl;
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        int64_t gi = base + (int64_t)tid * kScanItems + i;
+    for (int i = 0; i < ITEMS; ++i) {
+        int64_t gi = base + (int64_t)tid * ITEMS + i;
         if (gi < n) store(gi, run, v[i]);
         run += v[i];
     }
@@ -186,23 +187,38 @@ inline int grid_cap(int resident, int per_sm) {
     return per_sm > 0 ? std::max(1, std::min(resident, per_sm * device_sm_count())) : resident;
 }
 
-// Launch a scan over at most n_cap items.  *ticket and the scan_blocks(n_cap)
-// look-back words must be zero on entry (the render's prepare kernel clears them).
-template <class Load, class Store>
-cudaError_t launch_scan(const char *name, Load load, Store store, int64_t n_cap, const uint32_t *n_dev,
-                        uint32_t *ticket, unsigned long long *look, uint32_t *total,
-                        uint32_t *status, cudaStream_t stream, LookBack lb = LookBack{}, int per_sm = 0) {
-    int64_t nb = scan_blocks(n_cap);
+template <class Load, class Store, int ITEMS>
+cudaError_t launch_scan_as(const char *name, Load load, Store store, int64_t n_cap, const uint32_t *n_dev,
+                           uint32_t *ticket, unsigned long long *look, uint32_t *total, uint32_t *status,
+                           cudaStream_t stream, LookBack lb, int per_sm) {
+    const int64_t tile = (int64_t)kScanThreads * ITEMS;
+    int64_t nb = (n_cap + tile - 1) / tile;
     if (nb == 0) nb = 1;
-    static std::atomic<int> grid_cache[kDeviceCache];  // per <Load, Store> and device
+    static std::atomic<int> grid_cache[kDeviceCache];  // per <Load, Store, ITEMS> and device
     const int grid_res = per_device(grid_cache, [] {
-        return resident_grid((const void *)scan_kernel<Load, Store>, kScanThreads, 0, int64_t(1) << 30);
+        return resident_grid((const void *)scan_kernel<Load, Store, ITEMS>, kScanThreads, 0, int64_t(1) << 30);
     });
     const int grid = (int)std::min<int64_t>(grid_cap(grid_res, per_sm), nb);
     VPGS_LAUNCH(name, stream,
-                launch_k(scan_kernel<Load, Store>, (unsigned)grid, kScanThreads, 0, stream, load, store, n_cap, n_dev,
-                                                                         ticket, look, total, status, lb));
+                launch_k(scan_kernel<Load, Store, ITEMS>, (unsigned)grid, kScanThreads, 0, stream, load, store, n_cap,
+                         n_dev, ticket, look, total, status, lb));
     return cudaGetLastError();
+}
+
+// Launch a scan over at most n_cap items.  *ticket and the scan_blocks(n_cap)
+// look-back words must be zero on entry (the render's prepare kernel clears them).
+// wide: tiles of kScanItemsWide items per thread (fewer tiles in the look-back
+// chain, for scans of many millions of items) instead of kScanItems.
+template <class Load, class Store>
+cudaError_t launch_scan(const char *name, Load load, Store store, int64_t n_cap, const uint32_t *n_dev,
+                        uint32_t *ticket, unsigned long long *look, uint32_t *total,
+                        uint32_t *status, cudaStream_t stream, LookBack lb = LookBack{}, int per_sm = 0,
+                        bool wide = false) {
+    if (wide)
+        return launch_scan_as<Load, Store, kScanItemsWide>(name, load, store, n_cap, n_dev, ticket, look, total,
+                                                           status, stream, lb, per_sm);
+    return launch_scan_as<Load, Store, kScanItems>(name, load, store, n_cap, n_dev, ticket, look, total, status,
+                                                   stream, lb, per_sm);
 }
 
 // ---------------------------------------------------------------------------

@@ -419,9 +419,12 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
     (void)sms;
     uint32_t *n_vis = ws.counters + CNT_VISIBLE;
     uint32_t *n_inst = ws.counters + CNT_INSTANCES;
+    // calls of many views (above 4M pairs): wider scan tiles and depth-sort tiles,
+    // the offset scan on the resident grid (the visible pairs then fill it)
+    const bool many = L.VN > (int64_t(4) << 20);
     // 1. compaction of visible (view, Gaussian) pairs
     e = launch_scan("scan_visible", VisLoad{ws.tcount}, VisStore{ws.rec, ws.dkey[0], ws.dval[0], ws.vis_idx, L.VN},
-                    L.VN, nullptr, ws.counters + CNT_TICKET_A, ws.scan_look[0], n_vis, ws.status, s, lb);
+                    L.VN, nullptr, ws.counters + CNT_TICKET_A, ws.scan_look[0], n_vis, ws.status, s, lb, 0, many);
     if (e != cudaSuccess) return e;
     // 2. depth sort
     bool in1 = false;
@@ -429,7 +432,7 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
     // keys per thread: few for a frame's worth of visible Gaussians (short tiles
     // start the look-back chain sooner), more for many views' worth (fewer tiles
     // in the chain); the look-back space is sized for kDepthSortItems, the most tiles
-    const int depth_items = L.VN > (int64_t(4) << 20) ? 16 : kDepthSortItems;
+    const int depth_items = many ? 16 : kDepthSortItems;
     e = radix_sort_pairs("sort_depth_pass", ws.dkey[0], ws.dval[0], ws.dkey[1], ws.dval[1], L.VN, n_vis,
                          0, 32, ws.sort_hist[0], ws.counters + CNT_TICKET_D, ws.sort_look[0], ws.status, s,
                          &in1, depth_items, lb, VPGS_DEPTH_SORT_GRID);
@@ -441,7 +444,8 @@ cudaError_t build_tile_lists(const GaussIn &g, int V, const CamParams &cam, cons
     if (np_tile > 4) return cudaErrorInvalidValue;
     // 3. instance offsets, then emission
     e = launch_scan("scan_offsets", CountLoad{ws.tcount, dval}, OffsetStore{inst_off}, L.VN, n_vis,
-                    ws.counters + CNT_TICKET_O, ws.scan_look[1], n_inst, ws.status, s, lb, VPGS_OFFSET_SCAN_GRID);
+                    ws.counters + CNT_TICKET_O, ws.scan_look[1], n_inst, ws.status, s, lb,
+                    many ? 0 : VPGS_OFFSET_SCAN_GRID, many);
     if (e != cudaSuccess) return e;
     static std::atomic<int> emit_cache[kDeviceCache];
     const int emit_grid = per_device(emit_cache, [] {
