@@ -1,4 +1,5 @@
 """GPU anchor decoder (FP32 and BF16 tensor-core forms) against the FP64 oracle."""
+import copy
 import ctypes
 
 import numpy as np
@@ -92,6 +93,38 @@ def test_decode_other_gaussians_per_anchor(bf16, k):
     assert ref["flags"].mean() < (0.15 if bf16 else 0.02)
     _compare_outputs(out, ref, ref["flags"], sc.k, 1e-5)
     _backward_parity(sc, bf16)
+
+
+def _in_view_subset(n):
+    """The first n anchors of a street scene that decode to at least one
+    Gaussian (so that few-anchor cases still have outputs to compare)."""
+    sc0 = _street(n=2000, seed=2)
+    ref0 = _oracle(sc0, True)
+    sel = np.unique(ref0["src_index"] // sc0.k)[:n]
+    sc = copy.copy(sc0)
+    sc.anchors, sc.features = sc0.anchors[sel].copy(), sc0.features[sel].copy()
+    sc.scaling, sc.offsets = sc0.scaling[sel].copy(), sc0.offsets[sel].copy()
+    return sc
+
+
+@pytest.mark.parametrize("n", [1, 63, 64, 65, 130])
+@pytest.mark.parametrize("bf16", [False, True])
+def test_decode_few_anchors(bf16, n):
+    """Fewer 64-anchor chunks than resident forward blocks (most blocks find no
+    chunk and leave) and a ragged last chunk; a second call on the same decoder
+    starts its chunk tickets from zero again and gives the same outputs."""
+    sc = _in_view_subset(n)
+    ref = _oracle(sc, bf16)
+    assert ref["n"] >= 1
+    d, feats, T, out = _gpu(sc, bf16)
+    _compare_outputs(out, ref, ref["flags"], sc.k, 1e-5)
+    first = {k: out[k][: int(out["n"])].clone() for k in OUT_KEYS}
+    out2 = d.forward(dev(sc.anchors), feats, dev(sc.scaling), dev(sc.offsets), dev(oracle.flatten_mlp(sc.mlp)),
+                     sc.camera, T)
+    torch.cuda.synchronize()
+    assert int(out2["n"]) == int(out["n"])
+    for k in OUT_KEYS:
+        assert torch.equal(out2[k][: int(out2["n"])], first[k]), k
 
 
 def _backward_parity(sc, bf16):

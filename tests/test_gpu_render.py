@@ -439,6 +439,29 @@ def test_full_size_room_sampled_rows():
     assert_pose_close(dpose, ref["d_pose"])
 
 
+def test_one_view_with_more_visible_pairs_than_one_sort_round():
+    # 400,000 Gaussians, all in front of one 320x240 camera: the depth sort's
+    # tiles (1,024 keys) and the instance-offset scan's tiles outnumber their
+    # grids of 2 blocks per SM, so blocks take several tiles from the ticket
+    sc = scenes.random_gaussians(400_000, 320, 240, 300.0, seed=41, scale_range=(0.002, 0.012))
+    rows = [0, 120, 239]
+    g_up = scenes.upstream_grads(12, 1, 240, 320)
+    ref0 = oracle.render_scene(sc, rows=rows)
+    sel = np.zeros_like(ref0["flags"])
+    sel[:, rows] = True
+    ignore = ref0["flags"] | ~sel
+    r, g, T, out = _gpu_forward(sc)
+    shown = {k: (np.where(sel[:, None], v, 0) if k == "rgb" else np.where(sel, v, 0))
+             for k, v in out.items()}
+    assert_images_close(shown, ref0, ignore, what="400k visible rows")
+    gm = masked_upstream(g_up, ignore)
+    ref = oracle.render_scene(sc, rows=rows, grads=gm)
+    grads, dpose = _gpu_backward(r, g, T, out, gm)
+    for k in GRAD_KEYS:
+        assert_grad_close(grads[k], ref["d_" + k], k)
+    assert_pose_close(dpose, ref["d_pose"])
+
+
 def test_batched_views_equal_separate_views():
     sc = scenes.random_gaussians(3000, 160, 120, 140.0, seed=31, scale_range=(0.01, 0.1), n_views=4)
     r, g, T, out = _gpu_forward(sc)
