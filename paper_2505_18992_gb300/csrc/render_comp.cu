@@ -54,6 +54,10 @@ constexpr int kPix = VPGS_PIX;
 constexpr int kDirect = VPGS_BWD_DIRECT;  // at most this many active lanes: per-lane atomics, no reduction
 constexpr int kMaxThreads = 512;
 // list entries whose alphas the forward evaluates before blending them
+#ifndef VPGS_FWD_BATCH
+#define VPGS_FWD_BATCH 2  // records each forward thread stages per batch
+#endif
+constexpr int kFwdBatch = VPGS_FWD_BATCH;
 #ifndef VPGS_FWD_WALK
 #define VPGS_FWD_WALK 2
 #endif
@@ -190,7 +194,7 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                      vpgs_images out, const uint32_t *status, uint32_t *work) {
     grid_dep_enter();
     extern __shared__ float4 smem[];
-    const int NT = blockDim.x;
+    const int NT = blockDim.x * kFwdBatch;  // records per batch
     float4 *s0 = smem, *s1 = smem + NT, *s2 = smem + 2 * NT, *s3 = smem + 3 * NT;
     uint16_t *s_wl = reinterpret_cast<uint16_t *>(smem + 4 * NT);  // [NW][NT] per-warp lists
     __shared__ int s_tile;
@@ -233,12 +237,16 @@ composite_fwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
 #pragma unroll
         for (int q = 0; q < kPix; ++q) all_done = all_done && done[q];
         for (int b0 = start; b0 < end; b0 += NT) {
-            if (__syncthreads_count(all_done) == NT) break;
-            const int j = b0 + tid;
-            if (j < end) {
-                const Rec r = rec[ival[j]];
-                stage(r, ox, oy, s0[tid], s1[tid], s2[tid]);
-                if (r.r3.z < 0.f) s3[tid] = fine_extra(r, ox, oy, s0[tid].x, s0[tid].y);
+            if (__syncthreads_count(all_done) == (int)blockDim.x) break;
+#pragma unroll 1
+            for (int u = 0; u < kFwdBatch; ++u) {
+                const int k = tid + u * (int)blockDim.x;
+                const int j = b0 + k;
+                if (j < end) {
+                    const Rec r = rec[ival[j]];
+                    stage(r, ox, oy, s0[k], s1[k], s2[k]);
+                    if (r.r3.z < 0.f) s3[k] = fine_extra(r, ox, oy, s0[k].x, s0[k].y);
+                }
             }
             __syncthreads();
             bool any_fine;
@@ -704,7 +712,8 @@ cudaError_t launch_composite_fwd(const RenderWs &ws, const uint32_t *ival, int V
                                  int persistent_ctas, cudaStream_t s) {
     const int B = cam.tile_w * cam.tile_h / kPix;
     const int n_tiles = V * cam.T;
-    const size_t sm = comp_smem(B, false);
+    const int NB = B * kFwdBatch;  // records per batch: s0-s3, and a list per warp
+    const size_t sm = sizeof(float4) * 4 * (size_t)NB + sizeof(uint16_t) * (size_t)(B / 32) * NB;
     uint32_t *work = nullptr;
     int grid = n_tiles;
     if (persistent_ctas > 0) {
