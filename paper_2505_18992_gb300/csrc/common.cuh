@@ -22,9 +22,12 @@
 //                gradient: 0 = one global atomic per warp, 1 = per-warp shared
 //                slots summed per batch, 2 = shared-memory atomics per batch,
 //                -1 = by the tile's warps (1 from 2 warps per tile up, 0 for a
-//                one-warp tile, which has no warps' sums to combine)
+//                one-warp tile, which has no warps' sums to combine).  0 by
+//                default: with batches of 256 records (render_comp.cu,
+//                VPGS_BWD_BATCH) the shared slots of 1 and 2 would cost resident
+//                blocks
 #ifndef VPGS_BWD_ACC
-#define VPGS_BWD_ACC -1
+#define VPGS_BWD_ACC 0
 #endif
 //   VPGS_DEPTH_SORT_GRID, VPGS_OFFSET_SCAN_GRID  blocks per SM of the depth
 //                sort's passes and of the instance-offset scan (0: what is

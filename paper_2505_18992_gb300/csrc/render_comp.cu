@@ -58,6 +58,10 @@ constexpr int kMaxThreads = 512;
 #define VPGS_FWD_BATCH 2  // records each forward thread stages per batch
 #endif
 constexpr int kFwdBatch = VPGS_FWD_BATCH;
+#ifndef VPGS_BWD_BATCH
+#define VPGS_BWD_BATCH 2  // records each backward thread stages per batch
+#endif
+constexpr int kBwdBatch = VPGS_BWD_BATCH;
 #ifndef VPGS_FWD_WALK
 #define VPGS_FWD_WALK 2
 #endif
@@ -527,8 +531,8 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
                      const uint32_t *status, uint32_t *work) {
     grid_dep_enter();
     extern __shared__ float4 smem[];
-    const int NT = blockDim.x;
-    const int NW = NT >> 5;
+    const int NT = blockDim.x * kBwdBatch;  // records per batch
+    const int NW = blockDim.x >> 5;
     float4 *s0 = smem, *s1 = smem + NT, *s2 = smem + 2 * NT;
     uint32_t *s_id = reinterpret_cast<uint32_t *>(smem + 3 * NT);
     uint16_t *s_wl = reinterpret_cast<uint16_t *>(s_id + NT);             // [NW][NT] per-warp lists
@@ -608,16 +612,19 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
             const int b0 = max(start, b1 - NT);
             const int nb = b1 - b0;
             __syncthreads();
-            const int j = b0 + tid;
-            if (j < b1) {
-                const uint32_t id = ival[j];
-                stage(rec[id], ox, oy, s0[tid], s1[tid], s2[tid]);
-                s_id[tid] = id;
+#pragma unroll 1
+            for (int u = 0; u < kBwdBatch; ++u) {
+                const int k = tid + u * (int)blockDim.x;
+                if (b0 + k < b1) {
+                    const uint32_t id = ival[b0 + k];
+                    stage(rec[id], ox, oy, s0[k], s1[k], s2[k]);
+                    s_id[k] = id;
+                }
             }
             if (ACC == 1)
                 for (int e = lane; e < nb * kPartStride; e += 32) my_part[e] = 0.f;
             if (ACC == 2)
-                for (int e = tid; e < nb * kPartStride; e += NT) s_part[e] = 0.f;
+                for (int e = tid; e < nb * kPartStride; e += (int)blockDim.x) s_part[e] = 0.f;
             __syncthreads();
             const int k_end = min(nb, warp_max - (b0 - start));  // warp-uniform
             bool any_fine;
@@ -672,7 +679,7 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
             if (ACC != 0) {
                 __syncthreads();
                 // one thread per Gaussian of the batch: one global atomic per value
-                for (int k = tid; k < nb; k += NT) {
+                for (int k = tid; k < nb; k += (int)blockDim.x) {
                     float *dst = g2d + 10 * (int64_t)s_id[k];
 #pragma unroll
                     for (int sl = 0; sl < 10; ++sl) {
@@ -692,11 +699,15 @@ composite_bwd_kernel(const Rec *__restrict__ rec, const uint32_t *__restrict__ i
     }
 }
 
-static size_t comp_smem(int NT, bool bwd, int acc = 0) {
-    const size_t parts = acc == 1 ? (size_t)(NT / 32) * NT * kPartStride : (acc == 2 ? (size_t)NT * kPartStride : 0);
-    const size_t lists = sizeof(uint16_t) * (size_t)(NT / 32) * NT;
-    // forward: s0-s3 and the lists; backward: s0-s2, the ids, the lists and the parts
-    return sizeof(float4) * (bwd ? 3 : 4) * NT + lists + (bwd ? sizeof(uint32_t) * NT + sizeof(float) * parts : 0);
+// dynamic shared memory of a compositing block of `threads` threads staging
+// `records` per batch: forward s0-s3 and the warps' lists; backward s0-s2, the
+// ids, the lists and the per-Gaussian partial sums of the combination scheme
+static size_t comp_smem(int threads, int records, bool bwd, int acc = 0) {
+    const size_t warps = (size_t)threads / 32;
+    const size_t parts = acc == 1 ? warps * records * kPartStride : (acc == 2 ? (size_t)records * kPartStride : 0);
+    const size_t lists = sizeof(uint16_t) * warps * records;
+    return sizeof(float4) * (bwd ? 3 : 4) * records + lists +
+           (bwd ? sizeof(uint32_t) * records + sizeof(float) * parts : 0);
 }
 
 static int persistent_grid(const void *kernel, int B, size_t smem, int per_sm, int n_tiles) {
@@ -712,8 +723,7 @@ cudaError_t launch_composite_fwd(const RenderWs &ws, const uint32_t *ival, int V
                                  int persistent_ctas, cudaStream_t s) {
     const int B = cam.tile_w * cam.tile_h / kPix;
     const int n_tiles = V * cam.T;
-    const int NB = B * kFwdBatch;  // records per batch: s0-s3, and a list per warp
-    const size_t sm = sizeof(float4) * 4 * (size_t)NB + sizeof(uint16_t) * (size_t)(B / 32) * NB;
+    const size_t sm = comp_smem(B, B * kFwdBatch, false);
     uint32_t *work = nullptr;
     int grid = n_tiles;
     if (persistent_ctas > 0) {
@@ -740,7 +750,7 @@ static cudaError_t composite_bwd_as(const RenderWs &ws, const uint32_t *ival, in
                                     cudaStream_t s) {
     const int B = cam.tile_w * cam.tile_h / kPix;
     const int n_tiles = V * cam.T;
-    const size_t sm = comp_smem(B, true, ACC);
+    const size_t sm = comp_smem(B, B * kBwdBatch, true, ACC);
     const void *kern = (const void *)composite_bwd_kernel<NV, ACC>;
     uint32_t *work = nullptr;
     int grid = n_tiles;

@@ -137,9 +137,8 @@ def test_geometric_backward_three_views_ragged():
 
 @pytest.mark.parametrize("tile", [(8, 16), (8, 8), (32, 8)])
 def test_backward_parity_other_tile_shapes(planes, planes_ref, tile):
-    """A one-warp tile (8x8, two pixels per thread) adds its sums of a Gaussian by
-    global atomics, larger tiles combine their warps' sums through per-warp
-    shared slots first: both match the oracle."""
+    """Other tile shapes (a one-warp 8x8 tile, two- and four-warp tiles) add
+    their warps' sums of a Gaussian by global atomics: all match the oracle."""
     ref, gm = planes_ref
     r, g, T, out = _gpu_forward(planes, tile_w=tile[0], tile_h=tile[1])
     grads, dpose = _gpu_backward(r, g, T, out, gm)
