@@ -53,7 +53,6 @@ constexpr int kPix = VPGS_PIX;
 #endif
 constexpr int kDirect = VPGS_BWD_DIRECT;  // at most this many active lanes: per-lane atomics, no reduction
 constexpr int kMaxThreads = 512;
-// list entries whose alphas the forward evaluates before blending them
 #ifndef VPGS_FWD_BATCH
 #define VPGS_FWD_BATCH 2  // records each forward thread stages per batch
 #endif
@@ -62,6 +61,7 @@ constexpr int kFwdBatch = VPGS_FWD_BATCH;
 #define VPGS_BWD_BATCH 2  // records each backward thread stages per batch
 #endif
 constexpr int kBwdBatch = VPGS_BWD_BATCH;
+// list entries whose alphas the forward evaluates before blending them
 #ifndef VPGS_FWD_WALK
 #define VPGS_FWD_WALK 2
 #endif
