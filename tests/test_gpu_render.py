@@ -161,6 +161,18 @@ def test_persistent_launch_is_bit_identical(planes):
         assert np.array_equal(a[k], b[k]), k
 
 
+def test_persistent_backward_matches_the_oracle(planes, planes_ref):
+    """Forward and backward with persistent CTAs pulling tiles from a work queue
+    (the autotuner's other launch form) match the oracle."""
+    ref, gm = planes_ref
+    r, g, T, out = _gpu_forward(planes, persistent_ctas=4)
+    assert_images_close(out, ref, ref["flags"], what="persistent")
+    grads, dpose = _gpu_backward(r, g, T, out, gm)
+    for k in GRAD_KEYS:
+        assert_grad_close(grads[k], ref["d_" + k], k)
+    assert_pose_close(dpose, ref["d_pose"])
+
+
 def test_multiview_pose_gradients_and_ragged_image():
     sc = scenes.random_gaussians(300, 97, 61, 80.0, seed=21, scale_range=(0.02, 0.2), n_views=3)
     g_up = scenes.upstream_grads(3, 3, 61, 97)
