@@ -9,7 +9,9 @@ xi = (rho, phi) in se(3), xi = -lr * g (plain step) or the Adam direction
 rho and phi.  Exp is the matrix exponential of the 4x4 twist [[phi^, rho], [0, 0]].
 
 Pins: tests/test_oracle_pose.py (Exp(0) = I, Exp(xi) Exp(-xi) = I, rotation
-part orthonormal with det 1, Rodrigues angle, hand-worked Adam steps).
+part orthonormal with det 1, Rodrigues angle, the closed-form rotation and V
+translation on random twists, the left update moving T_cw's translation,
+hand-worked first and second Adam steps).
 """
 from __future__ import annotations
 
