@@ -14,8 +14,9 @@ the colour term and over pixels for the depth term, then the mean over the m
 keyframes.  Adam is Kingma and Ba's, with bias correction.
 
 Pins (tests/test_oracle_fusion.py): zero loss and gradients for identical
-renders, a hand-worked 2-pixel case, central differences of the gradients,
-and Adam's first step (lr * g / (|g| + eps)) and a hand-worked second step.
+renders, a hand-worked 2-pixel case, the 1/m over keyframes (duplicated and
+zero-difference keyframes), central differences of the gradients, and Adam's
+first step (lr * g / (|g| + eps)) and a hand-worked second step.
 """
 from __future__ import annotations
 

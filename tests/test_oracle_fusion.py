@@ -66,3 +66,19 @@ def test_adam_first_and_second_step():
     vh = (0.999 * 0.001 * g * g + 0.001 * g2 * g2) / (1 - 0.999 ** 2)
     assert np.allclose(p2, p - 0.1 * mh / np.sqrt(vh), rtol=1e-14, atol=0)
     assert math.isclose(m2[0], 0.9 * 0.05 + 0.1, rel_tol=1e-15)
+
+
+def test_keyframes_are_averaged():
+    # Eq. 14's 1/m: two copies of the same keyframe pair give the loss of one
+    # (a sum over keyframes would double it), and a second keyframe with zero
+    # difference halves it
+    rng = np.random.default_rng(5)
+    a, b = rng.uniform(size=(1, 3, 4, 6)), rng.uniform(size=(1, 3, 4, 6))
+    da, db = rng.uniform(1, 2, size=(1, 4, 6)), rng.uniform(1, 2, size=(1, 4, 6))
+    one = oracle.distill_loss(a, b, da, db, grads=False)["L"]
+    two = oracle.distill_loss(np.concatenate([a, a]), np.concatenate([b, b]),
+                              np.concatenate([da, da]), np.concatenate([db, db]), grads=False)["L"]
+    half = oracle.distill_loss(np.concatenate([a, a]), np.concatenate([b, a]),
+                               np.concatenate([da, da]), np.concatenate([db, da]), grads=False)["L"]
+    assert abs(two - one) <= 1e-15 * one
+    assert abs(half - one / 2) <= 1e-15 * one
